@@ -1,0 +1,220 @@
+"""Stage DAGs of the benchmark pipelines, as plain data.
+
+A pipeline is the program the library compiles: a DAG of stages, each a
+per-pixel function of producer values at constant offsets (Jangda & Guha,
+PACT'20, Sec. 2.2 Fig. 2 and Sec. 2.3).  Each stage is a postfix program over
+taps ``("tap", slot, dx, dy, chan, mode)``; ``mode`` is "same" (P(x+dx, y+dy)),
+"down2" (P(2x+dx, 2y+dy)) or "up2" (P(floor(x/2)+dx, floor(y/2)+dy)), the
+constant dependence vectors that alignment and scaling produce (Sec. 5).
+
+Format::
+
+    {"name": str,
+     "inputs": [channels of pipeline input j, ...],
+     "stages": [{"name", "channels", "inputs": [producer ids], "ops": [...]}],
+     "outputs": [stage ids]}
+
+Producer ids: stage index >= 0, or -(j+1) for pipeline input j.
+"""
+from __future__ import annotations
+
+from typing import List, Sequence
+
+
+class E:
+    """Postfix expression under construction (operator overloading)."""
+
+    __slots__ = ("ops",)
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+
+    @staticmethod
+    def of(v) -> "E":
+        return v if isinstance(v, E) else E([("const", float(v))])
+
+    def _bin(self, other, op, swap=False):
+        a, b = (E.of(other), self) if swap else (self, E.of(other))
+        return E(a.ops + b.ops + [(op,)])
+
+    def __add__(self, o): return self._bin(o, "add")
+    def __radd__(self, o): return self._bin(o, "add", True)
+    def __sub__(self, o): return self._bin(o, "sub")
+    def __rsub__(self, o): return self._bin(o, "sub", True)
+    def __mul__(self, o): return self._bin(o, "mul")
+    def __rmul__(self, o): return self._bin(o, "mul", True)
+    def __truediv__(self, o): return self._bin(o, "div")
+    def __rtruediv__(self, o): return self._bin(o, "div", True)
+    def __neg__(self): return E(self.ops + [("neg",)])
+
+
+def emin(a, b) -> E: return E(E.of(a).ops + E.of(b).ops + [("min",)])
+def emax(a, b) -> E: return E(E.of(a).ops + E.of(b).ops + [("max",)])
+def eabs(a) -> E: return E(E.of(a).ops + [("abs",)])
+def esqrt(a) -> E: return E(E.of(a).ops + [("sqrt",)])
+
+
+XPAR = E([("xpar",)])
+YPAR = E([("ypar",)])
+
+
+def ref(producer: int, dx: int = 0, dy: int = 0, chan: int = -1, mode: str = "same") -> E:
+    """A read of `producer` (stage id, or input(j)) at a constant offset."""
+    return E([("ref", int(producer), int(dx), int(dy), int(chan), mode)])
+
+
+def input_id(j: int) -> int:
+    return -(j + 1)
+
+
+class Builder:
+    def __init__(self, name: str, input_channels: Sequence[int]):
+        self.p = {"name": name, "inputs": list(input_channels), "stages": [], "outputs": []}
+
+    def stage(self, name: str, expr: E, channels: int = 1) -> int:
+        producers: List[int] = []
+        ops = []
+        for t in E.of(expr).ops:
+            if t[0] == "ref":
+                _, pid, dx, dy, chan, mode = t
+                if pid not in producers:
+                    producers.append(pid)
+                ops.append(("tap", producers.index(pid), dx, dy, chan, mode))
+            else:
+                ops.append(t)
+        self.p["stages"].append({"name": name, "channels": int(channels),
+                                 "inputs": producers, "ops": ops})
+        return len(self.p["stages"]) - 1
+
+    def output(self, *sids: int):
+        self.p["outputs"].extend(sids)
+
+    def build(self) -> dict:
+        return self.p
+
+
+def linear(producer: int, weights, scale: float = 1.0, mode: str = "same",
+           chan: int = -1) -> E:
+    """sum_{j,i} weights[j][i] * P(x + i - rx, y + j - ry) * scale, written row by
+    row (rx, ry = half the kernel width/height); zero weights are skipped."""
+    rows = len(weights)
+    cols = len(weights[0])
+    ry, rx = rows // 2, cols // 2
+    total = None
+    for j in range(rows):
+        row = None
+        for i in range(cols):
+            w = float(weights[j][i])
+            if w == 0.0:
+                continue
+            t = ref(producer, i - rx, j - ry, chan, mode)
+            t = t if w == 1.0 else w * t
+            row = t if row is None else row + t
+        if row is not None:
+            total = row if total is None else total + row
+    if total is None:
+        total = E.of(0.0)
+    return total if scale == 1.0 else total * scale
+
+
+BINOMIAL5 = [1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16]
+SOBEL_X = [[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]]
+SOBEL_Y = [[-1, -2, -1], [0, 0, 0], [1, 2, 1]]
+BOX3 = [[1, 1, 1], [1, 1, 1], [1, 1, 1]]
+
+
+def sharpen() -> dict:
+    """3-stage sharpen: horizontal then vertical 5-tap binomial blur,
+    out = clamp(in + 1.5 (in - blur), 0, 1)."""
+    b = Builder("sharpen", [1])
+    inp = input_id(0)
+    bx = b.stage("bx", linear(inp, [BINOMIAL5]))
+    by = b.stage("by", linear(bx, [[w] for w in BINOMIAL5]))
+    v = ref(inp)
+    out = b.stage("sharpen", emin(emax(v + 1.5 * (v - ref(by)), 0.0), 1.0))
+    b.output(out)
+    return b.build()
+
+
+def harris(normalized: bool = True, k: float = 0.04) -> dict:
+    """11-stage corner response: Sobel Ix, Iy; Ixx, Iyy, Ixy; 3x3 box of each;
+    det, trace, R = det - k trace^2.  normalized: Sobel x 1/8, box x 1/9."""
+    b = Builder("harris" if normalized else "harris_raw", [1])
+    inp = input_id(0)
+    sx = 1.0 / 8 if normalized else 1.0
+    sb = 1.0 / 9 if normalized else 1.0
+    ix = b.stage("Ix", linear(inp, SOBEL_X, sx))
+    iy = b.stage("Iy", linear(inp, SOBEL_Y, sx))
+    ixx = b.stage("Ixx", ref(ix) * ref(ix))
+    iyy = b.stage("Iyy", ref(iy) * ref(iy))
+    ixy = b.stage("Ixy", ref(ix) * ref(iy))
+    sxx = b.stage("Sxx", linear(ixx, BOX3, sb))
+    syy = b.stage("Syy", linear(iyy, BOX3, sb))
+    sxy = b.stage("Sxy", linear(ixy, BOX3, sb))
+    det = b.stage("det", ref(sxx) * ref(syy) - ref(sxy) * ref(sxy))
+    tr = b.stage("trace", ref(sxx) + ref(syy))
+    r = b.stage("R", ref(det) - k * (ref(tr) * ref(tr)))
+    b.output(r)
+    return b.build()
+
+
+def _down(p: int) -> E:
+    return linear(p, [[bj * bi for bi in BINOMIAL5] for bj in BINOMIAL5], mode="down2")
+
+
+def _up(p: int) -> E:
+    """Half-pixel bilinear upsample: along each axis even 2i -> 0.75 P(i) +
+    0.25 P(i-1), odd 2i+1 -> 0.75 P(i) + 0.25 P(i+1); (1-par)/par select."""
+    def row(dy):
+        left = ref(p, -1, dy, mode="up2")
+        right = ref(p, 1, dy, mode="up2")
+        return 0.75 * ref(p, 0, dy, mode="up2") + 0.25 * ((1.0 - XPAR) * left + XPAR * right)
+    return 0.75 * row(0) + 0.25 * ((1.0 - YPAR) * row(-1) + YPAR * row(1))
+
+
+def blend(levels: int = 6, channels: int = 3) -> dict:
+    """Laplacian-pyramid blend of A and B under mask M (36 stages at 6 levels):
+    Gaussian levels by 5x5 binomial downsample, Laplacian L_k = G_k -
+    up(G_{k+1}) (L_top = G_top), BL_k = M_k L^A_k + (1 - M_k) L^B_k,
+    R_top = BL_top, R_k = BL_k + up(R_{k+1}); output R_0."""
+    b = Builder("blend", [channels, channels, 1])
+    ga, gb, gm = [input_id(0)], [input_id(1)], [input_id(2)]
+    for k in range(1, levels):
+        ga.append(b.stage("GA%d" % k, _down(ga[-1]), channels))
+    for k in range(1, levels):
+        gb.append(b.stage("GB%d" % k, _down(gb[-1]), channels))
+    for k in range(1, levels):
+        gm.append(b.stage("GM%d" % k, _down(gm[-1]), 1))
+    la, lb = [], []
+    for k in range(levels - 1):
+        la.append(b.stage("LA%d" % k, ref(ga[k]) - _up(ga[k + 1]), channels))
+    for k in range(levels - 1):
+        lb.append(b.stage("LB%d" % k, ref(gb[k]) - _up(gb[k + 1]), channels))
+    la.append(ga[-1])
+    lb.append(gb[-1])
+    bl = []
+    for k in range(levels):
+        m = ref(gm[k], chan=0)
+        bl.append(b.stage("BL%d" % k, m * ref(la[k]) + (1.0 - m) * ref(lb[k]), channels))
+    r = bl[-1]
+    for k in range(levels - 2, -1, -1):
+        r = b.stage("R%d" % k, ref(bl[k]) + _up(r), channels)
+    b.output(r)
+    return b.build()
+
+
+def blur3() -> dict:
+    """The paper's running example (Fig. 2): blurx = 3-tap mean along x,
+    blury = 3-tap mean of blurx along y."""
+    b = Builder("blur", [1])
+    inp = input_id(0)
+    bx = b.stage("blurx", (ref(inp, -1, 0) + ref(inp) + ref(inp, 1, 0)) / 3.0)
+    by = b.stage("blury", (ref(bx, 0, -1) + ref(bx) + ref(bx, 0, 1)) / 3.0)
+    b.output(by)
+    return b.build()
+
+
+def by_name(name: str) -> dict:
+    table = {"sharpen": sharpen, "harris": harris, "harris_raw": lambda: harris(False),
+             "blend": blend, "blur": blur3}
+    return table[name]()
