@@ -1,0 +1,211 @@
+/*
+ * wt.h -- C ABI of the warp-tiled image-pipeline library (GB300, sm_103a).
+ *
+ * The library executes a DAG of stencil, pointwise and down/up-sampling
+ * stages over images as fused groups of warp-sized overlapped tiles, after
+ * Jangda & Guha, "Model-Based Warp Overlapped Tiling for Image Processing
+ * Programs on GPUs" (PACT'20).  Section numbers below refer to that paper.
+ *
+ * Conventions for every entry point:
+ *   - Returns wt_status (WT_OK == 0); on failure wt_last_error() gives a
+ *     thread-local message.  No entry point aborts the process.
+ *   - Images are caller-owned.  Device images live in device memory of the
+ *     current CUDA device; "host" images live in host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Pointers named *out are written only on success.
+ */
+#ifndef WT_H
+#define WT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WT_OK = 0,
+  WT_EINVAL = -1,       /* malformed argument or DAG                         */
+  WT_ENOMEM = -2,       /* host or device allocation failed                  */
+  WT_ECUDA = -3,        /* a CUDA runtime/driver call failed                 */
+  WT_EUNSUPPORTED = -4, /* valid request this build does not implement       */
+  WT_ETIMEOUT = -5,     /* a device-side bounded wait gave up                */
+  WT_EDEVICE = -6,      /* a device-side check raised the error word         */
+  WT_ECOMPILE = -7      /* run-time compilation of a group kernel failed     */
+} wt_status;
+
+/* Storage types.  Arithmetic is always FP32; 16-bit types are storage only
+ * (round to nearest even on store, exact widening on load).               */
+typedef enum { WT_F32 = 0, WT_F16 = 1, WT_BF16 = 2 } wt_dtype;
+
+/* ------------------------------------------------------------ stage DAG -- */
+
+/* Postfix opcodes of a stage program (Sec. 2.2 Fig. 2: each stage is a
+ * per-point function of producer values).                                 */
+typedef enum {
+  WT_OP_CONST = 1, /* push `value`                                           */
+  WT_OP_TAP = 2,   /* push producer inputs[slot] at a constant offset        */
+  WT_OP_ADD = 3, WT_OP_SUB = 4, WT_OP_MUL = 5, WT_OP_DIV = 6,
+  WT_OP_MIN = 7, WT_OP_MAX = 8,
+  WT_OP_NEG = 9, WT_OP_ABS = 10, WT_OP_SQRT = 11,
+  WT_OP_XPAR = 12, /* push (x & 1) of the output point, as 0.0 or 1.0       */
+  WT_OP_YPAR = 13  /* push (y & 1) of the output point                      */
+} wt_opcode;
+
+/* How a tap maps the output point (x, y) to the producer point; these are
+ * the constant dependence vectors after alignment and scaling (Sec. 2.3,
+ * Sec. 5).  The producer coordinate is clamped to the producer's domain
+ * (clamp-to-edge at every producer read).                                  */
+typedef enum {
+  WT_TAP_SAME = 0,  /* P(x + dx, y + dy)                        */
+  WT_TAP_DOWN2 = 1, /* P(2x + dx, 2y + dy)   producer one level finer   */
+  WT_TAP_UP2 = 2    /* P(x/2 + dx, y/2 + dy) producer one level coarser */
+} wt_tapmode;
+
+typedef struct {
+  int32_t op;   /* wt_opcode                                                 */
+  int32_t slot; /* TAP: index into the stage's `inputs`                      */
+  int32_t dx, dy;
+  int32_t chan; /* TAP: producer channel; -1 = the output point's channel
+                   (channel 0 if the producer has one channel)              */
+  int32_t mode; /* TAP: wt_tapmode                                           */
+  float value;  /* CONST                                                     */
+} wt_op;
+
+typedef struct {
+  int32_t channels;      /* planes of this stage's output (>= 1)            */
+  int32_t n_inputs;
+  const int32_t *inputs; /* producer ids: stage index < this stage's index,
+                            or -(j+1) for pipeline input j                  */
+  int32_t n_ops;
+  const wt_op *ops;      /* postfix program, at most 256 ops, stack <= 32   */
+} wt_stage;
+
+/* An image: `channels` planes of height x width elements of `dtype`, rows
+ * `pitch_bytes` apart, plane c starting at data + c * height * pitch_bytes.
+ * pitch_bytes must be a multiple of 16 and data 16-byte aligned (TMA rule). */
+typedef struct {
+  void *data;
+  int32_t width, height, channels;
+  int32_t dtype; /* wt_dtype */
+  int64_t pitch_bytes;
+} wt_image;
+
+typedef struct wt_pipeline wt_pipeline;
+
+#define WT_BOUNDARY_CLAMP 0
+
+/* Builds a pipeline from a stage DAG (Sec. 2.2-2.3; Fig. 4 "Create DAG").
+ * stages are in topological order; input_channels[j] gives the planes of
+ * pipeline input j; outputs are stage ids.  All inputs share one width and
+ * height (level 0); a stage's level follows from its taps (DOWN2 +1, UP2
+ * -1) and level l has width ceil(W / 2^l).  Copies everything it needs.
+ * Errors: WT_EINVAL (cycle/forward reference, mixed levels, negative level,
+ * bad program, bad channel), WT_EUNSUPPORTED (boundary other than clamp). */
+wt_status wt_pipeline_create(const wt_stage *stages, int32_t n_stages,
+                             const int32_t *input_channels, int32_t n_inputs,
+                             const int32_t *outputs, int32_t n_outputs,
+                             int32_t boundary, wt_pipeline **out);
+
+wt_status wt_pipeline_destroy(wt_pipeline *p);
+
+/* ------------------------------------------------------------- schedule -- */
+
+/* Per-group execution parameters (Sec. 4 OTPW tile, Sec. 5 hybrid tiling). */
+typedef struct {
+  int32_t tile_h;          /* T_y: output rows per warp tile (>= 1)          */
+  int32_t warps_per_block; /* 1..16; warps are independent (no block sync)  */
+  float frac_reg;          /* fracReg in [0,1]: share of the group's
+                              intermediate window bytes kept in registers;
+                              the rest lives in the warp's shared memory    */
+  int32_t vec;             /* pixels per lane along x: 4 or 8 (0 = auto)     */
+  int32_t max_regs;        /* register cap per thread (0 = 255)             */
+  int32_t chunk_rows;      /* TMA staging rows per chunk (0 = 8)             */
+  int32_t n_buffers;       /* TMA staging buffers per input (0 = 3)          */
+} wt_group_params;
+
+typedef enum {
+  WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */
+  WT_EXEC_PLAIN = 1  /* one simple kernel per stage, every intermediate in
+                        HBM: the unfused "plain method" baseline            */
+} wt_exec;
+
+typedef struct {
+  int32_t exec;                  /* wt_exec                                  */
+  int32_t n_groups;              /* FUSED: groups in topological order       */
+  const int32_t *group_of_stage; /* FUSED: n_stages entries in [0, n_groups);
+                                    every group a contiguous run of stages   */
+  const wt_group_params *params; /* FUSED: n_groups entries (NULL: defaults) */
+  int32_t intermediate_dtype;    /* storage of HBM intermediates (wt_dtype);
+                                    -1 = dtype of the first input           */
+} wt_schedule_desc;
+
+/* Installs an explicit schedule.  Groups whose taps change level are run
+ * with the per-stage kernel.  Kernels are compiled lazily (NVRTC, sm_103a)
+ * on the first run of each group and cached per device.  WT_EINVAL if the
+ * grouping is not contiguous or parameters are out of range.              */
+wt_status wt_schedule(wt_pipeline *p, const wt_schedule_desc *desc);
+
+/* Cost models used by wt_schedule_auto (Sec. 6).                           */
+typedef enum {
+  WT_MODEL_ANALYTIC = 0, /* Alg. 2 weighted cost, DP over groupings          */
+  WT_MODEL_LEARNED = 1   /* 3-layer MLP trained on measured runtimes        */
+} wt_model;
+
+/* Picks grouping, tile heights and fracReg for images of the given size and
+ * storage type by DP-Fusion over contiguous groupings with the chosen cost
+ * model (Sec. 2.4, Sec. 6), then installs the schedule.                    */
+wt_status wt_schedule_auto(wt_pipeline *p, int32_t width, int32_t height,
+                           int32_t dtype, int32_t model);
+
+/* Reads back the installed schedule: n_groups, group_of_stage (n_stages
+ * entries, caller-allocated, may be NULL) and params (n_groups entries,
+ * caller-allocated, may be NULL).                                          */
+wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups,
+                          int32_t *group_of_stage, wt_group_params *params);
+
+/* ------------------------------------------------------------------ run -- */
+
+/* Runs the pipeline on device images, asynchronously on `stream`
+ * (Fig. 4 "CUDA code generation" output, Sec. 4-5 execution).  inputs[j]
+ * match input_channels[j]; outputs[k] must have the level/size/channels of
+ * stage outputs[k].  Input and output dtypes may differ.  The first run for
+ * a new image size allocates the library's device workspace and compiles
+ * the group kernels; later runs allocate nothing and may be captured in a
+ * CUDA graph.  Device-side failures are reported by wt_check().           */
+wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                 const wt_image *outputs, int32_t n_outputs, void *stream);
+
+/* Same computation with host buffers: copies inputs to device (inside the
+ * call), runs, copies outputs back and synchronizes `stream`.  Host images
+ * use the same layout rules; pinned memory makes the copies asynchronous. */
+wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                      const wt_image *outputs, int32_t n_outputs, void *stream);
+
+/* Batched serving: n_images independent runs (inputs[i*n_inputs + j],
+ * outputs[i*n_outputs + k]) of images of any sizes, executed by ONE
+ * persistent launch per group that pulls warp tiles from a device work
+ * queue.  The pipeline must have a single fused group whose taps keep one
+ * level.  Call once outside capture per batch shape, then it may be
+ * captured in a CUDA graph.                                                */
+wt_status wt_run_batch(wt_pipeline *p, const wt_image *inputs,
+                       const wt_image *outputs, int32_t n_images, void *stream);
+
+/* Synchronizes `stream` and reads the device error word of the pipeline:
+ * WT_ETIMEOUT if a bounded mbarrier/queue wait gave up, WT_EDEVICE for any
+ * other device-side check; clears the word.                                */
+wt_status wt_check(wt_pipeline *p, void *stream);
+
+/* Number of kernel launches one wt_run issues with the installed schedule. */
+int32_t wt_launches_per_run(const wt_pipeline *p);
+
+const char *wt_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t wt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,51 @@
+/*
+ * wt_debug.h -- introspection entry points of the warp-tiled pipeline
+ * library, for tests and tools.  They never launch GPU work.
+ */
+#ifndef WT_DEBUG_H
+#define WT_DEBUG_H
+
+#include "wt.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Size in bytes of the argument block every generated kernel takes. */
+int64_t wt_debug_args_size(void);
+
+/* Describes launch `launch_index` of the run plan that wt_run would build
+ * for these images with the installed schedule, without running it:
+ *   src/src_cap/src_len: generated CUDA source (NUL-terminated, truncated to
+ *                        src_cap-1 bytes; src_len gets the full length);
+ *   args/args_cap:       the kernel's argument block (wt_debug_args_size()
+ *                        bytes), with tensor maps left zero;
+ *   launch[8]:           grid x, y, z, threads per block, dynamic shared
+ *                        bytes, fused (1) or per-stage (0), launches in the
+ *                        plan, unroll factor;
+ *   kname:               the kernel's entry-point name.
+ * Image pointers may be host pointers.  WT_EUNSUPPORTED if the launch reads
+ * or writes the library workspace (intermediates between groups).          */
+wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *inputs,
+                          int32_t n_inputs, const wt_image *outputs, int32_t n_outputs, char *src,
+                          int64_t src_cap, int64_t *src_len, void *args, int64_t args_cap,
+                          int32_t *launch, char *kname, int64_t kname_cap);
+
+/* Compiles launch `launch_index` of that run plan with NVRTC for sm_103a
+ * (no GPU needed) and returns the CUBIN size; WT_ECOMPILE with the NVRTC
+ * log in wt_last_error() on failure.                                       */
+wt_status wt_debug_compile(wt_pipeline *p, int32_t launch_index, const wt_image *inputs,
+                           int32_t n_inputs, const wt_image *outputs, int32_t n_outputs,
+                           int64_t *cubin_bytes);
+
+/* Halo/window analysis of schedule group `group` (Sec. 4 overlap, Sec. 5
+ * parallelogram skew): out = [fusable, halo_l, halo_r, halo_t, halo_b,
+ * unroll, n_nodes, then per node: id, src_chan, is_source, is_liveout, top,
+ * bot, delay, window, xl*1000+xr, in_smem].  *n_out gets the length.        */
+wt_status wt_debug_group_geometry(wt_pipeline *p, int32_t group, int32_t vec, float frac_reg,
+                                  int32_t *out, int32_t cap, int32_t *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

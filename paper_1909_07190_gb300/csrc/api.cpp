@@ -1,0 +1,356 @@
+// C ABI entry points (include/wt.h, include/wt_debug.h).  Every entry point
+// converts internal errors to a wt_status and a thread-local message.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "wt.h"
+#include "wt_debug.h"
+#include "wt_jit.hpp"
+#include "wt_runtime.hpp"
+#include "wt_sched.hpp"
+
+struct wt_pipeline : wt::Pipeline {};
+
+namespace {
+using wt::fail;
+thread_local std::string g_err;
+
+template <class F>
+wt_status guard(F &&f) {
+  try {
+    f();
+    g_err.clear();
+    return WT_OK;
+  } catch (const wt::Error &e) {
+    g_err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    g_err = "host allocation failed";
+    return WT_ENOMEM;
+  } catch (const std::exception &e) {
+    g_err = e.what();
+    return WT_EINVAL;
+  }
+}
+
+void default_schedule(wt::Pipeline &p) {
+  p.sched = wt::Schedule();
+  p.sched.exec = WT_EXEC_FUSED;
+  p.sched.n_groups = 1;
+  p.sched.group_of_stage.assign(p.stages.size(), 0);
+  p.sched.params.assign(1, wt::GroupParams());
+  p.sched.installed = true;
+}
+
+void install(wt::Pipeline &p, const wt_schedule_desc *d) {
+  wt::Schedule s;
+  if (!d) fail(WT_EINVAL, "null schedule");
+  if (d->exec != WT_EXEC_FUSED && d->exec != WT_EXEC_PLAIN) fail(WT_EINVAL, "bad exec mode");
+  s.exec = d->exec;
+  s.intermediate_dtype = d->intermediate_dtype;
+  if (s.intermediate_dtype < -1 || s.intermediate_dtype > WT_BF16) fail(WT_EINVAL, "bad intermediate dtype");
+  const int n = (int)p.stages.size();
+  if (s.exec == WT_EXEC_FUSED) {
+    if (d->n_groups < 1 || d->n_groups > n) fail(WT_EINVAL, "n_groups out of range");
+    if (!d->group_of_stage) fail(WT_EINVAL, "group_of_stage is required");
+    s.n_groups = d->n_groups;
+    s.group_of_stage.assign(d->group_of_stage, d->group_of_stage + n);
+    // contiguous runs in topological order, numbered 0..n_groups-1
+    int cur = 0;
+    for (int i = 0; i < n; i++) {
+      int g = s.group_of_stage[i];
+      if (g < 0 || g >= s.n_groups) fail(WT_EINVAL, "group index out of range");
+      if (i == 0 && g != 0) fail(WT_EINVAL, "groups must be numbered in topological order");
+      if (g == cur) continue;
+      if (g != cur + 1) fail(WT_EINVAL, "every group must be a contiguous run of stages");
+      cur = g;
+    }
+    if (cur != s.n_groups - 1) fail(WT_EINVAL, "empty group");
+    s.params.assign(s.n_groups, wt::GroupParams());
+    if (d->params)
+      for (int g = 0; g < s.n_groups; g++) {
+        const wt_group_params &q = d->params[g];
+        wt::GroupParams &r = s.params[g];
+        if (q.tile_h < 1 || q.tile_h > 4096) fail(WT_EINVAL, "tile_h out of range");
+        if (q.warps_per_block < 1 || q.warps_per_block > 16) fail(WT_EINVAL, "warps_per_block out of range");
+        if (!(q.frac_reg >= 0.f && q.frac_reg <= 1.f)) fail(WT_EINVAL, "frac_reg out of [0,1]");
+        if (q.vec != 0 && q.vec != 4 && q.vec != 8) fail(WT_EINVAL, "vec must be 0, 4 or 8");
+        if (q.max_regs < 0 || q.max_regs > 255) fail(WT_EINVAL, "max_regs out of range");
+        if (q.chunk_rows < 0 || q.chunk_rows > 64) fail(WT_EINVAL, "chunk_rows out of range");
+        if (q.n_buffers < 0 || q.n_buffers > 8) fail(WT_EINVAL, "n_buffers out of range");
+        r.tile_h = q.tile_h;
+        r.warps_per_block = q.warps_per_block;
+        r.frac_reg = q.frac_reg;
+        r.vec = q.vec;
+        r.max_regs = q.max_regs;
+        r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
+        r.n_buffers = q.n_buffers ? q.n_buffers : 3;
+      }
+  } else {
+    s.n_groups = n;
+    s.group_of_stage.resize(n);
+    for (int i = 0; i < n; i++) s.group_of_stage[i] = i;
+    s.params.assign(n, wt::GroupParams());
+  }
+  s.installed = true;
+  p.sched = s;
+}
+
+int64_t image_bytes(const wt_image &im) {
+  return im.pitch_bytes * (int64_t)im.height * im.channels;
+}
+}  // namespace
+
+extern "C" {
+
+const char *wt_last_error(void) { return g_err.c_str(); }
+
+int32_t wt_version(void) { return 100; }
+
+wt_status wt_pipeline_create(const wt_stage *stages, int32_t n_stages, const int32_t *input_channels,
+                             int32_t n_inputs, const int32_t *outputs, int32_t n_outputs, int32_t boundary,
+                             wt_pipeline **out) {
+  return guard([&] {
+    if (!out) wt::fail(WT_EINVAL, "null out");
+    if (boundary != WT_BOUNDARY_CLAMP) wt::fail(WT_EUNSUPPORTED, "only the clamp-to-edge boundary is supported");
+    auto p = std::make_unique<wt_pipeline>();
+    wt::build_pipeline(*p, stages, n_stages, input_channels, n_inputs, outputs, n_outputs);
+    default_schedule(*p);
+    *out = p.release();
+  });
+}
+
+wt_status wt_pipeline_destroy(wt_pipeline *p) {
+  return guard([&] { delete p; });
+}
+
+wt_status wt_schedule(wt_pipeline *p, const wt_schedule_desc *desc) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    std::lock_guard<std::mutex> lk(p->mu);
+    install(*p, desc);
+  });
+}
+
+wt_status wt_schedule_auto(wt_pipeline *p, int32_t width, int32_t height, int32_t dtype, int32_t model) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    if (width < 1 || height < 1) wt::fail(WT_EINVAL, "bad size");
+    if (dtype < WT_F32 || dtype > WT_BF16) wt::fail(WT_EINVAL, "bad dtype");
+    if (model != WT_MODEL_ANALYTIC && model != WT_MODEL_LEARNED) wt::fail(WT_EINVAL, "bad model");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::Schedule s = wt::auto_schedule(*p, width, height, dtype, model);
+    p->sched = s;
+  });
+}
+
+wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups, int32_t *group_of_stage,
+                          wt_group_params *params) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    const wt::Schedule &s = p->sched;
+    if (exec) *exec = s.exec;
+    if (n_groups) *n_groups = s.n_groups;
+    if (group_of_stage)
+      for (size_t i = 0; i < p->stages.size(); i++) group_of_stage[i] = s.group_of_stage[i];
+    if (params)
+      for (int g = 0; g < s.n_groups; g++) {
+        const wt::GroupParams &r = s.params[g];
+        params[g].tile_h = r.tile_h;
+        params[g].warps_per_block = r.warps_per_block;
+        params[g].frac_reg = r.frac_reg;
+        params[g].vec = r.vec;
+        params[g].max_regs = r.max_regs;
+        params[g].chunk_rows = r.chunk_rows;
+        params[g].n_buffers = r.n_buffers;
+      }
+  });
+}
+
+wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                 int32_t n_outputs, void *stream) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    if (!inputs || !outputs) wt::fail(WT_EINVAL, "null image array");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
+    wt::run_plan(*p, plan, (cudaStream_t)stream);
+  });
+}
+
+wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                      int32_t n_outputs, void *stream) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    if (!inputs || !outputs || n_inputs < 1 || n_outputs < 1 || n_inputs > 16 || n_outputs > 16)
+      wt::fail(WT_EINVAL, "bad image arrays");
+    std::lock_guard<std::mutex> lk(p->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    wt::Workspace &w = wt::workspace(*p, 0);
+    std::vector<wt_image> din(inputs, inputs + n_inputs), dout(outputs, outputs + n_outputs);
+    auto stage = [&](int key, const wt_image &h) -> void * {
+      int64_t need = image_bytes(h);
+      wt::Staging &s = w.staging[key];
+      if (s.bytes < need) {
+        if (s.ptr) {
+          wt::check_rt(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+          cudaFree(s.ptr);
+          s.ptr = nullptr;
+          s.bytes = 0;
+        }
+        if (cudaMalloc(&s.ptr, (size_t)need) != cudaSuccess) {
+          cudaGetLastError();
+          wt::fail(WT_ENOMEM, "cannot allocate staging buffer");
+        }
+        s.bytes = need;
+      }
+      return s.ptr;
+    };
+    for (int j = 0; j < n_inputs; j++) {
+      if (!inputs[j].data) wt::fail(WT_EINVAL, "null host input");
+      din[j].data = stage(j, inputs[j]);
+      wt::check_rt(cudaMemcpyAsync(din[j].data, inputs[j].data, (size_t)image_bytes(inputs[j]),
+                                   cudaMemcpyHostToDevice, st),
+                   "cudaMemcpyAsync(H2D)");
+    }
+    for (int k = 0; k < n_outputs; k++) {
+      if (!outputs[k].data) wt::fail(WT_EINVAL, "null host output");
+      dout[k].data = stage(100 + k, outputs[k]);
+    }
+    wt::RunPlan plan = wt::build_plan(*p, din.data(), n_inputs, dout.data(), n_outputs);
+    wt::run_plan(*p, plan, st);
+    for (int k = 0; k < n_outputs; k++)
+      wt::check_rt(cudaMemcpyAsync(outputs[k].data, dout[k].data, (size_t)image_bytes(outputs[k]),
+                                   cudaMemcpyDeviceToHost, st),
+                   "cudaMemcpyAsync(D2H)");
+    wt::check_rt(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  });
+}
+
+wt_status wt_run_batch(wt_pipeline *p, const wt_image *inputs, const wt_image *outputs, int32_t n_images,
+                       void *stream) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    if (!inputs || !outputs || n_images < 1) wt::fail(WT_EINVAL, "bad batch");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::run_batch(*p, inputs, outputs, n_images, (cudaStream_t)stream);
+  });
+}
+
+wt_status wt_check(wt_pipeline *p, void *stream) {
+  wt_status st = WT_OK;
+  wt_status rc = guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    wt::check_rt(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    if (!p->ws) return;
+    int32_t v = 0;
+    wt::check_rt(cudaMemcpy(&v, p->ws->err, sizeof v, cudaMemcpyDeviceToHost), "cudaMemcpy(error word)");
+    if (v != 0) {
+      wt::check_rt(cudaMemset(p->ws->err, 0, sizeof v), "cudaMemset");
+      st = v == 1 ? WT_ETIMEOUT : WT_EDEVICE;
+    }
+  });
+  if (rc != WT_OK) return rc;
+  if (st != WT_OK) g_err = st == WT_ETIMEOUT ? "a device-side bounded wait gave up" : "device-side check failed";
+  return st;
+}
+
+int32_t wt_launches_per_run(const wt_pipeline *p) {
+  if (!p) return -1;
+  int32_t n = 0;
+  wt_status rc = guard([&] {
+    auto groups = wt::schedule_groups(*p);
+    for (size_t gi = 0; gi < groups.size(); gi++) {
+      bool fused = p->sched.exec == WT_EXEC_FUSED &&
+                   wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable;
+      if (fused) {
+        n++;
+      } else {
+        for (int s : groups[gi])
+          if (!p->consumers[s].empty() || p->is_output[s]) n++;
+      }
+    }
+  });
+  return rc == WT_OK ? n : -1;
+}
+
+// ------------------------------------------------------------- debug API
+
+int64_t wt_debug_args_size(void) { return (int64_t)sizeof(wt::KernelArgs); }
+
+wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, int32_t n_inputs,
+                          const wt_image *outputs, int32_t n_outputs, char *src, int64_t src_cap,
+                          int64_t *src_len, void *args, int64_t args_cap, int32_t *launch, char *kname,
+                          int64_t kname_cap) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
+    if (launch_index < 0 || launch_index >= (int)plan.launches.size()) wt::fail(WT_EINVAL, "launch index");
+    const wt::Launch &L = plan.launches[launch_index];
+    std::string s = wt::launch_source(*p, L);
+    if (src_len) *src_len = (int64_t)s.size();
+    if (src && src_cap > 0) {
+      size_t n = std::min((size_t)src_cap - 1, s.size());
+      memcpy(src, s.data(), n);
+      src[n] = 0;
+    }
+    if (args) {
+      if (args_cap < (int64_t)sizeof(wt::KernelArgs)) wt::fail(WT_EINVAL, "args buffer too small");
+      wt::KernelArgs a;
+      wt::fill_args(*p, plan, L, nullptr, a, false);
+      memcpy(args, &a, sizeof a);
+    }
+    if (launch) {
+      launch[0] = (int32_t)L.grid[0];
+      launch[1] = (int32_t)L.grid[1];
+      launch[2] = (int32_t)L.grid[2];
+      launch[3] = L.block;
+      launch[4] = L.smem;
+      launch[5] = L.fused ? 1 : 0;
+      launch[6] = (int32_t)plan.launches.size();
+      launch[7] = L.fused ? L.geom.unroll : 0;
+    }
+    if (kname && kname_cap > 0) {
+      size_t n = std::min((size_t)kname_cap - 1, L.kname.size());
+      memcpy(kname, L.kname.data(), n);
+      kname[n] = 0;
+    }
+  });
+}
+
+wt_status wt_debug_compile(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, int32_t n_inputs,
+                           const wt_image *outputs, int32_t n_outputs, int64_t *cubin_bytes) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
+    if (launch_index < 0 || launch_index >= (int)plan.launches.size()) wt::fail(WT_EINVAL, "launch index");
+    const wt::Launch &L = plan.launches[launch_index];
+    std::string cubin = wt::compile_cubin(wt::launch_source(*p, L), L.kname, L.key.max_regs);
+    if (cubin_bytes) *cubin_bytes = (int64_t)cubin.size();
+  });
+}
+
+wt_status wt_debug_group_geometry(wt_pipeline *p, int32_t group, int32_t vec, float frac_reg, int32_t *out,
+                                  int32_t cap, int32_t *n_out) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    auto groups = wt::schedule_groups(*p);
+    if (group < 0 || group >= (int)groups.size()) wt::fail(WT_EINVAL, "group index");
+    wt::GroupGeom g = wt::analyze_group(*p, groups[group], vec, frac_reg, 4);
+    std::vector<int32_t> v = {g.fusable ? 1 : 0, g.halo_l, g.halo_r, g.halo_t, g.halo_b, g.unroll,
+                              (int32_t)g.nodes.size()};
+    for (const wt::Node &n : g.nodes) {
+      int32_t rec[10] = {n.id, n.src_chan, n.is_source, n.is_liveout, n.top, n.bot, n.delay, n.window,
+                         n.xl * 1000 + n.xr, n.in_smem};
+      v.insert(v.end(), rec, rec + 10);
+    }
+    if (n_out) *n_out = (int32_t)v.size();
+    if (out)
+      for (int i = 0; i < (int)v.size() && i < cap; i++) out[i] = v[i];
+  });
+}
+
+}  // extern "C"

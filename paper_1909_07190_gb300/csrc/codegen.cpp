@@ -1,0 +1,710 @@
+// CUDA source generation for group kernels (Fig. 4 "CUDA Code Generation").
+//
+// Fused groups (OTPW + hybrid tiling, Sec. 4-5, Alg. 1 / Alg. 3 in the
+// streaming form described in analysis.cpp):
+//   * one warp = one overlapped tile: 32 lanes along x, V pixels per lane
+//     (128-bit accesses), tile_h output rows; warps never synchronise with
+//     each other, and a warp only uses __syncwarp / shuffles (Sec. 4);
+//   * the tile's source rows (tile + halo) are staged by TMA into the warp's
+//     shared-memory ring, chunk by chunk, completion on per-buffer
+//     mbarriers, with bounded waits;
+//   * the warp walks the parallelogram tiles (skewed rows) in order; each
+//     stage keeps its last `window` rows either in registers (explicitly
+//     named scalars, rotated by unrolling: D4 of the paper) or in a
+//     shared-memory ring (the hybrid split, fracReg);
+//   * producer loads become the four load types of Sec. 5 / Fig. 5: own
+//     register (1), shared memory (2), another lane's register of the same
+//     parallelogram row via __shfl (3), another lane's register of an
+//     earlier parallelogram row (4: the neighbour values shuffled when that
+//     row was produced);
+//   * clamp-to-edge at every producer read: border tiles replicate edge
+//     rows/columns of each stage (and clamp ring reads), interior tiles run
+//     a guard-free body in the steady state.
+// Plain groups: one simple kernel per stage reading producers from global
+// memory with clamped scalar loads (the unfused baseline).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <set>
+#include <functional>
+#include <sstream>
+
+#include "wt_internal.hpp"
+
+namespace wt {
+
+std::string CodegenKey::str() const {
+  std::ostringstream s;
+  s << (plain ? "P" : "F") << (persistent ? "b" : "") << "|v" << vec << "|f" << frac_reg
+    << "|r" << max_regs << "|w" << nw << "|c" << chunk << "|n" << nbuf << "|s";
+  for (int x : stages) s << x << ",";
+  s << "|i";
+  for (int x : src_dtypes) s << x;
+  s << "|o";
+  for (int x : dst_dtypes) s << x;
+  return s.str();
+}
+
+static const char *tname(int dtype) {
+  return dtype == WT_F32 ? "f32" : (dtype == WT_F16 ? "f16" : "bf16");
+}
+
+static std::string flt(float v) {
+  if (std::isnan(v)) return "__int_as_float(0x7fc00000)";
+  if (std::isinf(v)) return v > 0 ? "__int_as_float(0x7f800000)" : "__int_as_float(0xff800000)";
+  char b[64];
+  snprintf(b, sizeof b, "%.9g", (double)v);
+  std::string s(b);
+  if (s.find_first_of(".e") == std::string::npos) s += ".0";
+  return "(" + s + "f)";
+}
+
+static int align_up(int v, int a) { return (v + a - 1) / a * a; }
+
+FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key) {
+  FusedLayout L;
+  L.V = key.vec;
+  const int V = L.V;
+  L.lpad = V * ((g.halo_l + V - 1) / V);
+  L.rpad = V * ((g.halo_r + V - 1) / V);
+  L.out_w = 32 * V - L.lpad - L.rpad;
+  if (L.out_w < V)
+    fail(WT_EUNSUPPORTED, "group halo (" + std::to_string(g.halo_l) + "+" +
+                              std::to_string(g.halo_r) + " px) too wide for a warp tile");
+  L.chunk = std::max({key.chunk, g.halo_t + 1, g.max_src_window});
+  L.nbuf = std::max(2, key.nbuf);
+  L.ring = L.chunk * L.nbuf;
+  int nsx = g.halo_b;
+  for (const Node &n : g.nodes)
+    if (!n.is_source) nsx = std::max(nsx, n.bot + n.delay);
+  L.nsx = nsx;
+  L.src_rows_extra = g.halo_b;
+  int off = 0;
+  int n_src = 0;
+  for (const Node &n : g.nodes)
+    if (n.is_source) n_src++;
+  L.chunk_bytes = 0;
+  for (int s = 0; s < n_src; s++) {
+    int dt = key.src_dtypes.at(s);
+    int esz = elem_bytes(dt);
+    int A = 16 / esz;
+    int boxw = 32 * V + ((V % A) ? A : 0);
+    if (boxw > 256) fail(WT_EUNSUPPORTED, "TMA box wider than 256 elements");
+    off = align_up(off, 128);
+    L.boxw.push_back(boxw);
+    L.esz.push_back(esz);
+    L.ring_off.push_back(off);
+    off += L.nbuf * L.chunk * boxw * esz;
+    L.chunk_bytes += L.chunk * boxw * esz;
+  }
+  L.win_off.assign(g.nodes.size(), -1);
+  for (size_t i = 0; i < g.nodes.size(); i++) {
+    const Node &n = g.nodes[i];
+    if (n.is_source || !n.in_smem) continue;
+    off = align_up(off, 16);
+    L.win_off[i] = off;
+    off += n.window * 32 * V * 4;
+  }
+  off = align_up(off, 8);
+  L.bar_off = off;
+  off += 8 * L.nbuf;
+  L.warp_bytes = align_up(off, 128);
+  return L;
+}
+
+namespace {
+
+struct Ctx {
+  const Pipeline &p;
+  const GroupGeom &g;
+  const CodegenKey &key;
+  const FusedLayout &L;
+  std::ostringstream o;
+  int V, U, n_src;
+  std::vector<int> ks;   // per node: first active step (constant)
+  std::vector<int> kec;  // per node: last active step minus tile_h
+  Ctx(const Pipeline &p_, const GroupGeom &g_, const CodegenKey &k_, const FusedLayout &L_)
+      : p(p_), g(g_), key(k_), L(L_) {}
+};
+
+std::string reg(int ni, int slot, int j) {
+  return "R" + std::to_string(ni) + "_" + std::to_string(slot) + "_" + std::to_string(j);
+}
+std::string tmp(int ni, int a, int j) {
+  return "T" + std::to_string(ni) + "_" + std::to_string(a) + "_" + std::to_string(j);
+}
+
+int slot_of(const Node &n, int u, int a) {
+  if (a < 0 || a >= n.window) fail(WT_EINVAL, "internal: window age out of range");
+  if (n.rotate) return ((u - a) % n.window + n.window) % n.window;
+  return n.window - 1 - a;
+}
+
+int width_of(const Node &n, int V) { return V + n.xl + n.xr; }
+
+// x-fixup of the values `v` (clamp-to-edge along x inside border tiles).
+void emit_xfix(Ctx &c, const std::vector<std::string> &v) {
+  const int V = c.V;
+  auto &o = c.o;
+  o << "if (xs < 0) { const int l0_ = (-xs) / " << V << "; const float b0_ = __shfl_sync(WT_FULL, "
+    << v[0] << ", l0_); if (lane < l0_) {";
+  for (int e = 0; e < V; e++) o << " " << v[e] << " = b0_;";
+  o << " } }\n";
+  o << "if (xs + " << 32 * V << " > W) { const int xl_ = W - 1 - xs; const int ll_ = xl_ / " << V
+    << "; const int el_ = xl_ - ll_ * " << V << "; float s_ = " << v[0] << ";";
+  for (int e = 1; e < V; e++) o << " if (el_ == " << e << ") s_ = " << v[e] << ";";
+  o << " const float bl_ = __shfl_sync(WT_FULL, s_, ll_); const int xb_ = xs + lane * " << V << ";";
+  for (int e = 0; e < V; e++) o << " if (xb_ + " << e << " > W - 1) " << v[e] << " = bl_;";
+  o << " }\n";
+}
+
+// Neighbour columns by warp shuffles: type (3) loads of Sec. 5.
+void emit_extend(Ctx &c, const Node &n, const std::vector<std::string> &v,
+                 const std::function<std::string(int)> &tgt) {
+  const int V = c.V;
+  for (int off = -n.xl; off < 0; off++) {
+    int q = -((-off + V - 1) / V);
+    int el = off - q * V;
+    c.o << tgt(n.xl + off) << " = __shfl_up_sync(WT_FULL, " << v[el] << ", " << -q << ");\n";
+  }
+  for (int off = V; off < V + n.xr; off++) {
+    int q = off / V;
+    int el = off - q * V;
+    c.o << tgt(n.xl + off) << " = __shfl_down_sync(WT_FULL, " << v[el] << ", " << q << ");\n";
+  }
+  for (int e = 0; e < V; e++) c.o << tgt(n.xl + e) << " = " << v[e] << ";\n";
+}
+
+void emit_load_vec(Ctx &c, int dtype, const std::string &addr, const std::vector<std::string> &v,
+                   int esz) {
+  for (int b = 0; b < c.V; b += 4)
+    c.o << "wt_ld4_" << tname(dtype) << "((const void *)(" << addr << " + " << b * esz << "), "
+        << v[b] << ", " << v[b + 1] << ", " << v[b + 2] << ", " << v[b + 3] << ");\n";
+}
+
+std::vector<std::string> names(const std::string &base, int n) {
+  std::vector<std::string> r;
+  for (int i = 0; i < n; i++) r.push_back(base + std::to_string(i));
+  return r;
+}
+
+// Shift register windows (non-rotating nodes) by one row.
+void emit_shift(Ctx &c, int ni) {
+  const Node &n = c.g.nodes[ni];
+  if (n.in_smem || n.rotate || n.window < 2) return;
+  int wd = width_of(n, c.V);
+  for (int s = 0; s + 1 < n.window; s++)
+    for (int j = 0; j < wd; j++) c.o << reg(ni, s, j) << " = " << reg(ni, s + 1, j) << ";\n";
+}
+
+// Row of a register-resident source, loaded from the TMA ring.
+void emit_source_row(Ctx &c, int ni, bool safe, int u) {
+  const Node &n = c.g.nodes[ni];
+  auto &o = c.o;
+  const int V = c.V;
+  int s = n.src_index;
+  emit_shift(c, ni);
+  o << "{\n";
+  if (safe) o << "if (k < nsrc) {\n";
+  if (safe) o << "const int ri = wt_clampi(y_top + k, 0, H - 1) - y_top;\n";
+  else o << "const int ri = k;\n";
+  std::vector<std::string> v = names("e", V);
+  o << "float";
+  for (int e = 0; e < V; e++) o << (e ? ", " : " ") << v[e];
+  o << ";\n";
+  emit_load_vec(c, c.key.src_dtypes[s], "lp" + std::to_string(s) + " + (ri % RING) * ROWB" +
+                                            std::to_string(s), v, c.L.esz[s]);
+  if (safe) emit_xfix(c, v);
+  int sl = slot_of(n, u, 0);
+  emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
+  if (safe) o << "}\n";
+  o << "}\n";
+}
+
+// Loads row (age a) of a shared-memory node into temporaries T<ni>_<a>_*.
+void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
+  const Node &n = c.g.nodes[ni];
+  auto &o = c.o;
+  const int V = c.V;
+  o << "{\n";
+  std::vector<std::string> v = names("q", V);
+  o << "float";
+  for (int e = 0; e < V; e++) o << (e ? ", " : " ") << v[e];
+  o << ";\n";
+  if (n.is_source) {
+    int s = n.src_index;
+    o << "int ri = k - " << a << ";\n";
+    if (safe) o << "ri = wt_clampi(y_top + ri, 0, H - 1) - y_top;\n";
+    emit_load_vec(c, c.key.src_dtypes[s], "lp" + std::to_string(s) + " + (ri % RING) * ROWB" +
+                                              std::to_string(s), v, c.L.esz[s]);
+    if (safe) emit_xfix(c, v);
+  } else {
+    o << "int kk = k - " << a << ";\n";
+    if (safe)
+      o << "{ const int rr = wt_clampi(y_top + kk - (" << n.delay << "), 0, H - 1); kk = rr - y_top + ("
+        << n.delay << "); }\n";
+    o << "const int sl = ((kk % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
+    emit_load_vec(c, WT_F32, "sp" + std::to_string(ni) + " + sl * " + std::to_string(32 * V * 4), v, 4);
+  }
+  emit_extend(c, n, v, [&](int j) { return tmp(ni, a, j); });
+  o << "}\n";
+}
+
+// Postfix program of stage `sid` -> C++ expression for element e.
+std::string emit_expr(Ctx &c, int sid, int ni_c, int e, int u) {
+  const Stage &S = c.p.stages[sid];
+  const Node &cn = c.g.nodes[ni_c];
+  std::vector<std::string> st;
+  for (const Op &op : S.ops) {
+    switch (op.op) {
+      case WT_OP_CONST: st.push_back(flt(op.value)); break;
+      case WT_OP_XPAR: st.push_back(flt((float)(e & 1))); break;
+      case WT_OP_YPAR: st.push_back("((float)(r & 1))"); break;
+      case WT_OP_TAP: {
+        int pid = S.inputs[op.slot];
+        int pc = pid >= 0 ? c.p.stages[pid].channels : c.p.in_channels[-pid - 1];
+        bool inside = pid >= 0 && std::find(c.g.stages.begin(), c.g.stages.end(), pid) != c.g.stages.end();
+        int spec = inside ? -1 : (pc == 1 ? 0 : op.chan);
+        int pi = c.g.node_of(pid, spec);
+        if (pi < 0) fail(WT_EINVAL, "internal: tap node not found");
+        const Node &pn = c.g.nodes[pi];
+        int a = cn.delay - pn.delay - op.dy;
+        int j = pn.xl + e + op.dx;
+        if (j < 0 || j >= width_of(pn, c.V)) fail(WT_EINVAL, "internal: tap column out of range");
+        if (pn.in_smem) st.push_back(tmp(pi, a, j));
+        else st.push_back(reg(pi, slot_of(pn, u, a), j));
+      } break;
+      case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
+      case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
+      case WT_OP_SQRT: st.back() = "sqrtf(" + st.back() + ")"; break;
+      default: {
+        std::string b = st.back();
+        st.pop_back();
+        std::string a = st.back();
+        st.pop_back();
+        const char *f = nullptr;
+        switch (op.op) {
+          case WT_OP_ADD: st.push_back("(" + a + " + " + b + ")"); break;
+          case WT_OP_SUB: st.push_back("(" + a + " - " + b + ")"); break;
+          case WT_OP_MUL: st.push_back("(" + a + " * " + b + ")"); break;
+          case WT_OP_DIV: st.push_back("(" + a + " / " + b + ")"); break;
+          case WT_OP_MIN: f = "fminf"; break;
+          case WT_OP_MAX: f = "fmaxf"; break;
+          default: fail(WT_EINVAL, "internal: opcode");
+        }
+        if (f) st.push_back(std::string(f) + "(" + a + ", " + b + ")");
+      }
+    }
+  }
+  return st.back();
+}
+
+// (producer node, age) pairs a stage reads from shared-memory windows.
+std::vector<std::pair<int, int>> smem_reads(Ctx &c, int sid, int ni_c) {
+  std::vector<std::pair<int, int>> r;
+  const Stage &S = c.p.stages[sid];
+  for (const Op &op : S.ops) {
+    if (op.op != WT_OP_TAP) continue;
+    int pid = S.inputs[op.slot];
+    int pc = pid >= 0 ? c.p.stages[pid].channels : c.p.in_channels[-pid - 1];
+    bool inside = pid >= 0 && std::find(c.g.stages.begin(), c.g.stages.end(), pid) != c.g.stages.end();
+    int spec = inside ? -1 : (pc == 1 ? 0 : op.chan);
+    int pi = c.g.node_of(pid, spec);
+    if (!c.g.nodes[pi].in_smem) continue;
+    std::pair<int, int> pr{pi, c.g.nodes[ni_c].delay - c.g.nodes[pi].delay - op.dy};
+    if (std::find(r.begin(), r.end(), pr) == r.end()) r.push_back(pr);
+  }
+  return r;
+}
+
+void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
+  const Node &n = c.g.nodes[ni];
+  auto &o = c.o;
+  const int V = c.V;
+  int dt = c.key.dst_dtypes.at(n.dst_index);
+  int esz = elem_bytes(dt);
+  bool rowcheck = safe || n.top > 0 || n.bot > 0;
+  o << "{\n";
+  if (rowcheck) o << "if (r >= y0 && r < y0 + T && r < H)\n";
+  if (n.channels == 1 && c.g.channels > 1) o << "if (ch == 0)\n";
+  o << "{ const int x = xs + lane * " << V << ";\n";
+  o << "if (lane >= " << c.L.lpad / V << " && lane < " << 32 - c.L.rpad / V << ") {\n";
+  std::string d = "a.dst[" + std::to_string(n.dst_index) + "]";
+  o << "unsigned char *op_ = (unsigned char *)" << d << ".ptr + (wt_i64)"
+    << (n.channels > 1 ? "ch" : "0") << " * " << d << ".plane + (wt_i64)r * " << d
+    << ".pitch + (wt_i64)x * " << esz << ";\n";
+  auto vec_store = [&]() {
+    for (int b = 0; b < V; b += 4)
+      o << "wt_st4_" << tname(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", "
+        << v[b + 2] << ", " << v[b + 3] << ");\n";
+  };
+  if (!safe) {
+    vec_store();
+  } else {
+    o << "if (x + " << V << " <= W) {\n";
+    vec_store();
+    o << "} else {\n";
+    for (int e = 0; e < V; e++)
+      o << "if (x + " << e << " < W) wt_st1_" << tname(dt) << "(op_ + " << e * esz << ", " << v[e]
+        << ");\n";
+    o << "}\n";
+  }
+  o << "} } }\n";
+}
+
+void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> &loaded) {
+  const Node &n = c.g.nodes[ni];
+  auto &o = c.o;
+  const int V = c.V;
+  int sid = n.id;
+  emit_shift(c, ni);
+  if (safe)
+    o << "if (k >= " << c.ks[ni] << " && k <= T + (" << c.kec[ni] << ")) {\n";
+  o << "{\n";
+  o << "const int r = y_top + k - (" << n.delay << ");\n";
+  o << "(void)r;\n";
+  for (auto &pr : smem_reads(c, sid, ni)) {
+    if (!safe && loaded.count(pr)) continue;
+    emit_load_tmp(c, pr.first, pr.second, safe);
+    if (!safe) loaded.insert(pr);
+  }
+  std::vector<std::string> v = names("v", V);
+  o << "float";
+  for (int e = 0; e < V; e++) o << (e ? ", " : " ") << v[e];
+  o << ";\n";
+  if (safe) {
+    o << "if (r > H - 1) {\n";
+    if (n.in_smem) {
+      o << "const int sl = (((k - 1) % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
+      emit_load_vec(c, WT_F32, "sp" + std::to_string(ni) + " + sl * " + std::to_string(32 * V * 4), v, 4);
+    } else {
+      int prev = n.rotate ? slot_of(n, u, n.window > 1 ? 1 : 0) : n.window - 1;
+      for (int e = 0; e < V; e++) o << v[e] << " = " << reg(ni, prev, n.xl + e) << ";\n";
+    }
+    o << "} else {\n";
+  }
+  for (int e = 0; e < V; e++) o << v[e] << " = " << emit_expr(c, sid, ni, e, u) << ";\n";
+  if (safe) {
+    o << "}\n";
+    emit_xfix(c, v);
+  }
+  if (n.in_smem) {
+    o << "{ const int sl = ((k % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
+    for (int b = 0; b < V; b += 4)
+      o << "wt_st4_f32(sp" << ni << " + sl * " << 32 * V * 4 << " + " << b * 4 << ", " << v[b] << ", "
+        << v[b + 1] << ", " << v[b + 2] << ", " << v[b + 3] << ");\n";
+    o << "}\n";
+  } else {
+    int sl = slot_of(n, u, 0);
+    emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
+    if (safe && n.window > 1) {
+      o << "if (r == 0) {\n";
+      int wd = width_of(n, V);
+      for (int a = 1; a < n.window; a++) {
+        int s2 = slot_of(n, u, a);
+        for (int j = 0; j < wd; j++) o << reg(ni, s2, j) << " = " << reg(ni, sl, j) << ";\n";
+      }
+      o << "}\n";
+    }
+  }
+  if (n.is_liveout) emit_store(c, ni, safe, v);
+  o << "}\n";
+  if (safe) o << "}\n";
+}
+
+void emit_step(Ctx &c, bool safe, int u) {
+  auto &o = c.o;
+  o << "{ // step phase " << u << (safe ? " (guarded)" : " (steady)") << "\n";
+  o << "const int k = kb + " << u << ";\n";
+  if (safe) o << "if (k >= nsteps) goto wt_tile_end;\n";
+  o << "if (k % CH == 0) { const int c_ = k / CH; if (c_ * CH < nrows) {"
+       " const int gc_ = cbase + c_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
+       " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = c_; goto wt_fail; } } }\n";
+  o << "if (k % CH == ISSUE) { const int c_ = k / CH + NB - 1; if (c_ * CH < nrows) { issue_chunk(c_); } }\n";
+  // temporaries for shared-memory windows used this step
+  std::set<std::pair<int, int>> all;
+  for (size_t ni = 0; ni < c.g.nodes.size(); ni++) {
+    const Node &n = c.g.nodes[ni];
+    if (n.is_source) continue;
+    for (auto &pr : smem_reads(c, n.id, (int)ni)) all.insert(pr);
+  }
+  for (auto &pr : all) {
+    const Node &pn = c.g.nodes[pr.first];
+    o << "float";
+    for (int j = 0; j < width_of(pn, c.V); j++) o << (j ? ", " : " ") << tmp(pr.first, pr.second, j);
+    o << ";\n";
+  }
+  std::set<std::pair<int, int>> loaded;
+  for (size_t ni = 0; ni < c.g.nodes.size(); ni++) {
+    const Node &n = c.g.nodes[ni];
+    if (n.is_source) {
+      if (!n.in_smem) emit_source_row(c, (int)ni, safe, u);
+      continue;
+    }
+    emit_stage(c, (int)ni, safe, u, loaded);
+  }
+  o << "}\n";
+}
+
+}  // namespace
+
+std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey &key,
+                       const std::string &kname) {
+  GroupGeom g = g0;
+  FusedLayout L = fused_layout(g, key);
+  Ctx c(p, g, key, L);
+  c.V = key.vec;
+  c.U = g.unroll;
+  int n_src = 0, n_dst = 0;
+  for (size_t i = 0; i < g.nodes.size(); i++) {
+    Node &n = g.nodes[i];
+    if (n.is_source) n.src_index = n_src++;
+    else if (n.is_liveout) n.dst_index = n_dst++;
+  }
+  c.n_src = n_src;
+  const int V = c.V, HT = g.halo_t, HB = g.halo_b;
+  c.ks.assign(g.nodes.size(), 0);
+  c.kec.assign(g.nodes.size(), 0);
+  int kss = 0, kse_c = 1 << 30;
+  for (size_t i = 0; i < g.nodes.size(); i++) {
+    const Node &n = g.nodes[i];
+    if (n.is_source) {
+      c.ks[i] = 0;
+      c.kec[i] = HT + HB - 1;
+    } else {
+      c.ks[i] = HT - n.top + n.delay;
+      c.kec[i] = HT - 1 + n.bot + n.delay;
+    }
+    kss = std::max(kss, c.ks[i]);
+    kse_c = std::min(kse_c, c.kec[i]);
+  }
+  auto &o = c.o;
+  o << kDeviceSource;
+  o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
+  o << "#define CH " << L.chunk << "\n#define NB " << L.nbuf
+    << "\n#define RING " << L.ring << "\n#define ISSUE " << (g.max_src_window - 1) << "\n";
+  for (int s = 0; s < n_src; s++) o << "#define ROWB" << s << " " << L.boxw[s] * L.esz[s] << "\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", 1) " << kname
+    << "(const __grid_constant__ WtArgs a) {\n";
+  o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
+  o << "const int lane = threadIdx.x & 31;\nconst int warp = threadIdx.x >> 5;\n";
+  o << "unsigned char *wb = wt_smem + warp * " << L.warp_bytes << ";\n";
+  o << "const wt_u32 bar = wt_smem_u32(wb + " << L.bar_off << ");\n";
+  o << "if (lane == 0) { for (int i = 0; i < NB; i++) wt_mbar_init(bar + 8u * i, 1u); wt_fence_mbar_init(); }\n";
+  o << "__syncwarp();\n";
+  o << "int cbase = 0;\n(void)cbase;\nint failc = 0, issued = 0;\n";
+  // register windows (explicit scalars, D4)
+  for (size_t i = 0; i < g.nodes.size(); i++) {
+    const Node &n = g.nodes[i];
+    if (n.in_smem) continue;
+    o << "float";
+    bool first = true;
+    for (int s = 0; s < n.window; s++)
+      for (int j = 0; j < width_of(n, V); j++) {
+        o << (first ? " " : ", ") << reg((int)i, s, j) << " = 0.f";
+        first = false;
+      }
+    o << ";\n";
+  }
+  if (key.persistent) {
+    o << "for (;;) {\n";
+    o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
+         "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
+    o << "const int *tt_ = a.tile_table + 4 * tile;\nconst int img = tt_[0];\n";
+    o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
+    o << "const int tx = tt_[1], ty = tt_[2], ch = tt_[3];\n";
+  } else {
+    o << "{\n";
+    o << "const int tile = blockIdx.x * " << key.nw << " + warp;\nif (tile >= a.n_tiles) return;\n";
+    o << "const WtArgs &ia = a;\n";
+    o << "const int tx = tile % a.tiles_x;\nconst int tr_ = tile / a.tiles_x;\n"
+         "const int ty = tr_ % a.tiles_y;\nconst int ch = tr_ / a.tiles_y;\n";
+  }
+  o << "const int W = ia.W, H = ia.H, T = ia.tile_h;\n";
+  o << "const int xs = tx * " << L.out_w << " - " << L.lpad << ";\n";
+  o << "const int y0 = ty * T;\nconst int y_top = y0 - " << HT << ";\n";
+  o << "const int nsteps = " << HT << " + T + " << L.nsx << ";\n";
+  o << "const int nsrc = " << HT << " + T + " << HB << ";\n";
+  o << "const int nrows = min(nsrc, H - y_top);\n";
+  o << "const bool border = xs < 0 || xs + " << 32 * V << " > W || y_top < 0 || y0 + T + " << HB
+    << " > H;\n";
+  for (int s = 0; s < n_src; s++) {
+    const Node *sn = nullptr;
+    for (const Node &n : g.nodes)
+      if (n.is_source && n.src_index == s) sn = &n;
+    int A = 16 / L.esz[s];
+    std::string zc = (sn->src_chan >= 0) ? std::to_string(sn->src_chan) : "ch";
+    o << "const int zc" << s << " = " << zc << ";\n";
+    if (V % A) o << "const int xb" << s << " = xs & ~" << (A - 1) << ";\n";
+    else o << "const int xb" << s << " = xs;\n";
+    o << "unsigned char *rb" << s << " = wb + " << L.ring_off[s] << ";\n";
+    o << "const unsigned char *lp" << s << " = rb" << s << " + (xs - xb" << s << ") * " << L.esz[s]
+      << " + lane * " << V * L.esz[s] << ";\n";
+  }
+  for (size_t i = 0; i < g.nodes.size(); i++)
+    if (L.win_off[i] >= 0)
+      o << "unsigned char *sp" << i << " = wb + " << L.win_off[i] << " + lane * " << V * 4 << ";\n";
+  // chunk issue: lane 0 arms the buffer's mbarrier and starts one TMA box per source
+  o << "auto issue_chunk = [&](int c_) {\n__syncwarp();\nif (lane == 0) {\nwt_fence_proxy_async();\n"
+       "const int gc_ = cbase + c_;\nconst wt_u32 b_ = bar + 8u * (wt_u32)(gc_ % NB);\n"
+       "wt_mbar_expect_tx(b_, "
+    << L.chunk_bytes << "u);\n";
+  for (int s = 0; s < n_src; s++)
+    o << "wt_tma_load_3d(wt_smem_u32(rb" << s << " + (gc_ % NB) * (CH * ROWB" << s << ")), &ia.tmap["
+      << s << "], xb" << s << ", y_top + c_ * CH, zc" << s << ", b_);\n";
+  o << "}\nissued = c_ + 1;\n};\n";
+  o << "for (int c_ = 0; c_ < NB - 1; c_++) if (c_ * CH < nrows) issue_chunk(c_);\n";
+  o << "const int kss = " << kss << ";\nconst int kse = T + (" << kse_c << ");\n";
+  o << "const int U = " << c.U << ";\n";
+  o << "int kf0 = border ? 0x3fffffff : ((kss + U - 1) / U) * U;\nint kf1 = kf0;\n";
+  o << "if (!border && kse + 1 - kf0 >= U) kf1 = kf0 + ((kse + 1 - kf0) / U) * U;\n";
+  // Steady-state steps of interior tiles run the guard-free body; all
+  // other steps run the guarded body (both unrolled over U phases so that
+  // register windows rotate by renaming).
+  o << "for (int kb = 0;; kb += U) {\n";
+  o << "if (kb >= kf0 && kb < kf1) {\n";
+  for (int u = 0; u < c.U; u++) emit_step(c, false, u);
+  o << "} else {\n";
+  for (int u = 0; u < c.U; u++) emit_step(c, true, u);
+  o << "}\n}\n";
+  o << "wt_tile_end:;\n";
+  o << "cbase += (nrows + CH - 1) / CH;\n";
+  o << "}\n";  // tile scope / persistent loop
+  o << "return;\n";
+  o << "wt_fail:\n";
+  o << "for (int c_ = failc + 1; c_ < issued; c_++) { const int gc_ = cbase + c_;"
+       " wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB), (wt_u32)((gc_ / NB) & 1), a.err); }\n";
+  o << "}\n";
+  return o.str();
+}
+
+std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid) {
+  std::vector<PlainSrc> r;
+  const Stage &S = p.stages[sid];
+  for (const Op &op : S.ops) {
+    if (op.op != WT_OP_TAP) continue;
+    int pid = S.inputs[op.slot];
+    int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
+    int spec = pc == 1 ? 0 : op.chan;
+    bool found = false;
+    for (auto &x : r)
+      if (x.slot == op.slot && x.chan == spec) found = true;
+    if (!found) r.push_back({op.slot, spec});
+  }
+  return r;
+}
+
+std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const std::string &kname) {
+  const Stage &S = p.stages[sid];
+  std::vector<PlainSrc> srcs = plain_sources(p, sid);
+  if ((int)srcs.size() > kMaxSrc) fail(WT_EUNSUPPORTED, "stage reads more than 8 sources");
+  const int PV = 4;  // output pixels per thread
+  std::ostringstream o;
+  o << kDeviceSource;
+  o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(128) " << kname
+    << "(const __grid_constant__ WtArgs a) {\n";
+  o << "const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * " << PV << ";\n";
+  o << "const int y = blockIdx.y;\nconst int ch = blockIdx.z;\nconst int W = a.W, H = a.H;\n";
+  o << "(void)H;\nif (x0 >= W) return;\n";
+  // rows to load: per (src, dy): x range per element
+  struct Row {
+    int s, dy, dxmin, dxmax, mode;
+  };
+  std::vector<Row> rows;
+  for (const Op &op : S.ops) {
+    if (op.op != WT_OP_TAP) continue;
+    int pid = S.inputs[op.slot];
+    int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
+    int spec = pc == 1 ? 0 : op.chan;
+    int s = 0;
+    for (size_t i = 0; i < srcs.size(); i++)
+      if (srcs[i].slot == op.slot && srcs[i].chan == spec) s = (int)i;
+    bool found = false;
+    for (auto &r : rows)
+      if (r.s == s && r.dy == op.dy) {
+        r.dxmin = std::min(r.dxmin, op.dx);
+        r.dxmax = std::max(r.dxmax, op.dx);
+        found = true;
+      }
+    if (!found) rows.push_back({s, op.dy, op.dx, op.dx, op.mode});
+  }
+  auto col_index = [&](int mode, int e, int dx) {
+    // offset of the producer column, relative to the row base, for element e
+    if (mode == WT_TAP_DOWN2) return 2 * e + dx;
+    if (mode == WT_TAP_UP2) return (e >> 1) + dx;
+    return e + dx;
+  };
+  for (size_t ri = 0; ri < rows.size(); ri++) {
+    const Row &r = rows[ri];
+    int s = r.s;
+    int dt = key.src_dtypes.at(s);
+    int lo = col_index(r.mode, 0, r.dxmin), hi = col_index(r.mode, PV - 1, r.dxmax);
+    std::string sd = "a.src[" + std::to_string(s) + "]";
+    std::string zc = srcs[s].chan >= 0 ? std::to_string(srcs[s].chan) : "ch";
+    std::string base = (r.mode == WT_TAP_DOWN2) ? "2 * x0" : (r.mode == WT_TAP_UP2 ? "(x0 >> 1)" : "x0");
+    std::string ybase = (r.mode == WT_TAP_DOWN2) ? "2 * y" : (r.mode == WT_TAP_UP2 ? "(y >> 1)" : "y");
+    o << "const unsigned char *rp" << ri << " = (const unsigned char *)" << sd << ".ptr + (wt_i64)" << zc
+      << " * " << sd << ".plane + (wt_i64)wt_clampi(" << ybase << " + (" << r.dy << "), 0, " << sd
+      << ".H - 1) * " << sd << ".pitch;\n";
+    for (int j = lo; j <= hi; j++)
+      o << "const float L" << ri << "_" << (j - lo) << " = wt_ld1_" << tname(dt) << "(rp" << ri
+        << " + (wt_i64)wt_clampi(" << base << " + (" << j << "), 0, " << sd << ".W - 1) * "
+        << elem_bytes(dt) << ");\n";
+  }
+  for (int e = 0; e < PV; e++) {
+    std::vector<std::string> st;
+    for (const Op &op : S.ops) {
+      switch (op.op) {
+        case WT_OP_CONST: st.push_back(flt(op.value)); break;
+        case WT_OP_XPAR: st.push_back("((float)((x0 + " + std::to_string(e) + ") & 1))"); break;
+        case WT_OP_YPAR: st.push_back("((float)(y & 1))"); break;
+        case WT_OP_TAP: {
+          int pid = S.inputs[op.slot];
+          int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
+          int spec = pc == 1 ? 0 : op.chan;
+          int s = 0;
+          for (size_t i = 0; i < srcs.size(); i++)
+            if (srcs[i].slot == op.slot && srcs[i].chan == spec) s = (int)i;
+          int ri = 0;
+          for (size_t i = 0; i < rows.size(); i++)
+            if (rows[i].s == s && rows[i].dy == op.dy) ri = (int)i;
+          int lo = col_index(rows[ri].mode, 0, rows[ri].dxmin);
+          int j = col_index(op.mode, e, op.dx) - lo;
+          st.push_back("L" + std::to_string(ri) + "_" + std::to_string(j));
+        } break;
+        case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
+        case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
+        case WT_OP_SQRT: st.back() = "sqrtf(" + st.back() + ")"; break;
+        default: {
+          std::string b = st.back();
+          st.pop_back();
+          std::string a = st.back();
+          st.pop_back();
+          switch (op.op) {
+            case WT_OP_ADD: st.push_back("(" + a + " + " + b + ")"); break;
+            case WT_OP_SUB: st.push_back("(" + a + " - " + b + ")"); break;
+            case WT_OP_MUL: st.push_back("(" + a + " * " + b + ")"); break;
+            case WT_OP_DIV: st.push_back("(" + a + " / " + b + ")"); break;
+            case WT_OP_MIN: st.push_back("fminf(" + a + ", " + b + ")"); break;
+            case WT_OP_MAX: st.push_back("fmaxf(" + a + ", " + b + ")"); break;
+            default: fail(WT_EINVAL, "internal: opcode");
+          }
+        }
+      }
+    }
+    o << "const float v" << e << " = " << st.back() << ";\n";
+  }
+  int dt = key.dst_dtypes.at(0);
+  int esz = elem_bytes(dt);
+  o << "unsigned char *op_ = (unsigned char *)a.dst[0].ptr + (wt_i64)" << (S.channels > 1 ? "ch" : "0")
+    << " * a.dst[0].plane + (wt_i64)y * a.dst[0].pitch + (wt_i64)x0 * " << esz << ";\n";
+  o << "if (x0 + " << PV << " <= W) { wt_st4_" << tname(dt) << "(op_, v0, v1, v2, v3); } else {\n";
+  for (int e = 0; e < PV; e++)
+    o << "if (x0 + " << e << " < W) wt_st1_" << tname(dt) << "(op_ + " << e * esz << ", v" << e << ");\n";
+  o << "}\n}\n";
+  return o.str();
+}
+
+}  // namespace wt

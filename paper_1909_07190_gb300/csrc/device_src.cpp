@@ -1,0 +1,155 @@
+// Hand-written device helpers shared by every generated group kernel.
+// The text below is prepended to each generated kernel and compiled with
+// NVRTC for sm_103a.  It uses only PTX instructions (cp.async.bulk.tensor,
+// mbarrier, cvt) and CUDA built-ins; no CUDA headers are needed.
+#include "wt_internal.hpp"
+
+namespace wt {
+
+const char *kDeviceSource = R"WTDEV(
+typedef unsigned long long wt_u64;
+typedef long long wt_i64;
+typedef unsigned int wt_u32;
+typedef unsigned short wt_u16;
+
+struct __align__(64) WtTmap { wt_u64 v[16]; };
+struct WtSrc { const void *ptr; int W, H, C, dtype; wt_i64 pitch, plane; };
+struct WtDst { void *ptr; int W, H, C, dtype; wt_i64 pitch, plane; };
+struct __align__(64) WtArgs {
+  WtTmap tmap[8];
+  WtSrc src[8];
+  WtDst dst[8];
+  int W, H;
+  int tile_h, tiles_x, tiles_y, n_tiles;
+  int chunk, nbuf;
+  int out_w;
+  int channels;
+  int *err;
+  const int *tile_table;
+  int *queue;
+  int n_images;
+  int pad0;
+  const void *img_tab;
+};
+
+#define WT_FULL 0xffffffffu
+#define WT_ERR_TIMEOUT 1
+#define WT_ERR_BOUNDS 2
+#define WT_WAIT_LIMIT (1 << 22)
+
+static __device__ __forceinline__ wt_u32 wt_smem_u32(const void *p) {
+  return (wt_u32)__cvta_generic_to_shared(p);
+}
+
+static __device__ __forceinline__ void wt_mbar_init(wt_u32 bar, wt_u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+static __device__ __forceinline__ void wt_fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+static __device__ __forceinline__ void wt_fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+static __device__ __forceinline__ void wt_mbar_expect_tx(wt_u32 bar, wt_u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+static __device__ __forceinline__ wt_u32 wt_mbar_try_wait(wt_u32 bar, wt_u32 parity) {
+  wt_u32 ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok;
+}
+// Bounded wait: returns 1 on completion, 0 (and raises the error word) if
+// the limit is reached, so a lost transfer never hangs the GPU.
+static __device__ __forceinline__ int wt_mbar_wait(wt_u32 bar, wt_u32 parity, int *err) {
+  for (int i = 0; i < WT_WAIT_LIMIT; i++)
+    if (wt_mbar_try_wait(bar, parity)) return 1;
+  atomicExch(err, WT_ERR_TIMEOUT);
+  return 0;
+}
+// 3-D tiled TMA load of one box into shared memory, completion on `bar`.
+static __device__ __forceinline__ void wt_tma_load_3d(wt_u32 dst, const WtTmap *map, int x, int y,
+                                                      int z, wt_u32 bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"((wt_u64)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// ------------------------------------------------------------ conversions
+static __device__ __forceinline__ float wt_h2f(wt_u16 h) {
+  float f;
+  asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+  return f;
+}
+static __device__ __forceinline__ wt_u16 wt_f2h(float f) {
+  wt_u16 h;
+  asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
+  return h;
+}
+static __device__ __forceinline__ float wt_b2f(wt_u16 b) { return __uint_as_float(((wt_u32)b) << 16); }
+static __device__ __forceinline__ wt_u16 wt_f2b(float f) {
+  wt_u16 h;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+  return h;
+}
+
+// ------------------------------------------------- vector loads (4 lanes)
+static __device__ __forceinline__ void wt_ld4_f32(const void *p, float &a, float &b, float &c,
+                                                  float &d) {
+  float4 v = *(const float4 *)p;
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+static __device__ __forceinline__ void wt_ld4_f16(const void *p, float &a, float &b, float &c,
+                                                  float &d) {
+  uint2 v = *(const uint2 *)p;
+  a = wt_h2f((wt_u16)(v.x & 0xffff)); b = wt_h2f((wt_u16)(v.x >> 16));
+  c = wt_h2f((wt_u16)(v.y & 0xffff)); d = wt_h2f((wt_u16)(v.y >> 16));
+}
+static __device__ __forceinline__ void wt_ld4_bf16(const void *p, float &a, float &b, float &c,
+                                                   float &d) {
+  uint2 v = *(const uint2 *)p;
+  a = __uint_as_float(v.x << 16); b = __uint_as_float(v.x & 0xffff0000u);
+  c = __uint_as_float(v.y << 16); d = __uint_as_float(v.y & 0xffff0000u);
+}
+// ------------------------------------------------ vector stores (4 lanes)
+static __device__ __forceinline__ void wt_st4_f32(void *p, float a, float b, float c, float d) {
+  *(float4 *)p = make_float4(a, b, c, d);
+}
+static __device__ __forceinline__ void wt_st4_f16(void *p, float a, float b, float c, float d) {
+  uint2 v;
+  v.x = (wt_u32)wt_f2h(a) | ((wt_u32)wt_f2h(b) << 16);
+  v.y = (wt_u32)wt_f2h(c) | ((wt_u32)wt_f2h(d) << 16);
+  *(uint2 *)p = v;
+}
+static __device__ __forceinline__ void wt_st4_bf16(void *p, float a, float b, float c, float d) {
+  uint2 v;
+  v.x = (wt_u32)wt_f2b(a) | ((wt_u32)wt_f2b(b) << 16);
+  v.y = (wt_u32)wt_f2b(c) | ((wt_u32)wt_f2b(d) << 16);
+  *(uint2 *)p = v;
+}
+// ------------------------------------------------------- scalar accesses
+static __device__ __forceinline__ float wt_ld1_f32(const void *p) { return __ldg((const float *)p); }
+static __device__ __forceinline__ float wt_ld1_f16(const void *p) {
+  return wt_h2f(__ldg((const unsigned short *)p));
+}
+static __device__ __forceinline__ float wt_ld1_bf16(const void *p) {
+  return wt_b2f(__ldg((const unsigned short *)p));
+}
+static __device__ __forceinline__ void wt_st1_f32(void *p, float v) { *(float *)p = v; }
+static __device__ __forceinline__ void wt_st1_f16(void *p, float v) { *(wt_u16 *)p = wt_f2h(v); }
+static __device__ __forceinline__ void wt_st1_bf16(void *p, float v) { *(wt_u16 *)p = wt_f2b(v); }
+
+static __device__ __forceinline__ int wt_clampi(int v, int lo, int hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+// WT-DEVICE-HELPERS-END
+)WTDEV";
+
+}  // namespace wt

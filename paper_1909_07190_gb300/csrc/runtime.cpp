@@ -1,0 +1,382 @@
+// Runtime: run plans, device workspace, kernel cache and launches.
+//
+// A run plan turns the installed schedule into launches: one fused
+// warp-tile kernel per fusable group, one per-stage kernel for every stage
+// of a non-fusable group (or of every stage under WT_EXEC_PLAIN).  Values
+// crossing group boundaries live in HBM: pipeline inputs/outputs in the
+// caller's images, other stages in the pipeline's workspace.
+#include "wt_runtime.hpp"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "wt_jit.hpp"
+
+namespace wt {
+
+// ------------------------------------------------------------- validation
+
+static void check_image(const wt_image &im, const char *what) {
+  if (!im.data) fail(WT_EINVAL, std::string(what) + ": null data");
+  if (im.width < 1 || im.height < 1 || im.channels < 1)
+    fail(WT_EINVAL, std::string(what) + ": empty image (width, height and channels must be >= 1)");
+  if (im.dtype < WT_F32 || im.dtype > WT_BF16) fail(WT_EINVAL, std::string(what) + ": bad dtype");
+  if (im.pitch_bytes % 16 != 0) fail(WT_EINVAL, std::string(what) + ": pitch_bytes must be a multiple of 16");
+  if (im.pitch_bytes < (int64_t)im.width * elem_bytes(im.dtype))
+    fail(WT_EINVAL, std::string(what) + ": pitch_bytes smaller than a row");
+  if (((uintptr_t)im.data) % 16 != 0) fail(WT_EINVAL, std::string(what) + ": data must be 16-byte aligned");
+}
+
+std::vector<std::vector<int>> schedule_groups(const Pipeline &p) {
+  std::vector<std::vector<int>> groups;
+  const Schedule &s = p.sched;
+  if (s.exec == WT_EXEC_PLAIN) {
+    for (size_t i = 0; i < p.stages.size(); i++) groups.push_back({(int)i});
+    return groups;
+  }
+  groups.resize(s.n_groups);
+  for (size_t i = 0; i < p.stages.size(); i++) groups[s.group_of_stage[i]].push_back((int)i);
+  return groups;
+}
+
+GroupParams group_params(const Pipeline &p, int gi) {
+  const Schedule &s = p.sched;
+  if (gi < (int)s.params.size()) return s.params[gi];
+  return GroupParams();
+}
+
+static int pick_vec(const GroupParams &gp, const std::vector<int> &src_dtypes) {
+  if (gp.vec == 4 || gp.vec == 8) return gp.vec;
+  (void)src_dtypes;
+  return 4;
+}
+
+// -------------------------------------------------------------- planning
+
+RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out) {
+  if (n_in != (int)p.in_channels.size())
+    fail(WT_EINVAL, "expected " + std::to_string(p.in_channels.size()) + " inputs");
+  if (n_out != (int)p.outputs.size())
+    fail(WT_EINVAL, "expected " + std::to_string(p.outputs.size()) + " outputs");
+  for (int j = 0; j < n_in; j++) {
+    check_image(in[j], "input");
+    if (in[j].channels != p.in_channels[j]) fail(WT_EINVAL, "input " + std::to_string(j) + ": channels");
+    if (in[j].width != in[0].width || in[j].height != in[0].height)
+      fail(WT_EINVAL, "all inputs must have the same width and height");
+  }
+  RunPlan plan;
+  plan.W = in[0].width;
+  plan.H = in[0].height;
+  const int n = (int)p.stages.size();
+  plan.loc.assign(n, Loc());
+  plan.in_loc.resize(n_in);
+  for (int j = 0; j < n_in; j++) {
+    Loc &l = plan.in_loc[j];
+    l.ptr = in[j].data; l.pitch = in[j].pitch_bytes;
+    l.plane = in[j].pitch_bytes * in[j].height;
+    l.W = in[j].width; l.H = in[j].height; l.C = in[j].channels; l.dtype = in[j].dtype;
+  }
+  for (int k = 0; k < n_out; k++) {
+    check_image(out[k], "output");
+    int s = p.outputs[k];
+    int w, h;
+    level_dims(plan.W, plan.H, p.stages[s].level, &w, &h);
+    if (out[k].width != w || out[k].height != h || out[k].channels != p.stages[s].channels)
+      fail(WT_EINVAL, "output " + std::to_string(k) + ": expected " + std::to_string(w) + "x" +
+                          std::to_string(h) + "x" + std::to_string(p.stages[s].channels));
+    Loc &l = plan.loc[s];
+    l.ptr = out[k].data; l.pitch = out[k].pitch_bytes; l.plane = out[k].pitch_bytes * out[k].height;
+    l.W = w; l.H = h; l.C = out[k].channels; l.dtype = out[k].dtype; l.user = true;
+  }
+  int mid = p.sched.intermediate_dtype;
+  if (mid < 0) mid = p.sched.exec == WT_EXEC_PLAIN ? WT_F32 : in[0].dtype;
+  plan.mid_dtype = mid;
+  auto groups = schedule_groups(p);
+  std::vector<int> group_of(n, 0);
+  for (size_t gi = 0; gi < groups.size(); gi++)
+    for (int s : groups[gi]) group_of[s] = (int)gi;
+  // Stages needing an HBM buffer: read by a later group (or every stage in
+  // plain mode), unless they are pipeline outputs.
+  auto materialize = [&](int s, bool need) {
+    if (!need || plan.loc[s].ptr || plan.loc[s].user) return;
+    Loc &l = plan.loc[s];
+    int w, h;
+    level_dims(plan.W, plan.H, p.stages[s].level, &w, &h);
+    l.W = w; l.H = h; l.C = p.stages[s].channels; l.dtype = mid;
+    l.pitch = ((int64_t)w * elem_bytes(mid) + 127) / 128 * 128;
+    l.plane = l.pitch * h;
+    l.ws_bytes = l.plane * l.C;
+    l.ws = true;
+  };
+  for (size_t gi = 0; gi < groups.size(); gi++) {
+    const auto &G = groups[gi];
+    GroupParams gp = group_params(p, (int)gi);
+    bool fused = p.sched.exec == WT_EXEC_FUSED;
+    GroupGeom geom;
+    if (fused) {
+      geom = analyze_group(p, G, 4, gp.frac_reg, 4);
+      fused = geom.fusable;
+    }
+    if (!fused) {
+      for (int s : G) {
+        if (p.consumers[s].empty() && !p.is_output[s]) continue;  // dead stage
+        materialize(s, !p.consumers[s].empty());
+        Launch L;
+        L.fused = false;
+        L.stages = {s};
+        L.params = gp;
+        plan.launches.push_back(L);
+      }
+      continue;
+    }
+    for (int s : geom.liveouts) materialize(s, true);
+    Launch L;
+    L.fused = true;
+    L.stages = G;
+    L.params = gp;
+    L.geom = geom;
+    plan.launches.push_back(L);
+  }
+  // Workspace offsets (256-byte aligned).
+  int64_t off = 0;
+  for (int s = 0; s < n; s++) {
+    if (!plan.loc[s].ws) continue;
+    off = (off + 255) / 256 * 256;
+    plan.loc[s].ws_off = off;
+    off += plan.loc[s].ws_bytes;
+  }
+  plan.ws_bytes = off;
+  // Resolve sources, destinations and keys.
+  for (Launch &L : plan.launches) {
+    CodegenKey &key = L.key;
+    key.stages = L.stages;
+    key.frac_reg = L.params.frac_reg;
+    key.max_regs = L.params.max_regs;
+    key.nw = std::max(1, std::min(16, L.params.warps_per_block));
+    key.chunk = L.params.chunk_rows > 0 ? L.params.chunk_rows : 8;
+    key.nbuf = L.params.n_buffers > 0 ? L.params.n_buffers : 3;
+    L.src.clear();
+    L.dst.clear();
+    auto loc_of = [&](int pid) -> const Loc & { return pid >= 0 ? plan.loc[pid] : plan.in_loc[-pid - 1]; };
+    if (L.fused) {
+      for (const Node &nd : L.geom.nodes)
+        if (nd.is_source) {
+          L.src.push_back(nd.id);
+          L.src_chan.push_back(nd.src_chan);
+          key.src_dtypes.push_back(loc_of(nd.id).dtype);
+        }
+      for (int s : L.geom.liveouts) {
+        L.dst.push_back(s);
+        key.dst_dtypes.push_back(plan.loc[s].dtype);
+      }
+      key.vec = pick_vec(L.params, key.src_dtypes);
+      if (key.vec != 4) L.geom = analyze_group(p, L.stages, key.vec, L.params.frac_reg, 4);
+      L.layout = fused_layout(L.geom, key);
+      level_dims(plan.W, plan.H, L.geom.level, &L.W, &L.H);
+      int th = std::max(1, L.params.tile_h);
+      int tiles_x = (L.W + L.layout.out_w - 1) / L.layout.out_w;
+      int tiles_y = (L.H + th - 1) / th;
+      int64_t nt = (int64_t)tiles_x * tiles_y * L.geom.channels;
+      if (nt > (1ll << 30)) fail(WT_EUNSUPPORTED, "too many tiles");
+      L.tiles_x = tiles_x; L.tiles_y = tiles_y; L.n_tiles = (int)nt;
+      L.block = 32 * key.nw;
+      L.grid[0] = (unsigned)((nt + key.nw - 1) / key.nw);
+      L.grid[1] = L.grid[2] = 1;
+      L.smem = key.nw * L.layout.warp_bytes;
+      if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "group needs more than 227 KB of shared memory per block");
+    } else {
+      int s = L.stages[0];
+      key.plain = true;
+      key.vec = 4;
+      key.nw = 4;
+      for (const PlainSrc &ps : plain_sources(p, s)) {
+        int pid = p.stages[s].inputs[ps.slot];
+        L.src.push_back(pid);
+        L.src_chan.push_back(ps.chan);
+        key.src_dtypes.push_back(loc_of(pid).dtype);
+      }
+      L.dst.push_back(s);
+      key.dst_dtypes.push_back(plan.loc[s].dtype);
+      level_dims(plan.W, plan.H, p.stages[s].level, &L.W, &L.H);
+      L.block = 128;
+      L.grid[0] = (unsigned)(((L.W + 3) / 4 + 127) / 128);
+      L.grid[1] = (unsigned)L.H;
+      L.grid[2] = (unsigned)p.stages[s].channels;
+      if (L.H > 65535 || L.grid[2] > 65535) fail(WT_EUNSUPPORTED, "image too tall for the per-stage kernel");
+      L.smem = 0;
+    }
+    char hx[24];
+    uint64_t h = fnv1a(key.str().data(), key.str().size(), p.hash);
+    snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
+    L.kname = std::string(L.fused ? "wt_fused_" : "wt_plain_") + hx;
+  }
+  return plan;
+}
+
+std::string launch_source(const Pipeline &p, const Launch &L) {
+  if (L.fused) return emit_fused(p, L.geom, L.key, L.kname);
+  return emit_plain(p, L.stages[0], L.key, L.kname);
+}
+
+// Fills the argument block of a launch.  `ws` is the workspace base (may be
+// null when every source/destination is a caller image).
+void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws, KernelArgs &a,
+               bool encode_tmaps) {
+  memset(&a, 0, sizeof a);
+  auto loc_of = [&](int pid) -> const Loc & { return pid >= 0 ? plan.loc[pid] : plan.in_loc[-pid - 1]; };
+  auto ptr_of = [&](const Loc &l) -> char * {
+    if (l.ws) {
+      if (!ws) fail(WT_EUNSUPPORTED, "launch reads or writes the workspace");
+      return ws + l.ws_off;
+    }
+    return (char *)l.ptr;
+  };
+  for (size_t i = 0; i < L.src.size(); i++) {
+    const Loc &l = loc_of(L.src[i]);
+    SrcDesc &d = a.src[i];
+    d.ptr = ptr_of(l);
+    d.W = l.W; d.H = l.H; d.C = l.C; d.dtype = l.dtype; d.pitch = l.pitch; d.plane = l.plane;
+    if (L.fused && !encode_tmaps) {
+      // Introspection only: a plain description of the box in place of the
+      // opaque tensor map (layout: struct DebugTmap in wt_internal.hpp).
+      DebugTmap t;
+      t.ptr = d.ptr; t.W = l.W; t.H = l.H; t.C = l.C; t.esz = elem_bytes(l.dtype);
+      t.pitch = l.pitch; t.plane = l.plane;
+      t.boxw = L.layout.boxw[i]; t.boxh = L.layout.chunk;
+      static_assert(sizeof(DebugTmap) <= sizeof(TmapBytes), "debug tensor map size");
+      memcpy(&a.tmap[i], &t, sizeof t);
+    }
+    if (L.fused && encode_tmaps) {
+      const Driver &drv = driver();
+      CUtensorMapDataType t = l.dtype == WT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                              : l.dtype == WT_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+      cuuint64_t dims[3] = {(cuuint64_t)l.W, (cuuint64_t)l.H, (cuuint64_t)l.C};
+      cuuint64_t strides[2] = {(cuuint64_t)l.pitch, (cuuint64_t)l.plane};
+      cuuint32_t box[3] = {(cuuint32_t)L.layout.boxw[i], (cuuint32_t)L.layout.chunk, 1};
+      cuuint32_t es[3] = {1, 1, 1};
+      static_assert(sizeof(CUtensorMap) == sizeof(TmapBytes), "tensor map size");
+      check_cu(drv.tensorMapEncodeTiled((CUtensorMap *)&a.tmap[i], t, 3, (void *)d.ptr, dims, strides, box,
+                                        es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE),
+               "cuTensorMapEncodeTiled");
+    }
+  }
+  for (size_t i = 0; i < L.dst.size(); i++) {
+    const Loc &l = plan.loc[L.dst[i]];
+    DstDesc &d = a.dst[i];
+    d.ptr = ptr_of(l);
+    d.W = l.W; d.H = l.H; d.C = l.C; d.dtype = l.dtype; d.pitch = l.pitch; d.plane = l.plane;
+  }
+  a.W = L.W;
+  a.H = L.H;
+  a.tile_h = std::max(1, L.params.tile_h);
+  a.tiles_x = L.tiles_x;
+  a.tiles_y = L.tiles_y;
+  a.n_tiles = L.n_tiles;
+  a.chunk = L.layout.chunk;
+  a.nbuf = L.layout.nbuf;
+  a.out_w = L.layout.out_w;
+  a.channels = L.fused ? L.geom.channels : 1;
+  (void)p;
+}
+
+// ---------------------------------------------------------- kernel cache
+
+struct CacheEntry {
+  Kernel k;
+  int smem_set = 0;
+};
+static std::mutex g_cache_mu;
+static std::map<std::string, CacheEntry> g_cache;
+
+Kernel &get_kernel(const Pipeline &p, const Launch &L, int device) {
+  std::string key = L.kname + "@" + std::to_string(device);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) return it->second.k;
+  }
+  const Driver &drv = driver();
+  std::string src = launch_source(p, L);
+  std::string cubin = compile_cubin(src, L.kname, L.key.max_regs);
+  CUmodule mod;
+  check_cu(drv.moduleLoadData(&mod, cubin.data()), "cuModuleLoadData");
+  CUfunction f;
+  check_cu(drv.moduleGetFunction(&f, mod, L.kname.c_str()), "cuModuleGetFunction");
+  CacheEntry e;
+  e.k.module = mod;
+  e.k.function = f;
+  e.k.name = L.kname;
+  drv.funcGetAttribute(&e.k.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, f);
+  drv.funcGetAttribute(&e.k.static_smem, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, f);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto ins = g_cache.emplace(key, e);
+  return ins.first->second.k;
+}
+
+void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream) {
+  const Driver &drv = driver();
+  if (L.smem > 48 * 1024)
+    check_cu(drv.funcSetAttribute((CUfunction)k.function, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                  L.smem),
+             "cuFuncSetAttribute");
+  void *params[] = {&a};
+  check_cu(drv.launchKernel((CUfunction)k.function, L.grid[0], L.grid[1], L.grid[2], (unsigned)L.block, 1, 1,
+                            (unsigned)L.smem, (CUstream)stream, params, nullptr),
+           "cuLaunchKernel");
+}
+
+// ------------------------------------------------------------- workspace
+
+Workspace::~Workspace() {
+  if (base) cudaFree(base);
+  if (err) cudaFree(err);
+  for (auto &kv : staging)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+}
+
+Workspace &workspace(Pipeline &p, int64_t bytes) {
+  int dev = 0;
+  check_rt(cudaGetDevice(&dev), "cudaGetDevice");
+  if (!p.ws || p.ws->device != dev) {
+    auto w = std::make_shared<Workspace>();
+    w->device = dev;
+    check_rt(cudaMalloc((void **)&w->err, 64), "cudaMalloc(error word)");
+    check_rt(cudaMemset(w->err, 0, 64), "cudaMemset");
+    p.ws = w;
+  }
+  Workspace &w = *p.ws;
+  if (bytes > w.bytes) {
+    if (w.base) {
+      check_rt(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+      cudaFree(w.base);
+      w.base = nullptr;
+      w.bytes = 0;
+    }
+    if (cudaMalloc((void **)&w.base, (size_t)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(WT_ENOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of workspace");
+    }
+    w.bytes = bytes;
+  }
+  return w;
+}
+
+void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream) {
+  Workspace &w = workspace(p, plan.ws_bytes);
+  int dev = w.device;
+  for (Launch &L : plan.launches) {
+    Kernel &k = get_kernel(p, L, dev);
+    KernelArgs a;
+    fill_args(p, plan, L, w.base, a, L.fused);
+    a.err = w.err;
+    launch(L, k, a, stream);
+  }
+}
+
+}  // namespace wt

@@ -1,0 +1,222 @@
+// Internal types of the warp-tiled pipeline library (host side).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wt.h"
+
+namespace wt {
+
+constexpr int kMaxSrc = 8;     // distinct external sources per group kernel
+constexpr int kMaxDst = 8;     // liveouts per group kernel
+constexpr int kMaxOps = 256;   // ops per stage program
+constexpr int kMaxStack = 32;  // postfix stack depth
+
+// Thrown inside the library, converted to a wt_status at the C boundary.
+struct Error {
+  wt_status code;
+  std::string msg;
+};
+[[noreturn]] void fail(wt_status code, const std::string &msg);
+
+struct Op {
+  int op = 0, slot = 0, dx = 0, dy = 0, chan = -1, mode = 0;
+  float value = 0.f;
+};
+
+// Footprint of one producer as read by one consumer (Sec. 2.3: the set of
+// dependence vectors, summarised as a box per tap mode).
+struct Edge {
+  int producer = 0;  // stage id or -(j+1)
+  int mode = 0;      // wt_tapmode (one mode per edge; checked)
+  int dxmin = 0, dxmax = 0, dymin = 0, dymax = 0;
+  std::vector<int> chans;  // distinct channel specs used (-1 or fixed)
+};
+
+struct Stage {
+  int channels = 1;
+  std::vector<int> inputs;
+  std::vector<Op> ops;
+  // derived
+  int level = 0;
+  std::vector<Edge> edges;  // one per input slot that is tapped
+};
+
+struct GroupParams {
+  int tile_h = 32;
+  int warps_per_block = 4;
+  float frac_reg = 1.f;
+  int vec = 0;
+  int max_regs = 0;
+  int chunk_rows = 8;
+  int n_buffers = 3;
+};
+
+struct Schedule {
+  int exec = WT_EXEC_FUSED;
+  std::vector<int> group_of_stage;
+  std::vector<GroupParams> params;
+  int n_groups = 0;
+  int intermediate_dtype = -1;
+  bool installed = false;
+};
+
+// Geometry of one fused group (Sec. 4 OTPW and Sec. 5 hybrid tiling, in the
+// streaming form used here: split dimension y, one lane row per warp).
+struct Node {
+  int id = 0;             // stage id, or -(j+1) for a pipeline input
+  int src_chan = -1;      // sources: channel spec (-1 = tile channel)
+  bool is_source = false; // read from memory (pipeline input or earlier group)
+  bool is_liveout = false;
+  int channels = 1;
+  int top = 0, bot = 0;   // rows needed above/below the output rows
+  int left = 0, right = 0;// columns needed left/right of the output columns
+  int delay = 0;          // e_n: stage n computes row y_top + k - e_n at step k
+  int window = 1;         // rows kept (rotation window)
+  int xl = 0, xr = 0;     // extra columns each lane needs from its neighbours
+  bool in_smem = false;   // window lives in shared memory (else registers)
+  bool rotate = true;     // rotating slot names (window divides unroll)
+  int src_index = -1;     // sources: index into the kernel's source table
+  int dst_index = -1;     // liveouts: index into the kernel's dst table
+};
+
+struct GroupGeom {
+  std::vector<int> stages;     // stage ids (topological)
+  std::vector<Node> nodes;     // sources first, then stages (same order)
+  std::vector<int> liveouts;   // stage ids
+  bool fusable = true;         // else: per-stage kernel
+  std::string why_not;         // reason when !fusable
+  int level = 0;
+  int channels = 1;            // tile channels (max over stages)
+  int halo_l = 0, halo_r = 0;  // x halo (pixels) over all sources
+  int halo_t = 0, halo_b = 0;  // y halo (rows) over all sources
+  int max_delay = 0;
+  int unroll = 1;
+  int max_src_window = 1;
+  int node_of(int id, int chan) const;
+};
+
+struct Pipeline;
+
+// Per-device compiled module cache entry.
+struct Kernel {
+  void *module = nullptr;    // CUmodule
+  void *function = nullptr;  // CUfunction
+  int regs = 0;
+  int static_smem = 0;
+  std::string name;
+};
+
+struct Workspace;  // runtime buffers (defined in runtime.cpp)
+
+struct Pipeline {
+  std::vector<Stage> stages;
+  std::vector<int> in_channels;
+  std::vector<int> outputs;
+  std::vector<std::vector<int>> consumers;
+  std::vector<char> is_output;
+  Schedule sched;
+  std::mutex mu;
+  std::shared_ptr<Workspace> ws;
+  uint64_t hash = 0;
+};
+
+// ir.cpp
+void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch,
+                    int n_in, const int32_t *outs, int n_out);
+void level_dims(int W, int H, int level, int *w, int *h);
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull);
+
+// analysis.cpp
+GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int vec,
+                        float frac_reg, int dtype_bytes);
+int elem_bytes(int dtype);
+
+// codegen.cpp
+struct CodegenKey {
+  std::vector<int> stages;
+  int vec = 4;
+  std::vector<int> src_dtypes, dst_dtypes;
+  float frac_reg = 1.f;
+  int max_regs = 0;
+  int nw = 4;        // warps per block (launch bound)
+  int chunk = 8;     // TMA rows per chunk
+  int nbuf = 3;      // TMA buffers per source
+  bool plain = false;
+  bool persistent = false;
+  std::string str() const;
+};
+
+// Shared-memory layout and tile geometry of a fused group kernel.
+struct FusedLayout {
+  int V = 4;
+  int lpad = 0, rpad = 0, out_w = 0;  // x halo (multiples of V), output columns
+  int chunk = 8, nbuf = 3, ring = 24; // ring = chunk * nbuf rows
+  int nsx = 0;                        // nsteps = halo_t + tile_h + nsx
+  int src_rows_extra = 0;             // source rows = halo_t + tile_h + halo_b
+  std::vector<int> boxw;              // per source: TMA box width (elements)
+  std::vector<int> esz;               // per source: element bytes
+  std::vector<int> ring_off;          // per source: byte offset in the warp slice
+  std::vector<int> win_off;           // per node: smem window offset (-1 = regs)
+  int bar_off = 0;
+  int warp_bytes = 0;
+  int chunk_bytes = 0;                // expect_tx per chunk (all sources)
+};
+FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key);
+std::string emit_fused(const Pipeline &p, const GroupGeom &g, const CodegenKey &key,
+                       const std::string &kname);
+std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key,
+                       const std::string &kname);
+// Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
+struct PlainSrc {
+  int slot, chan;
+};
+std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid);
+extern const char *kDeviceSource;  // device_src.cpp
+
+// Launch-argument block shared by every generated kernel (device layout is
+// mirrored in the device source).
+struct alignas(64) TmapBytes {
+  uint64_t v[16];
+};
+// What wt_debug_kernel stores in a tensor-map slot (no driver involved).
+struct DebugTmap {
+  const void *ptr;
+  int32_t W, H, C, esz;
+  int64_t pitch, plane;
+  int32_t boxw, boxh;
+};
+struct SrcDesc {
+  const void *ptr;
+  int32_t W, H, C, dtype;
+  int64_t pitch, plane;
+};
+struct DstDesc {
+  void *ptr;
+  int32_t W, H, C, dtype;
+  int64_t pitch, plane;
+};
+struct alignas(64) KernelArgs {
+  TmapBytes tmap[kMaxSrc];
+  SrcDesc src[kMaxSrc];
+  DstDesc dst[kMaxDst];
+  int32_t W, H;            // domain of the group's level
+  int32_t tile_h, tiles_x, tiles_y, n_tiles;
+  int32_t chunk, nbuf;
+  int32_t out_w;           // output columns per warp tile
+  int32_t channels;
+  int32_t *err;            // device error word
+  // persistent batched mode
+  const int32_t *tile_table;  // 4 ints per tile: image, tx, ty, c
+  int32_t *queue;             // atomic tile counter
+  int32_t n_images;
+  int32_t pad0;
+  const void *img_tab;        // per-image SrcDesc/DstDesc/tmaps
+};
+
+}  // namespace wt

@@ -1,0 +1,70 @@
+// Run plans and launches (runtime.cpp).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wt_internal.hpp"
+
+namespace wt {
+
+// Where a stage's (or input's) values live in HBM.
+struct Loc {
+  const void *ptr = nullptr;
+  int64_t pitch = 0, plane = 0;
+  int W = 0, H = 0, C = 0, dtype = WT_F32;
+  bool user = false;     // caller's output image
+  bool ws = false;       // lives in the workspace at ws_off
+  int64_t ws_off = 0, ws_bytes = 0;
+};
+
+struct Launch {
+  bool fused = true;
+  std::vector<int> stages;
+  GroupParams params;
+  GroupGeom geom;
+  FusedLayout layout;
+  CodegenKey key;
+  std::string kname;
+  std::vector<int> src, src_chan, dst;
+  int W = 0, H = 0;
+  int tiles_x = 0, tiles_y = 0, n_tiles = 0;
+  unsigned grid[3] = {1, 1, 1};
+  int block = 128;
+  int smem = 0;
+};
+
+struct RunPlan {
+  int W = 0, H = 0;
+  int mid_dtype = WT_F32;
+  std::vector<Loc> loc;     // per stage
+  std::vector<Loc> in_loc;  // per pipeline input
+  std::vector<Launch> launches;
+  int64_t ws_bytes = 0;
+};
+
+struct Staging {
+  void *ptr = nullptr;
+  int64_t bytes = 0;
+};
+
+struct Workspace {
+  int device = -1;
+  char *base = nullptr;
+  int64_t bytes = 0;
+  int32_t *err = nullptr;
+  std::map<int, Staging> staging;  // wt_run_host device copies
+  ~Workspace();
+};
+
+std::vector<std::vector<int>> schedule_groups(const Pipeline &p);
+GroupParams group_params(const Pipeline &p, int gi);
+RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out);
+std::string launch_source(const Pipeline &p, const Launch &L);
+void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws, KernelArgs &a,
+               bool encode_tmaps);
+Kernel &get_kernel(const Pipeline &p, const Launch &L, int device);
+void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream);
+Workspace &workspace(Pipeline &p, int64_t bytes);
+void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream);
+
+}  // namespace wt

@@ -1,0 +1,333 @@
+"""Thin Python binding of the C ABI in include/wt.h (argument marshalling only).
+
+Every computation runs in libwt.so's kernels; this module converts pipeline
+dicts (see pipelines.py) to ``wt_stage`` arrays and tensors to ``wt_image``
+descriptors.  There is no CPU fallback: if the library or a CUDA device is
+missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libwt.so")
+
+WT_OK, WT_EINVAL, WT_ENOMEM, WT_ECUDA, WT_EUNSUPPORTED, WT_ETIMEOUT, WT_EDEVICE, WT_ECOMPILE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+WT_F32, WT_F16, WT_BF16 = 0, 1, 2
+WT_EXEC_FUSED, WT_EXEC_PLAIN = 0, 1
+WT_MODEL_ANALYTIC, WT_MODEL_LEARNED = 0, 1
+OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
+           "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13}
+TAPMODES = {"same": 0, "down2": 1, "up2": 2}
+DTYPES = {"f32": WT_F32, "f16": WT_F16, "bf16": WT_BF16}
+STATUS = {0: "WT_OK", -1: "WT_EINVAL", -2: "WT_ENOMEM", -3: "WT_ECUDA", -4: "WT_EUNSUPPORTED",
+          -5: "WT_ETIMEOUT", -6: "WT_EDEVICE", -7: "WT_ECOMPILE"}
+
+
+class wt_op(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("slot", ctypes.c_int32), ("dx", ctypes.c_int32),
+                ("dy", ctypes.c_int32), ("chan", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("value", ctypes.c_float)]
+
+
+class wt_stage(ctypes.Structure):
+    _fields_ = [("channels", ctypes.c_int32), ("n_inputs", ctypes.c_int32),
+                ("inputs", ctypes.POINTER(ctypes.c_int32)), ("n_ops", ctypes.c_int32),
+                ("ops", ctypes.POINTER(wt_op))]
+
+
+class wt_image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("channels", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("pitch_bytes", ctypes.c_int64)]
+
+
+class wt_group_params(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("frac_reg", ctypes.c_float), ("vec", ctypes.c_int32), ("max_regs", ctypes.c_int32),
+                ("chunk_rows", ctypes.c_int32), ("n_buffers", ctypes.c_int32)]
+
+
+class wt_schedule_desc(ctypes.Structure):
+    _fields_ = [("exec", ctypes.c_int32), ("n_groups", ctypes.c_int32),
+                ("group_of_stage", ctypes.POINTER(ctypes.c_int32)),
+                ("params", ctypes.POINTER(wt_group_params)),
+                ("intermediate_dtype", ctypes.c_int32)]
+
+
+# Every symbol include/wt.h and include/wt_debug.h declare: (name, restype, argtypes).
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+SIGNATURES = [
+    ("wt_pipeline_create", _i32, [_P(wt_stage), _i32, _P(_i32), _i32, _P(_i32), _i32, _i32, _P(_vp)]),
+    ("wt_pipeline_destroy", _i32, [_vp]),
+    ("wt_schedule", _i32, [_vp, _P(wt_schedule_desc)]),
+    ("wt_schedule_auto", _i32, [_vp, _i32, _i32, _i32, _i32]),
+    ("wt_schedule_get", _i32, [_vp, _P(_i32), _P(_i32), _P(_i32), _P(wt_group_params)]),
+    ("wt_run", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
+    ("wt_run_host", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
+    ("wt_run_batch", _i32, [_vp, _P(wt_image), _P(wt_image), _i32, _vp]),
+    ("wt_check", _i32, [_vp, _vp]),
+    ("wt_launches_per_run", _i32, [_vp]),
+    ("wt_last_error", ctypes.c_char_p, []),
+    ("wt_version", _i32, []),
+    ("wt_debug_args_size", _i64, []),
+    ("wt_debug_kernel", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, ctypes.c_char_p, _i64,
+                               _P(_i64), _vp, _i64, _P(_i32), ctypes.c_char_p, _i64]),
+    ("wt_debug_compile", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i64)]),
+    ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class WtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def load(build_if_missing: bool = True):
+    """Loads libwt.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                from . import build as _build
+                _build.build()
+            if not os.path.exists(LIB_PATH):
+                raise WtError(WT_EUNSUPPORTED, "libwt.so is not built")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(rc: int):
+    if rc != WT_OK:
+        raise WtError(rc, (load().wt_last_error() or b"").decode(errors="replace"))
+
+
+def stage_array(pipe: dict):
+    """wt_stage[] for a pipeline dict, plus the ctypes objects keeping it alive."""
+    keep = []
+    st = (wt_stage * len(pipe["stages"]))()
+    for i, S in enumerate(pipe["stages"]):
+        ins = (_i32 * max(1, len(S["inputs"])))(*S["inputs"])
+        ops = (wt_op * len(S["ops"]))()
+        for j, t in enumerate(S["ops"]):
+            o = ops[j]
+            o.op = OPCODES[t[0]]
+            o.chan = -1
+            if t[0] == "const":
+                o.value = float(t[1])
+            elif t[0] == "tap":
+                o.slot, o.dx, o.dy = int(t[1]), int(t[2]), int(t[3])
+                if len(t) > 4:
+                    o.chan = int(t[4])
+                if len(t) > 5:
+                    o.mode = TAPMODES[t[5]]
+        keep += [ins, ops]
+        st[i].channels = int(S["channels"])
+        st[i].n_inputs = len(S["inputs"])
+        st[i].inputs = ins
+        st[i].n_ops = len(S["ops"])
+        st[i].ops = ops
+    return st, keep
+
+
+def image(data_ptr: int, width: int, height: int, channels: int, dtype: int, pitch_bytes: int) -> wt_image:
+    return wt_image(data_ptr, width, height, channels, dtype, pitch_bytes)
+
+
+def tensor_image(t) -> wt_image:
+    """wt_image for a torch tensor of shape (C, H, W) or (H, W) with a padded
+    row stride (elements): t.stride(-2) * element size must be a multiple of 16."""
+    import torch
+    dt = {torch.float32: WT_F32, torch.float16: WT_F16, torch.bfloat16: WT_BF16}[t.dtype]
+    if t.dim() == 2:
+        c, h, w = 1, t.shape[0], t.shape[1]
+    else:
+        c, h, w = t.shape
+    es = t.element_size()
+    if t.stride(-1) != 1:
+        raise ValueError("rows must be contiguous")
+    pitch = t.stride(-2) * es
+    if t.dim() == 3 and c > 1 and t.stride(0) != t.stride(1) * h:
+        raise ValueError("channel planes must be height*pitch apart")
+    return wt_image(t.data_ptr(), w, h, c, dt, pitch)
+
+
+class Pipeline:
+    """Owns a wt_pipeline handle."""
+
+    def __init__(self, pipe: dict):
+        lib = load()
+        self.spec = pipe
+        st, self._keep = stage_array(pipe)
+        inch = (_i32 * len(pipe["inputs"]))(*pipe["inputs"])
+        outs = (_i32 * len(pipe["outputs"]))(*pipe["outputs"])
+        h = _vp()
+        check(lib.wt_pipeline_create(st, len(pipe["stages"]), inch, len(pipe["inputs"]), outs,
+                                     len(pipe["outputs"]), 0, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().wt_pipeline_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- scheduling
+    def schedule(self, groups=None, params=None, exec_mode=WT_EXEC_FUSED, intermediate_dtype=-1):
+        """groups: group index per stage (contiguous runs); params: list of dicts
+        with wt_group_params fields, one per group."""
+        n = len(self.spec["stages"])
+        if groups is None:
+            groups = [0] * n
+        ng = max(groups) + 1
+        g = (_i32 * n)(*groups)
+        prm = (wt_group_params * ng)()
+        for i in range(ng):
+            d = dict(tile_h=32, warps_per_block=4, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
+                     n_buffers=0)
+            if params is not None:
+                d.update(params[i] if isinstance(params, (list, tuple)) else params)
+            for k, v in d.items():
+                setattr(prm[i], k, v)
+        desc = wt_schedule_desc(exec_mode, ng, g, prm, intermediate_dtype)
+        check(load().wt_schedule(self.h, ctypes.byref(desc)))
+
+    def schedule_auto(self, width, height, dtype=WT_F32, model=WT_MODEL_ANALYTIC):
+        check(load().wt_schedule_auto(self.h, width, height, dtype, model))
+
+    def schedule_get(self):
+        n = len(self.spec["stages"])
+        ex, ng = _i32(), _i32()
+        check(load().wt_schedule_get(self.h, ctypes.byref(ex), ctypes.byref(ng), None, None))
+        g = (_i32 * n)()
+        prm = (wt_group_params * ng.value)()
+        check(load().wt_schedule_get(self.h, None, None, g, prm))
+        params = [{f: getattr(prm[i], f) for f, _ in wt_group_params._fields_} for i in range(ng.value)]
+        return {"exec": ex.value, "groups": list(g), "params": params}
+
+    def launches_per_run(self) -> int:
+        return int(load().wt_launches_per_run(self.h))
+
+    # -- running
+    def run(self, inputs, outputs, stream=None):
+        """inputs/outputs: lists of wt_image (device memory)."""
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        check(load().wt_run(self.h, ia, len(inputs), oa, len(outputs), stream))
+
+    def run_host(self, inputs, outputs, stream=None):
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        check(load().wt_run_host(self.h, ia, len(inputs), oa, len(outputs), stream))
+
+    def run_batch(self, inputs, outputs, n_images, stream=None):
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        check(load().wt_run_batch(self.h, ia, oa, n_images, stream))
+
+    def check(self, stream=None):
+        check(load().wt_check(self.h, stream))
+
+    # -- introspection
+    def debug_kernel(self, index, inputs, outputs):
+        lib = load()
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        n = _i64()
+        check(lib.wt_debug_kernel(self.h, index, ia, len(inputs), oa, len(outputs), None, 0,
+                                  ctypes.byref(n), None, 0, None, None, 0))
+        src = ctypes.create_string_buffer(n.value + 1)
+        args = ctypes.create_string_buffer(int(lib.wt_debug_args_size()))
+        launch = (_i32 * 8)()
+        kname = ctypes.create_string_buffer(128)
+        check(lib.wt_debug_kernel(self.h, index, ia, len(inputs), oa, len(outputs), src, n.value + 1,
+                                  None, args, len(args), launch, kname, 128))
+        return {"source": src.value.decode(), "args": args.raw, "grid": tuple(launch[0:3]),
+                "block": launch[3], "smem": launch[4], "fused": bool(launch[5]),
+                "n_launches": launch[6], "unroll": launch[7], "name": kname.value.decode()}
+
+    def debug_compile(self, index, inputs, outputs) -> int:
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        n = _i64()
+        check(load().wt_debug_compile(self.h, index, ia, len(inputs), oa, len(outputs), ctypes.byref(n)))
+        return n.value
+
+    def group_geometry(self, group=0, vec=4, frac_reg=1.0):
+        out = (_i32 * 4096)()
+        n = _i32()
+        check(load().wt_debug_group_geometry(self.h, group, vec, frac_reg, out, 4096, ctypes.byref(n)))
+        v = list(out[:n.value])
+        head = dict(zip(["fusable", "halo_l", "halo_r", "halo_t", "halo_b", "unroll", "n_nodes"], v[:7]))
+        nodes = []
+        for i in range(head["n_nodes"]):
+            r = v[7 + 10 * i: 17 + 10 * i]
+            nodes.append(dict(id=r[0], src_chan=r[1], is_source=bool(r[2]), is_liveout=bool(r[3]),
+                              top=r[4], bot=r[5], delay=r[6], window=r[7], xl=r[8] // 1000,
+                              xr=r[8] % 1000, in_smem=bool(r[9])))
+        head["nodes"] = nodes
+        return head
+
+
+class DeviceImage:
+    """A planar device image (torch storage) with a 128-byte-aligned pitch.
+
+    PyTorch only provides the device memory; the library reads and writes it
+    through the wt_image descriptor."""
+
+    def __init__(self, c, h, w, dtype=WT_F32, device="cuda", pin_host=False):
+        import torch
+        tdt = {WT_F32: torch.float32, WT_F16: torch.float16, WT_BF16: torch.bfloat16}[dtype]
+        es = 4 if dtype == WT_F32 else 2
+        pitch_el = (w * es + 127) // 128 * 128 // es
+        if device == "cpu":
+            self.t = torch.empty((c, h, pitch_el), dtype=tdt, pin_memory=pin_host)
+        else:
+            self.t = torch.empty((c, h, pitch_el), dtype=tdt, device=device)
+        self.c, self.h, self.w, self.dtype = c, h, w, dtype
+        self.pitch = pitch_el * es
+
+    def view(self):
+        return self.t[:, :, :self.w]
+
+    def image(self) -> wt_image:
+        return wt_image(self.t.data_ptr(), self.w, self.h, self.c, self.dtype, self.pitch)
+
+    def upload(self, arr):
+        """Stores a float array (C,H,W) or (H,W) after rounding to the dtype."""
+        import numpy as np
+        import torch
+        from . import inputs as _inputs
+        a = np.asarray(arr, dtype=np.float32).reshape(self.c, self.h, self.w)
+        name = {WT_F32: "f32", WT_F16: "f16", WT_BF16: "bf16"}[self.dtype]
+        s = _inputs.storage_array(a, name)
+        if self.dtype == WT_BF16:
+            src = torch.from_numpy(s.view(np.int16)).view(torch.bfloat16)
+        else:
+            src = torch.from_numpy(s)
+        self.view().copy_(src)
+        return self
+
+    def download(self):
+        """float32 numpy copy of the image."""
+        return self.view().float().cpu().numpy()

@@ -1,0 +1,105 @@
+"""Runs a generated group kernel on the CPU through the fiber emulator.
+
+Test infrastructure for the CUDA path's code generator (never used by the
+library): wt_debug_kernel gives the kernel text and its argument block for
+host images; the text after the device-helper block is compiled with g++
+against wt_emu.h and executed lane by lane.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+
+from paper_1909_07190_gb300 import wt
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MARK = "// WT-DEVICE-HELPERS-END"
+CACHE = os.path.join(tempfile.gettempdir(), "wt_emu_cache")
+_loaded = {}
+
+NP_DTYPES = {wt.WT_F32: np.float32, wt.WT_F16: np.float16, wt.WT_BF16: np.uint16}
+
+
+class HostImage:
+    """A planar host image with a 16-byte-multiple pitch (padding poisoned)."""
+
+    def __init__(self, c, h, w, dtype=wt.WT_F32, fill=None):
+        npd = NP_DTYPES[dtype]
+        es = np.dtype(npd).itemsize
+        pitch_el = ((w * es + 63) // 64 * 64) // es + 16 // es  # deliberately > row
+        self.buf = np.empty((c, h, pitch_el), npd)
+        if npd == np.uint16:
+            self.buf.fill(0x7FC1)
+        else:
+            self.buf.fill(np.nan)
+        self.c, self.h, self.w, self.dtype = c, h, w, dtype
+        self.pitch = pitch_el * es
+        if fill is not None:
+            self.view()[...] = fill
+
+    def view(self):
+        return self.buf[:, :, :self.w]
+
+    def image(self):
+        return wt.image(self.buf.ctypes.data, self.w, self.h, self.c, self.dtype, self.pitch)
+
+    def padding_intact(self):
+        pad = self.buf[:, :, self.w:]
+        if pad.dtype == np.uint16:
+            return bool(np.all(pad == 0x7FC1))
+        return bool(np.all(np.isnan(pad)))
+
+
+def _compile(source: str, name: str) -> ctypes.CDLL:
+    body = source.split(MARK, 1)[1]
+    text = '#include "wt_emu.h"\n' + body + \
+        '\nextern "C" long wt_emu_offset_err() { return (long)offsetof(WtArgs, err); }\n'
+    h = hashlib.sha1((text + open(os.path.join(HERE, "wt_emu.h")).read() +
+                      open(os.path.join(HERE, "emu_rt.cpp")).read()).encode()).hexdigest()[:16]
+    if h in _loaded:
+        return _loaded[h]
+    os.makedirs(CACHE, exist_ok=True)
+    so = os.path.join(CACHE, "%s_%s.so" % (name, h))
+    if not os.path.exists(so):
+        src = os.path.join(CACHE, "%s_%s.cpp" % (name, h))
+        with open(src, "w") as f:
+            f.write(text)
+        tmp = so + ".%d.tmp" % os.getpid()
+        r = subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-w", "-I", HERE,
+                            src, os.path.join(HERE, "emu_rt.cpp"), "-o", tmp],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("emulator compile failed:\n" + r.stderr[-5000:])
+        os.replace(tmp, so)
+    lib = ctypes.CDLL(so)
+    _loaded[h] = lib
+    return lib
+
+
+def run(pipe: "wt.Pipeline", index: int, inputs, outputs):
+    """inputs/outputs: HostImage lists.  Runs launch `index` of the plan."""
+    ii = [x.image() for x in inputs]
+    oo = [x.image() for x in outputs]
+    d = pipe.debug_kernel(index, ii, oo)
+    lib = _compile(d["source"], d["name"])
+    args = bytearray(d["args"])
+    err = np.zeros(16, np.int32)
+    off = lib.wt_emu_offset_err()
+    args[off:off + 8] = int(err.ctypes.data).to_bytes(8, "little")
+    abuf = (ctypes.c_char * len(args)).from_buffer(args)
+    kfn = ctypes.cast(getattr(lib, d["name"]), ctypes.c_void_p)
+    lib.wt_emu_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
+    msg = ctypes.create_string_buffer(512)
+    gx, gy, gz = d["grid"]
+    rc = lib.wt_emu_run(kfn, ctypes.addressof(abuf), gx, gy, gz, d["block"], d["smem"], msg, 512)
+    if rc != 0:
+        raise RuntimeError("emulated kernel failed: " + msg.value.decode())
+    if err[0] != 0:
+        raise RuntimeError("emulated kernel raised error word %d" % err[0])
+    return d

@@ -1,0 +1,109 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every
+symbol the headers declare, validates DAGs and schedules, and reports errors
+through wt_status + wt_last_error."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1909_07190_gb300 import pipelines as P
+from paper_1909_07190_gb300 import wt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in ("wt.h", "wt_debug.h"):
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(wt_[a-z_0-9]+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = wt.load()
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names == {s[0] for s in wt.SIGNATURES}
+
+
+def test_version():
+    assert wt.load().wt_version() >= 100
+
+
+def _create(stages, inputs=(1,), outputs=(0,)):
+    st, keep = wt.stage_array({"stages": stages, "inputs": list(inputs), "outputs": list(outputs)})
+    h = ctypes.c_void_p()
+    ic = (ctypes.c_int32 * len(inputs))(*inputs)
+    oc = (ctypes.c_int32 * len(outputs))(*outputs)
+    rc = wt.load().wt_pipeline_create(st, len(stages), ic, len(inputs), oc, len(outputs), 0, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("stages,msg", [
+    ([{"channels": 1, "inputs": [1], "ops": [("tap", 0, 0, 0)]},
+      {"channels": 1, "inputs": [-1], "ops": [("tap", 0, 0, 0)]}], "topological"),
+    ([{"channels": 1, "inputs": [-1], "ops": [("tap", 0, 0, 0), ("add",)]}], "underflow"),
+    ([{"channels": 1, "inputs": [-1], "ops": [("tap", 0, 0, 0, -1, "up2")]}], "level"),
+    ([{"channels": 1, "inputs": [-1], "ops": [("tap", 0, 0, 0, 3)]}], "channel"),
+    ([{"channels": 1, "inputs": [-1], "ops": [("tap", 0, 99, 0)]}], "offset"),
+])
+def test_malformed_dag_rejected(stages, msg):
+    rc, h = _create(stages)
+    assert rc == wt.WT_EINVAL
+    assert msg in wt.load().wt_last_error().decode()
+
+
+def test_schedule_validation():
+    p = wt.Pipeline(P.harris())
+    with pytest.raises(wt.WtError, match="contiguous"):
+        p.schedule(groups=[0, 1, 0, 1, 1, 1, 1, 1, 1, 1, 1])
+    with pytest.raises(wt.WtError, match="tile_h"):
+        p.schedule(params=[dict(tile_h=0)])
+    with pytest.raises(wt.WtError, match="frac_reg"):
+        p.schedule(params=[dict(frac_reg=1.5)])
+    p.schedule(groups=[0] * 5 + [1] * 6, params=[dict(tile_h=8), dict(tile_h=16)])
+    s = p.schedule_get()
+    assert s["groups"] == [0] * 5 + [1] * 6 and s["params"][1]["tile_h"] == 16
+
+
+def test_launch_counts():
+    p = wt.Pipeline(P.harris())
+    assert p.launches_per_run() == 1
+    p.schedule(exec_mode=wt.WT_EXEC_PLAIN)
+    assert p.launches_per_run() == 11
+    b = wt.Pipeline(P.blend())
+    b.schedule(exec_mode=wt.WT_EXEC_PLAIN)
+    assert b.launches_per_run() == 36
+
+
+def test_bad_images_rejected_without_gpu():
+    p = wt.Pipeline(P.sharpen())
+    buf = np.zeros((8, 64), np.float32)
+    good = wt.image(buf.ctypes.data, 16, 8, 1, wt.WT_F32, 256)
+    bad_pitch = wt.image(buf.ctypes.data, 16, 8, 1, wt.WT_F32, 100)
+    empty = wt.image(buf.ctypes.data, 0, 8, 1, wt.WT_F32, 256)
+    with pytest.raises(wt.WtError, match="pitch"):
+        p.debug_kernel(0, [bad_pitch], [good])
+    with pytest.raises(wt.WtError, match="empty"):
+        p.debug_kernel(0, [empty], [good])
+    wrong = wt.image(buf.ctypes.data, 15, 8, 1, wt.WT_F32, 256)
+    with pytest.raises(wt.WtError, match="output 0"):
+        p.debug_kernel(0, [good], [wrong])
+
+
+def test_generated_kernels_compile_for_sm103a():
+    """NVRTC compiles the generated kernels for sm_103a (no GPU needed)."""
+    buf = np.zeros((64, 256), np.float32)
+    img = wt.image(buf.ctypes.data, 200, 64, 1, wt.WT_F32, 1024)
+    for name in ("sharpen", "harris"):
+        p = wt.Pipeline(P.by_name(name))
+        assert p.debug_compile(0, [img], [img]) > 10000
+        p.schedule(exec_mode=wt.WT_EXEC_PLAIN)
+        assert p.debug_compile(0, [img], [img]) > 1000
