@@ -138,7 +138,10 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
       if (inside) ids.push_back(g.node_of(e.producer, -1));
       else
         for (int ch : e.chans) ids.push_back(g.node_of(e.producer, norm_chan(ch, pc)));
-      for (int id : ids) d = std::max(d, g.nodes[id].delay + e.dymax);
+      // max(dymax, 0): with clamp-to-edge a tap above the consumer's row can
+      // resolve to the producer's row 0 at the top border, so the producer
+      // must have reached the consumer's own row as well.
+      for (int id : ids) d = std::max(d, g.nodes[id].delay + std::max(e.dymax, 0));
     }
     c.delay = d == INT_MIN ? 0 : d;
   }
@@ -154,7 +157,9 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
         for (int ch : e.chans) ids.push_back(g.node_of(e.producer, norm_chan(ch, pc)));
       for (int id : ids) {
         Node &q = g.nodes[id];
-        q.window = std::max(q.window, c.delay - q.delay - e.dymin + 1);
+        // keep rows down to the consumer's own row too (min(dymin, 0)): a
+        // tap below it can resolve to the last image row at the bottom border
+        q.window = std::max(q.window, c.delay - q.delay - std::min(e.dymin, 0) + 1);
       }
     }
   }

@@ -95,6 +95,7 @@ void install(wt::Pipeline &p, const wt_schedule_desc *d) {
   }
   s.installed = true;
   p.sched = s;
+  p.sched_version++;
 }
 
 int64_t image_bytes(const wt_image &im) {
@@ -142,6 +143,7 @@ wt_status wt_schedule_auto(wt_pipeline *p, int32_t width, int32_t height, int32_
     std::lock_guard<std::mutex> lk(p->mu);
     wt::Schedule s = wt::auto_schedule(*p, width, height, dtype, model);
     p->sched = s;
+    p->sched_version++;
   });
 }
 
@@ -174,8 +176,7 @@ wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const
     if (!p) wt::fail(WT_EINVAL, "null pipeline");
     if (!inputs || !outputs) wt::fail(WT_EINVAL, "null image array");
     std::lock_guard<std::mutex> lk(p->mu);
-    wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
-    wt::run_plan(*p, plan, (cudaStream_t)stream);
+    wt::run(*p, inputs, n_inputs, outputs, n_outputs, (cudaStream_t)stream);
   });
 }
 
@@ -218,8 +219,7 @@ wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, 
       if (!outputs[k].data) wt::fail(WT_EINVAL, "null host output");
       dout[k].data = stage(100 + k, outputs[k]);
     }
-    wt::RunPlan plan = wt::build_plan(*p, din.data(), n_inputs, dout.data(), n_outputs);
-    wt::run_plan(*p, plan, st);
+    wt::run(*p, din.data(), n_inputs, dout.data(), n_outputs, st);
     for (int k = 0; k < n_outputs; k++)
       wt::check_rt(cudaMemcpyAsync(outputs[k].data, dout[k].data, (size_t)image_bytes(outputs[k]),
                                    cudaMemcpyDeviceToHost, st),

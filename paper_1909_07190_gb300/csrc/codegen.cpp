@@ -72,7 +72,12 @@ FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key) {
   if (L.out_w < V)
     fail(WT_EUNSUPPORTED, "group halo (" + std::to_string(g.halo_l) + "+" +
                               std::to_string(g.halo_r) + " px) too wide for a warp tile");
-  L.chunk = std::max({key.chunk, g.halo_t + 1, g.max_src_window});
+  // Chunks hold a multiple of the unroll factor U so that waits and issues
+  // happen only at the start of an unrolled block (branch-free blocks).
+  const int U = std::max(1, g.unroll);
+  L.issue_blk = ((g.max_src_window - 1) + U - 1) / U * U;
+  int ch = std::max({key.chunk, g.halo_t + 1, g.max_src_window, L.issue_blk + U});
+  L.chunk = (ch + U - 1) / U * U;
   L.nbuf = std::max(2, key.nbuf);
   L.ring = L.chunk * L.nbuf;
   int nsx = g.halo_b;
@@ -418,10 +423,6 @@ void emit_step(Ctx &c, bool safe, int u) {
   o << "{ // step phase " << u << (safe ? " (guarded)" : " (steady)") << "\n";
   o << "const int k = kb + " << u << ";\n";
   if (safe) o << "if (k >= nsteps) goto wt_tile_end;\n";
-  o << "if (k % CH == 0) { const int c_ = k / CH; if (c_ * CH < nrows) {"
-       " const int gc_ = cbase + c_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
-       " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = c_; goto wt_fail; } } }\n";
-  o << "if (k % CH == ISSUE) { const int c_ = k / CH + NB - 1; if (c_ * CH < nrows) { issue_chunk(c_); } }\n";
   // temporaries for shared-memory windows used this step
   std::set<std::pair<int, int>> all;
   for (size_t ni = 0; ni < c.g.nodes.size(); ni++) {
@@ -483,7 +484,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   o << kDeviceSource;
   o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
   o << "#define CH " << L.chunk << "\n#define NB " << L.nbuf
-    << "\n#define RING " << L.ring << "\n#define ISSUE " << (g.max_src_window - 1) << "\n";
+    << "\n#define RING " << L.ring << "\n#define ISSUE " << L.issue_blk << "\n";
   for (int s = 0; s < n_src; s++) o << "#define ROWB" << s << " " << L.boxw[s] * L.esz[s] << "\n";
   o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", 1) " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
@@ -562,7 +563,14 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // Steady-state steps of interior tiles run the guard-free body; all
   // other steps run the guarded body (both unrolled over U phases so that
   // register windows rotate by renaming).
-  o << "for (int kb = 0;; kb += U) {\n";
+  o << "for (int kb = 0; kb < nsteps; kb += U) {\n";
+  // TMA bookkeeping once per block: wait for the chunk this block starts,
+  // refill the buffer whose rows no step reads any more.
+  o << "{ const int kc_ = kb % CH;\n"
+       "if (kc_ == 0) { const int c_ = kb / CH; if (c_ * CH < nrows) {"
+       " const int gc_ = cbase + c_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
+       " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = c_; goto wt_fail; } } }\n"
+       "if (kc_ == ISSUE) { const int c_ = kb / CH + NB - 1; if (c_ * CH < nrows) issue_chunk(c_); } }\n";
   o << "if (kb >= kf0 && kb < kf1) {\n";
   for (int u = 0; u < c.U; u++) emit_step(c, false, u);
   o << "} else {\n";

@@ -114,71 +114,6 @@ struct Kernel {
 
 struct Workspace;  // runtime buffers (defined in runtime.cpp)
 
-struct Pipeline {
-  std::vector<Stage> stages;
-  std::vector<int> in_channels;
-  std::vector<int> outputs;
-  std::vector<std::vector<int>> consumers;
-  std::vector<char> is_output;
-  Schedule sched;
-  std::mutex mu;
-  std::shared_ptr<Workspace> ws;
-  uint64_t hash = 0;
-};
-
-// ir.cpp
-void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch,
-                    int n_in, const int32_t *outs, int n_out);
-void level_dims(int W, int H, int level, int *w, int *h);
-uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull);
-
-// analysis.cpp
-GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int vec,
-                        float frac_reg, int dtype_bytes);
-int elem_bytes(int dtype);
-
-// codegen.cpp
-struct CodegenKey {
-  std::vector<int> stages;
-  int vec = 4;
-  std::vector<int> src_dtypes, dst_dtypes;
-  float frac_reg = 1.f;
-  int max_regs = 0;
-  int nw = 4;        // warps per block (launch bound)
-  int chunk = 8;     // TMA rows per chunk
-  int nbuf = 3;      // TMA buffers per source
-  bool plain = false;
-  bool persistent = false;
-  std::string str() const;
-};
-
-// Shared-memory layout and tile geometry of a fused group kernel.
-struct FusedLayout {
-  int V = 4;
-  int lpad = 0, rpad = 0, out_w = 0;  // x halo (multiples of V), output columns
-  int chunk = 8, nbuf = 3, ring = 24; // ring = chunk * nbuf rows
-  int nsx = 0;                        // nsteps = halo_t + tile_h + nsx
-  int src_rows_extra = 0;             // source rows = halo_t + tile_h + halo_b
-  std::vector<int> boxw;              // per source: TMA box width (elements)
-  std::vector<int> esz;               // per source: element bytes
-  std::vector<int> ring_off;          // per source: byte offset in the warp slice
-  std::vector<int> win_off;           // per node: smem window offset (-1 = regs)
-  int bar_off = 0;
-  int warp_bytes = 0;
-  int chunk_bytes = 0;                // expect_tx per chunk (all sources)
-};
-FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key);
-std::string emit_fused(const Pipeline &p, const GroupGeom &g, const CodegenKey &key,
-                       const std::string &kname);
-std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key,
-                       const std::string &kname);
-// Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
-struct PlainSrc {
-  int slot, chan;
-};
-std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid);
-extern const char *kDeviceSource;  // device_src.cpp
-
 // Launch-argument block shared by every generated kernel (device layout is
 // mirrored in the device source).
 struct alignas(64) TmapBytes {
@@ -218,5 +153,90 @@ struct alignas(64) KernelArgs {
   int32_t pad0;
   const void *img_tab;        // per-image SrcDesc/DstDesc/tmaps
 };
+
+
+// Launches of earlier runs, reused while the schedule, the device, the
+// workspace and the image descriptors stay the same (no re-planning, no
+// tensor-map re-encoding).
+struct CachedRun {
+  std::vector<void *> functions;   // CUfunction per launch
+  std::vector<KernelArgs> args;
+  std::vector<unsigned> grid;      // 3 per launch
+  std::vector<int> block, smem;
+};
+struct RunCache {
+  int device = -1;
+  uint64_t sched_version = 0;
+  uint64_t ws_generation = 0;
+  std::map<std::string, CachedRun> runs;  // key: raw bytes of the descriptors
+};
+
+struct Pipeline {
+  std::vector<Stage> stages;
+  std::vector<int> in_channels;
+  std::vector<int> outputs;
+  std::vector<std::vector<int>> consumers;
+  std::vector<char> is_output;
+  Schedule sched;
+  uint64_t sched_version = 1;
+  RunCache cache;
+  std::mutex mu;
+  std::shared_ptr<Workspace> ws;
+  uint64_t hash = 0;
+};
+
+// ir.cpp
+void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch,
+                    int n_in, const int32_t *outs, int n_out);
+void level_dims(int W, int H, int level, int *w, int *h);
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull);
+
+// analysis.cpp
+GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int vec,
+                        float frac_reg, int dtype_bytes);
+int elem_bytes(int dtype);
+
+// codegen.cpp
+struct CodegenKey {
+  std::vector<int> stages;
+  int vec = 4;
+  std::vector<int> src_dtypes, dst_dtypes;
+  float frac_reg = 1.f;
+  int max_regs = 0;
+  int nw = 4;        // warps per block (launch bound)
+  int chunk = 8;     // TMA rows per chunk
+  int nbuf = 3;      // TMA buffers per source
+  bool plain = false;
+  bool persistent = false;
+  std::string str() const;
+};
+
+// Shared-memory layout and tile geometry of a fused group kernel.
+struct FusedLayout {
+  int V = 4;
+  int lpad = 0, rpad = 0, out_w = 0;  // x halo (multiples of V), output columns
+  int chunk = 8, nbuf = 3, ring = 24; // ring = chunk * nbuf rows
+  int issue_blk = 0;                  // block offset in a chunk that refills a buffer
+  int nsx = 0;                        // nsteps = halo_t + tile_h + nsx
+  int src_rows_extra = 0;             // source rows = halo_t + tile_h + halo_b
+  std::vector<int> boxw;              // per source: TMA box width (elements)
+  std::vector<int> esz;               // per source: element bytes
+  std::vector<int> ring_off;          // per source: byte offset in the warp slice
+  std::vector<int> win_off;           // per node: smem window offset (-1 = regs)
+  int bar_off = 0;
+  int warp_bytes = 0;
+  int chunk_bytes = 0;                // expect_tx per chunk (all sources)
+};
+FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key);
+std::string emit_fused(const Pipeline &p, const GroupGeom &g, const CodegenKey &key,
+                       const std::string &kname);
+std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key,
+                       const std::string &kname);
+// Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
+struct PlainSrc {
+  int slot, chan;
+};
+std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid);
+extern const char *kDeviceSource;  // device_src.cpp
 
 }  // namespace wt

@@ -52,6 +52,7 @@ struct Workspace {
   char *base = nullptr;
   int64_t bytes = 0;
   int32_t *err = nullptr;
+  uint64_t generation = 1;         // bumped when `base` is reallocated
   std::map<int, Staging> staging;  // wt_run_host device copies
   ~Workspace();
 };
@@ -65,6 +66,8 @@ void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws
 Kernel &get_kernel(const Pipeline &p, const Launch &L, int device);
 void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream);
 Workspace &workspace(Pipeline &p, int64_t bytes);
-void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream);
+void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string *cache_key = nullptr);
+// wt_run: reuses the cached launches when schedule and images are unchanged.
+void run(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out, cudaStream_t stream);
 
 }  // namespace wt

@@ -1,0 +1,177 @@
+"""Generated kernels executed on the CPU by the lane emulator (tests/emu),
+compared with the FP64 oracle.  This checks the code generator's tiling,
+halo, window, clamp-to-edge and load-type logic without a GPU; the same
+kernel text runs on the GPU in the -m gpu tests."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1909_07190_gb300 import inputs as I
+from paper_1909_07190_gb300 import pipelines as P
+from paper_1909_07190_gb300 import wt
+
+from emu import emu
+
+
+def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mode=wt.WT_EXEC_FUSED,
+                 launch=0):
+    p = wt.Pipeline(spec)
+    if exec_mode == wt.WT_EXEC_PLAIN:
+        p.schedule(exec_mode=exec_mode)
+    else:
+        p.schedule(groups=groups, params=params)
+    shapes = O.shapes(spec["stages"], [np.zeros((c,) + imgs[0].shape[-2:]) for c in spec["inputs"]])
+    ins = [emu.HostImage(c, a.shape[-2], a.shape[-1], dtype) for a, c in zip(imgs, spec["inputs"])]
+    for h, a in zip(ins, imgs):
+        name = {wt.WT_F32: "f32", wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
+        h.view()[...] = I.storage_array(np.asarray(a, np.float32).reshape(h.view().shape), name)
+    outs = []
+    for sid in spec["outputs"]:
+        _, w, h, c = shapes[sid]
+        outs.append(emu.HostImage(c, h, w, dtype))
+    d = emu.run(p, launch, ins, outs)
+    for i in range(1, d["n_launches"]):
+        emu.run(p, i, ins, outs)
+    assert d["fused"] == (exec_mode == wt.WT_EXEC_FUSED)
+    for o in outs:
+        assert o.padding_intact(), "kernel wrote outside the image"
+    name = {wt.WT_F32: "f32", wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
+    return [I.from_storage(o.view(), name) for o in outs], d
+
+
+def oracle_of(spec, imgs):
+    return O.evaluate(spec["stages"], [np.asarray(a, np.float64) for a in imgs], spec["outputs"])
+
+
+def rnd(seed, w, h, c=1, dtype="f32"):
+    return I.round_to(I.uniform_image(seed, w, h, c), dtype)
+
+
+@pytest.mark.parametrize("name", ["sharpen", "harris", "blur"])
+@pytest.mark.parametrize("w,h", [(1, 1), (7, 5), (150, 70), (260, 9)])
+def test_fused_sizes(name, w, h):
+    spec = P.by_name(name)
+    img = rnd(w * 31 + h, w, h)
+    got, _ = run_emulated(spec, [img], params=[dict(tile_h=16, warps_per_block=2)])
+    ref = oracle_of(spec, [img])
+    assert np.abs(got[0] - ref[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("tile_h,frac,vec", [(1, 1.0, 4), (3, 0.0, 4), (5, 0.5, 8), (40, 0.0, 8), (2, 0.3, 4)])
+def test_fused_params(tile_h, frac, vec):
+    spec = P.harris()
+    img = rnd(5, 140, 61)
+    got, d = run_emulated(spec, [img], params=[dict(tile_h=tile_h, frac_reg=frac, vec=vec, warps_per_block=2)])
+    ref = oracle_of(spec, [img])
+    assert np.abs(got[0] - ref[0]).max() <= 1e-5
+
+
+def test_fused_sharpen_shared_windows():
+    spec = P.sharpen()
+    img = rnd(6, 133, 47)
+    got, _ = run_emulated(spec, [img], params=[dict(tile_h=7, frac_reg=0.0, warps_per_block=1)])
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [(wt.WT_F16, 2e-3), (wt.WT_BF16, 1.6e-2)])
+def test_fused_16bit(dtype, tol):
+    spec = P.harris()
+    name = {wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
+    img = rnd(7, 100, 40, dtype=name)
+    got, _ = run_emulated(spec, [img], dtype=dtype, params=[dict(tile_h=8, vec=4)])
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= tol
+
+
+def random_dag(seed, n_stages=6, n_inputs=2):
+    """Seeded random single-level DAG: stencils and pointwise combinations
+    with offsets in [-2, 2] and bounded values (test input, not a pipeline)."""
+    rng = np.random.default_rng(seed)
+    b = P.Builder("rand%d" % seed, [1] * n_inputs)
+    ids = [P.input_id(j) for j in range(n_inputs)]
+    outs = []
+    for s in range(n_stages):
+        k = int(rng.integers(1, 4))
+        expr = None
+        for _ in range(k):
+            src = ids[int(rng.integers(0, len(ids)))]
+            dx, dy = int(rng.integers(-2, 3)), int(rng.integers(-2, 3))
+            w = float(rng.uniform(-0.6, 0.6))
+            t = w * P.ref(src, dx, dy)
+            expr = t if expr is None else expr + t
+        kind = int(rng.integers(0, 4))
+        if kind == 1:
+            expr = P.emin(expr, 0.4)
+        elif kind == 2:
+            expr = P.eabs(expr) * 0.5
+        elif kind == 3:
+            other = ids[int(rng.integers(0, len(ids)))]
+            expr = expr * P.ref(other, int(rng.integers(-1, 2)), 0)
+        sid = b.stage("s%d" % s, expr)
+        ids.append(sid)
+        if rng.uniform() < 0.3:
+            outs.append(sid)
+    if ids[-1] not in outs:
+        outs.append(ids[-1])
+    b.output(*outs)
+    return b.build()
+
+
+@pytest.mark.parametrize("seed,frac,tile_h,vec", [(1, 0.6, 6, 4), (2, 0.0, 3, 4), (3, 1.0, 11, 8), (4, 0.3, 1, 4),
+                                                  (5, 0.6, 6, 8), (6, 1.0, 2, 4), (7, 0.0, 9, 8), (8, 0.5, 4, 4)])
+def test_fused_random_dags(seed, frac, tile_h, vec):
+    spec = random_dag(seed)
+    imgs = [rnd(100 + seed, 97, 43), rnd(200 + seed, 97, 43)]
+    got, _ = run_emulated(spec, imgs, params=[dict(tile_h=tile_h, warps_per_block=2, frac_reg=frac, vec=vec)])
+    ref = oracle_of(spec, imgs)
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() <= 1e-5 * max(1.0, np.abs(r).max())
+
+
+def single_stage(expr_fn, in_channels, channels):
+    b = P.Builder("one", in_channels)
+    b.output(b.stage("s", expr_fn(), channels))
+    return b.build()
+
+
+@pytest.mark.parametrize("mode", ["same", "down2", "up2"])
+def test_plain_kernel_modes(mode):
+    inp = P.input_id(0)
+    b = P.Builder("m", [1])
+    if mode == "same":
+        b.output(b.stage("s", P.linear(inp, P.SOBEL_X, 0.125) + P.XPAR * 0.5 - P.YPAR * 0.25))
+    else:
+        d = b.stage("d", P._down(inp))
+        b.output(d)
+        if mode == "up2":
+            b.output(b.stage("u", P._up(d) - P.ref(inp, 1, -1)))
+    spec = b.build()
+    for w, h in [(37, 23), (1, 1), (2, 3)]:
+        img = rnd(41 + w, w, h)
+        got, _ = run_emulated(spec, [img], exec_mode=wt.WT_EXEC_PLAIN)
+        for g, r in zip(got, oracle_of(spec, [img])):
+            assert np.abs(g - r).max() <= 1e-5
+
+
+def test_plain_kernel_channels():
+    """3-channel stage reading a 3-channel and a 1-channel input (broadcast)."""
+    spec = single_stage(lambda: P.ref(P.input_id(0), 1, 0) * P.ref(P.input_id(1), 0, -1, chan=0)
+                        + P.ref(P.input_id(0), 0, 0, chan=2), [3, 1], 3)
+    A = rnd(42, 29, 17, 3)
+    M = rnd(43, 29, 17, 1)
+    got, _ = run_emulated(spec, [A, M], exec_mode=wt.WT_EXEC_PLAIN)
+    assert np.abs(got[0] - oracle_of(spec, [A, M])[0]).max() <= 1e-6
+
+
+def test_fused_multichannel_group():
+    """Fused group over 3-channel stages with a 1-channel mask source."""
+    inp, m = P.input_id(0), P.input_id(1)
+    b = P.Builder("mc", [3, 1])
+    s0 = b.stage("blur", P.linear(inp, [[1, 2, 1]], 0.25), 3)
+    s1 = b.stage("mix", P.ref(m, 0, 0, chan=0) * P.ref(s0, 0, 1) + P.ref(inp, 0, 0, chan=1), 3)
+    b.output(s1)
+    spec = b.build()
+    A = rnd(44, 70, 33, 3)
+    M = rnd(45, 70, 33, 1)
+    got, d = run_emulated(spec, [A, M], params=[dict(tile_h=8, warps_per_block=2)])
+    assert d["fused"]
+    assert np.abs(got[0] - oracle_of(spec, [A, M])[0]).max() <= 1e-6

@@ -170,7 +170,7 @@ def test_full_size_sharpen_sampled():
     rng = np.random.default_rng(1)
     xs = np.concatenate([rng.integers(0, W, 400), [0, W - 1, 0, W - 1]])
     ys = np.concatenate([rng.integers(0, H, 400), [0, H - 1, H - 1, 0]])
-    ref = O.evaluate_points(spec["stages"], [img[None].astype(np.float64)], spec["outputs"][0], xs, ys)
+    ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys)
     assert np.abs(got[0][ys, xs] - ref).max() <= TOL["f32"]
 
 
@@ -184,7 +184,7 @@ def test_full_size_harris_sampled_and_plain_equal(dtype):
     rng = np.random.default_rng(2)
     xs = np.concatenate([rng.integers(0, W, 300), [0, W - 1, 0, W - 1, 5, W - 3]])
     ys = np.concatenate([rng.integers(0, H, 300), [0, H - 1, H - 1, 0, H - 2, 3]])
-    ref = O.evaluate_points(spec["stages"], [img[None].astype(np.float64)], spec["outputs"][0], xs, ys)
+    ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys)
     assert np.abs(fused[0][ys, xs] - ref).max() <= TOL[dtype]
     if dtype == "f32":
         plain = run_pipe(spec, [img], exec_mode=wt.WT_EXEC_PLAIN)[0][0]
