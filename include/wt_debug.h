@@ -38,6 +38,14 @@ wt_status wt_debug_compile(wt_pipeline *p, int32_t launch_index, const wt_image 
                            int32_t n_inputs, const wt_image *outputs, int32_t n_outputs,
                            int64_t *cubin_bytes);
 
+/* Shared-memory layout of fused launch `launch_index` for these images:
+ * out = [bytes per warp, mbarrier offset, chunk rows, buffers, pixels per
+ * lane, output columns per warp tile, n_sources, then per source: staging
+ * ring offset, bytes per buffer, TMA box width (elements), element bytes]. */
+wt_status wt_debug_layout(wt_pipeline *p, int32_t launch_index, const wt_image *inputs,
+                          int32_t n_inputs, const wt_image *outputs, int32_t n_outputs,
+                          int32_t *out, int32_t cap, int32_t *n_out);
+
 /* Halo/window analysis of schedule group `group` (Sec. 4 overlap, Sec. 5
  * parallelogram skew): out = [fusable, halo_l, halo_r, halo_t, halo_b,
  * unroll, n_nodes, then per node: id, src_chan, is_source, is_liveout, top,

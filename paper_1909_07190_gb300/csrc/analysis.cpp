@@ -9,14 +9,24 @@
 // parallelogram tiles of warp width W_i parallel to the group's right
 // hyperplane.  This implementation splits along y with W_y = 1: each
 // parallelogram tile is one skewed row, processed in order.  The skew of
-// stage n is its delay e_n = max over producers (e_p + dymax): at step k it
-// computes row y_top + k - e_n, so every right-hyperplane dependence is
-// already available (no cyclic dependence between adjacent tiles).  A stage
-// keeps the last `window` rows it produced, which is exactly the set of its
-// earlier parallelogram tiles its consumers still read.
+// node n is its delay e_n = max over producers (e_p + max(dymax, 0)): at
+// step k it computes row y_top + k - e_n, so every right-hyperplane
+// dependence is already available (no cyclic dependence between adjacent
+// tiles).  A node keeps the last `window` rows it produced: the earlier
+// parallelogram tiles its consumers still read.
+//
+// Kernel nodes: the group's sources (values read from memory), its stages,
+// and, for every linear stencil whose weight matrix has rank one (Sobel,
+// box, binomial), a synthetic row pass: S = sum_{i,j} u_j v_i P(x+i, y+j)
+// becomes H = sum_i v_i P(x+i, y) and S = sum_j u_j H(x, y+j).  With
+// clamp-to-edge at every read both forms are the same function (the clamps
+// in x and y commute); only the rounding differs.
 #include <algorithm>
 #include <climits>
+#include <cmath>
+#include <map>
 #include <numeric>
+#include <tuple>
 
 #include "wt_internal.hpp"
 
@@ -27,7 +37,7 @@ int elem_bytes(int dtype) { return dtype == WT_F32 ? 4 : 2; }
 int GroupGeom::node_of(int id, int chan) const {
   for (size_t i = 0; i < nodes.size(); i++) {
     const Node &n = nodes[i];
-    if (n.id != id) continue;
+    if (n.synthetic || n.id != id) continue;
     if (!n.is_source) return (int)i;
     if (n.src_chan == chan) return (int)i;
   }
@@ -39,8 +49,182 @@ static int norm_chan(int chan, int src_channels) {
   return chan;  // -1 = tile channel, else fixed
 }
 
+namespace {
+
+// Linear form of a postfix program: sum of coef * tap(node, dx, dy) + c.
+struct Lin {
+  bool ok = true;
+  bool is_const = true;
+  double c = 0;
+  std::map<std::tuple<int, int, int>, double> t;
+};
+
+Lin lin_scale(Lin a, double s) {
+  a.c *= s;
+  for (auto &kv : a.t) kv.second *= s;
+  return a;
+}
+
+Lin lin_add(const Lin &a, const Lin &b, double sb) {
+  Lin r;
+  r.ok = a.ok && b.ok;
+  r.is_const = a.is_const && b.is_const;
+  r.c = a.c + sb * b.c;
+  r.t = a.t;
+  for (auto &kv : b.t) r.t[kv.first] += sb * kv.second;
+  return r;
+}
+
+Lin linear_form(const std::vector<KOp> &prog) {
+  std::vector<Lin> st;
+  Lin bad;
+  bad.ok = false;
+  for (const KOp &o : prog) {
+    switch (o.op) {
+      case WT_OP_CONST: {
+        Lin l;
+        l.c = o.value;
+        st.push_back(l);
+      } break;
+      case WT_OP_TAP: {
+        Lin l;
+        l.is_const = false;
+        l.t[std::make_tuple(o.node, o.dx, o.dy)] = 1.0;
+        st.push_back(l);
+      } break;
+      case WT_OP_ADD: case WT_OP_SUB: {
+        Lin b = st.back(); st.pop_back();
+        Lin a = st.back(); st.pop_back();
+        st.push_back(lin_add(a, b, o.op == WT_OP_ADD ? 1.0 : -1.0));
+      } break;
+      case WT_OP_MUL: {
+        Lin b = st.back(); st.pop_back();
+        Lin a = st.back(); st.pop_back();
+        if (!a.ok || !b.ok) st.push_back(bad);
+        else if (a.is_const) st.push_back(lin_scale(b, a.c));
+        else if (b.is_const) st.push_back(lin_scale(a, b.c));
+        else st.push_back(bad);
+      } break;
+      case WT_OP_DIV: {
+        Lin b = st.back(); st.pop_back();
+        Lin a = st.back(); st.pop_back();
+        if (!a.ok || !b.ok || !b.is_const || b.c == 0) st.push_back(bad);
+        else st.push_back(lin_scale(a, 1.0 / b.c));
+      } break;
+      case WT_OP_NEG: st.back() = lin_scale(st.back(), -1.0); break;
+      case WT_OP_MIN: case WT_OP_MAX:
+        st.pop_back();
+        st.back() = bad;
+        break;
+      case WT_OP_XPAR: case WT_OP_YPAR: st.push_back(bad); break;
+      default: st.back() = bad;  // abs, sqrt: not linear in the taps
+    }
+  }
+  return st.empty() ? bad : st.back();
+}
+
+void push_const(std::vector<KOp> &p, double v) {
+  KOp o;
+  o.op = WT_OP_CONST;
+  o.value = (float)v;
+  p.push_back(o);
+}
+
+void push_op(std::vector<KOp> &p, int op) {
+  KOp o;
+  o.op = op;
+  p.push_back(o);
+}
+
+// sum_k w_k tap(node, dx_k, dy_k) as a postfix program (zeros skipped).
+std::vector<KOp> weighted_sum(int node, const std::vector<std::tuple<int, int, double>> &terms) {
+  std::vector<KOp> p;
+  bool first = true;
+  for (auto &t : terms) {
+    double w = std::get<2>(t);
+    if (w == 0) continue;
+    KOp tap;
+    tap.op = WT_OP_TAP;
+    tap.node = node;
+    tap.dx = std::get<0>(t);
+    tap.dy = std::get<1>(t);
+    p.push_back(tap);
+    if (w != 1.0) {
+      push_const(p, w);
+      push_op(p, WT_OP_MUL);
+    }
+    if (!first) push_op(p, WT_OP_ADD);
+    first = false;
+  }
+  if (first) push_const(p, 0.0);
+  return p;
+}
+
+// Splits node `ni` if its program is a rank-one linear stencil of one
+// producer; returns the index of the new synthetic row-pass node or -1.
+int try_split(GroupGeom &g, int ni) {
+  Lin l = linear_form(g.nodes[ni].prog);
+  if (!l.ok || l.is_const || l.t.empty()) return -1;
+  int prod = std::get<0>(l.t.begin()->first);
+  int x0 = INT_MAX, x1 = INT_MIN, y0 = INT_MAX, y1 = INT_MIN, nnz = 0;
+  double wmax = 0;
+  for (auto &kv : l.t) {
+    if (std::get<0>(kv.first) != prod) return -1;
+    if (kv.second == 0) continue;
+    nnz++;
+    x0 = std::min(x0, std::get<1>(kv.first));
+    x1 = std::max(x1, std::get<1>(kv.first));
+    y0 = std::min(y0, std::get<2>(kv.first));
+    y1 = std::max(y1, std::get<2>(kv.first));
+    wmax = std::max(wmax, std::fabs(kv.second));
+  }
+  if (nnz == 0 || x1 == x0 || y1 == y0) return -1;  // already one-dimensional
+  const int nx = x1 - x0 + 1, ny = y1 - y0 + 1;
+  std::vector<double> W((size_t)nx * ny, 0.0);
+  int pi = 0, pj = 0;
+  double pv = 0;
+  for (auto &kv : l.t) {
+    int i = std::get<1>(kv.first) - x0, j = std::get<2>(kv.first) - y0;
+    W[(size_t)j * nx + i] = kv.second;
+    if (std::fabs(kv.second) > std::fabs(pv)) {
+      pv = kv.second;
+      pi = i;
+      pj = j;
+    }
+  }
+  std::vector<double> v(nx), u(ny);
+  for (int i = 0; i < nx; i++) v[i] = W[(size_t)pj * nx + i];
+  for (int j = 0; j < ny; j++) u[j] = W[(size_t)j * nx + pi] / pv;
+  int nv = 0, nu = 0;
+  for (int i = 0; i < nx; i++) nv += v[i] != 0;
+  for (int j = 0; j < ny; j++) nu += u[j] != 0;
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++)
+      if (std::fabs(W[(size_t)j * nx + i] - u[j] * v[i]) > 1e-9 * wmax) return -1;  // rank > 1
+  if (nv + nu >= nnz) return -1;  // no saving
+  Node h;
+  h.synthetic = true;
+  h.id = g.nodes[ni].id;
+  h.channels = g.nodes[ni].channels;
+  std::vector<std::tuple<int, int, double>> ht, vt;
+  for (int i = 0; i < nx; i++) ht.emplace_back(x0 + i, 0, v[i]);
+  h.prog = weighted_sum(prod, ht);
+  const int hi = (int)g.nodes.size();
+  g.nodes.push_back(h);
+  for (int j = 0; j < ny; j++) vt.emplace_back(0, y0 + j, u[j]);
+  std::vector<KOp> np = weighted_sum(hi, vt);
+  if (l.c != 0) {
+    push_const(np, l.c);
+    push_op(np, WT_OP_ADD);
+  }
+  g.nodes[ni].prog = np;
+  return hi;
+}
+
+}  // namespace
+
 GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int vec,
-                        float frac_reg, int dtype_bytes) {
+                        float frac_reg, int dtype_bytes, bool split_separable) {
   GroupGeom g;
   g.stages = stages;
   std::vector<char> in_group(p.stages.size(), 0);
@@ -54,6 +238,7 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
       g.why_not = "group spans several levels";
     }
   }
+  auto pchan = [&](int pid) { return pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1]; };
   // Sources: distinct (producer outside the group, channel spec).
   for (int s : stages) {
     for (const Edge &e : p.stages[s].edges) {
@@ -62,7 +247,7 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
         g.fusable = false;
         g.why_not = "group contains a down/up-sampling tap";
       }
-      int pc = e.producer >= 0 ? p.stages[e.producer].channels : p.in_channels[-e.producer - 1];
+      int pc = pchan(e.producer);
       if (inside) {
         for (int c : e.chans) {
           int cc = norm_chan(c, pc);
@@ -85,7 +270,8 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
       }
     }
   }
-  int n_src = (int)g.nodes.size();
+  const int n_src = (int)g.nodes.size();
+  for (int i = 0; i < n_src; i++) g.order.push_back(i);
   for (int s : stages) {
     Node n;
     n.id = s;
@@ -97,71 +283,104 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
     g.nodes.push_back(n);
     if (out) g.liveouts.push_back(s);
   }
-  // Backward halo propagation (reverse topological order).
+  // Programs over kernel nodes.
+  for (int s : stages) {
+    const int ni = g.node_of(s, -1);
+    const Stage &S = p.stages[s];
+    for (const Op &op : S.ops) {
+      KOp k;
+      k.op = op.op;
+      k.value = op.value;
+      if (op.op == WT_OP_TAP) {
+        int pid = S.inputs[op.slot];
+        bool inside = pid >= 0 && in_group[pid];
+        k.node = inside ? g.node_of(pid, -1) : g.node_of(pid, norm_chan(op.chan, pchan(pid)));
+        k.dx = op.dx;
+        k.dy = op.dy;
+        if (k.node < 0) fail(WT_EINVAL, "internal: tap node not found");
+      }
+      g.nodes[ni].prog.push_back(k);
+    }
+  }
+  for (int s : stages) {
+    const int ni = g.node_of(s, -1);
+    if (split_separable && g.fusable) {
+      int hi = try_split(g, ni);
+      if (hi >= 0) {
+        g.order.push_back(hi);
+        g.n_split++;
+      }
+    }
+    g.order.push_back(ni);
+  }
+  // Edges (consumer node, producer node) with footprint boxes.
+  std::map<std::pair<int, int>, NodeEdge> em;
+  for (int ni : g.order) {
+    for (const KOp &k : g.nodes[ni].prog) {
+      if (k.op != WT_OP_TAP) continue;
+      auto key = std::make_pair(ni, k.node);
+      auto it = em.find(key);
+      if (it == em.end()) {
+        em[key] = NodeEdge{ni, k.node, k.dx, k.dx, k.dy, k.dy};
+      } else {
+        NodeEdge &e = it->second;
+        e.dxmin = std::min(e.dxmin, k.dx);
+        e.dxmax = std::max(e.dxmax, k.dx);
+        e.dymin = std::min(e.dymin, k.dy);
+        e.dymax = std::max(e.dymax, k.dy);
+      }
+    }
+  }
+  for (auto &kv : em) g.edges.push_back(kv.second);
+  std::vector<int> pos(g.nodes.size(), 0);
+  for (size_t i = 0; i < g.order.size(); i++) pos[g.order[i]] = (int)i;
+  // Backward halo propagation (reverse evaluation order).
   const int UNSET = INT_MIN / 4;
   for (Node &n : g.nodes) n.top = n.bot = n.left = n.right = UNSET;
   for (Node &n : g.nodes)
-    if (!n.is_source && n.is_liveout) n.top = n.bot = n.left = n.right = 0;
-  for (int i = (int)stages.size() - 1; i >= 0; i--) {
-    int s = stages[i];
-    Node &c = g.nodes[g.node_of(s, -1)];
-    if (c.top == UNSET) c.top = c.bot = c.left = c.right = 0;  // dead stage
-    for (const Edge &e : p.stages[s].edges) {
-      int pc = e.producer >= 0 ? p.stages[e.producer].channels : p.in_channels[-e.producer - 1];
-      bool inside = e.producer >= 0 && in_group[e.producer];
-      std::vector<int> ids;
-      if (inside) ids.push_back(g.node_of(e.producer, -1));
-      else
-        for (int ch : e.chans) ids.push_back(g.node_of(e.producer, norm_chan(ch, pc)));
-      for (int id : ids) {
-        Node &q = g.nodes[id];
-        q.left = std::max(q.left, std::max(0, c.left - e.dxmin));
-        q.right = std::max(q.right, std::max(0, c.right + e.dxmax));
-        q.top = std::max(q.top, std::max(0, c.top - e.dymin));
-        q.bot = std::max(q.bot, std::max(0, c.bot + e.dymax));
-        q.xl = std::max(q.xl, std::max(0, -e.dxmin));
-        q.xr = std::max(q.xr, std::max(0, e.dxmax));
-      }
+    if (!n.is_source && !n.synthetic && n.is_liveout) n.top = n.bot = n.left = n.right = 0;
+  for (int oi = (int)g.order.size() - 1; oi >= n_src; oi--) {
+    const int ci = g.order[oi];
+    Node &c = g.nodes[ci];
+    if (c.top == UNSET) c.top = c.bot = c.left = c.right = 0;  // dead node
+    for (const NodeEdge &e : g.edges) {
+      if (e.c != ci) continue;
+      Node &q = g.nodes[e.p];
+      q.left = std::max(q.left, std::max(0, c.left - e.dxmin));
+      q.right = std::max(q.right, std::max(0, c.right + e.dxmax));
+      q.top = std::max(q.top, std::max(0, c.top - e.dymin));
+      q.bot = std::max(q.bot, std::max(0, c.bot + e.dymax));
+      q.xl = std::max(q.xl, std::max(0, -e.dxmin));
+      q.xr = std::max(q.xr, std::max(0, e.dxmax));
     }
   }
   for (Node &n : g.nodes)
     if (n.top == UNSET) n.top = n.bot = n.left = n.right = 0;
   // Delays (forward) and windows.
-  for (int i = 0; i < n_src; i++) g.nodes[i].delay = 0;
-  for (int s : stages) {
-    Node &c = g.nodes[g.node_of(s, -1)];
-    int d = INT_MIN;
-    for (const Edge &e : p.stages[s].edges) {
-      int pc = e.producer >= 0 ? p.stages[e.producer].channels : p.in_channels[-e.producer - 1];
-      bool inside = e.producer >= 0 && in_group[e.producer];
-      std::vector<int> ids;
-      if (inside) ids.push_back(g.node_of(e.producer, -1));
-      else
-        for (int ch : e.chans) ids.push_back(g.node_of(e.producer, norm_chan(ch, pc)));
-      // max(dymax, 0): with clamp-to-edge a tap above the consumer's row can
-      // resolve to the producer's row 0 at the top border, so the producer
-      // must have reached the consumer's own row as well.
-      for (int id : ids) d = std::max(d, g.nodes[id].delay + std::max(e.dymax, 0));
+  for (int oi = 0; oi < (int)g.order.size(); oi++) {
+    const int ci = g.order[oi];
+    Node &c = g.nodes[ci];
+    if (c.is_source) {
+      c.delay = 0;
+      continue;
     }
+    int d = INT_MIN;
+    // max(dymax, 0): with clamp-to-edge a tap above the consumer's row can
+    // resolve to the producer's row 0 at the top border, so the producer
+    // must have reached the consumer's own row as well.
+    for (const NodeEdge &e : g.edges)
+      if (e.c == ci) {
+        if (pos[e.p] >= oi) fail(WT_EINVAL, "internal: node order");
+        d = std::max(d, g.nodes[e.p].delay + std::max(e.dymax, 0));
+      }
     c.delay = d == INT_MIN ? 0 : d;
   }
   for (Node &n : g.nodes) n.window = 1;
-  for (int s : stages) {
-    const Node &c = g.nodes[g.node_of(s, -1)];
-    for (const Edge &e : p.stages[s].edges) {
-      int pc = e.producer >= 0 ? p.stages[e.producer].channels : p.in_channels[-e.producer - 1];
-      bool inside = e.producer >= 0 && in_group[e.producer];
-      std::vector<int> ids;
-      if (inside) ids.push_back(g.node_of(e.producer, -1));
-      else
-        for (int ch : e.chans) ids.push_back(g.node_of(e.producer, norm_chan(ch, pc)));
-      for (int id : ids) {
-        Node &q = g.nodes[id];
-        // keep rows down to the consumer's own row too (min(dymin, 0)): a
-        // tap below it can resolve to the last image row at the bottom border
-        q.window = std::max(q.window, c.delay - q.delay - std::min(e.dymin, 0) + 1);
-      }
-    }
+  for (const NodeEdge &e : g.edges) {
+    Node &q = g.nodes[e.p];
+    // keep rows down to the consumer's own row too (min(dymin, 0)): a tap
+    // below it can resolve to the last image row at the bottom border
+    q.window = std::max(q.window, g.nodes[e.c].delay - q.delay - std::min(e.dymin, 0) + 1);
   }
   g.halo_l = g.halo_r = g.halo_t = g.halo_b = 0;
   g.max_delay = 0;

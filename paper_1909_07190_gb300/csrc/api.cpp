@@ -333,6 +333,29 @@ wt_status wt_debug_compile(wt_pipeline *p, int32_t launch_index, const wt_image 
   });
 }
 
+wt_status wt_debug_layout(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, int32_t n_inputs,
+                          const wt_image *outputs, int32_t n_outputs, int32_t *out, int32_t cap, int32_t *n_out) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
+    if (launch_index < 0 || launch_index >= (int)plan.launches.size()) wt::fail(WT_EINVAL, "launch index");
+    const wt::Launch &L = plan.launches[launch_index];
+    if (!L.fused) wt::fail(WT_EINVAL, "not a fused launch");
+    const wt::FusedLayout &F = L.layout;
+    std::vector<int32_t> v = {F.warp_bytes, F.bar_off, F.chunk, F.nbuf, F.V, F.out_w, (int32_t)F.boxw.size()};
+    for (size_t s = 0; s < F.boxw.size(); s++) {
+      v.push_back(F.ring_off[s]);
+      v.push_back(F.bufb[s]);
+      v.push_back(F.boxw[s]);
+      v.push_back(F.esz[s]);
+    }
+    if (n_out) *n_out = (int32_t)v.size();
+    if (out)
+      for (int i = 0; i < (int)v.size() && i < cap; i++) out[i] = v[i];
+  });
+}
+
 wt_status wt_debug_group_geometry(wt_pipeline *p, int32_t group, int32_t vec, float frac_reg, int32_t *out,
                                   int32_t cap, int32_t *n_out) {
   return guard([&] {

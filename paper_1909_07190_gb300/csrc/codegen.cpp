@@ -96,11 +96,14 @@ FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key) {
     int A = 16 / esz;
     int boxw = 32 * V + ((V % A) ? A : 0);
     if (boxw > 256) fail(WT_EUNSUPPORTED, "TMA box wider than 256 elements");
+    // every TMA destination (each staging buffer) starts on a 128-byte
+    // boundary: buffers are padded to a multiple of 128 bytes
     off = align_up(off, 128);
     L.boxw.push_back(boxw);
     L.esz.push_back(esz);
     L.ring_off.push_back(off);
-    off += L.nbuf * L.chunk * boxw * esz;
+    L.bufb.push_back(align_up(L.chunk * boxw * esz, 128));
+    off += L.nbuf * L.bufb.back();
     L.chunk_bytes += L.chunk * boxw * esz;
   }
   L.win_off.assign(g.nodes.size(), -1);
@@ -203,6 +206,14 @@ void emit_shift(Ctx &c, int ni) {
     for (int j = 0; j < wd; j++) c.o << reg(ni, s, j) << " = " << reg(ni, s + 1, j) << ";\n";
 }
 
+// Address of the lane's pixels of ring row `ri` of source s.
+std::string ring_row(int s, const std::string &ri) {
+  std::string S = std::to_string(s);
+  // chunk c of the current tile sits in buffer (cbase + c) % NB, where cbase
+  // counts the chunks of the warp's earlier tiles
+  return "lp" + S + " + ((cbase + " + ri + " / CH) % NB) * BUFB" + S + " + (" + ri + " % CH) * ROWB" + S;
+}
+
 // Row of a register-resident source, loaded from the TMA ring.
 void emit_source_row(Ctx &c, int ni, bool safe, int u) {
   const Node &n = c.g.nodes[ni];
@@ -218,8 +229,7 @@ void emit_source_row(Ctx &c, int ni, bool safe, int u) {
   o << "float";
   for (int e = 0; e < V; e++) o << (e ? ", " : " ") << v[e];
   o << ";\n";
-  emit_load_vec(c, c.key.src_dtypes[s], "lp" + std::to_string(s) + " + (ri % RING) * ROWB" +
-                                            std::to_string(s), v, c.L.esz[s]);
+  emit_load_vec(c, c.key.src_dtypes[s], ring_row(s, "ri"), v, c.L.esz[s]);
   if (safe) emit_xfix(c, v);
   int sl = slot_of(n, u, 0);
   emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
@@ -241,8 +251,7 @@ void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
     int s = n.src_index;
     o << "int ri = k - " << a << ";\n";
     if (safe) o << "ri = wt_clampi(y_top + ri, 0, H - 1) - y_top;\n";
-    emit_load_vec(c, c.key.src_dtypes[s], "lp" + std::to_string(s) + " + (ri % RING) * ROWB" +
-                                              std::to_string(s), v, c.L.esz[s]);
+    emit_load_vec(c, c.key.src_dtypes[s], ring_row(s, "ri"), v, c.L.esz[s]);
     if (safe) emit_xfix(c, v);
   } else {
     o << "int kk = k - " << a << ";\n";
@@ -256,23 +265,17 @@ void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
   o << "}\n";
 }
 
-// Postfix program of stage `sid` -> C++ expression for element e.
-std::string emit_expr(Ctx &c, int sid, int ni_c, int e, int u) {
-  const Stage &S = c.p.stages[sid];
+// Postfix program of kernel node `ni` -> C++ expression for element e.
+std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
   const Node &cn = c.g.nodes[ni_c];
   std::vector<std::string> st;
-  for (const Op &op : S.ops) {
+  for (const KOp &op : cn.prog) {
     switch (op.op) {
       case WT_OP_CONST: st.push_back(flt(op.value)); break;
       case WT_OP_XPAR: st.push_back(flt((float)(e & 1))); break;
       case WT_OP_YPAR: st.push_back("((float)(r & 1))"); break;
       case WT_OP_TAP: {
-        int pid = S.inputs[op.slot];
-        int pc = pid >= 0 ? c.p.stages[pid].channels : c.p.in_channels[-pid - 1];
-        bool inside = pid >= 0 && std::find(c.g.stages.begin(), c.g.stages.end(), pid) != c.g.stages.end();
-        int spec = inside ? -1 : (pc == 1 ? 0 : op.chan);
-        int pi = c.g.node_of(pid, spec);
-        if (pi < 0) fail(WT_EINVAL, "internal: tap node not found");
+        const int pi = op.node;
         const Node &pn = c.g.nodes[pi];
         int a = cn.delay - pn.delay - op.dy;
         int j = pn.xl + e + op.dx;
@@ -288,34 +291,27 @@ std::string emit_expr(Ctx &c, int sid, int ni_c, int e, int u) {
         st.pop_back();
         std::string a = st.back();
         st.pop_back();
-        const char *f = nullptr;
         switch (op.op) {
           case WT_OP_ADD: st.push_back("(" + a + " + " + b + ")"); break;
           case WT_OP_SUB: st.push_back("(" + a + " - " + b + ")"); break;
           case WT_OP_MUL: st.push_back("(" + a + " * " + b + ")"); break;
           case WT_OP_DIV: st.push_back("(" + a + " / " + b + ")"); break;
-          case WT_OP_MIN: f = "fminf"; break;
-          case WT_OP_MAX: f = "fmaxf"; break;
+          case WT_OP_MIN: st.push_back("fminf(" + a + ", " + b + ")"); break;
+          case WT_OP_MAX: st.push_back("fmaxf(" + a + ", " + b + ")"); break;
           default: fail(WT_EINVAL, "internal: opcode");
         }
-        if (f) st.push_back(std::string(f) + "(" + a + ", " + b + ")");
       }
     }
   }
   return st.back();
 }
 
-// (producer node, age) pairs a stage reads from shared-memory windows.
-std::vector<std::pair<int, int>> smem_reads(Ctx &c, int sid, int ni_c) {
+// (producer node, age) pairs a node reads from shared-memory windows.
+std::vector<std::pair<int, int>> smem_reads(Ctx &c, int ni_c) {
   std::vector<std::pair<int, int>> r;
-  const Stage &S = c.p.stages[sid];
-  for (const Op &op : S.ops) {
+  for (const KOp &op : c.g.nodes[ni_c].prog) {
     if (op.op != WT_OP_TAP) continue;
-    int pid = S.inputs[op.slot];
-    int pc = pid >= 0 ? c.p.stages[pid].channels : c.p.in_channels[-pid - 1];
-    bool inside = pid >= 0 && std::find(c.g.stages.begin(), c.g.stages.end(), pid) != c.g.stages.end();
-    int spec = inside ? -1 : (pc == 1 ? 0 : op.chan);
-    int pi = c.g.node_of(pid, spec);
+    const int pi = op.node;
     if (!c.g.nodes[pi].in_smem) continue;
     std::pair<int, int> pr{pi, c.g.nodes[ni_c].delay - c.g.nodes[pi].delay - op.dy};
     if (std::find(r.begin(), r.end(), pr) == r.end()) r.push_back(pr);
@@ -362,14 +358,13 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
   const Node &n = c.g.nodes[ni];
   auto &o = c.o;
   const int V = c.V;
-  int sid = n.id;
   emit_shift(c, ni);
   if (safe)
     o << "if (k >= " << c.ks[ni] << " && k <= T + (" << c.kec[ni] << ")) {\n";
   o << "{\n";
   o << "const int r = y_top + k - (" << n.delay << ");\n";
   o << "(void)r;\n";
-  for (auto &pr : smem_reads(c, sid, ni)) {
+  for (auto &pr : smem_reads(c, ni)) {
     if (!safe && loaded.count(pr)) continue;
     emit_load_tmp(c, pr.first, pr.second, safe);
     if (!safe) loaded.insert(pr);
@@ -389,7 +384,7 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     }
     o << "} else {\n";
   }
-  for (int e = 0; e < V; e++) o << v[e] << " = " << emit_expr(c, sid, ni, e, u) << ";\n";
+  for (int e = 0; e < V; e++) o << v[e] << " = " << emit_expr(c, ni, e, u) << ";\n";
   if (safe) {
     o << "}\n";
     emit_xfix(c, v);
@@ -425,10 +420,9 @@ void emit_step(Ctx &c, bool safe, int u) {
   if (safe) o << "if (k >= nsteps) goto wt_tile_end;\n";
   // temporaries for shared-memory windows used this step
   std::set<std::pair<int, int>> all;
-  for (size_t ni = 0; ni < c.g.nodes.size(); ni++) {
-    const Node &n = c.g.nodes[ni];
-    if (n.is_source) continue;
-    for (auto &pr : smem_reads(c, n.id, (int)ni)) all.insert(pr);
+  for (int ni : c.g.order) {
+    if (c.g.nodes[ni].is_source) continue;
+    for (auto &pr : smem_reads(c, ni)) all.insert(pr);
   }
   for (auto &pr : all) {
     const Node &pn = c.g.nodes[pr.first];
@@ -437,13 +431,13 @@ void emit_step(Ctx &c, bool safe, int u) {
     o << ";\n";
   }
   std::set<std::pair<int, int>> loaded;
-  for (size_t ni = 0; ni < c.g.nodes.size(); ni++) {
+  for (int ni : c.g.order) {
     const Node &n = c.g.nodes[ni];
     if (n.is_source) {
-      if (!n.in_smem) emit_source_row(c, (int)ni, safe, u);
+      if (!n.in_smem) emit_source_row(c, ni, safe, u);
       continue;
     }
-    emit_stage(c, (int)ni, safe, u, loaded);
+    emit_stage(c, ni, safe, u, loaded);
   }
   o << "}\n";
 }
@@ -485,7 +479,8 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
   o << "#define CH " << L.chunk << "\n#define NB " << L.nbuf
     << "\n#define RING " << L.ring << "\n#define ISSUE " << L.issue_blk << "\n";
-  for (int s = 0; s < n_src; s++) o << "#define ROWB" << s << " " << L.boxw[s] * L.esz[s] << "\n";
+  for (int s = 0; s < n_src; s++)
+    o << "#define ROWB" << s << " " << L.boxw[s] * L.esz[s] << "\n#define BUFB" << s << " " << L.bufb[s] << "\n";
   o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", 1) " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
   o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
@@ -516,8 +511,10 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
     o << "const int tx = tt_[1], ty = tt_[2], ch = tt_[3];\n";
   } else {
-    o << "{\n";
-    o << "const int tile = blockIdx.x * " << key.nw << " + warp;\nif (tile >= a.n_tiles) return;\n";
+    // persistent warps: each warp strides over the tiles (grid sized by the
+    // host to the resident capacity of the GPU)
+    o << "for (int tile = blockIdx.x * " << key.nw << " + warp; tile < a.n_tiles; tile += gridDim.x * "
+      << key.nw << ") {\n";
     o << "const WtArgs &ia = a;\n";
     o << "const int tx = tile % a.tiles_x;\nconst int tr_ = tile / a.tiles_x;\n"
          "const int ty = tr_ % a.tiles_y;\nconst int ch = tr_ / a.tiles_y;\n";
@@ -552,7 +549,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
        "wt_mbar_expect_tx(b_, "
     << L.chunk_bytes << "u);\n";
   for (int s = 0; s < n_src; s++)
-    o << "wt_tma_load_3d(wt_smem_u32(rb" << s << " + (gc_ % NB) * (CH * ROWB" << s << ")), &ia.tmap["
+    o << "wt_tma_load_3d(wt_smem_u32(rb" << s << " + (gc_ % NB) * BUFB" << s << "), &ia.tmap["
       << s << "], xb" << s << ", y_top + c_ * CH, zc" << s << ", b_);\n";
   o << "}\nissued = c_ + 1;\n};\n";
   o << "for (int c_ = 0; c_ < NB - 1; c_++) if (c_ * CH < nrows) issue_chunk(c_);\n";

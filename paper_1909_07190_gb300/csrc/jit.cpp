@@ -46,6 +46,7 @@ const Driver &driver() {
     WT_RESOLVE(cuFuncGetAttribute, funcGetAttribute);
     WT_RESOLVE(cuTensorMapEncodeTiled, tensorMapEncodeTiled);
     WT_RESOLVE(cuGetErrorString, getErrorString);
+    WT_RESOLVE(cuOccupancyMaxActiveBlocksPerMultiprocessor, occupancyMaxActiveBlocksPerMultiprocessor);
     g_drv.ok = true;
   });
   if (!g_drv.ok) fail(WT_ECUDA, g_drv_err.empty() ? "CUDA driver unavailable" : g_drv_err);

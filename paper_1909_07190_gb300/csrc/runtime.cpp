@@ -384,6 +384,22 @@ void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string
   CachedRun c;
   for (Launch &L : plan.launches) {
     Kernel &k = get_kernel(p, L, dev);
+    if (L.fused) {
+      // persistent warps: no more blocks than can be resident at once
+      const Driver &drv = driver();
+      if (L.smem > 48 * 1024)
+        check_cu(drv.funcSetAttribute((CUfunction)k.function, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                      L.smem),
+                 "cuFuncSetAttribute");
+      int per_sm = 0, sms = 0;
+      check_cu(drv.occupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (CUfunction)k.function, L.block,
+                                                             (size_t)L.smem),
+               "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+      check_rt(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+      if (per_sm < 1) fail(WT_EUNSUPPORTED, "group kernel cannot be resident (registers/shared memory)");
+      L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
+      L.resident_blocks_per_sm = per_sm;
+    }
     KernelArgs a;
     fill_args(p, plan, L, w.base, a, L.fused);
     a.err = w.err;

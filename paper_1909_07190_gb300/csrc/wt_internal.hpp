@@ -68,8 +68,18 @@ struct Schedule {
 
 // Geometry of one fused group (Sec. 4 OTPW and Sec. 5 hybrid tiling, in the
 // streaming form used here: split dimension y, one lane row per warp).
+// One op of a kernel node's postfix program; taps name kernel nodes.
+struct KOp {
+  int op = 0;
+  int node = -1;  // WT_OP_TAP: producer node index
+  int dx = 0, dy = 0;
+  float value = 0.f;
+};
+
 struct Node {
   int id = 0;             // stage id, or -(j+1) for a pipeline input
+  bool synthetic = false; // row pass of a split separable stencil (no stage)
+  std::vector<KOp> prog;  // stages and synthetic nodes: program over nodes
   int src_chan = -1;      // sources: channel spec (-1 = tile channel)
   bool is_source = false; // read from memory (pipeline input or earlier group)
   bool is_liveout = false;
@@ -85,9 +95,17 @@ struct Node {
   int dst_index = -1;     // liveouts: index into the kernel's dst table
 };
 
+struct NodeEdge {
+  int c = 0, p = 0;  // consumer and producer node
+  int dxmin = 0, dxmax = 0, dymin = 0, dymax = 0;
+};
+
 struct GroupGeom {
   std::vector<int> stages;     // stage ids (topological)
-  std::vector<Node> nodes;     // sources first, then stages (same order)
+  std::vector<Node> nodes;     // stable indices: sources, stages, synthetic
+  std::vector<int> order;      // evaluation order (sources first)
+  std::vector<NodeEdge> edges;
+  int n_split = 0;             // separable stencils split into two passes
   std::vector<int> liveouts;   // stage ids
   bool fusable = true;         // else: per-stage kernel
   std::string why_not;         // reason when !fusable
@@ -193,7 +211,7 @@ uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull);
 
 // analysis.cpp
 GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int vec,
-                        float frac_reg, int dtype_bytes);
+                        float frac_reg, int dtype_bytes, bool split_separable = true);
 int elem_bytes(int dtype);
 
 // codegen.cpp
@@ -220,6 +238,7 @@ struct FusedLayout {
   int nsx = 0;                        // nsteps = halo_t + tile_h + nsx
   int src_rows_extra = 0;             // source rows = halo_t + tile_h + halo_b
   std::vector<int> boxw;              // per source: TMA box width (elements)
+  std::vector<int> bufb;              // per source: bytes per staging buffer (128-multiple)
   std::vector<int> esz;               // per source: element bytes
   std::vector<int> ring_off;          // per source: byte offset in the warp slice
   std::vector<int> win_off;           // per node: smem window offset (-1 = regs)

@@ -21,6 +21,7 @@ struct Driver {
                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill) = nullptr;
   CUresult (*getErrorString)(CUresult, const char **) = nullptr;
+  CUresult (*occupancyMaxActiveBlocksPerMultiprocessor)(int *, CUfunction, int, size_t) = nullptr;
 };
 
 const Driver &driver();

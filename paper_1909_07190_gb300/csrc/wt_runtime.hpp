@@ -31,6 +31,7 @@ struct Launch {
   unsigned grid[3] = {1, 1, 1};
   int block = 128;
   int smem = 0;
+  int resident_blocks_per_sm = 0;
 };
 
 struct RunPlan {

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("wt_debug_kernel", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, ctypes.c_char_p, _i64,
                                _P(_i64), _vp, _i64, _P(_i32), ctypes.c_char_p, _i64]),
     ("wt_debug_compile", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i64)]),
+    ("wt_debug_layout", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
 ]
 
@@ -272,6 +273,18 @@ class Pipeline:
         n = _i64()
         check(load().wt_debug_compile(self.h, index, ia, len(inputs), oa, len(outputs), ctypes.byref(n)))
         return n.value
+
+    def debug_layout(self, index, inputs, outputs):
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        out = (_i32 * 256)()
+        n = _i32()
+        check(load().wt_debug_layout(self.h, index, ia, len(inputs), oa, len(outputs), out, 256, ctypes.byref(n)))
+        v = list(out[:n.value])
+        d = dict(zip(["warp_bytes", "bar_off", "chunk", "nbuf", "vec", "out_w", "n_src"], v[:7]))
+        d["sources"] = [dict(zip(["ring_off", "bufb", "boxw", "esz"], v[7 + 4 * i: 11 + 4 * i]))
+                        for i in range(d["n_src"])]
+        return d
 
     def group_geometry(self, group=0, vec=4, frac_reg=1.0):
         out = (_i32 * 4096)()

@@ -81,8 +81,10 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
     return lib
 
 
-def run(pipe: "wt.Pipeline", index: int, inputs, outputs):
-    """inputs/outputs: HostImage lists.  Runs launch `index` of the plan."""
+def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None):
+    """inputs/outputs: HostImage lists.  Runs launch `index` of the plan
+    (with at most `max_blocks` blocks: persistent warps then take several
+    tiles each)."""
     ii = [x.image() for x in inputs]
     oo = [x.image() for x in outputs]
     d = pipe.debug_kernel(index, ii, oo)
@@ -97,6 +99,8 @@ def run(pipe: "wt.Pipeline", index: int, inputs, outputs):
                                ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
     msg = ctypes.create_string_buffer(512)
     gx, gy, gz = d["grid"]
+    if max_blocks is not None and d["fused"]:
+        gx = min(gx, max_blocks)
     rc = lib.wt_emu_run(kfn, ctypes.addressof(abuf), gx, gy, gz, d["block"], d["smem"], msg, 512)
     if rc != 0:
         raise RuntimeError("emulated kernel failed: " + msg.value.decode())

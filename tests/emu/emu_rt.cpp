@@ -23,7 +23,7 @@ struct Lane {
 ucontext_t g_main;
 Lane g_lanes[32];
 int g_cur = 0;
-EmuDim g_bidx{0, 0, 0}, g_bdim{32, 1, 1};
+EmuDim g_bidx{0, 0, 0}, g_bdim{32, 1, 1}, g_gdim{1, 1, 1};
 void (*g_kernel)(WtArgs) = nullptr;
 const WtArgs *g_args = nullptr;
 // collective state
@@ -90,6 +90,7 @@ extern "C" {
 EmuDim *wt_emu_thread_idx() { return &g_lanes[g_cur].tid; }
 EmuDim *wt_emu_block_idx() { return &g_bidx; }
 EmuDim *wt_emu_block_dim() { return &g_bdim; }
+EmuDim *wt_emu_grid_dim() { return &g_gdim; }
 unsigned char *wt_emu_smem() { return wt_emu_smem_array; }
 void wt_emu_fail(const char *msg) { g_fail = msg; }
 
@@ -136,6 +137,7 @@ int wt_emu_run(void *kernel, const void *args, int gx, int gy, int gz, int block
       g_lanes[l].stack = (char *)p;
     }
   g_bdim = EmuDim{(unsigned)block, 1, 1};
+  g_gdim = EmuDim{(unsigned)gx, (unsigned)gy, (unsigned)gz};
   for (int bz = 0; bz < gz; bz++)
     for (int by = 0; by < gy; by++)
       for (int bx = 0; bx < gx; bx++) {

@@ -67,6 +67,7 @@ extern "C" {
 EmuDim *wt_emu_thread_idx();
 EmuDim *wt_emu_block_idx();
 EmuDim *wt_emu_block_dim();
+EmuDim *wt_emu_grid_dim();
 float wt_emu_shfl(float v, int src_lane, int kind);  // kind 0 idx, 1 up, 2 down
 int wt_emu_shfl_i(int v, int src_lane, int kind);
 int wt_emu_all(int pred);
@@ -78,6 +79,7 @@ void wt_emu_yield();
 #define threadIdx (*wt_emu_thread_idx())
 #define blockIdx (*wt_emu_block_idx())
 #define blockDim (*wt_emu_block_dim())
+#define gridDim (*wt_emu_grid_dim())
 #define wt_smem wt_emu_smem_array
 
 static inline float __shfl_sync(unsigned, float v, int l) { return wt_emu_shfl(v, l, 0); }

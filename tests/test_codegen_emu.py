@@ -14,7 +14,7 @@ from emu import emu
 
 
 def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mode=wt.WT_EXEC_FUSED,
-                 launch=0):
+                 launch=0, max_blocks=None):
     p = wt.Pipeline(spec)
     if exec_mode == wt.WT_EXEC_PLAIN:
         p.schedule(exec_mode=exec_mode)
@@ -29,9 +29,9 @@ def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mod
     for sid in spec["outputs"]:
         _, w, h, c = shapes[sid]
         outs.append(emu.HostImage(c, h, w, dtype))
-    d = emu.run(p, launch, ins, outs)
+    d = emu.run(p, launch, ins, outs, max_blocks)
     for i in range(1, d["n_launches"]):
-        emu.run(p, i, ins, outs)
+        emu.run(p, i, ins, outs, max_blocks)
     assert d["fused"] == (exec_mode == wt.WT_EXEC_FUSED)
     for o in outs:
         assert o.padding_intact(), "kernel wrote outside the image"
@@ -70,6 +70,16 @@ def test_fused_sharpen_shared_windows():
     spec = P.sharpen()
     img = rnd(6, 133, 47)
     got, _ = run_emulated(spec, [img], params=[dict(tile_h=7, frac_reg=0.0, warps_per_block=1)])
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("max_blocks", [1, 3])
+def test_fused_persistent_warps(max_blocks):
+    """Fewer blocks than tiles: each warp walks several tiles (mbarrier
+    phases and staging buffers carry over between tiles)."""
+    spec = P.harris()
+    img = rnd(8, 300, 77)
+    got, _ = run_emulated(spec, [img], params=[dict(tile_h=5, warps_per_block=2)], max_blocks=max_blocks)
     assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
 
 

@@ -107,3 +107,30 @@ def test_generated_kernels_compile_for_sm103a():
         assert p.debug_compile(0, [img], [img]) > 10000
         p.schedule(exec_mode=wt.WT_EXEC_PLAIN)
         assert p.debug_compile(0, [img], [img]) > 1000
+
+
+@pytest.mark.parametrize("name", ["sharpen", "harris", "blur"])
+@pytest.mark.parametrize("dtype", [wt.WT_F32, wt.WT_F16, wt.WT_BF16])
+@pytest.mark.parametrize("vec", [4, 8])
+@pytest.mark.parametrize("chunk", [0, 5, 8])
+def test_tma_layout_alignment(name, dtype, vec, chunk):
+    """Every TMA destination (each staging buffer of every source, in every
+    warp slice) starts on a 128-byte boundary; box rows are multiples of 16
+    bytes and at most 256 elements; the mbarriers are 8-byte aligned."""
+    es = 4 if dtype == wt.WT_F32 else 2
+    buf = np.zeros((64, 512), np.uint8)
+    img = wt.image(buf.ctypes.data, 100, 40, 1, dtype, 1024)
+    p = wt.Pipeline(P.by_name(name))
+    p.schedule(params=[dict(tile_h=16, vec=vec, chunk_rows=chunk, warps_per_block=3)])
+    L = p.debug_layout(0, [img], [img])
+    assert L["warp_bytes"] % 128 == 0 and L["bar_off"] % 8 == 0
+    assert L["chunk"] >= 1 and L["nbuf"] >= 2
+    for s in L["sources"]:
+        assert s["esz"] == es
+        assert s["boxw"] <= 256 and (s["boxw"] * es) % 16 == 0
+        assert s["bufb"] % 128 == 0 and s["bufb"] >= L["chunk"] * s["boxw"] * es
+        for b in range(L["nbuf"]):
+            assert (s["ring_off"] + b * s["bufb"]) % 128 == 0
+        assert s["ring_off"] + L["nbuf"] * s["bufb"] <= L["bar_off"]
+    # lanes' 16-bit vectors sit at 8-byte offsets, 32-bit ones at 16
+    assert (vec * es) % 8 == 0
