@@ -325,9 +325,9 @@ void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
   const int V = c.V;
   int dt = c.key.dst_dtypes.at(n.dst_index);
   int esz = elem_bytes(dt);
-  bool rowcheck = safe || n.top > 0 || n.bot > 0;
   o << "{\n";
-  if (rowcheck) o << "if (r >= y0 && r < y0 + T && r < H)\n";
+  if (safe) o << "if (r >= y0 && r < y0 + T && r < H)\n";
+  else o << "if (r >= y0 && r < y0 + T)\n";
   if (n.channels == 1 && c.g.channels > 1) o << "if (ch == 0)\n";
   o << "{ const int x = xs + lane * " << V << ";\n";
   o << "if (lane >= " << c.L.lpad / V << " && lane < " << 32 - c.L.rpad / V << ") {\n";
@@ -503,18 +503,17 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
       }
     o << ";\n";
   }
+  // Persistent warps pull tiles from a device queue (a.queue[0]); the last
+  // warp to leave resets the queue for the next launch (a.queue[1] counts
+  // the warps that left), so no per-launch clearing is needed.
+  o << "for (;;) {\n";
+  o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
+       "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
   if (key.persistent) {
-    o << "for (;;) {\n";
-    o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
-         "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
     o << "const int *tt_ = a.tile_table + 4 * tile;\nconst int img = tt_[0];\n";
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
     o << "const int tx = tt_[1], ty = tt_[2], ch = tt_[3];\n";
   } else {
-    // persistent warps: each warp strides over the tiles (grid sized by the
-    // host to the resident capacity of the GPU)
-    o << "for (int tile = blockIdx.x * " << key.nw << " + warp; tile < a.n_tiles; tile += gridDim.x * "
-      << key.nw << ") {\n";
     o << "const WtArgs &ia = a;\n";
     o << "const int tx = tile % a.tiles_x;\nconst int tr_ = tile / a.tiles_x;\n"
          "const int ty = tr_ % a.tiles_y;\nconst int ch = tr_ / a.tiles_y;\n";
@@ -553,10 +552,13 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
       << s << "], xb" << s << ", y_top + c_ * CH, zc" << s << ", b_);\n";
   o << "}\nissued = c_ + 1;\n};\n";
   o << "for (int c_ = 0; c_ < NB - 1; c_++) if (c_ * CH < nrows) issue_chunk(c_);\n";
-  o << "const int kss = " << kss << ";\nconst int kse = T + (" << kse_c << ");\n";
+  (void)kss;
+  (void)kse_c;
+  // Interior tiles run the guard-free body for every step: rows a node
+  // computes outside its range are never stored (row check at the store)
+  // and only read by rows that are themselves outside their range.  Border
+  // tiles run the guarded body (clamp-to-edge replication) throughout.
   o << "const int U = " << c.U << ";\n";
-  o << "int kf0 = border ? 0x3fffffff : ((kss + U - 1) / U) * U;\nint kf1 = kf0;\n";
-  o << "if (!border && kse + 1 - kf0 >= U) kf1 = kf0 + ((kse + 1 - kf0) / U) * U;\n";
   // Steady-state steps of interior tiles run the guard-free body; all
   // other steps run the guarded body (both unrolled over U phases so that
   // register windows rotate by renaming).
@@ -568,18 +570,22 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
        " const int gc_ = cbase + c_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
        " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = c_; goto wt_fail; } } }\n"
        "if (kc_ == ISSUE) { const int c_ = kb / CH + NB - 1; if (c_ * CH < nrows) issue_chunk(c_); } }\n";
-  o << "if (kb >= kf0 && kb < kf1) {\n";
+  o << "if (!border) {\n";
   for (int u = 0; u < c.U; u++) emit_step(c, false, u);
   o << "} else {\n";
   for (int u = 0; u < c.U; u++) emit_step(c, true, u);
   o << "}\n}\n";
   o << "wt_tile_end:;\n";
   o << "cbase += (nrows + CH - 1) / CH;\n";
-  o << "}\n";  // tile scope / persistent loop
+  o << "}\n";  // tile loop
+  o << "wt_exit:\n";
+  o << "if (lane == 0) {\n__threadfence();\nconst int d_ = atomicAdd(a.queue + 1, 1);\n"
+       "if (d_ == (int)(gridDim.x * " << key.nw << ") - 1) { atomicExch(a.queue, 0); atomicExch(a.queue + 1, 0); }\n}\n";
   o << "return;\n";
   o << "wt_fail:\n";
   o << "for (int c_ = failc + 1; c_ < issued; c_++) { const int gc_ = cbase + c_;"
        " wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB), (wt_u32)((gc_ / NB) & 1), a.err); }\n";
+  o << "goto wt_exit;\n";
   o << "}\n";
   return o.str();
 }

@@ -350,8 +350,10 @@ Workspace &workspace(Pipeline &p, int64_t bytes) {
   if (!p.ws || p.ws->device != dev) {
     auto w = std::make_shared<Workspace>();
     w->device = dev;
-    check_rt(cudaMalloc((void **)&w->err, 64), "cudaMalloc(error word)");
-    check_rt(cudaMemset(w->err, 0, 64), "cudaMemset");
+    // control block: error word at [0], then two tile-queue counters per
+    // launch of a plan (zero between launches: the kernels reset them)
+    check_rt(cudaMalloc((void **)&w->err, kCtrlBytes), "cudaMalloc(control block)");
+    check_rt(cudaMemset(w->err, 0, kCtrlBytes), "cudaMemset");
     p.ws = w;
   }
   Workspace &w = *p.ws;
@@ -372,6 +374,10 @@ Workspace &workspace(Pipeline &p, int64_t bytes) {
   return w;
 }
 
+int32_t *queue_counters(int32_t *ctrl, int launch_index) {
+  return ctrl + kCtrlQueueOffset / 4 + 2 * launch_index;
+}
+
 static std::string cache_key(const wt_image *in, int n_in, const wt_image *out, int n_out) {
   std::string k((const char *)in, sizeof(wt_image) * n_in);
   k.append((const char *)out, sizeof(wt_image) * n_out);
@@ -382,6 +388,8 @@ void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string
   Workspace &w = workspace(p, plan.ws_bytes);
   int dev = w.device;
   CachedRun c;
+  if ((int)plan.launches.size() > kMaxLaunches) fail(WT_EUNSUPPORTED, "more than 500 launches per run");
+  int li = 0;
   for (Launch &L : plan.launches) {
     Kernel &k = get_kernel(p, L, dev);
     if (L.fused) {
@@ -403,6 +411,7 @@ void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string
     KernelArgs a;
     fill_args(p, plan, L, w.base, a, L.fused);
     a.err = w.err;
+    a.queue = queue_counters(w.err, li++);
     launch(L, k, a, stream);
     c.functions.push_back(k.function);
     c.args.push_back(a);

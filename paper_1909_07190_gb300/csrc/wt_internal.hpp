@@ -64,6 +64,7 @@ struct Schedule {
   int n_groups = 0;
   int intermediate_dtype = -1;
   bool installed = false;
+  double predicted_cost = 0;  // model cost of the schedule (auto schedules)
 };
 
 // Geometry of one fused group (Sec. 4 OTPW and Sec. 5 hybrid tiling, in the

@@ -43,6 +43,14 @@ struct RunPlan {
   int64_t ws_bytes = 0;
 };
 
+// Device control block of a workspace: the error word at byte 0 and, from
+// kCtrlQueueOffset, two tile-queue counters per launch (next tile, warps
+// finished) that the last warp of each launch resets to zero.
+constexpr int kCtrlBytes = 4096;
+constexpr int kCtrlQueueOffset = 64;
+constexpr int kMaxLaunches = (kCtrlBytes - kCtrlQueueOffset) / 8;
+int32_t *queue_counters(int32_t *ctrl, int launch_index);
+
 struct Staging {
   void *ptr = nullptr;
   int64_t bytes = 0;

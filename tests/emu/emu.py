@@ -58,7 +58,8 @@ class HostImage:
 def _compile(source: str, name: str) -> ctypes.CDLL:
     body = source.split(MARK, 1)[1]
     text = '#include "wt_emu.h"\n' + body + \
-        '\nextern "C" long wt_emu_offset_err() { return (long)offsetof(WtArgs, err); }\n'
+        '\nextern "C" long wt_emu_offset_err() { return (long)offsetof(WtArgs, err); }\n' + \
+        'extern "C" long wt_emu_offset_queue() { return (long)offsetof(WtArgs, queue); }\n'
     h = hashlib.sha1((text + open(os.path.join(HERE, "wt_emu.h")).read() +
                       open(os.path.join(HERE, "emu_rt.cpp")).read()).encode()).hexdigest()[:16]
     if h in _loaded:
@@ -91,8 +92,11 @@ def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None):
     lib = _compile(d["source"], d["name"])
     args = bytearray(d["args"])
     err = np.zeros(16, np.int32)
+    queue = np.zeros(2, np.int32)
     off = lib.wt_emu_offset_err()
     args[off:off + 8] = int(err.ctypes.data).to_bytes(8, "little")
+    qoff = lib.wt_emu_offset_queue()
+    args[qoff:qoff + 8] = int(queue.ctypes.data).to_bytes(8, "little")
     abuf = (ctypes.c_char * len(args)).from_buffer(args)
     kfn = ctypes.cast(getattr(lib, d["name"]), ctypes.c_void_p)
     lib.wt_emu_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -106,4 +110,6 @@ def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None):
         raise RuntimeError("emulated kernel failed: " + msg.value.decode())
     if err[0] != 0:
         raise RuntimeError("emulated kernel raised error word %d" % err[0])
+    if d["fused"] and (queue[0] != 0 or queue[1] != 0):
+        raise RuntimeError("tile queue not reset at kernel exit: %s" % queue)
     return d

@@ -90,6 +90,7 @@ static inline int __all_sync(unsigned, int p) { return wt_emu_all(p); }
 static inline void __syncwarp(unsigned = 0xffffffffu) { wt_emu_syncwarp(); }
 static inline int atomicAdd(int *p, int v) { int o = *p; *p += v; return o; }
 static inline int atomicExch(int *p, int v) { int o = *p; *p = v; return o; }
+static inline void __threadfence() {}
 using std::min;
 using std::max;
 
