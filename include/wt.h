@@ -192,6 +192,25 @@ wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
 wt_status wt_run_batch(wt_pipeline *p, const wt_image *inputs,
                        const wt_image *outputs, int32_t n_images, void *stream);
 
+/* Runs like wt_run, but allocates no device memory.  The paper has no
+ * counterpart: this is for callers that cannot let a library call
+ * cudaMalloc -- processes whose device memory is handed to their own
+ * allocator up front under a fixed budget, and latency-critical paths where
+ * cudaMalloc/cudaFree may synchronize the device.  Intermediates between
+ * groups and the device status word live in one file-scope static device
+ * array of 32 MiB, held by every GPU that loads the library until exit;
+ * runs needing more than 32 MiB - 256 bytes of intermediates are rejected
+ * with WT_EINVAL (single-group schedules need none).  The first call on a
+ * device takes the array's address (cudaGetSymbolAddress).  It never
+ * compiles or loads kernels, because loading code allocates device memory:
+ * run the same schedule and image sizes/dtypes once with wt_run first,
+ * else WT_EUNSUPPORTED.  Every call on a device shares the array and the
+ * array keeps the last call's contents; each call clears the status word
+ * on `stream`.  Calls whose work overlaps on the GPU (other streams, or
+ * before an earlier call's kernels finished) race on the array.          */
+wt_status wt_run_static(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                        const wt_image *outputs, int32_t n_outputs, void *stream);
+
 /* Synchronizes `stream` and reads the device error word of the pipeline:
  * WT_ETIMEOUT if a bounded mbarrier/queue wait gave up, WT_EDEVICE for any
  * other device-side check; clears the word.                                */

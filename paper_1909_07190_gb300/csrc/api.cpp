@@ -103,6 +103,11 @@ int64_t image_bytes(const wt_image &im) {
 }
 }  // namespace
 
+namespace wt {
+// Sets the message wt_last_error() returns on this thread.
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace wt
+
 extern "C" {
 
 const char *wt_last_error(void) { return g_err.c_str(); }

@@ -323,6 +323,13 @@ Kernel &get_kernel(const Pipeline &p, const Launch &L, int device) {
   return ins.first->second.k;
 }
 
+Kernel *find_kernel(const Pipeline &p, const Launch &L, int device) {
+  (void)p;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_cache.find(L.kname + "@" + std::to_string(device));
+  return it == g_cache.end() ? nullptr : &it->second.k;
+}
+
 void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream) {
   const Driver &drv = driver();
   if (L.smem > 48 * 1024)

@@ -73,6 +73,9 @@ std::string launch_source(const Pipeline &p, const Launch &L);
 void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws, KernelArgs &a,
                bool encode_tmaps);
 Kernel &get_kernel(const Pipeline &p, const Launch &L, int device);
+// The loaded kernel of a launch, or null (never compiles or loads).
+Kernel *find_kernel(const Pipeline &p, const Launch &L, int device);
+void set_last_error(const std::string &msg);
 void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream);
 Workspace &workspace(Pipeline &p, int64_t bytes);
 void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string *cache_key = nullptr);

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("wt_run", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_run_host", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_run_batch", _i32, [_vp, _P(wt_image), _P(wt_image), _i32, _vp]),
+    ("wt_run_static", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_check", _i32, [_vp, _vp]),
     ("wt_launches_per_run", _i32, [_vp]),
     ("wt_last_error", ctypes.c_char_p, []),
@@ -240,6 +241,12 @@ class Pipeline:
         ia = (wt_image * len(inputs))(*inputs)
         oa = (wt_image * len(outputs))(*outputs)
         check(load().wt_run_host(self.h, ia, len(inputs), oa, len(outputs), stream))
+
+    def run_static(self, inputs, outputs, stream=None):
+        """wt_run_static: same result as run(), no device allocation."""
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        check(load().wt_run_static(self.h, ia, len(inputs), oa, len(outputs), stream))
 
     def run_batch(self, inputs, outputs, n_images, stream=None):
         ia = (wt_image * len(inputs))(*inputs)
