@@ -165,6 +165,63 @@ wt_status wt_schedule_auto(wt_pipeline *p, int32_t width, int32_t height,
 wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups,
                           int32_t *group_of_stage, wt_group_params *params);
 
+/* --------------------------------------------------- cost model (Sec. 6) -- */
+
+/* GPU quantities the cost function uses (Table 1).                         */
+typedef struct {
+  int32_t nsms, cores_per_sm;
+  double glmem_bw_gbs;
+  int32_t max_smem_per_block, smem_per_sm, max_warps_per_sm, max_blocks_per_sm;
+  int32_t regs_per_sm, max_regs_per_thread, warp_size, max_threads_per_sm;
+} wt_gpu_config;
+
+/* Configuration of CUDA device `device`, or (device < 0) of a GB300 from
+ * its published figures with the measured copy bandwidth of 6781 GB/s.   */
+wt_status wt_gpu_config_get(int32_t device, wt_gpu_config *out);
+
+/* Sec. 4: warp sizes of a thread block, W_x = min(B_x, WarpSize),
+ * W_y = min(B_y, WarpSize / W_x), W_z = min(B_z, WarpSize / (W_x W_y)).    */
+wt_status wt_otpw_warp_sizes(const int32_t block[3], int32_t warp_size, int32_t warp[3]);
+
+/* Sec. 4: points of one stage's scratchpad per thread block,
+ * prod_i ceil(B_i / W_i) * (T_i W_i + O_i).                               */
+wt_status wt_otpw_scratchpad(const int32_t block[3], const int32_t warp[3], const int32_t tile[3],
+                             const int32_t overlap[3], int64_t *points);
+
+/* Alg. 2 theoretical occupancy from shared memory per block, warps per
+ * block and registers per thread (fraction of MaxWarpPerSM).              */
+wt_status wt_cost_occupancy(const wt_gpu_config *cfg, int64_t smem_per_block, int32_t warps_per_block,
+                            int32_t regs_per_thread, double *occupancy, int32_t *blocks_per_sm);
+
+/* Minimum number of txn_bytes-sized, txn_bytes-aligned transactions that
+ * cover n accesses of access_bytes each (Alg. 2 MinGLTxs).               */
+wt_status wt_min_transactions(const int64_t *byte_addresses, int32_t n, int32_t access_bytes,
+                              int32_t txn_bytes, int64_t *txns);
+
+/* Alg. 2 terms of one candidate group: [0] global traffic relative to the
+ * pipeline's minimum bytes, [1] 1 - occupancy, [2] memTime / computeTime,
+ * [3] unallocated shared memory, [4] unused registers, [5] fraction of
+ * overlapped (redundant) computation, [6] idle fraction of the last wave. */
+typedef struct {
+  double terms[7];
+  double cost;       /* weighted sum (wt_cost_weights)                     */
+  int32_t feasible;  /* 0: the candidate exceeds shared memory/registers  */
+  int32_t regs_per_thread;
+  int32_t smem_per_block;
+  double occupancy, waves, work;
+} wt_cost_info;
+
+/* Cost of running stages [first_stage, first_stage + n_stages) as one
+ * fused group with parameters prm and txn_bytes (32 or 128) transactions
+ * on width x height images of dtype; cfg NULL = GB300 defaults.          */
+wt_status wt_cost_group(wt_pipeline *p, int32_t first_stage, int32_t n_stages, const wt_group_params *prm,
+                        int32_t txn_bytes, int32_t width, int32_t height, int32_t dtype,
+                        const wt_gpu_config *cfg, wt_cost_info *out);
+
+/* Gets and/or sets the seven cost weights w1..w7 of Alg. 2 (either pointer
+ * may be NULL).  Defaults: Table 3's Tesla V100 weights.                  */
+wt_status wt_cost_weights(const double *set7, double *get7);
+
 /* ------------------------------------------------------------------ run -- */
 
 /* Runs the pipeline on device images, asynchronously on `stream`

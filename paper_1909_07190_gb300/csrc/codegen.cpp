@@ -481,7 +481,11 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     << "\n#define RING " << L.ring << "\n#define ISSUE " << L.issue_blk << "\n";
   for (int s = 0; s < n_src; s++)
     o << "#define ROWB" << s << " " << L.boxw[s] * L.esz[s] << "\n#define BUFB" << s << " " << L.bufb[s] << "\n";
-  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", 1) " << kname
+  // register cap through the launch bounds (they take precedence over
+  // -maxrregcount): enough resident blocks that each thread gets <= max_regs
+  int min_blocks = 1;
+  if (key.max_regs > 0) min_blocks = std::max(1, 65536 / (key.max_regs * 32 * key.nw));
+  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", " << min_blocks << ") " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
   o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
   o << "const int lane = threadIdx.x & 31;\nconst int warp = threadIdx.x >> 5;\n";

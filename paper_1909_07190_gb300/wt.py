@@ -51,6 +51,20 @@ class wt_group_params(ctypes.Structure):
                 ("chunk_rows", ctypes.c_int32), ("n_buffers", ctypes.c_int32)]
 
 
+class wt_gpu_config(ctypes.Structure):
+    _fields_ = [("nsms", ctypes.c_int32), ("cores_per_sm", ctypes.c_int32), ("glmem_bw_gbs", ctypes.c_double),
+                ("max_smem_per_block", ctypes.c_int32), ("smem_per_sm", ctypes.c_int32),
+                ("max_warps_per_sm", ctypes.c_int32), ("max_blocks_per_sm", ctypes.c_int32),
+                ("regs_per_sm", ctypes.c_int32), ("max_regs_per_thread", ctypes.c_int32),
+                ("warp_size", ctypes.c_int32), ("max_threads_per_sm", ctypes.c_int32)]
+
+
+class wt_cost_info(ctypes.Structure):
+    _fields_ = [("terms", ctypes.c_double * 7), ("cost", ctypes.c_double), ("feasible", ctypes.c_int32),
+                ("regs_per_thread", ctypes.c_int32), ("smem_per_block", ctypes.c_int32),
+                ("occupancy", ctypes.c_double), ("waves", ctypes.c_double), ("work", ctypes.c_double)]
+
+
 class wt_schedule_desc(ctypes.Structure):
     _fields_ = [("exec", ctypes.c_int32), ("n_groups", ctypes.c_int32),
                 ("group_of_stage", ctypes.POINTER(ctypes.c_int32)),
@@ -69,6 +83,14 @@ SIGNATURES = [
     ("wt_schedule", _i32, [_vp, _P(wt_schedule_desc)]),
     ("wt_schedule_auto", _i32, [_vp, _i32, _i32, _i32, _i32]),
     ("wt_schedule_get", _i32, [_vp, _P(_i32), _P(_i32), _P(_i32), _P(wt_group_params)]),
+    ("wt_gpu_config_get", _i32, [_i32, _P(wt_gpu_config)]),
+    ("wt_otpw_warp_sizes", _i32, [_P(_i32), _i32, _P(_i32)]),
+    ("wt_otpw_scratchpad", _i32, [_P(_i32), _P(_i32), _P(_i32), _P(_i32), _P(_i64)]),
+    ("wt_cost_occupancy", _i32, [_P(wt_gpu_config), _i64, _i32, _i32, _P(ctypes.c_double), _P(_i32)]),
+    ("wt_min_transactions", _i32, [_P(_i64), _i32, _i32, _i32, _P(_i64)]),
+    ("wt_cost_group", _i32, [_vp, _i32, _i32, _P(wt_group_params), _i32, _i32, _i32, _i32,
+                             _P(wt_gpu_config), _P(wt_cost_info)]),
+    ("wt_cost_weights", _i32, [_P(ctypes.c_double), _P(ctypes.c_double)]),
     ("wt_run", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_run_host", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_run_batch", _i32, [_vp, _P(wt_image), _P(wt_image), _i32, _vp]),
@@ -227,6 +249,19 @@ class Pipeline:
         params = [{f: getattr(prm[i], f) for f, _ in wt_group_params._fields_} for i in range(ng.value)]
         return {"exec": ex.value, "groups": list(g), "params": params}
 
+    def cost_group(self, first, n, params, txn, width, height, dtype=WT_F32, cfg=None):
+        prm = wt_group_params()
+        d = dict(tile_h=32, warps_per_block=4, frac_reg=1.0, vec=4, max_regs=0, chunk_rows=0, n_buffers=0)
+        d.update(params)
+        for k, v in d.items():
+            setattr(prm, k, v)
+        info = wt_cost_info()
+        check(load().wt_cost_group(self.h, first, n, ctypes.byref(prm), txn, width, height, dtype,
+                                   ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(info)))
+        return {"terms": list(info.terms), "cost": info.cost, "feasible": bool(info.feasible),
+                "regs": info.regs_per_thread, "smem_per_block": info.smem_per_block,
+                "occupancy": info.occupancy, "waves": info.waves, "work": info.work}
+
     def launches_per_run(self) -> int:
         return int(load().wt_launches_per_run(self.h))
 
@@ -351,3 +386,48 @@ class DeviceImage:
     def download(self):
         """float32 numpy copy of the image."""
         return self.view().float().cpu().numpy()
+
+
+# ------------------------------------------------------------- cost model
+
+def gpu_config(device=-1) -> wt_gpu_config:
+    c = wt_gpu_config()
+    check(load().wt_gpu_config_get(device, ctypes.byref(c)))
+    return c
+
+
+def otpw_warp_sizes(block, warp_size=32):
+    b = (_i32 * 3)(*block)
+    w = (_i32 * 3)()
+    check(load().wt_otpw_warp_sizes(b, warp_size, w))
+    return list(w)
+
+
+def otpw_scratchpad(block, warp, tile, overlap) -> int:
+    n = _i64()
+    arr = [(_i32 * 3)(*v) for v in (block, warp, tile, overlap)]
+    check(load().wt_otpw_scratchpad(*arr, ctypes.byref(n)))
+    return n.value
+
+
+def cost_occupancy(cfg, smem_per_block, warps_per_block, regs_per_thread):
+    occ = ctypes.c_double()
+    tb = _i32()
+    check(load().wt_cost_occupancy(ctypes.byref(cfg), smem_per_block, warps_per_block, regs_per_thread,
+                                   ctypes.byref(occ), ctypes.byref(tb)))
+    return occ.value, tb.value
+
+
+def min_transactions(addresses, access_bytes, txn_bytes) -> int:
+    a = (_i64 * max(1, len(addresses)))(*addresses)
+    n = _i64()
+    check(load().wt_min_transactions(a, len(addresses), access_bytes, txn_bytes, ctypes.byref(n)))
+    return n.value
+
+
+def cost_weights(new=None):
+    lib = load()
+    out = (ctypes.c_double * 7)()
+    inp = (ctypes.c_double * 7)(*new) if new is not None else None
+    check(lib.wt_cost_weights(inp, out))
+    return list(out)

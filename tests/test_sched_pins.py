@@ -1,0 +1,126 @@
+"""The scheduler's formulas against the numbers the paper prints
+(tests/golden/paper_examples.json, each with its citation), plus
+properties of the cost function and of DP-Fusion."""
+import json
+import os
+
+import pytest
+
+from paper_1909_07190_gb300 import pipelines as P
+from paper_1909_07190_gb300 import wt
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_examples.json")))
+
+
+def cfg_from(d):
+    c = wt.wt_gpu_config()
+    c.nsms, c.cores_per_sm, c.glmem_bw_gbs = d["NSMs"], d["CoresPerSM"], d["GlMemBW_GBps"]
+    c.max_smem_per_block, c.smem_per_sm = d["MaxShMemPerTb"], d["ShMemPerSM"]
+    c.max_warps_per_sm, c.max_blocks_per_sm = d["MaxWarpPerSM"], d["MaxTbPerSM"]
+    c.regs_per_sm, c.max_regs_per_thread, c.warp_size = d["RegPerSM"], d["MaxRegPerTh"], d["WarpSize"]
+    c.max_threads_per_sm = d["MaxWarpPerSM"] * d["WarpSize"]
+    return c
+
+
+def test_warp_sizes_worked_example():
+    g = GOLD["warp_tile_example"]
+    w = wt.otpw_warp_sizes(g["block"])
+    assert w == g["warp_sizes"]
+    assert w[0] * w[1] * w[2] == 32
+    assert [t * s for t, s in zip(g["tile"], w)] == g["warp_tile"]
+
+
+@pytest.mark.parametrize("block", [[64, 4, 1], [32, 8, 2], [8, 16, 4], [256, 1, 1], [4, 4, 8]])
+def test_warp_sizes_cover_one_warp(block):
+    w = wt.otpw_warp_sizes(block)
+    assert w[0] * w[1] * w[2] == 32 and all(1 <= wi <= bi for wi, bi in zip(w, block))
+
+
+def test_blur_overlap_fraction():
+    g = GOLD["blur_otpw"]
+    # overlap per warp = O_x / (T_x * W_x) with W_x = 32 (blocks 64x4x1)
+    w = wt.otpw_warp_sizes(g["block"])
+    for tile, pct in ((8, g["tile8_overlap_pct"]), (16, g["tile16_overlap_pct"])):
+        frac = g["overlap_points_x"] / (tile * w[0])
+        assert round(100 * frac, 1) == pct
+
+
+def test_blur_scratchpad_and_occupancy_1080ti():
+    g, h = GOLD["blur_otpw"], GOLD["blur_hybrid"]
+    cfg = cfg_from(GOLD["gtx1080ti"])
+    w = wt.otpw_warp_sizes(g["block"])
+    full = wt.otpw_scratchpad(g["block"], w, [16, 1, 1], [g["overlap_points_x"], 0, 0]) * 4
+    assert full > g["tile16_smem_over_bytes"]            # "over 16KB"
+    occ, _ = wt.cost_occupancy(cfg, full, 8, h["registers"])
+    assert round(100 * occ, 1) == g["tile16_occupancy_pct"]
+    # half the tile in registers: the shared part is the first 8 of 16 tiles
+    half = wt.otpw_scratchpad(g["block"], w, [8, 1, 1], [g["overlap_points_x"], 0, 0]) * 4
+    occ, _ = wt.cost_occupancy(cfg, half, 8, h["registers"])
+    assert round(100 * occ, 1) == h["occupancy_pct"]
+    # tile 8 fits without hybrid tiling at full occupancy as well (Sec. 3)
+    occ8, _ = wt.cost_occupancy(cfg, wt.otpw_scratchpad(g["block"], w, [8, 1, 1], [2, 0, 0]) * 4, 8, 24)
+    assert occ8 == 1.0
+
+
+def test_occupancy_register_limit():
+    cfg = cfg_from(GOLD["gtx1080ti"])
+    occ, tb = wt.cost_occupancy(cfg, 0, 4, 128)     # 65536/128 = 512 threads = 16 warps
+    assert occ == 16 / 64 and tb == 4
+
+
+@pytest.mark.parametrize("addrs,acc,txn,want", [
+    ([4 * i for i in range(32)], 4, 128, 1),          # 32 floats, aligned: one 128 B line
+    ([4 * i for i in range(32)], 4, 32, 4),           # ... or four sectors
+    ([4 * i + 4 for i in range(32)], 4, 128, 2),      # shifted by one float: two lines
+    ([8 * i for i in range(32)], 4, 32, 8),           # stride 2: 256 B span
+    ([128 * i for i in range(32)], 4, 32, 32),        # one transaction per lane
+    ([16 * i for i in range(32)], 16, 128, 4),        # 128-bit accesses: 512 B
+])
+def test_min_transactions(addrs, acc, txn, want):
+    assert wt.min_transactions(addrs, acc, txn) == want
+
+
+def test_weights_default_to_table3_v100_and_roundtrip():
+    w0 = wt.cost_weights()
+    assert w0 == GOLD["weights"]["v100"]
+    wt.cost_weights([1, 2, 3, 4, 5, 6, 7])
+    assert wt.cost_weights() == [1, 2, 3, 4, 5, 6, 7]
+    wt.cost_weights(w0)
+
+
+def test_cost_terms_are_sane_for_harris():
+    p = wt.Pipeline(P.harris())
+    c = p.cost_group(0, 11, dict(tile_h=32, warps_per_block=4, frac_reg=1.0), 128, 4096, 4096)
+    assert c["feasible"]
+    t = c["terms"]
+    assert 0.99 < t[0] < 1.5                # traffic close to the pipeline minimum
+    assert 0 <= t[1] < 1 and 0 <= t[3] <= 1 and 0 <= t[6] < 1
+    assert 0 < t[5] < 0.5                   # halo recompute at tile height 32
+    # a shorter tile recomputes more
+    c8 = p.cost_group(0, 11, dict(tile_h=8, warps_per_block=4, frac_reg=1.0), 128, 4096, 4096)
+    assert c8["terms"][5] > t[5]
+    # one stage per group reads and writes far more than the fused group
+    cs = p.cost_group(0, 1, dict(tile_h=32, warps_per_block=4), 128, 4096, 4096)
+    assert cs["terms"][0] < t[0]            # (a single stage moves less than all 11)
+
+
+def test_cost_rejects_oversized_shared_memory():
+    p = wt.Pipeline(P.harris())
+    c = p.cost_group(0, 11, dict(tile_h=32, warps_per_block=16, frac_reg=0.0, vec=8), 128, 4096, 4096)
+    assert not c["feasible"]
+
+
+def test_auto_schedule_fuses_corner_response():
+    p = wt.Pipeline(P.harris())
+    p.schedule_auto(4096, 4096, wt.WT_F32, wt.WT_MODEL_ANALYTIC)
+    s = p.schedule_get()
+    assert s["exec"] == wt.WT_EXEC_FUSED
+    assert len(set(s["groups"])) <= 3       # the DP keeps most stages together
+
+
+def test_auto_schedule_blend_groups_by_level():
+    p = wt.Pipeline(P.blend())
+    p.schedule_auto(512, 512, wt.WT_BF16, wt.WT_MODEL_ANALYTIC)
+    s = p.schedule_get()
+    groups = s["groups"]
+    assert groups == sorted(groups) and groups[0] == 0
