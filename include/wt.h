@@ -122,8 +122,12 @@ typedef struct {
   int32_t vec;             /* pixels per lane along x: 4 or 8 (0 = auto)     */
   int32_t max_regs;        /* register cap per thread (0 = 255)             */
   int32_t chunk_rows;      /* TMA staging rows per chunk (0 = 8)             */
-  int32_t n_buffers;       /* TMA staging buffers per input (0 = 3)          */
+  int32_t n_buffers;       /* TMA staging buffers per input (0 = 2)          */
+  int32_t flags;           /* WT_FLAG_* bits; 0 = all features on            */
 } wt_group_params;
+
+#define WT_FLAG_NO_PAIRS 1      /* scalar FP32 instead of packed f32x2 pairs     */
+#define WT_FLAG_NO_TILE_SPLIT 2 /* one tile height (no short last round)         */
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */

@@ -85,7 +85,10 @@ void install(wt::Pipeline &p, const wt_schedule_desc *d) {
         r.vec = q.vec;
         r.max_regs = q.max_regs;
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
-        r.n_buffers = q.n_buffers ? q.n_buffers : 3;
+        r.n_buffers = q.n_buffers ? q.n_buffers : 2;
+        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT)) fail(WT_EINVAL, "unknown flags");
+        r.pairs = (q.flags & WT_FLAG_NO_PAIRS) ? 0 : 1;
+        r.tile_split = (q.flags & WT_FLAG_NO_TILE_SPLIT) ? 0 : 1;
       }
   } else {
     s.n_groups = n;
@@ -171,6 +174,7 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].max_regs = r.max_regs;
         params[g].chunk_rows = r.chunk_rows;
         params[g].n_buffers = r.n_buffers;
+        params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT);
       }
   });
 }
@@ -305,6 +309,8 @@ wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *
       if (args_cap < (int64_t)sizeof(wt::KernelArgs)) wt::fail(WT_EINVAL, "args buffer too small");
       wt::KernelArgs a;
       wt::fill_args(*p, plan, L, nullptr, a, false);
+      // as on the GPU with few resident warps: exercises both tile heights
+      if (L.fused) wt::split_tiles(L, a, 4 * L.key.nw);
       memcpy(args, &a, sizeof a);
     }
     if (launch) {

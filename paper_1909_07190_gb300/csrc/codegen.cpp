@@ -36,7 +36,7 @@ namespace wt {
 
 std::string CodegenKey::str() const {
   std::ostringstream s;
-  s << (plain ? "P" : "F") << (persistent ? "b" : "") << "|v" << vec << "|f" << frac_reg
+  s << (plain ? "P" : "F") << (persistent ? "b" : "") << (pairs ? "x2" : "") << "|v" << vec << "|f" << frac_reg
     << "|r" << max_regs << "|w" << nw << "|c" << chunk << "|n" << nbuf << "|s";
   for (int x : stages) s << x << ",";
   s << "|i";
@@ -306,6 +306,126 @@ std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
   return st.back();
 }
 
+// --------------------------------------------------- packed pair code
+// Expression tree of a node program for one element; leaves resolved to
+// register names (taps), constants, or the row parity.
+struct XN {
+  int op = 0;
+  std::string leaf;
+  float c = 0;
+  int a = -1, b = -1;
+};
+
+std::vector<XN> build_tree(Ctx &c, int ni, int e, int u) {
+  const Node &cn = c.g.nodes[ni];
+  std::vector<XN> t;
+  std::vector<int> st;
+  for (const KOp &op : cn.prog) {
+    XN x;
+    x.op = op.op;
+    switch (op.op) {
+      case WT_OP_CONST: x.c = op.value; break;
+      case WT_OP_XPAR: x.op = WT_OP_CONST; x.c = (float)(e & 1); break;
+      case WT_OP_YPAR: x.leaf = "((float)(r & 1))"; break;
+      case WT_OP_TAP: {
+        const Node &pn = c.g.nodes[op.node];
+        int a = cn.delay - pn.delay - op.dy;
+        int j = pn.xl + e + op.dx;
+        if (j < 0 || j >= width_of(pn, c.V)) fail(WT_EINVAL, "internal: tap column out of range");
+        x.leaf = pn.in_smem ? tmp(op.node, a, j) : reg(op.node, slot_of(pn, u, a), j);
+      } break;
+      case WT_OP_NEG: case WT_OP_ABS: case WT_OP_SQRT:
+        x.a = st.back();
+        st.pop_back();
+        break;
+      default:
+        x.b = st.back();
+        st.pop_back();
+        x.a = st.back();
+        st.pop_back();
+    }
+    t.push_back(x);
+    st.push_back((int)t.size() - 1);
+  }
+  return t;
+}
+
+struct PairEmit {
+  std::ostringstream &o;
+  const std::vector<XN> &A, &B;
+  int &tmpid;
+  std::string fresh() { return "p" + std::to_string(tmpid++); }
+  std::string leaf(const XN &x) { return x.op == WT_OP_CONST ? flt(x.c) : x.leaf; }
+  bool is_const(int i) { return A[i].op == WT_OP_CONST && B[i].op == WT_OP_CONST; }
+  std::string def(const std::string &rhs) {
+    std::string n = fresh();
+    o << "const wt_u64 " << n << " = " << rhs << ";\n";
+    return n;
+  }
+  std::string emit(int i) {
+    const XN &x = A[i], &y = B[i];
+    switch (x.op) {
+      case WT_OP_CONST: case WT_OP_TAP: case WT_OP_YPAR:
+        return def("wt_pk(" + leaf(x) + ", " + leaf(y) + ")");
+      case WT_OP_ADD: {
+        if (A[x.b].op == WT_OP_MUL) {
+          std::string m0 = emit(A[x.b].a), m1 = emit(A[x.b].b), s0 = emit(x.a);
+          return def("wt_fma2(" + m0 + ", " + m1 + ", " + s0 + ")");
+        }
+        if (A[x.a].op == WT_OP_MUL) {
+          std::string m0 = emit(A[x.a].a), m1 = emit(A[x.a].b), s0 = emit(x.b);
+          return def("wt_fma2(" + m0 + ", " + m1 + ", " + s0 + ")");
+        }
+        std::string l = emit(x.a), r = emit(x.b);
+        return def("wt_add2(" + l + ", " + r + ")");
+      }
+      case WT_OP_SUB: {
+        const XN &m = A[x.b];
+        if (m.op == WT_OP_MUL && (is_const(m.a) || is_const(m.b))) {
+          int ci = is_const(m.a) ? m.a : m.b, vi = is_const(m.a) ? m.b : m.a;
+          std::string v = emit(vi), s0 = emit(x.a);
+          std::string k = def("wt_pk(" + flt(-A[ci].c) + ", " + flt(-B[ci].c) + ")");
+          return def("wt_fma2(" + v + ", " + k + ", " + s0 + ")");
+        }
+        std::string l = emit(x.a), r = emit(x.b);
+        return def("wt_sub2(" + l + ", " + r + ")");
+      }
+      case WT_OP_MUL: {
+        std::string l = emit(x.a), r = emit(x.b);
+        return def("wt_mul2(" + l + ", " + r + ")");
+      }
+      default: {  // no packed form: unpack, scalar op, repack
+        std::string l = emit(x.a);
+        std::string r = x.b >= 0 ? emit(x.b) : "";
+        std::string n = fresh();
+        o << "float " << n << "a, " << n << "b, " << n << "c, " << n << "d;\n";
+        o << "wt_upk(" << l << ", " << n << "a, " << n << "b);\n";
+        if (x.b >= 0) o << "wt_upk(" << r << ", " << n << "c, " << n << "d);\n";
+        auto f = [&](const std::string &p, const std::string &q) -> std::string {
+          switch (x.op) {
+            case WT_OP_DIV: return "(" + p + " / " + q + ")";
+            case WT_OP_MIN: return "fminf(" + p + ", " + q + ")";
+            case WT_OP_MAX: return "fmaxf(" + p + ", " + q + ")";
+            case WT_OP_NEG: return "(-" + p + ")";
+            case WT_OP_ABS: return "fabsf(" + p + ")";
+            case WT_OP_SQRT: return "sqrtf(" + p + ")";
+          }
+          fail(WT_EINVAL, "internal: opcode");
+        };
+        return def("wt_pk(" + f(n + "a", n + "c") + ", " + f(n + "b", n + "d") + ")");
+      }
+    }
+  }
+};
+
+// Elements e and e+1 of node `ni` with packed f32x2 arithmetic.
+void emit_pair(Ctx &c, int ni, int e, int u, const std::vector<std::string> &v, int &tmpid) {
+  std::vector<XN> A = build_tree(c, ni, e, u), B = build_tree(c, ni, e + 1, u);
+  PairEmit pe{c.o, A, B, tmpid};
+  std::string r = pe.emit((int)A.size() - 1);
+  c.o << "wt_upk(" << r << ", " << v[e] << ", " << v[e + 1] << ");\n";
+}
+
 // (producer node, age) pairs a node reads from shared-memory windows.
 std::vector<std::pair<int, int>> smem_reads(Ctx &c, int ni_c) {
   std::vector<std::pair<int, int>> r;
@@ -384,7 +504,14 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     }
     o << "} else {\n";
   }
-  for (int e = 0; e < V; e++) o << v[e] << " = " << emit_expr(c, ni, e, u) << ";\n";
+  if (c.key.pairs) {
+    int tmpid = 0;
+    o << "{\n";
+    for (int e = 0; e < V; e += 2) emit_pair(c, ni, e, u, v, tmpid);
+    o << "}\n";
+  } else {
+    for (int e = 0; e < V; e++) o << v[e] << " = " << emit_expr(c, ni, e, u) << ";\n";
+  }
   if (safe) {
     o << "}\n";
     emit_xfix(c, v);
@@ -518,13 +645,19 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
     o << "const int tx = tt_[1], ty = tt_[2], ch = tt_[3];\n";
   } else {
+    // tall tiles first (tile rows [0, ty1) of tile_h rows), then short
+    // tiles of tile_h2 rows, so the last tiles handed out are short
     o << "const WtArgs &ia = a;\n";
-    o << "const int tx = tile % a.tiles_x;\nconst int tr_ = tile / a.tiles_x;\n"
-         "const int ty = tr_ % a.tiles_y;\nconst int ch = tr_ / a.tiles_y;\n";
+    o << "int tx, ch, y0, T;\n";
+    o << "if (tile < a.n_big) { tx = tile % a.tiles_x; const int tr_ = tile / a.tiles_x;"
+         " y0 = (tr_ % a.ty1) * a.tile_h; ch = tr_ / a.ty1; T = a.tile_h; }\n"
+         "else { const int j_ = tile - a.n_big; tx = j_ % a.tiles_x; const int tr_ = j_ / a.tiles_x;"
+         " y0 = a.ty1 * a.tile_h + (tr_ % a.ty2) * a.tile_h2; ch = tr_ / a.ty2; T = a.tile_h2; }\n";
   }
-  o << "const int W = ia.W, H = ia.H, T = ia.tile_h;\n";
+  if (key.persistent) o << "const int T = ia.tile_h, y0 = ty * T;\n";
+  o << "const int W = ia.W, H = ia.H;\n";
   o << "const int xs = tx * " << L.out_w << " - " << L.lpad << ";\n";
-  o << "const int y0 = ty * T;\nconst int y_top = y0 - " << HT << ";\n";
+  o << "const int y_top = y0 - " << HT << ";\n";
   o << "const int nsteps = " << HT << " + T + " << L.nsx << ";\n";
   o << "const int nsrc = " << HT << " + T + " << HB << ";\n";
   o << "const int nrows = min(nsrc, H - y_top);\n";

@@ -30,6 +30,7 @@ struct __align__(64) WtArgs {
   int n_images;
   int pad0;
   const void *img_tab;
+  int tile_h2, ty1, ty2, n_big;
 };
 
 #define WT_FULL 0xffffffffu
@@ -148,6 +149,36 @@ static __device__ __forceinline__ void wt_st1_bf16(void *p, float v) { *(wt_u16 
 
 static __device__ __forceinline__ int wt_clampi(int v, int lo, int hi) {
   return v < lo ? lo : (v > hi ? hi : v);
+}
+// ---------------------------------------- packed FP32 pairs (sm_100+)
+// Two FP32 lanes per instruction; each lane rounds like the scalar op.
+static __device__ __forceinline__ wt_u64 wt_pk(float a, float b) {
+  wt_u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+static __device__ __forceinline__ void wt_upk(wt_u64 v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+static __device__ __forceinline__ wt_u64 wt_add2(wt_u64 a, wt_u64 b) {
+  wt_u64 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+static __device__ __forceinline__ wt_u64 wt_sub2(wt_u64 a, wt_u64 b) {
+  wt_u64 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+static __device__ __forceinline__ wt_u64 wt_mul2(wt_u64 a, wt_u64 b) {
+  wt_u64 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+static __device__ __forceinline__ wt_u64 wt_fma2(wt_u64 a, wt_u64 b, wt_u64 c) {
+  wt_u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
 }
 // WT-DEVICE-HELPERS-END
 )WTDEV";

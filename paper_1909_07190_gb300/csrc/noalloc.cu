@@ -76,6 +76,7 @@ static void run_plan_at(Pipeline &p, RunPlan &plan, char *base, int32_t *err, cu
     }
     KernelArgs a;
     fill_args(p, plan, L, base, a, L.fused);
+    if (L.fused) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
     a.err = err;
     a.queue = queue_counters(err, li++);
     launch(L, *k, a, stream);

@@ -157,7 +157,8 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     key.max_regs = L.params.max_regs;
     key.nw = std::max(1, std::min(16, L.params.warps_per_block));
     key.chunk = L.params.chunk_rows > 0 ? L.params.chunk_rows : 8;
-    key.nbuf = L.params.n_buffers > 0 ? L.params.n_buffers : 3;
+    key.nbuf = L.params.n_buffers > 0 ? L.params.n_buffers : 2;
+    key.pairs = L.params.pairs != 0;
     L.src.clear();
     L.dst.clear();
     auto loc_of = [&](int pid) -> const Loc & { return pid >= 0 ? plan.loc[pid] : plan.in_loc[-pid - 1]; };
@@ -282,6 +283,11 @@ void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws
   a.tiles_x = L.tiles_x;
   a.tiles_y = L.tiles_y;
   a.n_tiles = L.n_tiles;
+  // one tile height unless split_tiles() assigns a short last round
+  a.tile_h2 = a.tile_h;
+  a.ty1 = L.tiles_y;
+  a.ty2 = 1;
+  a.n_big = L.n_tiles;
   a.chunk = L.layout.chunk;
   a.nbuf = L.layout.nbuf;
   a.out_w = L.layout.out_w;
@@ -381,6 +387,26 @@ Workspace &workspace(Pipeline &p, int64_t bytes) {
   return w;
 }
 
+// Two-level tile heights (load balance of the persistent warps): the last
+// round of tiles handed out is short, about one tile per resident warp, so
+// warps finish within one short tile of each other.
+void split_tiles(const Launch &L, KernelArgs &a, int resident_warps) {
+  const int T1 = std::max(1, L.params.tile_h);
+  const int T2 = std::max(4, T1 / 2);
+  if (!L.fused || T2 >= T1 || L.params.tile_split == 0) return;
+  const int C = L.geom.channels;
+  const int per_row = std::max(1, L.tiles_x * C);
+  int ty2 = (resident_warps + per_row - 1) / per_row;
+  int ty1 = std::max(0, (L.H - ty2 * T2) / T1);
+  if (ty1 < 1) return;  // too small to split
+  ty2 = (L.H - ty1 * T1 + T2 - 1) / T2;
+  a.tile_h2 = T2;
+  a.ty1 = ty1;
+  a.ty2 = std::max(1, ty2);
+  a.n_big = L.tiles_x * ty1 * C;
+  a.n_tiles = a.n_big + L.tiles_x * a.ty2 * C;
+}
+
 int32_t *queue_counters(int32_t *ctrl, int launch_index) {
   return ctrl + kCtrlQueueOffset / 4 + 2 * launch_index;
 }
@@ -417,6 +443,7 @@ void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string
     }
     KernelArgs a;
     fill_args(p, plan, L, w.base, a, L.fused);
+    if (L.fused) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
     a.err = w.err;
     a.queue = queue_counters(w.err, li++);
     launch(L, k, a, stream);

@@ -132,7 +132,7 @@ wt_status wt_cost_group(wt_pipeline *p, int32_t first_stage, int32_t n_stages, c
     q.frac_reg = prm->frac_reg;
     q.vec = prm->vec ? prm->vec : 4;
     q.chunk_rows = prm->chunk_rows ? prm->chunk_rows : 8;
-    q.n_buffers = prm->n_buffers ? prm->n_buffers : 3;
+    q.n_buffers = prm->n_buffers ? prm->n_buffers : 2;
     if (q.tile_h < 1 || q.warps_per_block < 1 || q.warps_per_block > 16) wt::fail(WT_EINVAL, "bad params");
     auto st = wt::stage_stats(*p, false);
     wt::CostInfo ci = wt::cost_group(*p, seg, q, txn_bytes, width, height, dtype, g, st, wt::current_weights(),

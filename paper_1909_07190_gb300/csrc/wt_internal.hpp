@@ -48,13 +48,15 @@ struct Stage {
 };
 
 struct GroupParams {
-  int tile_h = 32;
-  int warps_per_block = 4;
+  int tile_h = 16;
+  int warps_per_block = 2;
   float frac_reg = 1.f;
   int vec = 0;
   int max_regs = 0;
   int chunk_rows = 8;
-  int n_buffers = 3;
+  int n_buffers = 2;
+  int tile_split = 1;  // short tiles for the last round of the tile queue
+  int pairs = 1;       // packed f32x2 arithmetic where taps align
 };
 
 struct Schedule {
@@ -171,6 +173,9 @@ struct alignas(64) KernelArgs {
   int32_t n_images;
   int32_t pad0;
   const void *img_tab;        // per-image SrcDesc/DstDesc/tmaps
+  // two tile heights: tiles [0, n_big) have tile_h rows and cover tile
+  // rows [0, ty1); the rest have tile_h2 rows (short tiles end the run)
+  int32_t tile_h2, ty1, ty2, n_big;
 };
 
 
@@ -224,9 +229,10 @@ struct CodegenKey {
   int max_regs = 0;
   int nw = 4;        // warps per block (launch bound)
   int chunk = 8;     // TMA rows per chunk
-  int nbuf = 3;      // TMA buffers per source
+  int nbuf = 2;      // TMA buffers per source
   bool plain = false;
   bool persistent = false;
+  bool pairs = true;  // packed f32x2 arithmetic
   std::string str() const;
 };
 

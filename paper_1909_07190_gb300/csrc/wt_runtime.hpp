@@ -50,6 +50,7 @@ constexpr int kCtrlBytes = 4096;
 constexpr int kCtrlQueueOffset = 64;
 constexpr int kMaxLaunches = (kCtrlBytes - kCtrlQueueOffset) / 8;
 int32_t *queue_counters(int32_t *ctrl, int launch_index);
+void split_tiles(const Launch &L, KernelArgs &a, int resident_warps);
 
 struct Staging {
   void *ptr = nullptr;

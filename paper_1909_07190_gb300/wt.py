@@ -19,6 +19,7 @@ WT_OK, WT_EINVAL, WT_ENOMEM, WT_ECUDA, WT_EUNSUPPORTED, WT_ETIMEOUT, WT_EDEVICE,
 WT_F32, WT_F16, WT_BF16 = 0, 1, 2
 WT_EXEC_FUSED, WT_EXEC_PLAIN = 0, 1
 WT_MODEL_ANALYTIC, WT_MODEL_LEARNED = 0, 1
+WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT = 1, 2
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
            "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13}
 TAPMODES = {"same": 0, "down2": 1, "up2": 2}
@@ -48,7 +49,7 @@ class wt_image(ctypes.Structure):
 class wt_group_params(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("frac_reg", ctypes.c_float), ("vec", ctypes.c_int32), ("max_regs", ctypes.c_int32),
-                ("chunk_rows", ctypes.c_int32), ("n_buffers", ctypes.c_int32)]
+                ("chunk_rows", ctypes.c_int32), ("n_buffers", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class wt_gpu_config(ctypes.Structure):
@@ -227,8 +228,8 @@ class Pipeline:
         g = (_i32 * n)(*groups)
         prm = (wt_group_params * ng)()
         for i in range(ng):
-            d = dict(tile_h=32, warps_per_block=4, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
-                     n_buffers=0)
+            d = dict(tile_h=16, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
+                     n_buffers=0, flags=0)
             if params is not None:
                 d.update(params[i] if isinstance(params, (list, tuple)) else params)
             for k, v in d.items():
@@ -251,7 +252,7 @@ class Pipeline:
 
     def cost_group(self, first, n, params, txn, width, height, dtype=WT_F32, cfg=None):
         prm = wt_group_params()
-        d = dict(tile_h=32, warps_per_block=4, frac_reg=1.0, vec=4, max_regs=0, chunk_rows=0, n_buffers=0)
+        d = dict(tile_h=16, warps_per_block=2, frac_reg=1.0, vec=4, max_regs=0, chunk_rows=0, n_buffers=0)
         d.update(params)
         for k, v in d.items():
             setattr(prm, k, v)

@@ -45,6 +45,7 @@ struct alignas(64) WtArgs {
   int n_images;
   int pad0;
   const void *img_tab;
+  int tile_h2, ty1, ty2, n_big;
 };
 struct EmuTmap {  // the library's debug encoding of a tensor-map slot
   const void *ptr;
@@ -213,3 +214,28 @@ static inline void wt_st1_f32(void *p, float v) { memcpy(p, &v, 4); }
 static inline void wt_st1_f16(void *p, float v) { wt_u16 h = wt_f2h(v); memcpy(p, &h, 2); }
 static inline void wt_st1_bf16(void *p, float v) { wt_u16 h = wt_f2b(v); memcpy(p, &h, 2); }
 static inline int wt_clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ------------------------------------------------- packed FP32 pairs
+static inline wt_u64 wt_pk(float a, float b) {
+  wt_u64 r;
+  unsigned ua = __float_as_uint(a), ub = __float_as_uint(b);
+  r = (wt_u64)ua | ((wt_u64)ub << 32);
+  return r;
+}
+static inline void wt_upk(wt_u64 v, float &a, float &b) {
+  a = __uint_as_float((unsigned)(v & 0xffffffffu));
+  b = __uint_as_float((unsigned)(v >> 32));
+}
+static inline wt_u64 wt_add2(wt_u64 x, wt_u64 y) {
+  float a, b, c, d; wt_upk(x, a, b); wt_upk(y, c, d); return wt_pk(a + c, b + d);
+}
+static inline wt_u64 wt_sub2(wt_u64 x, wt_u64 y) {
+  float a, b, c, d; wt_upk(x, a, b); wt_upk(y, c, d); return wt_pk(a - c, b - d);
+}
+static inline wt_u64 wt_mul2(wt_u64 x, wt_u64 y) {
+  float a, b, c, d; wt_upk(x, a, b); wt_upk(y, c, d); return wt_pk(a * c, b * d);
+}
+static inline wt_u64 wt_fma2(wt_u64 x, wt_u64 y, wt_u64 z) {
+  float a, b, c, d, e, f; wt_upk(x, a, b); wt_upk(y, c, d); wt_upk(z, e, f);
+  return wt_pk(std::fma(a, c, e), std::fma(b, d, f));
+}
