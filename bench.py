@@ -4,10 +4,17 @@ Workload (default): the 11-stage corner-response pipeline on a 4096x4096
 single-channel FP32 image (uniform [0,1) from seed 190907192).  One step =
 one wt_run of the whole pipeline over one image.  Inputs are resident in HBM;
 consecutive steps rotate over buffer sets whose total size exceeds 3x L2, so
-every step reads and writes HBM.  Prints one JSON line (rank 0).
+every step reads and writes HBM.  The schedule is the library's default
+(one fused group) unless --tune on runs its measured schedule search
+(wt_schedule_tune) first; batches are always tuned.  Prints one JSON line
+(rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload harris|harris_f16|sharpen]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Workloads: harris (default), harris_f16, sharpen, and harris_batch -- 512
+images with sides uniform in [200, 4096], FP16 storage, one wt_run_batch
+(one persistent launch) per step.
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 method shards by image with no exchange): value = pixels of all ranks / max
@@ -37,7 +44,10 @@ WORKLOADS = {
     "harris": ("harris", 4096, 4096, "f32", I.SEED_BASE + 2),
     "harris_f16": ("harris", 4096, 4096, "f16", I.SEED_BASE + 2),
     "sharpen": ("sharpen", 2048, 2048, "f32", I.SEED_BASE + 1),
+    # 512 images, sides uniform in [200, 4096] (sizes from seed 190907193)
+    "harris_batch": ("harris", 0, 0, "f16", I.SEED_BASE + 3),
 }
+BATCH_IMAGES = 512
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -126,21 +136,37 @@ def cpu_oracle_rate(spec, img, budget_s):
     return px / dt / 1e6, O.num_threads(), n, dt
 
 
+def batch_sizes():
+    return I.batch_sizes(I.SEED_BASE + 3, BATCH_IMAGES, 200, 4096)
+
+
 def run_reference(args, rank):
+    """The FP64 oracle on the host cores, one bounded sample per step: the
+    whole image (single-image workloads) or one image of the batch, cycling
+    through the batch's sizes."""
     if rank != 0:
         return
     name, W, H, dt, seed = WORKLOADS[args.workload]
     spec = P.by_name(name)
-    img = I.round_to(I.uniform_image(seed, W, H)[0], dt)
-    for _ in range(args.warmup):
-        cpu_oracle_rate(spec, img, 0.0)
-    rates = []
+    if args.workload == "harris_batch":
+        sizes = batch_sizes()
+        imgs = [I.round_to(I.uniform_image(seed * 1000 + i, w, h)[0], dt) for i, (w, h) in
+                enumerate(sizes[:max(1, args.steps + args.warmup)])]
+        sample = "one image of the 512-image batch per step (its sizes in order)"
+    else:
+        imgs = [I.round_to(I.uniform_image(seed, W, H)[0], dt)]
+        sample = "one full %dx%d image per step" % (W, H)
+    for k in range(args.warmup):
+        cpu_oracle_rate(spec, imgs[k % len(imgs)], 0.0)
+    px = 0
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r, cores, n, _ = cpu_oracle_rate(spec, img, 0.0)
-        rates.append(r)
+    cores = 1
+    for k in range(args.steps):
+        img = imgs[(args.warmup + k) % len(imgs)]
+        _, cores, _, _ = cpu_oracle_rate(spec, img, 0.0)
+        px += img.shape[-1] * img.shape[-2]
     total = time.perf_counter() - t0
-    value = W * H * args.steps / total / 1e6
+    value = px / total / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixels/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -148,9 +174,115 @@ def run_reference(args, rank):
             "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H,
                        "channels": 1, "storage": dt},
             "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
-                             "sample": "one full %dx%d image per step" % (W, H)},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+class Single:
+    """One image per step, rotating over buffer sets larger than 3x L2."""
+
+    def __init__(self, wt, torch, spec, W, H, dtype, seed, local):
+        self.wt, self.torch = wt, torch
+        self.W, self.H, self.dtype = W, H, dtype
+        self.esz = 4 if dtype == wt.WT_F32 else 2
+        self.img = I.uniform_image(seed, W, H)[0]
+        set_bytes = 2 * W * H * self.esz
+        l2 = torch.cuda.get_device_properties(local).L2_cache_size
+        self.nsets = max(3, -(-3 * l2 // set_bytes))
+        self.ins = [wt.DeviceImage(1, H, W, dtype).upload(self.img) for _ in range(self.nsets)]
+        self.outs = [wt.DeviceImage(1, H, W, dtype) for _ in range(self.nsets)]
+        self.px = W * H
+        self.alg_bytes = 2 * W * H * self.esz
+        self.l2_note = "rotating %d input/output sets (%.0f MB) > 3x L2" % (self.nsets, self.nsets * set_bytes / 1e6)
+
+    def run(self, pipe, i, sp):
+        k = i % self.nsets
+        pipe.run([self.ins[k].image()], [self.outs[k].image()], sp)
+
+    def tune(self, pipe, sp):
+        return pipe.schedule_tune([self.ins[0].image()], [self.outs[0].image()], 0, 0, 20, sp)
+
+    def kernel_name(self, pipe):
+        return pipe.debug_kernel(0, [self.ins[0].image()], [self.outs[0].image()])["name"]
+
+    def e2e(self, pipe, sp, warmup, steps):
+        wt, torch = self.wt, self.torch
+        hin = wt.DeviceImage(1, self.H, self.W, self.dtype, device="cpu", pin_host=True)
+        hin.view().copy_(self.ins[0].view().cpu())
+        hout = wt.DeviceImage(1, self.H, self.W, self.dtype, device="cpu", pin_host=True)
+        for _ in range(warmup):
+            pipe.run_host([hin.image()], [hout.image()], sp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            pipe.run_host([hin.image()], [hout.image()], sp)
+        return self.px * steps / (time.perf_counter() - t0) / 1e6, self.px * self.esz, self.px * self.esz
+
+    def cpu_sample(self, dts):
+        return I.round_to(self.img, dts)
+
+
+class Batch:
+    """All 512 images per step (one wt_run_batch); 4.9 GB in + out, far
+    beyond L2.  Inputs drawn on the device with the host generator's stream."""
+
+    def __init__(self, wt, torch, spec, dtype, seed):
+        from paper_1909_07190_gb300 import inputs_torch as IT
+        self.wt, self.torch = wt, torch
+        self.dtype = dtype
+        self.esz = 4 if dtype == wt.WT_F32 else 2
+        self.sizes = batch_sizes()
+        self.seed = seed
+        self.ins, self.outs = [], []
+        for i, (w, h) in enumerate(self.sizes):
+            d = wt.DeviceImage(1, h, w, dtype)
+            d.view().copy_(IT.uniform_image(seed * 1000 + i, w, h).to(d.t.dtype))
+            self.ins.append(d)
+            self.outs.append(wt.DeviceImage(1, h, w, dtype))
+        self.ii = [x.image() for x in self.ins]
+        self.oo = [x.image() for x in self.outs]
+        self.px = sum(w * h for w, h in self.sizes)
+        self.alg_bytes = 2 * self.px * self.esz
+        self.l2_note = "batch of %d images, %.2f GB in+out (> L2)" % (len(self.sizes), self.alg_bytes / 1e9)
+
+    def run(self, pipe, i, sp):
+        pipe.run_batch(self.ii, self.oo, len(self.sizes), sp)
+
+    def tune(self, pipe, sp):
+        return pipe.schedule_tune(self.ii, self.oo, len(self.sizes), 0, 5, sp)
+
+    def kernel_name(self, pipe):
+        return pipe.debug_batch(0, self.ii[:1], self.oo[:1], 1)["name"]
+
+    def e2e(self, pipe, sp, warmup, steps):
+        """Pinned host images: per step every input copied in, one batched
+        run, every output copied back."""
+        torch = self.torch
+        hin = [torch.empty_like(x.t, device="cpu").pin_memory() for x in self.ins]
+        hout = [torch.empty_like(x.t, device="cpu").pin_memory() for x in self.outs]
+        for h, x in zip(hin, self.ins):
+            h.copy_(x.t)
+
+        def step():
+            for h, x in zip(hin, self.ins):
+                x.t.copy_(h, non_blocking=True)
+            pipe.run_batch(self.ii, self.oo, len(self.sizes), sp)
+            for h, x in zip(hout, self.outs):
+                h.copy_(x.t, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        nb = sum(x.t.numel() * x.t.element_size() for x in self.ins)
+        return self.px * steps / (time.perf_counter() - t0) / 1e6, nb, nb
+
+    def cpu_sample(self, dts):
+        w, h = self.sizes[0]
+        return I.round_to(I.uniform_image(self.seed * 1000, w, h)[0], dts)
 
 
 def run_ours(args, rank, world, local):
@@ -165,42 +297,44 @@ def run_ours(args, rank, world, local):
     name, W, H, dts, seed = WORKLOADS[args.workload]
     dtype = wt.DTYPES[dts]
     spec = P.by_name(name)
-    img = I.uniform_image(seed + rank, W, H)[0]
-    esz = 4 if dtype == wt.WT_F32 else 2
-    set_bytes = 2 * W * H * esz
-    l2 = torch.cuda.get_device_properties(local).L2_cache_size
-    nsets = max(3, -(-3 * l2 // set_bytes))
-    ins = [wt.DeviceImage(1, H, W, dtype).upload(img) for _ in range(nsets)]
-    outs = [wt.DeviceImage(1, H, W, dtype) for _ in range(nsets)]
+    batched = args.workload == "harris_batch"
+    work = Batch(wt, torch, spec, dtype, seed + 7919 * rank) if batched else \
+        Single(wt, torch, spec, W, H, dtype, seed + rank, local)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
     fused = wt.Pipeline(spec)
-    fused.schedule_auto(W, H, dtype, wt.WT_MODEL_ANALYTIC)
+    tune_t0 = time.perf_counter()
+    tune = args.tune == "on" or (args.tune == "auto" and batched)
+    tuning = None
+    if tune:
+        tuned_ms, n_timed = work.tune(fused, sp)
+        tuning = {"schedules_timed": n_timed, "tuned_ms": tuned_ms,
+                  "seconds": round(time.perf_counter() - tune_t0, 1)}
     plain = wt.Pipeline(spec)
     plain.schedule(exec_mode=wt.WT_EXEC_PLAIN)
 
-    def capture(pipe, n, start):
+    def capture(step_fn, n):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             cs = torch.cuda.current_stream().cuda_stream
-            for i in range(start, start + n):
-                pipe.run([ins[i % nsets].image()], [outs[i % nsets].image()], cs)
+            for i in range(n):
+                step_fn(i, cs)
         return g
 
-    def timed(pipe, steps, warmup, sampler=None, per_graph=100):
-        """Kernel-only time of exactly `steps` runs: CUDA graphs of up to
-        `per_graph` back-to-back runs over rotating buffer sets, replayed,
-        CUDA events around the replays (no host work inside the region)."""
-        for i in range(max(warmup, nsets)):
-            pipe.run([ins[i % nsets].image()], [outs[i % nsets].image()], sp)
+    def timed(step_fn, steps, warmup, per_graph, sampler=None):
+        """Kernel-only time of exactly `steps` steps: CUDA graphs of up to
+        `per_graph` back-to-back steps, replayed, CUDA events around the
+        replays (no host work inside the region)."""
+        # every buffer set once (plans and tensor maps are cached per set)
+        for i in range(max(warmup, getattr(work, "nsets", 1))):
+            step_fn(i, sp)
         torch.cuda.synchronize()
         n = min(per_graph, steps)
         full, rem = divmod(steps, n)
-        g = capture(pipe, n, 0)
-        gr = capture(pipe, rem, 0) if rem else None
-        for _ in range(max(1, warmup // n)):
-            g.replay()
+        g = capture(step_fn, n)
+        gr = capture(step_fn, rem) if rem else None
+        g.replay()
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -226,36 +360,29 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         return total, per
 
+    per_graph = 10 if batched else 100
     sampler = ClockSampler(local)
-    total_f, per_f = timed(fused, args.steps, args.warmup, sampler)
+    total_f, per_f = timed(lambda i, s: work.run(fused, i, s), args.steps, args.warmup, per_graph, sampler)
     clocks = sampler.summary()
-    plain_steps = max(3, args.steps // 8)
-    total_p, per_p = timed(plain, plain_steps, args.warmup)
     fused.check(sp)
-    plain.check(sp)
+    unfused = None
+    if not batched:
+        plain_steps = max(3, args.steps // 8)
+        total_p, _ = timed(lambda i, s: work.run(plain, i, s), plain_steps, args.warmup, per_graph)
+        plain.check(sp)
+        unfused = {"value": work.px * world * plain_steps / (total_p / 1e3) / 1e6, "unit": "Mpixels/s",
+                   "ms_per_step": total_p / plain_steps, "launches_per_step": plain.launches_per_run()}
 
-    # end to end through the C ABI with host buffers (pinned), copies inside
-    hin = wt.DeviceImage(1, H, W, dtype, device="cpu", pin_host=True)
-    hin.view().copy_(ins[0].view().cpu())
-    hout = wt.DeviceImage(1, H, W, dtype, device="cpu", pin_host=True)
-    for _ in range(args.warmup):
-        fused.run_host([hin.image()], [hout.image()], sp)
-    torch.cuda.synchronize()
-    e2e_steps = max(3, min(200, args.steps // 4))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        fused.run_host([hin.image()], [hout.image()], sp)
-    e2e_s = time.perf_counter() - t0
+    e2e_steps = max(3, min(200, args.steps // 4)) if not batched else 3
+    e2e_value, h2d, d2h = work.e2e(fused, sp, args.warmup if not batched else 1, e2e_steps)
 
-    px = W * H
-    value = px * world * args.steps / (total_f / 1e3) / 1e6
+    value = work.px * world * args.steps / (total_f / 1e3) / 1e6
     launch_ms = statistics.mean(per_f)
-    alg_bytes = 2 * px * esz
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    achieved = work.alg_bytes / (launch_ms / 1e3) / 1e9
     # DRAM bytes per launch from the committed ncu summary, used only when it
     # was taken on the kernel that ran here (same generated kernel name)
-    kname = fused.debug_kernel(0, [ins[0].image()], [outs[0].image()])["name"]
+    kname = work.kernel_name(fused)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -265,28 +392,30 @@ def run_ours(args, rank, world, local):
                 traffic = rec["dram_bytes_per_launch"]
         except Exception:
             traffic = None
+    launches = fused.launches_per_run()
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_f / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dts, "data": "synthetic",
         "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H, "channels": 1,
-                   "storage": dts, "stages": len(spec["stages"]),
-                   "l2": "rotating %d input/output sets (%.0f MB) > 3x L2" % (nsets, nsets * set_bytes / 1e6),
-                   "schedule": fused.schedule_get()},
+                   "storage": dts, "stages": len(spec["stages"]), "pixels_per_step": work.px,
+                   "l2": work.l2_note, "schedule": fused.schedule_get(),
+                   "tuning": tuning},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kname,
-                     "algorithmic_bytes_per_launch": alg_bytes},
-        "unfused": {"value": px * world * plain_steps / (total_p / 1e3) / 1e6, "unit": "Mpixels/s",
-                    "ms_per_step": total_p / plain_steps, "launches_per_step": plain.launches_per_run()},
-        "e2e": {"value": px * e2e_steps / e2e_s / 1e6, "unit": "Mpixels/s", "h2d_bytes_per_step": px * esz,
-                "d2h_bytes_per_step": px * esz},
-        "gpu_launches": args.steps * fused.launches_per_run(),
+                     "algorithmic_bytes_per_launch": work.alg_bytes // launches},
+        "unfused": unfused,
+        "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * launches,
         "clocks": clocks,
     }
+    if batched:
+        line["config"]["images"] = len(work.sizes)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, cores, n, dt = cpu_oracle_rate(spec, I.round_to(img, dts), args.cpu_seconds)
+        img = work.cpu_sample(dts)
+        r, cores, n, dt = cpu_oracle_rate(spec, img, args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d full %dx%d images, %.1f s" % (n, W, H, dt)}
+                                "sample": "%d full %dx%d images, %.1f s" % (n, img.shape[-1], img.shape[-2], dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -310,6 +439,9 @@ def main():
     ap.add_argument("--workload", default="harris", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", default="auto", choices=["auto", "on", "off"],
+                    help="measured schedule search before timing (auto: batches only; single images use the "
+                         "library's default schedule)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -245,13 +245,56 @@ wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                       const wt_image *outputs, int32_t n_outputs, void *stream);
 
 /* Batched serving: n_images independent runs (inputs[i*n_inputs + j],
- * outputs[i*n_outputs + k]) of images of any sizes, executed by ONE
- * persistent launch per group that pulls warp tiles from a device work
- * queue.  The pipeline must have a single fused group whose taps keep one
- * level.  Call once outside capture per batch shape, then it may be
- * captured in a CUDA graph.                                                */
+ * outputs[i*n_outputs + k], with n_inputs/n_outputs the pipeline's counts)
+ * of images of any sizes.  Each schedule group runs as ONE persistent
+ * launch whose warps pull warp tiles of every image from one device work
+ * queue (tile list: image, tile column, tile row, channel), so the batch
+ * costs one launch per group.  Every group of the schedule must fuse
+ * (WT_EUNSUPPORTED otherwise) and all images must share channels and
+ * dtypes (WT_EINVAL).  The first call for a set of image descriptors
+ * plans, compiles, allocates and uploads the tables (synchronizing
+ * `stream`); later calls with the same descriptors only launch, so they may
+ * be captured in a CUDA graph.  Intermediates between groups live in the
+ * pipeline's workspace, one slice per image.                               */
 wt_status wt_run_batch(wt_pipeline *p, const wt_image *inputs,
                        const wt_image *outputs, int32_t n_images, void *stream);
+
+/* ------------------------------------------- measured schedule search -- */
+
+/* Kernel time of the installed schedule on these images: 3 samples of
+ * `reps` back-to-back runs on `stream`, the minimum of the sample means
+ * (the timing protocol of Sec. 7), in *ms per run.  n_images = 0 times
+ * wt_run(inputs, n_inputs, outputs, n_outputs); n_images >= 1 times
+ * wt_run_batch over n_images images (n_inputs, n_outputs ignored).  The
+ * first runs (planning, compilation) are not timed.  WT_EDEVICE if a timed
+ * run raised the device error word.                                       */
+wt_status wt_schedule_time(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                           const wt_image *outputs, int32_t n_outputs, int32_t n_images,
+                           int32_t reps, void *stream, double *ms);
+
+/* The schedule search with device timings in place of the cost model's
+ * estimate (an autotuner), on the caller's images (same conventions as
+ * wt_schedule_time).  Candidates: the DP-Fusion grouping of the analytic
+ * model and, when it fuses, the whole pipeline as one group; then per group
+ * the max_variants (0 = 12) kernel variants -- warps per block, pixels per
+ * lane, register/shared placement, staging buffers -- that the analytic
+ * cost ranks best, and tile heights for the two fastest.  Kernels are
+ * compiled in parallel host threads first.  Installs the fastest schedule
+ * timed and returns its time (*best_ms) and the number of schedules timed
+ * (*n_timed; either may be null).  On failure the previous schedule stays
+ * installed.  Writes the outputs (every candidate runs).                   */
+wt_status wt_schedule_tune(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                           const wt_image *outputs, int32_t n_outputs, int32_t n_images,
+                           int32_t max_variants, int32_t reps, void *stream, double *best_ms,
+                           int32_t *n_timed);
+
+/* Compiles (NVRTC, parallel host threads) the kernels that these n_descs
+ * schedules would launch on these images (batched != 0: the persistent
+ * batch kernels), filling the process and disk kernel caches; runs nothing
+ * and installs nothing.  Schedules that do not plan are skipped.           */
+wt_status wt_prepare(wt_pipeline *p, const wt_schedule_desc *descs, int32_t n_descs,
+                     const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                     int32_t n_outputs, int32_t batched);
 
 /* Runs like wt_run, but allocates no device memory.  The paper has no
  * counterpart: this is for callers that cannot let a library call

@@ -31,6 +31,22 @@ wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *
                           int64_t src_cap, int64_t *src_len, void *args, int64_t args_cap,
                           int32_t *launch, char *kname, int64_t kname_cap);
 
+/* Describes launch `launch_index` of the batched run wt_run_batch would
+ * make for these n_images images (inputs[i*n_inputs + j], outputs[i*n_outputs
+ * + k]), without running it: the persistent kernel's source, its top-level
+ * argument block (tile count and image count set; table, queue and error
+ * pointers left zero for the caller), the n_images per-image argument blocks
+ * (wt_debug_args_size() bytes each, tensor maps in the introspection
+ * encoding of wt_debug_kernel) and the tile list, 4 int32 per tile (image,
+ * tile column, tile row, channel).  *n_tiles gets the tile count; null
+ * buffers are skipped, so a first call with nulls sizes them.  launch[8] as
+ * for wt_debug_kernel.  WT_EUNSUPPORTED if a group does not fuse.           */
+wt_status wt_debug_batch(wt_pipeline *p, int32_t launch_index, const wt_image *inputs,
+                         const wt_image *outputs, int32_t n_images, char *src, int64_t src_cap,
+                         int64_t *src_len, void *args, void *img_tab, int64_t img_tab_cap,
+                         int32_t *tiles, int64_t tiles_cap, int64_t *n_tiles, int32_t *launch,
+                         char *kname, int64_t kname_cap);
+
 /* Compiles launch `launch_index` of that run plan with NVRTC for sm_103a
  * (no GPU needed) and returns the CUBIN size; WT_ECOMPILE with the NVRTC
  * log in wt_last_error() on failure.                                       */

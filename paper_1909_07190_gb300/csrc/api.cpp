@@ -2,6 +2,7 @@
 // converts internal errors to a wt_status and a thread-local message.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "wt.h"
@@ -9,6 +10,7 @@
 #include "wt_jit.hpp"
 #include "wt_runtime.hpp"
 #include "wt_sched.hpp"
+#include "wt_tune.hpp"
 
 struct wt_pipeline : wt::Pipeline {};
 
@@ -43,7 +45,7 @@ void default_schedule(wt::Pipeline &p) {
   p.sched.installed = true;
 }
 
-void install(wt::Pipeline &p, const wt_schedule_desc *d) {
+wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
   wt::Schedule s;
   if (!d) fail(WT_EINVAL, "null schedule");
   if (d->exec != WT_EXEC_FUSED && d->exec != WT_EXEC_PLAIN) fail(WT_EINVAL, "bad exec mode");
@@ -97,7 +99,11 @@ void install(wt::Pipeline &p, const wt_schedule_desc *d) {
     s.params.assign(n, wt::GroupParams());
   }
   s.installed = true;
-  p.sched = s;
+  return s;
+}
+
+void install(wt::Pipeline &p, const wt_schedule_desc *d) {
+  p.sched = to_schedule(p, d);
   p.sched_version++;
 }
 
@@ -247,6 +253,47 @@ wt_status wt_run_batch(wt_pipeline *p, const wt_image *inputs, const wt_image *o
   });
 }
 
+wt_status wt_schedule_time(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                           int32_t n_outputs, int32_t n_images, int32_t reps, void *stream, double *ms) {
+  return guard([&] {
+    if (!p || !inputs || !outputs || !ms || n_images < 0 || reps < 1) wt::fail(WT_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(p->mu);
+    *ms = wt::time_installed(*p, inputs, n_inputs, outputs, n_outputs, n_images, (cudaStream_t)stream, reps);
+    if (!std::isfinite(*ms)) wt::fail(WT_EDEVICE, "a timed run raised the device error word");
+  });
+}
+
+wt_status wt_schedule_tune(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                           int32_t n_outputs, int32_t n_images, int32_t max_variants, int32_t reps, void *stream,
+                           double *best_ms, int32_t *n_timed) {
+  return guard([&] {
+    if (!p || !inputs || !outputs || n_images < 0) wt::fail(WT_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(p->mu);
+    const wt::Schedule user = p->sched;
+    try {
+      wt::TuneResult r = wt::tune(*p, inputs, n_inputs, outputs, n_outputs, n_images, max_variants, reps,
+                                  (cudaStream_t)stream);
+      if (best_ms) *best_ms = r.best_ms;
+      if (n_timed) *n_timed = r.timed;
+    } catch (...) {
+      p->sched = user;
+      p->sched_version++;
+      throw;
+    }
+  });
+}
+
+wt_status wt_prepare(wt_pipeline *p, const wt_schedule_desc *descs, int32_t n_descs, const wt_image *inputs,
+                     int32_t n_inputs, const wt_image *outputs, int32_t n_outputs, int32_t batched) {
+  return guard([&] {
+    if (!p || (n_descs > 0 && !descs) || n_descs < 0 || !inputs || !outputs) wt::fail(WT_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(p->mu);
+    std::vector<wt::Schedule> c;
+    for (int i = 0; i < n_descs; i++) c.push_back(to_schedule(*p, &descs[i]));
+    wt::precompile(*p, c, inputs, n_inputs, outputs, n_outputs, batched != 0);
+  });
+}
+
 wt_status wt_check(wt_pipeline *p, void *stream) {
   wt_status st = WT_OK;
   wt_status rc = guard([&] {
@@ -322,6 +369,64 @@ wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *
       launch[5] = L.fused ? 1 : 0;
       launch[6] = (int32_t)plan.launches.size();
       launch[7] = L.fused ? L.geom.unroll : 0;
+    }
+    if (kname && kname_cap > 0) {
+      size_t n = std::min((size_t)kname_cap - 1, L.kname.size());
+      memcpy(kname, L.kname.data(), n);
+      kname[n] = 0;
+    }
+  });
+}
+
+wt_status wt_debug_batch(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, const wt_image *outputs,
+                         int32_t n_images, char *src, int64_t src_cap, int64_t *src_len, void *args,
+                         void *img_tab, int64_t img_tab_cap, int32_t *tiles, int64_t tiles_cap,
+                         int64_t *n_tiles, int32_t *launch, char *kname, int64_t kname_cap) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    if (!inputs || !outputs || n_images < 1) wt::fail(WT_EINVAL, "bad batch");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::BatchPlan b = wt::build_batch(*p, inputs, outputs, n_images);
+    if (launch_index < 0 || launch_index >= (int)b.launches.size()) wt::fail(WT_EINVAL, "launch index");
+    const wt::Launch &L = b.launches[launch_index];
+    const std::vector<int32_t> &t = b.tiles[launch_index];
+    if (n_tiles) *n_tiles = (int64_t)t.size() / 4;
+    if (src_len || src) {
+      std::string s = wt::launch_source(*p, L);
+      if (src_len) *src_len = (int64_t)s.size();
+      if (src && src_cap > 0) {
+        size_t n = std::min((size_t)src_cap - 1, s.size());
+        memcpy(src, s.data(), n);
+        src[n] = 0;
+      }
+    }
+    if (img_tab) {
+      if (img_tab_cap < (int64_t)n_images * (int64_t)sizeof(wt::KernelArgs)) wt::fail(WT_EINVAL, "img_tab too small");
+      for (int i = 0; i < n_images; i++) {
+        wt::KernelArgs a = wt::batch_image_args(*p, b, launch_index, i, nullptr, false);
+        memcpy((char *)img_tab + (size_t)i * sizeof a, &a, sizeof a);
+      }
+    }
+    if (tiles) {
+      if (tiles_cap < (int64_t)t.size()) wt::fail(WT_EINVAL, "tile buffer too small");
+      memcpy(tiles, t.data(), t.size() * 4);
+    }
+    if (args) {
+      wt::KernelArgs a;
+      memset(&a, 0, sizeof a);
+      a.n_tiles = L.n_tiles;
+      a.n_images = n_images;
+      memcpy(args, &a, sizeof a);
+    }
+    if (launch) {
+      launch[0] = (int32_t)L.grid[0];
+      launch[1] = 1;
+      launch[2] = 1;
+      launch[3] = L.block;
+      launch[4] = L.smem;
+      launch[5] = 1;
+      launch[6] = (int32_t)b.launches.size();
+      launch[7] = L.geom.unroll;
     }
     if (kname && kname_cap > 0) {
       size_t n = std::min((size_t)kname_cap - 1, L.kname.size());

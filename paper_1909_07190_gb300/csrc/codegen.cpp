@@ -224,12 +224,15 @@ void emit_source_row(Ctx &c, int ni, bool safe, int u) {
   o << "{\n";
   if (safe) o << "if (k < nsrc) {\n";
   if (safe) o << "const int ri = wt_clampi(y_top + k, 0, H - 1) - y_top;\n";
-  else o << "const int ri = k;\n";
   std::vector<std::string> v = names("e", V);
   o << "float";
   for (int e = 0; e < V; e++) o << (e ? ", " : " ") << v[e];
   o << ";\n";
-  emit_load_vec(c, c.key.src_dtypes[s], ring_row(s, "ri"), v, c.L.esz[s]);
+  // guard-free steps read row kb + u of the chunk that block kb starts
+  // (chunks are a multiple of U rows): the block's row pointer plus u rows
+  const std::string S = std::to_string(s);
+  emit_load_vec(c, c.key.src_dtypes[s], safe ? ring_row(s, "ri") : "rp" + S + " + " + std::to_string(u) + " * ROWB" + S,
+                v, c.L.esz[s]);
   if (safe) emit_xfix(c, v);
   int sl = slot_of(n, u, 0);
   emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
@@ -451,7 +454,7 @@ void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
   if (n.channels == 1 && c.g.channels > 1) o << "if (ch == 0)\n";
   o << "{ const int x = xs + lane * " << V << ";\n";
   o << "if (lane >= " << c.L.lpad / V << " && lane < " << 32 - c.L.rpad / V << ") {\n";
-  std::string d = "a.dst[" + std::to_string(n.dst_index) + "]";
+  std::string d = "ia.dst[" + std::to_string(n.dst_index) + "]";
   o << "unsigned char *op_ = (unsigned char *)" << d << ".ptr + (wt_i64)"
     << (n.channels > 1 ? "ch" : "0") << " * " << d << ".plane + (wt_i64)r * " << d
     << ".pitch + (wt_i64)x * " << esz << ";\n";
@@ -645,16 +648,23 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
     o << "const int tx = tt_[1], ty = tt_[2], ch = tt_[3];\n";
   } else {
-    // tall tiles first (tile rows [0, ty1) of tile_h rows), then short
-    // tiles of tile_h2 rows, so the last tiles handed out are short
+    // tall tiles first (ty1 tile rows of tile_h rows below a band of ty2
+    // short rows), then the short tiles of tile_h2 rows: the last tiles
+    // handed out are short, and the slow bottom-border row is handed out
+    // before them, not in the final round
     o << "const WtArgs &ia = a;\n";
     o << "int tx, ch, y0, T;\n";
     o << "if (tile < a.n_big) { tx = tile % a.tiles_x; const int tr_ = tile / a.tiles_x;"
-         " y0 = (tr_ % a.ty1) * a.tile_h; ch = tr_ / a.ty1; T = a.tile_h; }\n"
+         " y0 = a.ty2 * a.tile_h2 + (tr_ % a.ty1) * a.tile_h; ch = tr_ / a.ty1; T = a.tile_h; }\n"
          "else { const int j_ = tile - a.n_big; tx = j_ % a.tiles_x; const int tr_ = j_ / a.tiles_x;"
-         " y0 = a.ty1 * a.tile_h + (tr_ % a.ty2) * a.tile_h2; ch = tr_ / a.ty2; T = a.tile_h2; }\n";
+         " y0 = (tr_ % a.ty2) * a.tile_h2; ch = tr_ / a.ty2; T = a.tile_h2; }\n";
   }
-  if (key.persistent) o << "const int T = ia.tile_h, y0 = ty * T;\n";
+  if (key.persistent) {
+    o << "const int T = ia.tile_h, y0 = ty * T;\n";
+    o << "if (lane == 0) {";
+    for (int s = 0; s < n_src; s++) o << " wt_tmap_acquire(&ia.tmap[" << s << "]);";
+    o << " }\n";
+  }
   o << "const int W = ia.W, H = ia.H;\n";
   o << "const int xs = tx * " << L.out_w << " - " << L.lpad << ";\n";
   o << "const int y_top = y0 - " << HT << ";\n";
@@ -708,6 +718,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
        " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = c_; goto wt_fail; } } }\n"
        "if (kc_ == ISSUE) { const int c_ = kb / CH + NB - 1; if (c_ * CH < nrows) issue_chunk(c_); } }\n";
   o << "if (!border) {\n";
+  for (int s = 0; s < n_src; s++) o << "const unsigned char *rp" << s << " = " << ring_row(s, "kb") << ";\n";
   for (int u = 0; u < c.U; u++) emit_step(c, false, u);
   o << "} else {\n";
   for (int u = 0; u < c.U; u++) emit_step(c, true, u);

@@ -51,6 +51,12 @@ static __device__ __forceinline__ void wt_fence_mbar_init() {
 static __device__ __forceinline__ void wt_fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// A tensor map read from global memory (batched runs keep one per image in
+// a device table written before the launch): acquire it for the async proxy
+// before the first bulk tensor copy that names it.
+static __device__ __forceinline__ void wt_tmap_acquire(const void *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((wt_u64)map) : "memory");
+}
 static __device__ __forceinline__ void wt_mbar_expect_tx(wt_u32 bar, wt_u32 bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");

@@ -12,7 +12,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
+#include <map>
+#include <mutex>
 #include <sstream>
+#include <thread>
 
 #include "wt_internal.hpp"
 #include "wt_jit.hpp"
@@ -65,6 +68,10 @@ void check_rt(int rc, const char *what) {
   fail(WT_ECUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)rc));
 }
 
+// compiled kernels of this process (NVRTC runs once per kernel text)
+static std::mutex g_cubin_mu;
+static std::map<std::string, std::string> g_cubins;
+
 static std::string cache_dir() {
   const char *e = getenv("WT_CACHE_DIR");
   if (e && *e) return e;
@@ -93,13 +100,26 @@ std::string compile_cubin(const std::string &src, const std::string &name, int m
   snprintf(hex, sizeof hex, "%016llx", (unsigned long long)h);
   std::string dir = cache_dir();
   std::string path = dir + "/" + name + "_" + hex + ".cubin";
+  {
+    std::lock_guard<std::mutex> lk(g_cubin_mu);
+    auto it = g_cubins.find(name + "_" + hex);
+    if (it != g_cubins.end()) return it->second;
+  }
+  auto remember = [&](const std::string &b) {
+    std::lock_guard<std::mutex> lk(g_cubin_mu);
+    if (g_cubins.size() > 512) g_cubins.clear();
+    g_cubins[name + "_" + hex] = b;
+  };
   if (!getenv("WT_NO_DISK_CACHE")) {
     std::ifstream f(path, std::ios::binary);
     if (f) {
       std::stringstream ss;
       ss << f.rdbuf();
       std::string b = ss.str();
-      if (!b.empty()) return b;
+      if (!b.empty()) {
+        remember(b);
+        return b;
+      }
     }
   }
   nvrtcProgram prog;
@@ -124,7 +144,8 @@ std::string compile_cubin(const std::string &src, const std::string &name, int m
   nvrtcDestroyProgram(&prog);
   if (!getenv("WT_NO_DISK_CACHE")) {
     mkdirs(dir);
-    std::string tmp = path + "." + std::to_string(getpid()) + ".tmp";
+    std::string tmp = path + "." + std::to_string(getpid()) + "." +
+                      std::to_string(std::hash<std::thread::id>()(std::this_thread::get_id())) + ".tmp";
     std::ofstream f(tmp, std::ios::binary);
     if (f) {
       f.write(cubin.data(), (std::streamsize)cubin.size());
@@ -132,6 +153,7 @@ std::string compile_cubin(const std::string &src, const std::string &name, int m
       rename(tmp.c_str(), path.c_str());
     }
   }
+  remember(cubin);
   return cubin;
 }
 

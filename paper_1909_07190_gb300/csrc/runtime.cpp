@@ -209,16 +209,21 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       if (L.H > 65535 || L.grid[2] > 65535) fail(WT_EUNSUPPORTED, "image too tall for the per-stage kernel");
       L.smem = 0;
     }
-    char hx[24];
-    // the generator's version is part of the name: a kernel whose code
-    // changes gets a new name (profiles and caches never mix versions)
-    static const char kCodegenVersion[] = "wt-codegen-3";
-    uint64_t h = fnv1a(key.str().data(), key.str().size(), p.hash);
-    h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
-    snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
-    L.kname = std::string(L.fused ? "wt_fused_" : "wt_plain_") + hx;
+    L.kname = kernel_name(p, key, L.fused);
   }
   return plan;
+}
+
+std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused) {
+  char hx[24];
+  // the generator's version is part of the name: a kernel whose code
+  // changes gets a new name (profiles and caches never mix versions)
+  static const char kCodegenVersion[] = "wt-codegen-4";
+  const std::string ks = key.str();
+  uint64_t h = fnv1a(ks.data(), ks.size(), p.hash);
+  h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
+  snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
+  return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }
 
 std::string launch_source(const Pipeline &p, const Launch &L) {
@@ -286,7 +291,7 @@ void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws
   // one tile height unless split_tiles() assigns a short last round
   a.tile_h2 = a.tile_h;
   a.ty1 = L.tiles_y;
-  a.ty2 = 1;
+  a.ty2 = 0;
   a.n_big = L.n_tiles;
   a.chunk = L.layout.chunk;
   a.nbuf = L.layout.nbuf;
@@ -389,22 +394,23 @@ Workspace &workspace(Pipeline &p, int64_t bytes) {
 
 // Two-level tile heights (load balance of the persistent warps): the last
 // round of tiles handed out is short, about one tile per resident warp, so
-// warps finish within one short tile of each other.
+// warps finish within one short tile of each other.  The short tiles form a
+// band of ty2 rows of tile_h2 at the top of the image, the tall tiles the
+// ty1 rows below it (the last one clipped by the image).
 void split_tiles(const Launch &L, KernelArgs &a, int resident_warps) {
   const int T1 = std::max(1, L.params.tile_h);
   const int T2 = std::max(4, T1 / 2);
   if (!L.fused || T2 >= T1 || L.params.tile_split == 0) return;
   const int C = L.geom.channels;
   const int per_row = std::max(1, L.tiles_x * C);
-  int ty2 = (resident_warps + per_row - 1) / per_row;
-  int ty1 = std::max(0, (L.H - ty2 * T2) / T1);
-  if (ty1 < 1) return;  // too small to split
-  ty2 = (L.H - ty1 * T1 + T2 - 1) / T2;
+  const int ty2 = (resident_warps + per_row - 1) / per_row;
+  if (L.H - ty2 * T2 < T1) return;  // too small to split
+  const int ty1 = (L.H - ty2 * T2 + T1 - 1) / T1;
   a.tile_h2 = T2;
   a.ty1 = ty1;
-  a.ty2 = std::max(1, ty2);
+  a.ty2 = ty2;
   a.n_big = L.tiles_x * ty1 * C;
-  a.n_tiles = a.n_big + L.tiles_x * a.ty2 * C;
+  a.n_tiles = a.n_big + L.tiles_x * ty2 * C;
 }
 
 int32_t *queue_counters(int32_t *ctrl, int launch_index) {

@@ -133,7 +133,8 @@ struct Kernel {
   std::string name;
 };
 
-struct Workspace;  // runtime buffers (defined in runtime.cpp)
+struct Workspace;   // runtime buffers (defined in runtime.cpp)
+struct BatchCache;  // batched-run launches and tables (batch.cpp)
 
 // Launch-argument block shared by every generated kernel (device layout is
 // mirrored in the device source).
@@ -206,6 +207,7 @@ struct Pipeline {
   RunCache cache;
   std::mutex mu;
   std::shared_ptr<Workspace> ws;
+  std::shared_ptr<BatchCache> batch;
   uint64_t hash = 0;
 };
 

@@ -71,6 +71,9 @@ std::vector<std::vector<int>> schedule_groups(const Pipeline &p);
 GroupParams group_params(const Pipeline &p, int gi);
 RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out);
 std::string launch_source(const Pipeline &p, const Launch &L);
+// Entry-point name of a generated kernel (a hash of the pipeline, the
+// codegen key and the generator version).
+std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused);
 void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws, KernelArgs &a,
                bool encode_tmaps);
 Kernel &get_kernel(const Pipeline &p, const Launch &L, int device);
@@ -82,5 +85,19 @@ Workspace &workspace(Pipeline &p, int64_t bytes);
 void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string *cache_key = nullptr);
 // wt_run: reuses the cached launches when schedule and images are unchanged.
 void run(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out, cudaStream_t stream);
+
+// Batched runs (batch.cpp): per-image plans (same kernels), each image's
+// slice of the workspace, and per group the persistent launch with its tile
+// list (4 ints per tile: image, tile column, tile row, channel).
+struct BatchPlan {
+  std::vector<RunPlan> img;
+  std::vector<int64_t> ws_off;
+  int64_t ws_bytes = 0;
+  std::vector<Launch> launches;
+  std::vector<std::vector<int32_t>> tiles;
+};
+BatchPlan build_batch(Pipeline &p, const wt_image *in, const wt_image *out, int n);
+KernelArgs batch_image_args(const Pipeline &p, const BatchPlan &b, int l, int i, char *ws, bool encode_tmaps);
+void run_batch(Pipeline &p, const wt_image *in, const wt_image *out, int n_images, cudaStream_t stream);
 
 }  // namespace wt

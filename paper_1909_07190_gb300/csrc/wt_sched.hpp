@@ -1,5 +1,5 @@
 // Scheduling: cost models and DP-Fusion (sched.cpp), learned model
-// (learned.cpp), batched runtime (batch.cpp).
+// (learned.cpp).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -82,8 +82,5 @@ Schedule auto_schedule(const Pipeline &p, int W, int H, int dtype, int model);
 // learned.cpp
 CandidateScorer learned_scorer(const Pipeline &p, int W, int H, int dtype, const GpuConfig &cfg,
                                const std::vector<StageStats> &st);
-
-// batch.cpp
-void run_batch(Pipeline &p, const wt_image *in, const wt_image *out, int n_images, cudaStream_t stream);
 
 }  // namespace wt

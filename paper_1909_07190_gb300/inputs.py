@@ -18,32 +18,49 @@ GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 SEED_BASE = 190907190
 
 
-def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
-    """n consecutive outputs (uint64) of the counter-based splitmix64 stream."""
+def splitmix64(seed: int, n: int, offset: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+    """n consecutive outputs (uint64) of the counter-based splitmix64 stream
+    (in place, in blocks that stay in cache)."""
+    z = np.empty(n, np.uint64) if out is None else out[:n]
+    blk = 1 << 18
+    t = np.empty(min(n, blk), np.uint64)
     with np.errstate(over="ignore"):
-        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
-        z = np.uint64(seed) + i * GOLDEN
-        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
-        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
-        z = z ^ (z >> np.uint64(31))
+        for s in range(0, n, blk):
+            e = min(n, s + blk)
+            zz, tt = z[s:e], t[:e - s]
+            zz[...] = np.arange(offset + s + 1, offset + e + 1, dtype=np.uint64)
+            np.multiply(zz, GOLDEN, out=zz)
+            np.add(zz, np.uint64(seed), out=zz)
+            np.right_shift(zz, np.uint64(30), out=tt)
+            np.bitwise_xor(zz, tt, out=zz)
+            np.multiply(zz, np.uint64(0xBF58476D1CE4E5B9), out=zz)
+            np.right_shift(zz, np.uint64(27), out=tt)
+            np.bitwise_xor(zz, tt, out=zz)
+            np.multiply(zz, np.uint64(0x94D049BB133111EB), out=zz)
+            np.right_shift(zz, np.uint64(31), out=tt)
+            np.bitwise_xor(zz, tt, out=zz)
     return z
 
 
-def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
-    """float32 values in [0, 1) with 24 random bits each."""
-    u = splitmix64(seed, n, offset)
-    return ((u >> np.uint64(40)).astype(np.float64) * (2.0 ** -24)).astype(np.float32)
+def uniform01(seed: int, n: int, offset: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+    """float32 values in [0, 1) with 24 random bits each (exact: the 24-bit
+    integer converts to float32 exactly and the scale is a power of two)."""
+    r = np.empty(n, np.float32) if out is None else out[:n]
+    blk = 1 << 18
+    u = np.empty(min(n, blk), np.uint64)
+    for s in range(0, n, blk):
+        e = min(n, s + blk)
+        uu = splitmix64(seed, e - s, offset + s, out=u)
+        np.right_shift(uu, np.uint64(40), out=uu)
+        r[s:e] = uu
+        np.multiply(r[s:e], np.float32(2.0 ** -24), out=r[s:e])
+    return r
 
 
-def uniform_image(seed: int, width: int, height: int, channels: int = 1,
-                  chunk: int = 1 << 24) -> np.ndarray:
+def uniform_image(seed: int, width: int, height: int, channels: int = 1) -> np.ndarray:
     """(channels, height, width) float32 image, uniform in [0, 1)."""
     n = width * height * channels
-    out = np.empty(n, np.float32)
-    for s in range(0, n, chunk):
-        e = min(n, s + chunk)
-        out[s:e] = uniform01(seed, e - s, s)
-    return out.reshape(channels, height, width)
+    return uniform01(seed, n).reshape(channels, height, width)
 
 
 def uniform_ints(seed: int, n: int, lo: int, hi: int) -> np.ndarray:

@@ -95,6 +95,11 @@ SIGNATURES = [
     ("wt_run", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_run_host", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_run_batch", _i32, [_vp, _P(wt_image), _P(wt_image), _i32, _vp]),
+    ("wt_schedule_time", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _i32, _i32, _vp,
+                                _P(ctypes.c_double)]),
+    ("wt_schedule_tune", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _i32, _i32, _i32, _vp,
+                                _P(ctypes.c_double), _P(_i32)]),
+    ("wt_prepare", _i32, [_vp, _P(wt_schedule_desc), _i32, _P(wt_image), _i32, _P(wt_image), _i32, _i32]),
     ("wt_run_static", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_check", _i32, [_vp, _vp]),
     ("wt_launches_per_run", _i32, [_vp]),
@@ -103,6 +108,8 @@ SIGNATURES = [
     ("wt_debug_args_size", _i64, []),
     ("wt_debug_kernel", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, ctypes.c_char_p, _i64,
                                _P(_i64), _vp, _i64, _P(_i32), ctypes.c_char_p, _i64]),
+    ("wt_debug_batch", _i32, [_vp, _i32, _P(wt_image), _P(wt_image), _i32, ctypes.c_char_p, _i64, _P(_i64),
+                              _vp, _vp, _i64, _P(_i32), _i64, _P(_i64), _P(_i32), ctypes.c_char_p, _i64]),
     ("wt_debug_compile", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i64)]),
     ("wt_debug_layout", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
@@ -289,6 +296,46 @@ class Pipeline:
         oa = (wt_image * len(outputs))(*outputs)
         check(load().wt_run_batch(self.h, ia, oa, n_images, stream))
 
+    def schedule_time(self, inputs, outputs, n_images=0, reps=20, stream=None) -> float:
+        """ms per run of the installed schedule (n_images >= 1: batched)."""
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        ms = ctypes.c_double()
+        check(load().wt_schedule_time(self.h, ia, len(inputs), oa, len(outputs), n_images, reps, stream,
+                                      ctypes.byref(ms)))
+        return ms.value
+
+    def schedule_tune(self, inputs, outputs, n_images=0, max_variants=0, reps=20, stream=None):
+        """Measured schedule search; installs the fastest.  Returns (ms, n_timed)."""
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        ms, nt = ctypes.c_double(), _i32()
+        check(load().wt_schedule_tune(self.h, ia, len(inputs), oa, len(outputs), n_images, max_variants, reps,
+                                      stream, ctypes.byref(ms), ctypes.byref(nt)))
+        return ms.value, nt.value
+
+    def prepare(self, schedules, inputs, outputs, batched=False):
+        """Compiles the kernels of schedules [(groups, params), ...] in parallel."""
+        n = len(self.spec["stages"])
+        keep, descs = [], (wt_schedule_desc * len(schedules))()
+        for k, (groups, params) in enumerate(schedules):
+            groups = [0] * n if groups is None else groups
+            ng = max(groups) + 1
+            g = (_i32 * n)(*groups)
+            prm = (wt_group_params * ng)()
+            for i in range(ng):
+                d = dict(tile_h=16, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
+                         n_buffers=0, flags=0)
+                if params is not None:
+                    d.update(params[i] if isinstance(params, (list, tuple)) else params)
+                for kk, v in d.items():
+                    setattr(prm[i], kk, v)
+            keep += [g, prm]
+            descs[k] = wt_schedule_desc(WT_EXEC_FUSED, ng, g, prm, -1)
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        check(load().wt_prepare(self.h, descs, len(schedules), ia, len(inputs), oa, len(outputs), int(batched)))
+
     def check(self, stream=None):
         check(load().wt_check(self.h, stream))
 
@@ -309,6 +356,28 @@ class Pipeline:
         return {"source": src.value.decode(), "args": args.raw, "grid": tuple(launch[0:3]),
                 "block": launch[3], "smem": launch[4], "fused": bool(launch[5]),
                 "n_launches": launch[6], "unroll": launch[7], "name": kname.value.decode()}
+
+    def debug_batch(self, index, inputs, outputs, n_images):
+        """inputs/outputs: flat lists, image-major (n_images * n_inputs)."""
+        lib = load()
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        n, nt = _i64(), _i64()
+        check(lib.wt_debug_batch(self.h, index, ia, oa, n_images, None, 0, ctypes.byref(n), None, None, 0,
+                                 None, 0, ctypes.byref(nt), None, None, 0))
+        asz = int(lib.wt_debug_args_size())
+        src = ctypes.create_string_buffer(n.value + 1)
+        args = ctypes.create_string_buffer(asz)
+        tab = ctypes.create_string_buffer(asz * n_images)
+        tiles = (_i32 * (4 * nt.value))()
+        launch = (_i32 * 8)()
+        kname = ctypes.create_string_buffer(128)
+        check(lib.wt_debug_batch(self.h, index, ia, oa, n_images, src, n.value + 1, None, args, tab, len(tab),
+                                 tiles, 4 * nt.value, None, launch, kname, 128))
+        return {"source": src.value.decode(), "args": args.raw, "img_tab": tab.raw,
+                "tiles": list(tiles), "n_tiles": nt.value, "grid": tuple(launch[0:3]), "block": launch[3],
+                "smem": launch[4], "fused": True, "n_launches": launch[6], "unroll": launch[7],
+                "name": kname.value.decode()}
 
     def debug_compile(self, index, inputs, outputs) -> int:
         ia = (wt_image * len(inputs))(*inputs)

@@ -59,7 +59,9 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
     body = source.split(MARK, 1)[1]
     text = '#include "wt_emu.h"\n' + body + \
         '\nextern "C" long wt_emu_offset_err() { return (long)offsetof(WtArgs, err); }\n' + \
-        'extern "C" long wt_emu_offset_queue() { return (long)offsetof(WtArgs, queue); }\n'
+        'extern "C" long wt_emu_offset_queue() { return (long)offsetof(WtArgs, queue); }\n' + \
+        'extern "C" long wt_emu_offset_tiles() { return (long)offsetof(WtArgs, tile_table); }\n' + \
+        'extern "C" long wt_emu_offset_imgtab() { return (long)offsetof(WtArgs, img_tab); }\n'
     h = hashlib.sha1((text + open(os.path.join(HERE, "wt_emu.h")).read() +
                       open(os.path.join(HERE, "emu_rt.cpp")).read()).encode()).hexdigest()[:16]
     if h in _loaded:
@@ -111,5 +113,37 @@ def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None):
     if err[0] != 0:
         raise RuntimeError("emulated kernel raised error word %d" % err[0])
     if d["fused"] and (queue[0] != 0 or queue[1] != 0):
+        raise RuntimeError("tile queue not reset at kernel exit: %s" % queue)
+    return d
+
+
+def run_batch(pipe: "wt.Pipeline", index: int, inputs, outputs, n_images, max_blocks=None):
+    """Batched launch `index` (one persistent kernel over all images' tiles).
+    inputs/outputs: flat HostImage lists, image-major."""
+    ii = [x.image() for x in inputs]
+    oo = [x.image() for x in outputs]
+    d = pipe.debug_batch(index, ii, oo, n_images)
+    lib = _compile(d["source"], d["name"])
+    args = bytearray(d["args"])
+    tab = np.frombuffer(bytearray(d["img_tab"]), np.uint8).copy()
+    tiles = np.asarray(d["tiles"], np.int32)
+    err = np.zeros(16, np.int32)
+    queue = np.zeros(2, np.int32)
+    for off_fn, arr in ((lib.wt_emu_offset_err, err), (lib.wt_emu_offset_queue, queue),
+                        (lib.wt_emu_offset_tiles, tiles), (lib.wt_emu_offset_imgtab, tab)):
+        off = off_fn()
+        args[off:off + 8] = int(arr.ctypes.data).to_bytes(8, "little")
+    abuf = (ctypes.c_char * len(args)).from_buffer(args)
+    kfn = ctypes.cast(getattr(lib, d["name"]), ctypes.c_void_p)
+    lib.wt_emu_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
+    msg = ctypes.create_string_buffer(512)
+    gx = d["grid"][0] if max_blocks is None else min(d["grid"][0], max_blocks)
+    rc = lib.wt_emu_run(kfn, ctypes.addressof(abuf), gx, 1, 1, d["block"], d["smem"], msg, 512)
+    if rc != 0:
+        raise RuntimeError("emulated kernel failed: " + msg.value.decode())
+    if err[0] != 0:
+        raise RuntimeError("emulated kernel raised error word %d" % err[0])
+    if queue[0] != 0 or queue[1] != 0:
         raise RuntimeError("tile queue not reset at kernel exit: %s" % queue)
     return d

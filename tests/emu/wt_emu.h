@@ -110,6 +110,7 @@ static inline unsigned char *wt_emu_sptr(wt_u32 a) { return wt_emu_smem() + a; }
 static inline void wt_mbar_init(wt_u32 bar, wt_u32) { memset(wt_emu_sptr(bar), 0, 8); }
 static inline void wt_fence_mbar_init() {}
 static inline void wt_fence_proxy_async() {}
+static inline void wt_tmap_acquire(const void *) {}
 static inline void wt_mbar_expect_tx(wt_u32 bar, wt_u32) {
   // the copies that follow complete synchronously: finish the phase now
   int32_t ph;
