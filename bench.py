@@ -304,6 +304,8 @@ def run_ours(args, rank, world, local):
     sp = stream.cuda_stream
 
     fused = wt.Pipeline(spec)
+    if args.params:
+        fused.schedule(params=json.loads(args.params))
     tune_t0 = time.perf_counter()
     tune = args.tune == "on" or (args.tune == "auto" and batched)
     tuning = None
@@ -439,6 +441,8 @@ def main():
     ap.add_argument("--workload", default="harris", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--params", default="",
+                    help="JSON group parameters of a one-group fused schedule (e.g. '{\"tile_h\": 20}')")
     ap.add_argument("--tune", default="auto", choices=["auto", "on", "off"],
                     help="measured schedule search before timing (auto: batches only; single images use the "
                          "library's default schedule)")

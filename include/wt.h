@@ -128,6 +128,7 @@ typedef struct {
 
 #define WT_FLAG_NO_PAIRS 1      /* scalar FP32 instead of packed f32x2 pairs     */
 #define WT_FLAG_NO_TILE_SPLIT 2 /* one tile height (no short last round)         */
+#define WT_FLAG_PLAIN 4         /* the group's stages as per-stage kernels       */
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */
@@ -295,6 +296,77 @@ wt_status wt_schedule_tune(wt_pipeline *p, const wt_image *inputs, int32_t n_inp
 wt_status wt_prepare(wt_pipeline *p, const wt_schedule_desc *descs, int32_t n_descs,
                      const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
                      int32_t n_outputs, int32_t batched);
+
+/* Per-launch kernel times of one wt_run of the installed schedule on these
+ * images: each launch repeated `reps` times on its own (it re-reads what the
+ * earlier launches wrote), 3 samples, the minimum of the means.  ms[i] and
+ * info[3i..3i+2] = (first stage, stage count, fused 1 / per-stage 0) for
+ * launch i, in launch order; *n_launches gets the count (arrays of `cap`
+ * entries; WT_EINVAL if too small).  Training data of the learned model.  */
+wt_status wt_schedule_time_launches(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                                    const wt_image *outputs, int32_t n_outputs, int32_t reps,
+                                    void *stream, double *ms, int32_t *info, int32_t cap,
+                                    int32_t *n_launches);
+
+/* ------------------------------------------------- learned cost model -- */
+
+/* A 3-layer FP32 MLP, WT_COSTMODEL_FEATURES -> 64 -> 64 -> 1 with ReLU, that
+ * predicts the natural log of one launch's kernel time in ms.  The paper's
+ * cost function is a hand-weighted sum of Alg. 2's terms whose weights are
+ * fitted per GPU (Sec. 6, Table 3); this model is trained instead on times
+ * the library measures.  Training and inference run in hand-written CUDA
+ * kernels; wt_schedule_auto(..., WT_MODEL_LEARNED) uses a trained or loaded
+ * model and falls back to the analytic model without one.                 */
+#define WT_COSTMODEL_FEATURES 18
+#define WT_COSTMODEL_HIDDEN 64
+/* parameters, in order: W1[64][18], b1[64], W2[64][64], b2[64], w3[64], b3 */
+#define WT_MLP_PARAMS (64 * 18 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* Features of one launch at image size width x height (level-0 pixels) and
+ * storage dtype: stages [first_stage, first_stage + n_stages) as one fused
+ * group with `params` (fused = 1), or stage first_stage's per-stage kernel
+ * (fused = 0, n_stages = 1, params may be null).  features[18] = log2 of the
+ * group's pixels, stages, computed nodes, operations per pixel, bytes read
+ * and written per pixel, y and x footprint growth, log2 tile height,
+ * pixels per lane, warps per block, fracReg, registers/255, shared bytes per
+ * block/227 KB, Alg. 2 occupancy, redundant-compute fraction, tail
+ * fraction, fused.  WT_EUNSUPPORTED if the launch is infeasible.           */
+wt_status wt_costmodel_features(wt_pipeline *p, int32_t first_stage, int32_t n_stages,
+                                const wt_group_params *params, int32_t fused, int32_t width,
+                                int32_t height, int32_t dtype, float *features);
+
+/* The MLP training kernel: `steps` Adam steps (beta 0.9/0.999, eps 1e-8,
+ * t0 steps taken before) on the mean squared error over mini-batches
+ * idx[steps][batch] of rows of x[n][18] with targets y[n], decoupled L2
+ * weight decay on the weight matrices.  params, adam_m, adam_v
+ * (WT_MLP_PARAMS floats each, host memory) are read and updated; loss[k]
+ * (may be null) = batch mean squared error before step k.  batch in
+ * [1, 128].  Synchronizes `stream`.                                        */
+wt_status wt_mlp_train_steps(float *params, float *adam_m, float *adam_v, int32_t t0,
+                             const float *x, const float *y, int32_t n, const int32_t *idx,
+                             int32_t steps, int32_t batch, float lr, float weight_decay,
+                             float *loss, void *stream);
+/* The MLP inference kernel: y[i] = MLP(params; x[i]) for n rows (host
+ * arrays).  Synchronizes `stream`.                                          */
+wt_status wt_mlp_forward(const float *params, const float *x, int32_t n, float *y, void *stream);
+
+/* Trains the process-wide model on n (features, log ms) pairs: features and
+ * targets standardised over the set, He-initialised weights and mini-batch
+ * order from `seed`, `epochs` passes of Adam (learning rate lr, batch in
+ * [1, 128]) on the GPU; installs it.  *final_loss (may be null) = mean
+ * squared error of the last epoch, in standardised units.                 */
+wt_status wt_costmodel_train(const float *features, const float *log_ms, int32_t n, int32_t epochs,
+                             int32_t batch, float lr, uint64_t seed, float *final_loss);
+/* Predicted log ms of n launches (features as wt_costmodel_features).
+ * WT_EUNSUPPORTED without a model.                                          */
+wt_status wt_costmodel_predict(const float *features, int32_t n, float *log_ms);
+/* 1 if a model is trained or loaded.                                       */
+int32_t wt_costmodel_ready(void);
+/* Drops the model (the analytic model is used again).                      */
+wt_status wt_costmodel_reset(void);
+/* Writes / reads the model (standardisation and parameters) as text.       */
+wt_status wt_costmodel_save(const char *path);
+wt_status wt_costmodel_load(const char *path);
 
 /* Runs like wt_run, but allocates no device memory.  The paper has no
  * counterpart: this is for callers that cannot let a library call

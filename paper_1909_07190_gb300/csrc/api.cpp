@@ -88,7 +88,8 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.max_regs = q.max_regs;
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
-        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT)) fail(WT_EINVAL, "unknown flags");
+        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN)) fail(WT_EINVAL, "unknown flags");
+        r.plain = (q.flags & WT_FLAG_PLAIN) ? 1 : 0;
         r.pairs = (q.flags & WT_FLAG_NO_PAIRS) ? 0 : 1;
         r.tile_split = (q.flags & WT_FLAG_NO_TILE_SPLIT) ? 0 : 1;
       }
@@ -180,7 +181,8 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].max_regs = r.max_regs;
         params[g].chunk_rows = r.chunk_rows;
         params[g].n_buffers = r.n_buffers;
-        params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT);
+        params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT) |
+                          (r.plain ? WT_FLAG_PLAIN : 0);
       }
   });
 }

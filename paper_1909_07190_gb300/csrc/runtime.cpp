@@ -114,7 +114,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
   for (size_t gi = 0; gi < groups.size(); gi++) {
     const auto &G = groups[gi];
     GroupParams gp = group_params(p, (int)gi);
-    bool fused = p.sched.exec == WT_EXEC_FUSED;
+    bool fused = p.sched.exec == WT_EXEC_FUSED && !gp.plain;
     GroupGeom geom;
     if (fused) {
       geom = analyze_group(p, G, 4, gp.frac_reg, 4);
@@ -469,6 +469,18 @@ void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string
   }
   if (rc.runs.size() >= 256) rc.runs.clear();
   rc.runs[*key] = std::move(c);
+}
+
+const CachedRun *cached_run(const Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out) {
+  int dev = 0;
+  check_rt(cudaGetDevice(&dev), "cudaGetDevice");
+  const RunCache &rc = p.cache;
+  if (!(in && out && n_in >= 1 && n_out >= 1 && n_in <= 64 && n_out <= 64)) return nullptr;
+  if (rc.device != dev || rc.sched_version != p.sched_version || !p.ws || p.ws->device != dev ||
+      rc.ws_generation != p.ws->generation)
+    return nullptr;
+  auto it = rc.runs.find(cache_key(in, n_in, out, n_out));
+  return it == rc.runs.end() ? nullptr : &it->second;
 }
 
 void run(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out, cudaStream_t stream) {

@@ -473,7 +473,10 @@ Schedule dp_fusion(const Pipeline &p, int W, int H, int dtype, const GpuConfig &
   for (size_t g = 0; g < segs.size(); g++) {
     for (int k = segs[g].first; k < segs[g].second; k++) s.group_of_stage[k] = (int)g;
     GroupParams prm = choice[segs[g].second].prm;
-    if (!choice[segs[g].second].fused) prm = GroupParams();
+    if (!choice[segs[g].second].fused) {
+      prm = GroupParams();
+      prm.plain = 1;
+    }
     s.params.push_back(prm);
   }
   s.installed = true;
@@ -488,10 +491,8 @@ Schedule auto_schedule(const Pipeline &p, int W, int H, int dtype, int model) {
   GpuConfig cfg = gpu ? device_config(dev) : default_gb300();
   std::vector<StageStats> st = stage_stats(p, false);
   CostWeights w = current_weights();
-  if (model == WT_MODEL_LEARNED) {
-    CandidateScorer sc = learned_scorer(p, W, H, dtype, cfg, st);
-    return dp_fusion(p, W, H, dtype, cfg, st, w, &sc, 16);
-  }
+  // the learned model when one is trained or loaded, else the analytic one
+  if (model == WT_MODEL_LEARNED && costmodel_ready()) return learned_schedule(p, W, H, dtype, cfg, st, 16);
   return dp_fusion(p, W, H, dtype, cfg, st, w, nullptr, 16);
 }
 

@@ -72,6 +72,49 @@ double time_installed(Pipeline &p, const wt_image *in, int n_in, const wt_image 
   return best;
 }
 
+std::vector<LaunchTime> time_launches(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out,
+                                      cudaStream_t s, int reps) {
+  run(p, in, n_in, out, n_out, s);
+  run(p, in, n_in, out, n_out, s);
+  check_rt(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  const CachedRun *c = cached_run(p, in, n_in, out, n_out);
+  if (!c) fail(WT_EUNSUPPORTED, "launches of this run are not cached");
+  RunPlan plan = build_plan(p, in, n_in, out, n_out);
+  if (plan.launches.size() != c->functions.size()) fail(WT_EUNSUPPORTED, "run plan changed");
+  const Driver &drv = driver();
+  cudaEvent_t e0, e1;
+  check_rt(cudaEventCreate(&e0), "cudaEventCreate");
+  check_rt(cudaEventCreate(&e1), "cudaEventCreate");
+  std::vector<LaunchTime> res(c->functions.size());
+  for (size_t i = 0; i < c->functions.size(); i++) {
+    const Launch &L = plan.launches[i];
+    res[i].first_stage = L.stages.front();
+    res[i].n_stages = (int)L.stages.size();
+    res[i].fused = L.fused;
+    res[i].ms = INFINITY;
+    KernelArgs a = c->args[i];
+    void *params[] = {&a};
+    // launch i alone, `reps` times (it reads what earlier launches wrote
+    // and rewrites the same outputs): 3 samples, the minimum of the means
+    for (int t = 0; t < 3; t++) {
+      check_rt(cudaEventRecord(e0, s), "cudaEventRecord");
+      for (int r = 0; r < reps; r++)
+        check_cu(drv.launchKernel((CUfunction)c->functions[i], c->grid[3 * i], c->grid[3 * i + 1],
+                                  c->grid[3 * i + 2], (unsigned)c->block[i], 1, 1, (unsigned)c->smem[i],
+                                  (CUstream)s, params, nullptr),
+                 "cuLaunchKernel");
+      check_rt(cudaEventRecord(e1, s), "cudaEventRecord");
+      check_rt(cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float ms = 0;
+      check_rt(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+      res[i].ms = std::min(res[i].ms, (double)ms / reps);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return res;
+}
+
 void precompile(Pipeline &p, const std::vector<Schedule> &cands, const wt_image *in, int n_in, const wt_image *out,
                 int n_out, bool persistent) {
   struct Job {

@@ -57,6 +57,7 @@ struct GroupParams {
   int n_buffers = 2;
   int tile_split = 1;  // short tiles for the last round of the tile queue
   int pairs = 1;       // packed f32x2 arithmetic where taps align
+  int plain = 0;       // run the group's stages as per-stage kernels
 };
 
 struct Schedule {

@@ -83,6 +83,8 @@ void set_last_error(const std::string &msg);
 void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream);
 Workspace &workspace(Pipeline &p, int64_t bytes);
 void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string *cache_key = nullptr);
+// The cached launches of an earlier run with these images, or null.
+const CachedRun *cached_run(const Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out);
 // wt_run: reuses the cached launches when schedule and images are unchanged.
 void run(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out, cudaStream_t stream);
 

@@ -79,8 +79,9 @@ Schedule dp_fusion(const Pipeline &p, int W, int H, int dtype, const GpuConfig &
                    int max_group);
 Schedule auto_schedule(const Pipeline &p, int W, int H, int dtype, int model);
 
-// learned.cpp
-CandidateScorer learned_scorer(const Pipeline &p, int W, int H, int dtype, const GpuConfig &cfg,
-                               const std::vector<StageStats> &st);
+// learned.cpp (see wt_learned.hpp)
+bool costmodel_ready();
+Schedule learned_schedule(const Pipeline &p, int W, int H, int dtype, const GpuConfig &cfg,
+                          const std::vector<StageStats> &st, int max_group);
 
 }  // namespace wt

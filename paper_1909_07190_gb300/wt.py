@@ -99,6 +99,21 @@ SIGNATURES = [
                                 _P(ctypes.c_double)]),
     ("wt_schedule_tune", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _i32, _i32, _i32, _vp,
                                 _P(ctypes.c_double), _P(_i32)]),
+    ("wt_schedule_time_launches", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _i32, _vp,
+                                         _P(ctypes.c_double), _P(_i32), _i32, _P(_i32)]),
+    ("wt_costmodel_features", _i32, [_vp, _i32, _i32, _P(wt_group_params), _i32, _i32, _i32, _i32,
+                                     _P(ctypes.c_float)]),
+    ("wt_mlp_train_steps", _i32, [_P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float), _i32,
+                                  _P(ctypes.c_float), _P(ctypes.c_float), _i32, _P(_i32), _i32, _i32,
+                                  ctypes.c_float, ctypes.c_float, _P(ctypes.c_float), _vp]),
+    ("wt_mlp_forward", _i32, [_P(ctypes.c_float), _P(ctypes.c_float), _i32, _P(ctypes.c_float), _vp]),
+    ("wt_costmodel_train", _i32, [_P(ctypes.c_float), _P(ctypes.c_float), _i32, _i32, _i32, ctypes.c_float,
+                                  ctypes.c_uint64, _P(ctypes.c_float)]),
+    ("wt_costmodel_predict", _i32, [_P(ctypes.c_float), _i32, _P(ctypes.c_float)]),
+    ("wt_costmodel_ready", _i32, []),
+    ("wt_costmodel_reset", _i32, []),
+    ("wt_costmodel_save", _i32, [ctypes.c_char_p]),
+    ("wt_costmodel_load", _i32, [ctypes.c_char_p]),
     ("wt_prepare", _i32, [_vp, _P(wt_schedule_desc), _i32, _P(wt_image), _i32, _P(wt_image), _i32, _i32]),
     ("wt_run_static", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_check", _i32, [_vp, _vp]),
@@ -314,6 +329,18 @@ class Pipeline:
                                       stream, ctypes.byref(ms), ctypes.byref(nt)))
         return ms.value, nt.value
 
+    def time_launches(self, inputs, outputs, reps=20, stream=None):
+        """[(first_stage, n_stages, fused, ms)] per launch of one run."""
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        cap = 4 * len(self.spec["stages"]) + 4
+        ms = (ctypes.c_double * cap)()
+        info = (_i32 * (3 * cap))()
+        n = _i32()
+        check(load().wt_schedule_time_launches(self.h, ia, len(inputs), oa, len(outputs), reps, stream, ms, info,
+                                               cap, ctypes.byref(n)))
+        return [(info[3 * i], info[3 * i + 1], bool(info[3 * i + 2]), ms[i]) for i in range(n.value)]
+
     def prepare(self, schedules, inputs, outputs, batched=False):
         """Compiles the kernels of schedules [(groups, params), ...] in parallel."""
         n = len(self.spec["stages"])
@@ -501,3 +528,87 @@ def cost_weights(new=None):
     inp = (ctypes.c_double * 7)(*new) if new is not None else None
     check(lib.wt_cost_weights(inp, out))
     return list(out)
+
+
+# ------------------------------------------------------------- learned model
+
+COSTMODEL_FEATURES = 18
+MLP_PARAMS = 64 * 18 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def _fptr(a):
+    import numpy as np
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_P(ctypes.c_float))
+
+
+def costmodel_features(pipe, first, n, params=None, fused=True, width=4096, height=4096, dtype=WT_F32):
+    """Feature vector (18 floats) of one launch (see wt_costmodel_features)."""
+    import numpy as np
+    f = np.zeros(COSTMODEL_FEATURES, np.float32)
+    prm = None
+    if params is not None:
+        prm = wt_group_params()
+        d = dict(tile_h=16, warps_per_block=2, frac_reg=1.0, vec=4, max_regs=0, chunk_rows=0, n_buffers=0, flags=0)
+        d.update(params)
+        for k, v in d.items():
+            setattr(prm, k, v)
+    check(load().wt_costmodel_features(pipe.h, first, n, ctypes.byref(prm) if prm is not None else None,
+                                       int(fused), width, height, dtype, _fptr(f)))
+    return f
+
+
+def mlp_train_steps(params, m, v, t0, x, y, idx, lr, weight_decay=0.0):
+    """Runs the training kernel; params/m/v (float32, MLP_PARAMS) updated in
+    place.  idx: (steps, batch) int32.  Returns the per-step losses."""
+    import numpy as np
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    idx = np.ascontiguousarray(idx, np.int32)
+    steps, batch = idx.shape
+    loss = np.zeros(max(1, steps), np.float32)
+    check(load().wt_mlp_train_steps(_fptr(params), _fptr(m), _fptr(v), t0, _fptr(x), _fptr(y), x.shape[0],
+                                    idx.ctypes.data_as(_P(_i32)), steps, batch, lr, weight_decay, _fptr(loss),
+                                    None))
+    return loss[:steps]
+
+
+def mlp_forward(params, x):
+    import numpy as np
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.zeros(x.shape[0], np.float32)
+    check(load().wt_mlp_forward(_fptr(params), _fptr(x), x.shape[0], _fptr(y), None))
+    return y
+
+
+def costmodel_train(features, log_ms, epochs=200, batch=64, lr=1e-3, seed=1):
+    import numpy as np
+    f = np.ascontiguousarray(features, np.float32)
+    y = np.ascontiguousarray(log_ms, np.float32)
+    loss = ctypes.c_float()
+    check(load().wt_costmodel_train(_fptr(f), _fptr(y), f.shape[0], epochs, batch, lr, seed, ctypes.byref(loss)))
+    return loss.value
+
+
+def costmodel_predict(features):
+    import numpy as np
+    f = np.ascontiguousarray(features, np.float32).reshape(-1, COSTMODEL_FEATURES)
+    y = np.zeros(f.shape[0], np.float32)
+    check(load().wt_costmodel_predict(_fptr(f), f.shape[0], _fptr(y)))
+    return y
+
+
+def costmodel_ready() -> bool:
+    return bool(load().wt_costmodel_ready())
+
+
+def costmodel_reset():
+    check(load().wt_costmodel_reset())
+
+
+def costmodel_save(path):
+    check(load().wt_costmodel_save(str(path).encode()))
+
+
+def costmodel_load(path):
+    check(load().wt_costmodel_load(str(path).encode()))

@@ -134,3 +134,42 @@ def test_tma_layout_alignment(name, dtype, vec, chunk):
         assert s["ring_off"] + L["nbuf"] * s["bufb"] <= L["bar_off"]
     # lanes' 16-bit vectors sit at 8-byte offsets, 32-bit ones at 16
     assert (vec * es) % 8 == 0
+
+
+def test_costmodel_features_cpu():
+    """Features of fused groups and per-stage kernels (no GPU needed)."""
+    p = wt.Pipeline(P.harris())
+    f = wt.costmodel_features(p, 0, 11, dict(tile_h=16, warps_per_block=2, frac_reg=1.0, vec=4), True, 4096, 4096)
+    assert f.shape == (18,)
+    assert f[0] == pytest.approx(24.0)          # log2(4096 * 4096)
+    assert f[1] == 11 and f[17] == 1            # stages, fused
+    assert f[8] == pytest.approx(4.0)           # log2 tile height
+    assert f[9] == 4 and f[10] == 2 and f[11] == 1.0
+    assert f[4] == 4 and f[5] == 4              # one FP32 input and output
+    assert f[6] == 4 and f[7] == 4              # two 3x3 footprints: 2 rows/cols each side
+    assert 0 < f[14] <= 1 and f[15] > 0         # occupancy, redundant compute
+    g = wt.costmodel_features(p, 0, 1, None, False, 4096, 4096)
+    assert g[17] == 0 and g[1] == 1
+    with pytest.raises(wt.WtError):
+        wt.costmodel_features(p, 5, 10, None, False, 64, 64)
+
+
+def test_costmodel_absent_falls_back_to_analytic():
+    wt.costmodel_reset()
+    assert not wt.costmodel_ready()
+    with pytest.raises(wt.WtError):
+        wt.costmodel_predict(np.zeros((1, 18), np.float32))
+    p = wt.Pipeline(P.sharpen())
+    p.schedule_auto(512, 512, wt.WT_F32, wt.WT_MODEL_LEARNED)
+    assert p.schedule_get()["exec"] == wt.WT_EXEC_FUSED
+
+
+def test_costmodel_load_rejects_bad_files(tmp_path):
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a model\n")
+    with pytest.raises(wt.WtError):
+        wt.costmodel_load(bad)
+    with pytest.raises(wt.WtError):
+        wt.costmodel_load(tmp_path / "missing.txt")
+    with pytest.raises(wt.WtError):
+        wt.costmodel_save(tmp_path / "none.txt")   # no model to save
