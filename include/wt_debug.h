@@ -47,6 +47,16 @@ wt_status wt_debug_batch(wt_pipeline *p, int32_t launch_index, const wt_image *i
                          int32_t *tiles, int64_t tiles_cap, int64_t *n_tiles, int32_t *launch,
                          char *kname, int64_t kname_cap);
 
+/* wt_debug_kernel with the plan's workspace (intermediates between groups)
+ * placed at `workspace` (ws_cap bytes; may be null, then launches that use
+ * it fail as above).  *ws_bytes (may be null) gets the workspace size the
+ * plan needs.                                                               */
+wt_status wt_debug_kernel_ws(wt_pipeline *p, int32_t launch_index, const wt_image *inputs,
+                             int32_t n_inputs, const wt_image *outputs, int32_t n_outputs,
+                             void *workspace, int64_t ws_cap, char *src, int64_t src_cap,
+                             int64_t *src_len, void *args, int64_t args_cap, int32_t *launch,
+                             char *kname, int64_t kname_cap, int64_t *ws_bytes);
+
 /* Compiles launch `launch_index` of that run plan with NVRTC for sm_103a
  * (no GPU needed) and returns the CUBIN size; WT_ECOMPILE with the NVRTC
  * log in wt_last_error() on failure.                                       */

@@ -138,17 +138,27 @@ void push_op(std::vector<KOp> &p, int op) {
 
 // sum_k w_k tap(node, dx_k, dy_k) as a postfix program (zeros skipped).
 std::vector<KOp> weighted_sum(int node, const std::vector<std::tuple<int, int, double>> &terms) {
+  // a positive term first, so that weights -1 become subtractions and
+  // weights 1 additions (no multiplies)
+  std::vector<std::tuple<int, int, double>> ts;
+  for (auto &t : terms)
+    if (std::get<2>(t) > 0) ts.push_back(t);
+  for (auto &t : terms)
+    if (std::get<2>(t) < 0) ts.push_back(t);
   std::vector<KOp> p;
   bool first = true;
-  for (auto &t : terms) {
+  for (auto &t : ts) {
     double w = std::get<2>(t);
-    if (w == 0) continue;
     KOp tap;
     tap.op = WT_OP_TAP;
     tap.node = node;
     tap.dx = std::get<0>(t);
     tap.dy = std::get<1>(t);
     p.push_back(tap);
+    if (!first && w == -1.0) {
+      push_op(p, WT_OP_SUB);
+      continue;
+    }
     if (w != 1.0) {
       push_const(p, w);
       push_op(p, WT_OP_MUL);
@@ -202,6 +212,14 @@ int try_split(GroupGeom &g, int ni) {
     for (int i = 0; i < nx; i++)
       if (std::fabs(W[(size_t)j * nx + i] - u[j] * v[i]) > 1e-9 * wmax) return -1;  // rank > 1
   if (nv + nu >= nnz) return -1;  // no saving
+  // the row pass gets the smallest weights that are whole multiples of its
+  // smallest nonzero weight (integer taps: additions and subtractions), the
+  // column pass the scale
+  double vmin = INFINITY;
+  for (int i = 0; i < nx; i++)
+    if (v[i] != 0) vmin = std::min(vmin, std::fabs(v[i]));
+  for (int i = 0; i < nx; i++) v[i] /= vmin;
+  for (int j = 0; j < ny; j++) u[j] *= vmin;
   Node h;
   h.synthetic = true;
   h.id = g.nodes[ni].id;

@@ -337,16 +337,18 @@ int32_t wt_launches_per_run(const wt_pipeline *p) {
 
 int64_t wt_debug_args_size(void) { return (int64_t)sizeof(wt::KernelArgs); }
 
-wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, int32_t n_inputs,
-                          const wt_image *outputs, int32_t n_outputs, char *src, int64_t src_cap,
-                          int64_t *src_len, void *args, int64_t args_cap, int32_t *launch, char *kname,
-                          int64_t kname_cap) {
+wt_status wt_debug_kernel_ws(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, int32_t n_inputs,
+                             const wt_image *outputs, int32_t n_outputs, void *workspace, int64_t ws_cap,
+                             char *src, int64_t src_cap, int64_t *src_len, void *args, int64_t args_cap,
+                             int32_t *launch, char *kname, int64_t kname_cap, int64_t *ws_bytes) {
   return guard([&] {
     if (!p) wt::fail(WT_EINVAL, "null pipeline");
     std::lock_guard<std::mutex> lk(p->mu);
     wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
     if (launch_index < 0 || launch_index >= (int)plan.launches.size()) wt::fail(WT_EINVAL, "launch index");
     const wt::Launch &L = plan.launches[launch_index];
+    if (ws_bytes) *ws_bytes = plan.ws_bytes;
+    if (workspace && ws_cap < plan.ws_bytes) wt::fail(WT_EINVAL, "workspace buffer too small");
     std::string s = wt::launch_source(*p, L);
     if (src_len) *src_len = (int64_t)s.size();
     if (src && src_cap > 0) {
@@ -357,7 +359,7 @@ wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *
     if (args) {
       if (args_cap < (int64_t)sizeof(wt::KernelArgs)) wt::fail(WT_EINVAL, "args buffer too small");
       wt::KernelArgs a;
-      wt::fill_args(*p, plan, L, nullptr, a, false);
+      wt::fill_args(*p, plan, L, (char *)workspace, a, false);
       // as on the GPU with few resident warps: exercises both tile heights
       if (L.fused) wt::split_tiles(L, a, 4 * L.key.nw);
       memcpy(args, &a, sizeof a);
@@ -378,6 +380,14 @@ wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *
       kname[n] = 0;
     }
   });
+}
+
+wt_status wt_debug_kernel(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, int32_t n_inputs,
+                          const wt_image *outputs, int32_t n_outputs, char *src, int64_t src_cap,
+                          int64_t *src_len, void *args, int64_t args_cap, int32_t *launch, char *kname,
+                          int64_t kname_cap) {
+  return wt_debug_kernel_ws(p, launch_index, inputs, n_inputs, outputs, n_outputs, nullptr, 0, src, src_cap,
+                            src_len, args, args_cap, launch, kname, kname_cap, nullptr);
 }
 
 wt_status wt_debug_batch(wt_pipeline *p, int32_t launch_index, const wt_image *inputs, const wt_image *outputs,

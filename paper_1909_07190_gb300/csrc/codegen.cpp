@@ -210,8 +210,13 @@ void emit_shift(Ctx &c, int ni) {
 std::string ring_row(int s, const std::string &ri) {
   std::string S = std::to_string(s);
   // chunk c of the current tile sits in buffer (cbase + c) % NB, where cbase
-  // counts the chunks of the warp's earlier tiles
-  return "lp" + S + " + ((cbase + " + ri + " / CH) % NB) * BUFB" + S + " + (" + ri + " % CH) * ROWB" + S;
+  // counts the chunks of the warp's earlier tiles.  Rows above the tile's
+  // first row (ri down to -(window - 1), read only for rows that are never
+  // stored) map into the ring too: ri + NB * CH selects the same buffer and
+  // row for ri >= 0 and a stale row of the ring for negative ri, so every
+  // address stays inside the warp's staging buffers.
+  const std::string rr = "(" + ri + " + NB * CH)";
+  return "lp" + S + " + ((cbase + " + rr + " / CH) % NB) * BUFB" + S + " + (" + rr + " % CH) * ROWB" + S;
 }
 
 // Row of a register-resident source, loaded from the TMA ring.
@@ -507,7 +512,13 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     }
     o << "} else {\n";
   }
-  if (c.key.pairs) {
+  // packed pairs for nodes whose taps all read the producer's own element
+  // pairs (dx = 0): a pair shifted by one column would have to be gathered
+  // into an aligned register pair first
+  bool pairs = c.key.pairs;
+  for (const KOp &op : n.prog)
+    if (op.op == WT_OP_TAP && op.dx != 0) pairs = false;
+  if (pairs) {
     int tmpid = 0;
     o << "{\n";
     for (int e = 0; e < V; e += 2) emit_pair(c, ni, e, u, v, tmpid);

@@ -125,6 +125,8 @@ SIGNATURES = [
                                _P(_i64), _vp, _i64, _P(_i32), ctypes.c_char_p, _i64]),
     ("wt_debug_batch", _i32, [_vp, _i32, _P(wt_image), _P(wt_image), _i32, ctypes.c_char_p, _i64, _P(_i64),
                               _vp, _vp, _i64, _P(_i32), _i64, _P(_i64), _P(_i32), ctypes.c_char_p, _i64]),
+    ("wt_debug_kernel_ws", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _vp, _i64, ctypes.c_char_p,
+                                  _i64, _P(_i64), _vp, _i64, _P(_i32), ctypes.c_char_p, _i64, _P(_i64)]),
     ("wt_debug_compile", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i64)]),
     ("wt_debug_layout", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
@@ -367,22 +369,35 @@ class Pipeline:
         check(load().wt_check(self.h, stream))
 
     # -- introspection
-    def debug_kernel(self, index, inputs, outputs):
+    def debug_kernel(self, index, inputs, outputs, workspace=None):
+        """workspace: (pointer, bytes) of a host buffer for the plan's
+        intermediates, or None."""
         lib = load()
         ia = (wt_image * len(inputs))(*inputs)
         oa = (wt_image * len(outputs))(*outputs)
-        n = _i64()
-        check(lib.wt_debug_kernel(self.h, index, ia, len(inputs), oa, len(outputs), None, 0,
-                                  ctypes.byref(n), None, 0, None, None, 0))
+        n, wsb = _i64(), _i64()
+        wp, wc = workspace if workspace is not None else (None, 0)
+        check(lib.wt_debug_kernel_ws(self.h, index, ia, len(inputs), oa, len(outputs), wp, wc, None, 0,
+                                     ctypes.byref(n), None, 0, None, None, 0, ctypes.byref(wsb)))
         src = ctypes.create_string_buffer(n.value + 1)
         args = ctypes.create_string_buffer(int(lib.wt_debug_args_size()))
         launch = (_i32 * 8)()
         kname = ctypes.create_string_buffer(128)
-        check(lib.wt_debug_kernel(self.h, index, ia, len(inputs), oa, len(outputs), src, n.value + 1,
-                                  None, args, len(args), launch, kname, 128))
+        check(lib.wt_debug_kernel_ws(self.h, index, ia, len(inputs), oa, len(outputs), wp, wc, src, n.value + 1,
+                                     None, args, len(args), launch, kname, 128, None))
         return {"source": src.value.decode(), "args": args.raw, "grid": tuple(launch[0:3]),
                 "block": launch[3], "smem": launch[4], "fused": bool(launch[5]),
-                "n_launches": launch[6], "unroll": launch[7], "name": kname.value.decode()}
+                "n_launches": launch[6], "unroll": launch[7], "name": kname.value.decode(),
+                "ws_bytes": wsb.value}
+
+    def debug_workspace_bytes(self, inputs, outputs) -> int:
+        lib = load()
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        wsb = _i64()
+        check(lib.wt_debug_kernel_ws(self.h, 0, ia, len(inputs), oa, len(outputs), None, 0, None, 0, None, None, 0,
+                                     None, None, 0, ctypes.byref(wsb)))
+        return wsb.value
 
     def debug_batch(self, index, inputs, outputs, n_images):
         """inputs/outputs: flat lists, image-major (n_images * n_inputs)."""

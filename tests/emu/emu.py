@@ -84,13 +84,24 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
     return lib
 
 
-def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None):
+def _register(lib, images, workspace=None):
+    """The global buffers the kernel may touch (for the memory checker)."""
+    lib.wt_emu_register.argtypes = [ctypes.c_void_p, ctypes.c_long]
+    lib.wt_emu_clear_ranges()
+    for x in images:
+        lib.wt_emu_register(x.buf.ctypes.data, x.buf.nbytes)
+    if workspace is not None and workspace.nbytes:
+        lib.wt_emu_register(workspace.ctypes.data, workspace.nbytes)
+
+
+def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None, workspace=None):
     """inputs/outputs: HostImage lists.  Runs launch `index` of the plan
     (with at most `max_blocks` blocks: persistent warps then take several
     tiles each)."""
     ii = [x.image() for x in inputs]
     oo = [x.image() for x in outputs]
-    d = pipe.debug_kernel(index, ii, oo)
+    ws = None if workspace is None else (workspace.ctypes.data, workspace.nbytes)
+    d = pipe.debug_kernel(index, ii, oo, ws)
     lib = _compile(d["source"], d["name"])
     args = bytearray(d["args"])
     err = np.zeros(16, np.int32)
@@ -107,6 +118,7 @@ def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None):
     gx, gy, gz = d["grid"]
     if max_blocks is not None and d["fused"]:
         gx = min(gx, max_blocks)
+    _register(lib, inputs + outputs, workspace)
     rc = lib.wt_emu_run(kfn, ctypes.addressof(abuf), gx, gy, gz, d["block"], d["smem"], msg, 512)
     if rc != 0:
         raise RuntimeError("emulated kernel failed: " + msg.value.decode())
@@ -139,6 +151,7 @@ def run_batch(pipe: "wt.Pipeline", index: int, inputs, outputs, n_images, max_bl
                                ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
     msg = ctypes.create_string_buffer(512)
     gx = d["grid"][0] if max_blocks is None else min(d["grid"][0], max_blocks)
+    _register(lib, inputs + outputs)
     rc = lib.wt_emu_run(kfn, ctypes.addressof(abuf), gx, 1, 1, d["block"], d["smem"], msg, 512)
     if rc != 0:
         raise RuntimeError("emulated kernel failed: " + msg.value.decode())

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "wt_emu.h"
 
@@ -92,7 +93,27 @@ EmuDim *wt_emu_block_idx() { return &g_bidx; }
 EmuDim *wt_emu_block_dim() { return &g_bdim; }
 EmuDim *wt_emu_grid_dim() { return &g_gdim; }
 unsigned char *wt_emu_smem() { return wt_emu_smem_array; }
-void wt_emu_fail(const char *msg) { g_fail = msg; }
+void wt_emu_fail(const char *msg) {
+  if (g_fail.empty()) g_fail = msg;
+}
+
+// Memory checker: every access of the generated code's load/store helpers
+// must fall inside the launch's shared-memory size or a registered global
+// buffer (the images of the run).
+static std::vector<std::pair<const unsigned char *, size_t>> g_ranges;
+static size_t g_smem_size = 0;
+void wt_emu_register(const void *p, long bytes) { g_ranges.push_back({(const unsigned char *)p, (size_t)bytes}); }
+void wt_emu_clear_ranges() { g_ranges.clear(); }
+void wt_emu_check(const void *p, long bytes, const char *what) {
+  const unsigned char *a = (const unsigned char *)p;
+  if (a >= wt_emu_smem_array && a + bytes <= wt_emu_smem_array + g_smem_size) return;
+  for (auto &r : g_ranges)
+    if (a >= r.first && a + bytes <= r.first + r.second) return;
+  char m[160];
+  snprintf(m, sizeof m, "out-of-bounds %s of %ld bytes (shared offset %ld)", what, bytes,
+           (long)(a - wt_emu_smem_array));
+  wt_emu_fail(m);
+}
 
 float wt_emu_shfl(float v, int arg, int kind) {
   int lane = (int)(g_lanes[g_cur].tid.x & 31);
@@ -120,6 +141,7 @@ void wt_emu_yield() { swapcontext(&g_lanes[g_cur].ctx, &g_main); }
 // Runs the whole grid, one warp at a time.  Returns 0, or -1 with a message.
 int wt_emu_run(void *kernel, const void *args, int gx, int gy, int gz, int block, int smem, char *msg,
                int msg_cap) {
+  g_smem_size = (size_t)smem;
   g_kernel = (void (*)(WtArgs))kernel;
   g_args = (const WtArgs *)args;
   g_fail.clear();

@@ -75,6 +75,7 @@ int wt_emu_all(int pred);
 void wt_emu_syncwarp();
 unsigned char *wt_emu_smem();
 void wt_emu_fail(const char *msg);
+void wt_emu_check(const void *p, long bytes, const char *what);
 void wt_emu_yield();
 }
 #define threadIdx (*wt_emu_thread_idx())
@@ -107,7 +108,10 @@ static inline unsigned char *wt_emu_sptr(wt_u32 a) { return wt_emu_smem() + a; }
 
 // ------------------------------------------------------ mbarrier / TMA
 // An emulated mbarrier keeps its completed-phase count in the first 4 bytes.
-static inline void wt_mbar_init(wt_u32 bar, wt_u32) { memset(wt_emu_sptr(bar), 0, 8); }
+static inline void wt_mbar_init(wt_u32 bar, wt_u32) {
+  wt_emu_check(wt_emu_sptr(bar), 8, "mbarrier");
+  memset(wt_emu_sptr(bar), 0, 8);
+}
 static inline void wt_fence_mbar_init() {}
 static inline void wt_fence_proxy_async() {}
 static inline void wt_tmap_acquire(const void *) {}
@@ -134,10 +138,14 @@ static inline int wt_mbar_wait(wt_u32 bar, wt_u32 parity, int *err) {
   atomicExch(err, WT_ERR_TIMEOUT);
   return 0;
 }
-static inline void wt_tma_load_3d(wt_u32 dst, const WtTmap *map, int x, int y, int z, wt_u32) {
+static inline void wt_tma_load_3d(wt_u32 dst, const WtTmap *map, int x, int y, int z, wt_u32 bar) {
   EmuTmap t;
   memcpy(&t, map, sizeof t);
   unsigned char *d = wt_emu_sptr(dst);
+  wt_emu_check(d, (long)t.boxw * t.boxh * t.esz, "TMA box");
+  wt_emu_check(wt_emu_sptr(bar), 8, "mbarrier");
+  if (dst % 128 != 0) wt_emu_fail("TMA destination not 128-byte aligned");
+  if (((long)x * t.esz) % 16 != 0) wt_emu_fail("TMA x coordinate not 16-byte aligned");
   for (int r = 0; r < t.boxh; r++)
     for (int c = 0; c < t.boxw; c++) {
       int gx = x + c, gy = y + r;
@@ -182,38 +190,44 @@ static inline wt_u16 wt_f2b(float f) {
 
 // ------------------------------------------------------ loads / stores
 static inline void wt_ld4_f32(const void *p, float &a, float &b, float &c, float &d) {
+  wt_emu_check(p, 16, "load");
   float v[4];
   memcpy(v, p, 16);
   a = v[0]; b = v[1]; c = v[2]; d = v[3];
 }
 static inline void wt_ld4_f16(const void *p, float &a, float &b, float &c, float &d) {
+  wt_emu_check(p, 8, "load");
   wt_u16 v[4];
   memcpy(v, p, 8);
   a = wt_h2f(v[0]); b = wt_h2f(v[1]); c = wt_h2f(v[2]); d = wt_h2f(v[3]);
 }
 static inline void wt_ld4_bf16(const void *p, float &a, float &b, float &c, float &d) {
+  wt_emu_check(p, 8, "load");
   wt_u16 v[4];
   memcpy(v, p, 8);
   a = wt_b2f(v[0]); b = wt_b2f(v[1]); c = wt_b2f(v[2]); d = wt_b2f(v[3]);
 }
 static inline void wt_st4_f32(void *p, float a, float b, float c, float d) {
+  wt_emu_check(p, 16, "store");
   float v[4] = {a, b, c, d};
   memcpy(p, v, 16);
 }
 static inline void wt_st4_f16(void *p, float a, float b, float c, float d) {
+  wt_emu_check(p, 8, "store");
   wt_u16 v[4] = {wt_f2h(a), wt_f2h(b), wt_f2h(c), wt_f2h(d)};
   memcpy(p, v, 8);
 }
 static inline void wt_st4_bf16(void *p, float a, float b, float c, float d) {
+  wt_emu_check(p, 8, "store");
   wt_u16 v[4] = {wt_f2b(a), wt_f2b(b), wt_f2b(c), wt_f2b(d)};
   memcpy(p, v, 8);
 }
-static inline float wt_ld1_f32(const void *p) { float v; memcpy(&v, p, 4); return v; }
-static inline float wt_ld1_f16(const void *p) { wt_u16 v; memcpy(&v, p, 2); return wt_h2f(v); }
-static inline float wt_ld1_bf16(const void *p) { wt_u16 v; memcpy(&v, p, 2); return wt_b2f(v); }
-static inline void wt_st1_f32(void *p, float v) { memcpy(p, &v, 4); }
-static inline void wt_st1_f16(void *p, float v) { wt_u16 h = wt_f2h(v); memcpy(p, &h, 2); }
-static inline void wt_st1_bf16(void *p, float v) { wt_u16 h = wt_f2b(v); memcpy(p, &h, 2); }
+static inline float wt_ld1_f32(const void *p) { wt_emu_check(p, 4, "load"); float v; memcpy(&v, p, 4); return v; }
+static inline float wt_ld1_f16(const void *p) { wt_emu_check(p, 2, "load"); wt_u16 v; memcpy(&v, p, 2); return wt_h2f(v); }
+static inline float wt_ld1_bf16(const void *p) { wt_emu_check(p, 2, "load"); wt_u16 v; memcpy(&v, p, 2); return wt_b2f(v); }
+static inline void wt_st1_f32(void *p, float v) { wt_emu_check(p, 4, "store"); memcpy(p, &v, 4); }
+static inline void wt_st1_f16(void *p, float v) { wt_emu_check(p, 2, "store"); wt_u16 h = wt_f2h(v); memcpy(p, &h, 2); }
+static inline void wt_st1_bf16(void *p, float v) { wt_emu_check(p, 2, "store"); wt_u16 h = wt_f2b(v); memcpy(p, &h, 2); }
 static inline int wt_clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ------------------------------------------------- packed FP32 pairs

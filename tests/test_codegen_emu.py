@@ -29,10 +29,14 @@ def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mod
     for sid in spec["outputs"]:
         _, w, h, c = shapes[sid]
         outs.append(emu.HostImage(c, h, w, dtype))
-    d = emu.run(p, launch, ins, outs, max_blocks)
+    # intermediates between groups: a poisoned host workspace
+    wsb = p.debug_workspace_bytes([x.image() for x in ins], [x.image() for x in outs])
+    ws = np.full(max(wsb, 16), 0xA5, np.uint8)
+    d = emu.run(p, launch, ins, outs, max_blocks, ws)
     for i in range(1, d["n_launches"]):
-        emu.run(p, i, ins, outs, max_blocks)
-    assert d["fused"] == (exec_mode == wt.WT_EXEC_FUSED)
+        emu.run(p, i, ins, outs, max_blocks, ws)
+    if exec_mode == wt.WT_EXEC_FUSED and d["n_launches"] == 1:
+        assert d["fused"]
     for o in outs:
         assert o.padding_intact(), "kernel wrote outside the image"
     name = {wt.WT_F32: "f32", wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
@@ -185,3 +189,16 @@ def test_fused_multichannel_group():
     got, d = run_emulated(spec, [A, M], params=[dict(tile_h=8, warps_per_block=2)])
     assert d["fused"]
     assert np.abs(got[0] - oracle_of(spec, [A, M])[0]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name,groups", [("sharpen", [0, 1, 2]), ("sharpen", [0, 0, 1]),
+                                         ("harris", list(range(11))), ("harris", [0] * 5 + [1] * 6)])
+@pytest.mark.parametrize("tile_h,frac", [(4, 0.0), (4, 1.0), (16, 0.0), (16, 1.0)])
+def test_fused_multi_group_schedules(name, groups, tile_h, frac):
+    """Groups that read and write intermediates in the workspace, with short
+    tiles and all-shared or all-register windows (every access checked)."""
+    spec = P.by_name(name)
+    img = rnd(70 + tile_h, 300, 41)
+    ng = max(groups) + 1
+    got, _ = run_emulated(spec, [img], groups=groups, params=[dict(tile_h=tile_h, frac_reg=frac)] * ng)
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
