@@ -454,8 +454,20 @@ void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
   int dt = c.key.dst_dtypes.at(n.dst_index);
   int esz = elem_bytes(dt);
   o << "{\n";
+  if (!safe) {
+    // per-tile row base and lane predicate: the conditional part is the
+    // store alone
+    std::string D = std::to_string(n.dst_index);
+    o << "if (r >= y0 && r < y0 + T" << (n.channels == 1 && c.g.channels > 1 ? " && ch == 0" : "") << ") {\n";
+    o << "unsigned char *op_ = ob" << D << " + (wt_i64)r * ia.dst[" << D << "].pitch;\n";
+    o << "if (st_lane) {\n";
+    for (int b = 0; b < V; b += 4)
+      o << "wt_st4_" << tname(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", " << v[b + 2]
+        << ", " << v[b + 3] << ");\n";
+    o << "} } }\n";
+    return;
+  }
   if (safe) o << "if (r >= y0 && r < y0 + T && r < H)\n";
-  else o << "if (r >= y0 && r < y0 + T)\n";
   if (n.channels == 1 && c.g.channels > 1) o << "if (ch == 0)\n";
   o << "{ const int x = xs + lane * " << V << ";\n";
   o << "if (lane >= " << c.L.lpad / V << " && lane < " << 32 - c.L.rpad / V << ") {\n";
@@ -682,6 +694,16 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   o << "const int nsteps = " << HT << " + T + " << L.nsx << ";\n";
   o << "const int nsrc = " << HT << " + T + " << HB << ";\n";
   o << "const int nrows = min(nsrc, H - y_top);\n";
+  o << "const bool st_lane = lane >= " << L.lpad / V << " && lane < " << 32 - L.rpad / V << ";\n";
+  o << "(void)st_lane;\n";
+  for (const Node &n : g.nodes)
+    if (n.is_liveout) {
+      std::string D = std::to_string(n.dst_index);
+      const int esz = elem_bytes(key.dst_dtypes.at(n.dst_index));
+      o << "unsigned char *ob" << D << " = (unsigned char *)ia.dst[" << D << "].ptr + (wt_i64)"
+        << (n.channels > 1 ? "ch" : "0") << " * ia.dst[" << D << "].plane + (wt_i64)(xs + lane * " << V << ") * " << esz
+        << ";\n(void)ob" << D << ";\n";
+    }
   o << "const bool border = xs < 0 || xs + " << 32 * V << " > W || y_top < 0 || y0 + T + " << HB
     << " > H;\n";
   for (int s = 0; s < n_src; s++) {
@@ -720,20 +742,26 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // Steady-state steps of interior tiles run the guard-free body; all
   // other steps run the guarded body (both unrolled over U phases so that
   // register windows rotate by renaming).
+  // chunk bookkeeping by counters (the block's row in its chunk, kc_, and
+  // the chunk, kch_; chunks are a multiple of U rows)
+  o << "int kc_ = 0, kch_ = 0;\n";
   o << "for (int kb = 0; kb < nsteps; kb += U) {\n";
   // TMA bookkeeping once per block: wait for the chunk this block starts,
   // refill the buffer whose rows no step reads any more.
-  o << "{ const int kc_ = kb % CH;\n"
-       "if (kc_ == 0) { const int c_ = kb / CH; if (c_ * CH < nrows) {"
-       " const int gc_ = cbase + c_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
-       " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = c_; goto wt_fail; } } }\n"
-       "if (kc_ == ISSUE) { const int c_ = kb / CH + NB - 1; if (c_ * CH < nrows) issue_chunk(c_); } }\n";
+  o << "if (kc_ == 0 && kch_ * CH < nrows) {"
+       " const int gc_ = cbase + kch_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
+       " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = kch_; goto wt_fail; } }\n"
+       "if (kc_ == ISSUE) { const int c_ = kch_ + NB - 1; if (c_ * CH < nrows) issue_chunk(c_); }\n";
   o << "if (!border) {\n";
-  for (int s = 0; s < n_src; s++) o << "const unsigned char *rp" << s << " = " << ring_row(s, "kb") << ";\n";
+  for (int s = 0; s < n_src; s++)
+    o << "const unsigned char *rp" << s << " = lp" << s << " + ((cbase + kch_) % NB) * BUFB" << s << " + kc_ * ROWB"
+      << s << ";\n";
   for (int u = 0; u < c.U; u++) emit_step(c, false, u);
   o << "} else {\n";
   for (int u = 0; u < c.U; u++) emit_step(c, true, u);
-  o << "}\n}\n";
+  o << "}\n";
+  o << "kc_ += U;\nif (kc_ == CH) { kc_ = 0; kch_++; }\n";
+  o << "}\n";
   o << "wt_tile_end:;\n";
   o << "cbase += (nrows + CH - 1) / CH;\n";
   o << "}\n";  // tile loop

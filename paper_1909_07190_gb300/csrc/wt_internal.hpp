@@ -48,7 +48,7 @@ struct Stage {
 };
 
 struct GroupParams {
-  int tile_h = 16;
+  int tile_h = 14;
   int warps_per_block = 2;
   float frac_reg = 1.f;
   int vec = 0;

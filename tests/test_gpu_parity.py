@@ -197,3 +197,16 @@ def test_error_word_clear_after_runs():
     img = rnd(19, 64, 64)
     _, p = run_pipe(spec, [img])
     p.check(stream())
+
+
+@pytest.mark.parametrize("name,groups", [("sharpen", [0, 1, 2]), ("harris", list(range(11))),
+                                         ("harris", [0] * 5 + [1] * 6)])
+@pytest.mark.parametrize("tile_h,frac", [(4, 0.0), (16, 0.5), (16, 1.0)])
+def test_multi_group_schedules(name, groups, tile_h, frac):
+    """Groups exchanging intermediates through the workspace, with
+    shared-memory source windows (fracReg 0) and short tiles."""
+    spec = P.by_name(name)
+    img = rnd(300 + tile_h, 1000, 333)
+    ng = max(groups) + 1
+    got = run_pipe(spec, [img], groups=groups, params=[dict(tile_h=tile_h, frac_reg=frac)] * ng)[0][0]
+    assert np.abs(got - oracle_out(spec, [img])[0]).max() <= TOL["f32"]
