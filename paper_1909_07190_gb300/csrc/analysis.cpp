@@ -218,6 +218,10 @@ int try_split(GroupGeom &g, int ni) {
   double vmin = INFINITY;
   for (int i = 0; i < nx; i++)
     if (v[i] != 0) vmin = std::min(vmin, std::fabs(v[i]));
+  // mostly positive row weights (their sign moves to the column pass)
+  double vsum = 0;
+  for (int i = 0; i < nx; i++) vsum += v[i];
+  if (vsum < 0) vmin = -vmin;
   for (int i = 0; i < nx; i++) v[i] /= vmin;
   for (int j = 0; j < ny; j++) u[j] *= vmin;
   Node h;

@@ -540,7 +540,14 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
   }
   if (safe) {
     o << "}\n";
-    emit_xfix(c, v);
+    // Columns outside the image must hold the edge column's value.  A node
+    // computed from edge-replicated producers by taps without an x offset
+    // (pointwise or vertical) and without the column parity is replicated
+    // already; only the others are fixed up.
+    bool xdep = false;
+    for (const KOp &op : n.prog)
+      if ((op.op == WT_OP_TAP && op.dx != 0) || op.op == WT_OP_XPAR) xdep = true;
+    if (xdep) emit_xfix(c, v);
   }
   if (n.in_smem) {
     o << "{ const int sl = ((k % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
