@@ -46,6 +46,8 @@ WORKLOADS = {
     "sharpen": ("sharpen", 2048, 2048, "f32", I.SEED_BASE + 1),
     # 512 images, sides uniform in [200, 4096] (sizes from seed 190907193)
     "harris_batch": ("harris", 0, 0, "f16", I.SEED_BASE + 3),
+    # two 8192x8192x3 images and a smooth mask, 6-level pyramids (36 stages)
+    "blend": ("blend", 8192, 8192, "bf16", I.SEED_BASE + 5),
 }
 BATCH_IMAGES = 512
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -136,6 +138,24 @@ def cpu_oracle_rate(spec, img, budget_s):
     return px / dt / 1e6, O.num_threads(), n, dt
 
 
+def cpu_blend_rate(dts, budget_s, w=1024, h=1024):
+    """Mpx/s of the FP64 oracle's blend on a bounded sample: repeated
+    1024x1024x3 blends (the same 36 stages)."""
+    from oracle import oracle as O
+    spec = P.blend()
+    ins = [I.round_to(I.uniform_image(I.SEED_BASE + 5, w, h, 3), dts).astype(np.float64),
+           I.round_to(I.uniform_image(I.SEED_BASE + 1005, w, h, 3), dts).astype(np.float64),
+           I.round_to(I.smooth_mask(I.SEED_BASE + 2005, w, h), dts).astype(np.float64)]
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.evaluate(spec["stages"], ins, spec["outputs"])
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return n * w * h / dt / 1e6, O.num_threads(), n, dt, "%d full %dx%dx3 blends, %.1f s" % (n, w, h, dt)
+
+
 def batch_sizes():
     return I.batch_sizes(I.SEED_BASE + 3, BATCH_IMAGES, 200, 4096)
 
@@ -148,6 +168,29 @@ def run_reference(args, rank):
         return
     name, W, H, dt, seed = WORKLOADS[args.workload]
     spec = P.by_name(name)
+    if name == "blend":
+        # bounded sample: one 1024x1024x3 blend per step
+        from oracle import oracle as O
+        for _ in range(args.warmup):
+            cpu_blend_rate(dt, 0.0)
+        px, t0 = 0, time.perf_counter()
+        cores = O.num_threads()
+        for _ in range(args.steps):
+            cpu_blend_rate(dt, 0.0)
+            px += 1024 * 1024
+        total = time.perf_counter() - t0
+        value = px / total / 1e6
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixels/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H,
+                           "channels": 3, "storage": dt},
+                "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
+                                 "sample": "one 1024x1024x3 blend per step"},
+                "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "harris_batch":
         sizes = batch_sizes()
         imgs = [I.round_to(I.uniform_image(seed * 1000 + i, w, h)[0], dt) for i, (w, h) in
@@ -221,6 +264,70 @@ class Single:
 
     def cpu_sample(self, dts):
         return I.round_to(self.img, dts)
+
+
+class Blend:
+    """The multi-scale blend: A, B (8192x8192x3) and the mask in, the 3-channel
+    blend out, BF16; three buffer sets (1.3 GB each, far beyond L2).  A and B
+    are drawn on the device with the host generator's stream, the mask on
+    the host.  Fused schedule: one group per pyramid level."""
+
+    def __init__(self, wt, torch, spec, W, H, dtype, seed):
+        from paper_1909_07190_gb300 import inputs_torch as IT
+        self.wt, self.torch = wt, torch
+        self.W, self.H, self.dtype = W, H, dtype
+        self.esz = 4 if dtype == wt.WT_F32 else 2
+        tdt = {wt.WT_F32: torch.float32, wt.WT_F16: torch.float16, wt.WT_BF16: torch.bfloat16}[dtype]
+        self.seeds = (seed, seed + 1000, seed + 2000)
+        self.mask = I.smooth_mask(self.seeds[2], W, H)
+        self.nsets = 3
+        self.ins, self.outs = [], []
+        for _ in range(self.nsets):
+            a = wt.DeviceImage(3, H, W, dtype)
+            a.view().copy_(IT.uniform_image(self.seeds[0], W, H, 3).to(tdt))
+            b = wt.DeviceImage(3, H, W, dtype)
+            b.view().copy_(IT.uniform_image(self.seeds[1], W, H, 3).to(tdt))
+            m = wt.DeviceImage(1, H, W, dtype)
+            m.view().copy_(torch.from_numpy(self.mask).to(tdt))
+            self.ins.append([a, b, m])
+            self.outs.append(wt.DeviceImage(3, H, W, dtype))
+        self.px = W * H
+        self.alg_bytes = (3 + 3 + 1 + 3) * W * H * self.esz
+        self.l2_note = "rotating %d input/output sets (%.0f MB) > 3x L2" % (self.nsets, self.alg_bytes / 1e6)
+
+    def schedule(self, fused, plain):
+        fused.schedule(groups=P.blend_groups())
+
+    def run(self, pipe, i, sp):
+        k = i % self.nsets
+        pipe.run([x.image() for x in self.ins[k]], [self.outs[k].image()], sp)
+
+    def tune(self, pipe, sp):
+        return pipe.schedule_tune([x.image() for x in self.ins[0]], [self.outs[0].image()], 0, 4, 5, sp)
+
+    def kernel_name(self, pipe):
+        # the largest launch: the finest level's group (the last one)
+        d = pipe.debug_kernel(pipe.launches_per_run() - 1, [x.image() for x in self.ins[0]],
+                              [self.outs[0].image()])
+        return d["name"]
+
+    def e2e(self, pipe, sp, warmup, steps):
+        wt, torch = self.wt, self.torch
+        hin = [wt.DeviceImage(x.c, self.H, self.W, self.dtype, device="cpu", pin_host=True) for x in self.ins[0]]
+        for h, x in zip(hin, self.ins[0]):
+            h.view().copy_(x.view().cpu())
+        hout = wt.DeviceImage(3, self.H, self.W, self.dtype, device="cpu", pin_host=True)
+        for _ in range(warmup):
+            pipe.run_host([h.image() for h in hin], [hout.image()], sp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            pipe.run_host([h.image() for h in hin], [hout.image()], sp)
+        nb = sum(h.t.numel() * h.t.element_size() for h in hin)
+        return self.px * steps / (time.perf_counter() - t0) / 1e6, nb, hout.t.numel() * hout.t.element_size()
+
+    def cpu_sample(self, dts):
+        return None
 
 
 class Batch:
@@ -298,14 +405,24 @@ def run_ours(args, rank, world, local):
     dtype = wt.DTYPES[dts]
     spec = P.by_name(name)
     batched = args.workload == "harris_batch"
-    work = Batch(wt, torch, spec, dtype, seed + 7919 * rank) if batched else \
-        Single(wt, torch, spec, W, H, dtype, seed + rank, local)
+    if batched:
+        work = Batch(wt, torch, spec, dtype, seed + 7919 * rank)
+    elif name == "blend":
+        work = Blend(wt, torch, spec, W, H, dtype, seed + 7919 * rank)
+    else:
+        work = Single(wt, torch, spec, W, H, dtype, seed + rank, local)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
     fused = wt.Pipeline(spec)
+    if hasattr(work, "schedule"):
+        work.schedule(fused, None)
     if args.params:
-        fused.schedule(params=json.loads(args.params))
+        prm = json.loads(args.params)
+        if hasattr(work, "schedule"):
+            fused.schedule(groups=P.blend_groups(), params=[prm] * 10)
+        else:
+            fused.schedule(params=prm)
     tune_t0 = time.perf_counter()
     tune = args.tune == "on" or (args.tune == "auto" and batched)
     tuning = None
@@ -414,10 +531,13 @@ def run_ours(args, rank, world, local):
     if batched:
         line["config"]["images"] = len(work.sizes)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        img = work.cpu_sample(dts)
-        r, cores, n, dt = cpu_oracle_rate(spec, img, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d full %dx%d images, %.1f s" % (n, img.shape[-1], img.shape[-2], dt)}
+        if name == "blend":
+            r, cores, n, dt, sample = cpu_blend_rate(dts, args.cpu_seconds)
+        else:
+            img = work.cpu_sample(dts)
+            r, cores, n, dt = cpu_oracle_rate(spec, img, args.cpu_seconds)
+            sample = "%d full %dx%d images, %.1f s" % (n, img.shape[-1], img.shape[-2], dt)
+        line["cpu_baseline"] = {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

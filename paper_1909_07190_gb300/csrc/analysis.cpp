@@ -34,10 +34,18 @@ namespace wt {
 
 int elem_bytes(int dtype) { return dtype == WT_F32 ? 4 : 2; }
 
+int GroupGeom::gather_of(int id, int chan, int mode) const {
+  for (size_t i = 0; i < nodes.size(); i++) {
+    const Node &n = nodes[i];
+    if (n.gather_mode == mode && n.id == id && n.src_chan == chan) return (int)i;
+  }
+  return -1;
+}
+
 int GroupGeom::node_of(int id, int chan) const {
   for (size_t i = 0; i < nodes.size(); i++) {
     const Node &n = nodes[i];
-    if (n.synthetic || n.id != id) continue;
+    if (n.synthetic || n.gather_mode || n.id != id) continue;
     if (!n.is_source) return (int)i;
     if (n.src_chan == chan) return (int)i;
   }
@@ -176,6 +184,9 @@ int try_split(GroupGeom &g, int ni) {
   Lin l = linear_form(g.nodes[ni].prog);
   if (!l.ok || l.is_const || l.t.empty()) return -1;
   int prod = std::get<0>(l.t.begin()->first);
+  // taps of another level (gather sources) address the producer's own grid:
+  // a row pass at this level would not separate them
+  if (g.nodes[prod].gather_mode) return -1;
   int x0 = INT_MAX, x1 = INT_MIN, y0 = INT_MAX, y1 = INT_MIN, nnz = 0;
   double wmax = 0;
   for (auto &kv : l.t) {
@@ -261,15 +272,34 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
     }
   }
   auto pchan = [&](int pid) { return pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1]; };
-  // Sources: distinct (producer outside the group, channel spec).
+  // Sources: distinct (producer outside the group, channel spec); producers
+  // outside the group read through a down/up-sampling tap are gather
+  // sources (added after the stages).
+  std::vector<Node> gathers;
   for (int s : stages) {
     for (const Edge &e : p.stages[s].edges) {
       bool inside = e.producer >= 0 && in_group[e.producer];
-      if (e.mode != WT_TAP_SAME) {
-        g.fusable = false;
-        g.why_not = "group contains a down/up-sampling tap";
-      }
       int pc = pchan(e.producer);
+      if (e.mode != WT_TAP_SAME) {
+        if (inside) {
+          g.fusable = false;
+          g.why_not = "group contains a down/up-sampling tap of a stage in the group";
+          continue;
+        }
+        for (int c : e.chans) {
+          int cc = norm_chan(c, pc);
+          bool dup = false;
+          for (const Node &q : gathers) dup |= q.id == e.producer && q.src_chan == cc && q.gather_mode == e.mode;
+          if (dup) continue;
+          Node n;
+          n.id = e.producer;
+          n.src_chan = cc;
+          n.channels = pc;
+          n.gather_mode = e.mode;
+          gathers.push_back(n);
+        }
+        continue;
+      }
       if (inside) {
         for (int c : e.chans) {
           int cc = norm_chan(c, pc);
@@ -305,6 +335,8 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
     g.nodes.push_back(n);
     if (out) g.liveouts.push_back(s);
   }
+  for (const Node &n : gathers) g.nodes.push_back(n);
+  g.n_gather = (int)gathers.size();
   // Programs over kernel nodes.
   for (int s : stages) {
     const int ni = g.node_of(s, -1);
@@ -316,7 +348,10 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
       if (op.op == WT_OP_TAP) {
         int pid = S.inputs[op.slot];
         bool inside = pid >= 0 && in_group[pid];
-        k.node = inside ? g.node_of(pid, -1) : g.node_of(pid, norm_chan(op.chan, pchan(pid)));
+        if (op.mode != WT_TAP_SAME && !inside)
+          k.node = g.gather_of(pid, norm_chan(op.chan, pchan(pid)), op.mode);
+        else
+          k.node = inside ? g.node_of(pid, -1) : g.node_of(pid, norm_chan(op.chan, pchan(pid)));
         k.dx = op.dx;
         k.dy = op.dy;
         if (k.node < 0) fail(WT_EINVAL, "internal: tap node not found");
@@ -340,6 +375,7 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
   for (int ni : g.order) {
     for (const KOp &k : g.nodes[ni].prog) {
       if (k.op != WT_OP_TAP) continue;
+      if (g.nodes[k.node].gather_mode) continue;  // no rows kept, no halo
       auto key = std::make_pair(ni, k.node);
       auto it = em.find(key);
       if (it == em.end()) {
@@ -419,6 +455,7 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
   std::iota(order.begin(), order.end(), 0);
   auto wbytes = [&](int i) {
     const Node &n = g.nodes[i];
+    if (n.gather_mode) return 0L;
     return (long)n.window * (vec + n.xl + n.xr) * 4;
   };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wbytes(a) < wbytes(b); });
@@ -428,6 +465,10 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
   long acc = 0;
   for (int i : order) {
     Node &n = g.nodes[i];
+    if (n.gather_mode) {
+      n.in_smem = false;
+      continue;
+    }
     if (acc + wbytes(i) <= budget) {
       n.in_smem = false;
       acc += wbytes(i);
@@ -466,7 +507,7 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
   g.unroll = (int)U;
   g.max_src_window = 1;
   for (int i = 0; i < n_src; i++) g.max_src_window = std::max(g.max_src_window, g.nodes[i].window);
-  if (n_src > kMaxSrc) {
+  if (n_src + g.n_gather > kMaxSrc) {
     g.fusable = false;
     g.why_not = "more than " + std::to_string(kMaxSrc) + " sources";
   }

@@ -273,6 +273,23 @@ void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
   o << "}\n";
 }
 
+// A tap of a gather source for element e of the consumer (row r): the
+// clamped pixel of the producer's level, loaded from memory.
+std::string gather_tap(Ctx &c, const Node &pn, int e, int dx, int dy) {
+  const std::string x = "(xs + lane * " + std::to_string(c.V) + " + " + std::to_string(e) + ")";
+  std::string tx, ty;
+  if (pn.gather_mode == WT_TAP_DOWN2) {
+    tx = "2 * " + x + " + (" + std::to_string(dx) + ")";
+    ty = "2 * r + (" + std::to_string(dy) + ")";
+  } else {
+    tx = "(" + x + " >> 1) + (" + std::to_string(dx) + ")";  // floor(x / 2)
+    ty = "(r >> 1) + (" + std::to_string(dy) + ")";
+  }
+  const std::string chan = pn.src_chan >= 0 ? std::to_string(pn.src_chan) : "ch";
+  return "wt_gather_" + std::string(tname(c.key.src_dtypes.at(pn.src_index))) + "(ia.src[" +
+         std::to_string(pn.src_index) + "], " + chan + ", " + tx + ", " + ty + ")";
+}
+
 // Postfix program of kernel node `ni` -> C++ expression for element e.
 std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
   const Node &cn = c.g.nodes[ni_c];
@@ -285,6 +302,10 @@ std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
       case WT_OP_TAP: {
         const int pi = op.node;
         const Node &pn = c.g.nodes[pi];
+        if (pn.gather_mode) {
+          st.push_back(gather_tap(c, pn, e, op.dx, op.dy));
+          break;
+        }
         int a = cn.delay - pn.delay - op.dy;
         int j = pn.xl + e + op.dx;
         if (j < 0 || j >= width_of(pn, c.V)) fail(WT_EINVAL, "internal: tap column out of range");
@@ -529,7 +550,7 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
   // into an aligned register pair first
   bool pairs = c.key.pairs;
   for (const KOp &op : n.prog)
-    if (op.op == WT_OP_TAP && op.dx != 0) pairs = false;
+    if (op.op == WT_OP_TAP && (op.dx != 0 || c.g.nodes[op.node].gather_mode)) pairs = false;
   if (pairs) {
     int tmpid = 0;
     o << "{\n";
@@ -546,7 +567,8 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     // already; only the others are fixed up.
     bool xdep = false;
     for (const KOp &op : n.prog)
-      if ((op.op == WT_OP_TAP && op.dx != 0) || op.op == WT_OP_XPAR) xdep = true;
+      if ((op.op == WT_OP_TAP && (op.dx != 0 || c.g.nodes[op.node].gather_mode)) || op.op == WT_OP_XPAR)
+        xdep = true;
     if (xdep) emit_xfix(c, v);
   }
   if (n.in_smem) {
@@ -618,6 +640,10 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     else if (n.is_liveout) n.dst_index = n_dst++;
   }
   c.n_src = n_src;
+  // gather sources follow the staged ones in the source table
+  int n_gather = 0;
+  for (Node &n : g.nodes)
+    if (n.gather_mode) n.src_index = n_src + n_gather++;
   const int V = c.V, HT = g.halo_t, HB = g.halo_b;
   c.ks.assign(g.nodes.size(), 0);
   c.kec.assign(g.nodes.size(), 0);
@@ -657,7 +683,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // register windows (explicit scalars, D4)
   for (size_t i = 0; i < g.nodes.size(); i++) {
     const Node &n = g.nodes[i];
-    if (n.in_smem) continue;
+    if (n.in_smem || n.gather_mode) continue;
     o << "float";
     bool first = true;
     for (int s = 0; s < n.window; s++)
@@ -670,9 +696,12 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // Persistent warps pull tiles from a device queue (a.queue[0]); the last
   // warp to leave resets the queue for the next launch (a.queue[1] counts
   // the warps that left), so no per-launch clearing is needed.
+  // The next tile's index is fetched when the current tile starts, so the
+  // atomic's latency overlaps the tile's work.
+  o << "int ntile_ = 0;\nif (lane == 0) ntile_ = atomicAdd(a.queue, 1);\n";
   o << "for (;;) {\n";
-  o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
-       "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
+  o << "const int tile = __shfl_sync(WT_FULL, ntile_, 0);\nif (tile >= a.n_tiles) break;\n"
+       "if (lane == 0) ntile_ = atomicAdd(a.queue, 1);\n";
   if (key.persistent) {
     o << "const int *tt_ = a.tile_table + 4 * tile;\nconst int img = tt_[0];\n";
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";

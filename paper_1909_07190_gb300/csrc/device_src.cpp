@@ -186,6 +186,19 @@ static __device__ __forceinline__ wt_u64 wt_fma2(wt_u64 a, wt_u64 b, wt_u64 c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
   return r;
 }
+// Gather-source tap: the pixel (x, y) of channel c, clamped to the
+// source's domain (clamp-to-edge), through the read-only path.
+#define WT_GATHER(T, ESZ)                                                                  \
+  static __device__ __forceinline__ float wt_gather_##T(const WtSrc &s, int c, int x, int y) { \
+    x = wt_clampi(x, 0, s.W - 1);                                                          \
+    y = wt_clampi(y, 0, s.H - 1);                                                          \
+    return wt_ld1_##T((const unsigned char *)s.ptr + (wt_i64)c * s.plane + (wt_i64)y * s.pitch + \
+                      (wt_i64)x * ESZ);                                                   \
+  }
+WT_GATHER(f32, 4)
+WT_GATHER(f16, 2)
+WT_GATHER(bf16, 2)
+#undef WT_GATHER
 // WT-DEVICE-HELPERS-END
 )WTDEV";
 

@@ -169,6 +169,14 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
           L.src_chan.push_back(nd.src_chan);
           key.src_dtypes.push_back(loc_of(nd.id).dtype);
         }
+      L.n_ring = (int)L.src.size();
+      // gather sources (other levels) after the staged ones
+      for (const Node &nd : L.geom.nodes)
+        if (nd.gather_mode) {
+          L.src.push_back(nd.id);
+          L.src_chan.push_back(nd.src_chan);
+          key.src_dtypes.push_back(loc_of(nd.id).dtype);
+        }
       for (int s : L.geom.liveouts) {
         L.dst.push_back(s);
         key.dst_dtypes.push_back(plan.loc[s].dtype);
@@ -218,7 +226,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused) {
   char hx[24];
   // the generator's version is part of the name: a kernel whose code
   // changes gets a new name (profiles and caches never mix versions)
-  static const char kCodegenVersion[] = "wt-codegen-8";
+  static const char kCodegenVersion[] = "wt-codegen-10";
   const std::string ks = key.str();
   uint64_t h = fnv1a(ks.data(), ks.size(), p.hash);
   h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
@@ -249,6 +257,7 @@ void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws
     SrcDesc &d = a.src[i];
     d.ptr = ptr_of(l);
     d.W = l.W; d.H = l.H; d.C = l.C; d.dtype = l.dtype; d.pitch = l.pitch; d.plane = l.plane;
+    if (L.fused && (int)i >= L.n_ring) continue;  // gather source: plain loads, no tensor map
     if (L.fused && !encode_tmaps) {
       // Introspection only: a plain description of the box in place of the
       // opaque tensor map (layout: struct DebugTmap in wt_internal.hpp).

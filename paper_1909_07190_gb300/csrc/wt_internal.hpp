@@ -97,6 +97,10 @@ struct Node {
   bool rotate = true;     // rotating slot names (window divides unroll)
   int src_index = -1;     // sources: index into the kernel's source table
   int dst_index = -1;     // liveouts: index into the kernel's dst table
+  // Gather source: a producer outside the group read through a down- or
+  // up-sampling tap (another level).  It has no window and is not staged:
+  // each tap loads the clamped pixel it names from memory.
+  int gather_mode = 0;    // WT_TAP_DOWN2 / WT_TAP_UP2, 0 = not a gather source
 };
 
 struct NodeEdge {
@@ -121,6 +125,8 @@ struct GroupGeom {
   int unroll = 1;
   int max_src_window = 1;
   int node_of(int id, int chan) const;
+  int gather_of(int id, int chan, int mode) const;
+  int n_gather = 0;            // gather sources (after the staged sources)
 };
 
 struct Pipeline;

@@ -26,6 +26,7 @@ struct Launch {
   CodegenKey key;
   std::string kname;
   std::vector<int> src, src_chan, dst;
+  int n_ring = 0;  // staged (TMA) sources: src[0, n_ring); gather sources after
   int W = 0, H = 0;
   int tiles_x = 0, tiles_y = 0, n_tiles = 0;
   unsigned grid[3] = {1, 1, 1};

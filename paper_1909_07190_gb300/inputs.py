@@ -120,11 +120,12 @@ def from_storage(a: np.ndarray, dtype: str) -> np.ndarray:
 
 # ------------------------------------------------------------ config inputs
 
-def smooth_mask(seed: int, width: int, height: int, terms: int = 8) -> np.ndarray:
+def smooth_mask(seed: int, width: int, height: int, terms: int = 8, region=None) -> np.ndarray:
     """(1, H, W) float32 mask = sigmoid(4 f / sigma_f) of a low-frequency field
     f(x, y) = sum_m a_m cos(2 pi (u_m x / W + v_m y / H) + phi_m), with integer
     u_m, v_m in [-3, 3] (not both 0), a_m ~ N(0, 1) (Box-Muller), phi_m in
-    [0, 2 pi), and sigma_f = sqrt(sum a_m^2 / 2).  Computed in float64."""
+    [0, 2 pi), and sigma_f = sqrt(sum a_m^2 / 2).  Computed in float64.
+    region = (x0, y0, w, h): only that window of the W x H mask (same values)."""
     u64 = splitmix64(seed, 8 * terms)
     f01 = (u64 >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
     uv = (u64[: 2 * terms] % np.uint64(7)).astype(np.int64) - 3
@@ -137,12 +138,13 @@ def smooth_mask(seed: int, width: int, height: int, terms: int = 8) -> np.ndarra
     amp = np.sqrt(-2.0 * np.log(r1)) * np.cos(2.0 * np.pi * r2)
     phi = 2.0 * np.pi * f01[4 * terms: 5 * terms]
     sigma = np.sqrt(np.sum(amp * amp) / 2.0)
-    xs = np.arange(width, dtype=np.float64) / width
-    ys = np.arange(height, dtype=np.float64) / height
-    out = np.empty((height, width), np.float32)
-    for y0 in range(0, height, 512):
-        y1 = min(height, y0 + 512)
-        f = np.zeros((y1 - y0, width))
+    rx0, ry0, rw, rh = region if region is not None else (0, 0, width, height)
+    xs = (rx0 + np.arange(rw, dtype=np.float64)) / width
+    ys = (ry0 + np.arange(rh, dtype=np.float64)) / height
+    out = np.empty((rh, rw), np.float32)
+    for y0 in range(0, rh, 512):
+        y1 = min(rh, y0 + 512)
+        f = np.zeros((y1 - y0, rw))
         for m in range(terms):
             f += amp[m] * np.cos(2.0 * np.pi * (us[m] * xs[None, :] + vs[m] * ys[y0:y1, None]) + phi[m])
         out[y0:y1] = (1.0 / (1.0 + np.exp(-4.0 * f / sigma))).astype(np.float32)

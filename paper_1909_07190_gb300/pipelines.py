@@ -179,28 +179,40 @@ def blend(levels: int = 6, channels: int = 3) -> dict:
     R_top = BL_top, R_k = BL_k + up(R_{k+1}); output R_0."""
     b = Builder("blend", [channels, channels, 1])
     ga, gb, gm = [input_id(0)], [input_id(1)], [input_id(2)]
+    # Stage order: the three Gaussian pyramids level by level, then the
+    # coarsest blend, then per level from coarse to fine L^A, L^B, BL, R, so
+    # that the stages of one level are contiguous (blend_groups()).
     for k in range(1, levels):
         ga.append(b.stage("GA%d" % k, _down(ga[-1]), channels))
-    for k in range(1, levels):
         gb.append(b.stage("GB%d" % k, _down(gb[-1]), channels))
-    for k in range(1, levels):
         gm.append(b.stage("GM%d" % k, _down(gm[-1]), 1))
-    la, lb = [], []
-    for k in range(levels - 1):
-        la.append(b.stage("LA%d" % k, ref(ga[k]) - _up(ga[k + 1]), channels))
-    for k in range(levels - 1):
-        lb.append(b.stage("LB%d" % k, ref(gb[k]) - _up(gb[k + 1]), channels))
-    la.append(ga[-1])
-    lb.append(gb[-1])
-    bl = []
-    for k in range(levels):
-        m = ref(gm[k], chan=0)
-        bl.append(b.stage("BL%d" % k, m * ref(la[k]) + (1.0 - m) * ref(lb[k]), channels))
-    r = bl[-1]
+    top = levels - 1
+    m = ref(gm[top], chan=0)
+    r = b.stage("BL%d" % top, m * ref(ga[top]) + (1.0 - m) * ref(gb[top]), channels)
     for k in range(levels - 2, -1, -1):
-        r = b.stage("R%d" % k, ref(bl[k]) + _up(r), channels)
+        la = b.stage("LA%d" % k, ref(ga[k]) - _up(ga[k + 1]), channels)
+        lb = b.stage("LB%d" % k, ref(gb[k]) - _up(gb[k + 1]), channels)
+        m = ref(gm[k], chan=0)
+        bl = b.stage("BL%d" % k, m * ref(la) + (1.0 - m) * ref(lb), channels)
+        r = b.stage("R%d" % k, ref(bl) + _up(r), channels)
     b.output(r)
     return b.build()
+
+
+def blend_groups(levels: int = 6) -> list:
+    """Group index per stage of blend(levels): one group per Gaussian level
+    (its three down-sampling stages; the coarsest with its blend stage),
+    then one group per finer level (L^A, L^B, BL, R).  Taps of the other
+    level read memory (gather sources)."""
+    g = []
+    for k in range(1, levels):
+        g += [k - 1] * 3
+    g.append(levels - 2)  # BL at the coarsest level joins its Gaussian group
+    nxt = levels - 1
+    for _ in range(levels - 1):
+        g += [nxt] * 4
+        nxt += 1
+    return g
 
 
 def blur3() -> dict:

@@ -254,3 +254,17 @@ static inline wt_u64 wt_fma2(wt_u64 x, wt_u64 y, wt_u64 z) {
   float a, b, c, d, e, f; wt_upk(x, a, b); wt_upk(y, c, d); wt_upk(z, e, f);
   return wt_pk(std::fma(a, c, e), std::fma(b, d, f));
 }
+
+// Gather-source tap: the pixel (x, y) of channel c, clamped to the
+// source's domain (clamp-to-edge), through the read-only path.
+#define WT_GATHER(T, ESZ)                                                                  \
+  static __device__ __forceinline__ float wt_gather_##T(const WtSrc &s, int c, int x, int y) { \
+    x = wt_clampi(x, 0, s.W - 1);                                                          \
+    y = wt_clampi(y, 0, s.H - 1);                                                          \
+    return wt_ld1_##T((const unsigned char *)s.ptr + (wt_i64)c * s.plane + (wt_i64)y * s.pitch + \
+                      (wt_i64)x * ESZ);                                                   \
+  }
+WT_GATHER(f32, 4)
+WT_GATHER(f16, 2)
+WT_GATHER(bf16, 2)
+#undef WT_GATHER

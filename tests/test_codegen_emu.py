@@ -202,3 +202,41 @@ def test_fused_multi_group_schedules(name, groups, tile_h, frac):
     ng = max(groups) + 1
     got, _ = run_emulated(spec, [img], groups=groups, params=[dict(tile_h=tile_h, frac_reg=frac)] * ng)
     assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
+
+
+def gather_spec(kind):
+    """Two-group pipelines whose second group reads the first at another
+    level (gather sources)."""
+    b = P.Builder("g_" + kind, [1])
+    inp = P.input_id(0)
+    d = b.stage("d", P._down(inp))
+    if kind == "down":
+        b.output(d)
+    elif kind == "up":
+        b.output(b.stage("u", P._up(d)))
+    else:  # Laplacian level: same-level source and up-sampled coarse level
+        b.output(b.stage("l", P.ref(inp, 1, -1) - P._up(d) * P.ref(inp)))
+    return b.build()
+
+
+@pytest.mark.parametrize("kind", ["down", "up", "lap"])
+@pytest.mark.parametrize("w,h,tile_h,vec", [(37, 23, 4, 4), (1, 1, 8, 4), (130, 9, 3, 8), (5, 77, 16, 4)])
+def test_fused_gather_sources(kind, w, h, tile_h, vec):
+    spec = gather_spec(kind)
+    img = rnd(90 + w, w, h)
+    ng = 1 if kind == "down" else 2
+    got, d = run_emulated(spec, [img], groups=[0] if kind == "down" else [0, 1],
+                          params=[dict(tile_h=tile_h, vec=vec)] * ng)
+    assert d["fused"]
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("w,h,tile_h", [(80, 50, 8), (131, 67, 5), (33, 3, 16)])
+def test_fused_blend_levels(w, h, tile_h):
+    """The 36-stage blend as 10 fused groups, one per level."""
+    spec = P.blend()
+    A, B = rnd(1, w, h, 3), rnd(2, w, h, 3)
+    M = I.smooth_mask(3, w, h)
+    got, d = run_emulated(spec, [A, B, M], groups=P.blend_groups(), params=[dict(tile_h=tile_h)] * 10)
+    assert d["n_launches"] == 10
+    assert np.abs(got[0] - oracle_of(spec, [A, B, M])[0]).max() <= 1e-5
