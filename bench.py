@@ -307,9 +307,8 @@ class Blend:
 
     def kernel_name(self, pipe):
         # the largest launch: the finest level's group (the last one)
-        d = pipe.debug_kernel(pipe.launches_per_run() - 1, [x.image() for x in self.ins[0]],
-                              [self.outs[0].image()])
-        return d["name"]
+        return pipe.kernel_name(pipe.launches_per_run() - 1, [x.image() for x in self.ins[0]],
+                                [self.outs[0].image()])
 
     def e2e(self, pipe, sp, warmup, steps):
         wt, torch = self.wt, self.torch

@@ -390,6 +390,16 @@ class Pipeline:
                 "n_launches": launch[6], "unroll": launch[7], "name": kname.value.decode(),
                 "ws_bytes": wsb.value}
 
+    def kernel_name(self, index, inputs, outputs) -> str:
+        """Entry-point name of launch `index` of the run plan for these images."""
+        lib = load()
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        kname = ctypes.create_string_buffer(128)
+        check(lib.wt_debug_kernel_ws(self.h, index, ia, len(inputs), oa, len(outputs), None, 0, None, 0, None, None,
+                                     0, None, kname, 128, None))
+        return kname.value.decode()
+
     def debug_workspace_bytes(self, inputs, outputs) -> int:
         lib = load()
         ia = (wt_image * len(inputs))(*inputs)
