@@ -696,12 +696,11 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // Persistent warps pull tiles from a device queue (a.queue[0]); the last
   // warp to leave resets the queue for the next launch (a.queue[1] counts
   // the warps that left), so no per-launch clearing is needed.
-  // The next tile's index is fetched when the current tile starts, so the
-  // atomic's latency overlaps the tile's work.
-  o << "int ntile_ = 0;\nif (lane == 0) ntile_ = atomicAdd(a.queue, 1);\n";
+  // A warp takes its next tile only when it is free (taking it earlier
+  // reserves tail tiles for busy warps while others idle).
   o << "for (;;) {\n";
-  o << "const int tile = __shfl_sync(WT_FULL, ntile_, 0);\nif (tile >= a.n_tiles) break;\n"
-       "if (lane == 0) ntile_ = atomicAdd(a.queue, 1);\n";
+  o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
+       "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
   if (key.persistent) {
     o << "const int *tt_ = a.tile_table + 4 * tile;\nconst int img = tt_[0];\n";
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
