@@ -132,6 +132,9 @@ struct Ctx {
   int V, U, n_src;
   std::vector<int> ks;   // per node: first active step (constant)
   std::vector<int> kec;  // per node: last active step minus tile_h
+  // gather-source values loaded for the stage being emitted:
+  // (gather node, element, dx, dy) -> variable
+  std::map<std::tuple<int, int, int, int>, std::string> gvar;
   Ctx(const Pipeline &p_, const GroupGeom &g_, const CodegenKey &k_, const FusedLayout &L_)
       : p(p_), g(g_), key(k_), L(L_) {}
 };
@@ -273,21 +276,66 @@ void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
   o << "}\n";
 }
 
-// A tap of a gather source for element e of the consumer (row r): the
-// clamped pixel of the producer's level, loaded from memory.
-std::string gather_tap(Ctx &c, const Node &pn, int e, int dx, int dy) {
-  const std::string x = "(xs + lane * " + std::to_string(c.V) + " + " + std::to_string(e) + ")";
-  std::string tx, ty;
-  if (pn.gather_mode == WT_TAP_DOWN2) {
-    tx = "2 * " + x + " + (" + std::to_string(dx) + ")";
-    ty = "2 * r + (" + std::to_string(dy) + ")";
-  } else {
-    tx = "(" + x + " >> 1) + (" + std::to_string(dx) + ")";  // floor(x / 2)
-    ty = "(r >> 1) + (" + std::to_string(dy) + ")";
+// A tap of a gather source for element e of the consumer: a variable
+// loaded by the stage's gather prologue.
+std::string gather_tap(Ctx &c, int gi, int e, int dx, int dy) {
+  auto it = c.gvar.find(std::make_tuple(gi, e, dx, dy));
+  if (it == c.gvar.end()) fail(WT_EINVAL, "internal: gather tap without a load");
+  return it->second;
+}
+
+// Gather prologue of a stage: every distinct pixel its taps of other levels
+// read, loaded once, with one clamped row address per distinct row and one
+// clamped column per distinct column.  The lane's first column X0 = xs +
+// lane * V is even (xs and V are), so element e's source column is a
+// constant offset from X0 / 2 (up-sampling: floor((X0 + e) / 2) + dx) or
+// from 2 X0 (down-sampling: 2 (X0 + e) + dx); rows likewise from r.
+void emit_gather_prologue(Ctx &c, int ni) {
+  const Node &n = c.g.nodes[ni];
+  auto &o = c.o;
+  c.gvar.clear();
+  struct Tap { int gi, dx, dy; };
+  std::vector<Tap> taps;
+  for (const KOp &op : n.prog)
+    if (op.op == WT_OP_TAP && c.g.nodes[op.node].gather_mode) taps.push_back({op.node, op.dx, op.dy});
+  if (taps.empty()) return;
+  std::map<std::pair<int, int>, std::string> rows, cols;
+  std::map<std::tuple<int, int, int>, std::string> vals;
+  int id = 0;
+  for (const Tap &t : taps) {
+    const Node &pn = c.g.nodes[t.gi];
+    const bool down = pn.gather_mode == WT_TAP_DOWN2;
+    const std::string S = "ia.src[" + std::to_string(pn.src_index) + "]";
+    const int esz = elem_bytes(c.key.src_dtypes.at(pn.src_index));
+    auto rk = std::make_pair(t.gi, t.dy);
+    if (!rows.count(rk)) {
+      std::string v = "gr" + std::to_string(id++);
+      const std::string chan = pn.src_chan >= 0 ? std::to_string(pn.src_chan) : "ch";
+      o << "const unsigned char *" << v << " = (const unsigned char *)" << S << ".ptr + (wt_i64)" << chan << " * "
+        << S << ".plane + (wt_i64)wt_clampi(" << (down ? "2 * r" : "(r >> 1)") << " + (" << t.dy << "), 0, " << S
+        << ".H - 1) * " << S << ".pitch;\n";
+      rows[rk] = v;
+    }
+    for (int e = 0; e < c.V; e++) {
+      const int off = down ? 2 * e + t.dx : (e >> 1) + t.dx;
+      auto ck = std::make_pair(t.gi, off);
+      if (!cols.count(ck)) {
+        std::string v = "gc" + std::to_string(id++);
+        o << "const int " << v << " = wt_clampi(" << (down ? "2 * (xs + lane * " + std::to_string(c.V) + ")"
+                                                           : "((xs + lane * " + std::to_string(c.V) + ") >> 1)")
+          << " + (" << off << "), 0, " << S << ".W - 1) * " << esz << ";\n";
+        cols[ck] = v;
+      }
+      auto vk = std::make_tuple(t.gi, t.dy, off);
+      if (!vals.count(vk)) {
+        std::string v = "gv" + std::to_string(id++);
+        o << "const float " << v << " = wt_ld1_" << tname(c.key.src_dtypes.at(pn.src_index)) << "(" << rows[rk]
+          << " + " << cols[ck] << ");\n";
+        vals[vk] = v;
+      }
+      c.gvar[std::make_tuple(t.gi, e, t.dx, t.dy)] = vals[vk];
+    }
   }
-  const std::string chan = pn.src_chan >= 0 ? std::to_string(pn.src_chan) : "ch";
-  return "wt_gather_" + std::string(tname(c.key.src_dtypes.at(pn.src_index))) + "(ia.src[" +
-         std::to_string(pn.src_index) + "], " + chan + ", " + tx + ", " + ty + ")";
 }
 
 // Postfix program of kernel node `ni` -> C++ expression for element e.
@@ -303,7 +351,7 @@ std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
         const int pi = op.node;
         const Node &pn = c.g.nodes[pi];
         if (pn.gather_mode) {
-          st.push_back(gather_tap(c, pn, e, op.dx, op.dy));
+          st.push_back(gather_tap(c, pi, e, op.dx, op.dy));
           break;
         }
         int a = cn.delay - pn.delay - op.dy;
@@ -545,6 +593,7 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     }
     o << "} else {\n";
   }
+  emit_gather_prologue(c, ni);
   // packed pairs for nodes whose taps all read the producer's own element
   // pairs (dx = 0): a pair shifted by one column would have to be gathered
   // into an aligned register pair first
