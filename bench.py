@@ -296,7 +296,8 @@ class Blend:
         self.l2_note = "rotating %d input/output sets (%.0f MB) > 3x L2" % (self.nsets, self.alg_bytes / 1e6)
 
     def schedule(self, fused, plain):
-        fused.schedule(groups=P.blend_groups())
+        groups, params = P.blend_schedule()
+        fused.schedule(groups=groups, params=params)
 
     def run(self, pipe, i, sp):
         k = i % self.nsets
@@ -419,7 +420,8 @@ def run_ours(args, rank, world, local):
     if args.params:
         prm = json.loads(args.params)
         if hasattr(work, "schedule"):
-            fused.schedule(groups=P.blend_groups(), params=[prm] * 10)
+            groups, params = P.blend_schedule()
+            fused.schedule(groups=groups, params=[dict(p, **prm) for p in params])
         else:
             fused.schedule(params=prm)
     tune_t0 = time.perf_counter()

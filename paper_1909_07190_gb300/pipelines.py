@@ -215,6 +215,18 @@ def blend_groups(levels: int = 6) -> list:
     return g
 
 
+def blend_schedule(levels: int = 6) -> tuple:
+    """(groups, params) of the blend's default schedule: blend_groups(), with
+    the pure down-sampling groups of levels 1..levels-2 run as per-stage
+    kernels (a fused group of gathers has nothing to keep on chip, and its
+    one-channel mask stage would be computed once per tile channel) and the
+    other groups fused."""
+    groups = blend_groups(levels)
+    plain = 4  # WT_FLAG_PLAIN
+    params = [dict(flags=plain)] * (levels - 2) + [dict()] * (levels)
+    return groups, params
+
+
 def blur3() -> dict:
     """The paper's running example (Fig. 2): blurx = 3-tap mean along x,
     blury = 3-tap mean of blurx along y."""

@@ -22,12 +22,15 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def run_blend(A, B, M, dtype, fused=True, params=None):
+def run_blend(A, B, M, dtype, fused=True, params=None, mixed=False):
     from paper_1909_07190_gb300 import wt
     dt = wt.DTYPES[dtype]
     spec = P.blend()
     p = wt.Pipeline(spec)
-    if fused:
+    if fused and mixed:
+        groups, prm = P.blend_schedule()
+        p.schedule(groups=groups, params=[dict(q, **(params or {})) for q in prm])
+    elif fused:
         p.schedule(groups=P.blend_groups(), params=[params or {}] * 10)
     else:
         p.schedule(exec_mode=wt.WT_EXEC_PLAIN)
@@ -53,6 +56,19 @@ def test_blend_fused_levels(dtype, w, h, tile_h):
     M = I.round_to(I.smooth_mask(13, w, h), dtype)
     got, p = run_blend(A, B, M, dtype, params=dict(tile_h=tile_h))
     assert p.launches_per_run() == 10
+    assert np.abs(got - oracle(A, B, M)).max() <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_blend_default_mixed_schedule(dtype):
+    """The default blend schedule: down-sampling groups per stage, the other
+    levels fused (18 launches)."""
+    w, h = 555, 301
+    A = I.round_to(I.uniform_image(31, w, h, 3), dtype)
+    B = I.round_to(I.uniform_image(32, w, h, 3), dtype)
+    M = I.round_to(I.smooth_mask(33, w, h), dtype)
+    got, p = run_blend(A, B, M, dtype, mixed=True)
+    assert p.launches_per_run() == 18
     assert np.abs(got - oracle(A, B, M)).max() <= TOL[dtype]
 
 
@@ -112,7 +128,8 @@ def test_blend_8192_bf16_sampled():
     ins[2].view().copy_(torch.from_numpy(I.smooth_mask(sm, W, H)).to(torch.bfloat16))
     out = wt.DeviceImage(3, H, W, dt)
     p = wt.Pipeline(P.blend())
-    p.schedule(groups=P.blend_groups())
+    groups, params = P.blend_schedule()
+    p.schedule(groups=groups, params=params)
     p.run([x.image() for x in ins], [out.image()], stream())
     p.check(stream())
     rng = np.random.default_rng(5)
