@@ -747,6 +747,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // the warps that left), so no per-launch clearing is needed.
   // A warp takes its next tile only when it is free (taking it earlier
   // reserves tail tiles for busy warps while others idle).
+  if (key.persistent) o << "int last_img_ = -1;\n";
   o << "for (;;) {\n";
   o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
        "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
@@ -768,9 +769,11 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   }
   if (key.persistent) {
     o << "const int T = ia.tile_h, y0 = ty * T;\n";
-    o << "if (lane == 0) {";
+    // the image's tensor maps, acquired when the warp moves to a new image
+    // (tiles are listed image by image)
+    o << "if (img != last_img_) {\nlast_img_ = img;\nif (lane == 0) {";
     for (int s = 0; s < n_src; s++) o << " wt_tmap_acquire(&ia.tmap[" << s << "]);";
-    o << " }\n";
+    o << " }\n}\n";
   }
   o << "const int W = ia.W, H = ia.H;\n";
   o << "const int xs = tx * " << L.out_w << " - " << L.lpad << ";\n";

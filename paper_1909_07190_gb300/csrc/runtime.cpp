@@ -227,9 +227,11 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused) {
   // the generator's version is part of the name: a kernel whose code
   // changes gets a new name (profiles and caches never mix versions)
   static const char kCodegenVersion[] = "wt-codegen-12";
+  static const char kBatchVersion[] = "wt-batch-13";  // the persistent variant's own changes
   const std::string ks = key.str();
   uint64_t h = fnv1a(ks.data(), ks.size(), p.hash);
   h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
+  if (key.persistent) h = fnv1a(kBatchVersion, sizeof kBatchVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }
