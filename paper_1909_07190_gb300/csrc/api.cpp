@@ -320,7 +320,7 @@ int32_t wt_launches_per_run(const wt_pipeline *p) {
   wt_status rc = guard([&] {
     auto groups = wt::schedule_groups(*p);
     for (size_t gi = 0; gi < groups.size(); gi++) {
-      bool fused = p->sched.exec == WT_EXEC_FUSED &&
+      bool fused = p->sched.exec == WT_EXEC_FUSED && !wt::group_params(*p, (int)gi).plain &&
                    wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable;
       if (fused) {
         n++;

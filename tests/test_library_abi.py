@@ -173,3 +173,13 @@ def test_costmodel_load_rejects_bad_files(tmp_path):
         wt.costmodel_load(tmp_path / "missing.txt")
     with pytest.raises(wt.WtError):
         wt.costmodel_save(tmp_path / "none.txt")   # no model to save
+
+
+def test_launch_count_with_per_stage_groups():
+    """Groups flagged to run per stage count one launch per live stage."""
+    p = wt.Pipeline(P.blend())
+    groups, params = P.blend_schedule()
+    p.schedule(groups=groups, params=params)
+    assert p.launches_per_run() == 4 * 3 + 6
+    p.schedule(groups=P.blend_groups())
+    assert p.launches_per_run() == 10
