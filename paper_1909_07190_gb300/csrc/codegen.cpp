@@ -747,41 +747,25 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // the warps that left), so no per-launch clearing is needed.
   // A warp takes its next tile only when it is free (taking it earlier
   // reserves tail tiles for busy warps while others idle).
-  const bool prefetch = !key.persistent;
   if (key.persistent) o << "int last_img_ = -1;\n";
-  if (prefetch) {
-    // tall tiles first (ty1 tile rows of tile_h rows below a band of ty2
-    // short rows), then the short tiles of tile_h2 rows: the last tiles
-    // handed out are short, and the slow bottom-border row is handed out
-    // before them, not in the final round
-    o << "auto decode_ = [&](int t_, int &tx_, int &ch_, int &y0_, int &T_) {\n"
-         "if (t_ < a.n_big) { tx_ = t_ % a.tiles_x; const int tr_ = t_ / a.tiles_x;"
-         " y0_ = a.ty2 * a.tile_h2 + (tr_ % a.ty1) * a.tile_h; ch_ = tr_ / a.ty1; T_ = a.tile_h; }\n"
-         "else { const int j_ = t_ - a.n_big; tx_ = j_ % a.tiles_x; const int tr_ = j_ / a.tiles_x;"
-         " y0_ = (tr_ % a.ty2) * a.tile_h2; ch_ = tr_ / a.ty2; T_ = a.tile_h2; }\n};\n";
-    // A tile taken while the current one finishes (its first chunk then
-    // loads during the current tile's last rows), or -1.  Tiles are taken
-    // early only while the queue is far from its end: near the end an early
-    // taker would hold a tile that an idle warp could run.
-    o << "int pf_tile_ = -1;\nconst int pf_margin_ = 2 * (int)gridDim.x * " << key.nw << ";\n";
-  }
   o << "for (;;) {\n";
-  if (prefetch) {
-    o << "int tile = 0;\nconst bool pf_ = pf_tile_ >= 0;\n"
-         "if (pf_) { tile = pf_tile_; pf_tile_ = -1; }\n"
-         "else { if (lane == 0) tile = atomicAdd(a.queue, 1); tile = __shfl_sync(WT_FULL, tile, 0); }\n"
-         "if (tile >= a.n_tiles) break;\n";
-  } else {
-    o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
-         "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
-  }
+  o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
+       "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
   if (key.persistent) {
     o << "const int *tt_ = a.tile_table + 4 * tile;\nconst int img = tt_[0];\n";
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
     o << "const int tx = tt_[1], ty = tt_[2], ch = tt_[3];\n";
   } else {
+    // tall tiles first (ty1 tile rows of tile_h rows below a band of ty2
+    // short rows), then the short tiles of tile_h2 rows: the last tiles
+    // handed out are short, and the slow bottom-border row is handed out
+    // before them, not in the final round
     o << "const WtArgs &ia = a;\n";
-    o << "int tx, ch, y0, T;\ndecode_(tile, tx, ch, y0, T);\n";
+    o << "int tx, ch, y0, T;\n";
+    o << "if (tile < a.n_big) { tx = tile % a.tiles_x; const int tr_ = tile / a.tiles_x;"
+         " y0 = a.ty2 * a.tile_h2 + (tr_ % a.ty1) * a.tile_h; ch = tr_ / a.ty1; T = a.tile_h; }\n"
+         "else { const int j_ = tile - a.n_big; tx = j_ % a.tiles_x; const int tr_ = j_ / a.tiles_x;"
+         " y0 = (tr_ % a.ty2) * a.tile_h2; ch = tr_ / a.ty2; T = a.tile_h2; }\n";
   }
   if (key.persistent) {
     o << "const int T = ia.tile_h, y0 = ty * T;\n";
@@ -834,34 +818,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     o << "wt_tma_load_3d(wt_smem_u32(rb" << s << " + (gc_ % NB) * BUFB" << s << "), &ia.tmap["
       << s << "], xb" << s << ", y_top + c_ * CH, zc" << s << ", b_);\n";
   o << "}\nissued = c_ + 1;\n};\n";
-  o << "const int nch_ = (nrows + CH - 1) / CH;\n";
-  if (prefetch) {
-    o << "issued = 0;\nfor (int c_ = pf_ ? 1 : 0; c_ < NB - 1; c_++) if (c_ * CH < nrows) issue_chunk(c_);\n"
-         "if (pf_ && issued < 1) issued = 1;\n";
-    // the next tile's first chunk, into the buffer after this tile's last
-    o << "auto prefetch_ = [&](int c_) {\nint nt_ = -1;\n"
-         "if (lane == 0 && *(volatile const int *)a.queue < a.n_tiles - pf_margin_) nt_ = atomicAdd(a.queue, 1);\n"
-         "nt_ = __shfl_sync(WT_FULL, nt_, 0);\nif (nt_ < 0) return;\npf_tile_ = nt_;\n"
-         "if (nt_ >= a.n_tiles) return;\n"
-         "int tx2_, ch2_, y02_, T2_;\ndecode_(nt_, tx2_, ch2_, y02_, T2_);\n"
-         "const int xs2_ = tx2_ * " << L.out_w << " - " << L.lpad << ";\n"
-         "__syncwarp();\nif (lane == 0) {\nwt_fence_proxy_async();\n"
-         "const int gc_ = cbase + c_;\nconst wt_u32 b_ = bar + 8u * (wt_u32)(gc_ % NB);\n"
-         "wt_mbar_expect_tx(b_, " << L.chunk_bytes << "u);\n";
-    for (int s = 0; s < n_src; s++) {
-      const Node *sn = nullptr;
-      for (const Node &n : g.nodes)
-        if (n.is_source && n.src_index == s) sn = &n;
-      int A = 16 / L.esz[s];
-      std::string xb2 = (V % A) ? "(xs2_ & ~" + std::to_string(A - 1) + ")" : "xs2_";
-      std::string zc2 = (sn->src_chan >= 0) ? std::to_string(sn->src_chan) : "ch2_";
-      o << "wt_tma_load_3d(wt_smem_u32(rb" << s << " + (gc_ % NB) * BUFB" << s << "), &ia.tmap[" << s << "], " << xb2
-        << ", y02_ - " << HT << ", " << zc2 << ", b_);\n";
-    }
-    o << "}\nissued = c_ + 1;\n};\n";
-  } else {
-    o << "for (int c_ = 0; c_ < NB - 1; c_++) if (c_ * CH < nrows) issue_chunk(c_);\n";
-  }
+  o << "for (int c_ = 0; c_ < NB - 1; c_++) if (c_ * CH < nrows) issue_chunk(c_);\n";
   (void)kss;
   (void)kse_c;
   // Interior tiles run the guard-free body for every step: rows a node
@@ -881,8 +838,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   o << "if (kc_ == 0 && kch_ * CH < nrows) {"
        " const int gc_ = cbase + kch_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
        " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = kch_; goto wt_fail; } }\n"
-       "if (kc_ == ISSUE) { const int c_ = kch_ + NB - 1; if (c_ * CH < nrows) issue_chunk(c_);"
-    << (prefetch ? " else if (c_ == nch_ && pf_tile_ < 0) prefetch_(c_);" : "") << " }\n";
+       "if (kc_ == ISSUE) { const int c_ = kch_ + NB - 1; if (c_ * CH < nrows) issue_chunk(c_); }\n";
   o << "if (!border) {\n";
   for (int s = 0; s < n_src; s++)
     o << "const unsigned char *rp" << s << " = lp" << s << " + ((cbase + kch_) % NB) * BUFB" << s << " + kc_ * ROWB"
@@ -894,7 +850,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   o << "kc_ += U;\nif (kc_ == CH) { kc_ = 0; kch_++; }\n";
   o << "}\n";
   o << "wt_tile_end:;\n";
-  o << "cbase += nch_;\n";
+  o << "cbase += (nrows + CH - 1) / CH;\n";
   o << "}\n";  // tile loop
   o << "wt_exit:\n";
   o << "if (lane == 0) {\n__threadfence();\nconst int d_ = atomicAdd(a.queue + 1, 1);\n"
