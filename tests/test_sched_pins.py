@@ -124,3 +124,15 @@ def test_auto_schedule_blend_groups_by_level():
     s = p.schedule_get()
     groups = s["groups"]
     assert groups == sorted(groups) and groups[0] == 0
+
+
+def test_dp_fusion_groups_blend_by_level():
+    """DP-Fusion over the 36-stage blend (stages ordered by level) finds one
+    fused group per pyramid level: taps of the neighbouring level are gather
+    sources, groups never span levels."""
+    spec = P.blend()
+    p = wt.Pipeline(spec)
+    p.schedule_auto(8192, 8192, wt.WT_BF16, wt.WT_MODEL_ANALYTIC)
+    s = p.schedule_get()
+    assert s["groups"] == P.blend_groups()
+    assert p.launches_per_run() == 10
