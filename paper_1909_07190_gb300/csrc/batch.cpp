@@ -66,7 +66,7 @@ BatchPlan build_batch(Pipeline &p, const wt_image *in, const wt_image *out, int 
   for (size_t l = 0; l < r0.launches.size(); l++) {
     Launch L = r0.launches[l];
     L.key.persistent = true;
-    L.kname = kernel_name(p, L.key, true);
+    L.kname = kernel_name(p, L.key, true, L.geom.n_gather > 0);
     std::vector<int32_t> &t = b.tiles[l];
     int64_t total = 0;
     for (int i = 0; i < n; i++) total += b.img[i].launches[l].n_tiles;

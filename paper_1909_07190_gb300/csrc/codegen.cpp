@@ -339,48 +339,88 @@ void emit_gather_prologue(Ctx &c, int ni) {
 }
 
 // Postfix program of kernel node `ni` -> C++ expression for element e.
+// Constants fold: operations on constants only are evaluated here in FP32
+// (the result the device would compute), and x * 0, x * 1, x + 0 and x - 0
+// simplify (exact for the finite values stages carry).  The column parity
+// of element e is such a constant, so an up-sampling stage keeps only the
+// taps of its own phase.
 std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
   const Node &cn = c.g.nodes[ni_c];
-  std::vector<std::string> st;
+  struct Val {
+    std::string s;
+    bool k = false;
+    float v = 0.f;
+  };
+  auto konst = [](float v) { Val x; x.s = flt(v); x.k = true; x.v = v; return x; };
+  auto expr = [](const std::string &s) { Val x; x.s = s; return x; };
+  std::vector<Val> st;
   for (const KOp &op : cn.prog) {
     switch (op.op) {
-      case WT_OP_CONST: st.push_back(flt(op.value)); break;
-      case WT_OP_XPAR: st.push_back(flt((float)(e & 1))); break;
-      case WT_OP_YPAR: st.push_back("((float)(r & 1))"); break;
+      case WT_OP_CONST: st.push_back(konst(op.value)); break;
+      case WT_OP_XPAR: st.push_back(konst((float)(e & 1))); break;
+      case WT_OP_YPAR: st.push_back(expr("((float)(r & 1))")); break;
       case WT_OP_TAP: {
         const int pi = op.node;
         const Node &pn = c.g.nodes[pi];
         if (pn.gather_mode) {
-          st.push_back(gather_tap(c, pi, e, op.dx, op.dy));
+          st.push_back(expr(gather_tap(c, pi, e, op.dx, op.dy)));
           break;
         }
         int a = cn.delay - pn.delay - op.dy;
         int j = pn.xl + e + op.dx;
         if (j < 0 || j >= width_of(pn, c.V)) fail(WT_EINVAL, "internal: tap column out of range");
-        if (pn.in_smem) st.push_back(tmp(pi, a, j));
-        else st.push_back(reg(pi, slot_of(pn, u, a), j));
+        if (pn.in_smem) st.push_back(expr(tmp(pi, a, j)));
+        else st.push_back(expr(reg(pi, slot_of(pn, u, a), j)));
       } break;
-      case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
-      case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
-      case WT_OP_SQRT: st.back() = "sqrtf(" + st.back() + ")"; break;
+      case WT_OP_NEG:
+        st.back() = st.back().k ? konst(-st.back().v) : expr("(-" + st.back().s + ")");
+        break;
+      case WT_OP_ABS:
+        st.back() = st.back().k ? konst(std::fabs(st.back().v)) : expr("fabsf(" + st.back().s + ")");
+        break;
+      case WT_OP_SQRT:
+        st.back() = st.back().k ? konst(std::sqrt(st.back().v)) : expr("sqrtf(" + st.back().s + ")");
+        break;
       default: {
-        std::string b = st.back();
+        Val b = st.back();
         st.pop_back();
-        std::string a = st.back();
+        Val a = st.back();
         st.pop_back();
+        if (a.k && b.k) {
+          float r = 0.f;
+          switch (op.op) {
+            case WT_OP_ADD: r = a.v + b.v; break;
+            case WT_OP_SUB: r = a.v - b.v; break;
+            case WT_OP_MUL: r = a.v * b.v; break;
+            case WT_OP_DIV: r = a.v / b.v; break;
+            case WT_OP_MIN: r = std::fmin(a.v, b.v); break;
+            case WT_OP_MAX: r = std::fmax(a.v, b.v); break;
+            default: fail(WT_EINVAL, "internal: opcode");
+          }
+          st.push_back(konst(r));
+          break;
+        }
+        if (op.op == WT_OP_MUL && ((a.k && a.v == 0.f) || (b.k && b.v == 0.f))) {
+          st.push_back(konst(0.f));
+          break;
+        }
+        if (op.op == WT_OP_MUL && a.k && a.v == 1.f) { st.push_back(b); break; }
+        if (op.op == WT_OP_MUL && b.k && b.v == 1.f) { st.push_back(a); break; }
+        if (op.op == WT_OP_ADD && a.k && a.v == 0.f) { st.push_back(b); break; }
+        if ((op.op == WT_OP_ADD || op.op == WT_OP_SUB) && b.k && b.v == 0.f) { st.push_back(a); break; }
         switch (op.op) {
-          case WT_OP_ADD: st.push_back("(" + a + " + " + b + ")"); break;
-          case WT_OP_SUB: st.push_back("(" + a + " - " + b + ")"); break;
-          case WT_OP_MUL: st.push_back("(" + a + " * " + b + ")"); break;
-          case WT_OP_DIV: st.push_back("(" + a + " / " + b + ")"); break;
-          case WT_OP_MIN: st.push_back("fminf(" + a + ", " + b + ")"); break;
-          case WT_OP_MAX: st.push_back("fmaxf(" + a + ", " + b + ")"); break;
+          case WT_OP_ADD: st.push_back(expr("(" + a.s + " + " + b.s + ")")); break;
+          case WT_OP_SUB: st.push_back(expr("(" + a.s + " - " + b.s + ")")); break;
+          case WT_OP_MUL: st.push_back(expr("(" + a.s + " * " + b.s + ")")); break;
+          case WT_OP_DIV: st.push_back(expr("(" + a.s + " / " + b.s + ")")); break;
+          case WT_OP_MIN: st.push_back(expr("fminf(" + a.s + ", " + b.s + ")")); break;
+          case WT_OP_MAX: st.push_back(expr("fmaxf(" + a.s + ", " + b.s + ")")); break;
           default: fail(WT_EINVAL, "internal: opcode");
         }
       }
     }
   }
-  return st.back();
+  return st.back().s;
 }
 
 // --------------------------------------------------- packed pair code

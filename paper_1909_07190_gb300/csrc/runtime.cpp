@@ -217,12 +217,12 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       if (L.H > 65535 || L.grid[2] > 65535) fail(WT_EUNSUPPORTED, "image too tall for the per-stage kernel");
       L.smem = 0;
     }
-    L.kname = kernel_name(p, key, L.fused);
+    L.kname = kernel_name(p, key, L.fused, L.fused && L.geom.n_gather > 0);
   }
   return plan;
 }
 
-std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused) {
+std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bool gather) {
   char hx[24];
   // the generator's version is part of the name: a kernel whose code
   // changes gets a new name (profiles and caches never mix versions)
@@ -232,6 +232,8 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused) {
   uint64_t h = fnv1a(ks.data(), ks.size(), p.hash);
   h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
   if (key.persistent) h = fnv1a(kBatchVersion, sizeof kBatchVersion, h);
+  static const char kGatherVersion[] = "wt-gather-2";  // kernels reading other levels
+  if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }

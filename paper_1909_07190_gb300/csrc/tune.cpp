@@ -131,7 +131,7 @@ void precompile(Pipeline &p, const std::vector<Schedule> &cands, const wt_image 
       for (Launch &L : plan.launches) {
         if (persistent && L.fused) {
           L.key.persistent = true;
-          L.kname = kernel_name(p, L.key, true);
+          L.kname = kernel_name(p, L.key, true, L.geom.n_gather > 0);
         }
         if (!names.insert(L.kname).second) continue;
         jobs.push_back({launch_source(p, L), L.kname, L.key.max_regs});

@@ -74,7 +74,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
 std::string launch_source(const Pipeline &p, const Launch &L);
 // Entry-point name of a generated kernel (a hash of the pipeline, the
 // codegen key and the generator version).
-std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused);
+std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bool gather = false);
 void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws, KernelArgs &a,
                bool encode_tmaps);
 Kernel &get_kernel(const Pipeline &p, const Launch &L, int device);
