@@ -924,7 +924,10 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
   const Stage &S = p.stages[sid];
   std::vector<PlainSrc> srcs = plain_sources(p, sid);
   if ((int)srcs.size() > kMaxSrc) fail(WT_EUNSUPPORTED, "stage reads more than 8 sources");
-  const int PV = 4;  // output pixels per thread
+  // Output pixels per thread.  With 8 the first column x0 of every row
+  // segment a thread reads (x0, 2 x0 or x0 / 2) is a multiple of 4, so
+  // interior threads load segments with aligned 4-element vectors.
+  const int PV = 8;
   std::ostringstream o;
   o << kDeviceSource;
   o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
@@ -973,10 +976,32 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     o << "const unsigned char *rp" << ri << " = (const unsigned char *)" << sd << ".ptr + (wt_i64)" << zc
       << " * " << sd << ".plane + (wt_i64)wt_clampi(" << ybase << " + (" << r.dy << "), 0, " << sd
       << ".H - 1) * " << sd << ".pitch;\n";
+    // the segment's columns base + lo .. base + hi: whole aligned 4-vectors
+    // when they lie inside the row, else clamped scalar loads
+    auto floor4 = [](int v) { return (v >= 0 ? v / 4 : -((-v + 3) / 4)) * 4; };
+    const int lo_a = floor4(lo);
+    const int hi_a = floor4(hi) + 3;
+    const int nv = (hi_a - lo_a + 1) / 4;
+    std::vector<std::string> vals(nv * 4);
+    o << "float";
+    for (int j = lo; j <= hi; j++) o << (j == lo ? " " : ", ") << "L" << ri << "_" << (j - lo);
+    o << ";\n";
+    o << "if (" << base << " + (" << lo_a << ") >= 0 && " << base << " + (" << hi_a << ") <= " << sd << ".W - 1) {\n";
+    for (int k = 0; k < nv; k++) {
+      o << "{ float q0, q1, q2, q3;\nwt_ld4_" << tname(dt) << "(rp" << ri << " + (wt_i64)(" << base << " + (" << lo_a + 4 * k
+        << ")) * " << elem_bytes(dt) << ", q0, q1, q2, q3);\n";
+      for (int t = 0; t < 4; t++) {
+        int j = lo_a + 4 * k + t;
+        if (j >= lo && j <= hi) o << "L" << ri << "_" << (j - lo) << " = q" << t << ";\n";
+      }
+      o << "}\n";
+    }
+    o << "} else {\n";
     for (int j = lo; j <= hi; j++)
-      o << "const float L" << ri << "_" << (j - lo) << " = wt_ld1_" << tname(dt) << "(rp" << ri
+      o << "L" << ri << "_" << (j - lo) << " = wt_ld1_" << tname(dt) << "(rp" << ri
         << " + (wt_i64)wt_clampi(" << base << " + (" << j << "), 0, " << sd << ".W - 1) * "
         << elem_bytes(dt) << ");\n";
+    o << "}\n";
   }
   for (int e = 0; e < PV; e++) {
     std::vector<std::string> st;
@@ -1025,7 +1050,11 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
   int esz = elem_bytes(dt);
   o << "unsigned char *op_ = (unsigned char *)a.dst[0].ptr + (wt_i64)" << (S.channels > 1 ? "ch" : "0")
     << " * a.dst[0].plane + (wt_i64)y * a.dst[0].pitch + (wt_i64)x0 * " << esz << ";\n";
-  o << "if (x0 + " << PV << " <= W) { wt_st4_" << tname(dt) << "(op_, v0, v1, v2, v3); } else {\n";
+  o << "if (x0 + " << PV << " <= W) {";
+  for (int b = 0; b < PV; b += 4)
+    o << " wt_st4_" << tname(dt) << "(op_ + " << b * esz << ", v" << b << ", v" << b + 1 << ", v" << b + 2 << ", v" << b + 3
+      << ");";
+  o << " } else {\n";
   for (int e = 0; e < PV; e++)
     o << "if (x0 + " << e << " < W) wt_st1_" << tname(dt) << "(op_ + " << e * esz << ", v" << e << ");\n";
   o << "}\n}\n";

@@ -211,7 +211,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       key.dst_dtypes.push_back(plan.loc[s].dtype);
       level_dims(plan.W, plan.H, p.stages[s].level, &L.W, &L.H);
       L.block = 128;
-      L.grid[0] = (unsigned)(((L.W + 3) / 4 + 127) / 128);
+      L.grid[0] = (unsigned)(((L.W + 7) / 8 + 127) / 128);
       L.grid[1] = (unsigned)L.H;
       L.grid[2] = (unsigned)p.stages[s].channels;
       if (L.H > 65535 || L.grid[2] > 65535) fail(WT_EUNSUPPORTED, "image too tall for the per-stage kernel");
@@ -227,11 +227,13 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   // the generator's version is part of the name: a kernel whose code
   // changes gets a new name (profiles and caches never mix versions)
   static const char kCodegenVersion[] = "wt-codegen-12";
+  static const char kPlainVersion[] = "wt-plain-2";  // the per-stage kernel's own changes
   static const char kBatchVersion[] = "wt-batch-13";  // the persistent variant's own changes
   const std::string ks = key.str();
   uint64_t h = fnv1a(ks.data(), ks.size(), p.hash);
   h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
   if (key.persistent) h = fnv1a(kBatchVersion, sizeof kBatchVersion, h);
+  if (!fused) h = fnv1a(kPlainVersion, sizeof kPlainVersion, h);
   static const char kGatherVersion[] = "wt-gather-2";  // kernels reading other levels
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));

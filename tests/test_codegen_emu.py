@@ -240,3 +240,26 @@ def test_fused_blend_levels(w, h, tile_h):
     got, d = run_emulated(spec, [A, B, M], groups=P.blend_groups(), params=[dict(tile_h=tile_h)] * 10)
     assert d["n_launches"] == 10
     assert np.abs(got[0] - oracle_of(spec, [A, B, M])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["sharpen", "harris"])
+@pytest.mark.parametrize("w,h,dtype,tol", [(150, 7, wt.WT_F32, 1e-5), (333, 5, wt.WT_F16, 2e-3),
+                                           (61, 9, wt.WT_BF16, 1.6e-2), (8, 3, wt.WT_F32, 1e-5)])
+def test_plain_kernels_interior_and_edges(name, w, h, dtype, tol):
+    """Per-stage kernels: interior threads load row segments as aligned
+    vectors, edge threads clamp each column."""
+    spec = P.by_name(name)
+    dn = {wt.WT_F32: "f32", wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
+    img = rnd(w + h, w, h, dtype=dn)
+    got, d = run_emulated(spec, [img], dtype=dtype, exec_mode=wt.WT_EXEC_PLAIN)
+    assert not d["fused"]
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= tol
+
+
+@pytest.mark.parametrize("w,h", [(96, 40), (37, 19)])
+def test_plain_blend(w, h):
+    spec = P.blend()
+    A, B = rnd(3, w, h, 3), rnd(4, w, h, 3)
+    M = I.smooth_mask(5, w, h)
+    got, d = run_emulated(spec, [A, B, M], exec_mode=wt.WT_EXEC_PLAIN)
+    assert np.abs(got[0] - oracle_of(spec, [A, B, M])[0]).max() <= 1e-5
