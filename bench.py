@@ -64,6 +64,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values: a job's time is its slowest rank's
+    (every rank holds the result)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(px_per_rank_step, world, steps, total_ms):
+    """Whole-job Mpixels/s: the pixels every rank processed over the slowest
+    rank's time (replicas: each rank runs its own images, weak scaling)."""
+    return px_per_rank_step * world * steps / (total_ms / 1e3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -472,11 +489,8 @@ def run_ours(args, rank, world, local):
             ev[full + 1].record(cur)
             torch.cuda.synchronize()
         per = [ev[r].elapsed_time(ev[r + 1]) / n for r in range(full)]
-        total = ev[0].elapsed_time(ev[full + 1])
+        total = max_over_ranks(ev[0].elapsed_time(ev[full + 1]), dist, "cuda")
         if dist is not None:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
             dist.barrier()
         return total, per
 
@@ -490,13 +504,13 @@ def run_ours(args, rank, world, local):
         plain_steps = max(3, args.steps // 8)
         total_p, _ = timed(lambda i, s: work.run(plain, i, s), plain_steps, args.warmup, per_graph)
         plain.check(sp)
-        unfused = {"value": work.px * world * plain_steps / (total_p / 1e3) / 1e6, "unit": "Mpixels/s",
+        unfused = {"value": job_rate(work.px, world, plain_steps, total_p), "unit": "Mpixels/s",
                    "ms_per_step": total_p / plain_steps, "launches_per_step": plain.launches_per_run()}
 
     e2e_steps = max(3, min(200, args.steps // 4)) if not batched else 3
     e2e_value, h2d, d2h = work.e2e(fused, sp, args.warmup if not batched else 1, e2e_steps)
 
-    value = work.px * world * args.steps / (total_f / 1e3) / 1e6
+    value = job_rate(work.px, world, args.steps, total_f)
     launch_ms = statistics.mean(per_f)
     peak, peak_kind = peaks()
     achieved = work.alg_bytes / (launch_ms / 1e3) / 1e9
