@@ -64,6 +64,31 @@ def peaks():
         return 6800.0, "fallback"
 
 
+FP32_LANE_OPS = 152 * 128 * 2.07e9   # GB300: SMs x FP32 lanes x max SM clock (FMA = 1 op)
+
+
+def ops_per_pixel(spec):
+    """FP32 operations of the stage programs per output pixel (level-0
+    pixel; channels counted): the algorithmic ALU work of the pipeline."""
+    arith = {"add", "sub", "mul", "div", "min", "max", "neg", "abs", "sqrt"}
+    level = {}
+    total = 0.0
+    for i, st in enumerate(spec["stages"]):
+        lv = None
+        for op in st["ops"]:
+            if op[0] != "tap":
+                continue
+            src = st["inputs"][op[1]]
+            base = level.get(src, 0) if src >= 0 else 0
+            mode = op[5] if len(op) > 5 else "same"
+            lv = base + (1 if mode == "down2" else -1 if mode == "up2" else 0)
+            break
+        level[i] = lv or 0
+        n = sum(1 for op in st["ops"] if op[0] in arith)
+        total += n * st["channels"] / 4.0 ** level[i]
+    return total
+
+
 def max_over_ranks(value, dist, device):
     """The largest of the ranks' values: a job's time is its slowest rank's
     (every rank holds the result)."""
@@ -537,7 +562,13 @@ def run_ours(args, rank, world, local):
                    "tuning": tuning},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kname,
-                     "algorithmic_bytes_per_launch": work.alg_bytes // launches},
+                     "algorithmic_bytes_per_launch": work.alg_bytes // launches,
+                     # the same run against the FP32 ALU: stage-program operations per pixel
+                     # x pixels/s over the derived lane-op peak
+                     "alu": {"ops_per_px": ops_per_pixel(spec),
+                             "achieved_tops": ops_per_pixel(spec) * value / 1e6 / world,
+                             "peak_tops": FP32_LANE_OPS / 1e12,
+                             "frac": ops_per_pixel(spec) * value * 1e6 / world / FP32_LANE_OPS}},
         "unfused": unfused,
         "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches,
