@@ -504,6 +504,12 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
       n.rotate = false;
     }
   }
+  for (const Node &n : g.nodes)
+    for (const KOp &k : n.prog)
+      if (k.op == WT_OP_YPAR) g.uses_ypar = true;
+  // an even unroll keeps each unrolled step's row parity fixed (row-parity
+  // selects then fold); register windows still divide it
+  if (g.uses_ypar && U % 2) U *= 2;
   g.unroll = (int)U;
   g.max_src_window = 1;
   for (int i = 0; i < n_src; i++) g.max_src_window = std::max(g.max_src_window, g.nodes[i].window);

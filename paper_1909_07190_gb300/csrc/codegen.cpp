@@ -36,7 +36,8 @@ namespace wt {
 
 std::string CodegenKey::str() const {
   std::ostringstream s;
-  s << (plain ? "P" : "F") << (persistent ? "b" : "") << (pairs ? "x2" : "") << "|v" << vec << "|f" << frac_reg
+  s << (plain ? "P" : "F") << (persistent ? "b" : "") << (pairs ? "x2" : "") << (even_rows ? "e" : "") << "|v" << vec
+    << "|f" << frac_reg
     << "|r" << max_regs << "|w" << nw << "|c" << chunk << "|n" << nbuf << "|s";
   for (int x : stages) s << x << ",";
   s << "|i";
@@ -358,7 +359,15 @@ std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
     switch (op.op) {
       case WT_OP_CONST: st.push_back(konst(op.value)); break;
       case WT_OP_XPAR: st.push_back(konst((float)(e & 1))); break;
-      case WT_OP_YPAR: st.push_back(expr("((float)(r & 1))")); break;
+      case WT_OP_YPAR:
+        if (c.key.even_rows) {
+          // r = y_top + kb + u - delay with y_top = y0 - halo_t, y0 and kb even
+          const int par = (((u - c.g.halo_t - cn.delay) % 2) + 2) % 2;
+          st.push_back(konst((float)par));
+        } else {
+          st.push_back(expr("((float)(r & 1))"));
+        }
+        break;
       case WT_OP_TAP: {
         const int pi = op.node;
         const Node &pn = c.g.nodes[pi];

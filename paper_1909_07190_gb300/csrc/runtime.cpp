@@ -159,6 +159,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     key.chunk = L.params.chunk_rows > 0 ? L.params.chunk_rows : 8;
     key.nbuf = L.params.n_buffers > 0 ? L.params.n_buffers : 2;
     key.pairs = L.params.pairs != 0;
+    key.even_rows = L.fused && L.geom.uses_ypar && L.params.tile_h % 2 == 0;
     L.src.clear();
     L.dst.clear();
     auto loc_of = [&](int pid) -> const Loc & { return pid >= 0 ? plan.loc[pid] : plan.in_loc[-pid - 1]; };
@@ -414,7 +415,8 @@ Workspace &workspace(Pipeline &p, int64_t bytes) {
 // ty1 rows below it (the last one clipped by the image).
 void split_tiles(const Launch &L, KernelArgs &a, int resident_warps) {
   const int T1 = std::max(1, L.params.tile_h);
-  const int T2 = std::max(4, T1 / 2);
+  // tiles of groups folding the row parity start on even rows: even heights
+  const int T2 = std::max(4, L.key.even_rows ? T1 / 2 / 2 * 2 : T1 / 2);
   if (!L.fused || T2 >= T1 || L.params.tile_split == 0) return;
   const int C = L.geom.channels;
   const int per_row = std::max(1, L.tiles_x * C);

@@ -124,6 +124,7 @@ struct GroupGeom {
   int max_delay = 0;
   int unroll = 1;
   int max_src_window = 1;
+  bool uses_ypar = false;      // some node selects on the row parity
   int node_of(int id, int chan) const;
   int gather_of(int id, int chan, int mode) const;
   int n_gather = 0;            // gather sources (after the staged sources)
@@ -242,6 +243,9 @@ struct CodegenKey {
   bool plain = false;
   bool persistent = false;
   bool pairs = true;  // packed f32x2 arithmetic
+  // every tile starts on an even row and the unroll is even: the row parity
+  // of each unrolled step is a compile-time constant
+  bool even_rows = false;
   std::string str() const;
 };
 
