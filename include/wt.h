@@ -172,6 +172,15 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
 
 /* --------------------------------------------------- cost model (Sec. 6) -- */
 
+/* Sec. 6 preprocessing: runs each stage's body alone in a one-thread
+ * micro-kernel on the current GPU and records its time per iteration
+ * (ns_per_iter[s]) and register count (regs[s]); either array (n_stages
+ * entries) may be null.  The pipeline keeps the results and the analytic
+ * cost model, the learned model's features and the measured search use
+ * them from then on (before, they use estimates from the stage programs).
+ * WT_ECUDA without a GPU.                                                  */
+wt_status wt_preprocess(wt_pipeline *p, double *ns_per_iter, int32_t *regs);
+
 /* GPU quantities the cost function uses (Table 1).                         */
 typedef struct {
   int32_t nsms, cores_per_sm;

@@ -163,6 +163,7 @@ std::string micro_source(const Pipeline &p, int sid, const std::string &name) {
 
 std::vector<StageStats> stage_stats(const Pipeline &p, bool measure) {
   std::vector<StageStats> r(p.stages.size());
+  const bool have = p.pre_ns.size() == p.stages.size() && p.pre_regs.size() == p.stages.size();
   for (size_t s = 0; s < p.stages.size(); s++) {
     int ops = 0;
     for (const Op &op : p.stages[s].ops)
@@ -170,6 +171,11 @@ std::vector<StageStats> stage_stats(const Pipeline &p, bool measure) {
     r[s].ns_per_iter = 0.5 + 0.5 * ops;  // estimate when not measured
     r[s].regs = 24;
     r[s].measured = false;
+    if (have) {  // measured by an earlier preprocessing run
+      r[s].ns_per_iter = p.pre_ns[s];
+      r[s].regs = p.pre_regs[s];
+      r[s].measured = true;
+    }
   }
   if (!measure) return r;
   int dev = 0;
@@ -202,6 +208,8 @@ std::vector<StageStats> stage_stats(const Pipeline &p, bool measure) {
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     r[s].ns_per_iter = (double)ms * 1e6 / iters;
+    int regs = 0;
+    if (drv.funcGetAttribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, f) == CUDA_SUCCESS && regs > 0) r[s].regs = regs;
     drv.moduleUnload(mod);
     r[s].measured = true;
   }

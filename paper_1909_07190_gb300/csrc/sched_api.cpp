@@ -149,6 +149,28 @@ wt_status wt_cost_group(wt_pipeline *p, int32_t first_stage, int32_t n_stages, c
   });
 }
 
+wt_status wt_preprocess(wt_pipeline *p, double *ns_per_iter, int32_t *regs) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    std::lock_guard<std::mutex> lk(p->mu);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      wt::fail(WT_ECUDA, "preprocessing needs a GPU");
+    }
+    auto st = wt::stage_stats(*p, true);
+    p->pre_ns.resize(st.size());
+    p->pre_regs.resize(st.size());
+    for (size_t s = 0; s < st.size(); s++) {
+      if (!st[s].measured) wt::fail(WT_ECUDA, "a stage's micro-kernel did not run");
+      p->pre_ns[s] = st[s].ns_per_iter;
+      p->pre_regs[s] = st[s].regs;
+      if (ns_per_iter) ns_per_iter[s] = st[s].ns_per_iter;
+      if (regs) regs[s] = st[s].regs;
+    }
+  });
+}
+
 wt_status wt_cost_weights(const double *set7, double *get7) {
   return guard([&] {
     if (set7) {

@@ -217,6 +217,10 @@ struct Pipeline {
   std::shared_ptr<Workspace> ws;
   std::shared_ptr<BatchCache> batch;
   uint64_t hash = 0;
+  // Sec. 6 preprocessing results (wt_preprocess): per stage, ns per
+  // iteration of its body alone and registers; empty until measured
+  std::vector<double> pre_ns;
+  std::vector<int> pre_regs;
 };
 
 // ir.cpp

@@ -91,6 +91,7 @@ SIGNATURES = [
     ("wt_min_transactions", _i32, [_P(_i64), _i32, _i32, _i32, _P(_i64)]),
     ("wt_cost_group", _i32, [_vp, _i32, _i32, _P(wt_group_params), _i32, _i32, _i32, _i32,
                              _P(wt_gpu_config), _P(wt_cost_info)]),
+    ("wt_preprocess", _i32, [_vp, _P(ctypes.c_double), _P(_i32)]),
     ("wt_cost_weights", _i32, [_P(ctypes.c_double), _P(ctypes.c_double)]),
     ("wt_run", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
     ("wt_run_host", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _vp]),
@@ -330,6 +331,14 @@ class Pipeline:
         check(load().wt_schedule_tune(self.h, ia, len(inputs), oa, len(outputs), n_images, max_variants, reps,
                                       stream, ctypes.byref(ms), ctypes.byref(nt)))
         return ms.value, nt.value
+
+    def preprocess(self):
+        """Sec. 6 micro-kernels: (ns per iteration, registers) per stage."""
+        n = len(self.spec["stages"])
+        ns = (ctypes.c_double * n)()
+        regs = (_i32 * n)()
+        check(load().wt_preprocess(self.h, ns, regs))
+        return list(ns), list(regs)
 
     def time_launches(self, inputs, outputs, reps=20, stream=None):
         """[(first_stage, n_stages, fused, ms)] per launch of one run."""

@@ -68,3 +68,16 @@ def test_prepare_compiles_without_running():
     y = wt.DeviceImage(1, 64, 64)
     p = wt.Pipeline(spec)
     p.prepare([(None, dict(tile_h=8, frac_reg=f)) for f in (0.0, 0.5, 1.0)], [x.image()], [y.image()])
+
+
+def test_preprocess_stage_microkernels():
+    """Sec. 6 preprocessing: each stage's body timed alone; heavier stage
+    programs take longer per iteration; the cost model then uses them."""
+    from paper_1909_07190_gb300 import wt
+    p = wt.Pipeline(P.harris())
+    ns, regs = p.preprocess()
+    assert len(ns) == 11 and all(t > 0 for t in ns) and all(r >= 1 for r in regs)
+    # Ix (six weighted taps) costs more per iteration than Ixx (one product)
+    assert ns[0] > ns[2]
+    c = p.cost_group(0, 11, dict(tile_h=14), 128, 1024, 1024)
+    assert c["feasible"] and c["cost"] > 0

@@ -183,3 +183,15 @@ def test_launch_count_with_per_stage_groups():
     assert p.launches_per_run() == 4 * 3 + 6
     p.schedule(groups=P.blend_groups())
     assert p.launches_per_run() == 10
+
+
+def test_preprocess_needs_a_gpu():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    p = wt.Pipeline(P.sharpen())
+    with pytest.raises(wt.WtError):
+        p.preprocess()
