@@ -1,5 +1,6 @@
 // Fiber runtime of the kernel emulator (see wt_emu.h): one ucontext fiber
-// per lane, lanes of a warp interleaved at warp collectives.
+// per thread of a block; lanes of a warp meet at warp collectives, all
+// threads of the block at block barriers.
 #include <sys/mman.h>
 #include <ucontext.h>
 
@@ -7,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "wt_emu.h"
@@ -21,65 +23,89 @@ struct Lane {
   bool done = false;
   EmuDim tid{0, 0, 0};
 };
+// Per warp: the state of the warp collective in progress.
+struct Warp {
+  int arrived = 0, gen = 0, kind = 0, done = 0, size = 32;
+  float fv[32], fres[32];
+  int iv[32], ires[32], arg[32];
+};
 ucontext_t g_main;
-Lane g_lanes[32];
+std::vector<Lane> g_lanes;  // every thread of the block being run
+std::vector<Warp> g_warps;
 int g_cur = 0;
+int g_block_threads = 0, g_block_done = 0, g_bar_arrived = 0, g_bar_gen = 0;
 EmuDim g_bidx{0, 0, 0}, g_bdim{32, 1, 1}, g_gdim{1, 1, 1};
 void (*g_kernel)(WtArgs) = nullptr;
 const WtArgs *g_args = nullptr;
-// collective state
-int g_arrived = 0, g_gen = 0, g_kind = 0, g_done = 0;
-float g_fv[32], g_fres[32];
-int g_iv[32], g_ires[32], g_arg[32];
-bool g_is_int = false;
 std::string g_fail;
 
 void trampoline() {
   g_kernel(*g_args);
-  g_lanes[g_cur].done = true;
-  g_done++;
-  swapcontext(&g_lanes[g_cur].ctx, &g_main);
+  Lane &L = g_lanes[g_cur];
+  L.done = true;
+  g_warps[L.tid.x / 32].done++;
+  g_block_done++;
+  swapcontext(&L.ctx, &g_main);
 }
 
-void complete() {
-  for (int l = 0; l < 32; l++) {
+void complete(Warp &W) {
+  for (int l = 0; l < W.size; l++) {
     int src = l;
-    if (g_kind == 0) src = g_arg[l] & 31;
-    else if (g_kind == 1) src = l - g_arg[l] < 0 ? l : l - g_arg[l];
-    else if (g_kind == 2) src = l + g_arg[l] > 31 ? l : l + g_arg[l];
-    if (g_kind == 3) {  // all
+    if (W.kind == 0) src = W.arg[l] & 31;
+    else if (W.kind == 1) src = l - W.arg[l] < 0 ? l : l - W.arg[l];
+    else if (W.kind == 2) src = l + W.arg[l] > 31 ? l : l + W.arg[l];
+    if (src >= W.size) src = l;
+    if (W.kind == 3) {  // all
       int all = 1;
-      for (int m = 0; m < 32; m++) all &= g_iv[m] != 0;
-      g_ires[l] = all;
-    } else if (g_kind == 4) {  // syncwarp
-      g_ires[l] = 0;
+      for (int m = 0; m < W.size; m++) all &= W.iv[m] != 0;
+      W.ires[l] = all;
+    } else if (W.kind == 4) {  // syncwarp
+      W.ires[l] = 0;
     } else {
-      g_fres[l] = g_fv[src];
-      g_ires[l] = g_iv[src];
+      W.fres[l] = W.fv[src];
+      W.ires[l] = W.iv[src];
     }
   }
 }
 
-// Posts this lane's contribution; returns once all 32 lanes have posted.
+Warp &my_warp() { return g_warps[g_lanes[g_cur].tid.x / 32]; }
+
+// Posts this lane's contribution; returns once every lane of its warp has.
 void collective(int kind) {
-  int lane = (int)(g_lanes[g_cur].tid.x & 31);
-  if (g_arrived == 0) g_kind = kind;
-  else if (g_kind != kind) {
-    g_fail = "lanes reached different warp collectives";
-  }
-  g_arrived++;
-  int gen = g_gen;
-  if (g_arrived == 32) {
-    complete();
-    g_arrived = 0;
-    g_gen++;
+  Warp &W = my_warp();
+  if (W.arrived == 0) W.kind = kind;
+  else if (W.kind != kind) g_fail = "lanes reached different warp collectives";
+  W.arrived++;
+  int gen = W.gen;
+  if (W.arrived == W.size) {
+    complete(W);
+    W.arrived = 0;
+    W.gen++;
     return;
   }
-  (void)lane;
-  while (g_gen == gen) {
-    if (g_arrived + g_done >= 32 && g_arrived < 32) {
+  while (W.gen == gen) {
+    if (W.arrived + W.done >= W.size && W.arrived < W.size) {
       g_fail = "warp collective with exited lanes";
-      g_gen++;  // release, the run is failed anyway
+      W.gen++;  // release, the run is failed anyway
+      break;
+    }
+    swapcontext(&g_lanes[g_cur].ctx, &g_main);
+  }
+}
+
+// Block-wide barrier: returns once every thread of the block has arrived.
+void block_barrier() {
+  g_bar_arrived++;
+  int gen = g_bar_gen;
+  if (g_bar_arrived == g_block_threads) {
+    g_bar_arrived = 0;
+    g_bar_gen++;
+    return;
+  }
+  while (g_bar_gen == gen) {
+    if (g_bar_arrived + g_block_done >= g_block_threads && g_bar_arrived < g_block_threads) {
+      g_fail = "block barrier with exited threads";
+      g_bar_gen++;
       break;
     }
     swapcontext(&g_lanes[g_cur].ctx, &g_main);
@@ -117,25 +143,29 @@ void wt_emu_check(const void *p, long bytes, const char *what) {
 
 float wt_emu_shfl(float v, int arg, int kind) {
   int lane = (int)(g_lanes[g_cur].tid.x & 31);
-  g_fv[lane] = v;
-  g_arg[lane] = arg;
+  Warp &W = my_warp();
+  W.fv[lane] = v;
+  W.arg[lane] = arg;
   collective(kind);
-  return g_fres[lane];
+  return W.fres[lane];
 }
 int wt_emu_shfl_i(int v, int arg, int kind) {
   int lane = (int)(g_lanes[g_cur].tid.x & 31);
-  g_iv[lane] = v;
-  g_arg[lane] = arg;
+  Warp &W = my_warp();
+  W.iv[lane] = v;
+  W.arg[lane] = arg;
   collective(kind);
-  return g_ires[lane];
+  return W.ires[lane];
 }
 int wt_emu_all(int pred) {
   int lane = (int)(g_lanes[g_cur].tid.x & 31);
-  g_iv[lane] = pred;
+  Warp &W = my_warp();
+  W.iv[lane] = pred;
   collective(3);
-  return g_ires[lane];
+  return W.ires[lane];
 }
 void wt_emu_syncwarp() { collective(4); }
+void wt_emu_syncthreads() { block_barrier(); }
 void wt_emu_yield() { swapcontext(&g_lanes[g_cur].ctx, &g_main); }
 
 // Runs the whole grid, one warp at a time.  Returns 0, or -1 with a message.
@@ -149,9 +179,14 @@ int wt_emu_run(void *kernel, const void *args, int gx, int gy, int gz, int block
     snprintf(msg, msg_cap, "shared memory request too large");
     return -1;
   }
-  for (int l = 0; l < 32; l++)
+  if (block < 1 || block > 1024) {
+    snprintf(msg, msg_cap, "bad block size");
+    return -1;
+  }
+  if ((int)g_lanes.size() < block) g_lanes.resize(block);
+  for (int l = 0; l < block; l++)
     if (!g_lanes[l].stack) {
-      void *p = mmap(nullptr, kStack, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+      void *p = mmap(nullptr, kStack, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS | MAP_NORESERVE, -1, 0);
       if (p == MAP_FAILED) {
         snprintf(msg, msg_cap, "mmap failed");
         return -1;
@@ -160,34 +195,38 @@ int wt_emu_run(void *kernel, const void *args, int gx, int gy, int gz, int block
     }
   g_bdim = EmuDim{(unsigned)block, 1, 1};
   g_gdim = EmuDim{(unsigned)gx, (unsigned)gy, (unsigned)gz};
+  const int nwarps = (block + 31) / 32;
   for (int bz = 0; bz < gz; bz++)
     for (int by = 0; by < gy; by++)
       for (int bx = 0; bx < gx; bx++) {
         g_bidx = EmuDim{(unsigned)bx, (unsigned)by, (unsigned)bz};
         memset(wt_emu_smem_array, 0xA5, (size_t)smem);  // poison
-        for (int w = 0; w < (block + 31) / 32; w++) {
-          g_arrived = 0;
-          g_done = 0;
-          for (int l = 0; l < 32; l++) {
-            Lane &L = g_lanes[l];
-            L.done = false;
-            L.tid = EmuDim{(unsigned)(w * 32 + l), 0, 0};
-            getcontext(&L.ctx);
-            L.ctx.uc_stack.ss_sp = L.stack;
-            L.ctx.uc_stack.ss_size = kStack;
-            L.ctx.uc_link = nullptr;
-            makecontext(&L.ctx, trampoline, 0);
+        // every thread of the block is a fiber: warps interleave at warp
+        // collectives and block barriers
+        g_warps.assign(nwarps, Warp());
+        for (int w = 0; w < nwarps; w++) g_warps[w].size = std::min(32, block - 32 * w);
+        g_block_threads = block;
+        g_block_done = 0;
+        g_bar_arrived = 0;
+        for (int l = 0; l < block; l++) {
+          Lane &L = g_lanes[l];
+          L.done = false;
+          L.tid = EmuDim{(unsigned)l, 0, 0};
+          getcontext(&L.ctx);
+          L.ctx.uc_stack.ss_sp = L.stack;
+          L.ctx.uc_stack.ss_size = kStack;
+          L.ctx.uc_link = nullptr;
+          makecontext(&L.ctx, trampoline, 0);
+        }
+        while (g_block_done < block) {
+          for (int l = 0; l < block; l++) {
+            if (g_lanes[l].done) continue;
+            g_cur = l;
+            swapcontext(&g_main, &g_lanes[l].ctx);
           }
-          while (g_done < 32) {
-            for (int l = 0; l < 32; l++) {
-              if (g_lanes[l].done) continue;
-              g_cur = l;
-              swapcontext(&g_main, &g_lanes[l].ctx);
-            }
-            if (!g_fail.empty()) {
-              snprintf(msg, msg_cap, "%s (block %d,%d,%d warp %d)", g_fail.c_str(), bx, by, bz, w);
-              return -1;
-            }
+          if (!g_fail.empty()) {
+            snprintf(msg, msg_cap, "%s (block %d,%d,%d)", g_fail.c_str(), bx, by, bz);
+            return -1;
           }
         }
       }

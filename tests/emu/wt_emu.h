@@ -73,6 +73,7 @@ float wt_emu_shfl(float v, int src_lane, int kind);  // kind 0 idx, 1 up, 2 down
 int wt_emu_shfl_i(int v, int src_lane, int kind);
 int wt_emu_all(int pred);
 void wt_emu_syncwarp();
+void wt_emu_syncthreads();
 unsigned char *wt_emu_smem();
 void wt_emu_fail(const char *msg);
 void wt_emu_check(const void *p, long bytes, const char *what);
@@ -90,6 +91,7 @@ static inline float __shfl_up_sync(unsigned, float v, int d) { return wt_emu_shf
 static inline float __shfl_down_sync(unsigned, float v, int d) { return wt_emu_shfl(v, d, 2); }
 static inline int __all_sync(unsigned, int p) { return wt_emu_all(p); }
 static inline void __syncwarp(unsigned = 0xffffffffu) { wt_emu_syncwarp(); }
+static inline void __syncthreads() { wt_emu_syncthreads(); }
 static inline int atomicAdd(int *p, int v) { int o = *p; *p += v; return o; }
 static inline int atomicExch(int *p, int v) { int o = *p; *p = v; return o; }
 static inline void __threadfence() {}
