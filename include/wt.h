@@ -129,6 +129,14 @@ typedef struct {
 #define WT_FLAG_NO_PAIRS 1      /* scalar FP32 instead of packed f32x2 pairs     */
 #define WT_FLAG_NO_TILE_SPLIT 2 /* one tile height (no short last round)         */
 #define WT_FLAG_PLAIN 4         /* the group's stages as per-stage kernels       */
+/* One overlapped tile per thread block (Sec. 3, Fig. 3: the tiling of the
+ * systems the paper compares with): each block computes a (32 vec) x tile_h
+ * output tile, every stage of the group over its tile-plus-halo region in
+ * shared memory, block barriers between stages; vec may be 1, 2, 4 or 8;
+ * warps_per_block sets the block size; frac_reg, chunk_rows, n_buffers and
+ * the other flags are ignored.  Groups that read other levels
+ * (down/up-sampling taps into the group) return WT_EUNSUPPORTED at run. */
+#define WT_FLAG_OTPTB 8
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */

@@ -77,7 +77,8 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         if (q.tile_h < 1 || q.tile_h > 4096) fail(WT_EINVAL, "tile_h out of range");
         if (q.warps_per_block < 1 || q.warps_per_block > 16) fail(WT_EINVAL, "warps_per_block out of range");
         if (!(q.frac_reg >= 0.f && q.frac_reg <= 1.f)) fail(WT_EINVAL, "frac_reg out of [0,1]");
-        if (q.vec != 0 && q.vec != 4 && q.vec != 8) fail(WT_EINVAL, "vec must be 0, 4 or 8");
+        if (q.vec != 0 && q.vec != 4 && q.vec != 8 && !((q.flags & WT_FLAG_OTPTB) && (q.vec == 1 || q.vec == 2)))
+          fail(WT_EINVAL, "vec must be 0, 4 or 8 (1 or 2 with WT_FLAG_OTPTB)");
         if (q.max_regs < 0 || q.max_regs > 255) fail(WT_EINVAL, "max_regs out of range");
         if (q.chunk_rows < 0 || q.chunk_rows > 64) fail(WT_EINVAL, "chunk_rows out of range");
         if (q.n_buffers < 0 || q.n_buffers > 8) fail(WT_EINVAL, "n_buffers out of range");
@@ -88,8 +89,10 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.max_regs = q.max_regs;
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
-        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN)) fail(WT_EINVAL, "unknown flags");
+        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB))
+          fail(WT_EINVAL, "unknown flags");
         r.plain = (q.flags & WT_FLAG_PLAIN) ? 1 : 0;
+        r.otptb = (q.flags & WT_FLAG_OTPTB) ? 1 : 0;
         r.pairs = (q.flags & WT_FLAG_NO_PAIRS) ? 0 : 1;
         r.tile_split = (q.flags & WT_FLAG_NO_TILE_SPLIT) ? 0 : 1;
       }
@@ -182,7 +185,7 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].chunk_rows = r.chunk_rows;
         params[g].n_buffers = r.n_buffers;
         params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT) |
-                          (r.plain ? WT_FLAG_PLAIN : 0);
+                          (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0);
       }
   });
 }
@@ -361,7 +364,7 @@ wt_status wt_debug_kernel_ws(wt_pipeline *p, int32_t launch_index, const wt_imag
       wt::KernelArgs a;
       wt::fill_args(*p, plan, L, (char *)workspace, a, false);
       // as on the GPU with few resident warps: exercises both tile heights
-      if (L.fused) wt::split_tiles(L, a, 4 * L.key.nw);
+      if (L.fused && !L.key.otptb) wt::split_tiles(L, a, 4 * L.key.nw);
       memcpy(args, &a, sizeof a);
     }
     if (launch) {
@@ -469,7 +472,7 @@ wt_status wt_debug_layout(wt_pipeline *p, int32_t launch_index, const wt_image *
     wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
     if (launch_index < 0 || launch_index >= (int)plan.launches.size()) wt::fail(WT_EINVAL, "launch index");
     const wt::Launch &L = plan.launches[launch_index];
-    if (!L.fused) wt::fail(WT_EINVAL, "not a fused launch");
+    if (!L.fused || L.key.otptb) wt::fail(WT_EINVAL, "not a warp-tiled group launch");
     const wt::FusedLayout &F = L.layout;
     std::vector<int32_t> v = {F.warp_bytes, F.bar_off, F.chunk, F.nbuf, F.V, F.out_w, (int32_t)F.boxw.size()};
     for (size_t s = 0; s < F.boxw.size(); s++) {

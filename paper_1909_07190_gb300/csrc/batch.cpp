@@ -50,7 +50,8 @@ BatchPlan build_batch(Pipeline &p, const wt_image *in, const wt_image *out, int 
     const RunPlan &r0 = b.img[0];
     if (i == 0) {
       for (const Launch &L : r.launches)
-        if (!L.fused) fail(WT_EUNSUPPORTED, "batched runs need a fused schedule whose groups all fuse");
+        if (!L.fused || L.key.otptb)
+          fail(WT_EUNSUPPORTED, "batched runs need a warp-tiled schedule whose groups all fuse");
     } else {
       bool same = r.launches.size() == r0.launches.size();
       for (size_t l = 0; same && l < r.launches.size(); l++) same = r.launches[l].kname == r0.launches[l].kname;

@@ -44,6 +44,7 @@ std::string CodegenKey::str() const {
   for (int x : src_dtypes) s << x;
   s << "|o";
   for (int x : dst_dtypes) s << x;
+  if (otptb) s << "|B" << tbx << "x" << tby;
   return s.str();
 }
 

@@ -182,6 +182,30 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
         L.dst.push_back(s);
         key.dst_dtypes.push_back(plan.loc[s].dtype);
       }
+      if (L.params.otptb) {
+        // one block per overlapped tile of (32 vec) x tile_h outputs
+        if (L.geom.n_gather > 0) fail(WT_EUNSUPPORTED, "block tiling of groups that read other levels");
+        key.otptb = true;
+        key.vec = L.params.vec > 0 ? L.params.vec : 4;
+        key.tbx = 32 * key.vec;
+        key.tby = std::max(1, L.params.tile_h);
+        key.frac_reg = 1.f;
+        key.chunk = key.nbuf = 0;
+        key.pairs = key.even_rows = false;
+        level_dims(plan.W, plan.H, L.geom.level, &L.W, &L.H);
+        const int64_t gx = (L.W + key.tbx - 1) / key.tbx, gy = (L.H + key.tby - 1) / key.tby;
+        if (gy > 65535 || L.geom.channels > 65535) fail(WT_EUNSUPPORTED, "too many block tiles");
+        L.tiles_x = (int)gx; L.tiles_y = (int)gy;
+        L.n_tiles = (int)(gx * gy * L.geom.channels);
+        L.block = 32 * key.nw;
+        L.grid[0] = (unsigned)gx;
+        L.grid[1] = (unsigned)gy;
+        L.grid[2] = (unsigned)L.geom.channels;
+        L.smem = otptb_layout(L.geom, key).smem;
+        if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "block tile needs more than 227 KB of shared memory");
+        L.kname = kernel_name(p, key, true);
+        continue;
+      }
       key.vec = pick_vec(L.params, key.src_dtypes);
       if (key.vec != 4) L.geom = analyze_group(p, L.stages, key.vec, L.params.frac_reg, 4);
       L.layout = fused_layout(L.geom, key);
@@ -237,11 +261,15 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (!fused) h = fnv1a(kPlainVersion, sizeof kPlainVersion, h);
   static const char kGatherVersion[] = "wt-gather-2";  // kernels reading other levels
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
+  static const char kOtptbVersion[] = "wt-otptb-1";  // the block-tile kernel's own changes
+  if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
+  if (key.otptb) return std::string("wt_otptb_") + hx;
   return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }
 
 std::string launch_source(const Pipeline &p, const Launch &L) {
+  if (L.key.otptb) return emit_otptb(p, L.geom, L.key, L.kname);
   if (L.fused) return emit_fused(p, L.geom, L.key, L.kname);
   return emit_plain(p, L.stages[0], L.key, L.kname);
 }
@@ -264,6 +292,7 @@ void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws
     SrcDesc &d = a.src[i];
     d.ptr = ptr_of(l);
     d.W = l.W; d.H = l.H; d.C = l.C; d.dtype = l.dtype; d.pitch = l.pitch; d.plane = l.plane;
+    if (L.key.otptb) continue;                    // block tiles: plain loads
     if (L.fused && (int)i >= L.n_ring) continue;  // gather source: plain loads, no tensor map
     if (L.fused && !encode_tmaps) {
       // Introspection only: a plain description of the box in place of the
@@ -461,12 +490,12 @@ void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string
                "cuOccupancyMaxActiveBlocksPerMultiprocessor");
       check_rt(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
       if (per_sm < 1) fail(WT_EUNSUPPORTED, "group kernel cannot be resident (registers/shared memory)");
-      L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
+      if (!L.key.otptb) L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
       L.resident_blocks_per_sm = per_sm;
     }
     KernelArgs a;
-    fill_args(p, plan, L, w.base, a, L.fused);
-    if (L.fused) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
+    fill_args(p, plan, L, w.base, a, L.fused && !L.key.otptb);
+    if (L.fused && !L.key.otptb) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
     a.err = w.err;
     a.queue = queue_counters(w.err, li++);
     launch(L, k, a, stream);

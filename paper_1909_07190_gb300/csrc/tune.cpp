@@ -129,7 +129,7 @@ void precompile(Pipeline &p, const std::vector<Schedule> &cands, const wt_image 
     try {
       RunPlan plan = build_plan(p, in, n_in, out, n_out);
       for (Launch &L : plan.launches) {
-        if (persistent && L.fused) {
+        if (persistent && L.fused && !L.key.otptb) {
           L.key.persistent = true;
           L.kname = kernel_name(p, L.key, true, L.geom.n_gather > 0);
         }

@@ -58,6 +58,8 @@ struct GroupParams {
   int tile_split = 1;  // short tiles for the last round of the tile queue
   int pairs = 1;       // packed f32x2 arithmetic where taps align
   int plain = 0;       // run the group's stages as per-stage kernels
+  int otptb = 0;       // one overlapped tile per thread block (the baseline
+                       // tiling the paper compares against)
 };
 
 struct Schedule {
@@ -250,6 +252,10 @@ struct CodegenKey {
   // every tile starts on an even row and the unroll is even: the row parity
   // of each unrolled step is a compile-time constant
   bool even_rows = false;
+  // one overlapped tile of tbx x tby outputs per thread block, stages in
+  // shared memory between block barriers
+  bool otptb = false;
+  int tbx = 0, tby = 0;
   std::string str() const;
 };
 
@@ -274,6 +280,17 @@ FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key);
 std::string emit_fused(const Pipeline &p, const GroupGeom &g, const CodegenKey &key,
                        const std::string &kname);
 std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key,
+                       const std::string &kname);
+// otptb.cpp: block-tile kernel of a fused group.  Per node, its region
+// relative to the tile origin (rx, ry, rw x rh points) and its FP32 buffer's
+// byte offset in dynamic shared memory (buffers of dead nodes are reused).
+struct OtptbLayout {
+  int tbx = 128, tby = 16;
+  std::vector<int> rx, ry, rw, rh, off;
+  int smem = 0;
+};
+OtptbLayout otptb_layout(const GroupGeom &g, const CodegenKey &key);
+std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &key,
                        const std::string &kname);
 // Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
 struct PlainSrc {

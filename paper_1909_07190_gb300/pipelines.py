@@ -227,18 +227,19 @@ def blend_schedule(levels: int = 6) -> tuple:
     return groups, params
 
 
-def blur3() -> dict:
+def blur3(channels: int = 1) -> dict:
     """The paper's running example (Fig. 2): blurx = 3-tap mean along x,
-    blury = 3-tap mean of blurx along y."""
-    b = Builder("blur", [1])
+    blury = 3-tap mean of blurx along y (per plane; the motivating timing
+    of Sec. 3 uses 3 planes)."""
+    b = Builder("blur", [channels])
     inp = input_id(0)
-    bx = b.stage("blurx", (ref(inp, -1, 0) + ref(inp) + ref(inp, 1, 0)) / 3.0)
-    by = b.stage("blury", (ref(bx, 0, -1) + ref(bx) + ref(bx, 0, 1)) / 3.0)
+    bx = b.stage("blurx", (ref(inp, -1, 0) + ref(inp) + ref(inp, 1, 0)) / 3.0, channels)
+    by = b.stage("blury", (ref(bx, 0, -1) + ref(bx) + ref(bx, 0, 1)) / 3.0, channels)
     b.output(by)
     return b.build()
 
 
 def by_name(name: str) -> dict:
     table = {"sharpen": sharpen, "harris": harris, "harris_raw": lambda: harris(False),
-             "blend": blend, "blur": blur3}
+             "blend": blend, "blur": blur3, "blur_rgb": lambda: blur3(3)}
     return table[name]()
