@@ -45,6 +45,7 @@ std::string CodegenKey::str() const {
   s << "|o";
   for (int x : dst_dtypes) s << x;
   if (otptb) s << "|B" << tbx << "x" << tby;
+  if (down) s << "|D" << tby;
   return s.str();
 }
 

@@ -235,6 +235,22 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       L.dst.push_back(s);
       key.dst_dtypes.push_back(plan.loc[s].dtype);
       level_dims(plan.W, plan.H, p.stages[s].level, &L.W, &L.H);
+      const int vo = L.params.vec == 8 ? 8 : 4;
+      if (p.sched.exec == WT_EXEC_FUSED && down_streamable(down_form(p, s), vo)) {
+        // separable down-sampling: producer rows streamed through warps
+        key.down = true;
+        key.vec = vo;
+        key.tby = std::max(1, L.params.tile_h);
+        L.block = 32 * key.nw;
+        const int64_t wy = (L.H + key.tby - 1) / key.tby;
+        L.grid[0] = (unsigned)((L.W + 32 * vo - 1) / (32 * vo));
+        L.grid[1] = (unsigned)((wy + key.nw - 1) / key.nw);
+        L.grid[2] = (unsigned)p.stages[s].channels;
+        if (L.grid[1] > 65535 || L.grid[2] > 65535) fail(WT_EUNSUPPORTED, "image too tall for the down-sampling kernel");
+        L.smem = 0;
+        L.kname = kernel_name(p, key, false);
+        continue;
+      }
       L.block = 128;
       L.grid[0] = (unsigned)(((L.W + 7) / 8 + 127) / 128);
       L.grid[1] = (unsigned)L.H;
@@ -263,13 +279,17 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
   static const char kOtptbVersion[] = "wt-otptb-1";  // the block-tile kernel's own changes
   if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
+  static const char kDownVersion[] = "wt-down-1";  // the down-sampling kernel's own changes
+  if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;
+  if (key.down) return std::string("wt_down_") + hx;
   return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }
 
 std::string launch_source(const Pipeline &p, const Launch &L) {
   if (L.key.otptb) return emit_otptb(p, L.geom, L.key, L.kname);
+  if (L.key.down) return emit_down(p, L.stages[0], L.key, L.kname);
   if (L.fused) return emit_fused(p, L.geom, L.key, L.kname);
   return emit_plain(p, L.stages[0], L.key, L.kname);
 }

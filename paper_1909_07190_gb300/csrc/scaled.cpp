@@ -1,0 +1,289 @@
+// Scaled streaming kernel of a down-sampling stage: a stage whose taps all
+// read one producer one level finer (P(2x + dx, 2y + dy), Sec. 2.3) with a
+// rank-one (separable) linear weight pattern, the pyramids' reduce step.
+//
+// A warp owns a strip of 32 VO output columns and T output rows and streams
+// the producer's rows through it at twice the output rate (the streaming of
+// Sec. 4 with the consumer one level coarser): each producer row is loaded
+// once, as 2 VO coalesced values per lane, filtered along x at stride 2 (the
+// taps left and right of a lane's segment come from its neighbours by warp
+// shuffles), and added, weighted, into the accumulators of the output rows
+// it contributes to; an output row is stored once its last row is in.  The
+// accumulators form a ring whose slots are fixed at compile time by
+// unrolling the step loop by the ring length.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <sstream>
+
+#include "wt_internal.hpp"
+
+namespace wt {
+
+namespace {
+
+const char *tn(int dtype) { return dtype == WT_F32 ? "f32" : dtype == WT_F16 ? "f16" : "bf16"; }
+
+std::string lit(double v) {
+  char b[64];
+  snprintf(b, sizeof b, "%.9g", (double)(float)v);
+  std::string r(b);
+  if (r.find_first_of(".e") == std::string::npos) r += ".0";
+  return "(" + r + "f)";
+}
+
+struct Lin {
+  bool ok = true, is_const = true;
+  double c = 0;
+  std::map<std::pair<int, int>, double> t;  // (dx, dy) -> weight
+};
+
+Lin add(const Lin &a, const Lin &b, double s) {
+  Lin r;
+  r.ok = a.ok && b.ok;
+  r.is_const = a.is_const && b.is_const;
+  r.c = a.c + s * b.c;
+  r.t = a.t;
+  for (auto &kv : b.t) r.t[kv.first] += s * kv.second;
+  return r;
+}
+
+Lin scale(Lin a, double s) {
+  a.c *= s;
+  for (auto &kv : a.t) kv.second *= s;
+  return a;
+}
+
+}  // namespace
+
+DownForm down_form(const Pipeline &p, int sid) {
+  DownForm f;
+  const Stage &S = p.stages[sid];
+  if (S.level < 1) return f;
+  int slot = -1, chan = -2;
+  Lin bad;
+  bad.ok = false;
+  std::vector<Lin> st;
+  for (const Op &op : S.ops) {
+    switch (op.op) {
+      case WT_OP_CONST: {
+        Lin l;
+        l.c = op.value;
+        st.push_back(l);
+      } break;
+      case WT_OP_TAP: {
+        if (op.mode != WT_TAP_DOWN2) return f;
+        const int pid = S.inputs[op.slot];
+        const int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
+        const int spec = pc == 1 ? 0 : op.chan;
+        if (slot < 0) {
+          slot = op.slot;
+          chan = spec;
+        } else if (slot != op.slot || chan != spec) {
+          return f;
+        }
+        Lin l;
+        l.is_const = false;
+        l.t[{op.dx, op.dy}] = 1.0;
+        st.push_back(l);
+      } break;
+      case WT_OP_ADD: case WT_OP_SUB: {
+        Lin b = st.back(); st.pop_back();
+        Lin a = st.back(); st.pop_back();
+        st.push_back(add(a, b, op.op == WT_OP_ADD ? 1.0 : -1.0));
+      } break;
+      case WT_OP_MUL: {
+        Lin b = st.back(); st.pop_back();
+        Lin a = st.back(); st.pop_back();
+        if (!a.ok || !b.ok) st.push_back(bad);
+        else if (a.is_const) st.push_back(scale(b, a.c));
+        else if (b.is_const) st.push_back(scale(a, b.c));
+        else st.push_back(bad);
+      } break;
+      case WT_OP_DIV: {
+        Lin b = st.back(); st.pop_back();
+        Lin a = st.back(); st.pop_back();
+        if (!a.ok || !b.ok || !b.is_const || b.c == 0) st.push_back(bad);
+        else st.push_back(scale(a, 1.0 / b.c));
+      } break;
+      case WT_OP_NEG: st.back() = scale(st.back(), -1.0); break;
+      default: return f;  // min, max, abs, sqrt, parities: not linear in the taps
+    }
+  }
+  if (st.size() != 1 || !st.back().ok || st.back().is_const) return f;
+  const Lin &l = st.back();
+  int x0 = 1 << 20, x1 = -(1 << 20), y0 = 1 << 20, y1 = -(1 << 20);
+  double wmax = 0, pv = 0;
+  int pi = 0, pj = 0;
+  for (auto &kv : l.t) {
+    if (kv.second == 0) continue;
+    x0 = std::min(x0, kv.first.first);
+    x1 = std::max(x1, kv.first.first);
+    y0 = std::min(y0, kv.first.second);
+    y1 = std::max(y1, kv.first.second);
+    wmax = std::max(wmax, std::fabs(kv.second));
+  }
+  if (wmax == 0) return f;
+  const int nx = x1 - x0 + 1, ny = y1 - y0 + 1;
+  std::vector<double> Wm((size_t)nx * ny, 0.0);
+  for (auto &kv : l.t) {
+    if (kv.second == 0) continue;
+    const int i = kv.first.first - x0, j = kv.first.second - y0;
+    Wm[(size_t)j * nx + i] = kv.second;
+    if (std::fabs(kv.second) > std::fabs(pv)) {
+      pv = kv.second;
+      pi = i;
+      pj = j;
+    }
+  }
+  std::vector<double> v(nx), u(ny);
+  for (int i = 0; i < nx; i++) v[i] = Wm[(size_t)pj * nx + i];
+  for (int j = 0; j < ny; j++) u[j] = Wm[(size_t)j * nx + pi] / pv;
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++)
+      if (std::fabs(Wm[(size_t)j * nx + i] - u[j] * v[i]) > 1e-9 * wmax) return f;  // rank > 1
+  f.ok = true;
+  f.slot = slot;
+  f.chan = chan;
+  f.dx0 = x0;
+  f.dy0 = y0;
+  f.wx = v;
+  f.wy = u;
+  f.c = l.c;
+  return f;
+}
+
+bool down_streamable(const DownForm &f, int vo) {
+  if (!f.ok) return false;
+  const int dx1 = f.dx0 + (int)f.wx.size() - 1;
+  // neighbour taps come from the adjacent lane only
+  return -f.dx0 <= 2 * vo && dx1 - 1 <= 2 * vo && (int)f.wy.size() <= 16;
+}
+
+std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const std::string &kname) {
+  const Stage &S = p.stages[sid];
+  const DownForm f = down_form(p, sid);
+  const int VO = key.vec, T = key.tby, NW = key.nw;
+  if (!down_streamable(f, VO) || T < 1) fail(WT_EINVAL, "internal: stage is not a streamable down-sampling stencil");
+  const int NX = (int)f.wx.size(), NY = (int)f.wy.size();
+  const int DX0 = f.dx0, DY0 = f.dy0, DY1 = f.dy0 + NY - 1;
+  const int DX1 = DX0 + NX - 1;
+  const int LH = std::max(0, -DX0);     // values left of the lane's own 2 VO
+  const int RH = std::max(0, DX1 - 1);  // values right of them
+  const int NV = LH + 2 * VO + RH;
+  const int NA = (DY1 - DY0) / 2 + 1;   // output rows open at once (ring)
+  const int sdt = key.src_dtypes.at(0), ddt = key.dst_dtypes.at(0);
+  const int sesz = elem_bytes(sdt), desz = elem_bytes(ddt);
+  std::ostringstream o;
+  o << kDeviceSource;
+  o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * NW << ") " << kname
+    << "(const __grid_constant__ WtArgs a) {\n";
+  o << "const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;\n";
+  o << "const int W = a.W, H = a.H;\n";
+  o << "const int xo0 = blockIdx.x * " << 32 * VO << ";\n";
+  o << "const int yo0 = (blockIdx.y * " << NW << " + wid) * " << T << ";\n";
+  o << "const int ch = blockIdx.z;\n(void)ch;\n";
+  o << "if (yo0 >= H) return;\n";
+  o << "const int Ws = a.src[0].W, Hs = a.src[0].H;\n";
+  o << "const unsigned char *sp = (const unsigned char *)a.src[0].ptr + (wt_i64)"
+    << (f.chan >= 0 ? std::to_string(f.chan) : std::string("ch")) << " * a.src[0].plane;\n";
+  o << "const wt_i64 pitch = a.src[0].pitch;\n";
+  o << "const int xs = 2 * (xo0 + lane * " << VO << ");\n";
+  // every column the warp reads lies inside the row: vector loads and
+  // shuffles; else clamped scalar loads
+  // (taps and the lanes' own segments, relative to lane 0's and lane 31's xs)
+  const int lo_off = std::min(DX0, 0), hi_off = std::max(2 * VO - 2 + DX1, 2 * VO - 1);
+  o << "const bool fast = 2 * xo0 + (" << lo_off << ") >= 0 && 2 * (xo0 + " << 31 * VO << ") + (" << hi_off
+    << ") <= Ws - 1;\n";
+  o << "float";
+  for (int s = 0; s < NA; s++)
+    for (int k = 0; k < VO; k++) o << (s || k ? ", " : " ") << "acc" << s << "_" << k << " = 0.f";
+  o << ";\n";
+  const int M_extra = NA - 1;  // steps after the last output row starts
+  o << "const int M = " << T + M_extra << ";\n";
+  o << "for (int m0 = 0; m0 < M; m0 += " << NA << ") {\n";
+  for (int u = 0; u < NA; u++) {
+    o << "{\nconst int m = m0 + " << u << ";\nif (m < M) {\n";
+    for (int q = 0; q < 2; q++) {
+      // producer row rho = DY0 + 2m + q (relative to 2 yo0)
+      o << "if (" << DY0 + q << " + 2 * m <= " << 2 * (T - 1) + DY1 << ") {\n";
+      o << "const unsigned char *rp = sp + (wt_i64)wt_clampi(2 * yo0 + (" << DY0 + q << ") + 2 * m, 0, Hs - 1) * pitch;\n";
+      o << "float";
+      for (int i = 0; i < NV; i++) o << (i ? ", " : " ") << "v" << i;
+      o << ";\n";
+      o << "if (fast) {\n";
+      for (int b = 0; b < 2 * VO; b += 4)
+        o << "wt_ld4_" << tn(sdt) << "(rp + (wt_i64)(xs + " << b << ") * " << sesz << ", v" << LH + b << ", v"
+          << LH + b + 1 << ", v" << LH + b + 2 << ", v" << LH + b + 3 << ");\n";
+      for (int k = 0; k < LH; k++) {
+        // left neighbour's value at its offset 2 VO - LH + k
+        o << "{ float t_ = __shfl_up_sync(0xffffffffu, v" << LH + 2 * VO - LH + k << ", 1);\n";
+        o << "v" << k << " = lane == 0 ? wt_ld1_" << tn(sdt) << "(rp + (wt_i64)(xs - " << LH - k << ") * " << sesz
+          << ") : t_; }\n";
+      }
+      for (int k = 0; k < RH; k++) {
+        o << "{ float t_ = __shfl_down_sync(0xffffffffu, v" << LH + k << ", 1);\n";
+        o << "v" << LH + 2 * VO + k << " = lane == 31 ? wt_ld1_" << tn(sdt) << "(rp + (wt_i64)(xs + "
+          << 2 * VO + k << ") * " << sesz << ") : t_; }\n";
+      }
+      o << "} else {\n";
+      for (int i = 0; i < NV; i++)
+        o << "v" << i << " = wt_ld1_" << tn(sdt) << "(rp + (wt_i64)wt_clampi(xs + (" << i - LH << "), 0, Ws - 1) * "
+          << sesz << ");\n";
+      o << "}\n";
+      // row pass at stride 2
+      for (int k = 0; k < VO; k++) {
+        o << "const float h" << k << " = ";
+        bool first = true;
+        for (int i = 0; i < NX; i++) {
+          if (f.wx[i] == 0) continue;
+          const int vi = LH + 2 * k + DX0 + i;
+          o << (first ? "" : " + ") << lit(f.wx[i]) << " * v" << vi;
+          first = false;
+        }
+        o << ";\n";
+      }
+      // column pass: this row is tap dy of output j = m + delta
+      for (int dy = DY0; dy <= DY1; dy++) {
+        if (((DY0 + q - dy) % 2 + 2) % 2 != 0) continue;
+        const double w = f.wy[dy - DY0];
+        const int delta = (DY0 + q - dy) / 2;  // <= 0
+        const int slot = ((u + delta) % NA + NA) % NA;
+        if (w == 0 && dy != DY0) continue;
+        for (int k = 0; k < VO; k++)
+          o << "acc" << slot << "_" << k << (dy == DY0 ? " = " : " += ") << lit(w) << " * h" << k << ";\n";
+        if (dy == DY1) {
+          // output j complete
+          o << "{ const int j = m + (" << delta << "), yo = yo0 + j;\n";
+          o << "if (j >= 0 && j < " << T << " && yo < H) {\n";
+          o << "unsigned char *op_ = (unsigned char *)a.dst[0].ptr + (wt_i64)" << (S.channels > 1 ? "ch" : "0")
+            << " * a.dst[0].plane + (wt_i64)yo * a.dst[0].pitch;\n";
+          o << "const int xo = xo0 + lane * " << VO << ";\n";
+          std::vector<std::string> outv;
+          for (int k = 0; k < VO; k++) {
+            std::string e = "acc" + std::to_string(slot) + "_" + std::to_string(k);
+            if (f.c != 0) e = "(" + e + " + " + lit(f.c) + ")";
+            outv.push_back(e);
+          }
+          o << "if (xo + " << VO << " <= W) {\n";
+          for (int b = 0; b < VO; b += 4)
+            o << "wt_st4_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << b << ") * " << desz << ", " << outv[b] << ", "
+              << outv[b + 1] << ", " << outv[b + 2] << ", " << outv[b + 3] << ");\n";
+          o << "} else {\n";
+          for (int k = 0; k < VO; k++)
+            o << "if (xo + " << k << " < W) wt_st1_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << k << ") * " << desz
+              << ", " << outv[k] << ");\n";
+          o << "}\n}\n}\n";
+        }
+      }
+      o << "}\n";
+    }
+    o << "}\n}\n";
+  }
+  o << "}\n}\n";
+  return o.str();
+}
+
+}  // namespace wt

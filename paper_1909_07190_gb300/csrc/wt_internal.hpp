@@ -256,6 +256,9 @@ struct CodegenKey {
   // shared memory between block barriers
   bool otptb = false;
   int tbx = 0, tby = 0;
+  // per-stage kernel of a separable down-sampling stage, streamed at two
+  // rates (scaled.cpp): vec outputs per lane, tby output rows per warp
+  bool down = false;
   std::string str() const;
 };
 
@@ -292,6 +295,21 @@ struct OtptbLayout {
 OtptbLayout otptb_layout(const GroupGeom &g, const CodegenKey &key);
 std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &key,
                        const std::string &kname);
+// scaled.cpp: a stage whose taps all read one producer one level finer
+// (DOWN2) in a rank-one linear pattern: sum_ij wy[j] wx[i] P(2x + dx0 + i,
+// 2y + dy0 + j) + c.
+struct DownForm {
+  bool ok = false;
+  int slot = 0, chan = 0;  // producer input slot and channel spec
+  int dx0 = 0, dy0 = 0;
+  std::vector<double> wx, wy;
+  double c = 0;
+};
+DownForm down_form(const Pipeline &p, int sid);
+// The streaming kernel handles the form with `vo` outputs per lane.
+bool down_streamable(const DownForm &f, int vo);
+std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key,
+                      const std::string &kname);
 // Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
 struct PlainSrc {
   int slot, chan;

@@ -8,7 +8,7 @@ the same group analysis.
 Arms, each one fused group over the whole pipeline unless noted:
   plain  per-stage kernels, intermediates in HBM (the unfused baseline)
   otptb  one overlapped tile per thread block (WT_FLAG_OTPTB), swept over
-         tile width 32 vec (vec 1, 2, 4, 8), tile height {4, 8, 16, 32, 64}
+         tile width 32 vec (vec 1, 2, 4, 8), tile height {4, 8, 16, 32, 64, 128}
          and {4, 8, 16} warps per block
   otpw   warp tiles, swept over tile height {8, 14, 20, 32}, fracReg
          {0 (Shared), 0.5 (HT), 1 (RT)} and {2, 4} warps per block
@@ -33,7 +33,7 @@ from . import wt
 
 SIZES = {"harris": (4096, 4096), "sharpen": (2048, 2048), "blur_rgb": (4096, 4096), "blur": (4096, 4096)}
 OTPTB_GRID = [dict(vec=v, tile_h=t, warps_per_block=w, flags=wt.WT_FLAG_OTPTB)
-              for v, t, w in itertools.product((1, 2, 4, 8), (4, 8, 16, 32, 64), (4, 8, 16))]
+              for v, t, w in itertools.product((1, 2, 4, 8), (4, 8, 16, 32, 64, 128), (4, 8, 16))]
 OTPW_GRID = [dict(tile_h=t, frac_reg=f, warps_per_block=w)
              for t, f, w in itertools.product((8, 14, 20, 32), (0.0, 0.5, 1.0), (2, 4))]
 

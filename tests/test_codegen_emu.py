@@ -35,7 +35,8 @@ def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mod
     d = emu.run(p, launch, ins, outs, max_blocks, ws)
     for i in range(1, d["n_launches"]):
         emu.run(p, i, ins, outs, max_blocks, ws)
-    if exec_mode == wt.WT_EXEC_FUSED and d["n_launches"] == 1:
+    per_stage = any((q or {}).get("flags", 0) & wt.WT_FLAG_PLAIN for q in (params or []))
+    if exec_mode == wt.WT_EXEC_FUSED and d["n_launches"] == 1 and not per_stage:
         assert d["fused"]
     for o in outs:
         assert o.padding_intact(), "kernel wrote outside the image"
