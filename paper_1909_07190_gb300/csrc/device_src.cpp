@@ -125,6 +125,28 @@ static __device__ __forceinline__ void wt_ld4_bf16(const void *p, float &a, floa
   a = __uint_as_float(v.x << 16); b = __uint_as_float(v.x & 0xffff0000u);
   c = __uint_as_float(v.y << 16); d = __uint_as_float(v.y & 0xffff0000u);
 }
+// ------------------------------- read-only 8-element loads (16-byte aligned)
+static __device__ __forceinline__ void wt_ld8_f32(const void *p, float &a, float &b, float &c, float &d,
+                                                  float &e, float &f, float &g, float &h) {
+  const float4 u = __ldg((const float4 *)p), w = __ldg((const float4 *)p + 1);
+  a = u.x; b = u.y; c = u.z; d = u.w; e = w.x; f = w.y; g = w.z; h = w.w;
+}
+static __device__ __forceinline__ void wt_ld8_f16(const void *p, float &a, float &b, float &c, float &d,
+                                                  float &e, float &f, float &g, float &h) {
+  const uint4 v = __ldg((const uint4 *)p);
+  a = wt_h2f((wt_u16)(v.x & 0xffff)); b = wt_h2f((wt_u16)(v.x >> 16));
+  c = wt_h2f((wt_u16)(v.y & 0xffff)); d = wt_h2f((wt_u16)(v.y >> 16));
+  e = wt_h2f((wt_u16)(v.z & 0xffff)); f = wt_h2f((wt_u16)(v.z >> 16));
+  g = wt_h2f((wt_u16)(v.w & 0xffff)); h = wt_h2f((wt_u16)(v.w >> 16));
+}
+static __device__ __forceinline__ void wt_ld8_bf16(const void *p, float &a, float &b, float &c, float &d,
+                                                   float &e, float &f, float &g, float &h) {
+  const uint4 v = __ldg((const uint4 *)p);
+  a = __uint_as_float(v.x << 16); b = __uint_as_float(v.x & 0xffff0000u);
+  c = __uint_as_float(v.y << 16); d = __uint_as_float(v.y & 0xffff0000u);
+  e = __uint_as_float(v.z << 16); f = __uint_as_float(v.z & 0xffff0000u);
+  g = __uint_as_float(v.w << 16); h = __uint_as_float(v.w & 0xffff0000u);
+}
 // ------------------------------------------------ vector stores (4 lanes)
 static __device__ __forceinline__ void wt_st4_f32(void *p, float a, float b, float c, float d) {
   *(float4 *)p = make_float4(a, b, c, d);

@@ -3,6 +3,7 @@
 // resolved through the runtime (cudaGetDriverEntryPointByVersion), so the
 // library loads on machines without a GPU driver; they are needed only
 // when a kernel is compiled or launched.
+#include <dlfcn.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvrtc.h>
@@ -72,11 +73,19 @@ void check_rt(int rc, const char *what) {
 static std::mutex g_cubin_mu;
 static std::map<std::string, std::string> g_cubins;
 
+// On-disk cubin cache: $WT_CACHE_DIR, else _build/kernel_cache beside the
+// library itself (the package directory), so that a build keeps its files
+// in its own tree.
 static std::string cache_dir() {
   const char *e = getenv("WT_CACHE_DIR");
   if (e && *e) return e;
-  const char *h = getenv("HOME");
-  return std::string(h && *h ? h : "/tmp") + "/.cache/wt_kernels";
+  Dl_info info;
+  if (dladdr((const void *)&cache_dir, &info) && info.dli_fname) {
+    std::string lib(info.dli_fname);
+    const size_t slash = lib.rfind('/');
+    if (slash != std::string::npos) return lib.substr(0, slash) + "/_build/kernel_cache";
+  }
+  return "_build/kernel_cache";
 }
 
 static void mkdirs(const std::string &d) {

@@ -173,6 +173,9 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
   const int RH = std::max(0, DX1 - 1);  // values right of them
   const int NV = LH + 2 * VO + RH;
   const int NA = (DY1 - DY0) / 2 + 1;   // output rows open at once (ring)
+  // steps: step m loads producer rows DY0 + 2m and DY0 + 2m + 1 (relative
+  // to 2 yo0); output row j is complete after step j + NA - 1
+  const int M = T + NA - 1;
   const int sdt = key.src_dtypes.at(0), ddt = key.dst_dtypes.at(0);
   const int sesz = elem_bytes(sdt), desz = elem_bytes(ddt);
   std::ostringstream o;
@@ -191,9 +194,12 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
     << (f.chan >= 0 ? std::to_string(f.chan) : std::string("ch")) << " * a.src[0].plane;\n";
   o << "const wt_i64 pitch = a.src[0].pitch;\n";
   o << "const int xs = 2 * (xo0 + lane * " << VO << ");\n";
-  // every column the warp reads lies inside the row: vector loads and
-  // shuffles; else clamped scalar loads
-  // (taps and the lanes' own segments, relative to lane 0's and lane 31's xs)
+  o << "unsigned char *dp = (unsigned char *)a.dst[0].ptr + (wt_i64)" << (S.channels > 1 ? "ch" : "0")
+    << " * a.dst[0].plane;\n";
+  o << "const int xo = xo0 + lane * " << VO << ";\n";
+  // every column the warp reads (taps and the lanes' own segments, relative
+  // to lane 0's and lane 31's xs) lies inside the row: 16-byte loads and
+  // shuffles; else clamped scalar loads.  Warp-uniform.
   const int lo_off = std::min(DX0, 0), hi_off = std::max(2 * VO - 2 + DX1, 2 * VO - 1);
   o << "const bool fast = 2 * xo0 + (" << lo_off << ") >= 0 && 2 * (xo0 + " << 31 * VO << ") + (" << hi_off
     << ") <= Ws - 1;\n";
@@ -201,46 +207,53 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
   for (int s = 0; s < NA; s++)
     for (int k = 0; k < VO; k++) o << (s || k ? ", " : " ") << "acc" << s << "_" << k << " = 0.f";
   o << ";\n";
-  const int M_extra = NA - 1;  // steps after the last output row starts
-  o << "const int M = " << T + M_extra << ";\n";
-  o << "for (int m0 = 0; m0 < M; m0 += " << NA << ") {\n";
-  for (int u = 0; u < NA; u++) {
-    o << "{\nconst int m = m0 + " << u << ";\nif (m < M) {\n";
+  auto vn = [](int q, int i) { return "v" + std::to_string(q) + "_" + std::to_string(i); };
+  // one step: slot base u (compile time), step index expression mexpr
+  auto step = [&](bool fast, int u, const std::string &mexpr) {
+    o << "{\nconst int m = " << mexpr << ";\n";
+    // both rows' loads first (in flight together)
     for (int q = 0; q < 2; q++) {
-      // producer row rho = DY0 + 2m + q (relative to 2 yo0)
-      o << "if (" << DY0 + q << " + 2 * m <= " << 2 * (T - 1) + DY1 << ") {\n";
-      o << "const unsigned char *rp = sp + (wt_i64)wt_clampi(2 * yo0 + (" << DY0 + q << ") + 2 * m, 0, Hs - 1) * pitch;\n";
+      o << "const unsigned char *rp" << q << " = sp + (wt_i64)wt_clampi(2 * yo0 + (" << DY0 + q
+        << ") + 2 * m, 0, Hs - 1) * pitch;\n";
       o << "float";
-      for (int i = 0; i < NV; i++) o << (i ? ", " : " ") << "v" << i;
+      for (int i = 0; i < NV; i++) o << (i ? ", " : " ") << vn(q, i);
       o << ";\n";
-      o << "if (fast) {\n";
-      for (int b = 0; b < 2 * VO; b += 4)
-        o << "wt_ld4_" << tn(sdt) << "(rp + (wt_i64)(xs + " << b << ") * " << sesz << ", v" << LH + b << ", v"
-          << LH + b + 1 << ", v" << LH + b + 2 << ", v" << LH + b + 3 << ");\n";
-      for (int k = 0; k < LH; k++) {
-        // left neighbour's value at its offset 2 VO - LH + k
-        o << "{ float t_ = __shfl_up_sync(0xffffffffu, v" << LH + 2 * VO - LH + k << ", 1);\n";
-        o << "v" << k << " = lane == 0 ? wt_ld1_" << tn(sdt) << "(rp + (wt_i64)(xs - " << LH - k << ") * " << sesz
-          << ") : t_; }\n";
+      if (fast) {
+        for (int b = 0; b < 2 * VO; b += 8) {
+          o << "wt_ld8_" << tn(sdt) << "(rp" << q << " + (wt_i64)(xs + " << b << ") * " << sesz;
+          for (int t = 0; t < 8; t++) o << ", " << vn(q, LH + b + t);
+          o << ");\n";
+        }
+        for (int k = 0; k < LH; k++)
+          o << "if (lane == 0) " << vn(q, k) << " = wt_ld1_" << tn(sdt) << "(rp" << q << " + (wt_i64)(xs - "
+            << LH - k << ") * " << sesz << ");\n";
+        for (int k = 0; k < RH; k++)
+          o << "if (lane == 31) " << vn(q, LH + 2 * VO + k) << " = wt_ld1_" << tn(sdt) << "(rp" << q
+            << " + (wt_i64)(xs + " << 2 * VO + k << ") * " << sesz << ");\n";
+      } else {
+        for (int i = 0; i < NV; i++)
+          o << vn(q, i) << " = wt_ld1_" << tn(sdt) << "(rp" << q << " + (wt_i64)wt_clampi(xs + (" << i - LH
+            << "), 0, Ws - 1) * " << sesz << ");\n";
       }
-      for (int k = 0; k < RH; k++) {
-        o << "{ float t_ = __shfl_down_sync(0xffffffffu, v" << LH + k << ", 1);\n";
-        o << "v" << LH + 2 * VO + k << " = lane == 31 ? wt_ld1_" << tn(sdt) << "(rp + (wt_i64)(xs + "
-          << 2 * VO + k << ") * " << sesz << ") : t_; }\n";
+    }
+    for (int q = 0; q < 2; q++) {
+      if (fast) {
+        // the neighbours' values: the left lane's last LH, the right lane's
+        // first RH (lanes 0 and 31 loaded theirs)
+        for (int k = 0; k < LH; k++)
+          o << "{ const float t_ = __shfl_up_sync(0xffffffffu, " << vn(q, 2 * VO + k) << ", 1); if (lane != 0) "
+            << vn(q, k) << " = t_; }\n";
+        for (int k = 0; k < RH; k++)
+          o << "{ const float t_ = __shfl_down_sync(0xffffffffu, " << vn(q, LH + k) << ", 1); if (lane != 31) "
+            << vn(q, LH + 2 * VO + k) << " = t_; }\n";
       }
-      o << "} else {\n";
-      for (int i = 0; i < NV; i++)
-        o << "v" << i << " = wt_ld1_" << tn(sdt) << "(rp + (wt_i64)wt_clampi(xs + (" << i - LH << "), 0, Ws - 1) * "
-          << sesz << ");\n";
-      o << "}\n";
       // row pass at stride 2
       for (int k = 0; k < VO; k++) {
-        o << "const float h" << k << " = ";
+        o << "const float h" << q << "_" << k << " = ";
         bool first = true;
         for (int i = 0; i < NX; i++) {
           if (f.wx[i] == 0) continue;
-          const int vi = LH + 2 * k + DX0 + i;
-          o << (first ? "" : " + ") << lit(f.wx[i]) << " * v" << vi;
+          o << (first ? "" : " + ") << lit(f.wx[i]) << " * " << vn(q, LH + 2 * k + DX0 + i);
           first = false;
         }
         o << ";\n";
@@ -253,34 +266,43 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         const int slot = ((u + delta) % NA + NA) % NA;
         if (w == 0 && dy != DY0) continue;
         for (int k = 0; k < VO; k++)
-          o << "acc" << slot << "_" << k << (dy == DY0 ? " = " : " += ") << lit(w) << " * h" << k << ";\n";
-        if (dy == DY1) {
-          // output j complete
-          o << "{ const int j = m + (" << delta << "), yo = yo0 + j;\n";
-          o << "if (j >= 0 && j < " << T << " && yo < H) {\n";
-          o << "unsigned char *op_ = (unsigned char *)a.dst[0].ptr + (wt_i64)" << (S.channels > 1 ? "ch" : "0")
-            << " * a.dst[0].plane + (wt_i64)yo * a.dst[0].pitch;\n";
-          o << "const int xo = xo0 + lane * " << VO << ";\n";
-          std::vector<std::string> outv;
-          for (int k = 0; k < VO; k++) {
-            std::string e = "acc" + std::to_string(slot) + "_" + std::to_string(k);
-            if (f.c != 0) e = "(" + e + " + " + lit(f.c) + ")";
-            outv.push_back(e);
-          }
-          o << "if (xo + " << VO << " <= W) {\n";
-          for (int b = 0; b < VO; b += 4)
-            o << "wt_st4_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << b << ") * " << desz << ", " << outv[b] << ", "
-              << outv[b + 1] << ", " << outv[b + 2] << ", " << outv[b + 3] << ");\n";
-          o << "} else {\n";
-          for (int k = 0; k < VO; k++)
-            o << "if (xo + " << k << " < W) wt_st1_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << k << ") * " << desz
-              << ", " << outv[k] << ");\n";
-          o << "}\n}\n}\n";
+          o << "acc" << slot << "_" << k << (dy == DY0 ? " = " : " += ") << lit(w) << " * h" << q << "_" << k
+            << ";\n";
+        if (dy != DY1) continue;
+        // output row j is complete (rows j < 0 and j >= T are not stored)
+        o << "{ const int j = m + (" << delta << "), yo = yo0 + j;\n";
+        o << "if (j >= 0 && j < " << T << " && yo < H) {\n";
+        o << "unsigned char *op_ = dp + (wt_i64)yo * a.dst[0].pitch;\n";
+        std::vector<std::string> outv;
+        for (int k = 0; k < VO; k++) {
+          std::string e = "acc" + std::to_string(slot) + "_" + std::to_string(k);
+          if (f.c != 0) e = "(" + e + " + " + lit(f.c) + ")";
+          outv.push_back(e);
         }
+        o << "if (xo + " << VO << " <= W) {\n";
+        for (int b = 0; b < VO; b += 4)
+          o << "wt_st4_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << b << ") * " << desz << ", " << outv[b] << ", "
+            << outv[b + 1] << ", " << outv[b + 2] << ", " << outv[b + 3] << ");\n";
+        o << "} else {\n";
+        for (int k = 0; k < VO; k++)
+          o << "if (xo + " << k << " < W) wt_st1_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << k << ") * " << desz
+            << ", " << outv[k] << ");\n";
+        o << "}\n}\n}\n";
       }
+    }
+    o << "}\n";
+  };
+  // whole rounds of NA steps (ring slots fixed per unrolled step), then the
+  // remaining M mod NA steps; both paths, chosen once per warp
+  const int full = M / NA * NA;
+  for (int fpath = 1; fpath >= 0; fpath--) {
+    o << (fpath ? "if (fast) {\n" : "} else {\n");
+    if (full > 0) {
+      o << "#pragma unroll 1\nfor (int m0 = 0; m0 < " << full << "; m0 += " << NA << ") {\n";
+      for (int u = 0; u < NA; u++) step(fpath != 0, u, "m0 + " + std::to_string(u));
       o << "}\n";
     }
-    o << "}\n}\n";
+    for (int u = 0; u < M - full; u++) step(fpath != 0, u, std::to_string(full + u));
   }
   o << "}\n}\n";
   return o.str();

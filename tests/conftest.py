@@ -8,3 +8,5 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+    # temporary files of the tests stay inside the repository tree (_build/)
+    os.makedirs(os.path.join(ROOT, "_build"), exist_ok=True)

@@ -11,7 +11,6 @@ import ctypes
 import hashlib
 import os
 import subprocess
-import tempfile
 
 import numpy as np
 
@@ -19,7 +18,8 @@ from paper_1909_07190_gb300 import wt
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 MARK = "// WT-DEVICE-HELPERS-END"
-CACHE = os.path.join(tempfile.gettempdir(), "wt_emu_cache")
+# compiled emulated kernels, kept inside the repository tree (git-ignored)
+CACHE = os.path.join(os.path.dirname(os.path.dirname(HERE)), "_build", "emu_cache")
 _loaded = {}
 
 NP_DTYPES = {wt.WT_F32: np.float32, wt.WT_F16: np.float16, wt.WT_BF16: np.uint16}

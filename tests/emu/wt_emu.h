@@ -191,36 +191,72 @@ static inline wt_u16 wt_f2b(float f) {
 }
 
 // ------------------------------------------------------ loads / stores
+// vector accesses must be naturally aligned, as on the GPU
+static inline void wt_emu_align(const void *p, long bytes) {
+  if ((long)((unsigned long)p % (unsigned long)bytes) != 0) wt_emu_fail("misaligned vector access");
+}
+static inline void wt_ld8_f32(const void *p, float &a, float &b, float &c, float &d, float &e, float &f,
+                              float &g, float &h) {
+  wt_emu_check(p, 32, "load");
+  wt_emu_align(p, 16);
+  float v[8];
+  memcpy(v, p, 32);
+  a = v[0]; b = v[1]; c = v[2]; d = v[3]; e = v[4]; f = v[5]; g = v[6]; h = v[7];
+}
+static inline void wt_ld8_f16(const void *p, float &a, float &b, float &c, float &d, float &e, float &f,
+                              float &g, float &h) {
+  wt_emu_check(p, 16, "load");
+  wt_emu_align(p, 16);
+  wt_u16 v[8];
+  memcpy(v, p, 16);
+  a = wt_h2f(v[0]); b = wt_h2f(v[1]); c = wt_h2f(v[2]); d = wt_h2f(v[3]);
+  e = wt_h2f(v[4]); f = wt_h2f(v[5]); g = wt_h2f(v[6]); h = wt_h2f(v[7]);
+}
+static inline void wt_ld8_bf16(const void *p, float &a, float &b, float &c, float &d, float &e, float &f,
+                               float &g, float &h) {
+  wt_emu_check(p, 16, "load");
+  wt_emu_align(p, 16);
+  wt_u16 v[8];
+  memcpy(v, p, 16);
+  a = wt_b2f(v[0]); b = wt_b2f(v[1]); c = wt_b2f(v[2]); d = wt_b2f(v[3]);
+  e = wt_b2f(v[4]); f = wt_b2f(v[5]); g = wt_b2f(v[6]); h = wt_b2f(v[7]);
+}
 static inline void wt_ld4_f32(const void *p, float &a, float &b, float &c, float &d) {
   wt_emu_check(p, 16, "load");
+  wt_emu_align(p, 16);
   float v[4];
   memcpy(v, p, 16);
   a = v[0]; b = v[1]; c = v[2]; d = v[3];
 }
 static inline void wt_ld4_f16(const void *p, float &a, float &b, float &c, float &d) {
   wt_emu_check(p, 8, "load");
+  wt_emu_align(p, 8);
   wt_u16 v[4];
   memcpy(v, p, 8);
   a = wt_h2f(v[0]); b = wt_h2f(v[1]); c = wt_h2f(v[2]); d = wt_h2f(v[3]);
 }
 static inline void wt_ld4_bf16(const void *p, float &a, float &b, float &c, float &d) {
   wt_emu_check(p, 8, "load");
+  wt_emu_align(p, 8);
   wt_u16 v[4];
   memcpy(v, p, 8);
   a = wt_b2f(v[0]); b = wt_b2f(v[1]); c = wt_b2f(v[2]); d = wt_b2f(v[3]);
 }
 static inline void wt_st4_f32(void *p, float a, float b, float c, float d) {
   wt_emu_check(p, 16, "store");
+  wt_emu_align(p, 16);
   float v[4] = {a, b, c, d};
   memcpy(p, v, 16);
 }
 static inline void wt_st4_f16(void *p, float a, float b, float c, float d) {
   wt_emu_check(p, 8, "store");
+  wt_emu_align(p, 8);
   wt_u16 v[4] = {wt_f2h(a), wt_f2h(b), wt_f2h(c), wt_f2h(d)};
   memcpy(p, v, 8);
 }
 static inline void wt_st4_bf16(void *p, float a, float b, float c, float d) {
   wt_emu_check(p, 8, "store");
+  wt_emu_align(p, 8);
   wt_u16 v[4] = {wt_f2b(a), wt_f2b(b), wt_f2b(c), wt_f2b(d)};
   memcpy(p, v, 8);
 }
