@@ -147,6 +147,43 @@ static __device__ __forceinline__ void wt_ld8_bf16(const void *p, float &a, floa
   e = __uint_as_float(v.z << 16); f = __uint_as_float(v.z & 0xffff0000u);
   g = __uint_as_float(v.w << 16); h = __uint_as_float(v.w & 0xffff0000u);
 }
+// --------------------------------------------- shared-memory row buffers
+// FP32 buffer element i of n (n: the buffer's length; bounds are checked
+// where the kernels are emulated on the host)
+static __device__ __forceinline__ float wt_sld(const float *b, int i, int n) { (void)n; return b[i]; }
+static __device__ __forceinline__ void wt_sst(float *b, int i, int n, float v) { (void)n; b[i] = v; }
+// 8 stored elements from shared memory (16-byte aligned), and one
+static __device__ __forceinline__ void wt_lds8_f32(const void *p, float &a, float &b, float &c, float &d,
+                                                   float &e, float &f, float &g, float &h) {
+  const float4 u = ((const float4 *)p)[0], w = ((const float4 *)p)[1];
+  a = u.x; b = u.y; c = u.z; d = u.w; e = w.x; f = w.y; g = w.z; h = w.w;
+}
+static __device__ __forceinline__ void wt_lds8_f16(const void *p, float &a, float &b, float &c, float &d,
+                                                   float &e, float &f, float &g, float &h) {
+  const uint4 v = *(const uint4 *)p;
+  a = wt_h2f((wt_u16)(v.x & 0xffff)); b = wt_h2f((wt_u16)(v.x >> 16));
+  c = wt_h2f((wt_u16)(v.y & 0xffff)); d = wt_h2f((wt_u16)(v.y >> 16));
+  e = wt_h2f((wt_u16)(v.z & 0xffff)); f = wt_h2f((wt_u16)(v.z >> 16));
+  g = wt_h2f((wt_u16)(v.w & 0xffff)); h = wt_h2f((wt_u16)(v.w >> 16));
+}
+static __device__ __forceinline__ void wt_lds8_bf16(const void *p, float &a, float &b, float &c, float &d,
+                                                    float &e, float &f, float &g, float &h) {
+  const uint4 v = *(const uint4 *)p;
+  a = __uint_as_float(v.x << 16); b = __uint_as_float(v.x & 0xffff0000u);
+  c = __uint_as_float(v.y << 16); d = __uint_as_float(v.y & 0xffff0000u);
+  e = __uint_as_float(v.z << 16); f = __uint_as_float(v.z & 0xffff0000u);
+  g = __uint_as_float(v.w << 16); h = __uint_as_float(v.w & 0xffff0000u);
+}
+static __device__ __forceinline__ float wt_lds1_f32(const void *p) { return *(const float *)p; }
+static __device__ __forceinline__ float wt_lds1_f16(const void *p) { return wt_h2f(*(const wt_u16 *)p); }
+static __device__ __forceinline__ float wt_lds1_bf16(const void *p) { return wt_b2f(*(const wt_u16 *)p); }
+// ------------------------------------- asynchronous copies global -> shared
+// 16 bytes (both addresses 16-byte aligned); completion by commit groups
+static __device__ __forceinline__ void wt_cp_async16(wt_u32 dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+static __device__ __forceinline__ void wt_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+#define WT_CP_ASYNC_WAIT(n) asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory")
 // ------------------------------------------------ vector stores (4 lanes)
 static __device__ __forceinline__ void wt_st4_f32(void *p, float a, float b, float c, float d) {
   *(float4 *)p = make_float4(a, b, c, d);

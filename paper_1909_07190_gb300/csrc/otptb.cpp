@@ -123,8 +123,9 @@ std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &
       const int dt = key.src_dtypes.at(s);
       const std::string S = "a.src[" + std::to_string(s) + "]";
       const std::string chan = n.src_chan >= 0 ? std::to_string(n.src_chan) : "ch";
-      o << buf(i) << "[t_] = wt_ld1_" << tn(dt) << "((const unsigned char *)" << S << ".ptr + (wt_i64)" << chan
-        << " * " << S << ".plane + (wt_i64)yc * " << S << ".pitch + (wt_i64)xc * " << elem_bytes(dt) << ");\n";
+      o << "wt_sst(" << buf(i) << ", t_, " << NP << ", wt_ld1_" << tn(dt) << "((const unsigned char *)" << S
+        << ".ptr + (wt_i64)" << chan << " * " << S << ".plane + (wt_i64)yc * " << S << ".pitch + (wt_i64)xc * "
+        << elem_bytes(dt) << "));\n";
     } else {
       std::vector<std::string> st;
       for (const KOp &op : n.prog) {
@@ -134,9 +135,10 @@ std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &
           case WT_OP_YPAR: st.push_back("((float)(yc & 1))"); break;
           case WT_OP_TAP: {
             const int q = op.node;
-            st.push_back(buf(q) + "[(yc + (" + std::to_string(op.dy) + ") - y0 - (" + std::to_string(L.ry[q]) +
-                         ")) * " + std::to_string(L.rw[q]) + " + (xc + (" + std::to_string(op.dx) + ") - x0 - (" +
-                         std::to_string(L.rx[q]) + "))]");
+            st.push_back("wt_sld(" + buf(q) + ", (yc + (" + std::to_string(op.dy) + ") - y0 - (" +
+                         std::to_string(L.ry[q]) + ")) * " + std::to_string(L.rw[q]) + " + (xc + (" +
+                         std::to_string(op.dx) + ") - x0 - (" + std::to_string(L.rx[q]) + ")), " +
+                         std::to_string(L.rw[q] * L.rh[q]) + ")");
           } break;
           case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
           case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
@@ -159,7 +161,7 @@ std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &
         }
       }
       o << "const float v_ = " << st.back() << ";\n";
-      o << buf(i) << "[t_] = v_;\n";
+      o << "wt_sst(" << buf(i) << ", t_, " << NP << ", v_);\n";
       if (n.is_liveout) {
         const int d = didx[i];
         const int dt = key.dst_dtypes.at(d);

@@ -247,7 +247,8 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
         L.grid[1] = (unsigned)((wy + key.nw - 1) / key.nw);
         L.grid[2] = (unsigned)p.stages[s].channels;
         if (L.grid[1] > 65535 || L.grid[2] > 65535) fail(WT_EUNSUPPORTED, "image too tall for the down-sampling kernel");
-        L.smem = 0;
+        L.smem = down_smem(p, s, key);
+        if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "down-sampling ring needs more than 227 KB of shared memory");
         L.kname = kernel_name(p, key, false);
         continue;
       }
@@ -279,7 +280,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
   static const char kOtptbVersion[] = "wt-otptb-1";  // the block-tile kernel's own changes
   if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
-  static const char kDownVersion[] = "wt-down-2";  // the down-sampling kernel's own changes
+  static const char kDownVersion[] = "wt-down-3";  // the down-sampling kernel's own changes
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;

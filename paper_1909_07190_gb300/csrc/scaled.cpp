@@ -161,6 +161,45 @@ bool down_streamable(const DownForm &f, int vo) {
   return -f.dx0 <= 2 * vo && dx1 - 1 <= 2 * vo && (int)f.wy.size() <= 16;
 }
 
+namespace {
+
+// Shared-memory ring of the fast path: per warp RL steps x 2 producer rows,
+// each row segment [left halo chunks | 32 x 2 VO own values | right halo
+// chunks] in the storage type (16-byte chunks).
+struct DownRing {
+  int che = 8;         // elements per 16-byte chunk
+  int ncl = 0, ncr = 0;  // halo chunks left / right of the warp's columns
+  int sege = 0, segb = 0;  // row segment: elements, bytes
+  int rl = 3;          // ring length in steps (multiple of NA)
+  int pd = 2;          // prefetch distance in steps (rl - 1)
+  int warp_bytes = 0;
+};
+
+DownRing down_ring(const DownForm &f, const CodegenKey &key) {
+  DownRing r;
+  const int esz = elem_bytes(key.src_dtypes.at(0));
+  const int VO = key.vec;
+  const int NX = (int)f.wx.size(), NY = (int)f.wy.size();
+  const int LH = std::max(0, -f.dx0), RH = std::max(0, f.dx0 + NX - 2);
+  const int NA = (NY - 1) / 2 + 1;
+  r.che = 16 / esz;
+  r.ncl = (LH + r.che - 1) / r.che;
+  r.ncr = (RH + r.che - 1) / r.che;
+  r.sege = (r.ncl + r.ncr) * r.che + 64 * VO;
+  r.segb = r.sege * esz;
+  const int depth = std::max(1, key.nbuf);  // requested prefetch distance (steps)
+  r.rl = NA * ((depth + 1 + NA - 1) / NA);
+  r.pd = r.rl - 1;
+  r.warp_bytes = r.rl * 2 * r.segb;
+  return r;
+}
+
+}  // namespace
+
+int down_smem(const Pipeline &p, int sid, const CodegenKey &key) {
+  return key.nw * down_ring(down_form(p, sid), key).warp_bytes;
+}
+
 std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const std::string &kname) {
   const Stage &S = p.stages[sid];
   const DownForm f = down_form(p, sid);
@@ -183,6 +222,8 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
   o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
   o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * NW << ") " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
+  const DownRing R = down_ring(f, key);
+  o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
   o << "const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;\n";
   o << "const int W = a.W, H = a.H;\n";
   o << "const int xo0 = blockIdx.x * " << 32 * VO << ";\n";
@@ -200,36 +241,68 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
   // every column the warp reads (taps and the lanes' own segments, relative
   // to lane 0's and lane 31's xs) lies inside the row: 16-byte loads and
   // shuffles; else clamped scalar loads.  Warp-uniform.
-  const int lo_off = std::min(DX0, 0), hi_off = std::max(2 * VO - 2 + DX1, 2 * VO - 1);
-  o << "const bool fast = 2 * xo0 + (" << lo_off << ") >= 0 && 2 * (xo0 + " << 31 * VO << ") + (" << hi_off
-    << ") <= Ws - 1;\n";
+  // The fast path copies the warp's columns and whole 16-byte halo chunks
+  // on both sides: all of them must lie inside the row.
+  o << "const bool fast = 2 * xo0 - " << R.ncl * R.che << " >= 0 && 2 * xo0 + " << 64 * VO + R.ncr * R.che
+    << " <= Ws;\n";
+  o << "unsigned char *wb = wt_smem + wid * " << R.warp_bytes << ";\n";
+  o << "const wt_u32 wbs = wt_smem_u32(wb);\n(void)wbs;\n";
   o << "float";
   for (int s = 0; s < NA; s++)
     for (int k = 0; k < VO; k++) o << (s || k ? ", " : " ") << "acc" << s << "_" << k << " = 0.f";
   o << ";\n";
   auto vn = [](int q, int i) { return "v" + std::to_string(q) + "_" + std::to_string(i); };
+  // cp.async of both producer rows of step `mexpr` into ring slot `slot`
+  auto issue = [&](int slot, const std::string &mexpr) {
+    for (int q = 0; q < 2; q++) {
+      o << "{ const unsigned char *gp = sp + (wt_i64)wt_clampi(2 * yo0 + (" << DY0 + q << ") + 2 * (" << mexpr
+        << "), 0, Hs - 1) * pitch;\n";
+      o << "const wt_u32 sb = wbs + " << (slot * 2 + q) * R.segb << ";\n";
+      for (int c = 0; c < 2 * VO * sesz / 16; c++)
+        o << "wt_cp_async16(sb + (" << R.ncl * R.che << " + lane * " << 2 * VO << ") * " << sesz << " + " << 16 * c
+          << ", gp + (wt_i64)xs * " << sesz << " + " << 16 * c << ");\n";
+      for (int c = 0; c < R.ncl; c++)
+        o << "if (lane == 0) wt_cp_async16(sb + " << 16 * c << ", gp + (wt_i64)(2 * xo0 - " << R.ncl * R.che
+          << ") * " << sesz << " + " << 16 * c << ");\n";
+      for (int c = 0; c < R.ncr; c++)
+        o << "if (lane == 31) wt_cp_async16(sb + " << (R.ncl * R.che + 64 * VO) * sesz + 16 * c
+          << ", gp + (wt_i64)(2 * xo0 + " << 64 * VO << ") * " << sesz << " + " << 16 * c << ");\n";
+      o << "}\n";
+    }
+  };
   // one step: slot base u (compile time), step index expression mexpr
   auto step = [&](bool fast, int u, const std::string &mexpr) {
     o << "{\nconst int m = " << mexpr << ";\n";
     // both rows' loads first (in flight together)
+    if (fast) {
+      // refill the slot freed by the previous step with the rows of step
+      // m + PD, then wait until this step's rows have landed
+      o << "if (m + " << R.pd << " < " << M << ") {\n";
+      issue(((u + R.pd) % R.rl), "m + " + std::to_string(R.pd));
+      o << "}\nwt_cp_async_commit();\nWT_CP_ASYNC_WAIT(" << R.pd << ");\n__syncwarp();\n";
+    }
     for (int q = 0; q < 2; q++) {
-      o << "const unsigned char *rp" << q << " = sp + (wt_i64)wt_clampi(2 * yo0 + (" << DY0 + q
-        << ") + 2 * m, 0, Hs - 1) * pitch;\n";
+      if (!fast)
+        o << "const unsigned char *rp" << q << " = sp + (wt_i64)wt_clampi(2 * yo0 + (" << DY0 + q
+          << ") + 2 * m, 0, Hs - 1) * pitch;\n";
       o << "float";
       for (int i = 0; i < NV; i++) o << (i ? ", " : " ") << vn(q, i);
       o << ";\n";
       if (fast) {
+        // this step's rows from the ring slot (copies waited for above)
+        const int row = (u % R.rl) * 2 + q;
+        o << "const unsigned char *sb" << q << " = wb + " << row * R.segb << " + (" << R.ncl * R.che << " + lane * "
+          << 2 * VO << ") * " << sesz << ";\n";
         for (int b = 0; b < 2 * VO; b += 8) {
-          o << "wt_ld8_" << tn(sdt) << "(rp" << q << " + (wt_i64)(xs + " << b << ") * " << sesz;
+          o << "wt_lds8_" << tn(sdt) << "(sb" << q << " + " << b * sesz;
           for (int t = 0; t < 8; t++) o << ", " << vn(q, LH + b + t);
           o << ");\n";
         }
         for (int k = 0; k < LH; k++)
-          o << "if (lane == 0) " << vn(q, k) << " = wt_ld1_" << tn(sdt) << "(rp" << q << " + (wt_i64)(xs - "
-            << LH - k << ") * " << sesz << ");\n";
+          o << vn(q, k) << " = wt_lds1_" << tn(sdt) << "(sb" << q << " - " << (LH - k) * sesz << ");\n";
         for (int k = 0; k < RH; k++)
-          o << "if (lane == 31) " << vn(q, LH + 2 * VO + k) << " = wt_ld1_" << tn(sdt) << "(rp" << q
-            << " + (wt_i64)(xs + " << 2 * VO + k << ") * " << sesz << ");\n";
+          o << vn(q, LH + 2 * VO + k) << " = wt_lds1_" << tn(sdt) << "(sb" << q << " + " << (2 * VO + k) * sesz
+            << ");\n";
       } else {
         for (int i = 0; i < NV; i++)
           o << vn(q, i) << " = wt_ld1_" << tn(sdt) << "(rp" << q << " + (wt_i64)wt_clampi(xs + (" << i - LH
@@ -237,16 +310,6 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
       }
     }
     for (int q = 0; q < 2; q++) {
-      if (fast) {
-        // the neighbours' values: the left lane's last LH, the right lane's
-        // first RH (lanes 0 and 31 loaded theirs)
-        for (int k = 0; k < LH; k++)
-          o << "{ const float t_ = __shfl_up_sync(0xffffffffu, " << vn(q, 2 * VO + k) << ", 1); if (lane != 0) "
-            << vn(q, k) << " = t_; }\n";
-        for (int k = 0; k < RH; k++)
-          o << "{ const float t_ = __shfl_down_sync(0xffffffffu, " << vn(q, LH + k) << ", 1); if (lane != 31) "
-            << vn(q, LH + 2 * VO + k) << " = t_; }\n";
-      }
       // row pass at stride 2
       for (int k = 0; k < VO; k++) {
         o << "const float h" << q << "_" << k << " = ";
@@ -290,19 +353,30 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         o << "}\n}\n}\n";
       }
     }
+    if (fast) o << "__syncwarp();\n";  // slot read by all lanes before its refill
     o << "}\n";
   };
   // whole rounds of NA steps (ring slots fixed per unrolled step), then the
   // remaining M mod NA steps; both paths, chosen once per warp
-  const int full = M / NA * NA;
   for (int fpath = 1; fpath >= 0; fpath--) {
+    // rounds of `un` steps: a multiple of NA (accumulator slots) and, on
+    // the fast path, of the ring length (ring slots)
+    const int un = fpath ? R.rl : NA;
+    const int full = M / un * un;
     o << (fpath ? "if (fast) {\n" : "} else {\n");
+    if (fpath) {
+      for (int m = 0; m < R.pd; m++) {
+        if (m < M) issue(m % R.rl, std::to_string(m));
+        o << "wt_cp_async_commit();\n";
+      }
+    }
     if (full > 0) {
-      o << "#pragma unroll 1\nfor (int m0 = 0; m0 < " << full << "; m0 += " << NA << ") {\n";
-      for (int u = 0; u < NA; u++) step(fpath != 0, u, "m0 + " + std::to_string(u));
+      o << "#pragma unroll 1\nfor (int m0 = 0; m0 < " << full << "; m0 += " << un << ") {\n";
+      for (int u = 0; u < un; u++) step(fpath != 0, u, "m0 + " + std::to_string(u));
       o << "}\n";
     }
     for (int u = 0; u < M - full; u++) step(fpath != 0, u, std::to_string(full + u));
+    if (fpath) o << "WT_CP_ASYNC_WAIT(0);\n";
   }
   o << "}\n}\n";
   return o.str();

@@ -310,6 +310,8 @@ DownForm down_form(const Pipeline &p, int sid);
 bool down_streamable(const DownForm &f, int vo);
 std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key,
                       const std::string &kname);
+// Dynamic shared memory of the down-sampling kernel (its cp.async ring).
+int down_smem(const Pipeline &p, int sid, const CodegenKey &key);
 // Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
 struct PlainSrc {
   int slot, chan;

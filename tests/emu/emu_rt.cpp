@@ -130,6 +130,14 @@ static std::vector<std::pair<const unsigned char *, size_t>> g_ranges;
 static size_t g_smem_size = 0;
 void wt_emu_register(const void *p, long bytes) { g_ranges.push_back({(const unsigned char *)p, (size_t)bytes}); }
 void wt_emu_clear_ranges() { g_ranges.clear(); }
+long wt_emu_smem_size() { return (long)g_smem_size; }
+bool wt_emu_in_global(const void *p, long bytes) {
+  const unsigned char *a = (const unsigned char *)p;
+  for (auto &r : g_ranges)
+    if (a >= r.first && a + bytes <= r.first + r.second) return true;
+  return false;
+}
+
 void wt_emu_check(const void *p, long bytes, const char *what) {
   const unsigned char *a = (const unsigned char *)p;
   if (a >= wt_emu_smem_array && a + bytes <= wt_emu_smem_array + g_smem_size) return;

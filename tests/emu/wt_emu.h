@@ -75,6 +75,8 @@ int wt_emu_all(int pred);
 void wt_emu_syncwarp();
 void wt_emu_syncthreads();
 unsigned char *wt_emu_smem();
+long wt_emu_smem_size();
+bool wt_emu_in_global(const void *p, long bytes);
 void wt_emu_fail(const char *msg);
 void wt_emu_check(const void *p, long bytes, const char *what);
 void wt_emu_yield();
@@ -221,6 +223,75 @@ static inline void wt_ld8_bf16(const void *p, float &a, float &b, float &c, floa
   a = wt_b2f(v[0]); b = wt_b2f(v[1]); c = wt_b2f(v[2]); d = wt_b2f(v[3]);
   e = wt_b2f(v[4]); f = wt_b2f(v[5]); g = wt_b2f(v[6]); h = wt_b2f(v[7]);
 }
+static inline bool wt_emu_in_smem(const void *p, long bytes) {
+  const unsigned char *a = (const unsigned char *)p;
+  return a >= wt_emu_smem() && a + bytes <= wt_emu_smem() + wt_emu_smem_size();
+}
+static inline float wt_sld(const float *b, int i, int n) {
+  if (i < 0 || i >= n || !wt_emu_in_smem(b + i, 4)) {
+    wt_emu_fail("shared buffer index out of range (load)");
+    return 0.f;
+  }
+  return b[i];
+}
+static inline void wt_sst(float *b, int i, int n, float v) {
+  if (i < 0 || i >= n || !wt_emu_in_smem(b + i, 4)) {
+    wt_emu_fail("shared buffer index out of range (store)");
+    return;
+  }
+  b[i] = v;
+}
+static inline void wt_lds8_f32(const void *p, float &a, float &b, float &c, float &d, float &e, float &f,
+                               float &g, float &h) {
+  if (!wt_emu_in_smem(p, 32) || ((unsigned long)p) % 16 != 0) {
+    wt_emu_fail("shared 32-byte load outside shared memory or misaligned");
+    a = b = c = d = e = f = g = h = 0.f;
+    return;
+  }
+  wt_ld8_f32(p, a, b, c, d, e, f, g, h);
+}
+static inline void wt_lds8_f16(const void *p, float &a, float &b, float &c, float &d, float &e, float &f,
+                               float &g, float &h) {
+  if (!wt_emu_in_smem(p, 16) || ((unsigned long)p) % 16 != 0) {
+    wt_emu_fail("shared 16-byte load outside shared memory or misaligned");
+    a = b = c = d = e = f = g = h = 0.f;
+    return;
+  }
+  wt_ld8_f16(p, a, b, c, d, e, f, g, h);
+}
+static inline void wt_lds8_bf16(const void *p, float &a, float &b, float &c, float &d, float &e, float &f,
+                                float &g, float &h) {
+  if (!wt_emu_in_smem(p, 16) || ((unsigned long)p) % 16 != 0) {
+    wt_emu_fail("shared 16-byte load outside shared memory or misaligned");
+    a = b = c = d = e = f = g = h = 0.f;
+    return;
+  }
+  wt_ld8_bf16(p, a, b, c, d, e, f, g, h);
+}
+static inline float wt_lds1_f32(const void *p) {
+  if (!wt_emu_in_smem(p, 4)) { wt_emu_fail("shared load outside shared memory"); return 0.f; }
+  float v; memcpy(&v, p, 4); return v;
+}
+static inline float wt_lds1_f16(const void *p) {
+  if (!wt_emu_in_smem(p, 2)) { wt_emu_fail("shared load outside shared memory"); return 0.f; }
+  wt_u16 v; memcpy(&v, p, 2); return wt_h2f(v);
+}
+static inline float wt_lds1_bf16(const void *p) {
+  if (!wt_emu_in_smem(p, 2)) { wt_emu_fail("shared load outside shared memory"); return 0.f; }
+  wt_u16 v; memcpy(&v, p, 2); return wt_b2f(v);
+}
+// cp.async: the copy completes at issue (a valid completion order); the
+// source must lie in a registered global buffer, the destination in shared
+// memory, both 16-byte aligned
+static inline void wt_cp_async16(wt_u32 dst, const void *src) {
+  if (dst % 16 != 0 || ((unsigned long)src) % 16 != 0) { wt_emu_fail("cp.async address not 16-byte aligned"); return; }
+  if (!wt_emu_in_smem(wt_emu_sptr(dst), 16)) { wt_emu_fail("cp.async destination outside shared memory"); return; }
+  if (wt_emu_in_smem(src, 16)) { wt_emu_fail("cp.async source in shared memory"); return; }
+  if (!wt_emu_in_global(src, 16)) { wt_emu_fail("cp.async source outside the registered buffers"); return; }
+  memcpy(wt_emu_sptr(dst), src, 16);
+}
+static inline void wt_cp_async_commit() {}
+#define WT_CP_ASYNC_WAIT(n) ((void)(n))
 static inline void wt_ld4_f32(const void *p, float &a, float &b, float &c, float &d) {
   wt_emu_check(p, 16, "load");
   wt_emu_align(p, 16);

@@ -106,3 +106,30 @@ def test_blend_default_schedule_streams_downs():
     groups, params = P.blend_schedule()
     got, d = run_emulated(spec, [A, B, M], groups=groups, params=params)
     assert np.abs(got[0] - oracle_of(spec, [A, B, M])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("w,h,tile_h,vec,nbuf", [(1100, 37, 14, 4, 2), (1100, 9, 3, 8, 1), (2100, 21, 5, 4, 5),
+                                                 (2100, 40, 32, 8, 2)])
+@pytest.mark.parametrize("dtype,tol", [(wt.WT_F32, 1e-6), (wt.WT_BF16, 1.6e-2)])
+def test_down_ring_path(w, h, tile_h, vec, nbuf, dtype, tol):
+    """Images wide enough that interior warps take the cp.async ring path
+    (their columns and both 16-byte halo chunks inside the row), with ring
+    lengths from 1 to 5 steps ahead, next to clamped border warps."""
+    spec = down_spec(channels=3, in_channels=3)
+    name = {wt.WT_F32: "f32", wt.WT_BF16: "bf16"}[dtype]
+    img = rnd(w + h + nbuf, w, h, 3, name)
+    got, d = run_emulated(spec, [img], dtype=dtype, groups=[0],
+                          params=[dict(tile_h=tile_h, vec=vec, n_buffers=nbuf, flags=4)])
+    assert d["smem"] > 0
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= tol
+
+
+def test_down_ring_odd_taps():
+    """Ring path with an even tap count (odd row span: two open output rows)
+    and taps right of the centre only."""
+    for weights, dx0, dy0 in [([[1, 3, 3, 1]] * 4, -1, -2), ([[1, 1, 2]], 1, -3)]:
+        spec = down_spec(weights, dx0=dx0, dy0=dy0, const=-0.5)
+        img = rnd(77 + dx0, 1500, 23)
+        got, _ = run_down(spec, img, 7, 4)
+        ref = oracle_of(spec, [img])[0]
+        assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
