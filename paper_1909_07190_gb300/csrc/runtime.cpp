@@ -235,7 +235,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       L.dst.push_back(s);
       key.dst_dtypes.push_back(plan.loc[s].dtype);
       level_dims(plan.W, plan.H, p.stages[s].level, &L.W, &L.H);
-      const int vo = L.params.vec == 4 ? 4 : 8;  // outputs per lane (default 8)
+      const int vo = L.params.vec == 8 ? 8 : 4;  // outputs per lane (default 4)
       if (p.sched.exec == WT_EXEC_FUSED && down_streamable(down_form(p, s), vo)) {
         // separable down-sampling: producer rows streamed through warps
         key.down = true;
@@ -280,7 +280,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
   static const char kOtptbVersion[] = "wt-otptb-1";  // the block-tile kernel's own changes
   if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
-  static const char kDownVersion[] = "wt-down-3";  // the down-sampling kernel's own changes
+  static const char kDownVersion[] = "wt-down-4";  // the down-sampling kernel's own changes
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;

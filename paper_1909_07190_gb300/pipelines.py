@@ -218,12 +218,15 @@ def blend_groups(levels: int = 6) -> list:
 def blend_schedule(levels: int = 6) -> tuple:
     """(groups, params) of the blend's default schedule: blend_groups(), with
     the pure down-sampling groups of levels 1..levels-2 run as per-stage
-    kernels (a fused group of gathers has nothing to keep on chip, and its
-    one-channel mask stage would be computed once per tile channel) and the
-    other groups fused."""
+    kernels (each a streaming down-sampling kernel: a fused group of gathers
+    has nothing to keep on chip, and its one-channel mask stage would be
+    computed once per tile channel) and the other groups fused."""
     groups = blend_groups(levels)
     plain = 4  # WT_FLAG_PLAIN
-    params = [dict(flags=plain)] * (levels - 2) + [dict()] * (levels)
+    # output rows per warp of the streaming down-sampling kernels: shorter
+    # at the small levels, where parallelism, not the row halo, limits them
+    down_rows = [14, 8] + [4] * max(0, levels - 4)
+    params = [dict(flags=plain, tile_h=t) for t in down_rows[:levels - 2]] + [dict()] * (levels)
     return groups, params
 
 

@@ -69,7 +69,9 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
     os.makedirs(CACHE, exist_ok=True)
     so = os.path.join(CACHE, "%s_%s.so" % (name, h))
     if not os.path.exists(so):
-        src = os.path.join(CACHE, "%s_%s.cpp" % (name, h))
+        # per-process file names: parallel test workers may build the same
+        # kernel at once
+        src = os.path.join(CACHE, "%s_%s.%d.cpp" % (name, h, os.getpid()))
         with open(src, "w") as f:
             f.write(text)
         tmp = so + ".%d.tmp" % os.getpid()
@@ -79,6 +81,7 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
         if r.returncode != 0:
             raise RuntimeError("emulator compile failed:\n" + r.stderr[-5000:])
         os.replace(tmp, so)
+        os.remove(src)
     lib = ctypes.CDLL(so)
     _loaded[h] = lib
     return lib
