@@ -293,6 +293,63 @@ std::string gather_tap(Ctx &c, int gi, int e, int dx, int dy) {
 // lane * V is even (xs and V are), so element e's source column is a
 // constant offset from X0 / 2 (up-sampling: floor((X0 + e) / 2) + dx) or
 // from 2 X0 (down-sampling: 2 (X0 + e) + dx); rows likewise from r.
+// Column of a gather tap relative to the lane's base column: element e of
+// the lane, tap offset dx (DOWN2: base 2 (xs + lane V); UP2: base
+// (xs >> 1) + lane V / 2, xs a multiple of V, so both bases are even).
+int gather_off(int mode, int e, int dx) { return mode == WT_TAP_DOWN2 ? 2 * e + dx : (e >> 1) + dx; }
+
+// Interior tiles: every gather row and column the guard-free body touches
+// lies inside the gather source (the tile's border test includes these
+// margins), so the loads need no clamps and read aligned pairs.
+void emit_gather_prologue_fast(Ctx &c, int ni) {
+  const Node &n = c.g.nodes[ni];
+  auto &o = c.o;
+  c.gvar.clear();
+  struct Tap { int gi, dx, dy; };
+  std::vector<Tap> taps;
+  for (const KOp &op : n.prog)
+    if (op.op == WT_OP_TAP && c.g.nodes[op.node].gather_mode) taps.push_back({op.node, op.dx, op.dy});
+  if (taps.empty()) return;
+  std::map<std::pair<int, int>, std::string> rows;
+  std::map<std::tuple<int, int, int>, std::string> vals;  // (gi, dy, pair start) -> first of two names
+  std::set<int> modes;
+  int id = 0;
+  for (const Tap &t : taps) modes.insert(c.g.nodes[t.gi].gather_mode);
+  for (int m : modes)
+    o << "const int gcb" << m << " = " << (m == WT_TAP_DOWN2 ? "2 * (xs + lane * " + std::to_string(c.V) + ")"
+                                                          : "(xs >> 1) + lane * " + std::to_string(c.V / 2))
+      << ";\n";
+  for (const Tap &t : taps) {
+    const Node &pn = c.g.nodes[t.gi];
+    const int m = pn.gather_mode;
+    const bool down = m == WT_TAP_DOWN2;
+    const std::string S = "ia.src[" + std::to_string(pn.src_index) + "]";
+    const int dt = c.key.src_dtypes.at(pn.src_index);
+    const int esz = elem_bytes(dt);
+    auto rk = std::make_pair(t.gi, t.dy);
+    if (!rows.count(rk)) {
+      std::string v = "gr" + std::to_string(id++);
+      const std::string chan = pn.src_chan >= 0 ? std::to_string(pn.src_chan) : "ch";
+      o << "const unsigned char *" << v << " = (const unsigned char *)" << S << ".ptr + (wt_i64)" << chan << " * "
+        << S << ".plane + (wt_i64)(" << (down ? "2 * r" : "(r >> 1)") << " + (" << t.dy << ")) * " << S
+        << ".pitch + (wt_i64)gcb" << m << " * " << esz << ";\n";
+      rows[rk] = v;
+    }
+    for (int e = 0; e < c.V; e++) {
+      const int off = gather_off(m, e, t.dx);
+      const int p0 = off - (((off % 2) + 2) % 2);  // the aligned pair holding it
+      auto vk = std::make_tuple(t.gi, t.dy, p0);
+      if (!vals.count(vk)) {
+        std::string v = "gv" + std::to_string(id++);
+        o << "float " << v << "a, " << v << "b;\nwt_ld2_" << tname(dt) << "(" << rows[rk] << " + (" << p0 * esz
+          << "), " << v << "a, " << v << "b);\n";
+        vals[vk] = v;
+      }
+      c.gvar[std::make_tuple(t.gi, e, t.dx, t.dy)] = vals[vk] + (off == p0 ? "a" : "b");
+    }
+  }
+}
+
 void emit_gather_prologue(Ctx &c, int ni) {
   const Node &n = c.g.nodes[ni];
   auto &o = c.o;
@@ -644,7 +701,8 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     }
     o << "} else {\n";
   }
-  emit_gather_prologue(c, ni);
+  if (safe) emit_gather_prologue(c, ni);
+  else emit_gather_prologue_fast(c, ni);
   // packed pairs for nodes whose taps all read the producer's own element
   // pairs (dx = 0): a pair shifted by one column would have to be gathered
   // into an aligned register pair first
@@ -842,8 +900,40 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
         << (n.channels > 1 ? "ch" : "0") << " * ia.dst[" << D << "].plane + (wt_i64)(xs + lane * " << V << ") * " << esz
         << ";\n(void)ob" << D << ";\n";
     }
-  o << "const bool border = xs < 0 || xs + " << 32 * V << " > W || y_top < 0 || y0 + T + " << HB
-    << " > H;\n";
+  o << "bool border = xs < 0 || xs + " << 32 * V << " > W || y_top < 0 || y0 + T + " << HB << " > H;\n";
+  // Gather sources: the guard-free body reads them unclamped, in aligned
+  // pairs, at every row it computes (garbage rows included: k from 0 to
+  // the last unrolled step), so a tile whose footprint reaches past a
+  // gather source's edge runs the guarded body.
+  for (size_t gi = 0; gi < g.nodes.size(); gi++) {
+    const Node &gn = g.nodes[gi];
+    if (!gn.gather_mode) continue;
+    int omin = 1 << 20, omax = -(1 << 20), dymin = 1 << 20, dymax = -(1 << 20), dmax = 0, dmin = 1 << 20;
+    for (const Node &cn : g.nodes)
+      for (const KOp &op : cn.prog)
+        if (op.op == WT_OP_TAP && op.node == (int)gi) {
+          for (int e = 0; e < V; e++) {
+            omin = std::min(omin, gather_off(gn.gather_mode, e, op.dx));
+            omax = std::max(omax, gather_off(gn.gather_mode, e, op.dx));
+          }
+          dymin = std::min(dymin, op.dy);
+          dymax = std::max(dymax, op.dy);
+          dmax = std::max(dmax, cn.delay);
+          dmin = std::min(dmin, cn.delay);
+        }
+    if (omin > omax) continue;
+    const int plo = omin - (((omin % 2) + 2) % 2), phi = omax + (((omax % 2) + 2) % 2 == 0 ? 1 : 0);
+    const bool down = gn.gather_mode == WT_TAP_DOWN2;
+    const std::string S = "ia.src[" + std::to_string(gn.src_index) + "]";
+    const std::string cb0 = down ? "2 * xs" : "(xs >> 1)";
+    const std::string cb31 = down ? "2 * (xs + " + std::to_string(31 * V) + ")"
+                                  : "((xs >> 1) + " + std::to_string(31 * V / 2) + ")";
+    const std::string rlo = "(y_top - " + std::to_string(dmax) + ")";
+    const std::string rhi = "(y_top + nsteps + " + std::to_string(c.U - 1 - dmin) + ")";
+    o << "border = border || " << cb0 << " + (" << plo << ") < 0 || " << cb31 << " + (" << phi << ") > " << S
+      << ".W - 1 || " << (down ? "2 * " + rlo : "(" + rlo + " >> 1)") << " + (" << dymin << ") < 0 || "
+      << (down ? "2 * " + rhi : "(" + rhi + " >> 1)") << " + (" << dymax << ") > " << S << ".H - 1;\n";
+  }
   for (int s = 0; s < n_src; s++) {
     const Node *sn = nullptr;
     for (const Node &n : g.nodes)

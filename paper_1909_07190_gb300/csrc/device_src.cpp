@@ -184,6 +184,19 @@ static __device__ __forceinline__ void wt_cp_async16(wt_u32 dst, const void *src
 }
 static __device__ __forceinline__ void wt_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 #define WT_CP_ASYNC_WAIT(n) asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory")
+// ------------------------------- read-only pairs (aligned to their size)
+static __device__ __forceinline__ void wt_ld2_f32(const void *p, float &a, float &b) {
+  const float2 v = __ldg((const float2 *)p);
+  a = v.x; b = v.y;
+}
+static __device__ __forceinline__ void wt_ld2_f16(const void *p, float &a, float &b) {
+  const wt_u32 v = __ldg((const unsigned int *)p);
+  a = wt_h2f((wt_u16)(v & 0xffff)); b = wt_h2f((wt_u16)(v >> 16));
+}
+static __device__ __forceinline__ void wt_ld2_bf16(const void *p, float &a, float &b) {
+  const wt_u32 v = __ldg((const unsigned int *)p);
+  a = __uint_as_float(v << 16); b = __uint_as_float(v & 0xffff0000u);
+}
 // ------------------------------------------------ vector stores (4 lanes)
 static __device__ __forceinline__ void wt_st4_f32(void *p, float a, float b, float c, float d) {
   *(float4 *)p = make_float4(a, b, c, d);

@@ -292,6 +292,27 @@ static inline void wt_cp_async16(wt_u32 dst, const void *src) {
 }
 static inline void wt_cp_async_commit() {}
 #define WT_CP_ASYNC_WAIT(n) ((void)(n))
+static inline void wt_ld2_f32(const void *p, float &a, float &b) {
+  wt_emu_check(p, 8, "load");
+  wt_emu_align(p, 8);
+  float v[2];
+  memcpy(v, p, 8);
+  a = v[0]; b = v[1];
+}
+static inline void wt_ld2_f16(const void *p, float &a, float &b) {
+  wt_emu_check(p, 4, "load");
+  wt_emu_align(p, 4);
+  wt_u16 v[2];
+  memcpy(v, p, 4);
+  a = wt_h2f(v[0]); b = wt_h2f(v[1]);
+}
+static inline void wt_ld2_bf16(const void *p, float &a, float &b) {
+  wt_emu_check(p, 4, "load");
+  wt_emu_align(p, 4);
+  wt_u16 v[2];
+  memcpy(v, p, 4);
+  a = wt_b2f(v[0]); b = wt_b2f(v[1]);
+}
 static inline void wt_ld4_f32(const void *p, float &a, float &b, float &c, float &d) {
   wt_emu_check(p, 16, "load");
   wt_emu_align(p, 16);

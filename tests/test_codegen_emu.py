@@ -221,8 +221,11 @@ def gather_spec(kind):
 
 
 @pytest.mark.parametrize("kind", ["down", "up", "lap"])
-@pytest.mark.parametrize("w,h,tile_h,vec", [(37, 23, 4, 4), (1, 1, 8, 4), (130, 9, 3, 8), (5, 77, 16, 4)])
+@pytest.mark.parametrize("w,h,tile_h,vec", [(37, 23, 4, 4), (1, 1, 8, 4), (130, 9, 3, 8), (5, 77, 16, 4),
+                                            (520, 90, 8, 4), (700, 61, 16, 8), (521, 97, 6, 4)])
 def test_fused_gather_sources(kind, w, h, tile_h, vec):
+    """Small images (every tile a border tile: clamped gathers) and wide
+    ones (interior tiles: unclamped aligned pair gathers)."""
     spec = gather_spec(kind)
     img = rnd(90 + w, w, h)
     ng = 1 if kind == "down" else 2
@@ -232,7 +235,7 @@ def test_fused_gather_sources(kind, w, h, tile_h, vec):
     assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
 
 
-@pytest.mark.parametrize("w,h,tile_h", [(80, 50, 8), (131, 67, 5), (33, 3, 16)])
+@pytest.mark.parametrize("w,h,tile_h", [(80, 50, 8), (131, 67, 5), (33, 3, 16), (520, 140, 14)])
 def test_fused_blend_levels(w, h, tile_h):
     """The 36-stage blend as 10 fused groups, one per level."""
     spec = P.blend()
