@@ -350,6 +350,138 @@ void emit_gather_prologue_fast(Ctx &c, int ni) {
   }
 }
 
+// Rolling windows of up-sampled gather rows (interior tiles, constant row
+// parity per unrolled step): node `ni` at step k computes row r and reads
+// gather rows (r >> 1) + dy, dy in [dymin, dymax]; the window holds those
+// rows for the lane's columns, and advances by one row (one new row
+// loaded) at every step where r is even, i.e. every second step, instead
+// of loading every row at every step.
+struct GWin {
+  int gi = -1, dymin = 0, dymax = 0, omin = 0, omax = 0;
+};
+std::vector<GWin> gather_windows(const Ctx &c, int ni) {
+  std::vector<GWin> r;
+  if (!c.key.even_rows) return r;
+  const Node &n = c.g.nodes[ni];
+  std::map<int, GWin> m;
+  for (const KOp &op : n.prog) {
+    if (op.op != WT_OP_TAP || !c.g.nodes[op.node].gather_mode) continue;
+    if (c.g.nodes[op.node].gather_mode != WT_TAP_UP2) return {};
+    auto it = m.find(op.node);
+    if (it == m.end()) {
+      GWin w;
+      w.gi = op.node;
+      w.dymin = w.dymax = op.dy;
+      w.omin = 1 << 20;
+      w.omax = -(1 << 20);
+      it = m.emplace(op.node, w).first;
+    }
+    GWin &w = it->second;
+    w.dymin = std::min(w.dymin, op.dy);
+    w.dymax = std::max(w.dymax, op.dy);
+    for (int e = 0; e < c.V; e++) {
+      w.omin = std::min(w.omin, gather_off(WT_TAP_UP2, e, op.dx));
+      w.omax = std::max(w.omax, gather_off(WT_TAP_UP2, e, op.dx));
+    }
+  }
+  for (auto &kv : m) r.push_back(kv.second);
+  return r;
+}
+
+std::string gwin_name(int ni, const GWin &w, int row, int off) {
+  return "GW" + std::to_string(ni) + "_" + std::to_string(w.gi) + "_" + std::to_string(row) + "_" +
+         (off < 0 ? "m" + std::to_string(-off) : std::to_string(off));
+}
+
+// Loads gather row `rowexpr` of window w into window row `slot` (aligned
+// pairs covering the window's columns; no clamps: interior tiles only).
+void emit_gwin_load(Ctx &c, int ni, const GWin &w, int slot, const std::string &rowexpr) {
+  auto &o = c.o;
+  const Node &pn = c.g.nodes[w.gi];
+  const std::string S = "ia.src[" + std::to_string(pn.src_index) + "]";
+  const int dt = c.key.src_dtypes.at(pn.src_index);
+  const int esz = elem_bytes(dt);
+  const std::string chan = pn.src_chan >= 0 ? std::to_string(pn.src_chan) : "ch";
+  o << "{ const unsigned char *gwr_ = (const unsigned char *)" << S << ".ptr + (wt_i64)" << chan << " * " << S
+    << ".plane + (wt_i64)(" << rowexpr << ") * " << S << ".pitch + (wt_i64)((xs >> 1) + lane * " << c.V / 2
+    << ") * " << esz << ";\n";
+  const int plo = w.omin - (((w.omin % 2) + 2) % 2);
+  for (int p0 = plo; p0 <= w.omax; p0 += 2) {
+    const std::string a = (p0 >= w.omin && p0 <= w.omax) ? gwin_name(ni, w, slot, p0) : "gwx_";
+    const std::string b = (p0 + 1 >= w.omin && p0 + 1 <= w.omax) ? gwin_name(ni, w, slot, p0 + 1) : "gwx_";
+    o << "wt_ld2_" << tname(dt) << "(gwr_ + (" << p0 * esz << "), " << a << ", " << b << ");\n";
+  }
+  o << "}\n";
+}
+
+// Row parity of node n at unrolled step u (tiles start on even rows).
+int row_parity(const Ctx &c, const Node &n, int u) { return (((u - c.g.halo_t - n.delay) % 2) + 2) % 2; }
+
+void emit_gwin_decl_init(Ctx &c) {
+  auto &o = c.o;
+  bool any = false;
+  for (int ni : c.g.order) {
+    const Node &n = c.g.nodes[ni];
+    if (n.is_source) continue;
+    for (const GWin &w : gather_windows(c, ni)) {
+      const int nr = w.dymax - w.dymin + 1;
+      o << "float";
+      bool first = true;
+      for (int j = 0; j < nr; j++)
+        for (int off = w.omin; off <= w.omax; off++) {
+          o << (first ? " " : ", ") << gwin_name(ni, w, j, off) << " = 0.f";
+          first = false;
+        }
+      o << ";\n";
+      any = true;
+    }
+  }
+  if (!any) return;
+  o << "float gwx_;\n(void)gwx_;\n";
+  // the first step of an interior tile finds its rows in the window: rows
+  // (r0 >> 1) + dy, one row earlier when step 0 itself advances (r0 even)
+  o << "if (!border) {\n";
+  for (int ni : c.g.order) {
+    const Node &n = c.g.nodes[ni];
+    if (n.is_source) continue;
+    for (const GWin &w : gather_windows(c, ni)) {
+      const int adv = row_parity(c, n, 0) == 0 ? 1 : 0;
+      for (int j = 0; j < w.dymax - w.dymin + 1; j++)
+        emit_gwin_load(c, ni, w, j, "((y_top - " + std::to_string(n.delay) + ") >> 1) - " + std::to_string(adv) +
+                                        " + (" + std::to_string(w.dymin + j) + ")");
+    }
+  }
+  o << "}\n";
+}
+
+// Interior step: advance the node's windows where its row is even, then
+// name the taps' values.
+bool emit_gwin_step(Ctx &c, int ni, int u) {
+  const std::vector<GWin> ws = gather_windows(c, ni);
+  if (ws.empty()) return false;
+  auto &o = c.o;
+  const Node &n = c.g.nodes[ni];
+  c.gvar.clear();
+  for (const GWin &w : ws) {
+    const int nr = w.dymax - w.dymin + 1;
+    if (row_parity(c, n, u) == 0) {
+      for (int j = 0; j + 1 < nr; j++)
+        for (int off = w.omin; off <= w.omax; off++)
+          o << gwin_name(ni, w, j, off) << " = " << gwin_name(ni, w, j + 1, off) << ";\n";
+      emit_gwin_load(c, ni, w, nr - 1, "(r >> 1) + (" + std::to_string(w.dymax) + ")");
+    }
+  }
+  for (const KOp &op : n.prog) {
+    if (op.op != WT_OP_TAP || !c.g.nodes[op.node].gather_mode) continue;
+    for (const GWin &w : ws)
+      if (w.gi == op.node)
+        for (int e = 0; e < c.V; e++)
+          c.gvar[std::make_tuple(op.node, e, op.dx, op.dy)] =
+              gwin_name(ni, w, op.dy - w.dymin, gather_off(WT_TAP_UP2, e, op.dx));
+  }
+  return true;
+}
+
 void emit_gather_prologue(Ctx &c, int ni) {
   const Node &n = c.g.nodes[ni];
   auto &o = c.o;
@@ -702,7 +834,7 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     o << "} else {\n";
   }
   if (safe) emit_gather_prologue(c, ni);
-  else emit_gather_prologue_fast(c, ni);
+  else if (!emit_gwin_step(c, ni, u)) emit_gather_prologue_fast(c, ni);
   // packed pairs for nodes whose taps all read the producer's own element
   // pairs (dx = 0): a pair shifted by one column would have to be gathered
   // into an aligned register pair first
@@ -972,6 +1104,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // register windows rotate by renaming).
   // chunk bookkeeping by counters (the block's row in its chunk, kc_, and
   // the chunk, kch_; chunks are a multiple of U rows)
+  emit_gwin_decl_init(c);
   o << "int kc_ = 0, kch_ = 0;\n";
   o << "for (int kb = 0; kb < nsteps; kb += U) {\n";
   // TMA bookkeeping once per block: wait for the chunk this block starts,

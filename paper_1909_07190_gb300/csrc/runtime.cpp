@@ -276,7 +276,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
   if (key.persistent) h = fnv1a(kBatchVersion, sizeof kBatchVersion, h);
   if (!fused) h = fnv1a(kPlainVersion, sizeof kPlainVersion, h);
-  static const char kGatherVersion[] = "wt-gather-3";  // kernels reading other levels
+  static const char kGatherVersion[] = "wt-gather-4";  // kernels reading other levels
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
   static const char kOtptbVersion[] = "wt-otptb-1";  // the block-tile kernel's own changes
   if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
