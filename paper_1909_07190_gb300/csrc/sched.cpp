@@ -130,10 +130,19 @@ std::string micro_source(const Pipeline &p, int sid, const std::string &name) {
   for (const Op &op : S.ops) {
     char b[64];
     switch (op.op) {
-      case WT_OP_CONST:
-        snprintf(b, sizeof b, "(%.9gf)", (double)op.value);
-        st.push_back(b);
-        break;
+      case WT_OP_CONST: {
+        // a valid FP32 literal for every value (integral ones need a point)
+        if (std::isnan(op.value)) {
+          st.push_back("__int_as_float(0x7fc00000)");
+        } else if (std::isinf(op.value)) {
+          st.push_back(op.value > 0 ? "__int_as_float(0x7f800000)" : "__int_as_float(0xff800000)");
+        } else {
+          snprintf(b, sizeof b, "%.9g", (double)op.value);
+          std::string v(b);
+          if (v.find_first_of(".e") == std::string::npos) v += ".0";
+          st.push_back("(" + v + "f)");
+        }
+      } break;
       case WT_OP_XPAR: st.push_back("((float)(it & 1))"); break;
       case WT_OP_YPAR: st.push_back("((float)((it >> 1) & 1))"); break;
       case WT_OP_TAP:
