@@ -226,7 +226,10 @@ def blend_schedule(levels: int = 6) -> tuple:
     # output rows per warp of the streaming down-sampling kernels: shorter
     # at the small levels, where parallelism, not the row halo, limits them
     down_rows = [14, 8] + [4] * max(0, levels - 4)
-    params = [dict(flags=plain, tile_h=t) for t in down_rows[:levels - 2]] + [dict()] * (levels)
+    params = [dict(flags=plain, tile_h=t) for t in down_rows[:levels - 2]]
+    # fused groups from the coarsest level to level 0: short warp tiles
+    # where the level is small (more tiles in flight), 14 rows at levels 1, 0
+    params += [dict(tile_h=8 if lv >= 2 else 14) for lv in range(levels - 1, -1, -1)]
     return groups, params
 
 
