@@ -286,6 +286,15 @@ TuneResult tune(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, 
       s.params[gi] = c.prm;
       vs.push_back(s);
     }
+    // the group's stages as per-stage kernels (single images only: batched
+    // runs need every group fused); a down-sampling stage then runs the
+    // streaming down-sampling kernel
+    if (!batched) {
+      Schedule s = best;
+      s.params[gi] = GroupParams();
+      s.params[gi].plain = 1;
+      vs.push_back(s);
+    }
     pre(vs);
     std::vector<std::pair<double, GroupParams>> timed;
     for (const Schedule &s : vs) {
@@ -301,9 +310,12 @@ TuneResult tune(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, 
                      [](const std::pair<double, GroupParams> &a, const std::pair<double, GroupParams> &b) {
                        return a.first < b.first;
                      });
+    bool has_down = false;  // per-stage kernels whose rows per warp matter
+    for (int sid : seg) has_down = has_down || down_streamable(down_form(p, sid), 4);
     for (size_t k = 0; k < std::min<size_t>(2, timed.size()); k++) {
       if (!std::isfinite(timed[k].first)) continue;
-      for (int T : {8, 11, 14, 17, 20, 23, 26, 32, 40, 48, 64}) {
+      if (timed[k].second.plain && !has_down) continue;
+      for (int T : {4, 8, 11, 14, 17, 20, 23, 26, 32, 40, 48, 64}) {
         if (T > std::max(8, gh) || T == timed[k].second.tile_h) continue;
         Schedule s = best;
         s.params[gi] = timed[k].second;
