@@ -1,5 +1,6 @@
 // C ABI entry points (include/wt.h, include/wt_debug.h).  Every entry point
 // converts internal errors to a wt_status and a thread-local message.
+#include <functional>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -200,6 +201,126 @@ wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const
   });
 }
 
+namespace {
+
+// Rows above (and below) an output row that the pipeline reads from its
+// inputs, over every path of same-level taps (Sec. 2.3 footprints summed
+// along the DAG); -1 when some stage is not at level 0.
+int pipeline_row_halo(const wt::Pipeline &p) {
+  const int n = (int)p.stages.size();
+  for (const wt::Stage &st : p.stages)
+    if (st.level != 0) return -1;
+  std::vector<int> top(n, 0), bot(n, 0);
+  int h = 0;
+  for (int c = n - 1; c >= 0; c--)
+    for (const wt::Edge &e : p.stages[c].edges) {
+      if (e.mode != WT_TAP_SAME) return -1;
+      const int t = top[c] + std::max(0, -e.dymin), b = bot[c] + std::max(0, e.dymax);
+      if (e.producer >= 0) {
+        top[e.producer] = std::max(top[e.producer], t);
+        bot[e.producer] = std::max(bot[e.producer], b);
+      } else {
+        h = std::max(h, std::max(t, b));
+      }
+    }
+  return h;
+}
+
+// wt_run_host in row bands for single-level pipelines: band b's input rows
+// (with the pipeline's halo) are copied in on one stream while band b-1
+// computes on a second and band b-2's output rows are copied out on a
+// third.  A band runs the pipeline on its sub-image; clamp-to-edge at a
+// band edge only changes rows within the halo of that edge, which the band
+// does not keep (its neighbour computes them), so the result equals the
+// whole-image run.  Returns false when the pipeline or the images do not
+// qualify (then the caller runs the whole image at once).
+bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt_image *outputs, int n_out,
+                     cudaStream_t user, wt::Workspace &w, const std::function<void *(int, const wt_image &)> &stage) {
+  const int h = pipeline_row_halo(p);
+  if (h < 0) return false;
+  const int H = inputs[0].height;
+  for (int j = 0; j < n_in; j++)
+    if (inputs[j].height != H) return false;
+  for (int k = 0; k < n_out; k++)
+    if (outputs[k].height != H) return false;
+  const int kBands = 8;
+  const int rows = (H + kBands - 1) / kBands;
+  if (rows < std::max(64, 4 * h)) return false;  // bands too short for their halo
+  const int nb = (H + rows - 1) / rows;
+  for (int i = 0; i < 3; i++)
+    if (!w.band_stream[i])
+      wt::check_rt(cudaStreamCreateWithFlags(&w.band_stream[i], cudaStreamNonBlocking), "cudaStreamCreate");
+  while ((int)w.band_events.size() < 3 * nb + 3) {
+    cudaEvent_t e;
+    wt::check_rt(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    w.band_events.push_back(e);
+  }
+  cudaStream_t sin = w.band_stream[0], scomp = w.band_stream[1], sout = w.band_stream[2];
+  cudaEvent_t *ev = w.band_events.data();
+  // after the caller's earlier work on its stream
+  wt::check_rt(cudaEventRecord(ev[0], user), "cudaEventRecord");
+  for (int i = 0; i < 3; i++) wt::check_rt(cudaStreamWaitEvent(w.band_stream[i], ev[0], 0), "cudaStreamWaitEvent");
+  // device copies: whole inputs; per output two band-sized scratch images
+  std::vector<wt_image> din(inputs, inputs + n_in);
+  for (int j = 0; j < n_in; j++) din[j].data = stage(j, inputs[j]);
+  const int brows = rows + 2 * h;
+  std::vector<wt_image> scratch[2];
+  for (int q = 0; q < 2; q++)
+    for (int k = 0; k < n_out; k++) {
+      wt_image sc = outputs[k];
+      sc.height = std::min(H, brows);
+      sc.data = stage(200 + 16 * q + k, sc);
+      scratch[q].push_back(sc);
+    }
+  int copied = 0;  // input rows [0, copied) are on the device
+  for (int b = 0; b < nb; b++) {
+    const int y0 = b * rows, y1 = std::min(H, y0 + rows);
+    const int ys = std::max(0, y0 - h), ye = std::min(H, y1 + h);
+    // copy in the rows this band needs that are not there yet
+    if (ye > copied) {
+      for (int j = 0; j < n_in; j++)
+        for (int c = 0; c < inputs[j].channels; c++) {
+          const int64_t plane = inputs[j].pitch_bytes * (int64_t)H;
+          const int64_t off = c * plane + copied * inputs[j].pitch_bytes;
+          wt::check_rt(cudaMemcpyAsync((char *)din[j].data + off, (const char *)inputs[j].data + off,
+                                       (size_t)((ye - copied) * inputs[j].pitch_bytes), cudaMemcpyHostToDevice, sin),
+                       "cudaMemcpyAsync(H2D band)");
+        }
+      copied = ye;
+    }
+    cudaEvent_t in_done = ev[1 + 3 * b], comp_done = ev[2 + 3 * b], out_done = ev[3 + 3 * b];
+    wt::check_rt(cudaEventRecord(in_done, sin), "cudaEventRecord");
+    wt::check_rt(cudaStreamWaitEvent(scomp, in_done, 0), "cudaStreamWaitEvent");
+    // the scratch this band writes was copied out two bands ago
+    if (b >= 2) wt::check_rt(cudaStreamWaitEvent(scomp, ev[3 + 3 * (b - 2)], 0), "cudaStreamWaitEvent");
+    std::vector<wt_image> bin(din), bout(scratch[b % 2]);
+    for (int j = 0; j < n_in; j++) {
+      bin[j].data = (char *)din[j].data + (int64_t)ys * din[j].pitch_bytes;
+      bin[j].height = ye - ys;
+    }
+    // a sub-image of a multi-plane image keeps the whole image's plane
+    // stride only if it has one plane; multi-plane inputs were excluded
+    for (int k = 0; k < n_out; k++) bout[k].height = ye - ys;
+    wt::run(p, bin.data(), n_in, bout.data(), n_out, scomp);
+    wt::check_rt(cudaEventRecord(comp_done, scomp), "cudaEventRecord");
+    wt::check_rt(cudaStreamWaitEvent(sout, comp_done, 0), "cudaStreamWaitEvent");
+    for (int k = 0; k < n_out; k++)
+      for (int c = 0; c < outputs[k].channels; c++) {
+        const int64_t hp = outputs[k].pitch_bytes * (int64_t)H, sp = outputs[k].pitch_bytes * (int64_t)(ye - ys);
+        wt::check_rt(cudaMemcpyAsync((char *)outputs[k].data + c * hp + (int64_t)y0 * outputs[k].pitch_bytes,
+                                     (const char *)bout[k].data + c * sp + (int64_t)(y0 - ys) * outputs[k].pitch_bytes,
+                                     (size_t)((y1 - y0) * outputs[k].pitch_bytes), cudaMemcpyDeviceToHost, sout),
+                     "cudaMemcpyAsync(D2H band)");
+      }
+    wt::check_rt(cudaEventRecord(out_done, sout), "cudaEventRecord");
+  }
+  wt::check_rt(cudaStreamSynchronize(sout), "cudaStreamSynchronize");
+  wt::check_rt(cudaStreamSynchronize(scomp), "cudaStreamSynchronize");
+  return true;
+}
+
+}  // namespace
+
 wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
                       int32_t n_outputs, void *stream) {
   return guard([&] {
@@ -228,8 +349,14 @@ wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, 
       }
       return s.ptr;
     };
-    for (int j = 0; j < n_inputs; j++) {
+    for (int j = 0; j < n_inputs; j++)
       if (!inputs[j].data) wt::fail(WT_EINVAL, "null host input");
+    for (int k = 0; k < n_outputs; k++)
+      if (!outputs[k].data) wt::fail(WT_EINVAL, "null host output");
+    bool single_plane = true;
+    for (int j = 0; j < n_inputs; j++) single_plane = single_plane && inputs[j].channels == 1;
+    if (single_plane && run_host_banded(*p, inputs, n_inputs, outputs, n_outputs, st, w, stage)) return;
+    for (int j = 0; j < n_inputs; j++) {
       din[j].data = stage(j, inputs[j]);
       wt::check_rt(cudaMemcpyAsync(din[j].data, inputs[j].data, (size_t)image_bytes(inputs[j]),
                                    cudaMemcpyHostToDevice, st),

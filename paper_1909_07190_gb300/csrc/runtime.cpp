@@ -426,6 +426,9 @@ Workspace::~Workspace() {
   if (err) cudaFree(err);
   for (auto &kv : staging)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
+  for (cudaStream_t s : band_stream)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : band_events) cudaEventDestroy(e);
 }
 
 Workspace &workspace(Pipeline &p, int64_t bytes) {

@@ -65,6 +65,10 @@ struct Workspace {
   int32_t *err = nullptr;
   uint64_t generation = 1;         // bumped when `base` is reallocated
   std::map<int, Staging> staging;  // wt_run_host device copies
+  // wt_run_host row bands: copy-in, compute and copy-out streams, and
+  // events (created on first use)
+  cudaStream_t band_stream[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> band_events;
   ~Workspace();
 };
 
