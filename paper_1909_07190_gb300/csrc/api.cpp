@@ -243,9 +243,12 @@ bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt
     if (inputs[j].height != H) return false;
   for (int k = 0; k < n_out; k++)
     if (outputs[k].height != H) return false;
-  const int kBands = 8;
+  // up to 16 bands (pipeline fill and drain: one band's copy each), none
+  // shorter than 64 rows or 4 halos
+  const int min_rows = std::max(64, 4 * h);
+  const int kBands = std::min(16, H / min_rows);
+  if (kBands < 2) return false;
   const int rows = (H + kBands - 1) / kBands;
-  if (rows < std::max(64, 4 * h)) return false;  // bands too short for their halo
   const int nb = (H + rows - 1) / rows;
   for (int i = 0; i < 3; i++)
     if (!w.band_stream[i])
