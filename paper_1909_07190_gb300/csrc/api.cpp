@@ -253,17 +253,15 @@ bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt
   for (int i = 0; i < 3; i++)
     if (!w.band_stream[i])
       wt::check_rt(cudaStreamCreateWithFlags(&w.band_stream[i], cudaStreamNonBlocking), "cudaStreamCreate");
-  while ((int)w.band_events.size() < 3 * nb + 3) {
+  while ((int)w.band_events.size() < 3 * nb + 4) {
     cudaEvent_t e;
     wt::check_rt(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
     w.band_events.push_back(e);
   }
   cudaStream_t sin = w.band_stream[0], scomp = w.band_stream[1], sout = w.band_stream[2];
   cudaEvent_t *ev = w.band_events.data();
-  // after the caller's earlier work on its stream
-  wt::check_rt(cudaEventRecord(ev[0], user), "cudaEventRecord");
-  for (int i = 0; i < 3; i++) wt::check_rt(cudaStreamWaitEvent(w.band_stream[i], ev[0], 0), "cudaStreamWaitEvent");
   // device copies: whole inputs; per output two band-sized scratch images
+  // (allocated here, never while a graph is being captured)
   std::vector<wt_image> din(inputs, inputs + n_in);
   for (int j = 0; j < n_in; j++) din[j].data = stage(j, inputs[j]);
   const int brows = rows + 2 * h;
@@ -275,50 +273,119 @@ bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt
       sc.data = stage(200 + 16 * q + k, sc);
       scratch[q].push_back(sc);
     }
-  int copied = 0;  // input rows [0, copied) are on the device
+  struct Band {
+    int y0, y1, ys, ye;
+    std::vector<wt_image> in, out;
+  };
+  std::vector<Band> bands;
   for (int b = 0; b < nb; b++) {
-    const int y0 = b * rows, y1 = std::min(H, y0 + rows);
-    const int ys = std::max(0, y0 - h), ye = std::min(H, y1 + h);
-    // copy in the rows this band needs that are not there yet
-    if (ye > copied) {
-      for (int j = 0; j < n_in; j++)
-        for (int c = 0; c < inputs[j].channels; c++) {
-          const int64_t plane = inputs[j].pitch_bytes * (int64_t)H;
-          const int64_t off = c * plane + copied * inputs[j].pitch_bytes;
+    Band B;
+    B.y0 = b * rows;
+    B.y1 = std::min(H, B.y0 + rows);
+    B.ys = std::max(0, B.y0 - h);
+    B.ye = std::min(H, B.y1 + h);
+    B.in = din;
+    B.out = scratch[b % 2];
+    for (int j = 0; j < n_in; j++) {
+      B.in[j].data = (char *)din[j].data + (int64_t)B.ys * din[j].pitch_bytes;
+      B.in[j].height = B.ye - B.ys;
+    }
+    // (a row range of a one-plane input is itself an image; multi-plane
+    // inputs were excluded)
+    for (int k = 0; k < n_out; k++) B.out[k].height = B.ye - B.ys;
+    bands.push_back(B);
+  }
+  // Work of one call, forked from and joined back to `origin`.
+  auto submit = [&](cudaStream_t origin) {
+    wt::check_rt(cudaEventRecord(ev[0], origin), "cudaEventRecord");
+    for (int i = 0; i < 3; i++)
+      if (w.band_stream[i] != origin)
+        wt::check_rt(cudaStreamWaitEvent(w.band_stream[i], ev[0], 0), "cudaStreamWaitEvent");
+    int copied = 0;  // input rows [0, copied) are on the device
+    for (int b = 0; b < nb; b++) {
+      const Band &B = bands[b];
+      // copy in the rows this band needs that are not there yet
+      if (B.ye > copied) {
+        for (int j = 0; j < n_in; j++) {
+          const int64_t off = copied * inputs[j].pitch_bytes;
           wt::check_rt(cudaMemcpyAsync((char *)din[j].data + off, (const char *)inputs[j].data + off,
-                                       (size_t)((ye - copied) * inputs[j].pitch_bytes), cudaMemcpyHostToDevice, sin),
+                                       (size_t)((B.ye - copied) * inputs[j].pitch_bytes), cudaMemcpyHostToDevice,
+                                       sin),
                        "cudaMemcpyAsync(H2D band)");
         }
-      copied = ye;
-    }
-    cudaEvent_t in_done = ev[1 + 3 * b], comp_done = ev[2 + 3 * b], out_done = ev[3 + 3 * b];
-    wt::check_rt(cudaEventRecord(in_done, sin), "cudaEventRecord");
-    wt::check_rt(cudaStreamWaitEvent(scomp, in_done, 0), "cudaStreamWaitEvent");
-    // the scratch this band writes was copied out two bands ago
-    if (b >= 2) wt::check_rt(cudaStreamWaitEvent(scomp, ev[3 + 3 * (b - 2)], 0), "cudaStreamWaitEvent");
-    std::vector<wt_image> bin(din), bout(scratch[b % 2]);
-    for (int j = 0; j < n_in; j++) {
-      bin[j].data = (char *)din[j].data + (int64_t)ys * din[j].pitch_bytes;
-      bin[j].height = ye - ys;
-    }
-    // a sub-image of a multi-plane image keeps the whole image's plane
-    // stride only if it has one plane; multi-plane inputs were excluded
-    for (int k = 0; k < n_out; k++) bout[k].height = ye - ys;
-    wt::run(p, bin.data(), n_in, bout.data(), n_out, scomp);
-    wt::check_rt(cudaEventRecord(comp_done, scomp), "cudaEventRecord");
-    wt::check_rt(cudaStreamWaitEvent(sout, comp_done, 0), "cudaStreamWaitEvent");
-    for (int k = 0; k < n_out; k++)
-      for (int c = 0; c < outputs[k].channels; c++) {
-        const int64_t hp = outputs[k].pitch_bytes * (int64_t)H, sp = outputs[k].pitch_bytes * (int64_t)(ye - ys);
-        wt::check_rt(cudaMemcpyAsync((char *)outputs[k].data + c * hp + (int64_t)y0 * outputs[k].pitch_bytes,
-                                     (const char *)bout[k].data + c * sp + (int64_t)(y0 - ys) * outputs[k].pitch_bytes,
-                                     (size_t)((y1 - y0) * outputs[k].pitch_bytes), cudaMemcpyDeviceToHost, sout),
-                     "cudaMemcpyAsync(D2H band)");
+        copied = B.ye;
       }
-    wt::check_rt(cudaEventRecord(out_done, sout), "cudaEventRecord");
+      cudaEvent_t in_done = ev[1 + 3 * b], comp_done = ev[2 + 3 * b], out_done = ev[3 + 3 * b];
+      wt::check_rt(cudaEventRecord(in_done, sin), "cudaEventRecord");
+      wt::check_rt(cudaStreamWaitEvent(scomp, in_done, 0), "cudaStreamWaitEvent");
+      // the scratch this band writes was copied out two bands ago
+      if (b >= 2) wt::check_rt(cudaStreamWaitEvent(scomp, ev[3 + 3 * (b - 2)], 0), "cudaStreamWaitEvent");
+      wt::run(p, B.in.data(), n_in, B.out.data(), n_out, scomp);
+      wt::check_rt(cudaEventRecord(comp_done, scomp), "cudaEventRecord");
+      wt::check_rt(cudaStreamWaitEvent(sout, comp_done, 0), "cudaStreamWaitEvent");
+      for (int k = 0; k < n_out; k++)
+        for (int c = 0; c < outputs[k].channels; c++) {
+          const int64_t hp = outputs[k].pitch_bytes * (int64_t)H;
+          const int64_t sp = outputs[k].pitch_bytes * (int64_t)(B.ye - B.ys);
+          wt::check_rt(
+              cudaMemcpyAsync((char *)outputs[k].data + c * hp + (int64_t)B.y0 * outputs[k].pitch_bytes,
+                              (const char *)B.out[k].data + c * sp + (int64_t)(B.y0 - B.ys) * outputs[k].pitch_bytes,
+                              (size_t)((B.y1 - B.y0) * outputs[k].pitch_bytes), cudaMemcpyDeviceToHost, sout),
+              "cudaMemcpyAsync(D2H band)");
+        }
+      wt::check_rt(cudaEventRecord(out_done, sout), "cudaEventRecord");
+    }
+    // join
+    cudaEvent_t jc = ev[1 + 3 * nb], jo = ev[2 + 3 * nb];
+    wt::check_rt(cudaEventRecord(jc, scomp), "cudaEventRecord");
+    wt::check_rt(cudaEventRecord(jo, sout), "cudaEventRecord");
+    wt::check_rt(cudaStreamWaitEvent(origin, jc, 0), "cudaStreamWaitEvent");
+    wt::check_rt(cudaStreamWaitEvent(origin, jo, 0), "cudaStreamWaitEvent");
+    if (origin != sin) {
+      cudaEvent_t ji = ev[3 + 3 * nb];
+      wt::check_rt(cudaEventRecord(ji, sin), "cudaEventRecord");
+      wt::check_rt(cudaStreamWaitEvent(origin, ji, 0), "cudaStreamWaitEvent");
+    }
+  };
+  // The same images again: replay the captured call (one launch instead of
+  // some ten API calls per band); the second time: capture it.
+  std::string key((const char *)inputs, sizeof(wt_image) * n_in);
+  key.append((const char *)outputs, sizeof(wt_image) * n_out);
+  key += "|" + std::to_string(p.sched_version) + "|" + std::to_string(w.generation);
+  auto it = w.host_graphs.find(key);
+  if (it != w.host_graphs.end() && it->second) {
+    wt::check_rt(cudaGraphLaunch(it->second, user), "cudaGraphLaunch");
+    wt::check_rt(cudaStreamSynchronize(user), "cudaStreamSynchronize");
+    return true;
   }
-  wt::check_rt(cudaStreamSynchronize(sout), "cudaStreamSynchronize");
-  wt::check_rt(cudaStreamSynchronize(scomp), "cudaStreamSynchronize");
+  bool cached = true;  // every band's launches planned: nothing but launches to capture
+  for (const Band &B : bands) cached = cached && wt::cached_run(p, B.in.data(), n_in, B.out.data(), n_out);
+  if (it != w.host_graphs.end() && cached) {
+    wt::check_rt(cudaStreamBeginCapture(sin, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    try {
+      submit(sin);
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(sin, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t g = nullptr;
+    wt::check_rt(cudaStreamEndCapture(sin, &g), "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    wt::check_rt(ie, "cudaGraphInstantiate");
+    it->second = ex;
+    wt::check_rt(cudaGraphLaunch(ex, user), "cudaGraphLaunch");
+    wt::check_rt(cudaStreamSynchronize(user), "cudaStreamSynchronize");
+    return true;
+  }
+  submit(user);
+  wt::check_rt(cudaStreamSynchronize(user), "cudaStreamSynchronize");
+  if (w.host_graphs.size() >= 64) w.clear_host_graphs();
+  w.host_graphs.emplace(key, nullptr);
   return true;
 }
 
@@ -338,6 +405,7 @@ wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, 
       int64_t need = image_bytes(h);
       wt::Staging &s = w.staging[key];
       if (s.bytes < need) {
+        w.clear_host_graphs();  // captured calls use the old buffers
         if (s.ptr) {
           wt::check_rt(cudaStreamSynchronize(st), "cudaStreamSynchronize");
           cudaFree(s.ptr);

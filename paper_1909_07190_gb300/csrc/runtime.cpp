@@ -421,7 +421,14 @@ void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream) {
 
 // ------------------------------------------------------------- workspace
 
+void Workspace::clear_host_graphs() {
+  for (auto &kv : host_graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  host_graphs.clear();
+}
+
 Workspace::~Workspace() {
+  clear_host_graphs();
   if (base) cudaFree(base);
   if (err) cudaFree(err);
   for (auto &kv : staging)

@@ -69,6 +69,10 @@ struct Workspace {
   // events (created on first use)
   cudaStream_t band_stream[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> band_events;
+  // banded host runs captured as CUDA graphs, by image descriptors (null:
+  // seen once, captured at the next call)
+  std::map<std::string, cudaGraphExec_t> host_graphs;
+  void clear_host_graphs();
   ~Workspace();
 };
 

@@ -75,3 +75,37 @@ def test_run_host_bands_multi_output_and_planes():
     ref = oracle_out(spec, [img])
     for g, r in zip(got, ref):
         assert np.abs(g - r).max() <= 1e-5
+
+
+def test_run_host_repeated_calls_replay():
+    """Calls with the same host images: the first runs the bands directly,
+    the second captures them into a CUDA graph, later ones replay it.  New
+    input contents each call; every result against the device run."""
+    wt = wtmod()
+    spec = P.harris()
+    W, H = 1024, 1536
+    p = wt.Pipeline(spec)
+    hin = wt.DeviceImage(1, H, W, device="cpu", pin_host=True)
+    hout = wt.DeviceImage(1, H, W, device="cpu", pin_host=True)
+    din, dout = wt.DeviceImage(1, H, W), wt.DeviceImage(1, H, W)
+    for call in range(4):
+        img = rnd(100 + call, W, H)
+        hin.view().copy_(torch.from_numpy(img))
+        p.run_host([hin.image()], [hout.image()], stream())
+        din.view().copy_(hin.view())
+        p.run([din.image()], [dout.image()], stream())
+        p.check(stream())
+        torch.cuda.synchronize()
+        assert torch.equal(hout.view(), dout.view().cpu()), call
+    # other host buffers of the same size, then the first ones again
+    hin2 = wt.DeviceImage(1, H, W, device="cpu", pin_host=True)
+    hout2 = wt.DeviceImage(1, H, W, device="cpu", pin_host=True)
+    hin2.view().copy_(hin.view() * 0.5)
+    for _ in range(3):
+        p.run_host([hin2.image()], [hout2.image()], stream())
+    p.run_host([hin.image()], [hout.image()], stream())
+    din.view().copy_(hin2.view())
+    p.run([din.image()], [dout.image()], stream())
+    torch.cuda.synchronize()
+    assert torch.equal(hout2.view(), dout.view().cpu())
+    assert not torch.equal(hout2.view(), hout.view())
