@@ -243,10 +243,13 @@ bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt
     if (inputs[j].height != H) return false;
   for (int k = 0; k < n_out; k++)
     if (outputs[k].height != H) return false;
-  // up to 16 bands (pipeline fill and drain: one band's copy each), none
-  // shorter than 64 rows or 4 halos
+  // Up to 16 bands (pipeline fill and drain cost one band's copies), none
+  // shorter than 64 rows or 4 halos, and none copying less than 4 MiB in
+  // (shorter copies lose link bandwidth to per-copy latency).
+  int64_t in_bytes = 0;
+  for (int j = 0; j < n_in; j++) in_bytes += image_bytes(inputs[j]);
   const int min_rows = std::max(64, 4 * h);
-  const int kBands = std::min(16, H / min_rows);
+  const int kBands = (int)std::min<int64_t>({16, H / min_rows, in_bytes / (4 << 20)});
   if (kBands < 2) return false;
   const int rows = (H + kBands - 1) / kBands;
   const int nb = (H + rows - 1) / rows;
