@@ -43,12 +43,13 @@ def host_vs_device(spec, img, dtype="f32", groups=None, params=None):
     return [h.view().float().numpy() for h in hout]
 
 
-@pytest.mark.parametrize("W,H", [(1000, 1100), (4096, 4096), (333, 2049)])
+@pytest.mark.parametrize("W,H", [(1536, 1500), (4096, 4096), (1100, 3001)])
 def test_run_host_bands_harris(W, H):
+    """Images of 2 to 16 bands (at least 4 MiB of input per band)."""
     spec = P.harris()
     img = rnd(W + H, W, H)
     got = host_vs_device(spec, img)
-    if W * H <= 1100 * 1000:
+    if W * H <= 1536 * 1500:
         ref = oracle_out(spec, [img])[0]
         assert np.abs(got[0][0] - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
 
@@ -56,7 +57,7 @@ def test_run_host_bands_harris(W, H):
 def test_run_host_bands_multi_group_f16():
     """Sharpen as three groups (intermediates in the workspace), FP16."""
     spec = P.sharpen()
-    img = rnd(7, 2048, 1500, dtype="f16")
+    img = rnd(7, 4096, 2048, dtype="f16")
     got = host_vs_device(spec, img, "f16", groups=[0, 1, 2], params=[dict(tile_h=16)] * 3)
     assert np.abs(got[0][0] - oracle_out(spec, [img])[0]).max() <= 2e-3
 
@@ -70,7 +71,7 @@ def test_run_host_bands_multi_output_and_planes():
     s2 = b.stage("edge", P.ref(s0, 1, 0) - P.ref(s0, -1, 3))
     b.output(s1, s2)
     spec = b.build()
-    img = rnd(8, 700, 900)
+    img = rnd(8, 1500, 1500)
     got = host_vs_device(spec, img)
     ref = oracle_out(spec, [img])
     for g, r in zip(got, ref):
@@ -83,7 +84,7 @@ def test_run_host_repeated_calls_replay():
     input contents each call; every result against the device run."""
     wt = wtmod()
     spec = P.harris()
-    W, H = 1024, 1536
+    W, H = 2048, 1536
     p = wt.Pipeline(spec)
     hin = wt.DeviceImage(1, H, W, device="cpu", pin_host=True)
     hout = wt.DeviceImage(1, H, W, device="cpu", pin_host=True)
