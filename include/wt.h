@@ -257,8 +257,18 @@ wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                  const wt_image *outputs, int32_t n_outputs, void *stream);
 
 /* Same computation with host buffers: copies inputs to device (inside the
- * call), runs, copies outputs back and synchronizes `stream`.  Host images
- * use the same layout rules; pinned memory makes the copies asynchronous. */
+ * call), runs, copies outputs back; returns when the outputs are on the
+ * host.  Work is ordered after earlier work on `stream`.  Host images use
+ * the same layout rules; pinned memory makes the copies asynchronous.
+ * Pipelines whose stages are all at level 0, with one-plane inputs of at
+ * least 8 MiB, run in row bands (each band's rows plus the pipeline's row
+ * halo; results identical to the whole-image run) with the copy-in, the
+ * compute and the copy-out of consecutive bands overlapped on the library's
+ * own streams.  The second call with the same host image descriptors
+ * captures that work as a CUDA graph; later calls with them replay it, so
+ * the host buffers must stay allocated while the pipeline may be called
+ * with them (a different size or schedule discards the captured graphs).
+ * Device staging buffers are allocated on first use and kept.             */
 wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                       const wt_image *outputs, int32_t n_outputs, void *stream);
 
