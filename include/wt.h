@@ -265,10 +265,9 @@ wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
  * halo; results identical to the whole-image run) with the copy-in, the
  * compute and the copy-out of consecutive bands overlapped on the library's
  * own streams.  The second call with the same host image descriptors
- * captures that work as a CUDA graph; later calls with them replay it, so
- * the host buffers must stay allocated while the pipeline may be called
- * with them (a different size or schedule discards the captured graphs).
- * Device staging buffers are allocated on first use and kept.             */
+ * captures that work as a CUDA graph; later calls with them replay it (a
+ * new schedule or larger staging discards the captured graphs).  Device
+ * staging buffers are allocated on first use and kept.                    */
 wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                       const wt_image *outputs, int32_t n_outputs, void *stream);
 
