@@ -513,9 +513,13 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
   g.unroll = (int)U;
   g.max_src_window = 1;
   for (int i = 0; i < n_src; i++) g.max_src_window = std::max(g.max_src_window, g.nodes[i].window);
-  if (n_src + g.n_gather > kMaxSrc) {
+  if (n_src > kMaxSrc) {
     g.fusable = false;
-    g.why_not = "more than " + std::to_string(kMaxSrc) + " sources";
+    g.why_not = "more than " + std::to_string(kMaxSrc) + " staged sources";
+  }
+  if (n_src + g.n_gather > kMaxAllSrc) {
+    g.fusable = false;
+    g.why_not = "more than " + std::to_string(kMaxAllSrc) + " sources";
   }
   if ((int)g.liveouts.size() > kMaxDst) {
     g.fusable = false;

@@ -1157,7 +1157,7 @@ std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid) {
 std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const std::string &kname) {
   const Stage &S = p.stages[sid];
   std::vector<PlainSrc> srcs = plain_sources(p, sid);
-  if ((int)srcs.size() > kMaxSrc) fail(WT_EUNSUPPORTED, "stage reads more than 8 sources");
+  if ((int)srcs.size() > kMaxAllSrc) fail(WT_EUNSUPPORTED, "stage reads more than 24 sources");
   // Output pixels per thread.  With 8 the first column x0 of every row
   // segment a thread reads (x0, 2 x0 or x0 / 2) is a multiple of 4, so
   // interior threads load segments with aligned 4-element vectors.

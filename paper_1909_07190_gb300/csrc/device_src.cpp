@@ -16,8 +16,8 @@ struct __align__(64) WtTmap { wt_u64 v[16]; };
 struct WtSrc { const void *ptr; int W, H, C, dtype; wt_i64 pitch, plane; };
 struct WtDst { void *ptr; int W, H, C, dtype; wt_i64 pitch, plane; };
 struct __align__(64) WtArgs {
-  WtTmap tmap[8];
-  WtSrc src[8];
+  WtTmap tmap[8];  // TMA-staged sources
+  WtSrc src[24];   // staged sources, then gather sources
   WtDst dst[8];
   int W, H;
   int tile_h, tiles_x, tiles_y, n_tiles;

@@ -12,7 +12,8 @@
 
 namespace wt {
 
-constexpr int kMaxSrc = 8;     // distinct external sources per group kernel
+constexpr int kMaxSrc = 8;     // TMA-staged sources per group kernel
+constexpr int kMaxAllSrc = 24; // all external sources (staged and gathered)
 constexpr int kMaxDst = 8;     // liveouts per group kernel
 constexpr int kMaxOps = 256;   // ops per stage program
 constexpr int kMaxStack = 32;  // postfix stack depth
@@ -170,7 +171,7 @@ struct DstDesc {
 };
 struct alignas(64) KernelArgs {
   TmapBytes tmap[kMaxSrc];
-  SrcDesc src[kMaxSrc];
+  SrcDesc src[kMaxAllSrc];
   DstDesc dst[kMaxDst];
   int32_t W, H;            // domain of the group's level
   int32_t tile_h, tiles_x, tiles_y, n_tiles;

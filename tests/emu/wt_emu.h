@@ -32,7 +32,7 @@ struct WtSrc { const void *ptr; int W, H, C, dtype; wt_i64 pitch, plane; };
 struct WtDst { void *ptr; int W, H, C, dtype; wt_i64 pitch, plane; };
 struct alignas(64) WtArgs {
   WtTmap tmap[8];
-  WtSrc src[8];
+  WtSrc src[24];
   WtDst dst[8];
   int W, H;
   int tile_h, tiles_x, tiles_y, n_tiles;
