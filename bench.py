@@ -48,6 +48,8 @@ WORKLOADS = {
     "harris_batch": ("harris", 0, 0, "f16", I.SEED_BASE + 3),
     # two 8192x8192x3 images and a smooth mask, 6-level pyramids (36 stages)
     "blend": ("blend", 8192, 8192, "bf16", I.SEED_BASE + 5),
+    # bilateral filter through a grid of 8x8-pixel cells and 8 intensity bins
+    "bilateral": ("bilateral", 4096, 4096, "f32", I.SEED_BASE + 6),
 }
 BATCH_IMAGES = 512
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -238,6 +240,9 @@ def run_reference(args, rank):
         imgs = [I.round_to(I.uniform_image(seed * 1000 + i, w, h)[0], dt) for i, (w, h) in
                 enumerate(sizes[:max(1, args.steps + args.warmup)])]
         sample = "one image of the 512-image batch per step (its sizes in order)"
+    elif name == "bilateral":
+        imgs = [I.round_to(I.uniform_image(seed, W, H)[0][:1024, :1024], dt)]
+        sample = "one 1024x1024 crop of the %dx%d image per step" % (W, H)
     else:
         imgs = [I.round_to(I.uniform_image(seed, W, H)[0], dt)]
         sample = "one full %dx%d image per step" % (W, H)
@@ -304,6 +309,17 @@ def launch_io_bytes(spec, stages, W, H, esz):
     return sum(size(p) for p in reads) + sum(size(s) for s in writes)
 
 
+def dominant_launch(pipe, ins, outs, spec, W, H, esz, sp):
+    """(kernel name, algorithmic bytes, mean ms, launches) of the launch of
+    one run that takes the most time, from per-launch CUDA events on the
+    stream."""
+    t = pipe.time_launches(ins, outs, 20, sp)
+    i = max(range(len(t)), key=lambda k: t[k][3])
+    first, n, _, ms = t[i]
+    return (pipe.kernel_name(i, ins, outs), launch_io_bytes(spec, list(range(first, first + n)), W, H, esz), ms,
+            len(t))
+
+
 class Single:
     """One image per step, rotating over buffer sets larger than 3x L2."""
 
@@ -331,6 +347,10 @@ class Single:
     def kernel_name(self, pipe):
         return pipe.debug_kernel(0, [self.ins[0].image()], [self.outs[0].image()])["name"]
 
+    def dominant(self, pipe, sp, spec):
+        return dominant_launch(pipe, [self.ins[0].image()], [self.outs[0].image()], spec, self.W, self.H, self.esz,
+                               sp)
+
     def e2e(self, pipe, sp, warmup, steps):
         wt, torch = self.wt, self.torch
         hin = wt.DeviceImage(1, self.H, self.W, self.dtype, device="cpu", pin_host=True)
@@ -346,6 +366,19 @@ class Single:
 
     def cpu_sample(self, dts):
         return I.round_to(self.img, dts)
+
+
+class Grid(Single):
+    """The bilateral filter through a grid: one image per step like Single,
+    with the pipeline's level-by-level schedule; the CPU oracle runs on a
+    1024x1024 crop (its grid at level 1 alone is 16 planes)."""
+
+    def schedule(self, fused, plain):
+        groups, params = P.bilateral_schedule()
+        fused.schedule(groups=groups, params=params)
+
+    def cpu_sample(self, dts):
+        return I.round_to(self.img[:1024, :1024], dts)
 
 
 class Blend:
@@ -395,13 +428,8 @@ class Blend:
         return pipe.kernel_name(index, [x.image() for x in self.ins[0]], [self.outs[0].image()])
 
     def dominant(self, pipe, sp, spec):
-        """(kernel name, algorithmic bytes, mean ms) of the launch that takes
-        the most time, from per-launch CUDA events on the stream."""
-        t = pipe.time_launches([x.image() for x in self.ins[0]], [self.outs[0].image()], 20, sp)
-        i = max(range(len(t)), key=lambda k: t[k][3])
-        first, n, _, ms = t[i]
-        stages = list(range(first, first + n))
-        return self.kernel_name(pipe, i), launch_io_bytes(spec, stages, self.W, self.H, self.esz), ms, len(t)
+        return dominant_launch(pipe, [x.image() for x in self.ins[0]], [self.outs[0].image()], spec, self.W, self.H,
+                               self.esz, sp)
 
     def e2e(self, pipe, sp, warmup, steps):
         wt, torch = self.wt, self.torch
@@ -504,6 +532,8 @@ def run_ours(args, rank, world, local):
         work = Batch(wt, torch, spec, dtype, seed + 7919 * rank)
     elif name == "blend":
         work = Blend(wt, torch, spec, W, H, dtype, seed + 7919 * rank)
+    elif name == "bilateral":
+        work = Grid(wt, torch, spec, W, H, dtype, seed + rank, local)
     else:
         work = Single(wt, torch, spec, W, H, dtype, seed + rank, local)
     stream = torch.cuda.current_stream()
@@ -514,7 +544,7 @@ def run_ours(args, rank, world, local):
         work.schedule(fused, None)
     if args.params:
         prm = json.loads(args.params)
-        if hasattr(work, "schedule"):
+        if name == "blend":
             groups, params = P.blend_schedule()
             fused.schedule(groups=groups, params=[dict(p, **prm) for p in params])
         else:
@@ -644,7 +674,7 @@ def run_ours(args, rank, world, local):
         else:
             img = work.cpu_sample(dts)
             r, cores, n, dt = cpu_oracle_rate(spec, img, args.cpu_seconds)
-            sample = "%d full %dx%d images, %.1f s" % (n, img.shape[-1], img.shape[-2], dt)
+            sample = "%d images of %dx%d, %.1f s" % (n, img.shape[-1], img.shape[-2], dt)
         line["cpu_baseline"] = {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -50,7 +50,9 @@ typedef enum {
   WT_OP_MIN = 7, WT_OP_MAX = 8,
   WT_OP_NEG = 9, WT_OP_ABS = 10, WT_OP_SQRT = 11,
   WT_OP_XPAR = 12, /* push (x & 1) of the output point, as 0.0 or 1.0       */
-  WT_OP_YPAR = 13  /* push (y & 1) of the output point                      */
+  WT_OP_YPAR = 13, /* push (y & 1) of the output point                      */
+  WT_OP_CHAN = 14  /* push the output point's channel index (0.0, 1.0, ...):
+                      per-plane programs such as a histogram's bins         */
 } wt_opcode;
 
 /* How a tap maps the output point (x, y) to the producer point; these are

@@ -54,7 +54,7 @@ int or_dag_shapes(const or_stage *st, int n_st, const or_input *in, int n_in,
     for (int i = 0; i < S->n_ops; i++) {
       const or_op *o = &S->ops[i];
       switch (o->op) {
-        case OR_CONST: case OR_XPAR: case OR_YPAR: depth++; break;
+        case OR_CONST: case OR_XPAR: case OR_YPAR: case OR_CHAN: depth++; break;
         case OR_TAP: {
           if (o->slot < 0 || o->slot >= S->n_in) return -4;
           int p = S->in[o->slot];
@@ -112,6 +112,7 @@ static double eval_point(const or_stage *S, const src_box *src, int x, int y, in
       case OR_CONST: stk[sp++] = o->value; break;
       case OR_XPAR: stk[sp++] = (double)(x & 1); break;
       case OR_YPAR: stk[sp++] = (double)(y & 1); break;
+      case OR_CHAN: stk[sp++] = (double)c; break;
       case OR_TAP: {
         const src_box *p = &src[o->slot];
         int px = clampi(tap_coord(o->mode, x, o->dx), 0, p->W - 1);
@@ -326,6 +327,7 @@ static double brute_rec(const or_stage *st, const int32_t *W, const int32_t *H,
       case OR_CONST: stk[sp++] = o->value; break;
       case OR_XPAR: stk[sp++] = (double)(x & 1); break;
       case OR_YPAR: stk[sp++] = (double)(y & 1); break;
+      case OR_CHAN: stk[sp++] = (double)c; break;
       case OR_TAP: {
         int p = S->in[o->slot];
         int pw, ph, pcn;

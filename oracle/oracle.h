@@ -41,7 +41,8 @@ enum or_opcode {
   OR_MIN = 7, OR_MAX = 8,
   OR_NEG = 9, OR_ABS = 10, OR_SQRT = 11,
   OR_XPAR = 12, /* push (x & 1) of the consumer point           */
-  OR_YPAR = 13  /* push (y & 1) of the consumer point           */
+  OR_YPAR = 13, /* push (y & 1) of the consumer point           */
+  OR_CHAN = 14  /* push the consumer point's channel index      */
 };
 enum or_tapmode { OR_SAME = 0, OR_DOWN2 = 1, OR_UP2 = 2 };
 

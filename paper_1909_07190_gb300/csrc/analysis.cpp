@@ -124,7 +124,7 @@ Lin linear_form(const std::vector<KOp> &prog) {
         st.pop_back();
         st.back() = bad;
         break;
-      case WT_OP_XPAR: case WT_OP_YPAR: st.push_back(bad); break;
+      case WT_OP_XPAR: case WT_OP_YPAR: case WT_OP_CHAN: st.push_back(bad); break;
       default: st.back() = bad;  // abs, sqrt: not linear in the taps
     }
   }

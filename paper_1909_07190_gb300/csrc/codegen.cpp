@@ -550,6 +550,8 @@ std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
     switch (op.op) {
       case WT_OP_CONST: st.push_back(konst(op.value)); break;
       case WT_OP_XPAR: st.push_back(konst((float)(e & 1))); break;
+      // a one-plane stage is plane 0 whichever tile channel computes it
+      case WT_OP_CHAN: st.push_back(cn.channels == 1 ? konst(0.f) : expr("((float)ch)")); break;
       case WT_OP_YPAR:
         if (c.key.even_rows) {
           // r = y_top + kb + u - delay with y_top = y0 - halo_t, y0 and kb even
@@ -644,6 +646,14 @@ std::vector<XN> build_tree(Ctx &c, int ni, int e, int u) {
       case WT_OP_CONST: x.c = op.value; break;
       case WT_OP_XPAR: x.op = WT_OP_CONST; x.c = (float)(e & 1); break;
       case WT_OP_YPAR: x.leaf = "((float)(r & 1))"; break;
+      case WT_OP_CHAN:
+        if (cn.channels == 1) {
+          x.op = WT_OP_CONST;
+          x.c = 0.f;
+        } else {
+          x.leaf = "((float)ch)";
+        }
+        break;
       case WT_OP_TAP: {
         const Node &pn = c.g.nodes[op.node];
         int a = cn.delay - pn.delay - op.dy;
@@ -682,7 +692,7 @@ struct PairEmit {
   std::string emit(int i) {
     const XN &x = A[i], &y = B[i];
     switch (x.op) {
-      case WT_OP_CONST: case WT_OP_TAP: case WT_OP_YPAR:
+      case WT_OP_CONST: case WT_OP_TAP: case WT_OP_YPAR: case WT_OP_CHAN:
         return def("wt_pk(" + leaf(x) + ", " + leaf(y) + ")");
       case WT_OP_ADD: {
         if (A[x.b].op == WT_OP_MUL) {
@@ -1244,6 +1254,7 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
         case WT_OP_CONST: st.push_back(flt(op.value)); break;
         case WT_OP_XPAR: st.push_back("((float)((x0 + " + std::to_string(e) + ") & 1))"); break;
         case WT_OP_YPAR: st.push_back("((float)(y & 1))"); break;
+        case WT_OP_CHAN: st.push_back("((float)ch)"); break;
         case WT_OP_TAP: {
           int pid = S.inputs[op.slot];
           int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];

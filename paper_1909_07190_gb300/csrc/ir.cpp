@@ -72,7 +72,7 @@ void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch
       q.op = o.op; q.slot = o.slot; q.dx = o.dx; q.dy = o.dy;
       q.chan = o.chan; q.mode = o.mode; q.value = o.value;
       switch (o.op) {
-        case WT_OP_CONST: case WT_OP_XPAR: case WT_OP_YPAR:
+        case WT_OP_CONST: case WT_OP_XPAR: case WT_OP_YPAR: case WT_OP_CHAN:
           depth++;
           break;
         case WT_OP_TAP: {

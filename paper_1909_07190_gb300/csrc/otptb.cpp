@@ -133,6 +133,7 @@ std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &
           case WT_OP_CONST: st.push_back(lit(op.value)); break;
           case WT_OP_XPAR: st.push_back("((float)(xc & 1))"); break;
           case WT_OP_YPAR: st.push_back("((float)(yc & 1))"); break;
+          case WT_OP_CHAN: st.push_back(n.channels == 1 ? "(0.0f)" : "((float)ch)"); break;
           case WT_OP_TAP: {
             const int q = op.node;
             st.push_back("wt_sld(" + buf(q) + ", (yc + (" + std::to_string(op.dy) + ") - y0 - (" +

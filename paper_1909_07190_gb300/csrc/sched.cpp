@@ -145,6 +145,7 @@ std::string micro_source(const Pipeline &p, int sid, const std::string &name) {
       } break;
       case WT_OP_XPAR: st.push_back("((float)(it & 1))"); break;
       case WT_OP_YPAR: st.push_back("((float)((it >> 1) & 1))"); break;
+      case WT_OP_CHAN: st.push_back("((float)((it >> 2) & 7))"); break;
       case WT_OP_TAP:
         snprintf(b, sizeof b, "sm[(base + %d) & 1023]", 37 * tap++ + 11 * op.dx + 101 * op.dy);
         st.push_back(b);

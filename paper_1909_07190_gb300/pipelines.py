@@ -56,6 +56,7 @@ def esqrt(a) -> E: return E(E.of(a).ops + [("sqrt",)])
 
 XPAR = E([("xpar",)])
 YPAR = E([("ypar",)])
+CHAN = E([("chan",)])  # the output point's channel index
 
 
 def ref(producer: int, dx: int = 0, dy: int = 0, chan: int = -1, mode: str = "same") -> E:
@@ -245,7 +246,88 @@ def blur3(channels: int = 1) -> dict:
     return b.build()
 
 
+def _grid_stages(b: "Builder", inp: int, bins: int, levels: int) -> int:
+    """Stages of a bilateral grid's construction; returns the blurred grid.
+
+    Channel z < bins of a grid cell holds the sum over the cell's pixels of
+    the tent weight max(0, 1 - |I (bins - 1) - z|), channel bins + z the same
+    weights times I (intensity I in [0, 1]).  G1 (level 1) splats every
+    pixel of a 2x2 block and sums them: the histogram step, a reduction;
+    G2 .. G_levels sum 2x2 blocks of the level below; B blurs the grid with
+    a 3x3 binomial in x and y."""
+    nb = bins
+    is_v = emin(emax(CHAN - float(nb - 1), 0.0), 1.0)  # 1 on the value channels
+    z = CHAN - float(nb) * is_v                           # the channel's bin
+
+    def splat(t):
+        w = emax(1.0 - eabs(t * float(nb - 1) - z), 0.0)
+        return w * (1.0 + is_v * (t - 1.0))
+
+    taps = [ref(inp, i, j, mode="down2") for j in (0, 1) for i in (0, 1)]
+    g = b.stage("G1", splat(taps[0]) + splat(taps[1]) + splat(taps[2]) + splat(taps[3]), 2 * nb)
+    for k in range(2, levels + 1):
+        box = ref(g, 0, 0, mode="down2") + ref(g, 1, 0, mode="down2") + ref(g, 0, 1, mode="down2") \
+            + ref(g, 1, 1, mode="down2")
+        g = b.stage("G%d" % k, box, 2 * nb)
+    return b.stage("B", linear(g, [[1, 2, 1], [2, 4, 2], [1, 2, 1]], 1.0 / 16), 2 * nb)
+
+
+def bilateral_grid(bins: int = 8, levels: int = 3) -> dict:
+    """Bilateral-grid construction: the histogram (splat and 2x2 sums down
+    `levels` levels) and the blur that follows it.  Output: the blurred grid,
+    2 bins channels at level `levels`."""
+    b = Builder("bilateral_grid", [1])
+    b.output(_grid_stages(b, input_id(0), bins, levels))
+    return b.build()
+
+
+def bilateral_filter(bins: int = 8, levels: int = 3) -> dict:
+    """Bilateral filter through the grid: construction as bilateral_grid(),
+    then the blurred grid is brought back to level 1 by nearest up-sampling
+    (U) and sliced at every pixel, linearly in intensity and at the pixel's
+    own cell in x and y: out = sum_z w_z(I) V_z / (sum_z w_z(I) W_z + 1e-6)
+    with the tent weights w_z of the construction."""
+    nb = bins
+    b = Builder("bilateral_filter", [1])
+    inp = input_id(0)
+    g = _grid_stages(b, inp, bins, levels)
+    for k in range(levels - 1, 0, -1):
+        g = b.stage("U%d" % k, ref(g, 0, 0, mode="up2"), 2 * nb)
+    t = ref(inp)
+    num, den = None, None
+    for zb in range(nb):
+        w = emax(1.0 - eabs(t * float(nb - 1) - float(zb)), 0.0)
+        v = w * ref(g, 0, 0, chan=nb + zb, mode="up2")
+        d = w * ref(g, 0, 0, chan=zb, mode="up2")
+        num = v if num is None else num + v
+        den = d if den is None else den + d
+    b.output(b.stage("out", num / (den + 1e-6)))
+    return b.build()
+
+
+def bilateral_schedule(bins: int = 8, levels: int = 3) -> tuple:
+    """(groups, params) of bilateral_filter(bins, levels): one group per run
+    of stages at one level; the 2x2 sums below the first level run as
+    per-stage streaming down-sampling kernels, the other groups fused."""
+    spec = bilateral_filter(bins, levels)
+    names = [st["name"] for st in spec["stages"]]
+    groups, params, cur = [], [], -1
+    prev_level = None
+    for n in names:
+        level = {"G1": 1, "B": levels, "out": 0}.get(n)
+        if level is None:
+            level = int(n[1:])
+        if level != prev_level:
+            cur += 1
+            plain = n.startswith("G") and n != "G1" and n != "G%d" % levels
+            params.append(dict(flags=4, tile_h=8) if plain else dict(tile_h=8))
+        groups.append(cur)
+        prev_level = level
+    return groups, params
+
+
 def by_name(name: str) -> dict:
     table = {"sharpen": sharpen, "harris": harris, "harris_raw": lambda: harris(False),
-             "blend": blend, "blur": blur3, "blur_rgb": lambda: blur3(3)}
+             "blend": blend, "blur": blur3, "blur_rgb": lambda: blur3(3),
+             "bilateral_grid": bilateral_grid, "bilateral": bilateral_filter}
     return table[name]()

@@ -1,0 +1,80 @@
+"""Per-plane programs (the channel-index op) and the bilateral grid
+(histogram as a splat-and-sum reduction, then 2x2 sums and a blur of the
+grid, then slicing) run by the generated kernels in the block emulator,
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_1909_07190_gb300 import pipelines as P
+from paper_1909_07190_gb300 import wt
+
+from test_codegen_emu import oracle_of, rnd, run_emulated
+
+
+def chan_spec():
+    inp = P.input_id(0)
+    b = P.Builder("chan", [1])
+    s0 = b.stage("planes", P.ref(inp, 1, 0) * (P.CHAN + 1.0) - P.CHAN * P.ref(inp, 0, -1), 4)
+    s1 = b.stage("one", P.ref(s0, 0, 1, chan=2) + P.CHAN + P.ref(s0, -1, 0, chan=0))
+    s2 = b.stage("mix", P.ref(s0) * P.CHAN + P.ref(s1), 4)
+    b.output(s1, s2)
+    return b.build()
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain", "otptb"])
+def test_chan_op(mode):
+    """Plane-dependent programs in one group (a one-plane stage sees plane 0
+    whatever tile channel computes it) and per stage."""
+    spec = chan_spec()
+    img = rnd(80, 150, 37)
+    if mode == "plain":
+        got, _ = run_emulated(spec, [img], exec_mode=wt.WT_EXEC_PLAIN)
+    elif mode == "otptb":
+        got, _ = run_emulated(spec, [img], groups=[0, 1, 1],
+                              params=[dict(tile_h=8, warps_per_block=2, flags=wt.WT_FLAG_OTPTB)] * 2)
+    else:
+        got, _ = run_emulated(spec, [img], groups=[0, 1, 1], params=[dict(tile_h=8)] * 2)
+    for g, r in zip(got, oracle_of(spec, [img])):
+        assert np.abs(g - r).max() <= 1e-5
+
+
+def grid_groups(spec):
+    """One group per level run (consecutive stages of one level)."""
+    from paper_1909_07190_gb300 import pipelines as P2
+    lv = []
+    for st in spec["stages"]:
+        level = 0
+        for op in st["ops"]:
+            if op[0] == "tap":
+                pid = st["inputs"][op[1]]
+                level = (0 if pid < 0 else lv[pid]) + {"same": 0, "down2": 1, "up2": -1}[op[5]]
+                break
+        lv.append(level)
+    g, cur = [0], 0
+    for i in range(1, len(lv)):
+        if lv[i] != lv[i - 1]:
+            cur += 1
+        g.append(cur)
+    return g
+
+
+@pytest.mark.parametrize("w,h,tile_h", [(67, 45, 8), (130, 70, 4), (9, 5, 8)])
+def test_bilateral_grid(w, h, tile_h):
+    spec = P.bilateral_grid(4, 3)
+    img = rnd(81 + w, w, h)
+    g = grid_groups(spec)
+    got, _ = run_emulated(spec, [img], groups=g, params=[dict(tile_h=tile_h)] * (max(g) + 1))
+    ref = oracle_of(spec, [img])[0]
+    assert np.abs(got[0] - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("w,h", [(67, 45), (300, 41)])
+def test_bilateral_filter(w, h):
+    spec = P.bilateral_filter(4, 3)
+    img = rnd(82 + w, w, h)
+    g = grid_groups(spec)
+    got, _ = run_emulated(spec, [img], groups=g, params=[dict(tile_h=8)] * (max(g) + 1))
+    ref = oracle_of(spec, [img])[0]
+    assert np.abs(got[0] - ref).max() <= 1e-5
+    got, _ = run_emulated(spec, [img], exec_mode=wt.WT_EXEC_PLAIN)
+    assert np.abs(got[0] - ref).max() <= 1e-5

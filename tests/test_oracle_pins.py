@@ -272,3 +272,76 @@ def test_malformed_dags_rejected():
     under = [{"channels": 1, "inputs": [-1], "ops": [("tap", 0, 0, 0), ("add",)]}]
     with pytest.raises(ValueError, match="-4"):
         O.shapes(under, [img])
+
+
+# ------------------------------------------- channel index and the grid
+
+
+def test_chan_op_pushes_the_channel():
+    """CHAN is the output point's channel: plane c of a 5-channel stage is
+    c everywhere; a one-channel stage sees 0."""
+    b = P.Builder("chan", [1])
+    s0 = b.stage("planes", P.CHAN + 0.0 * P.ref(P.input_id(0)), 5)
+    s1 = b.stage("one", P.CHAN + P.ref(s0, 0, 0, chan=3))
+    b.output(s0, s1)
+    spec = b.build()
+    img = I.uniform_image(5, 9, 7)
+    out = O.evaluate(spec["stages"], [img.astype(np.float64)], spec["outputs"])
+    for c in range(5):
+        assert np.all(out[0][c] == c)
+    assert np.all(out[1] == 3.0)
+
+
+def block_sums(img, levels):
+    """Sum over 2^levels x 2^levels blocks of the image extended by edge
+    replication (the clamp-to-edge reads of the 2x2 sums), computed level by
+    level with plain numpy."""
+    a = np.asarray(img, np.float64)
+    for _ in range(levels):
+        h, w = a.shape
+        ph, pw = (h + 1) // 2 * 2, (w + 1) // 2 * 2
+        a = np.pad(a, ((0, ph - h), (0, pw - w)), mode="edge")
+        a = a[0::2, 0::2] + a[1::2, 0::2] + a[0::2, 1::2] + a[1::2, 1::2]
+    return a
+
+
+@pytest.mark.parametrize("w,h", [(16, 16), (37, 21), (8, 9)])
+def test_grid_partition_of_unity(w, h):
+    """The tent weights of each pixel sum to 1 over the bins, so before the
+    blur the weight channels of a cell sum to its pixel count and the value
+    channels to its intensity sum (closed forms by block sums)."""
+    bins, levels = 6, 3
+    spec = P.bilateral_grid(bins, levels)
+    img = I.uniform_image(9, w, h)[0].astype(np.float64)
+    st = spec["stages"]
+    g3 = O.evaluate(st, [img[None]], [levels - 1])[0]   # G3: before the blur
+    assert np.allclose(g3[:bins].sum(0), block_sums(np.ones_like(img), levels), rtol=0, atol=1e-12)
+    assert np.allclose(g3[bins:].sum(0), block_sums(img, levels), rtol=0, atol=1e-11)
+
+
+def test_grid_of_a_constant_image():
+    """A constant image c: every cell's bin z holds 64 max(0, 1 - |c (bins-1) -
+    z|) weight and c times that value, before and after the blur."""
+    bins, levels = 8, 3
+    spec = P.bilateral_grid(bins, levels)
+    c = 0.3
+    img = np.full((1, 19, 27), c)
+    g = O.evaluate(spec["stages"], [img], spec["outputs"])[0]
+    for zb in range(bins):
+        wz = 64 * max(0.0, 1 - abs(c * (bins - 1) - zb))
+        assert np.allclose(g[zb], wz, atol=1e-12) and np.allclose(g[bins + zb], c * wz, atol=1e-12)
+
+
+def test_bilateral_filter_constant_and_brute_force():
+    """A constant image comes out unchanged (up to the 1e-6 guard of the
+    division); on a tiny image the DAG evaluator equals the recursive brute
+    force at every pixel."""
+    spec = P.bilateral_filter(4, 2)
+    out = O.evaluate(spec["stages"], [np.full((1, 13, 10), 0.7)], spec["outputs"])[0]
+    assert np.abs(out - 0.7).max() < 1e-6
+    img = I.uniform_image(10, 6, 5).astype(np.float64)
+    full = O.evaluate(spec["stages"], [img], spec["outputs"])[0]
+    sid = spec["outputs"][0]
+    for y in range(5):
+        for x in range(6):
+            assert abs(O.brute(spec["stages"], [img], sid, x, y) - full[0, y, x]) < 1e-12
