@@ -524,8 +524,10 @@ int32_t wt_launches_per_run(const wt_pipeline *p) {
   wt_status rc = guard([&] {
     auto groups = wt::schedule_groups(*p);
     for (size_t gi = 0; gi < groups.size(); gi++) {
-      bool fused = p->sched.exec == WT_EXEC_FUSED && !wt::group_params(*p, (int)gi).plain &&
-                   wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable;
+      const wt::GroupParams gp = wt::group_params(*p, (int)gi);
+      bool fused = p->sched.exec == WT_EXEC_FUSED && !gp.plain &&
+                   ((!gp.otptb && wt::chain_form(*p, groups[gi]).ok) ||
+                    wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable);
       if (fused) {
         n++;
       } else {

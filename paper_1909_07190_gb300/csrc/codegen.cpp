@@ -46,6 +46,7 @@ std::string CodegenKey::str() const {
   for (int x : dst_dtypes) s << x;
   if (otptb) s << "|B" << tbx << "x" << tby;
   if (down) s << "|D" << tby;
+  if (chain) s << "|R";
   return s.str();
 }
 

@@ -115,6 +115,18 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     const auto &G = groups[gi];
     GroupParams gp = group_params(p, (int)gi);
     bool fused = p.sched.exec == WT_EXEC_FUSED && !gp.plain;
+    if (fused && !gp.otptb && chain_form(p, G).ok) {
+      // a reduction chain across levels: one launch, only its last stage
+      // written
+      materialize(G.back(), !p.consumers[G.back()].empty());
+      Launch L;
+      L.fused = false;
+      L.stages = G;
+      L.params = gp;
+      L.key.chain = true;
+      plan.launches.push_back(L);
+      continue;
+    }
     GroupGeom geom;
     if (fused) {
       geom = analyze_group(p, G, 4, gp.frac_reg, 4);
@@ -221,6 +233,26 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       L.grid[1] = L.grid[2] = 1;
       L.smem = key.nw * L.layout.warp_bytes;
       if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "group needs more than 227 KB of shared memory per block");
+    } else if (key.chain) {
+      const ChainForm cf = chain_form(p, L.stages);
+      const int last = L.stages.back();
+      key.plain = true;
+      key.vec = 1;
+      key.nw = 4;
+      L.src.push_back(cf.producer);
+      L.src_chan.push_back(0);
+      key.src_dtypes.push_back(loc_of(cf.producer).dtype);
+      L.dst.push_back(last);
+      key.dst_dtypes.push_back(plan.loc[last].dtype);
+      level_dims(plan.W, plan.H, p.stages[last].level, &L.W, &L.H);
+      L.block = 128;
+      L.grid[0] = (unsigned)((L.W + 127) / 128);
+      L.grid[1] = (unsigned)L.H;
+      L.grid[2] = 1;
+      if (L.H > 65535) fail(WT_EUNSUPPORTED, "image too tall for the reduction-chain kernel");
+      L.smem = 0;
+      L.kname = kernel_name(p, key, false);
+      continue;
     } else {
       int s = L.stages[0];
       key.plain = true;
@@ -282,15 +314,19 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
   static const char kDownVersion[] = "wt-down-4";  // the down-sampling kernel's own changes
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
+  static const char kChainVersion[] = "wt-chain-1";  // the reduction-chain kernel's own changes
+  if (key.chain) h = fnv1a(kChainVersion, sizeof kChainVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;
   if (key.down) return std::string("wt_down_") + hx;
+  if (key.chain) return std::string("wt_chain_") + hx;
   return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }
 
 std::string launch_source(const Pipeline &p, const Launch &L) {
   if (L.key.otptb) return emit_otptb(p, L.geom, L.key, L.kname);
   if (L.key.down) return emit_down(p, L.stages[0], L.key, L.kname);
+  if (L.key.chain) return emit_chain(p, L.stages, L.key, L.kname);
   if (L.fused) return emit_fused(p, L.geom, L.key, L.kname);
   return emit_plain(p, L.stages[0], L.key, L.kname);
 }

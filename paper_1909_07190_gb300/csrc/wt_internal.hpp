@@ -1,6 +1,7 @@
 // Internal types of the warp-tiled pipeline library (host side).
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -260,6 +261,8 @@ struct CodegenKey {
   // per-stage kernel of a separable down-sampling stage, streamed at two
   // rates (scaled.cpp): vec outputs per lane, tby output rows per warp
   bool down = false;
+  // reduction chain across levels (chain.cpp)
+  bool chain = false;
   std::string str() const;
 };
 
@@ -313,6 +316,19 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key,
                       const std::string &kname);
 // Dynamic shared memory of the down-sampling kernel (its cp.async ring).
 int down_smem(const Pipeline &p, int sid, const CodegenKey &key);
+// chain.cpp: a group S1..Sk, each stage one level coarser: S1 a program of
+// one one-plane producer's DOWN2 taps inside its 2x2 block, every later
+// stage a weighted 2x2 sum of the one before (w[m][i + 2 j] for S(m+2));
+// only Sk leaves the group.
+struct ChainForm {
+  bool ok = false;
+  int producer = 0;
+  int C = 1;
+  std::vector<std::array<double, 4>> w;
+};
+ChainForm chain_form(const Pipeline &p, const std::vector<int> &stages);
+std::string emit_chain(const Pipeline &p, const std::vector<int> &stages, const CodegenKey &key,
+                       const std::string &kname);
 // Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
 struct PlainSrc {
   int slot, chan;

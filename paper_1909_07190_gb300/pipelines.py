@@ -306,23 +306,12 @@ def bilateral_filter(bins: int = 8, levels: int = 3) -> dict:
 
 
 def bilateral_schedule(bins: int = 8, levels: int = 3) -> tuple:
-    """(groups, params) of bilateral_filter(bins, levels): one group per run
-    of stages at one level; the 2x2 sums below the first level run as
-    per-stage streaming down-sampling kernels, the other groups fused."""
-    spec = bilateral_filter(bins, levels)
-    names = [st["name"] for st in spec["stages"]]
-    groups, params, cur = [], [], -1
-    prev_level = None
-    for n in names:
-        level = {"G1": 1, "B": levels, "out": 0}.get(n)
-        if level is None:
-            level = int(n[1:])
-        if level != prev_level:
-            cur += 1
-            plain = n.startswith("G") and n != "G1" and n != "G%d" % levels
-            params.append(dict(flags=4, tile_h=8) if plain else dict(tile_h=8))
-        groups.append(cur)
-        prev_level = level
+    """(groups, params) of bilateral_filter(bins, levels): the histogram's
+    splat and 2x2 sums as one reduction chain across the levels, the grid's
+    blur, the nearest up-sampling stages, and the slice, each one group."""
+    n_stages = levels + 1 + (levels - 1) + 1
+    groups = [0] * levels + list(range(1, n_stages - levels + 1))
+    params = [dict(tile_h=8)] * (max(groups) + 1)
     return groups, params
 
 

@@ -53,7 +53,7 @@ def test_bilateral_filter_default_schedule(w, h):
     img = rnd(92 + w, w, h)
     groups, params = P.bilateral_schedule()
     got, p = run_pipe(spec, [img], groups=groups, params=params)
-    assert p.launches_per_run() == 6
+    assert p.launches_per_run() == 5
     assert close(got[0], oracle_out(spec, [img])[0])
     plain = run_pipe(spec, [img], exec_mode=wtmod().WT_EXEC_PLAIN)[0][0]
     assert close(plain, got[0])

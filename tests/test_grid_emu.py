@@ -78,3 +78,41 @@ def test_bilateral_filter(w, h):
     assert np.abs(got[0] - ref).max() <= 1e-5
     got, _ = run_emulated(spec, [img], exec_mode=wt.WT_EXEC_PLAIN)
     assert np.abs(got[0] - ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("w,h,bins,levels", [(67, 45, 4, 3), (130, 70, 3, 2), (9, 5, 4, 3), (270, 33, 2, 4),
+                                             (33, 1, 4, 3)])
+def test_reduction_chain(w, h, bins, levels):
+    """The grid's splat and 2x2 sums as one cross-level launch (the chain
+    kernel), then the blur, against the oracle; odd sizes make every level
+    clamp its own edge."""
+    spec = P.bilateral_grid(bins, levels)
+    img = rnd(83 + w + levels, w, h)
+    groups = [0] * levels + [1]
+    got, d = run_emulated(spec, [img], groups=groups, params=[dict(tile_h=8)] * 2)
+    assert d["name"].startswith("wt_chain_")
+    assert d["n_launches"] == 2
+    ref = oracle_of(spec, [img])[0]
+    assert np.abs(got[0] - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+def test_reduction_chain_weighted_and_filter():
+    """Weighted 2x2 sums (a chain of binomial-like reductions) and the full
+    bilateral filter with its chain."""
+    inp = P.input_id(0)
+    b = P.Builder("chain", [1])
+    s0 = b.stage("sq", P.ref(inp, 0, 0, mode="down2") * P.ref(inp, 1, 1, mode="down2") + P.CHAN, 3)
+    s1 = b.stage("w1", 0.5 * P.ref(s0, 0, 0, mode="down2") + 0.25 * P.ref(s0, 1, 0, mode="down2")
+                 - P.ref(s0, 1, 1, mode="down2"), 3)
+    s2 = b.stage("w2", P.ref(s1, 0, 1, mode="down2") * 2.0 + P.ref(s1, 1, 0, mode="down2") / 4.0, 3)
+    b.output(s2)
+    spec = b.build()
+    img = rnd(84, 91, 37)
+    got, d = run_emulated(spec, [img], groups=[0, 0, 0], params=[dict()])
+    assert d["name"].startswith("wt_chain_")
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
+    spec = P.bilateral_filter(4, 3)
+    groups, params = P.bilateral_schedule(4, 3)
+    img = rnd(85, 150, 77)
+    got, d = run_emulated(spec, [img], groups=groups, params=params)
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
