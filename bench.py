@@ -52,6 +52,8 @@ WORKLOADS = {
     "bilateral": ("bilateral", 4096, 4096, "f32", I.SEED_BASE + 6),
 }
 BATCH_IMAGES = 512
+# pyramid levels a tap mode moves (down: the producer is finer)
+LEVEL_DELTA = {"same": 0, "down2": 1, "up2": -1, "down4": 2, "up4": -2, "down8": 3, "up8": -3}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -83,7 +85,7 @@ def ops_per_pixel(spec):
             src = st["inputs"][op[1]]
             base = level.get(src, 0) if src >= 0 else 0
             mode = op[5] if len(op) > 5 else "same"
-            lv = base + (1 if mode == "down2" else -1 if mode == "up2" else 0)
+            lv = base + LEVEL_DELTA[mode]
             break
         level[i] = lv or 0
         n = sum(1 for op in st["ops"] if op[0] in arith)
@@ -281,7 +283,7 @@ def stage_levels(spec):
                 continue
             pid = st["inputs"][op[1]]
             pl = 0 if pid < 0 else lv[pid]
-            level = pl + {"same": 0, "down2": 1, "up2": -1}[op[5]]
+            level = pl + LEVEL_DELTA[op[5]]
             break
         lv.append(0 if level is None else level)
     return lv

@@ -62,8 +62,12 @@ typedef enum {
 typedef enum {
   WT_TAP_SAME = 0,  /* P(x + dx, y + dy)                        */
   WT_TAP_DOWN2 = 1, /* P(2x + dx, 2y + dy)   producer one level finer   */
-  WT_TAP_UP2 = 2    /* P(x/2 + dx, y/2 + dy) producer one level coarser */
-} wt_tapmode;
+  WT_TAP_UP2 = 2,   /* P(x/2 + dx, y/2 + dy) producer one level coarser */
+  WT_TAP_DOWN4 = 3, /* P(4x + dx, 4y + dy)   two levels finer            */
+  WT_TAP_UP4 = 4,   /* P(x/4 + dx, y/4 + dy) two levels coarser          */
+  WT_TAP_DOWN8 = 5, /* P(8x + dx, 8y + dy)   three levels finer          */
+  WT_TAP_UP8 = 6    /* P(x/8 + dx, y/8 + dy) three levels coarser        */
+} wt_tapmode;       /* (divisions round down; odd modes scale down, even up) */
 
 typedef struct {
   int32_t op;   /* wt_opcode                                                 */

@@ -31,8 +31,12 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 
 /* Source coordinate of a tap along one axis (Sec. 2.3; Sec. 5 scaling). */
 static int tap_coord(int mode, int p, int d) {
-  if (mode == OR_DOWN2) return 2 * p + d;
-  if (mode == OR_UP2) return (p >> 1) + d; /* p >= 0: floor(p/2) */
+  /* modes 2s-1: down by 2^s (P(2^s p + d)); 2s: up by 2^s (P(floor(p / 2^s) + d)) */
+  if (mode > 0) {
+    const int s = (mode + 1) / 2;
+    if (mode & 1) return (p << s) + d;
+    return (p >> s) + d; /* p >= 0: floor(p / 2^s) */
+  }
   return p + d;
 }
 
@@ -65,8 +69,8 @@ int or_dag_shapes(const or_stage *st, int n_st, const or_input *in, int n_in,
           if (o->chan < 0 && pc != 1 && pc != S->channels) return -4;
           int implied;
           if (o->mode == OR_SAME) implied = pl;
-          else if (o->mode == OR_DOWN2) implied = pl + 1;
-          else if (o->mode == OR_UP2) implied = pl - 1;
+          else if (o->mode >= OR_DOWN2 && o->mode <= OR_UP8)
+            implied = (o->mode & 1) ? pl + (o->mode + 1) / 2 : pl - (o->mode + 1) / 2;
           else return -4;
           if (lv == INT_MIN) lv = implied;
           else if (lv != implied) return -2;

@@ -18,7 +18,8 @@
  *   - Boundary: every producer read is clamped to the producer's domain
  *     (clamp-to-edge at every stage, not only at the input).
  *   - Sampling: a tap in DOWN2 mode reads P(2x+dx, 2y+dy); in UP2 mode it
- *     reads P(floor(x/2)+dx, floor(y/2)+dy); XPAR/YPAR push x&1, y&1 of the
+ *     reads P(floor(x/2)+dx, floor(y/2)+dy); DOWN4/UP4 and DOWN8/UP8 scale
+ *     by 4 and 8 (two and three levels); XPAR/YPAR push x&1, y&1 of the
  *     consumer point (Sec. 5 "alignment and scaling" makes such dependences
  *     constant).  Domain of level l: W_l = ceil(W_{l-1}/2).
  *   - Channels are planar; a tap with chan < 0 reads the consumer's channel
@@ -44,7 +45,8 @@ enum or_opcode {
   OR_YPAR = 13, /* push (y & 1) of the consumer point           */
   OR_CHAN = 14  /* push the consumer point's channel index      */
 };
-enum or_tapmode { OR_SAME = 0, OR_DOWN2 = 1, OR_UP2 = 2 };
+/* down by 2^s: mode 2s-1 (producer s levels finer); up by 2^s: mode 2s */
+enum or_tapmode { OR_SAME = 0, OR_DOWN2 = 1, OR_UP2 = 2, OR_DOWN4 = 3, OR_UP4 = 4, OR_DOWN8 = 5, OR_UP8 = 6 };
 
 typedef struct {
   int32_t op, slot, dx, dy, chan, mode;

@@ -13,7 +13,8 @@ Pipeline format (plain data, shared with the CUDA path only as an input):
     op tuples: ("const", v) | ("tap", slot, dx, dy[, chan[, mode]]) |
                ("add",) ("sub",) ("mul",) ("div",) ("min",) ("max",)
                ("neg",) ("abs",) ("sqrt",) ("xpar",) ("ypar",) ("chan",)
-    mode: "same" | "down2" | "up2";  chan: -1 = consumer's channel.
+    mode: "same" | "down2" | "up2" | "down4" | "up4" | "down8" | "up8";
+          chan: -1 = consumer's channel.
     inputs: stage index >= 0, or -(j+1) for pipeline input j.
 """
 from __future__ import annotations
@@ -32,7 +33,7 @@ _lib = None
 
 _OPS = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7,
         "max": 8, "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14}
-_MODES = {"same": 0, "down2": 1, "up2": 2}
+_MODES = {"same": 0, "down2": 1, "up2": 2, "down4": 3, "up4": 4, "down8": 5, "up8": 6}
 
 
 class _Op(ctypes.Structure):

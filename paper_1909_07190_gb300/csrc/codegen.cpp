@@ -295,9 +295,26 @@ std::string gather_tap(Ctx &c, int gi, int e, int dx, int dy) {
 // constant offset from X0 / 2 (up-sampling: floor((X0 + e) / 2) + dx) or
 // from 2 X0 (down-sampling: 2 (X0 + e) + dx); rows likewise from r.
 // Column of a gather tap relative to the lane's base column: element e of
-// the lane, tap offset dx (DOWN2: base 2 (xs + lane V); UP2: base
-// (xs >> 1) + lane V / 2, xs a multiple of V, so both bases are even).
-int gather_off(int mode, int e, int dx) { return mode == WT_TAP_DOWN2 ? 2 * e + dx : (e >> 1) + dx; }
+// the lane, tap offset dx.  Down by 2^s: base (xs + lane V) 2^s, offset
+// e 2^s + dx.  Up by 2^s: base (xs + lane V) >> s, offset (e >> s) + dx,
+// exact because xs + lane V is a multiple of V (a power of two): either
+// 2^s divides it, or the lane's V columns lie in one 2^s-column cell.
+int gather_off(int mode, int e, int dx) {
+  const int s = tap_shift(mode);
+  return tap_is_down(mode) ? (e << s) + dx : (e >> s) + dx;
+}
+// The lane's base column and a row's producer row, as expressions.
+std::string gather_base(int mode, int V) {
+  const int s = tap_shift(mode);
+  const std::string b = "(xs + lane * " + std::to_string(V) + ")";
+  return tap_is_down(mode) ? "(" + b + " * " + std::to_string(1 << s) + ")" : "(" + b + " >> " + std::to_string(s) + ")";
+}
+std::string gather_row(int mode, const std::string &r) {
+  const int s = tap_shift(mode);
+  return tap_is_down(mode) ? "(" + r + " * " + std::to_string(1 << s) + ")" : "(" + r + " >> " + std::to_string(s) + ")";
+}
+// Aligned pair loads need an even base column: every down mode, and up by 2.
+bool gather_pairs(int mode) { return tap_is_down(mode) || tap_shift(mode) == 1; }
 
 // Interior tiles: every gather row and column the guard-free body touches
 // lies inside the gather source (the tile's border test includes these
@@ -316,14 +333,10 @@ void emit_gather_prologue_fast(Ctx &c, int ni) {
   std::set<int> modes;
   int id = 0;
   for (const Tap &t : taps) modes.insert(c.g.nodes[t.gi].gather_mode);
-  for (int m : modes)
-    o << "const int gcb" << m << " = " << (m == WT_TAP_DOWN2 ? "2 * (xs + lane * " + std::to_string(c.V) + ")"
-                                                          : "(xs >> 1) + lane * " + std::to_string(c.V / 2))
-      << ";\n";
+  for (int m : modes) o << "const int gcb" << m << " = " << gather_base(m, c.V) << ";\n";
   for (const Tap &t : taps) {
     const Node &pn = c.g.nodes[t.gi];
     const int m = pn.gather_mode;
-    const bool down = m == WT_TAP_DOWN2;
     const std::string S = "ia.src[" + std::to_string(pn.src_index) + "]";
     const int dt = c.key.src_dtypes.at(pn.src_index);
     const int esz = elem_bytes(dt);
@@ -332,12 +345,23 @@ void emit_gather_prologue_fast(Ctx &c, int ni) {
       std::string v = "gr" + std::to_string(id++);
       const std::string chan = pn.src_chan >= 0 ? std::to_string(pn.src_chan) : "ch";
       o << "const unsigned char *" << v << " = (const unsigned char *)" << S << ".ptr + (wt_i64)" << chan << " * "
-        << S << ".plane + (wt_i64)(" << (down ? "2 * r" : "(r >> 1)") << " + (" << t.dy << ")) * " << S
+        << S << ".plane + (wt_i64)(" << gather_row(m, "r") << " + (" << t.dy << ")) * " << S
         << ".pitch + (wt_i64)gcb" << m << " * " << esz << ";\n";
       rows[rk] = v;
     }
     for (int e = 0; e < c.V; e++) {
       const int off = gather_off(m, e, t.dx);
+      if (!gather_pairs(m)) {
+        // up by 4 or 8: one value per (row, offset), scalar loads
+        auto vk = std::make_tuple(t.gi, t.dy, off);
+        if (!vals.count(vk)) {
+          std::string v = "gv" + std::to_string(id++);
+          o << "const float " << v << " = wt_ld1_" << tname(dt) << "(" << rows[rk] << " + (" << off * esz << "));\n";
+          vals[vk] = v;
+        }
+        c.gvar[std::make_tuple(t.gi, e, t.dx, t.dy)] = vals[vk];
+        continue;
+      }
       const int p0 = off - (((off % 2) + 2) % 2);  // the aligned pair holding it
       auto vk = std::make_tuple(t.gi, t.dy, p0);
       if (!vals.count(vk)) {
@@ -497,7 +521,7 @@ void emit_gather_prologue(Ctx &c, int ni) {
   int id = 0;
   for (const Tap &t : taps) {
     const Node &pn = c.g.nodes[t.gi];
-    const bool down = pn.gather_mode == WT_TAP_DOWN2;
+    const int m = pn.gather_mode;
     const std::string S = "ia.src[" + std::to_string(pn.src_index) + "]";
     const int esz = elem_bytes(c.key.src_dtypes.at(pn.src_index));
     auto rk = std::make_pair(t.gi, t.dy);
@@ -505,18 +529,17 @@ void emit_gather_prologue(Ctx &c, int ni) {
       std::string v = "gr" + std::to_string(id++);
       const std::string chan = pn.src_chan >= 0 ? std::to_string(pn.src_chan) : "ch";
       o << "const unsigned char *" << v << " = (const unsigned char *)" << S << ".ptr + (wt_i64)" << chan << " * "
-        << S << ".plane + (wt_i64)wt_clampi(" << (down ? "2 * r" : "(r >> 1)") << " + (" << t.dy << "), 0, " << S
+        << S << ".plane + (wt_i64)wt_clampi(" << gather_row(m, "r") << " + (" << t.dy << "), 0, " << S
         << ".H - 1) * " << S << ".pitch;\n";
       rows[rk] = v;
     }
     for (int e = 0; e < c.V; e++) {
-      const int off = down ? 2 * e + t.dx : (e >> 1) + t.dx;
+      const int off = gather_off(m, e, t.dx);
       auto ck = std::make_pair(t.gi, off);
       if (!cols.count(ck)) {
         std::string v = "gc" + std::to_string(id++);
-        o << "const int " << v << " = wt_clampi(" << (down ? "2 * (xs + lane * " + std::to_string(c.V) + ")"
-                                                           : "((xs + lane * " + std::to_string(c.V) + ") >> 1)")
-          << " + (" << off << "), 0, " << S << ".W - 1) * " << esz << ";\n";
+        o << "const int " << v << " = wt_clampi(" << gather_base(m, c.V) << " + (" << off << "), 0, " << S
+          << ".W - 1) * " << esz << ";\n";
         cols[ck] = v;
       }
       auto vk = std::make_tuple(t.gi, t.dy, off);
@@ -1065,17 +1088,22 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
           dmin = std::min(dmin, cn.delay);
         }
     if (omin > omax) continue;
-    const int plo = omin - (((omin % 2) + 2) % 2), phi = omax + (((omax % 2) + 2) % 2 == 0 ? 1 : 0);
-    const bool down = gn.gather_mode == WT_TAP_DOWN2;
+    const int gm = gn.gather_mode;
+    // columns read: whole aligned pairs where the loads are pairs
+    const bool pr = gather_pairs(gm);
+    const int plo = pr ? omin - (((omin % 2) + 2) % 2) : omin;
+    const int phi = pr ? omax + (((omax % 2) + 2) % 2 == 0 ? 1 : 0) : omax;
     const std::string S = "ia.src[" + std::to_string(gn.src_index) + "]";
-    const std::string cb0 = down ? "2 * xs" : "(xs >> 1)";
-    const std::string cb31 = down ? "2 * (xs + " + std::to_string(31 * V) + ")"
-                                  : "((xs >> 1) + " + std::to_string(31 * V / 2) + ")";
+    const int gs = tap_shift(gm);
+    const bool down = tap_is_down(gm);
+    const std::string cb0 = down ? "(xs * " + std::to_string(1 << gs) + ")" : "(xs >> " + std::to_string(gs) + ")";
+    const std::string cb31 = down ? "((xs + " + std::to_string(31 * V) + ") * " + std::to_string(1 << gs) + ")"
+                                  : "((xs + " + std::to_string(31 * V) + ") >> " + std::to_string(gs) + ")";
     const std::string rlo = "(y_top - " + std::to_string(dmax) + ")";
     const std::string rhi = "(y_top + nsteps + " + std::to_string(c.U - 1 - dmin) + ")";
     o << "border = border || " << cb0 << " + (" << plo << ") < 0 || " << cb31 << " + (" << phi << ") > " << S
-      << ".W - 1 || " << (down ? "2 * " + rlo : "(" + rlo + " >> 1)") << " + (" << dymin << ") < 0 || "
-      << (down ? "2 * " + rhi : "(" + rhi + " >> 1)") << " + (" << dymax << ") > " << S << ".H - 1;\n";
+      << ".W - 1 || " << gather_row(gm, rlo) << " + (" << dymin << ") < 0 || " << gather_row(gm, rhi) << " + ("
+      << dymax << ") > " << S << ".H - 1;\n";
   }
   for (int s = 0; s < n_src; s++) {
     const Node *sn = nullptr;
@@ -1205,8 +1233,10 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
   }
   auto col_index = [&](int mode, int e, int dx) {
     // offset of the producer column, relative to the row base, for element e
-    if (mode == WT_TAP_DOWN2) return 2 * e + dx;
-    if (mode == WT_TAP_UP2) return (e >> 1) + dx;
+    // (x0 is a multiple of 8: (x0 + e) >> s = (x0 >> s) + (e >> s) for s <= 3)
+    const int s = tap_shift(mode);
+    if (tap_is_down(mode)) return (e << s) + dx;
+    if (tap_is_up(mode)) return (e >> s) + dx;
     return e + dx;
   };
   for (size_t ri = 0; ri < rows.size(); ri++) {
@@ -1216,8 +1246,14 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     int lo = col_index(r.mode, 0, r.dxmin), hi = col_index(r.mode, PV - 1, r.dxmax);
     std::string sd = "a.src[" + std::to_string(s) + "]";
     std::string zc = srcs[s].chan >= 0 ? std::to_string(srcs[s].chan) : "ch";
-    std::string base = (r.mode == WT_TAP_DOWN2) ? "2 * x0" : (r.mode == WT_TAP_UP2 ? "(x0 >> 1)" : "x0");
-    std::string ybase = (r.mode == WT_TAP_DOWN2) ? "2 * y" : (r.mode == WT_TAP_UP2 ? "(y >> 1)" : "y");
+    const int sh = tap_shift(r.mode);
+    std::string base = tap_is_down(r.mode) ? "(x0 * " + std::to_string(1 << sh) + ")"
+                       : (tap_is_up(r.mode) ? "(x0 >> " + std::to_string(sh) + ")" : "x0");
+    std::string ybase = tap_is_down(r.mode) ? "(y * " + std::to_string(1 << sh) + ")"
+                        : (tap_is_up(r.mode) ? "(y >> " + std::to_string(sh) + ")" : "y");
+    // aligned 4-vectors need a base that is a multiple of 4: every mode but
+    // up by 4 or 8 (x0 >> 2 or x0 >> 3 of a multiple of 8)
+    const bool vec_ok = !(tap_is_up(r.mode) && sh >= 2);
     o << "const unsigned char *rp" << ri << " = (const unsigned char *)" << sd << ".ptr + (wt_i64)" << zc
       << " * " << sd << ".plane + (wt_i64)wt_clampi(" << ybase << " + (" << r.dy << "), 0, " << sd
       << ".H - 1) * " << sd << ".pitch;\n";
@@ -1231,7 +1267,8 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     o << "float";
     for (int j = lo; j <= hi; j++) o << (j == lo ? " " : ", ") << "L" << ri << "_" << (j - lo);
     o << ";\n";
-    o << "if (" << base << " + (" << lo_a << ") >= 0 && " << base << " + (" << hi_a << ") <= " << sd << ".W - 1) {\n";
+    o << "if (" << (vec_ok ? "true" : "false") << " && " << base << " + (" << lo_a << ") >= 0 && " << base << " + ("
+      << hi_a << ") <= " << sd << ".W - 1) {\n";
     for (int k = 0; k < nv; k++) {
       o << "{ float q0, q1, q2, q3;\nwt_ld4_" << tname(dt) << "(rp" << ri << " + (wt_i64)(" << base << " + (" << lo_a + 4 * k
         << ")) * " << elem_bytes(dt) << ", q0, q1, q2, q3);\n";

@@ -78,7 +78,7 @@ void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch
         case WT_OP_TAP: {
           if (o.slot < 0 || o.slot >= (int)T.inputs.size())
             fail(WT_EINVAL, "stage " + std::to_string(s) + ": tap slot out of range");
-          if (o.mode < WT_TAP_SAME || o.mode > WT_TAP_UP2)
+          if (o.mode < WT_TAP_SAME || o.mode > WT_TAP_UP8)
             fail(WT_EINVAL, "stage " + std::to_string(s) + ": bad tap mode");
           if (o.dx < -64 || o.dx > 64 || o.dy < -64 || o.dy > 64)
             fail(WT_EINVAL, "stage " + std::to_string(s) + ": tap offset beyond +-64");
@@ -89,7 +89,7 @@ void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch
           if (o.chan < 0 && pc != 1 && pc != S.channels)
             fail(WT_EINVAL, "stage " + std::to_string(s) +
                                 ": same-channel tap of a producer with a different channel count");
-          int implied = o.mode == WT_TAP_SAME ? pl : (o.mode == WT_TAP_DOWN2 ? pl + 1 : pl - 1);
+          int implied = pl + tap_level_delta(o.mode);
           if (lv == INT_MIN) lv = implied;
           else if (lv != implied)
             fail(WT_EINVAL, "stage " + std::to_string(s) + ": taps imply different levels");

@@ -13,6 +13,14 @@
 
 namespace wt {
 
+// Tap modes (wt_tapmode): 0 same level; 2s - 1 down by 2^s (producer s
+// levels finer, P(2^s x + dx)); 2s up by 2^s (producer s levels coarser,
+// P(floor(x / 2^s) + dx)).
+inline int tap_shift(int mode) { return (mode + 1) / 2; }
+inline bool tap_is_down(int mode) { return mode > 0 && (mode & 1); }
+inline bool tap_is_up(int mode) { return mode > 0 && !(mode & 1); }
+inline int tap_level_delta(int mode) { return tap_is_down(mode) ? tap_shift(mode) : -tap_shift(mode); }
+
 constexpr int kMaxSrc = 8;     // TMA-staged sources per group kernel
 constexpr int kMaxAllSrc = 24; // all external sources (staged and gathered)
 constexpr int kMaxDst = 8;     // liveouts per group kernel

@@ -4,7 +4,8 @@ A pipeline is the program the library compiles: a DAG of stages, each a
 per-pixel function of producer values at constant offsets (Jangda & Guha,
 PACT'20, Sec. 2.2 Fig. 2 and Sec. 2.3).  Each stage is a postfix program over
 taps ``("tap", slot, dx, dy, chan, mode)``; ``mode`` is "same" (P(x+dx, y+dy)),
-"down2" (P(2x+dx, 2y+dy)) or "up2" (P(floor(x/2)+dx, floor(y/2)+dy)), the
+"down2" (P(2x+dx, 2y+dy)) or "up2" (P(floor(x/2)+dx, floor(y/2)+dy)) (also
+"down4"/"up4" and "down8"/"up8": scale 4 and 8), the
 constant dependence vectors that alignment and scaling produce (Sec. 5).
 
 Format::
@@ -283,22 +284,27 @@ def bilateral_grid(bins: int = 8, levels: int = 3) -> dict:
 
 def bilateral_filter(bins: int = 8, levels: int = 3) -> dict:
     """Bilateral filter through the grid: construction as bilateral_grid(),
-    then the blurred grid is brought back to level 1 by nearest up-sampling
-    (U) and sliced at every pixel, linearly in intensity and at the pixel's
-    own cell in x and y: out = sum_z w_z(I) V_z / (sum_z w_z(I) W_z + 1e-6)
-    with the tent weights w_z of the construction."""
+    then every pixel slices the blurred grid linearly in intensity and at
+    its own cell in x and y, reading the grid directly by an up-sampling tap
+    of scale 2^levels (levels <= 3; coarser grids are first brought to level
+    3 by nearest up-sampling stages U):
+    out = sum_z w_z(I) V_z / (sum_z w_z(I) W_z + 1e-6), w_z the tent
+    weights of the construction."""
     nb = bins
     b = Builder("bilateral_filter", [1])
     inp = input_id(0)
     g = _grid_stages(b, inp, bins, levels)
-    for k in range(levels - 1, 0, -1):
-        g = b.stage("U%d" % k, ref(g, 0, 0, mode="up2"), 2 * nb)
+    lv = levels
+    while lv > 3:
+        lv -= 1
+        g = b.stage("U%d" % lv, ref(g, 0, 0, mode="up2"), 2 * nb)
+    mode = {1: "up2", 2: "up4", 3: "up8"}[lv]
     t = ref(inp)
     num, den = None, None
     for zb in range(nb):
         w = emax(1.0 - eabs(t * float(nb - 1) - float(zb)), 0.0)
-        v = w * ref(g, 0, 0, chan=nb + zb, mode="up2")
-        d = w * ref(g, 0, 0, chan=zb, mode="up2")
+        v = w * ref(g, 0, 0, chan=nb + zb, mode=mode)
+        d = w * ref(g, 0, 0, chan=zb, mode=mode)
         num = v if num is None else num + v
         den = d if den is None else den + d
     b.output(b.stage("out", num / (den + 1e-6)))
@@ -307,9 +313,10 @@ def bilateral_filter(bins: int = 8, levels: int = 3) -> dict:
 
 def bilateral_schedule(bins: int = 8, levels: int = 3) -> tuple:
     """(groups, params) of bilateral_filter(bins, levels): the histogram's
-    splat and 2x2 sums as one reduction chain across the levels, the grid's
-    blur, the nearest up-sampling stages, and the slice, each one group."""
-    n_stages = levels + 1 + (levels - 1) + 1
+    splat and 2x2 sums as one reduction chain across the levels, then the
+    grid's blur, any nearest up-sampling stages and the slice, one group
+    each."""
+    n_stages = len(bilateral_filter(bins, levels)["stages"])
     groups = [0] * levels + list(range(1, n_stages - levels + 1))
     params = [dict(tile_h=8)] * (max(groups) + 1)
     return groups, params

@@ -22,7 +22,7 @@ WT_MODEL_ANALYTIC, WT_MODEL_LEARNED = 0, 1
 WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT, WT_FLAG_PLAIN, WT_FLAG_OTPTB = 1, 2, 4, 8
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
            "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14}
-TAPMODES = {"same": 0, "down2": 1, "up2": 2}
+TAPMODES = {"same": 0, "down2": 1, "up2": 2, "down4": 3, "up4": 4, "down8": 5, "up8": 6}
 DTYPES = {"f32": WT_F32, "f16": WT_F16, "bf16": WT_BF16}
 STATUS = {0: "WT_OK", -1: "WT_EINVAL", -2: "WT_ENOMEM", -3: "WT_ECUDA", -4: "WT_EUNSUPPORTED",
           -5: "WT_ETIMEOUT", -6: "WT_EDEVICE", -7: "WT_ECOMPILE"}

@@ -53,7 +53,7 @@ def test_bilateral_filter_default_schedule(w, h):
     img = rnd(92 + w, w, h)
     groups, params = P.bilateral_schedule()
     got, p = run_pipe(spec, [img], groups=groups, params=params)
-    assert p.launches_per_run() == 5
+    assert p.launches_per_run() == 3
     assert close(got[0], oracle_out(spec, [img])[0])
     plain = run_pipe(spec, [img], exec_mode=wtmod().WT_EXEC_PLAIN)[0][0]
     assert close(plain, got[0])
@@ -72,3 +72,18 @@ def test_bilateral_filter_4096_sampled():
     ys = np.concatenate([rng.integers(0, H, 60), [0, H - 1, H - 1, 0, 4095, 9]])
     ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys)
     assert np.abs(got[0][ys, xs] - ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("k", [4, 8])
+@pytest.mark.parametrize("w,h", [(1000, 517), (67, 45)])
+def test_scaled_modes_gpu(k, w, h):
+    """Taps scaling by 4 and 8: fused groups with gathers of another level
+    two or three levels away, and per-stage kernels."""
+    from test_modes_emu import scaled_spec
+    wt = wtmod()
+    spec = scaled_spec(k)
+    img = rnd(k * 7 + w, w, h)
+    got = run_pipe(spec, [img], groups=[0, 1], params=[dict(tile_h=8)] * 2)[0]
+    plain = run_pipe(spec, [img], exec_mode=wt.WT_EXEC_PLAIN)[0]
+    for g, q, r in zip(got, plain, oracle_out(spec, [img])):
+        assert np.abs(g - r).max() <= 1e-5 and np.abs(q - r).max() <= 1e-5

@@ -345,3 +345,28 @@ def test_bilateral_filter_constant_and_brute_force():
     for y in range(5):
         for x in range(6):
             assert abs(O.brute(spec["stages"], [img], sid, x, y) - full[0, y, x]) < 1e-12
+
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_scaled_taps_on_ramps(s):
+    """Taps scaling by 4 and 8 read P(2^s x + d) (down) and P(floor(x / 2^s) +
+    d) (up), clamped: on a ramp P(x, y) = x + 1000 y the values are those
+    coordinates (closed form); a level-s domain is ceil(W / 2^s) wide."""
+    W, H = 67, 45
+    k = 1 << s
+    ramp = (np.arange(W)[None, :] + 1000.0 * np.arange(H)[:, None])[None]
+    b = P.Builder("ramp", [1])
+    d = b.stage("down", P.ref(P.input_id(0), 1, -1, mode="down%d" % k))
+    u = b.stage("up", P.ref(d, -1, 2, mode="up%d" % k))
+    b.output(d, u)
+    spec = b.build()
+    shp = O.shapes(spec["stages"], [ramp])
+    assert shp[0][1:3] == (-(-W // k), -(-H // k)) and shp[1][1:3] == (W, H)
+    dn, up = O.evaluate(spec["stages"], [ramp], spec["outputs"])
+    h, w = dn.shape[1:]
+    ys, xs = np.mgrid[0:h, 0:w]
+    dref = np.clip(xs * k + 1, 0, W - 1) + 1000.0 * np.clip(ys * k - 1, 0, H - 1)
+    assert np.array_equal(dn[0], dref)
+    ys, xs = np.mgrid[0:H, 0:W]
+    uref = dref[np.clip((ys >> s) + 2, 0, h - 1), np.clip((xs >> s) - 1, 0, w - 1)]
+    assert np.array_equal(up[0], uref)
