@@ -226,6 +226,41 @@ TuneResult tune(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, 
   groupings.push_back(dp);
   std::vector<int> all((size_t)p.stages.size());
   for (size_t i = 0; i < all.size(); i++) all[i] = (int)i;
+  // the DP choice with every longest run of stages that forms a reduction
+  // chain across levels merged into one group (the DP never proposes
+  // groups that span levels); other stages keep their DP groups
+  {
+    const size_t n = p.stages.size();
+    std::vector<int> g(n);
+    int ng = 0, prev_dp = -1;
+    bool any = false;
+    for (size_t s = 0; s < n;) {
+      size_t end = s;
+      for (size_t e = s + 1; e < n && e - s < 6; e++) {
+        std::vector<int> run;
+        for (size_t q = s; q <= e; q++) run.push_back((int)q);
+        if (chain_form(p, run).ok) end = e;
+      }
+      if (end > s) {
+        for (size_t q = s; q <= end; q++) g[q] = ng;
+        ng++;
+        any = true;
+        prev_dp = -1;
+        s = end + 1;
+        continue;
+      }
+      g[s] = (prev_dp >= 0 && dp.group_of_stage[s] == prev_dp) ? ng - 1 : ng++;
+      prev_dp = dp.group_of_stage[s];
+      s++;
+    }
+    if (any) {
+      Schedule ch = dp;
+      ch.n_groups = ng;
+      ch.group_of_stage = g;
+      ch.params.assign(ng, GroupParams());
+      groupings.push_back(ch);
+    }
+  }
   if (dp.n_groups != 1 && all.size() <= 24 && analyze_group(p, all, 4, 1.f, 4).fusable) {
     Schedule one;
     one.exec = WT_EXEC_FUSED;

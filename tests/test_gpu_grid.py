@@ -87,3 +87,23 @@ def test_scaled_modes_gpu(k, w, h):
     plain = run_pipe(spec, [img], exec_mode=wt.WT_EXEC_PLAIN)[0]
     for g, q, r in zip(got, plain, oracle_out(spec, [img])):
         assert np.abs(g - r).max() <= 1e-5 and np.abs(q - r).max() <= 1e-5
+
+
+def test_tune_finds_reduction_chain():
+    """The measured search merges the grid's splat and 2x2 sums into one
+    cross-level group (the DP alone keeps them apart) and keeps parity."""
+    wt = wtmod()
+    spec = P.bilateral_filter()
+    W, H = 2048, 1024
+    img = rnd(93, W, H)
+    p = wt.Pipeline(spec)
+    x = wt.DeviceImage(1, H, W).upload(img)
+    y = wt.DeviceImage(1, H, W)
+    s = torch.cuda.current_stream().cuda_stream
+    ms, n = p.schedule_tune([x.image()], [y.image()], 0, 4, 5, s)
+    assert n > 0 and ms > 0
+    assert p.launches_per_run() <= 4, p.schedule_get()["groups"]
+    p.run([x.image()], [y.image()], s)
+    p.check(s)
+    got = y.download()[0]
+    assert close(got, oracle_out(spec, [img])[0])
