@@ -230,8 +230,11 @@ def blend_schedule(levels: int = 6) -> tuple:
     down_rows = [14, 8] + [4] * max(0, levels - 4)
     params = [dict(flags=plain, tile_h=t) for t in down_rows[:levels - 2]]
     # fused groups from the coarsest level to level 0: short warp tiles
-    # where the level is small (more tiles in flight), 14 rows at levels 1, 0
-    params += [dict(tile_h=8 if lv >= 2 else 14) for lv in range(levels - 1, -1, -1)]
+    # where the level is small (more tiles in flight); at levels 1 and 0, 14
+    # rows, 4-row staging chunks and at most 112 registers, so that 20 warps
+    # fit on an SM (the level-0 group is bound by memory latency)
+    params += [dict(tile_h=8) if lv >= 2 else dict(tile_h=14, chunk_rows=4, max_regs=112)
+               for lv in range(levels - 1, -1, -1)]
     return groups, params
 
 
