@@ -25,17 +25,6 @@ namespace wt {
 
 namespace {
 
-const char *tn(int dtype) { return dtype == WT_F32 ? "f32" : dtype == WT_F16 ? "f16" : "bf16"; }
-
-std::string lit(double v) {
-  if (std::isnan(v)) return "__int_as_float(0x7fc00000)";
-  if (std::isinf(v)) return v > 0 ? "__int_as_float(0x7f800000)" : "__int_as_float(0xff800000)";
-  char b[64];
-  snprintf(b, sizeof b, "%.9g", (double)(float)v);
-  std::string r(b);
-  if (r.find_first_of(".e") == std::string::npos) r += ".0";
-  return "(" + r + "f)";
-}
 
 // Expression of S1 for one channel: the postfix program with the channel
 // index a constant, folded (operations on constants evaluated in FP32 as
@@ -51,7 +40,7 @@ Ex konst(float v) {
   Ex e;
   e.k = true;
   e.v = v;
-  e.s = lit(v);
+  e.s = float_literal(v);
   return e;
 }
 
@@ -294,21 +283,21 @@ std::string emit_chain(const Pipeline &p, const std::vector<int> &stages, const 
       o << "{ const int x1 = " << x << ", y1 = " << y << ";\n";
       if (inner) {
         o << "float t0, t1, t2, t3;\n";
-        o << "wt_ld2_" << tn(sdt) << "(sp + (wt_i64)(2 * y1) * pitch + (wt_i64)(2 * x1) * " << sesz << ", t0, t1);\n";
-        o << "wt_ld2_" << tn(sdt) << "(sp + (wt_i64)(2 * y1 + 1) * pitch + (wt_i64)(2 * x1) * " << sesz
+        o << "wt_ld2_" << dtype_name(sdt) << "(sp + (wt_i64)(2 * y1) * pitch + (wt_i64)(2 * x1) * " << sesz << ", t0, t1);\n";
+        o << "wt_ld2_" << dtype_name(sdt) << "(sp + (wt_i64)(2 * y1 + 1) * pitch + (wt_i64)(2 * x1) * " << sesz
           << ", t2, t3);\n";
       } else {
         o << "const int xa = wt_clampi(2 * x1, 0, Ws - 1), xb = wt_clampi(2 * x1 + 1, 0, Ws - 1);\n";
         o << "const int ya = wt_clampi(2 * y1, 0, Hs - 1), yb = wt_clampi(2 * y1 + 1, 0, Hs - 1);\n";
-        o << "const float t0 = wt_ld1_" << tn(sdt) << "(sp + (wt_i64)ya * pitch + (wt_i64)xa * " << sesz << ");\n";
-        o << "const float t1 = wt_ld1_" << tn(sdt) << "(sp + (wt_i64)ya * pitch + (wt_i64)xb * " << sesz << ");\n";
-        o << "const float t2 = wt_ld1_" << tn(sdt) << "(sp + (wt_i64)yb * pitch + (wt_i64)xa * " << sesz << ");\n";
-        o << "const float t3 = wt_ld1_" << tn(sdt) << "(sp + (wt_i64)yb * pitch + (wt_i64)xb * " << sesz << ");\n";
+        o << "const float t0 = wt_ld1_" << dtype_name(sdt) << "(sp + (wt_i64)ya * pitch + (wt_i64)xa * " << sesz << ");\n";
+        o << "const float t1 = wt_ld1_" << dtype_name(sdt) << "(sp + (wt_i64)ya * pitch + (wt_i64)xb * " << sesz << ");\n";
+        o << "const float t2 = wt_ld1_" << dtype_name(sdt) << "(sp + (wt_i64)yb * pitch + (wt_i64)xa * " << sesz << ");\n";
+        o << "const float t3 = wt_ld1_" << dtype_name(sdt) << "(sp + (wt_i64)yb * pitch + (wt_i64)xb * " << sesz << ");\n";
       }
       o << "(void)t0; (void)t1; (void)t2; (void)t3;\n";
       for (int c = 0; c < C; c++) {
         if (l.w == 1.0) o << "acc" << c << " += " << s1[c] << ";\n";
-        else o << "acc" << c << " += " << lit(l.w) << " * " << s1[c] << ";\n";
+        else o << "acc" << c << " += " << float_literal(l.w) << " * " << s1[c] << ";\n";
       }
       o << "}\n";
     }
@@ -321,7 +310,7 @@ std::string emit_chain(const Pipeline &p, const std::vector<int> &stages, const 
   o << "unsigned char *dp = (unsigned char *)a.dst[0].ptr + (wt_i64)Y * a.dst[0].pitch + (wt_i64)X * " << desz
     << ";\n";
   for (int c = 0; c < C; c++)
-    o << "wt_st1_" << tn(ddt) << "(dp + (wt_i64)" << c << " * a.dst[0].plane, acc" << c << ");\n";
+    o << "wt_st1_" << dtype_name(ddt) << "(dp + (wt_i64)" << c << " * a.dst[0].plane, acc" << c << ");\n";
   o << "}\n";
   return o.str();
 }

@@ -34,6 +34,19 @@
 
 namespace wt {
 
+const char *dtype_name(int dtype) { return dtype == WT_F32 ? "f32" : (dtype == WT_F16 ? "f16" : "bf16"); }
+
+std::string float_literal(float v) {
+  if (std::isnan(v)) return "__int_as_float(0x7fc00000)";
+  if (std::isinf(v)) return v > 0 ? "__int_as_float(0x7f800000)" : "__int_as_float(0xff800000)";
+  char b[64];
+  snprintf(b, sizeof b, "%.9g", (double)v);
+  std::string s(b);
+  if (s.find_first_of(".e") == std::string::npos) s += ".0";
+  return "(" + s + "f)";
+}
+
+
 std::string CodegenKey::str() const {
   std::ostringstream s;
   s << (plain ? "P" : "F") << (persistent ? "b" : "") << (pairs ? "x2" : "") << (even_rows ? "e" : "") << "|v" << vec
@@ -50,19 +63,6 @@ std::string CodegenKey::str() const {
   return s.str();
 }
 
-static const char *tname(int dtype) {
-  return dtype == WT_F32 ? "f32" : (dtype == WT_F16 ? "f16" : "bf16");
-}
-
-static std::string flt(float v) {
-  if (std::isnan(v)) return "__int_as_float(0x7fc00000)";
-  if (std::isinf(v)) return v > 0 ? "__int_as_float(0x7f800000)" : "__int_as_float(0xff800000)";
-  char b[64];
-  snprintf(b, sizeof b, "%.9g", (double)v);
-  std::string s(b);
-  if (s.find_first_of(".e") == std::string::npos) s += ".0";
-  return "(" + s + "f)";
-}
 
 static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
@@ -194,7 +194,7 @@ void emit_extend(Ctx &c, const Node &n, const std::vector<std::string> &v,
 void emit_load_vec(Ctx &c, int dtype, const std::string &addr, const std::vector<std::string> &v,
                    int esz) {
   for (int b = 0; b < c.V; b += 4)
-    c.o << "wt_ld4_" << tname(dtype) << "((const void *)(" << addr << " + " << b * esz << "), "
+    c.o << "wt_ld4_" << dtype_name(dtype) << "((const void *)(" << addr << " + " << b * esz << "), "
         << v[b] << ", " << v[b + 1] << ", " << v[b + 2] << ", " << v[b + 3] << ");\n";
 }
 
@@ -356,7 +356,7 @@ void emit_gather_prologue_fast(Ctx &c, int ni) {
         auto vk = std::make_tuple(t.gi, t.dy, off);
         if (!vals.count(vk)) {
           std::string v = "gv" + std::to_string(id++);
-          o << "const float " << v << " = wt_ld1_" << tname(dt) << "(" << rows[rk] << " + (" << off * esz << "));\n";
+          o << "const float " << v << " = wt_ld1_" << dtype_name(dt) << "(" << rows[rk] << " + (" << off * esz << "));\n";
           vals[vk] = v;
         }
         c.gvar[std::make_tuple(t.gi, e, t.dx, t.dy)] = vals[vk];
@@ -366,7 +366,7 @@ void emit_gather_prologue_fast(Ctx &c, int ni) {
       auto vk = std::make_tuple(t.gi, t.dy, p0);
       if (!vals.count(vk)) {
         std::string v = "gv" + std::to_string(id++);
-        o << "float " << v << "a, " << v << "b;\nwt_ld2_" << tname(dt) << "(" << rows[rk] << " + (" << p0 * esz
+        o << "float " << v << "a, " << v << "b;\nwt_ld2_" << dtype_name(dt) << "(" << rows[rk] << " + (" << p0 * esz
           << "), " << v << "a, " << v << "b);\n";
         vals[vk] = v;
       }
@@ -434,7 +434,7 @@ void emit_gwin_load(Ctx &c, int ni, const GWin &w, int slot, const std::string &
   for (int p0 = plo; p0 <= w.omax; p0 += 2) {
     const std::string a = (p0 >= w.omin && p0 <= w.omax) ? gwin_name(ni, w, slot, p0) : "gwx_";
     const std::string b = (p0 + 1 >= w.omin && p0 + 1 <= w.omax) ? gwin_name(ni, w, slot, p0 + 1) : "gwx_";
-    o << "wt_ld2_" << tname(dt) << "(gwr_ + (" << p0 * esz << "), " << a << ", " << b << ");\n";
+    o << "wt_ld2_" << dtype_name(dt) << "(gwr_ + (" << p0 * esz << "), " << a << ", " << b << ");\n";
   }
   o << "}\n";
 }
@@ -545,7 +545,7 @@ void emit_gather_prologue(Ctx &c, int ni) {
       auto vk = std::make_tuple(t.gi, t.dy, off);
       if (!vals.count(vk)) {
         std::string v = "gv" + std::to_string(id++);
-        o << "const float " << v << " = wt_ld1_" << tname(c.key.src_dtypes.at(pn.src_index)) << "(" << rows[rk]
+        o << "const float " << v << " = wt_ld1_" << dtype_name(c.key.src_dtypes.at(pn.src_index)) << "(" << rows[rk]
           << " + " << cols[ck] << ");\n";
         vals[vk] = v;
       }
@@ -567,7 +567,7 @@ std::string emit_expr(Ctx &c, int ni_c, int e, int u) {
     bool k = false;
     float v = 0.f;
   };
-  auto konst = [](float v) { Val x; x.s = flt(v); x.k = true; x.v = v; return x; };
+  auto konst = [](float v) { Val x; x.s = float_literal(v); x.k = true; x.v = v; return x; };
   auto expr = [](const std::string &s) { Val x; x.s = s; return x; };
   std::vector<Val> st;
   for (const KOp &op : cn.prog) {
@@ -706,7 +706,7 @@ struct PairEmit {
   const std::vector<XN> &A, &B;
   int &tmpid;
   std::string fresh() { return "p" + std::to_string(tmpid++); }
-  std::string leaf(const XN &x) { return x.op == WT_OP_CONST ? flt(x.c) : x.leaf; }
+  std::string leaf(const XN &x) { return x.op == WT_OP_CONST ? float_literal(x.c) : x.leaf; }
   bool is_const(int i) { return A[i].op == WT_OP_CONST && B[i].op == WT_OP_CONST; }
   std::string def(const std::string &rhs) {
     std::string n = fresh();
@@ -735,7 +735,7 @@ struct PairEmit {
         if (m.op == WT_OP_MUL && (is_const(m.a) || is_const(m.b))) {
           int ci = is_const(m.a) ? m.a : m.b, vi = is_const(m.a) ? m.b : m.a;
           std::string v = emit(vi), s0 = emit(x.a);
-          std::string k = def("wt_pk(" + flt(-A[ci].c) + ", " + flt(-B[ci].c) + ")");
+          std::string k = def("wt_pk(" + float_literal(-A[ci].c) + ", " + float_literal(-B[ci].c) + ")");
           return def("wt_fma2(" + v + ", " + k + ", " + s0 + ")");
         }
         std::string l = emit(x.a), r = emit(x.b);
@@ -805,7 +805,7 @@ void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
     o << "unsigned char *op_ = ob" << D << " + (wt_i64)r * ia.dst[" << D << "].pitch;\n";
     o << "if (st_lane) {\n";
     for (int b = 0; b < V; b += 4)
-      o << "wt_st4_" << tname(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", " << v[b + 2]
+      o << "wt_st4_" << dtype_name(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", " << v[b + 2]
         << ", " << v[b + 3] << ");\n";
     o << "} } }\n";
     return;
@@ -820,7 +820,7 @@ void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
     << ".pitch + (wt_i64)x * " << esz << ";\n";
   auto vec_store = [&]() {
     for (int b = 0; b < V; b += 4)
-      o << "wt_st4_" << tname(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", "
+      o << "wt_st4_" << dtype_name(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", "
         << v[b + 2] << ", " << v[b + 3] << ");\n";
   };
   if (!safe) {
@@ -830,7 +830,7 @@ void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
     vec_store();
     o << "} else {\n";
     for (int e = 0; e < V; e++)
-      o << "if (x + " << e << " < W) wt_st1_" << tname(dt) << "(op_ + " << e * esz << ", " << v[e]
+      o << "if (x + " << e << " < W) wt_st1_" << dtype_name(dt) << "(op_ + " << e * esz << ", " << v[e]
         << ");\n";
     o << "}\n";
   }
@@ -1270,7 +1270,7 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     o << "if (" << (vec_ok ? "true" : "false") << " && " << base << " + (" << lo_a << ") >= 0 && " << base << " + ("
       << hi_a << ") <= " << sd << ".W - 1) {\n";
     for (int k = 0; k < nv; k++) {
-      o << "{ float q0, q1, q2, q3;\nwt_ld4_" << tname(dt) << "(rp" << ri << " + (wt_i64)(" << base << " + (" << lo_a + 4 * k
+      o << "{ float q0, q1, q2, q3;\nwt_ld4_" << dtype_name(dt) << "(rp" << ri << " + (wt_i64)(" << base << " + (" << lo_a + 4 * k
         << ")) * " << elem_bytes(dt) << ", q0, q1, q2, q3);\n";
       for (int t = 0; t < 4; t++) {
         int j = lo_a + 4 * k + t;
@@ -1280,7 +1280,7 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     }
     o << "} else {\n";
     for (int j = lo; j <= hi; j++)
-      o << "L" << ri << "_" << (j - lo) << " = wt_ld1_" << tname(dt) << "(rp" << ri
+      o << "L" << ri << "_" << (j - lo) << " = wt_ld1_" << dtype_name(dt) << "(rp" << ri
         << " + (wt_i64)wt_clampi(" << base << " + (" << j << "), 0, " << sd << ".W - 1) * "
         << elem_bytes(dt) << ");\n";
     o << "}\n";
@@ -1289,7 +1289,7 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     std::vector<std::string> st;
     for (const Op &op : S.ops) {
       switch (op.op) {
-        case WT_OP_CONST: st.push_back(flt(op.value)); break;
+        case WT_OP_CONST: st.push_back(float_literal(op.value)); break;
         case WT_OP_XPAR: st.push_back("((float)((x0 + " + std::to_string(e) + ") & 1))"); break;
         case WT_OP_YPAR: st.push_back("((float)(y & 1))"); break;
         case WT_OP_CHAN: st.push_back("((float)ch)"); break;
@@ -1335,11 +1335,11 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     << " * a.dst[0].plane + (wt_i64)y * a.dst[0].pitch + (wt_i64)x0 * " << esz << ";\n";
   o << "if (x0 + " << PV << " <= W) {";
   for (int b = 0; b < PV; b += 4)
-    o << " wt_st4_" << tname(dt) << "(op_ + " << b * esz << ", v" << b << ", v" << b + 1 << ", v" << b + 2 << ", v" << b + 3
+    o << " wt_st4_" << dtype_name(dt) << "(op_ + " << b * esz << ", v" << b << ", v" << b + 1 << ", v" << b + 2 << ", v" << b + 3
       << ");";
   o << " } else {\n";
   for (int e = 0; e < PV; e++)
-    o << "if (x0 + " << e << " < W) wt_st1_" << tname(dt) << "(op_ + " << e * esz << ", v" << e << ");\n";
+    o << "if (x0 + " << e << " < W) wt_st1_" << dtype_name(dt) << "(op_ + " << e * esz << ", v" << e << ");\n";
   o << "}\n}\n";
   return o.str();
 }

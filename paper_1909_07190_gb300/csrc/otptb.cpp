@@ -24,17 +24,6 @@ namespace wt {
 
 namespace {
 
-const char *tn(int dtype) { return dtype == WT_F32 ? "f32" : dtype == WT_F16 ? "f16" : "bf16"; }
-
-std::string lit(float v) {
-  if (std::isnan(v)) return "__int_as_float(0x7fc00000)";
-  if (std::isinf(v)) return v > 0 ? "__int_as_float(0x7f800000)" : "__int_as_float(0xff800000)";
-  char b[64];
-  snprintf(b, sizeof b, "%.9g", (double)v);
-  std::string r(b);
-  if (r.find_first_of(".e") == std::string::npos) r += ".0";
-  return "(" + r + "f)";
-}
 
 }  // namespace
 
@@ -123,14 +112,14 @@ std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &
       const int dt = key.src_dtypes.at(s);
       const std::string S = "a.src[" + std::to_string(s) + "]";
       const std::string chan = n.src_chan >= 0 ? std::to_string(n.src_chan) : "ch";
-      o << "wt_sst(" << buf(i) << ", t_, " << NP << ", wt_ld1_" << tn(dt) << "((const unsigned char *)" << S
+      o << "wt_sst(" << buf(i) << ", t_, " << NP << ", wt_ld1_" << dtype_name(dt) << "((const unsigned char *)" << S
         << ".ptr + (wt_i64)" << chan << " * " << S << ".plane + (wt_i64)yc * " << S << ".pitch + (wt_i64)xc * "
         << elem_bytes(dt) << "));\n";
     } else {
       std::vector<std::string> st;
       for (const KOp &op : n.prog) {
         switch (op.op) {
-          case WT_OP_CONST: st.push_back(lit(op.value)); break;
+          case WT_OP_CONST: st.push_back(float_literal(op.value)); break;
           case WT_OP_XPAR: st.push_back("((float)(xc & 1))"); break;
           case WT_OP_YPAR: st.push_back("((float)(yc & 1))"); break;
           case WT_OP_CHAN: st.push_back(n.channels == 1 ? "(0.0f)" : "((float)ch)"); break;
@@ -169,7 +158,7 @@ std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &
         const std::string D = "a.dst[" + std::to_string(d) + "]";
         o << "if (x >= x0 && x < x0 + " << L.tbx << " && y >= y0 && y < y0 + " << L.tby
           << " && x < W && y < H" << (n.channels == 1 && g.channels > 1 ? " && ch == 0" : "") << ")\n";
-        o << "wt_st1_" << tn(dt) << "((unsigned char *)" << D << ".ptr + (wt_i64)" << (n.channels > 1 ? "ch" : "0")
+        o << "wt_st1_" << dtype_name(dt) << "((unsigned char *)" << D << ".ptr + (wt_i64)" << (n.channels > 1 ? "ch" : "0")
           << " * " << D << ".plane + (wt_i64)y * " << D << ".pitch + (wt_i64)x * " << elem_bytes(dt) << ", v_);\n";
       }
     }

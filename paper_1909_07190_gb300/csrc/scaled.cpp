@@ -23,15 +23,6 @@ namespace wt {
 
 namespace {
 
-const char *tn(int dtype) { return dtype == WT_F32 ? "f32" : dtype == WT_F16 ? "f16" : "bf16"; }
-
-std::string lit(double v) {
-  char b[64];
-  snprintf(b, sizeof b, "%.9g", (double)(float)v);
-  std::string r(b);
-  if (r.find_first_of(".e") == std::string::npos) r += ".0";
-  return "(" + r + "f)";
-}
 
 struct Lin {
   bool ok = true, is_const = true;
@@ -294,18 +285,18 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         o << "const unsigned char *sb" << q << " = wb + " << row * R.segb << " + (" << R.ncl * R.che << " + lane * "
           << 2 * VO << ") * " << sesz << ";\n";
         for (int b = 0; b < 2 * VO; b += 8) {
-          o << "wt_lds8_" << tn(sdt) << "(sb" << q << " + " << b * sesz;
+          o << "wt_lds8_" << dtype_name(sdt) << "(sb" << q << " + " << b * sesz;
           for (int t = 0; t < 8; t++) o << ", " << vn(q, LH + b + t);
           o << ");\n";
         }
         for (int k = 0; k < LH; k++)
-          o << vn(q, k) << " = wt_lds1_" << tn(sdt) << "(sb" << q << " - " << (LH - k) * sesz << ");\n";
+          o << vn(q, k) << " = wt_lds1_" << dtype_name(sdt) << "(sb" << q << " - " << (LH - k) * sesz << ");\n";
         for (int k = 0; k < RH; k++)
-          o << vn(q, LH + 2 * VO + k) << " = wt_lds1_" << tn(sdt) << "(sb" << q << " + " << (2 * VO + k) * sesz
+          o << vn(q, LH + 2 * VO + k) << " = wt_lds1_" << dtype_name(sdt) << "(sb" << q << " + " << (2 * VO + k) * sesz
             << ");\n";
       } else {
         for (int i = 0; i < NV; i++)
-          o << vn(q, i) << " = wt_ld1_" << tn(sdt) << "(rp" << q << " + (wt_i64)wt_clampi(xs + (" << i - LH
+          o << vn(q, i) << " = wt_ld1_" << dtype_name(sdt) << "(rp" << q << " + (wt_i64)wt_clampi(xs + (" << i - LH
             << "), 0, Ws - 1) * " << sesz << ");\n";
       }
     }
@@ -316,7 +307,7 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         bool first = true;
         for (int i = 0; i < NX; i++) {
           if (f.wx[i] == 0) continue;
-          o << (first ? "" : " + ") << lit(f.wx[i]) << " * " << vn(q, LH + 2 * k + DX0 + i);
+          o << (first ? "" : " + ") << float_literal(f.wx[i]) << " * " << vn(q, LH + 2 * k + DX0 + i);
           first = false;
         }
         o << ";\n";
@@ -329,7 +320,7 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         const int slot = ((u + delta) % NA + NA) % NA;
         if (w == 0 && dy != DY0) continue;
         for (int k = 0; k < VO; k++)
-          o << "acc" << slot << "_" << k << (dy == DY0 ? " = " : " += ") << lit(w) << " * h" << q << "_" << k
+          o << "acc" << slot << "_" << k << (dy == DY0 ? " = " : " += ") << float_literal(w) << " * h" << q << "_" << k
             << ";\n";
         if (dy != DY1) continue;
         // output row j is complete (rows j < 0 and j >= T are not stored)
@@ -339,16 +330,16 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         std::vector<std::string> outv;
         for (int k = 0; k < VO; k++) {
           std::string e = "acc" + std::to_string(slot) + "_" + std::to_string(k);
-          if (f.c != 0) e = "(" + e + " + " + lit(f.c) + ")";
+          if (f.c != 0) e = "(" + e + " + " + float_literal(f.c) + ")";
           outv.push_back(e);
         }
         o << "if (xo + " << VO << " <= W) {\n";
         for (int b = 0; b < VO; b += 4)
-          o << "wt_st4_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << b << ") * " << desz << ", " << outv[b] << ", "
+          o << "wt_st4_" << dtype_name(ddt) << "(op_ + (wt_i64)(xo + " << b << ") * " << desz << ", " << outv[b] << ", "
             << outv[b + 1] << ", " << outv[b + 2] << ", " << outv[b + 3] << ");\n";
         o << "} else {\n";
         for (int k = 0; k < VO; k++)
-          o << "if (xo + " << k << " < W) wt_st1_" << tn(ddt) << "(op_ + (wt_i64)(xo + " << k << ") * " << desz
+          o << "if (xo + " << k << " < W) wt_st1_" << dtype_name(ddt) << "(op_ + (wt_i64)(xo + " << k << ") * " << desz
             << ", " << outv[k] << ");\n";
         o << "}\n}\n}\n";
       }

@@ -337,6 +337,12 @@ struct ChainForm {
 ChainForm chain_form(const Pipeline &p, const std::vector<int> &stages);
 std::string emit_chain(const Pipeline &p, const std::vector<int> &stages, const CodegenKey &key,
                        const std::string &kname);
+// Code-generation helpers shared by the kernel generators (codegen.cpp):
+// the device helpers' dtype suffix ("f32", "f16", "bf16"), and an FP32
+// literal of v (NaN and infinities by bit pattern, integral values with a
+// point).
+const char *dtype_name(int dtype);
+std::string float_literal(float v);
 // Source table of a plain (per-stage) kernel: distinct (slot, channel spec).
 struct PlainSrc {
   int slot, chan;
