@@ -143,6 +143,11 @@ typedef struct {
  * the other flags are ignored.  Groups that read other levels
  * (down/up-sampling taps into the group) return WT_EUNSUPPORTED at run. */
 #define WT_FLAG_OTPTB 8
+/* Shared-memory windows of intermediates (the share 1 - frac_reg) stored
+ * in the group's 16-bit storage type (that of its first staged source) when
+ * it is FP16 or BF16, halving their bytes; values are rounded to that type
+ * (RNE) when stored, arithmetic stays FP32.  No effect on FP32 groups.     */
+#define WT_FLAG_SMEM16 16
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */

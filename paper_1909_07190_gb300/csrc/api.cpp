@@ -90,8 +90,9 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.max_regs = q.max_regs;
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
-        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB))
+        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB | WT_FLAG_SMEM16))
           fail(WT_EINVAL, "unknown flags");
+        r.smem16 = (q.flags & WT_FLAG_SMEM16) ? 1 : 0;
         r.plain = (q.flags & WT_FLAG_PLAIN) ? 1 : 0;
         r.otptb = (q.flags & WT_FLAG_OTPTB) ? 1 : 0;
         r.pairs = (q.flags & WT_FLAG_NO_PAIRS) ? 0 : 1;
@@ -186,7 +187,8 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].chunk_rows = r.chunk_rows;
         params[g].n_buffers = r.n_buffers;
         params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT) |
-                          (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0);
+                          (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0) |
+                          (r.smem16 ? WT_FLAG_SMEM16 : 0);
       }
   });
 }

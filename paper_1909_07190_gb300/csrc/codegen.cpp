@@ -58,6 +58,7 @@ std::string CodegenKey::str() const {
   s << "|o";
   for (int x : dst_dtypes) s << x;
   if (otptb) s << "|B" << tbx << "x" << tby;
+  if (win_dtype != WT_F32) s << "|W" << win_dtype;
   if (down) s << "|D" << tby;
   if (chain) s << "|R";
   return s.str();
@@ -116,7 +117,7 @@ FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key) {
     if (n.is_source || !n.in_smem) continue;
     off = align_up(off, 16);
     L.win_off[i] = off;
-    off += n.window * 32 * V * 4;
+    off += n.window * 32 * V * elem_bytes(key.win_dtype);
   }
   off = align_up(off, 8);
   L.bar_off = off;
@@ -274,7 +275,8 @@ void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
       o << "{ const int rr = wt_clampi(y_top + kk - (" << n.delay << "), 0, H - 1); kk = rr - y_top + ("
         << n.delay << "); }\n";
     o << "const int sl = ((kk % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
-    emit_load_vec(c, WT_F32, "sp" + std::to_string(ni) + " + sl * " + std::to_string(32 * V * 4), v, 4);
+    emit_load_vec(c, c.key.win_dtype, "sp" + std::to_string(ni) + " + sl * " +
+                      std::to_string(32 * V * elem_bytes(c.key.win_dtype)), v, elem_bytes(c.key.win_dtype));
   }
   emit_extend(c, n, v, [&](int j) { return tmp(ni, a, j); });
   o << "}\n";
@@ -860,7 +862,8 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
     o << "if (r > H - 1) {\n";
     if (n.in_smem) {
       o << "const int sl = (((k - 1) % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
-      emit_load_vec(c, WT_F32, "sp" + std::to_string(ni) + " + sl * " + std::to_string(32 * V * 4), v, 4);
+      emit_load_vec(c, c.key.win_dtype, "sp" + std::to_string(ni) + " + sl * " +
+                        std::to_string(32 * V * elem_bytes(c.key.win_dtype)), v, elem_bytes(c.key.win_dtype));
     } else {
       int prev = n.rotate ? slot_of(n, u, n.window > 1 ? 1 : 0) : n.window - 1;
       for (int e = 0; e < V; e++) o << v[e] << " = " << reg(ni, prev, n.xl + e) << ";\n";
@@ -897,9 +900,10 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
   }
   if (n.in_smem) {
     o << "{ const int sl = ((k % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
+    const int we = elem_bytes(c.key.win_dtype);
     for (int b = 0; b < V; b += 4)
-      o << "wt_st4_f32(sp" << ni << " + sl * " << 32 * V * 4 << " + " << b * 4 << ", " << v[b] << ", "
-        << v[b + 1] << ", " << v[b + 2] << ", " << v[b + 3] << ");\n";
+      o << "wt_st4_" << dtype_name(c.key.win_dtype) << "(sp" << ni << " + sl * " << 32 * V * we << " + " << b * we
+        << ", " << v[b] << ", " << v[b + 1] << ", " << v[b + 2] << ", " << v[b + 3] << ");\n";
     o << "}\n";
   } else {
     int sl = slot_of(n, u, 0);
@@ -1120,7 +1124,8 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   }
   for (size_t i = 0; i < g.nodes.size(); i++)
     if (L.win_off[i] >= 0)
-      o << "unsigned char *sp" << i << " = wb + " << L.win_off[i] << " + lane * " << V * 4 << ";\n";
+      o << "unsigned char *sp" << i << " = wb + " << L.win_off[i] << " + lane * " << V * elem_bytes(key.win_dtype)
+        << ";\n";
   // chunk issue: lane 0 arms the buffer's mbarrier and starts one TMA box per source
   o << "auto issue_chunk = [&](int c_) {\n__syncwarp();\nif (lane == 0) {\nwt_fence_proxy_async();\n"
        "const int gc_ = cbase + c_;\nconst wt_u32 b_ = bar + 8u * (wt_u32)(gc_ % NB);\n"

@@ -220,6 +220,9 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       }
       key.vec = pick_vec(L.params, key.src_dtypes);
       if (key.vec != 4) L.geom = analyze_group(p, L.stages, key.vec, L.params.frac_reg, 4);
+      // 16-bit windows when asked for and the group's storage is 16-bit
+      if (L.params.smem16 && !key.src_dtypes.empty() && key.src_dtypes[0] != WT_F32)
+        key.win_dtype = key.src_dtypes[0];
       L.layout = fused_layout(L.geom, key);
       level_dims(plan.W, plan.H, L.geom.level, &L.W, &L.H);
       int th = std::max(1, L.params.tile_h);

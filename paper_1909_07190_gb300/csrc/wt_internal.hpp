@@ -68,6 +68,7 @@ struct GroupParams {
   int tile_split = 1;  // short tiles for the last round of the tile queue
   int pairs = 1;       // packed f32x2 arithmetic where taps align
   int plain = 0;       // run the group's stages as per-stage kernels
+  int smem16 = 0;      // shared-memory windows in the 16-bit storage type
   int otptb = 0;       // one overlapped tile per thread block (the baseline
                        // tiling the paper compares against)
 };
@@ -262,6 +263,9 @@ struct CodegenKey {
   // every tile starts on an even row and the unroll is even: the row parity
   // of each unrolled step is a compile-time constant
   bool even_rows = false;
+  // storage type of the intermediates' shared-memory windows (FP32, or the
+  // group's 16-bit storage type; arithmetic stays FP32)
+  int win_dtype = WT_F32;
   // one overlapped tile of tbx x tby outputs per thread block, stages in
   // shared memory between block barriers
   bool otptb = false;

@@ -19,7 +19,7 @@ WT_OK, WT_EINVAL, WT_ENOMEM, WT_ECUDA, WT_EUNSUPPORTED, WT_ETIMEOUT, WT_EDEVICE,
 WT_F32, WT_F16, WT_BF16 = 0, 1, 2
 WT_EXEC_FUSED, WT_EXEC_PLAIN = 0, 1
 WT_MODEL_ANALYTIC, WT_MODEL_LEARNED = 0, 1
-WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT, WT_FLAG_PLAIN, WT_FLAG_OTPTB = 1, 2, 4, 8
+WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT, WT_FLAG_PLAIN, WT_FLAG_OTPTB, WT_FLAG_SMEM16 = 1, 2, 4, 8, 16
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
            "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14}
 TAPMODES = {"same": 0, "down2": 1, "up2": 2, "down4": 3, "up4": 4, "down8": 5, "up8": 6}

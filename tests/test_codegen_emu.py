@@ -267,3 +267,23 @@ def test_plain_blend(w, h):
     M = I.smooth_mask(5, w, h)
     got, d = run_emulated(spec, [A, B, M], exec_mode=wt.WT_EXEC_PLAIN)
     assert np.abs(got[0] - oracle_of(spec, [A, B, M])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["harris", "sharpen"])
+@pytest.mark.parametrize("dtype,tol", [(wt.WT_F16, 2e-3), (wt.WT_BF16, 1.6e-2)])
+@pytest.mark.parametrize("frac", [0.0, 0.5])
+def test_fused_16bit_shared_windows(name, dtype, tol, frac):
+    """Intermediates' shared-memory windows in the 16-bit storage type
+    (rounded when stored, FP32 arithmetic) against the oracle with the
+    storage type's tolerance; an FP32 group ignores the flag."""
+    spec = P.by_name(name)
+    dn = {wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
+    img = rnd(95, 150, 37, 1, dn)
+    prm = dict(tile_h=8, frac_reg=frac, flags=wt.WT_FLAG_SMEM16)
+    got, d = run_emulated(spec, [img], dtype=dtype, params=[prm])
+    ref = oracle_of(spec, [img])[0]
+    assert np.abs(got[0] - ref).max() <= tol * max(1.0, np.abs(ref).max())
+    img32 = rnd(96, 150, 37)
+    _, d32 = run_emulated(spec, [img32], params=[prm])
+    _, d32b = run_emulated(spec, [img32], params=[dict(tile_h=8, frac_reg=frac)])
+    assert d32["name"] == d32b["name"]

@@ -210,3 +210,17 @@ def test_multi_group_schedules(name, groups, tile_h, frac):
     ng = max(groups) + 1
     got = run_pipe(spec, [img], groups=groups, params=[dict(tile_h=tile_h, frac_reg=frac)] * ng)[0][0]
     assert np.abs(got - oracle_out(spec, [img])[0]).max() <= TOL["f32"]
+
+
+@pytest.mark.parametrize("frac", [0.0, 0.5])
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_16bit_shared_windows(frac, dtype):
+    """Intermediates' shared-memory windows stored in the 16-bit storage
+    type, corner response against the oracle at the storage tolerance."""
+    wt = wtmod()
+    spec = P.harris()
+    img = rnd(97, 1000, 517, dtype=dtype)
+    got = run_pipe(spec, [img], dtype=dtype,
+                   params=[dict(tile_h=16, frac_reg=frac, flags=wt.WT_FLAG_SMEM16)])[0][0]
+    ref = oracle_out(spec, [img])[0]
+    assert np.abs(got - ref).max() <= TOL[dtype] * max(1.0, np.abs(ref).max())
