@@ -318,10 +318,11 @@ def bilateral_schedule(bins: int = 8, levels: int = 3) -> tuple:
     """(groups, params) of bilateral_filter(bins, levels): the histogram's
     splat and 2x2 sums as one reduction chain across the levels, then the
     grid's blur, any nearest up-sampling stages and the slice, one group
-    each."""
+    each, as per-stage kernels (single stages: measured faster per stage
+    than as warp-tile groups)."""
     n_stages = len(bilateral_filter(bins, levels)["stages"])
     groups = [0] * levels + list(range(1, n_stages - levels + 1))
-    params = [dict(tile_h=8)] * (max(groups) + 1)
+    params = [dict(tile_h=8)] + [dict(flags=4)] * (max(groups))
     return groups, params
 
 
