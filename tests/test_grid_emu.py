@@ -116,3 +116,30 @@ def test_reduction_chain_weighted_and_filter():
     img = rnd(85, 150, 77)
     got, d = run_emulated(spec, [img], groups=groups, params=params)
     assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
+
+
+def chain_spec(const=0.0, extra_consumer=False, slot_offset=0):
+    inp = P.input_id(0)
+    b = P.Builder("c", [1])
+    s0 = b.stage("s1", P.ref(inp, 0, 0, mode="down2") + P.ref(inp, 1, slot_offset, mode="down2"), 2)
+    s1 = b.stage("s2", P.ref(s0, 0, 0, mode="down2") + P.ref(s0, 1, 1, mode="down2") + const, 2)
+    outs = [s1]
+    if extra_consumer:
+        outs.append(b.stage("side", P.ref(s0) * 2.0, 2))
+    b.output(*outs)
+    return b.build()
+
+
+@pytest.mark.parametrize("case", ["chain", "const", "consumed", "far_tap"])
+def test_chain_detection(case):
+    """Only true reduction chains become one launch: a constant term, an
+    intermediate read outside the group, or a tap outside the 2x2 block
+    leave the group to per-stage kernels; every case matches the oracle."""
+    spec = {"chain": chain_spec(), "const": chain_spec(const=0.5), "consumed": chain_spec(extra_consumer=True),
+            "far_tap": chain_spec(slot_offset=2)}[case]
+    img = rnd(98, 45, 31)
+    groups = [0, 0] + ([1] if case == "consumed" else [])
+    got, d = run_emulated(spec, [img], groups=groups, params=[dict()] * (max(groups) + 1))
+    assert d["name"].startswith("wt_chain_") == (case == "chain")
+    for g, r in zip(got, oracle_of(spec, [img])):
+        assert np.abs(g - r).max() <= 1e-5
