@@ -14,6 +14,8 @@
 // region (its region is the consumer's grown by the footprint, and the
 // clamped point lies between the consumer region's edge and the tile).
 #include <algorithm>
+#include <functional>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <sstream>
@@ -95,76 +97,117 @@ std::string emit_otptb(const Pipeline &p, const GroupGeom &g, const CodegenKey &
   const int nt = 32 * key.nw;
   int src_i = 0, dst_i = 0;
   std::vector<int> sidx(g.nodes.size(), -1), didx(g.nodes.size(), -1);
+  int mx_l = 0, mx_r = 0, mx_t = 0, mx_b = 0;
   for (size_t i = 0; i < g.nodes.size(); i++) {
     if (g.nodes[i].is_source) sidx[i] = src_i++;
     else if (g.nodes[i].is_liveout) didx[i] = dst_i++;
+    mx_l = std::max(mx_l, g.nodes[i].left);
+    mx_r = std::max(mx_r, g.nodes[i].right);
+    mx_t = std::max(mx_t, g.nodes[i].top);
+    mx_b = std::max(mx_b, g.nodes[i].bot);
   }
+  // Every region inside the image: no clamping, and a region point's tap is
+  // a constant offset in the producer's buffer from the point's own row and
+  // column there (block-uniform).
+  o << "const bool inner = x0 - " << mx_l << " >= 0 && x0 + " << L.tbx + mx_r << " <= W && y0 - " << mx_t
+    << " >= 0 && y0 + " << L.tby + mx_b << " <= H;\n";
   auto buf = [&](int i) { return "((float *)(wt_smem + " + std::to_string(L.off[i]) + "))"; };
-  for (int i : g.order) {
-    const Node &n = g.nodes[i];
-    const std::string RW = std::to_string(L.rw[i]), NP = std::to_string(L.rw[i] * L.rh[i]);
-    o << "for (int t_ = threadIdx.x; t_ < " << NP << "; t_ += " << nt << ") {\n";
-    o << "const int x = x0 + (" << L.rx[i] << ") + t_ % " << RW << ", y = y0 + (" << L.ry[i] << ") + t_ / " << RW
-      << ";\n";
-    o << "const int xc = wt_clampi(x, 0, W - 1), yc = wt_clampi(y, 0, H - 1);\n(void)xc;\n(void)yc;\n";
-    if (n.is_source) {
-      const int s = sidx[i];
-      const int dt = key.src_dtypes.at(s);
-      const std::string S = "a.src[" + std::to_string(s) + "]";
-      const std::string chan = n.src_chan >= 0 ? std::to_string(n.src_chan) : "ch";
-      o << "wt_sst(" << buf(i) << ", t_, " << NP << ", wt_ld1_" << dtype_name(dt) << "((const unsigned char *)" << S
-        << ".ptr + (wt_i64)" << chan << " * " << S << ".plane + (wt_i64)yc * " << S << ".pitch + (wt_i64)xc * "
-        << elem_bytes(dt) << "));\n";
-    } else {
-      std::vector<std::string> st;
-      for (const KOp &op : n.prog) {
-        switch (op.op) {
-          case WT_OP_CONST: st.push_back(float_literal(op.value)); break;
-          case WT_OP_XPAR: st.push_back("((float)(xc & 1))"); break;
-          case WT_OP_YPAR: st.push_back("((float)(yc & 1))"); break;
-          case WT_OP_CHAN: st.push_back(n.channels == 1 ? "(0.0f)" : "((float)ch)"); break;
-          case WT_OP_TAP: {
-            const int q = op.node;
-            st.push_back("wt_sld(" + buf(q) + ", (yc + (" + std::to_string(op.dy) + ") - y0 - (" +
-                         std::to_string(L.ry[q]) + ")) * " + std::to_string(L.rw[q]) + " + (xc + (" +
-                         std::to_string(op.dx) + ") - x0 - (" + std::to_string(L.rx[q]) + ")), " +
-                         std::to_string(L.rw[q] * L.rh[q]) + ")");
-          } break;
-          case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
-          case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
-          case WT_OP_SQRT: st.back() = "sqrtf(" + st.back() + ")"; break;
-          default: {
-            std::string b = st.back();
-            st.pop_back();
-            std::string a = st.back();
-            st.pop_back();
-            switch (op.op) {
-              case WT_OP_ADD: st.push_back("(" + a + " + " + b + ")"); break;
-              case WT_OP_SUB: st.push_back("(" + a + " - " + b + ")"); break;
-              case WT_OP_MUL: st.push_back("(" + a + " * " + b + ")"); break;
-              case WT_OP_DIV: st.push_back("(" + a + " / " + b + ")"); break;
-              case WT_OP_MIN: st.push_back("fminf(" + a + ", " + b + ")"); break;
-              case WT_OP_MAX: st.push_back("fmaxf(" + a + ", " + b + ")"); break;
-              default: fail(WT_EINVAL, "internal: opcode");
-            }
+  // the value expression of node i; tap(q, dx, dy) gives a producer read
+  auto expr_of = [&](const Node &n, const std::string &xp, const std::string &yp,
+                     const std::function<std::string(const KOp &)> &tap) {
+    std::vector<std::string> st;
+    for (const KOp &op : n.prog) {
+      switch (op.op) {
+        case WT_OP_CONST: st.push_back(float_literal(op.value)); break;
+        case WT_OP_XPAR: st.push_back("((float)(" + xp + " & 1))"); break;
+        case WT_OP_YPAR: st.push_back("((float)(" + yp + " & 1))"); break;
+        case WT_OP_CHAN: st.push_back(n.channels == 1 ? "(0.0f)" : "((float)ch)"); break;
+        case WT_OP_TAP: st.push_back(tap(op)); break;
+        case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
+        case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
+        case WT_OP_SQRT: st.back() = "sqrtf(" + st.back() + ")"; break;
+        default: {
+          std::string b = st.back();
+          st.pop_back();
+          std::string a = st.back();
+          st.pop_back();
+          switch (op.op) {
+            case WT_OP_ADD: st.push_back("(" + a + " + " + b + ")"); break;
+            case WT_OP_SUB: st.push_back("(" + a + " - " + b + ")"); break;
+            case WT_OP_MUL: st.push_back("(" + a + " * " + b + ")"); break;
+            case WT_OP_DIV: st.push_back("(" + a + " / " + b + ")"); break;
+            case WT_OP_MIN: st.push_back("fminf(" + a + ", " + b + ")"); break;
+            case WT_OP_MAX: st.push_back("fmaxf(" + a + ", " + b + ")"); break;
+            default: fail(WT_EINVAL, "internal: opcode");
           }
         }
       }
-      o << "const float v_ = " << st.back() << ";\n";
-      o << "wt_sst(" << buf(i) << ", t_, " << NP << ", v_);\n";
-      if (n.is_liveout) {
-        const int d = didx[i];
-        const int dt = key.dst_dtypes.at(d);
-        const std::string D = "a.dst[" + std::to_string(d) + "]";
-        o << "if (x >= x0 && x < x0 + " << L.tbx << " && y >= y0 && y < y0 + " << L.tby
-          << " && x < W && y < H" << (n.channels == 1 && g.channels > 1 ? " && ch == 0" : "") << ")\n";
-        o << "wt_st1_" << dtype_name(dt) << "((unsigned char *)" << D << ".ptr + (wt_i64)" << (n.channels > 1 ? "ch" : "0")
-          << " * " << D << ".plane + (wt_i64)y * " << D << ".pitch + (wt_i64)x * " << elem_bytes(dt) << ", v_);\n";
-      }
     }
-    o << "}\n__syncthreads();\n";
+    return st.back();
+  };
+  auto store_liveout = [&](const Node &n, int i) {
+    if (!n.is_liveout) return;
+    const int d = didx[i];
+    const int dt = key.dst_dtypes.at(d);
+    const std::string D = "a.dst[" + std::to_string(d) + "]";
+    o << "if (x >= x0 && x < x0 + " << L.tbx << " && y >= y0 && y < y0 + " << L.tby << " && x < W && y < H"
+      << (n.channels == 1 && g.channels > 1 ? " && ch == 0" : "") << ")\n";
+    o << "wt_st1_" << dtype_name(dt) << "((unsigned char *)" << D << ".ptr + (wt_i64)" << (n.channels > 1 ? "ch" : "0")
+      << " * " << D << ".plane + (wt_i64)y * " << D << ".pitch + (wt_i64)x * " << elem_bytes(dt) << ", v_);\n";
+  };
+  for (int pass = 0; pass < 2; pass++) {
+    const bool fast = pass == 0;
+    o << (fast ? "if (inner) {\n" : "} else {\n");
+    for (int i : g.order) {
+      const Node &n = g.nodes[i];
+      const std::string RW = std::to_string(L.rw[i]), NP = std::to_string(L.rw[i] * L.rh[i]);
+      if (fast) {
+        // rows of the region by warp, columns by lane: no division
+        o << "for (int ly = threadIdx.x >> 5; ly < " << L.rh[i] << "; ly += " << key.nw << ")\n";
+        o << "for (int lx = threadIdx.x & 31; lx < " << L.rw[i] << "; lx += 32) {\n";
+        o << "const int t_ = ly * " << RW << " + lx;\n";
+        o << "const int x = x0 + (" << L.rx[i] << ") + lx, y = y0 + (" << L.ry[i] << ") + ly;\n(void)x;\n(void)y;\n";
+      } else {
+        o << "for (int t_ = threadIdx.x; t_ < " << NP << "; t_ += " << nt << ") {\n";
+        o << "const int x = x0 + (" << L.rx[i] << ") + t_ % " << RW << ", y = y0 + (" << L.ry[i] << ") + t_ / "
+          << RW << ";\n";
+        o << "const int xc = wt_clampi(x, 0, W - 1), yc = wt_clampi(y, 0, H - 1);\n(void)xc;\n(void)yc;\n";
+      }
+      if (n.is_source) {
+        const int s = sidx[i];
+        const int dt = key.src_dtypes.at(s);
+        const std::string S = "a.src[" + std::to_string(s) + "]";
+        const std::string chan = n.src_chan >= 0 ? std::to_string(n.src_chan) : "ch";
+        o << "wt_sst(" << buf(i) << ", t_, " << NP << ", wt_ld1_" << dtype_name(dt) << "((const unsigned char *)"
+          << S << ".ptr + (wt_i64)" << chan << " * " << S << ".plane + (wt_i64)" << (fast ? "y" : "yc") << " * " << S
+          << ".pitch + (wt_i64)" << (fast ? "x" : "xc") << " * " << elem_bytes(dt) << "));\n";
+      } else {
+        std::string e;
+        if (fast) {
+          // producer index = ly * RWq + lx + constant
+          std::map<int, std::string> base;  // per producer region width
+          e = expr_of(n, "x", "y", [&](const KOp &op) {
+            const int q = op.node;
+            const int off = (op.dy + L.ry[i] - L.ry[q]) * L.rw[q] + (op.dx + L.rx[i] - L.rx[q]);
+            return "wt_sld(" + buf(q) + ", ly * " + std::to_string(L.rw[q]) + " + lx + (" + std::to_string(off) +
+                   "), " + std::to_string(L.rw[q] * L.rh[q]) + ")";
+          });
+        } else {
+          e = expr_of(n, "xc", "yc", [&](const KOp &op) {
+            const int q = op.node;
+            return "wt_sld(" + buf(q) + ", (yc + (" + std::to_string(op.dy) + ") - y0 - (" + std::to_string(L.ry[q]) +
+                   ")) * " + std::to_string(L.rw[q]) + " + (xc + (" + std::to_string(op.dx) + ") - x0 - (" +
+                   std::to_string(L.rx[q]) + ")), " + std::to_string(L.rw[q] * L.rh[q]) + ")";
+          });
+        }
+        o << "const float v_ = " << e << ";\n";
+        o << "wt_sst(" << buf(i) << ", t_, " << NP << ", v_);\n";
+        store_liveout(n, i);
+      }
+      o << "}\n__syncthreads();\n";
+    }
   }
-  o << "}\n";
+  o << "}\n}\n";
   return o.str();
 }
 

@@ -313,7 +313,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (!fused) h = fnv1a(kPlainVersion, sizeof kPlainVersion, h);
   static const char kGatherVersion[] = "wt-gather-4";  // kernels reading other levels
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
-  static const char kOtptbVersion[] = "wt-otptb-1";  // the block-tile kernel's own changes
+  static const char kOtptbVersion[] = "wt-otptb-2";  // the block-tile kernel's own changes
   if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
   static const char kDownVersion[] = "wt-down-4";  // the down-sampling kernel's own changes
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);

@@ -120,3 +120,16 @@ def test_otptb_refuses_other_levels():
     img = rnd(50, 40, 30)
     with pytest.raises(wt.WtError):
         run_emulated(spec, [img], groups=[0, 1], params=[dict(tile_h=8), blk(8, 2)], launch=1)
+
+
+@pytest.mark.parametrize("name", ["harris", "sharpen"])
+@pytest.mark.parametrize("vec,tile_h,warps", [(4, 16, 8), (1, 8, 4), (2, 32, 16)])
+def test_otptb_interior_tiles(name, vec, tile_h, warps):
+    """Images large enough for interior block tiles (every region inside
+    the image: row-by-warp, column-by-lane loops and constant tap offsets)
+    next to clamped border tiles."""
+    spec = P.by_name(name)
+    img = rnd(400 + vec + tile_h, 600, 200)
+    got, _ = run_emulated(spec, [img], params=[blk(tile_h, warps, vec)])
+    ref = oracle_of(spec, [img])[0]
+    assert np.abs(got[0] - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
