@@ -59,14 +59,20 @@ int or_dag_shapes(const or_stage *st, int n_st, const or_input *in, int n_in,
       const or_op *o = &S->ops[i];
       switch (o->op) {
         case OR_CONST: case OR_XPAR: case OR_YPAR: case OR_CHAN: depth++; break;
-        case OR_TAP: {
+        case OR_TAP: case OR_TAPZ: {
           if (o->slot < 0 || o->slot >= S->n_in) return -4;
           int p = S->in[o->slot];
           if (p >= s || p < -n_in) return -1;
           int pl = p >= 0 ? level[p] : 0;
           int pc = p >= 0 ? C[p] : in[-p - 1].channels;
-          if (o->chan >= 0 && o->chan >= pc) return -4;
-          if (o->chan < 0 && pc != 1 && pc != S->channels) return -4;
+          if (o->op == OR_TAPZ) {
+            /* a plane offset reads planes of the same depth (or the one
+               plane of a one-plane producer), at the consumer's level */
+            if (o->mode != OR_SAME || (pc != 1 && pc != S->channels)) return -4;
+          } else {
+            if (o->chan >= 0 && o->chan >= pc) return -4;
+            if (o->chan < 0 && pc != 1 && pc != S->channels) return -4;
+          }
           int implied;
           if (o->mode == OR_SAME) implied = pl;
           else if (o->mode >= OR_DOWN2 && o->mode <= OR_UP8)
@@ -122,6 +128,13 @@ static double eval_point(const or_stage *S, const src_box *src, int x, int y, in
         int px = clampi(tap_coord(o->mode, x, o->dx), 0, p->W - 1);
         int py = clampi(tap_coord(o->mode, y, o->dy), 0, p->H - 1);
         int pc = o->chan >= 0 ? o->chan : (p->C == 1 ? 0 : c);
+        stk[sp++] = p->data[((size_t)pc * p->bh + (py - p->y0)) * p->bw + (px - p->x0)];
+      } break;
+      case OR_TAPZ: {
+        const src_box *p = &src[o->slot];
+        int px = clampi(x + o->dx, 0, p->W - 1);
+        int py = clampi(y + o->dy, 0, p->H - 1);
+        int pc = clampi(c + o->chan, 0, p->C - 1);
         stk[sp++] = p->data[((size_t)pc * p->bh + (py - p->y0)) * p->bw + (px - p->x0)];
       } break;
       case OR_ADD: sp--; stk[sp - 1] = stk[sp - 1] + stk[sp]; break;
@@ -223,7 +236,7 @@ static void propagate_need(const or_stage *st, int last, const int32_t *W,
     const or_stage *S = &st[s];
     for (int i = 0; i < S->n_ops; i++) {
       const or_op *o = &S->ops[i];
-      if (o->op != OR_TAP) continue;
+      if (o->op != OR_TAP && o->op != OR_TAPZ) continue;
       int p = S->in[o->slot];
       if (p < 0) continue;
       int x0, x1, y0, y1;
@@ -340,6 +353,17 @@ static double brute_rec(const or_stage *st, const int32_t *W, const int32_t *H,
         int px = clampi(tap_coord(o->mode, x, o->dx), 0, pw - 1);
         int py = clampi(tap_coord(o->mode, y, o->dy), 0, ph - 1);
         int pc = o->chan >= 0 ? o->chan : (pcn == 1 ? 0 : c);
+        if (p < 0) stk[sp++] = in[-p - 1].data[((size_t)pc * ph + py) * pw + px];
+        else stk[sp++] = brute_rec(st, W, H, C, in, p, px, py, pc);
+      } break;
+      case OR_TAPZ: {
+        int p = S->in[o->slot];
+        int pw, ph, pcn;
+        if (p < 0) { pw = in[-p - 1].width; ph = in[-p - 1].height; pcn = in[-p - 1].channels; }
+        else { pw = W[p]; ph = H[p]; pcn = C[p]; }
+        int px = clampi(x + o->dx, 0, pw - 1);
+        int py = clampi(y + o->dy, 0, ph - 1);
+        int pc = clampi(c + o->chan, 0, pcn - 1);
         if (p < 0) stk[sp++] = in[-p - 1].data[((size_t)pc * ph + py) * pw + px];
         else stk[sp++] = brute_rec(st, W, H, C, in, p, px, py, pc);
       } break;

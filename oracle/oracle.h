@@ -24,6 +24,9 @@
  *     constant).  Domain of level l: W_l = ceil(W_{l-1}/2).
  *   - Channels are planar; a tap with chan < 0 reads the consumer's channel
  *     (channel 0 when the producer has one channel).
+ *   - Volumes (App. A, 3-D groups): a D x H x W volume is an image of D
+ *     planes; a TAPZ reads the producer at plane offset dz from the
+ *     consumer's plane, clamped to [0, D-1] like x and y.
  *
  * Layout of every array: planar, data[(c*H + y)*W + x], FP64.
  */
@@ -43,7 +46,10 @@ enum or_opcode {
   OR_NEG = 9, OR_ABS = 10, OR_SQRT = 11,
   OR_XPAR = 12, /* push (x & 1) of the consumer point           */
   OR_YPAR = 13, /* push (y & 1) of the consumer point           */
-  OR_CHAN = 14  /* push the consumer point's channel index      */
+  OR_CHAN = 14, /* push the consumer point's channel index      */
+  OR_TAPZ = 15  /* push producer in[slot] at (x+dx, y+dy) of plane
+                   clamp(c + chan, 0, C_p - 1): a 3-D tap whose plane
+                   offset dz is held in `chan` (mode must be same)    */
 };
 /* down by 2^s: mode 2s-1 (producer s levels finer); up by 2^s: mode 2s */
 enum or_tapmode { OR_SAME = 0, OR_DOWN2 = 1, OR_UP2 = 2, OR_DOWN4 = 3, OR_UP4 = 4, OR_DOWN8 = 5, OR_UP8 = 6 };

@@ -11,6 +11,7 @@ Pipeline format (plain data, shared with the CUDA path only as an input):
     stages: list of dicts {"channels": int, "inputs": [int, ...],
                            "ops": [tuple, ...]}
     op tuples: ("const", v) | ("tap", slot, dx, dy[, chan[, mode]]) |
+               ("tapz", slot, dx, dy, dz) (plane offset dz, clamped) |
                ("add",) ("sub",) ("mul",) ("div",) ("min",) ("max",)
                ("neg",) ("abs",) ("sqrt",) ("xpar",) ("ypar",) ("chan",)
     mode: "same" | "down2" | "up2" | "down4" | "up4" | "down8" | "up8";
@@ -32,7 +33,8 @@ _lock = threading.Lock()
 _lib = None
 
 _OPS = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7,
-        "max": 8, "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14}
+        "max": 8, "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14,
+        "tapz": 15}
 _MODES = {"same": 0, "down2": 1, "up2": 2, "down4": 3, "up4": 4, "down8": 5, "up8": 6}
 
 
@@ -133,6 +135,8 @@ class _Packed:
                         o.chan = int(t[4])
                     if len(t) > 5:
                         o.mode = _MODES[t[5]]
+                elif name == "tapz":
+                    o.slot, o.dx, o.dy, o.chan = int(t[1]), int(t[2]), int(t[3]), int(t[4])
             self.keep += [ins, ops]
             self.st[s].channels = int(S["channels"])
             self.st[s].n_in = len(S["inputs"])

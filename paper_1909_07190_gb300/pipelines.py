@@ -65,6 +65,13 @@ def ref(producer: int, dx: int = 0, dy: int = 0, chan: int = -1, mode: str = "sa
     return E([("ref", int(producer), int(dx), int(dy), int(chan), mode)])
 
 
+def refz(producer: int, dx: int = 0, dy: int = 0, dz: int = 0) -> E:
+    """A 3-D read: `producer` at (x + dx, y + dy) of plane z + dz, where z is
+    the output point's plane (a D x H x W volume is an image of D planes);
+    every coordinate is clamped to the volume (App. A's 3-D groups)."""
+    return E([("refz", int(producer), int(dx), int(dy), int(dz))])
+
+
 def input_id(j: int) -> int:
     return -(j + 1)
 
@@ -82,6 +89,11 @@ class Builder:
                 if pid not in producers:
                     producers.append(pid)
                 ops.append(("tap", producers.index(pid), dx, dy, chan, mode))
+            elif t[0] == "refz":
+                _, pid, dx, dy, dz = t
+                if pid not in producers:
+                    producers.append(pid)
+                ops.append(("tapz", producers.index(pid), dx, dy, dz))
             else:
                 ops.append(t)
         self.p["stages"].append({"name": name, "channels": int(channels),
@@ -326,8 +338,48 @@ def bilateral_schedule(bins: int = 8, levels: int = 3) -> tuple:
     return groups, params
 
 
+def _lin3(producer: int, weights, axis: str) -> E:
+    """sum_i weights[i] * P at offset i - r along `axis` ("x", "y" or "z")."""
+    r = len(weights) // 2
+    total = None
+    for i, w in enumerate(weights):
+        d = i - r
+        t = refz(producer, d if axis == "x" else 0, d if axis == "y" else 0, d if axis == "z" else 0)
+        t = t if w == 1.0 else float(w) * t
+        total = t if total is None else total + t
+    return total
+
+
+def unsharp3d(depth: int = 64, amount: float = 1.5) -> dict:
+    """3-D unsharp mask over a `depth`-plane volume: 5-tap binomial blur along
+    x, y and z (three stages), out = clamp(v + amount (v - blur), 0, 1)."""
+    b = Builder("unsharp3d", [depth])
+    inp = input_id(0)
+    bx = b.stage("bx", _lin3(inp, BINOMIAL5, "x"), depth)
+    by = b.stage("by", _lin3(bx, BINOMIAL5, "y"), depth)
+    bz = b.stage("bz", _lin3(by, BINOMIAL5, "z"), depth)
+    v = refz(inp)
+    b.output(b.stage("sharpen", emin(emax(v + amount * (v - refz(bz)), 0.0), 1.0), depth))
+    return b.build()
+
+
+def heat3d(steps: int = 4, depth: int = 64, alpha: float = 0.125) -> dict:
+    """`steps` explicit time steps of 3-D diffusion, each a 7-point stencil
+    u' = u + alpha (sum of the six face neighbours - 6 u) with clamp-to-edge
+    (zero flux) boundaries; alpha <= 1/6 keeps it stable."""
+    b = Builder("heat3d", [depth])
+    u = input_id(0)
+    for k in range(steps):
+        nb = (refz(u, -1, 0, 0) + refz(u, 1, 0, 0) + refz(u, 0, -1, 0) + refz(u, 0, 1, 0)
+              + refz(u, 0, 0, -1) + refz(u, 0, 0, 1))
+        u = b.stage("step%d" % k, refz(u) + alpha * (nb - 6.0 * refz(u)), depth)
+    b.output(u)
+    return b.build()
+
+
 def by_name(name: str) -> dict:
     table = {"sharpen": sharpen, "harris": harris, "harris_raw": lambda: harris(False),
              "blend": blend, "blur": blur3, "blur_rgb": lambda: blur3(3),
-             "bilateral_grid": bilateral_grid, "bilateral": bilateral_filter}
+             "bilateral_grid": bilateral_grid, "bilateral": bilateral_filter,
+             "unsharp3d": unsharp3d, "heat3d": heat3d}
     return table[name]()
