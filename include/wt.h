@@ -51,8 +51,14 @@ typedef enum {
   WT_OP_NEG = 9, WT_OP_ABS = 10, WT_OP_SQRT = 11,
   WT_OP_XPAR = 12, /* push (x & 1) of the output point, as 0.0 or 1.0       */
   WT_OP_YPAR = 13, /* push (y & 1) of the output point                      */
-  WT_OP_CHAN = 14  /* push the output point's channel index (0.0, 1.0, ...):
+  WT_OP_CHAN = 14, /* push the output point's channel index (0.0, 1.0, ...):
                       per-plane programs such as a histogram's bins         */
+  /* 3-D tap (App. A, groups over volumes): a D x H x W volume is an image
+   * of D planes; push producer inputs[slot] at (x + dx, y + dy) of plane
+   * clamp(z + chan, 0, D - 1), z = the output point's plane.  `chan` holds
+   * the plane offset dz (-16..16); mode must be WT_TAP_SAME; the producer
+   * has the stage's plane count, or one plane (then plane 0 is read).     */
+  WT_OP_TAPZ = 15
 } wt_opcode;
 
 /* How a tap maps the output point (x, y) to the producer point; these are
@@ -130,6 +136,10 @@ typedef struct {
   int32_t chunk_rows;      /* TMA staging rows per chunk (0 = 8)             */
   int32_t n_buffers;       /* TMA staging buffers per input (0 = 2)          */
   int32_t flags;           /* WT_FLAG_* bits; 0 = all features on            */
+  int32_t tile_o;          /* 3-D groups: points of the axis that is neither
+                              x nor streamed (planes, or rows with
+                              WT_FLAG_ZSTREAM) per warp tile, held in
+                              registers (0 = 4)                              */
 } wt_group_params;
 
 #define WT_FLAG_NO_PAIRS 1      /* scalar FP32 instead of packed f32x2 pairs     */
@@ -148,6 +158,15 @@ typedef struct {
  * it is FP16 or BF16, halving their bytes; values are rounded to that type
  * (RNE) when stored, arithmetic stays FP32.  No effect on FP32 groups.     */
 #define WT_FLAG_SMEM16 16
+/* Groups with plane-offset taps (WT_OP_TAPZ) run as 3-D warp tiles (App. A
+ * generalised hybrid tiling): lanes along x (vec = 1, 2 or 4 points each,
+ * 0 = 2), tile_h points along the streamed (split) axis, tile_o points of
+ * the third axis in registers.  The split axis is y (rows) by default; with
+ * this flag it is z (planes) and tile_o counts rows.  frac_reg, chunk_rows,
+ * n_buffers and the other flags are ignored for such groups; a group the
+ * 3-D kernel cannot take (other levels, parity or channel ops, fixed-
+ * channel taps, windows above 192 registers) runs per stage.              */
+#define WT_FLAG_ZSTREAM 32
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */

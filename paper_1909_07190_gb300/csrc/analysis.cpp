@@ -270,6 +270,12 @@ GroupGeom analyze_group(const Pipeline &p, const std::vector<int> &stages, int v
       g.fusable = false;
       g.why_not = "group spans several levels";
     }
+    if (p.stages[s].has_z) {
+      // plane-offset taps: the 3-D group kernel (vol.cpp) or per stage
+      g.fusable = false;
+      g.why_not = "plane-offset taps (3-D group)";
+      return g;
+    }
   }
   auto pchan = [&](int pid) { return pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1]; };
   // Sources: distinct (producer outside the group, channel spec); producers

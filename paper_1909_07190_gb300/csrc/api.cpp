@@ -78,8 +78,13 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         if (q.tile_h < 1 || q.tile_h > 4096) fail(WT_EINVAL, "tile_h out of range");
         if (q.warps_per_block < 1 || q.warps_per_block > 16) fail(WT_EINVAL, "warps_per_block out of range");
         if (!(q.frac_reg >= 0.f && q.frac_reg <= 1.f)) fail(WT_EINVAL, "frac_reg out of [0,1]");
-        if (q.vec != 0 && q.vec != 4 && q.vec != 8 && !((q.flags & WT_FLAG_OTPTB) && (q.vec == 1 || q.vec == 2)))
-          fail(WT_EINVAL, "vec must be 0, 4 or 8 (1 or 2 with WT_FLAG_OTPTB)");
+        bool zgroup = false;  // the group has a plane-offset tap: a 3-D group
+        for (int i = 0; i < n; i++)
+          if (s.group_of_stage[i] == g && p.stages[i].has_z) zgroup = true;
+        if (q.vec != 0 && q.vec != 4 && q.vec != 8 &&
+            !((q.flags & WT_FLAG_OTPTB) && (q.vec == 1 || q.vec == 2)) && !(zgroup && (q.vec == 1 || q.vec == 2)))
+          fail(WT_EINVAL, "vec must be 0, 4 or 8 (1 or 2 with WT_FLAG_OTPTB or in 3-D groups)");
+        if (q.tile_o < 0 || q.tile_o > 64) fail(WT_EINVAL, "tile_o out of range");
         if (q.max_regs < 0 || q.max_regs > 255) fail(WT_EINVAL, "max_regs out of range");
         if (q.chunk_rows < 0 || q.chunk_rows > 64) fail(WT_EINVAL, "chunk_rows out of range");
         if (q.n_buffers < 0 || q.n_buffers > 8) fail(WT_EINVAL, "n_buffers out of range");
@@ -90,8 +95,11 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.max_regs = q.max_regs;
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
-        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB | WT_FLAG_SMEM16))
+        if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB | WT_FLAG_SMEM16 |
+                        WT_FLAG_ZSTREAM))
           fail(WT_EINVAL, "unknown flags");
+        r.tile_o = q.tile_o;
+        r.zstream = (q.flags & WT_FLAG_ZSTREAM) ? 1 : 0;
         r.smem16 = (q.flags & WT_FLAG_SMEM16) ? 1 : 0;
         r.plain = (q.flags & WT_FLAG_PLAIN) ? 1 : 0;
         r.otptb = (q.flags & WT_FLAG_OTPTB) ? 1 : 0;
@@ -188,7 +196,8 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].n_buffers = r.n_buffers;
         params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT) |
                           (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0) |
-                          (r.smem16 ? WT_FLAG_SMEM16 : 0);
+                          (r.smem16 ? WT_FLAG_SMEM16 : 0) | (r.zstream ? WT_FLAG_ZSTREAM : 0);
+        params[g].tile_o = r.tile_o;
       }
   });
 }

@@ -118,6 +118,8 @@ int pchannels(const Pipeline &p, int pid) { return pid >= 0 ? p.stages[pid].chan
 }  // namespace
 
 ChainForm chain_form(const Pipeline &p, const std::vector<int> &stages) {
+  for (int sid : stages)
+    if (p.stages[sid].has_z) return ChainForm();
   ChainForm f;
   const int k = (int)stages.size();
   if (k < 2 || k > 6) return f;

@@ -61,6 +61,7 @@ std::string CodegenKey::str() const {
   if (win_dtype != WT_F32) s << "|W" << win_dtype;
   if (down) s << "|D" << tby;
   if (chain) s << "|R";
+  if (vol) s << "|Z" << vol_split << "x" << vol_to << "x" << tby;
   return s.str();
 }
 
@@ -1186,10 +1187,11 @@ std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid) {
   std::vector<PlainSrc> r;
   const Stage &S = p.stages[sid];
   for (const Op &op : S.ops) {
-    if (op.op != WT_OP_TAP) continue;
+    if (op.op != WT_OP_TAP && op.op != WT_OP_TAPZ) continue;
     int pid = S.inputs[op.slot];
     int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
-    int spec = pc == 1 ? 0 : op.chan;
+    // plane-offset taps read planes relative to the output's (spec -1)
+    int spec = pc == 1 ? 0 : (op.op == WT_OP_TAPZ ? -1 : op.chan);
     bool found = false;
     for (auto &x : r)
       if (x.slot == op.slot && x.chan == spec) found = true;
@@ -1216,25 +1218,32 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
   o << "(void)H;\nif (x0 >= W) return;\n";
   // rows to load: per (src, dy): x range per element
   struct Row {
-    int s, dy, dxmin, dxmax, mode;
+    int s, dy, dxmin, dxmax, mode, dz;
   };
   std::vector<Row> rows;
-  for (const Op &op : S.ops) {
-    if (op.op != WT_OP_TAP) continue;
+  // source index and plane offset of a tap
+  auto tap_src = [&](const Op &op, int *dz) {
     int pid = S.inputs[op.slot];
     int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
-    int spec = pc == 1 ? 0 : op.chan;
+    int spec = pc == 1 ? 0 : (op.op == WT_OP_TAPZ ? -1 : op.chan);
+    *dz = (op.op == WT_OP_TAPZ && pc != 1) ? op.chan : 0;
     int s = 0;
     for (size_t i = 0; i < srcs.size(); i++)
       if (srcs[i].slot == op.slot && srcs[i].chan == spec) s = (int)i;
+    return s;
+  };
+  for (const Op &op : S.ops) {
+    if (op.op != WT_OP_TAP && op.op != WT_OP_TAPZ) continue;
+    int dz = 0;
+    const int s = tap_src(op, &dz);
     bool found = false;
     for (auto &r : rows)
-      if (r.s == s && r.dy == op.dy) {
+      if (r.s == s && r.dy == op.dy && r.dz == dz) {
         r.dxmin = std::min(r.dxmin, op.dx);
         r.dxmax = std::max(r.dxmax, op.dx);
         found = true;
       }
-    if (!found) rows.push_back({s, op.dy, op.dx, op.dx, op.mode});
+    if (!found) rows.push_back({s, op.dy, op.dx, op.dx, op.mode, dz});
   }
   auto col_index = [&](int mode, int e, int dx) {
     // offset of the producer column, relative to the row base, for element e
@@ -1250,7 +1259,9 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     int dt = key.src_dtypes.at(s);
     int lo = col_index(r.mode, 0, r.dxmin), hi = col_index(r.mode, PV - 1, r.dxmax);
     std::string sd = "a.src[" + std::to_string(s) + "]";
-    std::string zc = srcs[s].chan >= 0 ? std::to_string(srcs[s].chan) : "ch";
+    std::string zc = srcs[s].chan >= 0 ? std::to_string(srcs[s].chan)
+                     : r.dz == 0 ? std::string("ch")
+                                 : "wt_clampi(ch + (" + std::to_string(r.dz) + "), 0, " + sd + ".C - 1)";
     const int sh = tap_shift(r.mode);
     std::string base = tap_is_down(r.mode) ? "(x0 * " + std::to_string(1 << sh) + ")"
                        : (tap_is_up(r.mode) ? "(x0 >> " + std::to_string(sh) + ")" : "x0");
@@ -1298,16 +1309,12 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
         case WT_OP_XPAR: st.push_back("((float)((x0 + " + std::to_string(e) + ") & 1))"); break;
         case WT_OP_YPAR: st.push_back("((float)(y & 1))"); break;
         case WT_OP_CHAN: st.push_back("((float)ch)"); break;
-        case WT_OP_TAP: {
-          int pid = S.inputs[op.slot];
-          int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
-          int spec = pc == 1 ? 0 : op.chan;
-          int s = 0;
-          for (size_t i = 0; i < srcs.size(); i++)
-            if (srcs[i].slot == op.slot && srcs[i].chan == spec) s = (int)i;
+        case WT_OP_TAP: case WT_OP_TAPZ: {
+          int dz = 0;
+          const int s = tap_src(op, &dz);
           int ri = 0;
           for (size_t i = 0; i < rows.size(); i++)
-            if (rows[i].s == s && rows[i].dy == op.dy) ri = (int)i;
+            if (rows[i].s == s && rows[i].dy == op.dy && rows[i].dz == dz) ri = (int)i;
           int lo = col_index(rows[ri].mode, 0, rows[ri].dxmin);
           int j = col_index(op.mode, e, op.dx) - lo;
           st.push_back("L" + std::to_string(ri) + "_" + std::to_string(j));

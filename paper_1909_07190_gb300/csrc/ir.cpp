@@ -75,7 +75,7 @@ void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch
         case WT_OP_CONST: case WT_OP_XPAR: case WT_OP_YPAR: case WT_OP_CHAN:
           depth++;
           break;
-        case WT_OP_TAP: {
+        case WT_OP_TAP: case WT_OP_TAPZ: {
           if (o.slot < 0 || o.slot >= (int)T.inputs.size())
             fail(WT_EINVAL, "stage " + std::to_string(s) + ": tap slot out of range");
           if (o.mode < WT_TAP_SAME || o.mode > WT_TAP_UP8)
@@ -85,10 +85,20 @@ void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch
           int pid = T.inputs[o.slot];
           int pl = pid >= 0 ? p.stages[pid].level : 0;
           int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
-          if (o.chan >= pc) fail(WT_EINVAL, "stage " + std::to_string(s) + ": tap channel out of range");
-          if (o.chan < 0 && pc != 1 && pc != S.channels)
-            fail(WT_EINVAL, "stage " + std::to_string(s) +
-                                ": same-channel tap of a producer with a different channel count");
+          if (o.op == WT_OP_TAPZ) {
+            // plane offset in `chan`; planes of the same depth, same level
+            if (o.mode != WT_TAP_SAME) fail(WT_EINVAL, "stage " + std::to_string(s) + ": plane tap with a scaling mode");
+            if (o.chan < -16 || o.chan > 16)
+              fail(WT_EINVAL, "stage " + std::to_string(s) + ": plane offset beyond +-16");
+            if (pc != 1 && pc != S.channels)
+              fail(WT_EINVAL, "stage " + std::to_string(s) + ": plane tap of a producer with another plane count");
+            T.has_z = true;
+          } else {
+            if (o.chan >= pc) fail(WT_EINVAL, "stage " + std::to_string(s) + ": tap channel out of range");
+            if (o.chan < 0 && pc != 1 && pc != S.channels)
+              fail(WT_EINVAL, "stage " + std::to_string(s) +
+                                  ": same-channel tap of a producer with a different channel count");
+          }
           int implied = pl + tap_level_delta(o.mode);
           if (lv == INT_MIN) lv = implied;
           else if (lv != implied)
@@ -97,16 +107,21 @@ void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch
             fail(WT_EINVAL, "stage " + std::to_string(s) + ": one producer read in two tap modes");
           slot_mode[o.slot] = o.mode;
           Edge &e = edges[o.slot];
+          const int dz = o.op == WT_OP_TAPZ ? o.chan : 0;
           if (!used[o.slot]) {
             used[o.slot] = 1;
             e.producer = pid; e.mode = o.mode;
             e.dxmin = e.dxmax = o.dx; e.dymin = e.dymax = o.dy;
+            e.dzmin = e.dzmax = dz;
           } else {
             e.dxmin = std::min(e.dxmin, o.dx); e.dxmax = std::max(e.dxmax, o.dx);
             e.dymin = std::min(e.dymin, o.dy); e.dymax = std::max(e.dymax, o.dy);
+            e.dzmin = std::min(e.dzmin, dz); e.dzmax = std::max(e.dzmax, dz);
           }
-          if (std::find(e.chans.begin(), e.chans.end(), o.chan) == e.chans.end())
-            e.chans.push_back(o.chan);
+          if (o.op == WT_OP_TAPZ) e.zrel = true;
+          const int spec = o.op == WT_OP_TAPZ ? -1 : o.chan;
+          if (std::find(e.chans.begin(), e.chans.end(), spec) == e.chans.end())
+            e.chans.push_back(spec);
           depth++;
         } break;
         case WT_OP_ADD: case WT_OP_SUB: case WT_OP_MUL: case WT_OP_DIV:
@@ -137,6 +152,8 @@ void build_pipeline(Pipeline &p, const wt_stage *st, int n, const int32_t *in_ch
       h = fnv1a(&q.value, sizeof(float), h);
     }
   }
+  p.has_z = false;
+  for (const Stage &T : p.stages) p.has_z = p.has_z || T.has_z;
   p.outputs.assign(outs, outs + n_out);
   p.is_output.assign(n, 0);
   for (int o : p.outputs) {

@@ -115,6 +115,25 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     const auto &G = groups[gi];
     GroupParams gp = group_params(p, (int)gi);
     bool fused = p.sched.exec == WT_EXEC_FUSED && !gp.plain;
+    bool zgroup = false;
+    for (int s : G) zgroup = zgroup || p.stages[s].has_z;
+    if (fused && zgroup) {
+      // plane-offset taps: a 3-D group (App. A), else per-stage kernels
+      const int V = gp.vec > 0 ? gp.vec : 2;
+      VolGeom vg = vol_analyze(p, G, gp.zstream, gp.tile_o > 0 ? gp.tile_o : 4, std::max(1, gp.tile_h), V);
+      if (vg.ok) {
+        for (int s : vg.liveouts) materialize(s, !p.consumers[s].empty());
+        Launch L;
+        L.fused = false;
+        L.stages = G;
+        L.params = gp;
+        L.key.vol = true;
+        L.vol = vg;
+        plan.launches.push_back(L);
+        continue;
+      }
+      fused = false;
+    }
     if (fused && !gp.otptb && chain_form(p, G).ok) {
       // a reduction chain across levels: one launch, only its last stage
       // written
@@ -236,6 +255,40 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       L.grid[1] = L.grid[2] = 1;
       L.smem = key.nw * L.layout.warp_bytes;
       if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "group needs more than 227 KB of shared memory per block");
+    } else if (key.vol) {
+      const VolGeom &vg = L.vol;
+      key.plain = true;
+      key.vec = vg.V;
+      key.tby = vg.Ts;
+      key.vol_split = vg.split;
+      key.vol_to = vg.To;
+      key.pairs = false;
+      key.chunk = key.nbuf = 0;
+      key.frac_reg = 1.f;
+      for (const VolNode &nd : vg.nodes)
+        if (nd.source) {
+          L.src.push_back(nd.id);
+          L.src_chan.push_back(-1);
+          key.src_dtypes.push_back(loc_of(nd.id).dtype);
+        }
+      for (int s : vg.liveouts) {
+        L.dst.push_back(s);
+        key.dst_dtypes.push_back(plan.loc[s].dtype);
+      }
+      level_dims(plan.W, plan.H, vg.level, &L.W, &L.H);
+      const int NS = vg.split == 0 ? L.H : vg.D, NO = vg.split == 0 ? vg.D : L.H;
+      const int64_t tx = (L.W + vg.ow - 1) / vg.ow, ts = (NS + vg.Ts - 1) / vg.Ts, to = (NO + vg.To - 1) / vg.To;
+      const int64_t nt = tx * ts * to;
+      if (nt * 32 >= (1ll << 31)) fail(WT_EUNSUPPORTED, "too many 3-D tiles");
+      L.tiles_x = (int)tx;
+      L.tiles_y = (int)ts;
+      L.n_tiles = (int)nt;
+      L.block = 32 * key.nw;
+      L.grid[0] = (unsigned)((nt + key.nw - 1) / key.nw);
+      L.grid[1] = L.grid[2] = 1;
+      L.smem = 0;
+      L.kname = kernel_name(p, key, false);
+      continue;
     } else if (key.chain) {
       const ChainForm cf = chain_form(p, L.stages);
       const int last = L.stages.back();
@@ -319,10 +372,13 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   static const char kChainVersion[] = "wt-chain-1";  // the reduction-chain kernel's own changes
   if (key.chain) h = fnv1a(kChainVersion, sizeof kChainVersion, h);
+  static const char kVolVersion[] = "wt-vol-1";  // the 3-D group kernel's own changes
+  if (key.vol) h = fnv1a(kVolVersion, sizeof kVolVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;
   if (key.down) return std::string("wt_down_") + hx;
   if (key.chain) return std::string("wt_chain_") + hx;
+  if (key.vol) return std::string("wt_vol_") + hx;
   return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }
 
@@ -330,6 +386,7 @@ std::string launch_source(const Pipeline &p, const Launch &L) {
   if (L.key.otptb) return emit_otptb(p, L.geom, L.key, L.kname);
   if (L.key.down) return emit_down(p, L.stages[0], L.key, L.kname);
   if (L.key.chain) return emit_chain(p, L.stages, L.key, L.kname);
+  if (L.key.vol) return emit_vol(p, L.vol, L.key, L.kname);
   if (L.fused) return emit_fused(p, L.geom, L.key, L.kname);
   return emit_plain(p, L.stages[0], L.key, L.kname);
 }
@@ -401,7 +458,7 @@ void fill_args(const Pipeline &p, const RunPlan &plan, const Launch &L, char *ws
   a.chunk = L.layout.chunk;
   a.nbuf = L.layout.nbuf;
   a.out_w = L.layout.out_w;
-  a.channels = L.fused ? L.geom.channels : 1;
+  a.channels = L.fused ? L.geom.channels : (L.key.vol ? L.vol.D : 1);
   (void)p;
 }
 

@@ -49,6 +49,7 @@ Lin scale(Lin a, double s) {
 }  // namespace
 
 DownForm down_form(const Pipeline &p, int sid) {
+  if (p.stages[sid].has_z) return DownForm();
   DownForm f;
   const Stage &S = p.stages[sid];
   if (S.level < 1) return f;

@@ -1,0 +1,572 @@
+// 3-D fused groups: the generalised hybrid tiling of App. A (Alg. 3,
+// Fig. 8) on volumes.
+//
+// A D x H x W volume is an image of D planes; stages read producers at
+// constant offsets (dx, dy, dz) (WT_OP_TAPZ, clamp-to-edge in every axis).
+// One warp computes one overlapped tile of a group:
+//   * x: 32 lanes x V points; the tile's outputs are the columns left after
+//     the group's x halo (overlapped tiling, Sec. 4);
+//   * the split axis s (rows, or planes with WT_FLAG_ZSTREAM): streamed, Ts
+//     output points per tile; each node keeps a window of its last rows
+//     (register rotation by unrolling, Sec. 5);
+//   * the third axis o: a register tile (App. A: R_j = T_j for the axes
+//     that are not split) of vol_to output points plus each node's halo.
+// Producer reads are then register reads: along o from another o point of
+// the same thread (Type 1 of Fig. 8 with W_o = 1), along s from an older
+// window slot, along x from the V + xl + xr values each stored row holds,
+// its neighbours' values exchanged by shuffles when the row was stored
+// (Types 3/4).  Sources (pipeline inputs, earlier groups) are read from
+// memory at each tap row.
+//
+// Clamp-to-edge at every stage: a node's value at a point outside the
+// volume is its value at the clamped point.  Rows before 0 are not computed;
+// when row 0 is, it is copied into the older slots; rows past the end copy
+// the previous row.  o points outside [0, N_o) copy their nearest in-range
+// neighbour after each row; x points outside [0, W) take the value of
+// column 0 or W-1 by shuffle (border tiles only).
+#include <algorithm>
+#include <numeric>
+#include <set>
+#include <sstream>
+#include <tuple>
+
+#include "wt_internal.hpp"
+
+namespace wt {
+
+int VolGeom::node_of(int id) const {
+  for (size_t i = 0; i < nodes.size(); i++)
+    if (nodes[i].id == id) return (int)i;
+  return -1;
+}
+
+namespace {
+
+// A tap of a group stage in (x, s, o) coordinates.
+struct VTap {
+  int node = 0;  // producer node index
+  int dx = 0, ds = 0, dO = 0;
+};
+
+// Taps of stage program ops, in program order (non-tap ops: node = -1).
+std::vector<VTap> stage_taps(const Pipeline &p, const VolGeom &g, int sid) {
+  const Stage &S = p.stages[sid];
+  std::vector<VTap> out;
+  for (const Op &op : S.ops) {
+    VTap t;
+    t.node = -1;
+    if (op.op == WT_OP_TAP || op.op == WT_OP_TAPZ) {
+      const int dz = op.op == WT_OP_TAPZ ? op.chan : 0;
+      t.node = g.node_of(S.inputs[op.slot]);
+      t.dx = op.dx;
+      t.ds = g.split == 0 ? op.dy : dz;
+      t.dO = g.split == 0 ? dz : op.dy;
+    }
+    out.push_back(t);
+  }
+  return out;
+}
+
+}  // namespace
+
+VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V) {
+  VolGeom g;
+  g.split = split;
+  g.To = std::max(1, To);
+  g.Ts = std::max(1, Ts);
+  g.V = V;
+  auto no = [&](const std::string &why) {
+    g.ok = false;
+    g.why = why;
+    return g;
+  };
+  if (V != 1 && V != 2 && V != 4) return no("vec must be 1, 2 or 4");
+  if (stages.empty()) return no("empty group");
+  g.D = p.stages[stages[0]].channels;
+  g.level = p.stages[stages[0]].level;
+  std::set<int> in_group(stages.begin(), stages.end());
+  // sources in order of first use, then the stages
+  std::vector<int> src_ids;
+  for (int s : stages) {
+    const Stage &S = p.stages[s];
+    if (S.channels != g.D) return no("stages of a 3-D group need one plane count");
+    if (S.level != g.level) return no("stages of a 3-D group need one level");
+    for (const Op &op : S.ops) {
+      if (op.op == WT_OP_XPAR || op.op == WT_OP_YPAR || op.op == WT_OP_CHAN)
+        return no("parity and channel ops are not supported in 3-D groups");
+      if (op.op != WT_OP_TAP && op.op != WT_OP_TAPZ) continue;
+      if (op.op == WT_OP_TAP && (op.mode != WT_TAP_SAME || op.chan >= 0))
+        return no("3-D groups read producers at their own level and plane offsets only");
+      const int pid = S.inputs[op.slot];
+      if (in_group.count(pid)) continue;
+      if (std::find(src_ids.begin(), src_ids.end(), pid) == src_ids.end()) src_ids.push_back(pid);
+    }
+  }
+  if ((int)src_ids.size() > kMaxAllSrc) return no("too many sources");
+  for (size_t k = 0; k < src_ids.size(); k++) {
+    const int id = src_ids[k];
+    VolNode n;
+    n.id = id;
+    n.source = true;
+    n.src_index = (int)k;
+    n.planes = id >= 0 ? p.stages[id].channels : p.in_channels[-id - 1];
+    if (n.planes != 1 && n.planes != g.D) return no("a source of a 3-D group has another plane count");
+    g.nodes.push_back(n);
+  }
+  for (int s : stages) {
+    VolNode n;
+    n.id = s;
+    n.planes = g.D;
+    g.nodes.push_back(n);
+  }
+  for (int s : stages) {
+    bool live = p.is_output[s] != 0;
+    for (int c : p.consumers[s])
+      if (!in_group.count(c)) live = true;
+    if (live) {
+      g.nodes[g.node_of(s)].dst_index = (int)g.liveouts.size();
+      g.liveouts.push_back(s);
+    }
+  }
+  if (g.liveouts.empty()) return no("group without liveouts");
+  if ((int)g.liveouts.size() > kMaxDst) return no("too many liveouts");
+  const int N = (int)g.nodes.size();
+  // Backward pass over the stages (reverse topological order): x, o and s
+  // requirements of every producer from its consumers' (Sec. 4 overlapped
+  // tiles; App. A right hyperplanes per axis).
+  std::vector<int> nl(N, 0), nr(N, 0), lead(N, 0), need_lo(N, 0), olo(N, 0), ohi(N, 0);
+  std::vector<char> needed(N, 0);
+  for (int s : g.liveouts) needed[g.node_of(s)] = 1;
+  for (int k = (int)stages.size() - 1; k >= 0; k--) {
+    const int ci = g.node_of(stages[k]);
+    if (!needed[ci]) continue;
+    // every consumer covers at least the tile's own columns, rows and o
+    // points (final here: its consumers come later in the order)
+    nl[ci] = std::max(nl[ci], 0); nr[ci] = std::max(nr[ci], 0);
+    olo[ci] = std::max(olo[ci], 0); ohi[ci] = std::max(ohi[ci], 0);
+    need_lo[ci] = std::min(need_lo[ci], 0);
+    for (const VTap &t : stage_taps(p, g, stages[k])) {
+      if (t.node < 0) continue;
+      const int pi = t.node;
+      if (!needed[pi]) {
+        needed[pi] = 1;
+        nl[pi] = nl[ci] - t.dx; nr[pi] = nr[ci] + t.dx;
+        lead[pi] = lead[ci] + std::max(0, t.ds);
+        need_lo[pi] = need_lo[ci] + t.ds;
+        olo[pi] = olo[ci] - t.dO; ohi[pi] = ohi[ci] + t.dO;
+      } else {
+        nl[pi] = std::max(nl[pi], nl[ci] - t.dx); nr[pi] = std::max(nr[pi], nr[ci] + t.dx);
+        lead[pi] = std::max(lead[pi], lead[ci] + std::max(0, t.ds));
+        need_lo[pi] = std::min(need_lo[pi], need_lo[ci] + t.ds);
+        olo[pi] = std::max(olo[pi], olo[ci] - t.dO); ohi[pi] = std::max(ohi[pi], ohi[ci] + t.dO);
+      }
+    }
+  }
+  // sources likewise
+  for (int i = 0; i < N; i++) {
+    if (!needed[i]) continue;
+    nl[i] = std::max(nl[i], 0); nr[i] = std::max(nr[i], 0);
+    olo[i] = std::max(olo[i], 0); ohi[i] = std::max(ohi[i], 0);
+    need_lo[i] = std::min(need_lo[i], 0);
+  }
+  for (int k = 0; k < (int)stages.size(); k++)
+    if (!needed[g.node_of(stages[k])]) return no("dead stage inside a 3-D group");
+  g.pro = 0;
+  for (int i = 0; i < N; i++) {
+    VolNode &n = g.nodes[i];
+    n.lead = lead[i];
+    n.need_lo = need_lo[i];
+    n.olo = olo[i];
+    n.ohi = ohi[i];
+    g.hxl = std::max(g.hxl, nl[i]);
+    g.hxr = std::max(g.hxr, nr[i]);
+    // sources are read at their consumers' rows: no prologue of their own
+    if (!n.source) g.pro = std::max(g.pro, n.lead - n.need_lo);
+  }
+  // windows and stored neighbour values of the group's stages
+  for (int k = 0; k < (int)stages.size(); k++) {
+    const int ci = g.node_of(stages[k]);
+    for (const VTap &t : stage_taps(p, g, stages[k])) {
+      if (t.node < 0) continue;
+      VolNode &pn = g.nodes[t.node];
+      const VolNode &cn = g.nodes[ci];
+      if (pn.source) {
+        g.xml = std::max(g.xml, -t.dx);
+        g.xmr = std::max(g.xmr, t.dx);
+        continue;
+      }
+      pn.window = std::max(pn.window, pn.lead - cn.lead - t.ds + 1);
+      // a row past the end copies the previous one: keep it
+      if (t.ds > 0) pn.window = std::max(pn.window, 2);
+      pn.xl = std::max(pn.xl, -t.dx);
+      pn.xr = std::max(pn.xr, t.dx);
+    }
+  }
+  for (VolNode &n : g.nodes)
+    if (!n.source && (n.xl > 32 * V - 1 || n.xr > 32 * V - 1)) return no("x taps wider than a warp tile");
+  g.hxlp = (g.hxl + V - 1) / V * V;
+  g.ow = (32 * V - g.hxlp - g.hxr) / V * V;
+  if (g.ow < V) return no("x halo leaves no output columns");
+  // unroll: the least common multiple of the windows when small, else the
+  // largest window (nodes whose window does not divide it shift)
+  int U = 1;
+  for (const VolNode &n : g.nodes)
+    if (!n.source) U = std::lcm(U, n.window);
+  if (U > 8) {
+    U = 1;
+    for (const VolNode &n : g.nodes)
+      if (!n.source) U = std::max(U, n.window);
+  }
+  g.U = U;
+  g.regs = 0;
+  for (VolNode &n : g.nodes) {
+    if (n.source) continue;
+    n.rotate = U % n.window == 0;
+    g.regs += n.window * (g.To + n.olo + n.ohi) * (V + n.xl + n.xr);
+  }
+  if (g.regs > 192) return no("3-D group windows need " + std::to_string(g.regs) +
+                              " registers per thread; lower tile_o or vec");
+  g.ok = true;
+  return g;
+}
+
+namespace {
+
+struct Emit {
+  const Pipeline &p;
+  const VolGeom &g;
+  const CodegenKey &key;
+  std::ostringstream o;
+  Emit(const Pipeline &pp, const VolGeom &gg, const CodegenKey &k) : p(pp), g(gg), key(k) {}
+
+  int ninst(const VolNode &n) const { return g.To + n.olo + n.ohi; }
+  // slot of age a at unrolled step u
+  int slot(const VolNode &n, int u, int a) const {
+    if (n.rotate) return ((u - a) % n.window + n.window) % n.window;
+    return a;
+  }
+  // register of node ni, slot sl, o point j (relative to o0), x entry e
+  // (relative to the lane's first column; -xl .. V - 1 + xr)
+  std::string reg(int ni, int sl, int j, int e) const {
+    const VolNode &n = g.nodes[ni];
+    return "w" + std::to_string(ni) + "_" + std::to_string(sl) + "_" + std::to_string(j + n.olo) + "_" +
+           std::to_string(e + n.xl);
+  }
+  std::string s_index(const std::string &r) const { return "wt_clampi(" + r + ", 0, NS - 1)"; }
+  std::string o_index(const std::string &j) const { return "wt_clampi(o0 + (" + j + "), 0, NO - 1)"; }
+
+  // Address (unsigned char *) of row r, o point j of source si, column 0.
+  std::string src_row(int si, const std::string &r, int j) const {
+    const VolNode &n = g.nodes[si];
+    const std::string S = "a.src[" + std::to_string(n.src_index) + "]";
+    std::string zi, yi;
+    if (g.split == 0) {
+      zi = n.planes == 1 ? "0" : o_index(std::to_string(j));
+      yi = s_index(r);
+    } else {
+      zi = n.planes == 1 ? "0" : s_index(r);
+      yi = o_index(std::to_string(j));
+    }
+    return "((const unsigned char *)" + S + ".ptr + (wt_i64)" + zi + " * " + S + ".plane + (wt_i64)" + yi +
+           " * " + S + ".pitch)";
+  }
+
+  // Source rows a stage reads: one per (source, ds, dO), with the tap
+  // columns it spans, in order of first use.
+  struct SrcRow {
+    int si, ds, dO, lo, hi;
+  };
+  std::vector<SrcRow> src_rows(int sid) const {
+    std::vector<SrcRow> rows;
+    for (const VTap &t : stage_taps(p, g, sid)) {
+      if (t.node < 0 || !g.nodes[t.node].source) continue;
+      bool found = false;
+      for (SrcRow &r : rows)
+        if (r.si == t.node && r.ds == t.ds && r.dO == t.dO) {
+          r.lo = std::min(r.lo, t.dx);
+          r.hi = std::max(r.hi, t.dx);
+          found = true;
+        }
+      if (!found) rows.push_back({t.node, t.ds, t.dO, t.dx, t.dx});
+    }
+    return rows;
+  }
+  void program(int sid, int ni, int u, bool safe);
+  void store_row(int ni, int u, bool safe);
+  void liveout(int ni, int u);
+  void step(int u, bool safe);
+  std::string run();
+};
+
+// Evaluates stage `sid` (node ni) for every o point of its range at the
+// node's row of step u, into the age-0 slot; sources are loaded per tap row.
+void Emit::program(int sid, int ni, int u, bool safe) {
+  const Stage &S = p.stages[sid];
+  const VolNode &n = g.nodes[ni];
+  const std::vector<VTap> taps = stage_taps(p, g, sid);
+  const int V = g.V;
+  const int sl0 = slot(n, u, 0);
+  const std::vector<SrcRow> rows = src_rows(sid);
+  for (int j = -n.olo; j < g.To + n.ohi; j++) {
+    o << "{\n";
+    // source values: column xl0 + c for c in [lo, V - 1 + hi]
+    for (size_t ri = 0; ri < rows.size(); ri++) {
+      const SrcRow &r = rows[ri];
+      const VolNode &sn = g.nodes[r.si];
+      const int dt = key.src_dtypes.at(sn.src_index);
+      const int esz = elem_bytes(dt);
+      o << "{ const unsigned char *rp_ = " << src_row(r.si, "rn + (" + std::to_string(r.ds) + ")", j + r.dO)
+        << ";\n";
+      for (int c = r.lo; c < V + r.hi; c++) {
+        const std::string col = "(xl0 + (" + std::to_string(c) + "))";
+        o << "S" << ri << "_" << (c - r.lo) << " = wt_ld1_" << dtype_name(dt) << "(rp_ + (wt_i64)"
+          << (safe ? "wt_clampi(" + col + ", 0, W - 1)" : col) << " * " << esz << ");\n";
+      }
+      o << "}\n";
+    }
+    for (int e = 0; e < V; e++) {
+      std::vector<std::string> st;
+      for (size_t k = 0; k < S.ops.size(); k++) {
+        const Op &op = S.ops[k];
+        switch (op.op) {
+          case WT_OP_CONST: st.push_back(float_literal(op.value)); break;
+          case WT_OP_TAP: case WT_OP_TAPZ: {
+            const VTap &t = taps[k];
+            const VolNode &pn = g.nodes[t.node];
+            if (pn.source) {
+              int ri = 0;
+              for (size_t q = 0; q < rows.size(); q++)
+                if (rows[q].si == t.node && rows[q].ds == t.ds && rows[q].dO == t.dO) ri = (int)q;
+              st.push_back("S" + std::to_string(ri) + "_" + std::to_string(e + t.dx - rows[ri].lo));
+            } else {
+              const int age = pn.lead - n.lead - t.ds;
+              st.push_back(reg(t.node, slot(pn, u, age), j + t.dO, e + t.dx));
+            }
+          } break;
+          case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
+          case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
+          case WT_OP_SQRT: st.back() = "sqrtf(" + st.back() + ")"; break;
+          default: {
+            std::string b = st.back();
+            st.pop_back();
+            std::string a = st.back();
+            st.pop_back();
+            switch (op.op) {
+              case WT_OP_ADD: st.push_back("(" + a + " + " + b + ")"); break;
+              case WT_OP_SUB: st.push_back("(" + a + " - " + b + ")"); break;
+              case WT_OP_MUL: st.push_back("(" + a + " * " + b + ")"); break;
+              case WT_OP_DIV: st.push_back("(" + a + " / " + b + ")"); break;
+              case WT_OP_MIN: st.push_back("fminf(" + a + ", " + b + ")"); break;
+              case WT_OP_MAX: st.push_back("fmaxf(" + a + ", " + b + ")"); break;
+              default: fail(WT_EINVAL, "internal: opcode in a 3-D group");
+            }
+          }
+        }
+      }
+      o << "v" << e << " = " << st.back() << ";\n";
+    }
+    // clamp-to-edge along x in border tiles: columns left of 0 take column
+    // 0's value (element 0 of lane -xs/V), columns right of W-1 take W-1's
+    if (safe) {
+      o << "if (xb) {\n";
+      o << "const float fl_ = __shfl_sync(WT_FULL, v0, lz_);\n";
+      o << "float sr_ = v0;\n";
+      for (int e = 1; e < V; e++) o << "if (ez_ == " << e << ") sr_ = v" << e << ";\n";
+      o << "const float fr_ = __shfl_sync(WT_FULL, sr_, lw_);\n";
+      for (int e = 0; e < V; e++)
+        o << "if (xl0 + " << e << " < 0) v" << e << " = fl_; else if (xl0 + " << e << " > W - 1) v" << e
+          << " = fr_;\n";
+      o << "}\n";
+    }
+    for (int e = 0; e < V; e++) o << reg(ni, sl0, j, e) << " = v" << e << ";\n";
+    // neighbour values: entry e' < 0 from lane - ceil(-e'/V), entry >= V from
+    // lane + floor(e'/V)
+    for (int e = -n.xl; e < 0; e++) {
+      const int dl = (-e + V - 1) / V;
+      const int src = e + dl * V;
+      o << reg(ni, sl0, j, e) << " = __shfl_up_sync(WT_FULL, v" << src << ", " << dl << ");\n";
+    }
+    for (int e = V; e < V + n.xr; e++) {
+      const int dl = e / V;
+      const int src = e - dl * V;
+      o << reg(ni, sl0, j, e) << " = __shfl_down_sync(WT_FULL, v" << src << ", " << dl << ");\n";
+    }
+    o << "}\n";
+  }
+}
+
+// o points outside [0, NO): copies of the nearest in-range point (all
+// stored entries), after every o point of the row is computed.
+void Emit::store_row(int ni, int u, bool safe) {
+  (void)safe;
+  const VolNode &n = g.nodes[ni];
+  const int sl0 = slot(n, u, 0);
+  const int V = g.V;
+  if (n.olo + n.ohi == 0 && g.To == 1) return;
+  o << "if (ob) {\n";
+  for (int j = -n.olo + 1; j < g.To + n.ohi; j++) {
+    o << "if (o0 + " << j << " > NO - 1) {";
+    for (int e = -n.xl; e < V + n.xr; e++) o << " " << reg(ni, sl0, j, e) << " = " << reg(ni, sl0, j - 1, e) << ";";
+    o << " }\n";
+  }
+  for (int j = g.To + n.ohi - 2; j >= -n.olo; j--) {
+    o << "if (o0 + " << j << " < 0) {";
+    for (int e = -n.xl; e < V + n.xr; e++) o << " " << reg(ni, sl0, j, e) << " = " << reg(ni, sl0, j + 1, e) << ";";
+    o << " }\n";
+  }
+  o << "}\n";
+}
+
+void Emit::liveout(int ni, int u) {
+  const VolNode &n = g.nodes[ni];
+  const int sl0 = slot(n, u, 0);
+  const int V = g.V;
+  const int dt = key.dst_dtypes.at(n.dst_index);
+  const int esz = elem_bytes(dt);
+  const std::string D = "a.dst[" + std::to_string(n.dst_index) + "]";
+  o << "if (rn >= s0 && rn < s0 + " << g.Ts << " && rn < NS && olane) {\n";
+  for (int j = 0; j < g.To; j++) {
+    o << "if (o0 + " << j << " < NO) {\n";
+    std::string zi = g.split == 0 ? "(o0 + " + std::to_string(j) + ")" : "rn";
+    std::string yi = g.split == 0 ? "rn" : "(o0 + " + std::to_string(j) + ")";
+    o << "unsigned char *dp_ = (unsigned char *)" << D << ".ptr + (wt_i64)" << zi << " * " << D
+      << ".plane + (wt_i64)" << yi << " * " << D << ".pitch + (wt_i64)xl0 * " << esz << ";\n";
+    for (int e = 0; e < V; e++)
+      o << "if (xl0 + " << e << " < W) wt_st1_" << dtype_name(dt) << "(dp_ + " << e * esz << ", "
+        << reg(ni, sl0, j, e) << ");\n";
+    o << "}\n";
+  }
+  o << "}\n";
+}
+
+void Emit::step(int u, bool safe) {
+  const int V = g.V;
+  for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+    const VolNode &n = g.nodes[ni];
+    if (n.source) continue;
+    o << "{ // stage " << n.id << "\n";
+    o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
+    o << "if (rn >= 0 && rn < NS) {\n";
+    program(n.id, (int)ni, u, safe);
+    store_row((int)ni, u, safe);
+    o << "}";
+    if (n.window > 1) {
+      // past the end: the previous row's values (clamp-to-edge)
+      o << " else if (rn >= NS) {\n";
+      const int s0l = slot(n, u, 0), s1l = slot(n, u, 1);
+      for (int j = -n.olo; j < g.To + n.ohi; j++)
+        for (int e = -n.xl; e < V + n.xr; e++) o << reg((int)ni, s0l, j, e) << " = " << reg((int)ni, s1l, j, e) << ";\n";
+      o << "}\n";
+      // row 0 stands for the rows before it
+      o << "if (rn == 0) {\n";
+      for (int a = 1; a < n.window; a++) {
+        const int sa = slot(n, u, a);
+        for (int j = -n.olo; j < g.To + n.ohi; j++)
+          for (int e = -n.xl; e < V + n.xr; e++) o << reg((int)ni, sa, j, e) << " = " << reg((int)ni, s0l, j, e) << ";\n";
+      }
+      o << "}\n";
+    } else {
+      o << "\n";
+    }
+    if (n.dst_index >= 0) liveout((int)ni, u);
+    o << "}\n";
+  }
+}
+
+std::string Emit::run() {
+  const int V = g.V;
+  o << "const int lane = threadIdx.x & 31;\n";
+  o << "const int t_ = blockIdx.x * " << key.nw << " + (threadIdx.x >> 5);\n";
+  o << "if (t_ >= a.n_tiles) return;\n";
+  o << "const int W = a.W;\n";
+  if (g.split == 0) o << "const int NS = a.H, NO = a.channels;\n";
+  else o << "const int NS = a.channels, NO = a.H;\n";
+  o << "const int tx_ = t_ % a.tiles_x, rest_ = t_ / a.tiles_x;\n";
+  o << "const int s0 = (rest_ % a.tiles_y) * " << g.Ts << ", o0 = (rest_ / a.tiles_y) * " << g.To << ";\n";
+  o << "const int xs = tx_ * " << g.ow << " - " << g.hxlp << ";\n";
+  o << "const int xl0 = xs + lane * " << V << ";\n";
+  o << "const bool olane = lane * " << V << " >= " << g.hxlp << " && lane * " << V << " < " << g.hxlp + g.ow
+    << ";\n";
+  // border tiles: some column a lane computes or reads lies outside [0, W)
+  o << "const bool xb = xs - " << g.xml << " < 0 || xs + " << 32 * V + g.xmr << " > W;\n";
+  int OL = 0, OH = 0;
+  for (const VolNode &n : g.nodes) {
+    OL = std::max(OL, n.olo);
+    OH = std::max(OH, n.ohi);
+  }
+  o << "const bool ob = o0 - " << OL << " < 0 || o0 + " << g.To - 1 + OH << " > NO - 1;\n";
+  o << "const int lz_ = wt_clampi(-xs / " << V << ", 0, 31);\n";
+  o << "const int lw_ = wt_clampi((W - 1 - xs) / " << V << ", 0, 31), ez_ = (W - 1 - xs) - ((W - 1 - xs) / " << V
+    << ") * " << V << ";\n";
+  o << "(void)lz_; (void)lw_; (void)ez_; (void)xb; (void)ob; (void)olane;\n";
+  // window registers
+  for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+    const VolNode &n = g.nodes[ni];
+    if (n.source) continue;
+    for (int sl = 0; sl < n.window; sl++)
+      for (int j = -n.olo; j < g.To + n.ohi; j++) {
+        o << "float";
+        for (int e = -n.xl; e < V + n.xr; e++) o << (e > -n.xl ? ", " : " ") << reg((int)ni, sl, j, e) << " = 0.f";
+        o << ";\n";
+      }
+  }
+  // per-row scratch: computed values and source values
+  o << "float";
+  for (int e = 0; e < V; e++) o << (e ? ", " : " ") << "v" << e;
+  o << ";\n";
+  std::vector<int> swidth;
+  for (const VolNode &n : g.nodes) {
+    if (n.source) continue;
+    const std::vector<SrcRow> rows = src_rows(n.id);
+    for (size_t ri = 0; ri < rows.size(); ri++) {
+      if (swidth.size() <= ri) swidth.push_back(0);
+      swidth[ri] = std::max(swidth[ri], V + rows[ri].hi - rows[ri].lo);
+    }
+  }
+  for (size_t ri = 0; ri < swidth.size(); ri++)
+    for (int c = 0; c < swidth[ri]; c++) o << "float S" << ri << "_" << c << ";\n";
+  o << "const int nsteps = min(" << g.Ts << ", NS - s0) + " << g.pro << ";\n";
+  auto loop = [&](bool safe) {
+    o << "#pragma unroll 1\n";
+    o << "for (int kb = 0; kb < nsteps; kb += " << g.U << ") {\n";
+    for (int u = 0; u < g.U; u++) {
+      o << "{ const int k = kb + " << u << ";\nif (k < nsteps) {\n";
+      // shift the windows that do not rotate by renaming
+      for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+        const VolNode &n = g.nodes[ni];
+        if (n.source || n.rotate || n.window < 2) continue;
+        for (int a = n.window - 1; a >= 1; a--)
+          for (int j = -n.olo; j < g.To + n.ohi; j++)
+            for (int e = -n.xl; e < V + n.xr; e++)
+              o << reg((int)ni, a, j, e) << " = " << reg((int)ni, a - 1, j, e) << ";\n";
+      }
+      step(u, safe);
+      o << "}\n}\n";
+    }
+    o << "}\n";
+  };
+  o << "if (!xb) {\n";
+  loop(false);
+  o << "} else {\n";
+  loop(true);
+  o << "}\n";
+  return o.str();
+}
+
+}  // namespace
+
+std::string emit_vol(const Pipeline &p, const VolGeom &g, const CodegenKey &key, const std::string &kname) {
+  if (!g.ok) fail(WT_EINVAL, "internal: not a 3-D group: " + g.why);
+  Emit e(p, g, key);
+  const std::string body = e.run();
+  std::ostringstream o;
+  o << kDeviceSource;
+  o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ") " << kname
+    << "(const __grid_constant__ WtArgs a) {\n";
+  o << body;
+  o << "}\n";
+  return o.str();
+}
+
+}  // namespace wt

@@ -46,6 +46,8 @@ struct Edge {
   int mode = 0;      // wt_tapmode (one mode per edge; checked)
   int dxmin = 0, dxmax = 0, dymin = 0, dymax = 0;
   std::vector<int> chans;  // distinct channel specs used (-1 or fixed)
+  bool zrel = false;       // some tap is a plane-offset (3-D) tap
+  int dzmin = 0, dzmax = 0;
 };
 
 struct Stage {
@@ -55,6 +57,7 @@ struct Stage {
   // derived
   int level = 0;
   std::vector<Edge> edges;  // one per input slot that is tapped
+  bool has_z = false;       // a plane-offset (WT_OP_TAPZ) tap in its program
 };
 
 struct GroupParams {
@@ -71,6 +74,8 @@ struct GroupParams {
   int smem16 = 0;      // shared-memory windows in the 16-bit storage type
   int otptb = 0;       // one overlapped tile per thread block (the baseline
                        // tiling the paper compares against)
+  int tile_o = 0;      // 3-D groups: planes (rows when streaming planes) per tile
+  int zstream = 0;     // 3-D groups: stream along planes instead of rows
 };
 
 struct Schedule {
@@ -230,6 +235,7 @@ struct Pipeline {
   std::shared_ptr<Workspace> ws;
   std::shared_ptr<BatchCache> batch;
   uint64_t hash = 0;
+  bool has_z = false;  // some stage has a plane-offset (3-D) tap
   // Sec. 6 preprocessing results (wt_preprocess): per stage, ns per
   // iteration of its body alone and registers; empty until measured
   std::vector<double> pre_ns;
@@ -275,6 +281,10 @@ struct CodegenKey {
   bool down = false;
   // reduction chain across levels (chain.cpp)
   bool chain = false;
+  // 3-D group (vol.cpp): split (streamed) axis 0 = rows, 1 = planes; vol_to
+  // points of the other non-x axis per warp tile; tby streamed points
+  bool vol = false;
+  int vol_split = 0, vol_to = 0;
   std::string str() const;
 };
 
@@ -353,5 +363,43 @@ struct PlainSrc {
 };
 std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid);
 extern const char *kDeviceSource;  // device_src.cpp
+
+// vol.cpp: a fused group over a volume (App. A, generalised hybrid
+// tiling).  A D x H x W volume is an image of D planes.  Warp tiles stream
+// along the split axis s (rows, or planes), lanes cover x (V points each),
+// and the third axis o is a register tile of vol_to points plus halos: each
+// node keeps, per o point of its range, a window of its last `window`
+// streamed rows, V + xl + xr values per lane.  Producer reads along o are
+// same-thread register reads; along x, neighbour values were exchanged by
+// shuffles when the row was stored; along s, older window slots.
+struct VolNode {
+  int id = 0;            // stage id, or -(j+1) for a pipeline input
+  bool source = false;   // read from memory (outside the group)
+  int lead = 0;          // rows ahead of the output row
+  int window = 1;        // streamed rows kept
+  int olo = 0, ohi = 0;  // o points below/above the tile's range
+  int xl = 0, xr = 0;    // neighbour values per lane stored left/right
+  int need_lo = 0;       // first needed row relative to the tile (<= 0)
+  int src_index = -1, dst_index = -1;
+  int planes = 1;        // planes of the image (sources: 1 or D)
+  bool rotate = true;    // slots rotate by unrolling (window divides U)
+};
+struct VolGeom {
+  bool ok = false;
+  std::string why;
+  int split = 0, To = 4, Ts = 32, V = 2;
+  int D = 1, level = 0;
+  std::vector<VolNode> nodes;  // sources first, then the group's stages
+  std::vector<int> liveouts;   // stage ids
+  int hxl = 0, hxlp = 0, hxr = 0, ow = 0;  // x halo, V-rounded left halo, outputs
+  int xml = 0, xmr = 0;        // source columns read left/right of a lane's V
+  int pro = 0;                 // prologue steps
+  int U = 1;                   // unrolled steps per loop iteration
+  int regs = 0;                // window registers per thread
+  int node_of(int id) const;
+};
+// Geometry of a 3-D group, or ok = false with the reason.
+VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V);
+std::string emit_vol(const Pipeline &p, const VolGeom &g, const CodegenKey &key, const std::string &kname);
 
 }  // namespace wt

@@ -24,6 +24,7 @@ struct Launch {
   GroupGeom geom;
   FusedLayout layout;
   CodegenKey key;
+  VolGeom vol;  // 3-D group (key.vol)
   std::string kname;
   std::vector<int> src, src_chan, dst;
   int n_ring = 0;  // staged (TMA) sources: src[0, n_ring); gather sources after

@@ -20,8 +20,10 @@ WT_F32, WT_F16, WT_BF16 = 0, 1, 2
 WT_EXEC_FUSED, WT_EXEC_PLAIN = 0, 1
 WT_MODEL_ANALYTIC, WT_MODEL_LEARNED = 0, 1
 WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT, WT_FLAG_PLAIN, WT_FLAG_OTPTB, WT_FLAG_SMEM16 = 1, 2, 4, 8, 16
+WT_FLAG_ZSTREAM = 32
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
-           "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14}
+           "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14,
+           "tapz": 15}
 TAPMODES = {"same": 0, "down2": 1, "up2": 2, "down4": 3, "up4": 4, "down8": 5, "up8": 6}
 DTYPES = {"f32": WT_F32, "f16": WT_F16, "bf16": WT_BF16}
 STATUS = {0: "WT_OK", -1: "WT_EINVAL", -2: "WT_ENOMEM", -3: "WT_ECUDA", -4: "WT_EUNSUPPORTED",
@@ -49,7 +51,8 @@ class wt_image(ctypes.Structure):
 class wt_group_params(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("frac_reg", ctypes.c_float), ("vec", ctypes.c_int32), ("max_regs", ctypes.c_int32),
-                ("chunk_rows", ctypes.c_int32), ("n_buffers", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("chunk_rows", ctypes.c_int32), ("n_buffers", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("tile_o", ctypes.c_int32)]
 
 
 class wt_gpu_config(ctypes.Structure):
@@ -186,6 +189,8 @@ def stage_array(pipe: dict):
                     o.chan = int(t[4])
                 if len(t) > 5:
                     o.mode = TAPMODES[t[5]]
+            elif t[0] == "tapz":
+                o.slot, o.dx, o.dy, o.chan = int(t[1]), int(t[2]), int(t[3]), int(t[4])
         keep += [ins, ops]
         st[i].channels = int(S["channels"])
         st[i].n_inputs = len(S["inputs"])

@@ -37,7 +37,7 @@ def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mod
         emu.run(p, i, ins, outs, max_blocks, ws)
     per_stage = any((q or {}).get("flags", 0) & wt.WT_FLAG_PLAIN for q in (params or []))
     if exec_mode == wt.WT_EXEC_FUSED and d["n_launches"] == 1 and not per_stage:
-        assert d["fused"] or d["name"].startswith("wt_chain_")
+        assert d["fused"] or d["name"].startswith(("wt_chain_", "wt_vol_"))
     for o in outs:
         assert o.padding_intact(), "kernel wrote outside the image"
     name = {wt.WT_F32: "f32", wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]

@@ -146,3 +146,16 @@ def test_plane_tap_rejects_other_depths_and_modes():
     b.output(b.stage("s", P.refz(inp, 0, 0, 1), 4))
     with pytest.raises(Exception):
         run(b.build(), [vol(9, 3, 4, 4)])
+
+
+def test_point_evaluation_matches_full_volumes():
+    """The region-restricted evaluator (used for sampled parity of full-size
+    volumes) against the full evaluation."""
+    D = 9
+    v = vol(10, D, 20, 30)
+    rng = np.random.default_rng(2)
+    xs, ys, zs = rng.integers(0, 30, 300), rng.integers(0, 20, 300), rng.integers(0, D, 300)
+    for spec in (P.unsharp3d(depth=D), P.heat3d(2, depth=D)):
+        full = run(spec, [v])[0]
+        pts = O.evaluate_points(spec["stages"], [v], spec["outputs"][0], xs, ys, zs)
+        assert np.abs(pts - full[zs, ys, xs]).max() < 1e-15
