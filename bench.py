@@ -50,7 +50,31 @@ WORKLOADS = {
     "blend": ("blend", 8192, 8192, "bf16", I.SEED_BASE + 5),
     # bilateral filter through a grid of 8x8-pixel cells and 8 intensity bins
     "bilateral": ("bilateral", 4096, 4096, "f32", I.SEED_BASE + 6),
+    # 3-D groups: 512x512x256 FP32 volumes (a pixel is a voxel)
+    "unsharp3d": ("unsharp3d", 512, 512, "f32", I.SEED_BASE + 8),
+    "heat3d": ("heat3d", 512, 512, "f32", I.SEED_BASE + 9),
 }
+VOLUME_DEPTH = 256
+# 3-D group parameters: the fastest of the 3-D study's sweep on one GB300
+VOLUME_PARAMS = {"unsharp3d": dict(tile_h=32, tile_o=4, vec=2, warps_per_block=4, flags=32),
+                 "heat3d": dict(tile_h=32, tile_o=4, vec=2, warps_per_block=4, flags=32)}
+
+
+def spec_for(name):
+    """The workload's stage DAG (volumes: VOLUME_DEPTH planes; the heat
+    workload is two fused diffusion steps)."""
+    if name == "unsharp3d":
+        return P.unsharp3d(depth=VOLUME_DEPTH)
+    if name == "heat3d":
+        return P.heat3d(2, depth=VOLUME_DEPTH)
+    return P.by_name(name)
+
+
+def spec_for_depth(name, depth):
+    """A volume workload's DAG at another depth (bounded CPU samples)."""
+    return P.unsharp3d(depth=depth) if name == "unsharp3d" else P.heat3d(2, depth=depth)
+
+
 BATCH_IMAGES = 512
 # pyramid levels a tap mode moves (down: the producer is finer)
 LEVEL_DELTA = {"same": 0, "down2": 1, "up2": -1, "down4": 2, "up4": -2, "down8": 3, "up8": -3}
@@ -180,7 +204,7 @@ def cpu_oracle_rate(spec, img, budget_s):
         dt = time.perf_counter() - t0
         if dt >= budget_s:
             break
-    px = n * img.shape[-1] * img.shape[-2]
+    px = n * img.size  # pixels of every plane of a volume (voxels)
     return px / dt / 1e6, O.num_threads(), n, dt
 
 
@@ -213,7 +237,7 @@ def run_reference(args, rank):
     if rank != 0:
         return
     name, W, H, dt, seed = WORKLOADS[args.workload]
-    spec = P.by_name(name)
+    spec = spec_for(name)
     if name == "blend":
         # bounded sample: one 1024x1024x3 blend per step
         from oracle import oracle as O
@@ -245,18 +269,22 @@ def run_reference(args, rank):
     elif name == "bilateral":
         imgs = [I.round_to(I.uniform_image(seed, W, H)[0][:1024, :1024], dt)]
         sample = "one 1024x1024 crop of the %dx%d image per step" % (W, H)
+    elif name in ("unsharp3d", "heat3d"):
+        imgs = [I.round_to(I.uniform_image(seed, W, H, VOLUME_DEPTH)[:32], dt)]
+        sample = "the first 32 planes of the %dx%dx%d volume per step" % (W, H, VOLUME_DEPTH)
     else:
         imgs = [I.round_to(I.uniform_image(seed, W, H)[0], dt)]
         sample = "one full %dx%d image per step" % (W, H)
     for k in range(args.warmup):
-        cpu_oracle_rate(spec, imgs[k % len(imgs)], 0.0)
+        img = imgs[k % len(imgs)]
+        cpu_oracle_rate(spec if img.ndim == 2 else spec_for_depth(name, img.shape[0]), img, 0.0)
     px = 0
     t0 = time.perf_counter()
     cores = 1
     for k in range(args.steps):
         img = imgs[(args.warmup + k) % len(imgs)]
-        _, cores, _, _ = cpu_oracle_rate(spec, img, 0.0)
-        px += img.shape[-1] * img.shape[-2]
+        _, cores, _, _ = cpu_oracle_rate(spec if img.ndim == 2 else spec_for_depth(name, img.shape[0]), img, 0.0)
+        px += img.size
     total = time.perf_counter() - t0
     value = px / total / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixels/s",
@@ -264,7 +292,7 @@ def run_reference(args, rank):
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H,
-                       "channels": 1, "storage": dt},
+                       "channels": VOLUME_DEPTH if name in ("unsharp3d", "heat3d") else 1, "storage": dt},
             "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -325,18 +353,23 @@ def dominant_launch(pipe, ins, outs, spec, W, H, esz, sp):
 class Single:
     """One image per step, rotating over buffer sets larger than 3x L2."""
 
+    planes = 1
+
     def __init__(self, wt, torch, spec, W, H, dtype, seed, local):
         self.wt, self.torch = wt, torch
         self.W, self.H, self.dtype = W, H, dtype
         self.esz = 4 if dtype == wt.WT_F32 else 2
-        self.img = I.uniform_image(seed, W, H)[0]
-        set_bytes = 2 * W * H * self.esz
+        C = self.planes
+        self.img = I.uniform_image(seed, W, H, C)
+        if C == 1:
+            self.img = self.img[0]
+        set_bytes = 2 * W * H * C * self.esz
         l2 = torch.cuda.get_device_properties(local).L2_cache_size
         self.nsets = max(3, -(-3 * l2 // set_bytes))
-        self.ins = [wt.DeviceImage(1, H, W, dtype).upload(self.img) for _ in range(self.nsets)]
-        self.outs = [wt.DeviceImage(1, H, W, dtype) for _ in range(self.nsets)]
-        self.px = W * H
-        self.alg_bytes = 2 * W * H * self.esz
+        self.ins = [wt.DeviceImage(C, H, W, dtype).upload(self.img) for _ in range(self.nsets)]
+        self.outs = [wt.DeviceImage(C, H, W, dtype) for _ in range(self.nsets)]
+        self.px = W * H * C
+        self.alg_bytes = 2 * W * H * C * self.esz
         self.l2_note = "rotating %d input/output sets (%.0f MB) > 3x L2" % (self.nsets, self.nsets * set_bytes / 1e6)
 
     def run(self, pipe, i, sp):
@@ -355,9 +388,9 @@ class Single:
 
     def e2e(self, pipe, sp, warmup, steps):
         wt, torch = self.wt, self.torch
-        hin = wt.DeviceImage(1, self.H, self.W, self.dtype, device="cpu", pin_host=True)
+        hin = wt.DeviceImage(self.planes, self.H, self.W, self.dtype, device="cpu", pin_host=True)
         hin.view().copy_(self.ins[0].view().cpu())
-        hout = wt.DeviceImage(1, self.H, self.W, self.dtype, device="cpu", pin_host=True)
+        hout = wt.DeviceImage(self.planes, self.H, self.W, self.dtype, device="cpu", pin_host=True)
         for _ in range(warmup):
             pipe.run_host([hin.image()], [hout.image()], sp)
         torch.cuda.synchronize()
@@ -368,6 +401,23 @@ class Single:
 
     def cpu_sample(self, dts):
         return I.round_to(self.img, dts)
+
+
+class Volume(Single):
+    """A 512x512x256 volume per step (3-D group, App. A), rotating over
+    buffer sets like Single; the CPU oracle runs on its first 32 planes."""
+
+    planes = VOLUME_DEPTH
+
+    def __init__(self, wt, torch, spec, W, H, dtype, seed, local, name):
+        self.name = name
+        super().__init__(wt, torch, spec, W, H, dtype, seed, local)
+
+    def schedule(self, fused, plain):
+        fused.schedule(params=[VOLUME_PARAMS[self.name]])
+
+    def cpu_sample(self, dts):
+        return I.round_to(self.img[:32], dts)
 
 
 class Grid(Single):
@@ -528,7 +578,7 @@ def run_ours(args, rank, world, local):
         # a smaller square case of the same workload (profiling captures)
         W = H = args.size
     dtype = wt.DTYPES[dts]
-    spec = P.by_name(name)
+    spec = spec_for(name)
     batched = args.workload == "harris_batch"
     if batched:
         work = Batch(wt, torch, spec, dtype, seed + 7919 * rank)
@@ -536,6 +586,8 @@ def run_ours(args, rank, world, local):
         work = Blend(wt, torch, spec, W, H, dtype, seed + 7919 * rank)
     elif name == "bilateral":
         work = Grid(wt, torch, spec, W, H, dtype, seed + rank, local)
+    elif name in ("unsharp3d", "heat3d"):
+        work = Volume(wt, torch, spec, W, H, dtype, seed + rank, local, name)
     else:
         work = Single(wt, torch, spec, W, H, dtype, seed + rank, local)
     stream = torch.cuda.current_stream()
@@ -646,11 +698,15 @@ def run_ours(args, rank, world, local):
                 traffic = rec["dram_bytes_per_launch"]
         except Exception:
             traffic = None
+    # stage-program operations per pixel (per voxel: a volume's planes are
+    # its pixels, so the channel count is not a multiplier)
+    opx = ops_per_pixel(spec) / getattr(work, "planes", 1)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_f / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dts, "data": "synthetic",
-        "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H, "channels": 1,
+        "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H,
+                   "channels": getattr(work, "planes", 1),
                    "storage": dts, "stages": len(spec["stages"]), "pixels_per_step": work.px,
                    "l2": work.l2_note, "schedule": fused.schedule_get(),
                    "tuning": tuning},
@@ -659,10 +715,10 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms, "whole_run": run_roof,
                      # the same run against the FP32 ALU: stage-program operations per pixel
                      # x pixels/s over the derived lane-op peak
-                     "alu": {"ops_per_px": ops_per_pixel(spec),
-                             "achieved_tops": ops_per_pixel(spec) * value / 1e6 / world,
+                     "alu": {"ops_per_px": opx,
+                             "achieved_tops": opx * value / 1e6 / world,
                              "peak_tops": FP32_LANE_OPS / 1e12,
-                             "frac": ops_per_pixel(spec) * value * 1e6 / world / FP32_LANE_OPS}},
+                             "frac": opx * value * 1e6 / world / FP32_LANE_OPS}},
         "unfused": unfused,
         "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches,
@@ -675,8 +731,10 @@ def run_ours(args, rank, world, local):
             r, cores, n, dt, sample = cpu_blend_rate(dts, args.cpu_seconds)
         else:
             img = work.cpu_sample(dts)
-            r, cores, n, dt = cpu_oracle_rate(spec, img, args.cpu_seconds)
-            sample = "%d images of %dx%d, %.1f s" % (n, img.shape[-1], img.shape[-2], dt)
+            cspec = spec if img.ndim == 2 else spec_for_depth(name, img.shape[0])
+            r, cores, n, dt = cpu_oracle_rate(cspec, img, args.cpu_seconds)
+            sample = "%d images of %dx%d%s, %.1f s" % (n, img.shape[-1], img.shape[-2],
+                                                      "" if img.ndim == 2 else "x%d" % img.shape[0], dt)
         line["cpu_baseline"] = {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)

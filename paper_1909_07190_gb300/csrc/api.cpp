@@ -536,9 +536,13 @@ int32_t wt_launches_per_run(const wt_pipeline *p) {
     auto groups = wt::schedule_groups(*p);
     for (size_t gi = 0; gi < groups.size(); gi++) {
       const wt::GroupParams gp = wt::group_params(*p, (int)gi);
+      bool zgroup = false;
+      for (int s : groups[gi]) zgroup = zgroup || p->stages[s].has_z;
       bool fused = p->sched.exec == WT_EXEC_FUSED && !gp.plain &&
-                   ((!gp.otptb && wt::chain_form(*p, groups[gi]).ok) ||
-                    wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable);
+                   (zgroup ? wt::vol_analyze(*p, groups[gi], gp.zstream, gp.tile_o > 0 ? gp.tile_o : 4,
+                                             std::max(1, gp.tile_h), gp.vec > 0 ? gp.vec : 2).ok
+                           : ((!gp.otptb && wt::chain_form(*p, groups[gi]).ok) ||
+                              wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable));
       if (fused) {
         n++;
       } else {
