@@ -165,7 +165,7 @@ typedef struct {
  * this flag it is z (planes) and tile_o counts rows.  frac_reg, chunk_rows,
  * n_buffers and the other flags are ignored for such groups; a group the
  * 3-D kernel cannot take (other levels, parity or channel ops, fixed-
- * channel taps, windows above 192 registers) runs per stage.              */
+ * channel taps, windows above 224 registers) runs per stage.              */
 #define WT_FLAG_ZSTREAM 32
 
 typedef enum {

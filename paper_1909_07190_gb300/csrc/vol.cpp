@@ -26,6 +26,7 @@
 // column 0 or W-1 by shuffle (border tiles only).
 #include <algorithm>
 #include <numeric>
+#include <map>
 #include <set>
 #include <sstream>
 #include <tuple>
@@ -33,6 +34,9 @@
 #include "wt_internal.hpp"
 
 namespace wt {
+
+// Rows a source is loaded ahead of its first use.
+constexpr int kVolPrefetch = 2;
 
 int VolGeom::node_of(int id) const {
   for (size_t i = 0; i < nodes.size(); i++)
@@ -180,8 +184,10 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
     n.ohi = ohi[i];
     g.hxl = std::max(g.hxl, nl[i]);
     g.hxr = std::max(g.hxr, nr[i]);
-    // sources are read at their consumers' rows: no prologue of their own
-    if (!n.source) g.pro = std::max(g.pro, n.lead - n.need_lo);
+    // sources are loaded kVolPrefetch rows before their first use, so that
+    // a load's latency overlaps the steps in between
+    if (n.source) n.lead += kVolPrefetch;
+    g.pro = std::max(g.pro, n.lead - n.need_lo);
   }
   // windows and stored neighbour values of the group's stages
   for (int k = 0; k < (int)stages.size(); k++) {
@@ -190,12 +196,14 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
       if (t.node < 0) continue;
       VolNode &pn = g.nodes[t.node];
       const VolNode &cn = g.nodes[ci];
+      pn.window = std::max(pn.window, pn.lead - cn.lead - t.ds + 1);
       if (pn.source) {
+        // sources keep their own V values per row; neighbours by shuffle
+        // at the tap (their loads are clamped: no copies at the borders)
         g.xml = std::max(g.xml, -t.dx);
         g.xmr = std::max(g.xmr, t.dx);
         continue;
       }
-      pn.window = std::max(pn.window, pn.lead - cn.lead - t.ds + 1);
       // a row past the end copies the previous one: keep it
       if (t.ds > 0) pn.window = std::max(pn.window, 2);
       pn.xl = std::max(pn.xl, -t.dx);
@@ -203,28 +211,26 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
     }
   }
   for (VolNode &n : g.nodes)
-    if (!n.source && (n.xl > 32 * V - 1 || n.xr > 32 * V - 1)) return no("x taps wider than a warp tile");
+    if (n.xl > 32 * V - 1 || n.xr > 32 * V - 1) return no("x taps wider than a warp tile");
+  if (g.xml > 32 * V - 1 || g.xmr > 32 * V - 1) return no("x taps wider than a warp tile");
   g.hxlp = (g.hxl + V - 1) / V * V;
   g.ow = (32 * V - g.hxlp - g.hxr) / V * V;
   if (g.ow < V) return no("x halo leaves no output columns");
   // unroll: the least common multiple of the windows when small, else the
   // largest window (nodes whose window does not divide it shift)
   int U = 1;
-  for (const VolNode &n : g.nodes)
-    if (!n.source) U = std::lcm(U, n.window);
+  for (const VolNode &n : g.nodes) U = std::lcm(U, n.window);
   if (U > 8) {
     U = 1;
-    for (const VolNode &n : g.nodes)
-      if (!n.source) U = std::max(U, n.window);
+    for (const VolNode &n : g.nodes) U = std::max(U, n.window);
   }
   g.U = U;
   g.regs = 0;
   for (VolNode &n : g.nodes) {
-    if (n.source) continue;
     n.rotate = U % n.window == 0;
     g.regs += n.window * (g.To + n.olo + n.ohi) * (V + n.xl + n.xr);
   }
-  if (g.regs > 192) return no("3-D group windows need " + std::to_string(g.regs) +
+  if (g.regs > 224) return no("3-D group windows need " + std::to_string(g.regs) +
                               " registers per thread; lower tile_o or vec");
   g.ok = true;
   return g;
@@ -271,26 +277,19 @@ struct Emit {
            " * " + S + ".pitch)";
   }
 
-  // Source rows a stage reads: one per (source, ds, dO), with the tap
-  // columns it spans, in order of first use.
-  struct SrcRow {
-    int si, ds, dO, lo, hi;
-  };
-  std::vector<SrcRow> src_rows(int sid) const {
-    std::vector<SrcRow> rows;
-    for (const VTap &t : stage_taps(p, g, sid)) {
-      if (t.node < 0 || !g.nodes[t.node].source) continue;
-      bool found = false;
-      for (SrcRow &r : rows)
-        if (r.si == t.node && r.ds == t.ds && r.dO == t.dO) {
-          r.lo = std::min(r.lo, t.dx);
-          r.hi = std::max(r.hi, t.dx);
-          found = true;
-        }
-      if (!found) rows.push_back({t.node, t.ds, t.dO, t.dx, t.dx});
+  // A source value at x entry e (any integer) of its window register: own
+  // entries directly, others from the lane that holds them.
+  std::string src_val(int si, int sl, int j, int e) const {
+    const int V = g.V;
+    if (e >= 0 && e < V) return reg(si, sl, j, e);
+    if (e < 0) {
+      const int dl = (-e + V - 1) / V;
+      return "__shfl_up_sync(WT_FULL, " + reg(si, sl, j, e + dl * V) + ", " + std::to_string(dl) + ")";
     }
-    return rows;
+    const int dl = e / V;
+    return "__shfl_down_sync(WT_FULL, " + reg(si, sl, j, e - dl * V) + ", " + std::to_string(dl) + ")";
   }
+  void load_source(int si, int u, bool safe);
   void program(int sid, int ni, int u, bool safe);
   void store_row(int ni, int u, bool safe);
   void liveout(int ni, int u);
@@ -299,31 +298,29 @@ struct Emit {
 };
 
 // Evaluates stage `sid` (node ni) for every o point of its range at the
-// node's row of step u, into the age-0 slot; sources are loaded per tap row.
+// node's row of step u, into the age-0 slot.
 void Emit::program(int sid, int ni, int u, bool safe) {
   const Stage &S = p.stages[sid];
   const VolNode &n = g.nodes[ni];
   const std::vector<VTap> taps = stage_taps(p, g, sid);
   const int V = g.V;
   const int sl0 = slot(n, u, 0);
-  const std::vector<SrcRow> rows = src_rows(sid);
   for (int j = -n.olo; j < g.To + n.ohi; j++) {
     o << "{\n";
-    // source values: column xl0 + c for c in [lo, V - 1 + hi]
-    for (size_t ri = 0; ri < rows.size(); ri++) {
-      const SrcRow &r = rows[ri];
-      const VolNode &sn = g.nodes[r.si];
-      const int dt = key.src_dtypes.at(sn.src_index);
-      const int esz = elem_bytes(dt);
-      o << "{ const unsigned char *rp_ = " << src_row(r.si, "rn + (" + std::to_string(r.ds) + ")", j + r.dO)
-        << ";\n";
-      for (int c = r.lo; c < V + r.hi; c++) {
-        const std::string col = "(xl0 + (" + std::to_string(c) + "))";
-        o << "S" << ri << "_" << (c - r.lo) << " = wt_ld1_" << dtype_name(dt) << "(rp_ + (wt_i64)"
-          << (safe ? "wt_clampi(" + col + ", 0, W - 1)" : col) << " * " << esz << ");\n";
+    // shuffled source neighbours, once per o point
+    std::map<std::tuple<int, int, int, int>, std::string> nb;
+    for (int e = 0; e < V; e++)
+      for (const VTap &t : taps) {
+        if (t.node < 0 || !g.nodes[t.node].source) continue;
+        const int ee = e + t.dx;
+        if (ee >= 0 && ee < V) continue;
+        const VolNode &pn = g.nodes[t.node];
+        auto key4 = std::make_tuple(t.node, slot(pn, u, pn.lead - n.lead - t.ds), j + t.dO, ee);
+        if (nb.count(key4)) continue;
+        const std::string name = "nb" + std::to_string(nb.size()) + "_";
+        o << "const float " << name << " = " << src_val(t.node, std::get<1>(key4), std::get<2>(key4), ee) << ";\n";
+        nb[key4] = name;
       }
-      o << "}\n";
-    }
     for (int e = 0; e < V; e++) {
       std::vector<std::string> st;
       for (size_t k = 0; k < S.ops.size(); k++) {
@@ -333,15 +330,12 @@ void Emit::program(int sid, int ni, int u, bool safe) {
           case WT_OP_TAP: case WT_OP_TAPZ: {
             const VTap &t = taps[k];
             const VolNode &pn = g.nodes[t.node];
-            if (pn.source) {
-              int ri = 0;
-              for (size_t q = 0; q < rows.size(); q++)
-                if (rows[q].si == t.node && rows[q].ds == t.ds && rows[q].dO == t.dO) ri = (int)q;
-              st.push_back("S" + std::to_string(ri) + "_" + std::to_string(e + t.dx - rows[ri].lo));
-            } else {
-              const int age = pn.lead - n.lead - t.ds;
-              st.push_back(reg(t.node, slot(pn, u, age), j + t.dO, e + t.dx));
-            }
+            const int age = pn.lead - n.lead - t.ds;
+            const int ee = e + t.dx;
+            if (pn.source && (ee < 0 || ee >= V))
+              st.push_back(nb.at(std::make_tuple(t.node, slot(pn, u, age), j + t.dO, ee)));
+            else
+              st.push_back(reg(t.node, slot(pn, u, age), j + t.dO, ee));
           } break;
           case WT_OP_NEG: st.back() = "(-" + st.back() + ")"; break;
           case WT_OP_ABS: st.back() = "fabsf(" + st.back() + ")"; break;
@@ -395,6 +389,37 @@ void Emit::program(int sid, int ni, int u, bool safe) {
   }
 }
 
+// Loads source si's row of step u (clamped row and o point: a source's
+// value outside the volume is the clamped point's) into its age-0 slot:
+// the lane's V columns, one vector load in interior tiles (the first column
+// is a multiple of V and rows are 16-byte aligned), clamped scalar loads
+// in border tiles.
+void Emit::load_source(int si, int u, bool safe) {
+  const VolNode &n = g.nodes[si];
+  const int V = g.V;
+  const int sl0 = slot(n, u, 0);
+  const int dt = key.src_dtypes.at(n.src_index);
+  const int esz = elem_bytes(dt);
+  const std::string dn = dtype_name(dt);
+  for (int j = -n.olo; j < g.To + n.ohi; j++) {
+    o << "{ const unsigned char *rp_ = " << src_row(si, "rn", j) << ";\n";
+    if (!safe && V == 4) {
+      o << "wt_ld4_" << dn << "(rp_ + (wt_i64)xl0 * " << esz << ", " << reg(si, sl0, j, 0) << ", "
+        << reg(si, sl0, j, 1) << ", " << reg(si, sl0, j, 2) << ", " << reg(si, sl0, j, 3) << ");\n";
+    } else if (!safe && V == 2) {
+      o << "wt_ld2_" << dn << "(rp_ + (wt_i64)xl0 * " << esz << ", " << reg(si, sl0, j, 0) << ", "
+        << reg(si, sl0, j, 1) << ");\n";
+    } else {
+      for (int e = 0; e < V; e++) {
+        const std::string col = "(xl0 + " + std::to_string(e) + ")";
+        o << reg(si, sl0, j, e) << " = wt_ld1_" << dn << "(rp_ + (wt_i64)"
+          << (safe ? "wt_clampi(" + col + ", 0, W - 1)" : col) << " * " << esz << ");\n";
+      }
+    }
+    o << "}\n";
+  }
+}
+
 // o points outside [0, NO): copies of the nearest in-range point (all
 // stored entries), after every o point of the row is computed.
 void Emit::store_row(int ni, int u, bool safe) {
@@ -443,7 +468,13 @@ void Emit::step(int u, bool safe) {
   const int V = g.V;
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
     const VolNode &n = g.nodes[ni];
-    if (n.source) continue;
+    if (n.source) {
+      o << "{ // source " << n.id << "\n";
+      o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
+      load_source((int)ni, u, safe);
+      o << "}\n";
+      continue;
+    }
     o << "{ // stage " << n.id << "\n";
     o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
     o << "if (rn >= 0 && rn < NS) {\n";
@@ -502,7 +533,6 @@ std::string Emit::run() {
   // window registers
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
     const VolNode &n = g.nodes[ni];
-    if (n.source) continue;
     for (int sl = 0; sl < n.window; sl++)
       for (int j = -n.olo; j < g.To + n.ohi; j++) {
         o << "float";
@@ -514,17 +544,6 @@ std::string Emit::run() {
   o << "float";
   for (int e = 0; e < V; e++) o << (e ? ", " : " ") << "v" << e;
   o << ";\n";
-  std::vector<int> swidth;
-  for (const VolNode &n : g.nodes) {
-    if (n.source) continue;
-    const std::vector<SrcRow> rows = src_rows(n.id);
-    for (size_t ri = 0; ri < rows.size(); ri++) {
-      if (swidth.size() <= ri) swidth.push_back(0);
-      swidth[ri] = std::max(swidth[ri], V + rows[ri].hi - rows[ri].lo);
-    }
-  }
-  for (size_t ri = 0; ri < swidth.size(); ri++)
-    for (int c = 0; c < swidth[ri]; c++) o << "float S" << ri << "_" << c << ";\n";
   o << "const int nsteps = min(" << g.Ts << ", NS - s0) + " << g.pro << ";\n";
   auto loop = [&](bool safe) {
     o << "#pragma unroll 1\n";
@@ -534,7 +553,7 @@ std::string Emit::run() {
       // shift the windows that do not rotate by renaming
       for (size_t ni = 0; ni < g.nodes.size(); ni++) {
         const VolNode &n = g.nodes[ni];
-        if (n.source || n.rotate || n.window < 2) continue;
+        if (n.rotate || n.window < 2) continue;
         for (int a = n.window - 1; a >= 1; a--)
           for (int j = -n.olo; j < g.To + n.ohi; j++)
             for (int e = -n.xl; e < V + n.xr; e++)
