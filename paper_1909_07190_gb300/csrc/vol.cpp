@@ -197,22 +197,19 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
       VolNode &pn = g.nodes[t.node];
       const VolNode &cn = g.nodes[ci];
       pn.window = std::max(pn.window, pn.lead - cn.lead - t.ds + 1);
+      // every node keeps its own V values per row; x neighbours come by
+      // shuffle at the tap (fewer registers, more warps per SM)
+      if (-t.dx > 32 * V - 1 || t.dx > 32 * V - 1) return no("x taps wider than a warp tile");
       if (pn.source) {
-        // sources keep their own V values per row; neighbours by shuffle
-        // at the tap (their loads are clamped: no copies at the borders)
+        // loads are clamped: no copies at the borders
         g.xml = std::max(g.xml, -t.dx);
         g.xmr = std::max(g.xmr, t.dx);
         continue;
       }
       // a row past the end copies the previous one: keep it
       if (t.ds > 0) pn.window = std::max(pn.window, 2);
-      pn.xl = std::max(pn.xl, -t.dx);
-      pn.xr = std::max(pn.xr, t.dx);
     }
   }
-  for (VolNode &n : g.nodes)
-    if (n.xl > 32 * V - 1 || n.xr > 32 * V - 1) return no("x taps wider than a warp tile");
-  if (g.xml > 32 * V - 1 || g.xmr > 32 * V - 1) return no("x taps wider than a warp tile");
   g.hxlp = (g.hxl + V - 1) / V * V;
   g.ow = (32 * V - g.hxlp - g.hxr) / V * V;
   if (g.ow < V) return no("x halo leaves no output columns");
@@ -277,7 +274,7 @@ struct Emit {
            " * " + S + ".pitch)";
   }
 
-  // A source value at x entry e (any integer) of its window register: own
+  // A node's value at x entry e (any integer) of its window register: own
   // entries directly, others from the lane that holds them.
   std::string src_val(int si, int sl, int j, int e) const {
     const int V = g.V;
@@ -307,11 +304,11 @@ void Emit::program(int sid, int ni, int u, bool safe) {
   const int sl0 = slot(n, u, 0);
   for (int j = -n.olo; j < g.To + n.ohi; j++) {
     o << "{\n";
-    // shuffled source neighbours, once per o point
+    // producers' x neighbours by shuffle, once per o point
     std::map<std::tuple<int, int, int, int>, std::string> nb;
     for (int e = 0; e < V; e++)
       for (const VTap &t : taps) {
-        if (t.node < 0 || !g.nodes[t.node].source) continue;
+        if (t.node < 0) continue;
         const int ee = e + t.dx;
         if (ee >= 0 && ee < V) continue;
         const VolNode &pn = g.nodes[t.node];
@@ -332,7 +329,7 @@ void Emit::program(int sid, int ni, int u, bool safe) {
             const VolNode &pn = g.nodes[t.node];
             const int age = pn.lead - n.lead - t.ds;
             const int ee = e + t.dx;
-            if (pn.source && (ee < 0 || ee >= V))
+            if (ee < 0 || ee >= V)
               st.push_back(nb.at(std::make_tuple(t.node, slot(pn, u, age), j + t.dO, ee)));
             else
               st.push_back(reg(t.node, slot(pn, u, age), j + t.dO, ee));

@@ -13,7 +13,8 @@ Arms:
   plain  per-stage kernels, FP32 intermediates in HBM (the unfused path)
   fused  one 3-D group, swept in two rounds: split axis {rows, planes} x
          tile_o {1, 2, 4, 8} x vec {1, 2, 4} at tile_h 32 and 4 warps, then
-         tile_h {8, 16, 64, 128} x warps {2, 4, 8} around the best
+         tile_h {16, 64, 128} x warps {2, 4, 8} x register cap {none, 128,
+         168} around the best
 Time per run: CUDA events on the launching stream, mean over `reps` runs
 after 3 warm-up runs (inputs and outputs of 268 MB each exceed the L2).
 HBM fraction: (input + output bytes) / time / the measured copy bandwidth.
@@ -96,7 +97,8 @@ def study(name, reps, stream, flush, log):
 
     run_grid(grid1)
     best = min(rows, key=lambda r: r[0])[1]
-    grid2 = [dict(best, tile_h=t, warps_per_block=w) for t, w in itertools.product((8, 16, 64, 128), (2, 4, 8))]
+    grid2 = [dict(best, tile_h=t, warps_per_block=w, max_regs=r)
+             for t, w, r in itertools.product((16, 64, 128), (2, 4, 8), (0, 128, 168))]
     run_grid(grid2)
     torch.cuda.synchronize()
     ms, prm = min(rows, key=lambda r: r[0])
