@@ -255,24 +255,7 @@ struct Emit {
     return "w" + std::to_string(ni) + "_" + std::to_string(sl) + "_" + std::to_string(j + n.olo) + "_" +
            std::to_string(e + n.xl);
   }
-  std::string s_index(const std::string &r) const { return "wt_clampi(" + r + ", 0, NS - 1)"; }
   std::string o_index(const std::string &j) const { return "wt_clampi(o0 + (" + j + "), 0, NO - 1)"; }
-
-  // Address (unsigned char *) of row r, o point j of source si, column 0.
-  std::string src_row(int si, const std::string &r, int j) const {
-    const VolNode &n = g.nodes[si];
-    const std::string S = "a.src[" + std::to_string(n.src_index) + "]";
-    std::string zi, yi;
-    if (g.split == 0) {
-      zi = n.planes == 1 ? "0" : o_index(std::to_string(j));
-      yi = s_index(r);
-    } else {
-      zi = n.planes == 1 ? "0" : s_index(r);
-      yi = o_index(std::to_string(j));
-    }
-    return "((const unsigned char *)" + S + ".ptr + (wt_i64)" + zi + " * " + S + ".plane + (wt_i64)" + yi +
-           " * " + S + ".pitch)";
-  }
 
   // A node's value at x entry e (any integer) of its window register: own
   // entries directly, others from the lane that holds them.
@@ -289,7 +272,7 @@ struct Emit {
   void load_source(int si, int u, bool safe);
   void program(int sid, int ni, int u, bool safe);
   void store_row(int ni, int u, bool safe);
-  void liveout(int ni, int u);
+  void liveout(int ni, int u, bool safe);
   void step(int u, bool safe);
   std::string run();
 };
@@ -398,8 +381,14 @@ void Emit::load_source(int si, int u, bool safe) {
   const int dt = key.src_dtypes.at(n.src_index);
   const int esz = elem_bytes(dt);
   const std::string dn = dtype_name(dt);
+  const std::string S = "a.src[" + std::to_string(n.src_index) + "]";
+  // the row's base once per step; each o point's offset was computed once
+  // per tile
+  if (g.split == 0) o << "const unsigned char *rb_ = sb" << si << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".pitch;\n";
+  else if (n.planes == 1) o << "const unsigned char *rb_ = sb" << si << ";\n";
+  else o << "const unsigned char *rb_ = sb" << si << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".plane;\n";
   for (int j = -n.olo; j < g.To + n.ohi; j++) {
-    o << "{ const unsigned char *rp_ = " << src_row(si, "rn", j) << ";\n";
+    o << "{ const unsigned char *rp_ = rb_ + so" << si << "_" << j + n.olo << ";\n";
     if (!safe && V == 4) {
       o << "wt_ld4_" << dn << "(rp_ + (wt_i64)xl0 * " << esz << ", " << reg(si, sl0, j, 0) << ", "
         << reg(si, sl0, j, 1) << ", " << reg(si, sl0, j, 2) << ", " << reg(si, sl0, j, 3) << ");\n";
@@ -439,23 +428,29 @@ void Emit::store_row(int ni, int u, bool safe) {
   o << "}\n";
 }
 
-void Emit::liveout(int ni, int u) {
+void Emit::liveout(int ni, int u, bool safe) {
   const VolNode &n = g.nodes[ni];
   const int sl0 = slot(n, u, 0);
   const int V = g.V;
   const int dt = key.dst_dtypes.at(n.dst_index);
   const int esz = elem_bytes(dt);
   const std::string D = "a.dst[" + std::to_string(n.dst_index) + "]";
+  const std::string dn = dtype_name(dt);
   o << "if (rn >= s0 && rn < s0 + " << g.Ts << " && rn < NS && olane) {\n";
+  o << "unsigned char *db_ = db" << ni << " + (wt_i64)rn * " << D << (g.split == 0 ? ".pitch" : ".plane") << ";\n";
   for (int j = 0; j < g.To; j++) {
     o << "if (o0 + " << j << " < NO) {\n";
-    std::string zi = g.split == 0 ? "(o0 + " + std::to_string(j) + ")" : "rn";
-    std::string yi = g.split == 0 ? "rn" : "(o0 + " + std::to_string(j) + ")";
-    o << "unsigned char *dp_ = (unsigned char *)" << D << ".ptr + (wt_i64)" << zi << " * " << D
-      << ".plane + (wt_i64)" << yi << " * " << D << ".pitch + (wt_i64)xl0 * " << esz << ";\n";
-    for (int e = 0; e < V; e++)
-      o << "if (xl0 + " << e << " < W) wt_st1_" << dtype_name(dt) << "(dp_ + " << e * esz << ", "
-        << reg(ni, sl0, j, e) << ");\n";
+    o << "unsigned char *dp_ = db_ + do" << ni << "_" << j << ";\n";
+    if (!safe && V == 4 && dt == WT_F32) {
+      // interior tile: every column is inside the row, 16-byte aligned
+      o << "wt_st4_f32(dp_, " << reg(ni, sl0, j, 0) << ", " << reg(ni, sl0, j, 1) << ", " << reg(ni, sl0, j, 2) << ", "
+        << reg(ni, sl0, j, 3) << ");\n";
+    } else {
+      for (int e = 0; e < V; e++) {
+        if (safe) o << "if (xl0 + " << e << " < W) ";
+        o << "wt_st1_" << dn << "(dp_ + " << e * esz << ", " << reg(ni, sl0, j, e) << ");\n";
+      }
+    }
     o << "}\n";
   }
   o << "}\n";
@@ -496,7 +491,7 @@ void Emit::step(int u, bool safe) {
     } else {
       o << "\n";
     }
-    if (n.dst_index >= 0) liveout((int)ni, u);
+    if (n.dst_index >= 0) liveout((int)ni, u, safe);
     o << "}\n";
   }
 }
@@ -541,6 +536,28 @@ std::string Emit::run() {
   o << "float";
   for (int e = 0; e < V; e++) o << (e ? ", " : " ") << "v" << e;
   o << ";\n";
+  // per-tile bases: sources' o-point offsets, liveouts' lane column
+  for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+    const VolNode &n = g.nodes[ni];
+    if (n.source) {
+      const std::string S = "a.src[" + std::to_string(n.src_index) + "]";
+      o << "const unsigned char *sb" << ni << " = (const unsigned char *)" << S << ".ptr;\n";
+      for (int j = -n.olo; j < g.To + n.ohi; j++) {
+        std::string off;
+        if (g.split == 0) off = n.planes == 1 ? "0" : "(wt_i64)" + o_index(std::to_string(j)) + " * " + S + ".plane";
+        else off = "(wt_i64)" + o_index(std::to_string(j)) + " * " + S + ".pitch";
+        o << "const wt_i64 so" << ni << "_" << j + n.olo << " = " << off << ";\n";
+      }
+    }
+    if (n.dst_index >= 0) {
+      const std::string D = "a.dst[" + std::to_string(n.dst_index) + "]";
+      const int esz = elem_bytes(key.dst_dtypes.at(n.dst_index));
+      o << "unsigned char *db" << ni << " = (unsigned char *)" << D << ".ptr + (wt_i64)xl0 * " << esz << ";\n";
+      for (int j = 0; j < g.To; j++)
+        o << "const wt_i64 do" << ni << "_" << j << " = (wt_i64)(o0 + " << j << ") * " << D
+          << (g.split == 0 ? ".plane" : ".pitch") << ";\n";
+    }
+  }
   o << "const int nsteps = min(" << g.Ts << ", NS - s0) + " << g.pro << ";\n";
   auto loop = [&](bool safe) {
     o << "#pragma unroll 1\n";

@@ -12,7 +12,8 @@ of 3-D heat diffusion (7-point stencils).
 Arms:
   plain  per-stage kernels, FP32 intermediates in HBM (the unfused path)
   fused  one 3-D group, swept in two rounds: split axis {rows, planes} x
-         tile_o {1, 2, 4, 8} x vec {1, 2, 4} at tile_h 32 and 4 warps, then
+         tile_o {1, 2, 4, 8} x vec {1, 2, 4} x register cap {none, 128} at
+         tile_h 32 and 4 warps, then
          tile_h {16, 64, 128} x warps {2, 4, 8} x register cap {none, 128,
          168} around the best
 Time per run: CUDA events on the launching stream, mean over `reps` runs
@@ -78,8 +79,8 @@ def study(name, reps, stream, flush, log):
         return ms
 
     rows, worst, first = [], 0.0, True
-    grid1 = [dict(tile_h=32, tile_o=o, vec=v, warps_per_block=4, flags=wt.WT_FLAG_ZSTREAM if s else 0)
-             for s, o, v in itertools.product((0, 1), (1, 2, 4, 8), (1, 2, 4))]
+    grid1 = [dict(tile_h=32, tile_o=o, vec=v, warps_per_block=4, max_regs=r, flags=wt.WT_FLAG_ZSTREAM if s else 0)
+             for s, o, v, r in itertools.product((0, 1), (1, 2, 4, 8), (1, 2, 4), (0, 128))]
 
     def run_grid(grid):
         nonlocal worst, first

@@ -129,3 +129,13 @@ def test_launch_count_of_3d_groups():
     assert p.launches_per_run() == 4
     p.schedule(exec_mode=wt.WT_EXEC_PLAIN)
     assert p.launches_per_run() == 4
+
+
+@pytest.mark.parametrize("split,tile_o,vec", [(0, 2, 4), (1, 2, 4), (1, 4, 2), (0, 1, 1)])
+def test_interior_tiles_vector_paths(split, tile_o, vec):
+    """Volumes wide enough for interior tiles (vector loads and stores,
+    no clamps) between the border ones."""
+    D, H, W = 7, 11, 300
+    spec = P.heat3d(2, depth=D)
+    img = rnd(15 + vec, W, H, D)
+    check(spec, [img], [vparams(split, tile_o, vec, 5)])
