@@ -372,7 +372,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   static const char kChainVersion[] = "wt-chain-1";  // the reduction-chain kernel's own changes
   if (key.chain) h = fnv1a(kChainVersion, sizeof kChainVersion, h);
-  static const char kVolVersion[] = "wt-vol-4";  // the 3-D group kernel's own changes
+  static const char kVolVersion[] = "wt-vol-5";  // the 3-D group kernel's own changes
   if (key.vol) h = fnv1a(kVolVersion, sizeof kVolVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;

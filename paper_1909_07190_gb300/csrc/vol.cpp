@@ -595,7 +595,11 @@ std::string emit_vol(const Pipeline &p, const VolGeom &g, const CodegenKey &key,
   std::ostringstream o;
   o << kDeviceSource;
   o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
-  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ") " << kname
+  // a register cap is applied through the launch bounds (resident blocks
+  // per SM), which take precedence over the compiler's register option
+  int min_blocks = 1;
+  if (key.max_regs > 0) min_blocks = std::max(1, 65536 / (key.max_regs * 32 * key.nw));
+  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", " << min_blocks << ") " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
   o << body;
   o << "}\n";
