@@ -13,10 +13,9 @@
 //     that are not split) of vol_to output points plus each node's halo.
 // Producer reads are then register reads: along o from another o point of
 // the same thread (Type 1 of Fig. 8 with W_o = 1), along s from an older
-// window slot, along x from the V + xl + xr values each stored row holds,
-// its neighbours' values exchanged by shuffles when the row was stored
-// (Types 3/4).  Sources (pipeline inputs, earlier groups) are read from
-// memory at each tap row.
+// window slot, along x from the lane that holds the column, by shuffle at
+// the tap (Types 3/4).  Sources (pipeline inputs, earlier groups) are
+// register windows too, each row loaded two steps before its first use.
 //
 // Clamp-to-edge at every stage: a node's value at a point outside the
 // volume is its value at the clamped point.  Rows before 0 are not computed;
@@ -189,7 +188,7 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
     if (n.source) n.lead += kVolPrefetch;
     g.pro = std::max(g.pro, n.lead - n.need_lo);
   }
-  // windows and stored neighbour values of the group's stages
+  // windows of every node, source x margins
   for (int k = 0; k < (int)stages.size(); k++) {
     const int ci = g.node_of(stages[k]);
     for (const VTap &t : stage_taps(p, g, stages[k])) {
@@ -353,18 +352,6 @@ void Emit::program(int sid, int ni, int u, bool safe) {
       o << "}\n";
     }
     for (int e = 0; e < V; e++) o << reg(ni, sl0, j, e) << " = v" << e << ";\n";
-    // neighbour values: entry e' < 0 from lane - ceil(-e'/V), entry >= V from
-    // lane + floor(e'/V)
-    for (int e = -n.xl; e < 0; e++) {
-      const int dl = (-e + V - 1) / V;
-      const int src = e + dl * V;
-      o << reg(ni, sl0, j, e) << " = __shfl_up_sync(WT_FULL, v" << src << ", " << dl << ");\n";
-    }
-    for (int e = V; e < V + n.xr; e++) {
-      const int dl = e / V;
-      const int src = e - dl * V;
-      o << reg(ni, sl0, j, e) << " = __shfl_down_sync(WT_FULL, v" << src << ", " << dl << ");\n";
-    }
     o << "}\n";
   }
 }

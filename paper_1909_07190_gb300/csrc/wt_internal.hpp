@@ -369,16 +369,17 @@ extern const char *kDeviceSource;  // device_src.cpp
 // along the split axis s (rows, or planes), lanes cover x (V points each),
 // and the third axis o is a register tile of vol_to points plus halos: each
 // node keeps, per o point of its range, a window of its last `window`
-// streamed rows, V + xl + xr values per lane.  Producer reads along o are
-// same-thread register reads; along x, neighbour values were exchanged by
-// shuffles when the row was stored; along s, older window slots.
+// streamed rows, V values per lane.  Producer reads along o are
+// same-thread register reads; along x, shuffles from the lane that holds
+// the column; along s, older window slots.
 struct VolNode {
   int id = 0;            // stage id, or -(j+1) for a pipeline input
   bool source = false;   // read from memory (outside the group)
   int lead = 0;          // rows ahead of the output row
   int window = 1;        // streamed rows kept
   int olo = 0, ohi = 0;  // o points below/above the tile's range
-  int xl = 0, xr = 0;    // neighbour values per lane stored left/right
+  int xl = 0, xr = 0;    // neighbour values stored per lane (kept 0: x
+                         // neighbours come by shuffle at the tap)
   int need_lo = 0;       // first needed row relative to the tile (<= 0)
   int src_index = -1, dst_index = -1;
   int planes = 1;        // planes of the image (sources: 1 or D)
