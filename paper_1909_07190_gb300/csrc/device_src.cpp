@@ -182,6 +182,10 @@ static __device__ __forceinline__ float wt_lds1_bf16(const void *p) { return wt_
 static __device__ __forceinline__ void wt_cp_async16(wt_u32 dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// 4 bytes (both addresses 4-byte aligned)
+static __device__ __forceinline__ void wt_cp_async4(wt_u32 dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
 static __device__ __forceinline__ void wt_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 #define WT_CP_ASYNC_WAIT(n) asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory")
 // ------------------------------- read-only pairs (aligned to their size)

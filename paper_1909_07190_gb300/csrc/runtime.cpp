@@ -286,7 +286,8 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       L.block = 32 * key.nw;
       L.grid[0] = (unsigned)((nt + key.nw - 1) / key.nw);
       L.grid[1] = L.grid[2] = 1;
-      L.smem = 0;
+      L.smem = key.nw * vol_warp_smem(vg, key, nullptr);
+      if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "3-D group needs more than 227 KB of shared memory per block");
       L.kname = kernel_name(p, key, false);
       continue;
     } else if (key.chain) {
@@ -372,7 +373,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   static const char kChainVersion[] = "wt-chain-1";  // the reduction-chain kernel's own changes
   if (key.chain) h = fnv1a(kChainVersion, sizeof kChainVersion, h);
-  static const char kVolVersion[] = "wt-vol-5";  // the 3-D group kernel's own changes
+  static const char kVolVersion[] = "wt-vol-6";  // the 3-D group kernel's own changes
   if (key.vol) h = fnv1a(kVolVersion, sizeof kVolVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;

@@ -43,6 +43,25 @@ int VolGeom::node_of(int id) const {
   return -1;
 }
 
+// Shared-memory rows of source si: 32 V columns plus the sources' x
+// margins plus alignment slack, rounded to 16 bytes.
+static int src_row_bytes(const VolGeom &g, const CodegenKey &key, int si) {
+  const int esz = elem_bytes(key.src_dtypes.at(g.nodes[si].src_index));
+  return (((32 * g.V + g.xml + g.xmr + 4 / esz) * esz) + 15) / 16 * 16;
+}
+
+int vol_warp_smem(const VolGeom &g, const CodegenKey &key, std::vector<int> *offs) {
+  int off = 0;
+  if (offs) offs->assign(g.nodes.size(), -1);
+  for (size_t i = 0; i < g.nodes.size(); i++) {
+    const VolNode &n = g.nodes[i];
+    if (!n.source) continue;
+    if (offs) (*offs)[i] = off;
+    off += n.window * (g.To + n.olo + n.ohi) * src_row_bytes(g, key, (int)i);
+  }
+  return off;
+}
+
 namespace {
 
 // A tap of a group stage in (x, s, o) coordinates.
@@ -214,17 +233,20 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
   if (g.ow < V) return no("x halo leaves no output columns");
   // unroll: the least common multiple of the windows when small, else the
   // largest window (nodes whose window does not divide it shift)
+  // (sources live in shared memory, their slots chosen at run time)
   int U = 1;
-  for (const VolNode &n : g.nodes) U = std::lcm(U, n.window);
+  for (const VolNode &n : g.nodes)
+    if (!n.source) U = std::lcm(U, n.window);
   if (U > 8) {
     U = 1;
-    for (const VolNode &n : g.nodes) U = std::max(U, n.window);
+    for (const VolNode &n : g.nodes)
+      if (!n.source) U = std::max(U, n.window);
   }
   g.U = U;
   g.regs = 0;
   for (VolNode &n : g.nodes) {
     n.rotate = U % n.window == 0;
-    g.regs += n.window * (g.To + n.olo + n.ohi) * (V + n.xl + n.xr);
+    if (!n.source) g.regs += n.window * (g.To + n.olo + n.ohi) * (V + n.xl + n.xr);
   }
   if (g.regs > 224) return no("3-D group windows need " + std::to_string(g.regs) +
                               " registers per thread; lower tile_o or vec");
@@ -268,7 +290,9 @@ struct Emit {
     const int dl = e / V;
     return "__shfl_down_sync(WT_FULL, " + reg(si, sl, j, e - dl * V) + ", " + std::to_string(dl) + ")";
   }
-  void load_source(int si, int u, bool safe);
+  void load_source(int si, bool safe);
+  std::string src_tap(int si, int age, int j, int e) const;
+  std::set<int> src_ages(int si) const;
   void program(int sid, int ni, int u, bool safe);
   void store_row(int ni, int u, bool safe);
   void liveout(int ni, int u, bool safe);
@@ -290,7 +314,7 @@ void Emit::program(int sid, int ni, int u, bool safe) {
     std::map<std::tuple<int, int, int, int>, std::string> nb;
     for (int e = 0; e < V; e++)
       for (const VTap &t : taps) {
-        if (t.node < 0) continue;
+        if (t.node < 0 || g.nodes[t.node].source) continue;
         const int ee = e + t.dx;
         if (ee >= 0 && ee < V) continue;
         const VolNode &pn = g.nodes[t.node];
@@ -311,7 +335,9 @@ void Emit::program(int sid, int ni, int u, bool safe) {
             const VolNode &pn = g.nodes[t.node];
             const int age = pn.lead - n.lead - t.ds;
             const int ee = e + t.dx;
-            if (ee < 0 || ee >= V)
+            if (pn.source)
+              st.push_back(src_tap(t.node, age, j + t.dO, ee));
+            else if (ee < 0 || ee >= V)
               st.push_back(nb.at(std::make_tuple(t.node, slot(pn, u, age), j + t.dO, ee)));
             else
               st.push_back(reg(t.node, slot(pn, u, age), j + t.dO, ee));
@@ -356,41 +382,63 @@ void Emit::program(int sid, int ni, int u, bool safe) {
   }
 }
 
-// Loads source si's row of step u (clamped row and o point: a source's
-// value outside the volume is the clamped point's) into its age-0 slot:
-// the lane's V columns, one vector load in interior tiles (the first column
-// is a multiple of V and rows are 16-byte aligned), clamped scalar loads
-// in border tiles.
-void Emit::load_source(int si, int u, bool safe) {
+// Stages source si's row of this step (clamped row and o point: a
+// source's value outside the volume is the clamped point's) into its
+// run-time slot sk of the warp's shared memory, by asynchronous copies:
+// interior tiles copy the row segment in 4-byte chunks from an aligned
+// start column `seg`, border tiles copy element by element from clamped
+// columns (16-bit elements by plain loads and stores).
+void Emit::load_source(int si, bool safe) {
   const VolNode &n = g.nodes[si];
   const int V = g.V;
-  const int sl0 = slot(n, u, 0);
   const int dt = key.src_dtypes.at(n.src_index);
   const int esz = elem_bytes(dt);
-  const std::string dn = dtype_name(dt);
+  const int NI = g.To + n.olo + n.ohi;
+  const int RB = src_row_bytes(g, key, si);
+  const int M = 4 / esz - 1;
   const std::string S = "a.src[" + std::to_string(n.src_index) + "]";
-  // the row's base once per step; each o point's offset was computed once
-  // per tile
-  if (g.split == 0) o << "const unsigned char *rb_ = sb" << si << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".pitch;\n";
-  else if (n.planes == 1) o << "const unsigned char *rb_ = sb" << si << ";\n";
-  else o << "const unsigned char *rb_ = sb" << si << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".plane;\n";
+  const std::string sn = std::to_string(si);
+  if (g.split == 0) o << "const unsigned char *rb_ = sb" << sn << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".pitch;\n";
+  else if (n.planes == 1) o << "const unsigned char *rb_ = sb" << sn << ";\n";
+  else o << "const unsigned char *rb_ = sb" << sn << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".plane;\n";
+  o << "unsigned char *sd_ = ss" << sn << " + sk" << sn << " * " << NI * RB << ";\n";
+  const int RL = 32 * V + g.xml + g.xmr;              // elements per staged row
+  const int NC = ((RL + M) * esz + 3) / 4;            // 4-byte chunks from seg
   for (int j = -n.olo; j < g.To + n.ohi; j++) {
-    o << "{ const unsigned char *rp_ = rb_ + so" << si << "_" << j + n.olo << ";\n";
-    if (!safe && V == 4) {
-      o << "wt_ld4_" << dn << "(rp_ + (wt_i64)xl0 * " << esz << ", " << reg(si, sl0, j, 0) << ", "
-        << reg(si, sl0, j, 1) << ", " << reg(si, sl0, j, 2) << ", " << reg(si, sl0, j, 3) << ");\n";
-    } else if (!safe && V == 2) {
-      o << "wt_ld2_" << dn << "(rp_ + (wt_i64)xl0 * " << esz << ", " << reg(si, sl0, j, 0) << ", "
-        << reg(si, sl0, j, 1) << ");\n";
+    o << "{ const unsigned char *rp_ = rb_ + so" << sn << "_" << j + n.olo << ";\n";
+    o << "const wt_u32 dp_ = wt_smem_u32(sd_ + " << (j + n.olo) * RB << ");\n";
+    if (!safe) {
+      o << "rp_ += (wt_i64)seg" << sn << " * " << esz << ";\n";
+      for (int m = 0; 32 * m < NC; m++) {
+        const bool guard = 32 * (m + 1) > NC;
+        o << "{ const int c_ = lane + " << 32 * m << ";";
+        if (guard) o << " if (c_ < " << NC << ")";
+        o << " wt_cp_async4(dp_ + 4u * (wt_u32)c_, rp_ + 4 * c_); }\n";
+      }
     } else {
-      for (int e = 0; e < V; e++) {
-        const std::string col = "(xl0 + " + std::to_string(e) + ")";
-        o << reg(si, sl0, j, e) << " = wt_ld1_" << dn << "(rp_ + (wt_i64)"
-          << (safe ? "wt_clampi(" + col + ", 0, W - 1)" : col) << " * " << esz << ");\n";
+      for (int m = 0; 32 * m < RL; m++) {
+        const bool guard = 32 * (m + 1) > RL;
+        o << "{ const int i_ = lane + " << 32 * m << ";";
+        if (guard) o << " if (i_ < " << RL << ")";
+        o << " { const int c_ = wt_clampi(seg" << sn << " + i_, 0, W - 1);";
+        if (esz == 4) o << " wt_cp_async4(dp_ + 4u * (wt_u32)i_, rp_ + 4 * c_);";
+        else o << " *(wt_u16 *)(sd_ + " << (j + n.olo) * RB << " + 2 * i_) = *(const wt_u16 *)(rp_ + 2 * c_);";
+        o << " } }\n";
       }
     }
     o << "}\n";
   }
+}
+
+// A source tap: the staged value at o point j (relative), x entry e of the
+// lane, from the row of the given age.
+std::string Emit::src_tap(int si, int age, int j, int e) const {
+  const VolNode &n = g.nodes[si];
+  const int dt = key.src_dtypes.at(n.src_index);
+  const int esz = elem_bytes(dt);
+  const int RB = src_row_bytes(g, key, si);
+  return "wt_lds1_" + std::string(dtype_name(dt)) + "(sa" + std::to_string(si) + "_" + std::to_string(age) + " + " +
+         std::to_string((j + n.olo) * RB + e * esz) + ")";
 }
 
 // o points outside [0, NO): copies of the nearest in-range point (all
@@ -443,17 +491,47 @@ void Emit::liveout(int ni, int u, bool safe) {
   o << "}\n";
 }
 
+// Ages (rows back from the newest) at which stages read source si.
+std::set<int> Emit::src_ages(int si) const {
+  std::set<int> ages;
+  for (const VolNode &c : g.nodes) {
+    if (c.source) continue;
+    for (const VTap &t : stage_taps(p, g, c.id))
+      if (t.node == si) ages.insert(g.nodes[si].lead - c.lead - t.ds);
+  }
+  return ages;
+}
+
 void Emit::step(int u, bool safe) {
   const int V = g.V;
+  // every lane is done with the slots this step's copies overwrite
+  o << "__syncwarp();\n";
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
     const VolNode &n = g.nodes[ni];
-    if (n.source) {
-      o << "{ // source " << n.id << "\n";
-      o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
-      load_source((int)ni, u, safe);
-      o << "}\n";
-      continue;
+    if (!n.source) continue;
+    o << "const int sk" << ni << " = k % " << n.window << ";\n";
+    o << "{ // source " << n.id << "\n";
+    o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
+    load_source((int)ni, safe);
+    o << "}\n";
+  }
+  // rows staged kVolPrefetch or more steps ago have landed (a stage reads a
+  // source no less than kVolPrefetch rows back); one commit group per step
+  o << "wt_cp_async_commit();\nWT_CP_ASYNC_WAIT(" << kVolPrefetch << ");\n__syncwarp();\n";
+  for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+    const VolNode &n = g.nodes[ni];
+    if (!n.source) continue;
+    const int NI = g.To + n.olo + n.ohi;
+    for (int a : src_ages((int)ni)) {
+      o << "int t" << ni << "_" << a << " = sk" << ni << " - " << a << "; if (t" << ni << "_" << a << " < 0) t" << ni
+        << "_" << a << " += " << n.window << ";\n";
+      o << "const unsigned char *sa" << ni << "_" << a << " = sl" << ni << " + t" << ni << "_" << a << " * "
+        << NI * src_row_bytes(g, key, (int)ni) << ";\n";
     }
+  }
+  for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+    const VolNode &n = g.nodes[ni];
+    if (n.source) continue;
     o << "{ // stage " << n.id << "\n";
     o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
     o << "if (rn >= 0 && rn < NS) {\n";
@@ -498,7 +576,12 @@ std::string Emit::run() {
   o << "const bool olane = lane * " << V << " >= " << g.hxlp << " && lane * " << V << " < " << g.hxlp + g.ow
     << ";\n";
   // border tiles: some column a lane computes or reads lies outside [0, W)
-  o << "const bool xb = xs - " << g.xml << " < 0 || xs + " << 32 * V + g.xmr << " > W;\n";
+  // (interior tiles copy source rows from an aligned start up to 2 M
+  // elements past the tile's last column: M = 1 for 16-bit sources)
+  int M2 = 0;
+  for (const VolNode &n : g.nodes)
+    if (n.source && elem_bytes(key.src_dtypes.at(n.src_index)) == 2) M2 = 2;
+  o << "const bool xb = xs - " << g.xml << " < 0 || xs + " << 32 * V + g.xmr + M2 << " > W;\n";
   int OL = 0, OH = 0;
   for (const VolNode &n : g.nodes) {
     OL = std::max(OL, n.olo);
@@ -512,6 +595,7 @@ std::string Emit::run() {
   // window registers
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
     const VolNode &n = g.nodes[ni];
+    if (n.source) continue;
     for (int sl = 0; sl < n.window; sl++)
       for (int j = -n.olo; j < g.To + n.ohi; j++) {
         o << "float";
@@ -523,12 +607,24 @@ std::string Emit::run() {
   o << "float";
   for (int e = 0; e < V; e++) o << (e ? ", " : " ") << "v" << e;
   o << ";\n";
+  std::vector<int> soff;
+  const int WB = vol_warp_smem(g, key, &soff);
+  o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
+  o << "unsigned char *wsm_ = wt_smem + (threadIdx.x >> 5) * " << WB << ";\n";
   // per-tile bases: sources' o-point offsets, liveouts' lane column
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
     const VolNode &n = g.nodes[ni];
     if (n.source) {
       const std::string S = "a.src[" + std::to_string(n.src_index) + "]";
+      const int esz = elem_bytes(key.src_dtypes.at(n.src_index));
       o << "const unsigned char *sb" << ni << " = (const unsigned char *)" << S << ".ptr;\n";
+      // staged rows: the warp's slots, the segment's first column, the
+      // lane's first value
+      o << "unsigned char *ss" << ni << " = wsm_ + " << soff[ni] << ";\n";
+      o << "const int seg" << ni << " = xb ? xs - " << g.xml << " : ((xs - " << g.xml << ") & ~" << 4 / esz - 1
+        << ");\n";
+      o << "const unsigned char *sl" << ni << " = ss" << ni << " + (lane * " << V << " + " << g.xml << " + (xs - "
+        << g.xml << " - seg" << ni << ")) * " << esz << ";\n";
       for (int j = -n.olo; j < g.To + n.ohi; j++) {
         std::string off;
         if (g.split == 0) off = n.planes == 1 ? "0" : "(wt_i64)" + o_index(std::to_string(j)) + " * " + S + ".plane";
@@ -554,7 +650,7 @@ std::string Emit::run() {
       // shift the windows that do not rotate by renaming
       for (size_t ni = 0; ni < g.nodes.size(); ni++) {
         const VolNode &n = g.nodes[ni];
-        if (n.rotate || n.window < 2) continue;
+        if (n.source || n.rotate || n.window < 2) continue;
         for (int a = n.window - 1; a >= 1; a--)
           for (int j = -n.olo; j < g.To + n.ohi; j++)
             for (int e = -n.xl; e < V + n.xr; e++)
@@ -570,6 +666,8 @@ std::string Emit::run() {
   o << "} else {\n";
   loop(true);
   o << "}\n";
+  // no copy may land in shared memory after the warp has left
+  o << "WT_CP_ASYNC_WAIT(0);\n";
   return o.str();
 }
 

@@ -402,5 +402,8 @@ struct VolGeom {
 // Geometry of a 3-D group, or ok = false with the reason.
 VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V);
 std::string emit_vol(const Pipeline &p, const VolGeom &g, const CodegenKey &key, const std::string &kname);
+// Shared memory per warp of a 3-D group kernel (its sources' staged rows);
+// `offs` (optional) receives each source node's byte offset.
+int vol_warp_smem(const VolGeom &g, const CodegenKey &key, std::vector<int> *offs);
 
 }  // namespace wt

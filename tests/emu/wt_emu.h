@@ -290,6 +290,13 @@ static inline void wt_cp_async16(wt_u32 dst, const void *src) {
   if (!wt_emu_in_global(src, 16)) { wt_emu_fail("cp.async source outside the registered buffers"); return; }
   memcpy(wt_emu_sptr(dst), src, 16);
 }
+static inline void wt_cp_async4(wt_u32 dst, const void *src) {
+  if (dst % 4 != 0 || ((unsigned long)src) % 4 != 0) { wt_emu_fail("cp.async address not 4-byte aligned"); return; }
+  if (!wt_emu_in_smem(wt_emu_sptr(dst), 4)) { wt_emu_fail("cp.async destination outside shared memory"); return; }
+  if (wt_emu_in_smem(src, 4)) { wt_emu_fail("cp.async source in shared memory"); return; }
+  if (!wt_emu_in_global(src, 4)) { wt_emu_fail("cp.async source outside the registered buffers"); return; }
+  memcpy(wt_emu_sptr(dst), src, 4);
+}
 static inline void wt_cp_async_commit() {}
 #define WT_CP_ASYNC_WAIT(n) ((void)(n))
 static inline void wt_ld2_f32(const void *p, float &a, float &b) {

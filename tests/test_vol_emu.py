@@ -139,3 +139,16 @@ def test_interior_tiles_vector_paths(split, tile_o, vec):
     spec = P.heat3d(2, depth=D)
     img = rnd(15 + vec, W, H, D)
     check(spec, [img], [vparams(split, tile_o, vec, 5)])
+
+
+@pytest.mark.parametrize("dtype,vec", [("f16", 1), ("bf16", 2), ("f16", 4)])
+def test_interior_tiles_sixteen_bit(dtype, vec):
+    """16-bit sources staged from an even start column in interior tiles."""
+    D, H, W = 5, 9, 301
+    spec = P.heat3d(2, depth=D)
+    img = rnd(16 + vec, W, H, D, dtype=dtype)
+    got, d = run_emulated(spec, [img], dtype={"f16": wt.WT_F16, "bf16": wt.WT_BF16}[dtype],
+                          params=[vparams(1, 2, vec, 4)])
+    assert d["name"].startswith("wt_vol_")
+    ref = oracle_of(spec, [img])[0]
+    assert np.abs(got[0] - ref).max() <= (2e-3 if dtype == "f16" else 1.6e-2)
