@@ -120,7 +120,8 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     if (fused && zgroup) {
       // plane-offset taps: a 3-D group (App. A), else per-stage kernels
       const int V = gp.vec > 0 ? gp.vec : 2;
-      VolGeom vg = vol_analyze(p, G, gp.zstream, gp.tile_o > 0 ? gp.tile_o : 4, std::max(1, gp.tile_h), V);
+      VolGeom vg = vol_analyze(p, G, gp.zstream, gp.tile_o > 0 ? gp.tile_o : 4, std::max(1, gp.tile_h), V,
+                               gp.frac_reg < 1.f);
       if (vg.ok) {
         for (int s : vg.liveouts) materialize(s, !p.consumers[s].empty());
         Launch L;
@@ -264,7 +265,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       key.vol_to = vg.To;
       key.pairs = false;
       key.chunk = key.nbuf = 0;
-      key.frac_reg = 1.f;
+      key.frac_reg = vg.staged ? 0.f : 1.f;
       for (const VolNode &nd : vg.nodes)
         if (nd.source) {
           L.src.push_back(nd.id);

@@ -53,6 +53,7 @@ static int src_row_bytes(const VolGeom &g, const CodegenKey &key, int si) {
 int vol_warp_smem(const VolGeom &g, const CodegenKey &key, std::vector<int> *offs) {
   int off = 0;
   if (offs) offs->assign(g.nodes.size(), -1);
+  if (!g.staged) return 0;
   for (size_t i = 0; i < g.nodes.size(); i++) {
     const VolNode &n = g.nodes[i];
     if (!n.source) continue;
@@ -91,8 +92,10 @@ std::vector<VTap> stage_taps(const Pipeline &p, const VolGeom &g, int sid) {
 
 }  // namespace
 
-VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V) {
+VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V,
+                    bool staged) {
   VolGeom g;
+  g.staged = staged;
   g.split = split;
   g.To = std::max(1, To);
   g.Ts = std::max(1, Ts);
@@ -233,20 +236,21 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
   if (g.ow < V) return no("x halo leaves no output columns");
   // unroll: the least common multiple of the windows when small, else the
   // largest window (nodes whose window does not divide it shift)
-  // (sources live in shared memory, their slots chosen at run time)
+  // (staged sources live in shared memory, their slots chosen at run time)
+  auto in_regs = [&](const VolNode &n) { return !n.source || !g.staged; };
   int U = 1;
   for (const VolNode &n : g.nodes)
-    if (!n.source) U = std::lcm(U, n.window);
+    if (in_regs(n)) U = std::lcm(U, n.window);
   if (U > 8) {
     U = 1;
     for (const VolNode &n : g.nodes)
-      if (!n.source) U = std::max(U, n.window);
+      if (in_regs(n)) U = std::max(U, n.window);
   }
   g.U = U;
   g.regs = 0;
   for (VolNode &n : g.nodes) {
     n.rotate = U % n.window == 0;
-    if (!n.source) g.regs += n.window * (g.To + n.olo + n.ohi) * (V + n.xl + n.xr);
+    if (in_regs(n)) g.regs += n.window * (g.To + n.olo + n.ohi) * (V + n.xl + n.xr);
   }
   if (g.regs > 224) return no("3-D group windows need " + std::to_string(g.regs) +
                               " registers per thread; lower tile_o or vec");
@@ -291,6 +295,7 @@ struct Emit {
     return "__shfl_down_sync(WT_FULL, " + reg(si, sl, j, e - dl * V) + ", " + std::to_string(dl) + ")";
   }
   void load_source(int si, bool safe);
+  void load_source_regs(int si, int u, bool safe);
   std::string src_tap(int si, int age, int j, int e) const;
   std::set<int> src_ages(int si) const;
   void program(int sid, int ni, int u, bool safe);
@@ -314,7 +319,7 @@ void Emit::program(int sid, int ni, int u, bool safe) {
     std::map<std::tuple<int, int, int, int>, std::string> nb;
     for (int e = 0; e < V; e++)
       for (const VTap &t : taps) {
-        if (t.node < 0 || g.nodes[t.node].source) continue;
+        if (t.node < 0 || (g.nodes[t.node].source && g.staged)) continue;
         const int ee = e + t.dx;
         if (ee >= 0 && ee < V) continue;
         const VolNode &pn = g.nodes[t.node];
@@ -335,7 +340,7 @@ void Emit::program(int sid, int ni, int u, bool safe) {
             const VolNode &pn = g.nodes[t.node];
             const int age = pn.lead - n.lead - t.ds;
             const int ee = e + t.dx;
-            if (pn.source)
+            if (pn.source && g.staged)
               st.push_back(src_tap(t.node, age, j + t.dO, ee));
             else if (ee < 0 || ee >= V)
               st.push_back(nb.at(std::make_tuple(t.node, slot(pn, u, age), j + t.dO, ee)));
@@ -430,6 +435,40 @@ void Emit::load_source(int si, bool safe) {
   }
 }
 
+// Loads source si's row of step u into its age-0 register slot (sources in
+// registers, frac_reg = 1): the lane's V columns, one vector load in
+// interior tiles (the first column is a multiple of V and rows are 16-byte
+// aligned), clamped scalar loads in border tiles.
+void Emit::load_source_regs(int si, int u, bool safe) {
+  const VolNode &n = g.nodes[si];
+  const int V = g.V;
+  const int sl0 = slot(n, u, 0);
+  const int dt = key.src_dtypes.at(n.src_index);
+  const int esz = elem_bytes(dt);
+  const std::string dn = dtype_name(dt);
+  const std::string S = "a.src[" + std::to_string(n.src_index) + "]";
+  if (g.split == 0) o << "const unsigned char *rb_ = sb" << si << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".pitch;\n";
+  else if (n.planes == 1) o << "const unsigned char *rb_ = sb" << si << ";\n";
+  else o << "const unsigned char *rb_ = sb" << si << " + (wt_i64)wt_clampi(rn, 0, NS - 1) * " << S << ".plane;\n";
+  for (int j = -n.olo; j < g.To + n.ohi; j++) {
+    o << "{ const unsigned char *rp_ = rb_ + so" << si << "_" << j + n.olo << ";\n";
+    if (!safe && V == 4) {
+      o << "wt_ld4_" << dn << "(rp_ + (wt_i64)xl0 * " << esz << ", " << reg(si, sl0, j, 0) << ", "
+        << reg(si, sl0, j, 1) << ", " << reg(si, sl0, j, 2) << ", " << reg(si, sl0, j, 3) << ");\n";
+    } else if (!safe && V == 2) {
+      o << "wt_ld2_" << dn << "(rp_ + (wt_i64)xl0 * " << esz << ", " << reg(si, sl0, j, 0) << ", "
+        << reg(si, sl0, j, 1) << ");\n";
+    } else {
+      for (int e = 0; e < V; e++) {
+        const std::string col = "(xl0 + " + std::to_string(e) + ")";
+        o << reg(si, sl0, j, e) << " = wt_ld1_" << dn << "(rp_ + (wt_i64)"
+          << (safe ? "wt_clampi(" + col + ", 0, W - 1)" : col) << " * " << esz << ");\n";
+      }
+    }
+    o << "}\n";
+  }
+}
+
 // A source tap: the staged value at o point j (relative), x entry e of the
 // lane, from the row of the given age.
 std::string Emit::src_tap(int si, int age, int j, int e) const {
@@ -504,29 +543,41 @@ std::set<int> Emit::src_ages(int si) const {
 
 void Emit::step(int u, bool safe) {
   const int V = g.V;
-  // every lane is done with the slots this step's copies overwrite
-  o << "__syncwarp();\n";
-  for (size_t ni = 0; ni < g.nodes.size(); ni++) {
-    const VolNode &n = g.nodes[ni];
-    if (!n.source) continue;
-    o << "const int sk" << ni << " = k % " << n.window << ";\n";
-    o << "{ // source " << n.id << "\n";
-    o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
-    load_source((int)ni, safe);
-    o << "}\n";
-  }
-  // rows staged kVolPrefetch or more steps ago have landed (a stage reads a
-  // source no less than kVolPrefetch rows back); one commit group per step
-  o << "wt_cp_async_commit();\nWT_CP_ASYNC_WAIT(" << kVolPrefetch << ");\n__syncwarp();\n";
-  for (size_t ni = 0; ni < g.nodes.size(); ni++) {
-    const VolNode &n = g.nodes[ni];
-    if (!n.source) continue;
-    const int NI = g.To + n.olo + n.ohi;
-    for (int a : src_ages((int)ni)) {
-      o << "int t" << ni << "_" << a << " = sk" << ni << " - " << a << "; if (t" << ni << "_" << a << " < 0) t" << ni
-        << "_" << a << " += " << n.window << ";\n";
-      o << "const unsigned char *sa" << ni << "_" << a << " = sl" << ni << " + t" << ni << "_" << a << " * "
-        << NI * src_row_bytes(g, key, (int)ni) << ";\n";
+  if (!g.staged) {
+    // sources in registers: this step's rows straight into their windows
+    for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+      const VolNode &n = g.nodes[ni];
+      if (!n.source) continue;
+      o << "{ // source " << n.id << "\n";
+      o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
+      load_source_regs((int)ni, u, safe);
+      o << "}\n";
+    }
+  } else {
+    // every lane is done with the slots this step's copies overwrite
+    o << "__syncwarp();\n";
+    for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+      const VolNode &n = g.nodes[ni];
+      if (!n.source) continue;
+      o << "const int sk" << ni << " = k % " << n.window << ";\n";
+      o << "{ // source " << n.id << "\n";
+      o << "const int rn = s0 - " << g.pro << " + k + " << n.lead << ";\n";
+      load_source((int)ni, safe);
+      o << "}\n";
+    }
+    // rows staged kVolPrefetch or more steps ago have landed (a stage reads
+    // a source no less than kVolPrefetch rows back); one group per step
+    o << "wt_cp_async_commit();\nWT_CP_ASYNC_WAIT(" << kVolPrefetch << ");\n__syncwarp();\n";
+    for (size_t ni = 0; ni < g.nodes.size(); ni++) {
+      const VolNode &n = g.nodes[ni];
+      if (!n.source) continue;
+      const int NI = g.To + n.olo + n.ohi;
+      for (int a : src_ages((int)ni)) {
+        o << "int t" << ni << "_" << a << " = sk" << ni << " - " << a << "; if (t" << ni << "_" << a << " < 0) t" << ni
+          << "_" << a << " += " << n.window << ";\n";
+        o << "const unsigned char *sa" << ni << "_" << a << " = sl" << ni << " + t" << ni << "_" << a << " * "
+          << NI * src_row_bytes(g, key, (int)ni) << ";\n";
+      }
     }
   }
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
@@ -580,7 +631,7 @@ std::string Emit::run() {
   // elements past the tile's last column: M = 1 for 16-bit sources)
   int M2 = 0;
   for (const VolNode &n : g.nodes)
-    if (n.source && elem_bytes(key.src_dtypes.at(n.src_index)) == 2) M2 = 2;
+    if (g.staged && n.source && elem_bytes(key.src_dtypes.at(n.src_index)) == 2) M2 = 2;
   o << "const bool xb = xs - " << g.xml << " < 0 || xs + " << 32 * V + g.xmr + M2 << " > W;\n";
   int OL = 0, OH = 0;
   for (const VolNode &n : g.nodes) {
@@ -595,7 +646,7 @@ std::string Emit::run() {
   // window registers
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
     const VolNode &n = g.nodes[ni];
-    if (n.source) continue;
+    if (n.source && g.staged) continue;
     for (int sl = 0; sl < n.window; sl++)
       for (int j = -n.olo; j < g.To + n.ohi; j++) {
         o << "float";
@@ -609,8 +660,10 @@ std::string Emit::run() {
   o << ";\n";
   std::vector<int> soff;
   const int WB = vol_warp_smem(g, key, &soff);
-  o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
-  o << "unsigned char *wsm_ = wt_smem + (threadIdx.x >> 5) * " << WB << ";\n";
+  if (g.staged) {
+    o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
+    o << "unsigned char *wsm_ = wt_smem + (threadIdx.x >> 5) * " << WB << ";\n";
+  }
   // per-tile bases: sources' o-point offsets, liveouts' lane column
   for (size_t ni = 0; ni < g.nodes.size(); ni++) {
     const VolNode &n = g.nodes[ni];
@@ -620,11 +673,13 @@ std::string Emit::run() {
       o << "const unsigned char *sb" << ni << " = (const unsigned char *)" << S << ".ptr;\n";
       // staged rows: the warp's slots, the segment's first column, the
       // lane's first value
+      if (g.staged) {
       o << "unsigned char *ss" << ni << " = wsm_ + " << soff[ni] << ";\n";
       o << "const int seg" << ni << " = xb ? xs - " << g.xml << " : ((xs - " << g.xml << ") & ~" << 4 / esz - 1
         << ");\n";
       o << "const unsigned char *sl" << ni << " = ss" << ni << " + (lane * " << V << " + " << g.xml << " + (xs - "
         << g.xml << " - seg" << ni << ")) * " << esz << ";\n";
+      }
       for (int j = -n.olo; j < g.To + n.ohi; j++) {
         std::string off;
         if (g.split == 0) off = n.planes == 1 ? "0" : "(wt_i64)" + o_index(std::to_string(j)) + " * " + S + ".plane";
@@ -650,7 +705,7 @@ std::string Emit::run() {
       // shift the windows that do not rotate by renaming
       for (size_t ni = 0; ni < g.nodes.size(); ni++) {
         const VolNode &n = g.nodes[ni];
-        if (n.source || n.rotate || n.window < 2) continue;
+        if ((n.source && g.staged) || n.rotate || n.window < 2) continue;
         for (int a = n.window - 1; a >= 1; a--)
           for (int j = -n.olo; j < g.To + n.ohi; j++)
             for (int e = -n.xl; e < V + n.xr; e++)
@@ -667,7 +722,7 @@ std::string Emit::run() {
   loop(true);
   o << "}\n";
   // no copy may land in shared memory after the warp has left
-  o << "WT_CP_ASYNC_WAIT(0);\n";
+  if (g.staged) o << "WT_CP_ASYNC_WAIT(0);\n";
   return o.str();
 }
 

@@ -387,6 +387,7 @@ struct VolNode {
 };
 struct VolGeom {
   bool ok = false;
+  bool staged = false;         // sources staged in shared memory (else registers)
   std::string why;
   int split = 0, To = 4, Ts = 32, V = 2;
   int D = 1, level = 0;
@@ -400,7 +401,10 @@ struct VolGeom {
   int node_of(int id) const;
 };
 // Geometry of a 3-D group, or ok = false with the reason.
-VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V);
+// `staged`: sources in the warp's shared memory (frac_reg < 1), else in
+// registers like the stages' windows.
+VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V,
+                    bool staged);
 std::string emit_vol(const Pipeline &p, const VolGeom &g, const CodegenKey &key, const std::string &kname);
 // Shared memory per warp of a 3-D group kernel (its sources' staged rows);
 // `offs` (optional) receives each source node's byte offset.

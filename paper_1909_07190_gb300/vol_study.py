@@ -12,8 +12,9 @@ of 3-D heat diffusion (7-point stencils).
 Arms:
   plain  per-stage kernels, FP32 intermediates in HBM (the unfused path)
   fused  one 3-D group, swept in two rounds: split axis {rows, planes} x
-         tile_o {1, 2, 4, 8} x vec {1, 2, 4} x register cap {none, 96} at
-         tile_h 32 and 4 warps, then tile_h {16, 64, 128} x warps {2, 4, 8}
+         tile_o {1, 2, 4, 8} x vec {1, 2} x register cap {none, 96} x
+         sources in registers (frac_reg 1) or staged in shared memory
+         (frac_reg 0) at tile_h 32 and 4 warps, then tile_h {16, 64, 128} x warps {2, 4, 8}
          x register cap {none, 64, 80, 96, 128} around the best
 Time per run: CUDA events on the launching stream, mean over `reps` runs
 after 3 warm-up runs (inputs and outputs of 268 MB each exceed the L2).
@@ -78,8 +79,9 @@ def study(name, reps, stream, flush, log):
         return ms
 
     rows, worst, first = [], 0.0, True
-    grid1 = [dict(tile_h=32, tile_o=o, vec=v, warps_per_block=4, max_regs=r, flags=wt.WT_FLAG_ZSTREAM if s else 0)
-             for s, o, v, r in itertools.product((0, 1), (1, 2, 4, 8), (1, 2, 4), (0, 96))]
+    grid1 = [dict(tile_h=32, tile_o=o, vec=v, warps_per_block=4, max_regs=r, frac_reg=f,
+                  flags=wt.WT_FLAG_ZSTREAM if s else 0)
+             for s, o, v, r, f in itertools.product((0, 1), (1, 2, 4, 8), (1, 2), (0, 96), (1.0, 0.0))]
 
     def run_grid(grid):
         nonlocal worst, first
@@ -107,6 +109,11 @@ def study(name, reps, stream, flush, log):
         k = "planes" if p["flags"] & wt.WT_FLAG_ZSTREAM else "rows"
         if k not in by_split or t < by_split[k][0]:
             by_split[k] = (t, p)
+    by_place = {}
+    for t, p in rows:
+        k = "registers" if p["frac_reg"] >= 1.0 else "shared"
+        if k not in by_place or t < by_place[k][0]:
+            by_place[k] = (t, p)
     peak, kind = hbm_peak()
     vox = W * H * D
     io = 2 * vox * 4
@@ -116,6 +123,7 @@ def study(name, reps, stream, flush, log):
            "speedup": plain_ms / ms, "hbm_gbs": io / (ms * 1e-3) / 1e9, "hbm_peak_gbs": peak, "peak_kind": kind,
            "hbm_frac": io / (ms * 1e-3) / 1e9 / peak,
            "best_by_split": {k: {"us": v[0] * 1e3, "params": v[1]} for k, v in by_split.items()},
+           "best_by_source_placement": {k: {"us": v[0] * 1e3, "params": v[1]} for k, v in by_place.items()},
            "configs": len(rows), "max_diff": worst}
     return out
 

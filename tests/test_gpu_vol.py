@@ -19,8 +19,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def vparams(split, tile_o=4, vec=2, tile_h=16, warps=4):
-    return dict(tile_h=tile_h, tile_o=tile_o, vec=vec, warps_per_block=warps, flags=32 if split else 0)
+def vparams(split, tile_o=4, vec=2, tile_h=16, warps=4, staged=False):
+    """staged: sources in the warp's shared memory (frac_reg < 1)."""
+    return dict(tile_h=tile_h, tile_o=tile_o, vec=vec, warps_per_block=warps, flags=32 if split else 0,
+                frac_reg=0.0 if staged else 1.0)
 
 
 def close(got, ref, rel=1e-5):
@@ -87,3 +89,28 @@ def test_full_size_sampled(name, split):
     ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys, zs)
     g = got[0][zs, ys, xs]
     assert np.abs(g - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("vec,W", [(1, 333), (2, 1000), (4, 77)])
+def test_staged_sources_gpu(split, vec, W):
+    """Sources staged in shared memory by asynchronous copies (frac_reg 0)."""
+    D = 13
+    spec = P.unsharp3d(depth=D)
+    img = rnd(40 + vec, W, 61, D)
+    got, p = run_pipe(spec, [img], params=[vparams(split, 2, vec, 16, staged=True)])
+    assert p.launches_per_run() == 1
+    assert close(got[0], oracle_out(spec, [img])[0])
+
+
+def test_staged_full_size_sampled():
+    W = H = 512
+    D = 256
+    spec = P.heat3d(2, depth=D)
+    img = I.uniform_image(I.SEED_BASE + 8, W, H, D)
+    got, p = run_pipe(spec, [img], params=[vparams(1, 4, 1, 64, staged=True)])
+    assert p.launches_per_run() == 1
+    rng = np.random.default_rng(5)
+    xs, ys, zs = rng.integers(0, W, 3000), rng.integers(0, H, 3000), rng.integers(0, D, 3000)
+    ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys, zs)
+    assert np.abs(got[0][zs, ys, xs] - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())

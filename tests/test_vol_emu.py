@@ -15,8 +15,10 @@ from test_codegen_emu import oracle_of, rnd, run_emulated
 Z = wt.WT_FLAG_ZSTREAM
 
 
-def vparams(split, tile_o=4, vec=2, tile_h=8, warps=2):
-    return dict(tile_h=tile_h, tile_o=tile_o, vec=vec, warps_per_block=warps, flags=Z if split else 0)
+def vparams(split, tile_o=4, vec=2, tile_h=8, warps=2, staged=False):
+    """staged: sources in the warp's shared memory (frac_reg < 1)."""
+    return dict(tile_h=tile_h, tile_o=tile_o, vec=vec, warps_per_block=warps, flags=Z if split else 0,
+                frac_reg=0.0 if staged else 1.0)
 
 
 def check(spec, imgs, params, groups=None, tol=1e-5, prefix="wt_vol_"):
@@ -152,3 +154,26 @@ def test_interior_tiles_sixteen_bit(dtype, vec):
     assert d["name"].startswith("wt_vol_")
     ref = oracle_of(spec, [img])[0]
     assert np.abs(got[0] - ref).max() <= (2e-3 if dtype == "f16" else 1.6e-2)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("name,W", [("heat3d", 70), ("unsharp3d", 300), ("heat3d", 301)])
+@pytest.mark.parametrize("vec", [1, 2, 4])
+def test_staged_sources(split, name, W, vec):
+    """frac_reg < 1: source rows staged in shared memory by asynchronous
+    copies (interior tiles from an aligned start, border tiles clamped)."""
+    D, H = 6, 10
+    spec = P.heat3d(2, depth=D) if name == "heat3d" else P.unsharp3d(depth=D)
+    img = rnd(20 + W + vec, W, H, D)
+    check(spec, [img], [vparams(split, 2, vec, 5, staged=True)])
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_staged_sixteen_bit(dtype):
+    D, H, W = 5, 9, 301
+    spec = P.heat3d(2, depth=D)
+    img = rnd(30, W, H, D, dtype=dtype)
+    got, d = run_emulated(spec, [img], dtype={"f16": wt.WT_F16, "bf16": wt.WT_BF16}[dtype],
+                          params=[vparams(1, 2, 1, 4, staged=True)])
+    assert d["name"].startswith("wt_vol_")
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= (2e-3 if dtype == "f16" else 1.6e-2)
