@@ -162,8 +162,10 @@ typedef struct {
  * generalised hybrid tiling): lanes along x (vec = 1, 2 or 4 points each,
  * 0 = 2), tile_h points along the streamed (split) axis, tile_o points of
  * the third axis in registers.  The split axis is y (rows) by default; with
- * this flag it is z (planes) and tile_o counts rows.  frac_reg, chunk_rows,
- * n_buffers and the other flags are ignored for such groups; a group the
+ * this flag it is z (planes) and tile_o counts rows.  frac_reg = 1 keeps
+ * source rows in registers; below 1 they are staged in the warp's shared
+ * memory by asynchronous copies.  chunk_rows, n_buffers and the other
+ * flags are ignored for such groups; a group the
  * 3-D kernel cannot take (other levels, parity or channel ops, fixed-
  * channel taps, windows above 224 registers) runs per stage.              */
 #define WT_FLAG_ZSTREAM 32
