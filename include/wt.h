@@ -164,7 +164,8 @@ typedef struct {
  * the third axis in registers.  The split axis is y (rows) by default; with
  * this flag it is z (planes) and tile_o counts rows.  frac_reg = 1 keeps
  * source rows in registers; below 1 they are staged in the warp's shared
- * memory by asynchronous copies.  chunk_rows, n_buffers and the other
+ * memory by asynchronous copies; n_buffers (1..8) sets how many rows ahead
+ * of their first use source rows are loaded.  chunk_rows and the other
  * flags are ignored for such groups; a group the
  * 3-D kernel cannot take (other levels, parity or channel ops, fixed-
  * channel taps, windows above 224 registers) runs per stage.              */

@@ -540,7 +540,8 @@ int32_t wt_launches_per_run(const wt_pipeline *p) {
       for (int s : groups[gi]) zgroup = zgroup || p->stages[s].has_z;
       bool fused = p->sched.exec == WT_EXEC_FUSED && !gp.plain &&
                    (zgroup ? wt::vol_analyze(*p, groups[gi], gp.zstream, gp.tile_o > 0 ? gp.tile_o : 4,
-                                             std::max(1, gp.tile_h), gp.vec > 0 ? gp.vec : 2, gp.frac_reg < 1.f).ok
+                                             std::max(1, gp.tile_h), gp.vec > 0 ? gp.vec : 2, gp.frac_reg < 1.f,
+                                             gp.n_buffers).ok
                            : ((!gp.otptb && wt::chain_form(*p, groups[gi]).ok) ||
                               wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable));
       if (fused) {

@@ -121,7 +121,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       // plane-offset taps: a 3-D group (App. A), else per-stage kernels
       const int V = gp.vec > 0 ? gp.vec : 2;
       VolGeom vg = vol_analyze(p, G, gp.zstream, gp.tile_o > 0 ? gp.tile_o : 4, std::max(1, gp.tile_h), V,
-                               gp.frac_reg < 1.f);
+                               gp.frac_reg < 1.f, gp.n_buffers);
       if (vg.ok) {
         for (int s : vg.liveouts) materialize(s, !p.consumers[s].empty());
         Launch L;
@@ -264,7 +264,8 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       key.vol_split = vg.split;
       key.vol_to = vg.To;
       key.pairs = false;
-      key.chunk = key.nbuf = 0;
+      key.chunk = 0;
+      key.nbuf = vg.prefetch;
       key.frac_reg = vg.staged ? 0.f : 1.f;
       for (const VolNode &nd : vg.nodes)
         if (nd.source) {
@@ -374,7 +375,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   static const char kChainVersion[] = "wt-chain-1";  // the reduction-chain kernel's own changes
   if (key.chain) h = fnv1a(kChainVersion, sizeof kChainVersion, h);
-  static const char kVolVersion[] = "wt-vol-6";  // the 3-D group kernel's own changes
+  static const char kVolVersion[] = "wt-vol-7";  // the 3-D group kernel's own changes
   if (key.vol) h = fnv1a(kVolVersion, sizeof kVolVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;

@@ -34,8 +34,6 @@
 
 namespace wt {
 
-// Rows a source is loaded ahead of its first use.
-constexpr int kVolPrefetch = 2;
 
 int VolGeom::node_of(int id) const {
   for (size_t i = 0; i < nodes.size(); i++)
@@ -93,9 +91,10 @@ std::vector<VTap> stage_taps(const Pipeline &p, const VolGeom &g, int sid) {
 }  // namespace
 
 VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V,
-                    bool staged) {
+                    bool staged, int prefetch) {
   VolGeom g;
   g.staged = staged;
+  g.prefetch = std::max(1, std::min(8, prefetch));
   g.split = split;
   g.To = std::max(1, To);
   g.Ts = std::max(1, Ts);
@@ -205,9 +204,9 @@ VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split
     n.ohi = ohi[i];
     g.hxl = std::max(g.hxl, nl[i]);
     g.hxr = std::max(g.hxr, nr[i]);
-    // sources are loaded kVolPrefetch rows before their first use, so that
-    // a load's latency overlaps the steps in between
-    if (n.source) n.lead += kVolPrefetch;
+    // sources are loaded `prefetch` rows before their first use, so that a
+    // load's latency overlaps the steps in between
+    if (n.source) n.lead += g.prefetch;
     g.pro = std::max(g.pro, n.lead - n.need_lo);
   }
   // windows of every node, source x margins
@@ -565,9 +564,9 @@ void Emit::step(int u, bool safe) {
       load_source((int)ni, safe);
       o << "}\n";
     }
-    // rows staged kVolPrefetch or more steps ago have landed (a stage reads
-    // a source no less than kVolPrefetch rows back); one group per step
-    o << "wt_cp_async_commit();\nWT_CP_ASYNC_WAIT(" << kVolPrefetch << ");\n__syncwarp();\n";
+    // rows staged `prefetch` or more steps ago have landed (a stage reads a
+    // source no less than `prefetch` rows back); one group per step
+    o << "wt_cp_async_commit();\nWT_CP_ASYNC_WAIT(" << g.prefetch << ");\n__syncwarp();\n";
     for (size_t ni = 0; ni < g.nodes.size(); ni++) {
       const VolNode &n = g.nodes[ni];
       if (!n.source) continue;

@@ -388,6 +388,7 @@ struct VolNode {
 struct VolGeom {
   bool ok = false;
   bool staged = false;         // sources staged in shared memory (else registers)
+  int prefetch = 2;            // rows a source is loaded ahead of its first use
   std::string why;
   int split = 0, To = 4, Ts = 32, V = 2;
   int D = 1, level = 0;
@@ -402,9 +403,10 @@ struct VolGeom {
 };
 // Geometry of a 3-D group, or ok = false with the reason.
 // `staged`: sources in the warp's shared memory (frac_reg < 1), else in
-// registers like the stages' windows.
+// registers like the stages' windows; `prefetch`: rows a source is loaded
+// ahead of its first use (1..8).
 VolGeom vol_analyze(const Pipeline &p, const std::vector<int> &stages, int split, int To, int Ts, int V,
-                    bool staged);
+                    bool staged, int prefetch);
 std::string emit_vol(const Pipeline &p, const VolGeom &g, const CodegenKey &key, const std::string &kname);
 // Shared memory per warp of a 3-D group kernel (its sources' staged rows);
 // `offs` (optional) receives each source node's byte offset.

@@ -15,7 +15,8 @@ Arms:
          tile_o {1, 2, 4, 8} x vec {1, 2} x register cap {none, 96} x
          sources in registers (frac_reg 1) or staged in shared memory
          (frac_reg 0) at tile_h 32 and 4 warps, then tile_h {16, 64, 128} x warps {2, 4, 8}
-         x register cap {none, 64, 80, 96, 128} around the best
+         x register cap {none, 80, 96, 128} around the best, then source
+         look-ahead (n_buffers) {1, 3, 4} rows against the default 2
 Time per run: CUDA events on the launching stream, mean over `reps` runs
 after 3 warm-up runs (inputs and outputs of 268 MB each exceed the L2).
 HBM fraction: (input + output bytes) / time / the measured copy bandwidth.
@@ -100,7 +101,10 @@ def study(name, reps, stream, flush, log):
     run_grid(grid1)
     best = min(rows, key=lambda r: r[0])[1]
     grid2 = [dict(best, tile_h=t, warps_per_block=w, max_regs=r)
-             for t, w, r in itertools.product((16, 64, 128), (2, 4, 8), (0, 64, 80, 96, 128))]
+             for t, w, r in itertools.product((16, 64, 128), (2, 4, 8), (0, 80, 96, 128))]
+    run_grid(grid2)
+    best = min(rows, key=lambda r: r[0])[1]
+    grid2 = [dict(best, n_buffers=b) for b in (1, 3, 4)]
     run_grid(grid2)
     torch.cuda.synchronize()
     ms, prm = min(rows, key=lambda r: r[0])

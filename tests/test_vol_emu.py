@@ -177,3 +177,13 @@ def test_staged_sixteen_bit(dtype):
                           params=[vparams(1, 2, 1, 4, staged=True)])
     assert d["name"].startswith("wt_vol_")
     assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= (2e-3 if dtype == "f16" else 1.6e-2)
+
+
+@pytest.mark.parametrize("staged", [False, True])
+@pytest.mark.parametrize("ahead", [1, 3, 5])
+def test_prefetch_distance(staged, ahead):
+    """n_buffers rows of look-ahead for the sources (1..8)."""
+    D, H, W = 6, 12, 140
+    spec = P.unsharp3d(depth=D)
+    img = rnd(50 + ahead, W, H, D)
+    check(spec, [img], [dict(vparams(1, 2, 1, 6, staged=staged), n_buffers=ahead)])
