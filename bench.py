@@ -56,8 +56,10 @@ WORKLOADS = {
 }
 VOLUME_DEPTH = 256
 # 3-D group parameters: the fastest of the 3-D study's sweep on one GB300
-VOLUME_PARAMS = {"unsharp3d": dict(tile_h=64, tile_o=4, vec=1, warps_per_block=4, max_regs=128, flags=32),
-                 "heat3d": dict(tile_h=128, tile_o=4, vec=1, warps_per_block=8, max_regs=96, flags=32)}
+VOLUME_PARAMS = {"unsharp3d": dict(tile_h=64, tile_o=4, vec=1, warps_per_block=4, max_regs=128, n_buffers=1,
+                                    flags=32),
+                 "heat3d": dict(tile_h=64, tile_o=4, vec=1, warps_per_block=2, max_regs=128, n_buffers=1,
+                                frac_reg=0.0, flags=32)}
 
 
 def spec_for(name):
