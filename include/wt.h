@@ -170,6 +170,14 @@ typedef struct {
  * 3-D kernel cannot take (other levels, parity or channel ops, fixed-
  * channel taps, windows above 224 registers) runs per stage.              */
 #define WT_FLAG_ZSTREAM 32
+/* Test only (failure detection without a GPU fault): in warp-tile group
+ * kernels the first staging chunk of every tile is armed for bytes that no
+ * copy delivers (no copy is issued for it, so nothing is in flight) and
+ * bounded waits give up after 256 polls.  Every warp's first wait times
+ * out, raises the error word and the warp drains its other copies and
+ * exits; the run writes no output and wt_check() returns WT_ETIMEOUT.
+ * Other kernel kinds ignore the flag.                                      */
+#define WT_FLAG_TEST_STALL 64
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */
@@ -432,23 +440,29 @@ wt_status wt_costmodel_load(const char *path);
  * cudaMalloc -- processes whose device memory is handed to their own
  * allocator up front under a fixed budget, and latency-critical paths where
  * cudaMalloc/cudaFree may synchronize the device.  Intermediates between
- * groups and the device status word live in one file-scope static device
- * array of 32 MiB, held by every GPU that loads the library until exit;
- * runs needing more than 32 MiB - 256 bytes of intermediates are rejected
- * with WT_EINVAL (single-group schedules need none).  The first call on a
- * device takes the array's address (cudaGetSymbolAddress).  It never
- * compiles or loads kernels, because loading code allocates device memory:
- * run the same schedule and image sizes/dtypes once with wt_run first,
- * else WT_EUNSUPPORTED.  Every call on a device shares the array and the
- * array keeps the last call's contents; each call clears the status word
- * on `stream`.  Calls whose work overlaps on the GPU (other streams, or
- * before an earlier call's kernels finished) race on the array.          */
+ * groups, the device status word and the tile-queue counters live in one
+ * file-scope static device array of 32 MiB, held by every GPU that loads
+ * the library until exit: a 4 KiB control block, then at most
+ * 32 MiB - 4 KiB of intermediates; runs needing more are rejected with
+ * WT_EINVAL (single-group schedules need none).  The first call on a device
+ * takes the array's address (cudaGetSymbolAddress).  It never compiles or
+ * loads kernels, because loading code allocates device memory: run the same
+ * schedule and image sizes/dtypes once with wt_run first, else
+ * WT_EUNSUPPORTED.  Every call on a device shares the array and the array
+ * keeps the last call's contents; each call clears the control block on
+ * `stream`.  Calls whose work overlaps on the GPU (other streams, or before
+ * an earlier call's kernels finished) race on the array.  Device-side
+ * failures (bounded waits, device checks) are reported by wt_check() of the
+ * pipeline, which reads the static status word once a wt_run_static call
+ * has run it on the current device.                                       */
 wt_status wt_run_static(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                         const wt_image *outputs, int32_t n_outputs, void *stream);
 
-/* Synchronizes `stream` and reads the device error word of the pipeline:
+/* Synchronizes `stream` and reads the device error word of the pipeline
+ * (and, after wt_run_static on the current device, the static scratch's
+ * status word, which every wt_run_static call on the device shares):
  * WT_ETIMEOUT if a bounded mbarrier/queue wait gave up, WT_EDEVICE for any
- * other device-side check; clears the word.                                */
+ * other device-side check; clears the words.                               */
 wt_status wt_check(wt_pipeline *p, void *stream);
 
 /* Number of kernel launches one wt_run issues with the installed schedule. */

@@ -79,6 +79,21 @@ wt_status wt_debug_layout(wt_pipeline *p, int32_t launch_index, const wt_image *
 wt_status wt_debug_group_geometry(wt_pipeline *p, int32_t group, int32_t vec, float frac_reg,
                                   int32_t *out, int32_t cap, int32_t *n_out);
 
+/* Failure injection for tests of the error paths (no GPU fault involved).
+ * kind 0: host allocation points (pipeline creation, run planning), which
+ * then fail as an out-of-memory condition; kind 1: the library's device
+ * allocations (workspace, control block, host-run staging, batch tables,
+ * cost-model and preprocessing buffers).  The allocation of that kind
+ * after `after` successful ones fails once, with WT_ENOMEM at the entry
+ * point; after < 0 disarms.  Process-wide, not thread-safe with respect to
+ * concurrent library calls.                                                */
+wt_status wt_debug_inject_alloc_failure(int32_t kind, int32_t after);
+
+/* Live pipelines (created, not destroyed) and device bytes the library
+ * holds in workspaces, staging buffers, batch tables and temporary
+ * buffers; either pointer may be null.  For leak tests.                     */
+wt_status wt_debug_live_objects(int64_t *pipelines, int64_t *device_bytes);
+
 #ifdef __cplusplus
 }
 #endif

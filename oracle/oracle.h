@@ -14,7 +14,7 @@
  *   the method must reach is the UNFUSED definition: evaluate every stage in
  *   topological order into a full array over its domain.
  *
- * Readings taken where the paper is silent (listed again in the design doc):
+ * Readings taken where the paper is silent:
  *   - Boundary: every producer read is clamped to the producer's domain
  *     (clamp-to-edge at every stage, not only at the input).
  *   - Sampling: a tap in DOWN2 mode reads P(2x+dx, 2y+dy); in UP2 mode it

@@ -15,6 +15,11 @@
 
 struct wt_pipeline : wt::Pipeline {};
 
+namespace wt {
+void inject_alloc_failure(int kind, int after);
+void live_objects(long long *pipelines, long long *device_bytes);
+}  // namespace wt
+
 namespace {
 using wt::fail;
 thread_local std::string g_err;
@@ -96,7 +101,7 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
         if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB | WT_FLAG_SMEM16 |
-                        WT_FLAG_ZSTREAM))
+                        WT_FLAG_ZSTREAM | WT_FLAG_TEST_STALL))
           fail(WT_EINVAL, "unknown flags");
         r.tile_o = q.tile_o;
         r.zstream = (q.flags & WT_FLAG_ZSTREAM) ? 1 : 0;
@@ -105,6 +110,7 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.otptb = (q.flags & WT_FLAG_OTPTB) ? 1 : 0;
         r.pairs = (q.flags & WT_FLAG_NO_PAIRS) ? 0 : 1;
         r.tile_split = (q.flags & WT_FLAG_NO_TILE_SPLIT) ? 0 : 1;
+        r.test_stall = (q.flags & WT_FLAG_TEST_STALL) ? 1 : 0;
       }
   } else {
     s.n_groups = n;
@@ -143,8 +149,10 @@ wt_status wt_pipeline_create(const wt_stage *stages, int32_t n_stages, const int
   return guard([&] {
     if (!out) wt::fail(WT_EINVAL, "null out");
     if (boundary != WT_BOUNDARY_CLAMP) wt::fail(WT_EUNSUPPORTED, "only the clamp-to-edge boundary is supported");
+    wt::host_alloc_point();
     auto p = std::make_unique<wt_pipeline>();
     wt::build_pipeline(*p, stages, n_stages, input_channels, n_inputs, outputs, n_outputs);
+    wt::host_alloc_point();
     default_schedule(*p);
     *out = p.release();
   });
@@ -196,7 +204,8 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].n_buffers = r.n_buffers;
         params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT) |
                           (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0) |
-                          (r.smem16 ? WT_FLAG_SMEM16 : 0) | (r.zstream ? WT_FLAG_ZSTREAM : 0);
+                          (r.smem16 ? WT_FLAG_SMEM16 : 0) | (r.zstream ? WT_FLAG_ZSTREAM : 0) |
+                          (r.test_stall ? WT_FLAG_TEST_STALL : 0);
         params[g].tile_o = r.tile_o;
       }
   });
@@ -422,11 +431,11 @@ wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, 
         w.clear_host_graphs();  // captured calls use the old buffers
         if (s.ptr) {
           wt::check_rt(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-          cudaFree(s.ptr);
+          wt::dev_free(s.ptr, (size_t)s.bytes);
           s.ptr = nullptr;
           s.bytes = 0;
         }
-        if (cudaMalloc(&s.ptr, (size_t)need) != cudaSuccess) {
+        if (wt::dev_alloc(&s.ptr, (size_t)need) != cudaSuccess) {
           cudaGetLastError();
           wt::fail(WT_ENOMEM, "cannot allocate staging buffer");
         }
@@ -516,12 +525,20 @@ wt_status wt_check(wt_pipeline *p, void *stream) {
   wt_status rc = guard([&] {
     if (!p) wt::fail(WT_EINVAL, "null pipeline");
     wt::check_rt(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
-    if (!p->ws) return;
-    int32_t v = 0;
-    wt::check_rt(cudaMemcpy(&v, p->ws->err, sizeof v, cudaMemcpyDeviceToHost), "cudaMemcpy(error word)");
-    if (v != 0) {
-      wt::check_rt(cudaMemset(p->ws->err, 0, sizeof v), "cudaMemset");
-      st = v == 1 ? WT_ETIMEOUT : WT_EDEVICE;
+    // the workspace's error word (wt_run, wt_run_batch, wt_run_host) and,
+    // after wt_run_static on this device, the static scratch's status word
+    int dev = 0;
+    wt::check_rt(cudaGetDevice(&dev), "cudaGetDevice");
+    int32_t *words[2] = {p->ws ? p->ws->err : nullptr,
+                         dev < 64 && (p->static_devs >> dev & 1) ? wt::static_status_word(dev) : nullptr};
+    for (int32_t *w : words) {
+      if (!w) continue;
+      int32_t v = 0;
+      wt::check_rt(cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost), "cudaMemcpy(error word)");
+      if (v != 0) {
+        wt::check_rt(cudaMemset(w, 0, sizeof v), "cudaMemset");
+        if (st == WT_OK) st = v == 1 ? WT_ETIMEOUT : WT_EDEVICE;
+      }
     }
   });
   if (rc != WT_OK) return rc;
@@ -723,6 +740,22 @@ wt_status wt_debug_group_geometry(wt_pipeline *p, int32_t group, int32_t vec, fl
     if (n_out) *n_out = (int32_t)v.size();
     if (out)
       for (int i = 0; i < (int)v.size() && i < cap; i++) out[i] = v[i];
+  });
+}
+
+wt_status wt_debug_inject_alloc_failure(int32_t kind, int32_t after) {
+  return guard([&] {
+    if (kind != wt::kAllocHost && kind != wt::kAllocDevice) wt::fail(WT_EINVAL, "kind must be 0 or 1");
+    wt::inject_alloc_failure(kind, after);
+  });
+}
+
+wt_status wt_debug_live_objects(int64_t *pipelines, int64_t *device_bytes) {
+  return guard([&] {
+    long long a = 0, b = 0;
+    wt::live_objects(&a, &b);
+    if (pipelines) *pipelines = a;
+    if (device_bytes) *device_bytes = b;
   });
 }
 

@@ -29,7 +29,7 @@ struct BatchCache {
   int64_t table_bytes = 0;
   CachedRun run;
   ~BatchCache() {
-    if (table) cudaFree(table);
+    dev_free(table, (size_t)table_bytes);
   }
 };
 
@@ -128,7 +128,7 @@ void run_batch(Pipeline &p, const wt_image *in, const wt_image *out, int n, cuda
   }
   auto bc = std::make_shared<BatchCache>();
   bc->device = dev;
-  if (cudaMalloc(&bc->table, (size_t)bytes) != cudaSuccess) {
+  if (dev_alloc(&bc->table, (size_t)bytes) != cudaSuccess) {
     cudaGetLastError();
     fail(WT_ENOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of batch tables");
   }

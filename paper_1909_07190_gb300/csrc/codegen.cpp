@@ -62,6 +62,7 @@ std::string CodegenKey::str() const {
   if (down) s << "|D" << tby;
   if (chain) s << "|R";
   if (vol) s << "|Z" << vol_split << "x" << vol_to << "x" << tby;
+  if (test_stall) s << "|STALL";
   return s.str();
 }
 
@@ -990,6 +991,8 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     kse_c = std::min(kse_c, c.kec[i]);
   }
   auto &o = c.o;
+  // test-only stall: bounded waits give up after a few polls
+  if (key.test_stall) o << "#define WT_WAIT_LIMIT 256\n";
   o << kDeviceSource;
   o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
   o << "#define CH " << L.chunk << "\n#define NB " << L.nbuf
@@ -1132,9 +1135,13 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
        "const int gc_ = cbase + c_;\nconst wt_u32 b_ = bar + 8u * (wt_u32)(gc_ % NB);\n"
        "wt_mbar_expect_tx(b_, "
     << L.chunk_bytes << "u);\n";
+  // (test-only stall: chunk 0 of every tile is armed but never copied, so
+  // its wait gives up with nothing in flight)
+  if (key.test_stall) o << "if (c_ != 0) {\n";
   for (int s = 0; s < n_src; s++)
     o << "wt_tma_load_3d(wt_smem_u32(rb" << s << " + (gc_ % NB) * BUFB" << s << "), &ia.tmap["
       << s << "], xb" << s << ", y_top + c_ * CH, zc" << s << ", b_);\n";
+  if (key.test_stall) o << "}\n";
   o << "}\nissued = c_ + 1;\n};\n";
   o << "for (int c_ = 0; c_ < NB - 1; c_++) if (c_ * CH < nrows) issue_chunk(c_);\n";
   (void)kss;

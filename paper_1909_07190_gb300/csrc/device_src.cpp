@@ -36,7 +36,9 @@ struct __align__(64) WtArgs {
 #define WT_FULL 0xffffffffu
 #define WT_ERR_TIMEOUT 1
 #define WT_ERR_BOUNDS 2
+#ifndef WT_WAIT_LIMIT
 #define WT_WAIT_LIMIT (1 << 22)
+#endif
 
 static __device__ __forceinline__ wt_u32 wt_smem_u32(const void *p) {
   return (wt_u32)__cvta_generic_to_shared(p);

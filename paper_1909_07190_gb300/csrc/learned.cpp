@@ -139,15 +139,14 @@ struct Rng {
 
 struct DevBuf {
   void *p = nullptr;
-  explicit DevBuf(size_t n) {
-    if (n && cudaMalloc(&p, n) != cudaSuccess) {
+  size_t bytes = 0;
+  explicit DevBuf(size_t n) : bytes(n) {
+    if (n && dev_alloc(&p, n) != cudaSuccess) {
       cudaGetLastError();
       fail(WT_ENOMEM, "cannot allocate " + std::to_string(n) + " bytes for the cost model");
     }
   }
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
+  ~DevBuf() { dev_free(p, bytes); }
   float *f() const { return (float *)p; }
   int *i() const { return (int *)p; }
 };

@@ -49,6 +49,12 @@ char *scratch_address(int dev) {
 
 namespace wt {
 
+int32_t *static_status_word(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return (int32_t *)g_base[dev];
+}
+
 // Launches a plan whose workspace is `base` and whose status word is `err`;
 // every kernel must already be loaded (loading code allocates device memory).
 static void run_plan_at(Pipeline &p, RunPlan &plan, char *base, int32_t *err, cudaStream_t stream, int dev) {
@@ -60,25 +66,7 @@ static void run_plan_at(Pipeline &p, RunPlan &plan, char *base, int32_t *err, cu
       fail(WT_EUNSUPPORTED,
            "group kernel " + L.kname + " is not loaded on this device; run the pipeline once with wt_run "
            "(same schedule, image sizes and dtypes) first, since loading kernel code allocates device memory");
-    if (L.fused) {
-      const Driver &drv = driver();
-      if (L.smem > 48 * 1024)
-        check_cu(drv.funcSetAttribute((CUfunction)k->function, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
-                                      L.smem),
-                 "cuFuncSetAttribute");
-      int per_sm = 0, sms = 0;
-      check_cu(drv.occupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (CUfunction)k->function, L.block,
-                                                             (size_t)L.smem),
-               "cuOccupancyMaxActiveBlocksPerMultiprocessor");
-      check_rt(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-      if (per_sm < 1) fail(WT_EUNSUPPORTED, "group kernel cannot be resident");
-      L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
-    }
-    KernelArgs a;
-    fill_args(p, plan, L, base, a, L.fused);
-    if (L.fused) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
-    a.err = err;
-    a.queue = queue_counters(err, li++);
+    KernelArgs a = launch_args(p, plan, L, *k, base, err, li++, dev);
     launch(L, *k, a, stream);
   }
 }
@@ -107,6 +95,7 @@ extern "C" wt_status wt_run_static(wt_pipeline *p, const wt_image *inputs, int32
     // intermediates need no clearing
     wt::check_rt(cudaMemsetAsync(base, 0, kStatusBytes, st), "cudaMemsetAsync(status word)");
     wt::run_plan_at(*p, plan, base + kStatusBytes, (int32_t *)base, st, dev);
+    p->static_devs |= uint64_t(1) << dev;
     wt::set_last_error("");
     return WT_OK;
   } catch (const wt::Error &e) {

@@ -7,6 +7,7 @@
 // caller's images, other stages in the pipeline's workspace.
 #include "wt_runtime.hpp"
 
+#include <atomic>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -57,6 +58,7 @@ static int pick_vec(const GroupParams &gp, const std::vector<int> &src_dtypes) {
 // -------------------------------------------------------------- planning
 
 RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out) {
+  host_alloc_point();
   if (n_in != (int)p.in_channels.size())
     fail(WT_EINVAL, "expected " + std::to_string(p.in_channels.size()) + " inputs");
   if (n_out != (int)p.outputs.size())
@@ -191,6 +193,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     key.chunk = L.params.chunk_rows > 0 ? L.params.chunk_rows : 8;
     key.nbuf = L.params.n_buffers > 0 ? L.params.n_buffers : 2;
     key.pairs = L.params.pairs != 0;
+    key.test_stall = L.params.test_stall != 0;
     key.even_rows = L.fused && L.geom.uses_ypar && L.params.tile_h % 2 == 0;
     L.src.clear();
     L.dst.clear();
@@ -518,6 +521,55 @@ void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream) {
            "cuLaunchKernel");
 }
 
+// ------------------------------------------------ allocation accounting
+
+namespace {
+std::atomic<int> g_inject_kind{-1};
+std::atomic<int> g_inject_after{-1};
+std::atomic<long long> g_device_bytes{0};
+std::atomic<long long> g_live_pipelines{0};
+
+// true once for the injected failure: the (after+1)-th point of that kind
+bool injected(int kind) {
+  if (g_inject_kind.load() != kind) return false;
+  if (g_inject_after.fetch_sub(1) != 0) return false;
+  g_inject_kind.store(-1);
+  return true;
+}
+}  // namespace
+
+void host_alloc_point() {
+  if (injected(kAllocHost)) throw std::bad_alloc();
+}
+
+int dev_alloc(void **ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (injected(kAllocDevice)) return (int)cudaErrorMemoryAllocation;
+  cudaError_t rc = cudaMalloc(ptr, bytes);
+  if (rc == cudaSuccess) g_device_bytes += (long long)bytes;
+  else *ptr = nullptr;
+  return (int)rc;
+}
+
+void dev_free(void *ptr, size_t bytes) {
+  if (!ptr) return;
+  cudaFree(ptr);
+  g_device_bytes -= (long long)bytes;
+}
+
+LiveCounter::LiveCounter() { g_live_pipelines++; }
+LiveCounter::~LiveCounter() { g_live_pipelines--; }
+
+void inject_alloc_failure(int kind, int after) {
+  g_inject_after.store(after);
+  g_inject_kind.store(after < 0 ? -1 : kind);
+}
+
+void live_objects(long long *pipelines, long long *device_bytes) {
+  if (pipelines) *pipelines = g_live_pipelines.load();
+  if (device_bytes) *device_bytes = g_device_bytes.load();
+}
+
 // ------------------------------------------------------------- workspace
 
 void Workspace::clear_host_graphs() {
@@ -528,10 +580,9 @@ void Workspace::clear_host_graphs() {
 
 Workspace::~Workspace() {
   clear_host_graphs();
-  if (base) cudaFree(base);
-  if (err) cudaFree(err);
-  for (auto &kv : staging)
-    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  dev_free(base, (size_t)bytes);
+  dev_free(err, kCtrlBytes);
+  for (auto &kv : staging) dev_free(kv.second.ptr, (size_t)kv.second.bytes);
   for (cudaStream_t s : band_stream)
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : band_events) cudaEventDestroy(e);
@@ -545,7 +596,10 @@ Workspace &workspace(Pipeline &p, int64_t bytes) {
     w->device = dev;
     // control block: error word at [0], then two tile-queue counters per
     // launch of a plan (zero between launches: the kernels reset them)
-    check_rt(cudaMalloc((void **)&w->err, kCtrlBytes), "cudaMalloc(control block)");
+    if (dev_alloc((void **)&w->err, kCtrlBytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(WT_ENOMEM, "cannot allocate the device control block");
+    }
     check_rt(cudaMemset(w->err, 0, kCtrlBytes), "cudaMemset");
     p.ws = w;
   }
@@ -553,11 +607,11 @@ Workspace &workspace(Pipeline &p, int64_t bytes) {
   if (bytes > w.bytes) {
     if (w.base) {
       check_rt(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
-      cudaFree(w.base);
+      dev_free(w.base, (size_t)w.bytes);
       w.base = nullptr;
       w.bytes = 0;
     }
-    if (cudaMalloc((void **)&w.base, (size_t)bytes) != cudaSuccess) {
+    if (dev_alloc((void **)&w.base, (size_t)bytes) != cudaSuccess) {
       cudaGetLastError();
       fail(WT_ENOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of workspace");
     }
@@ -599,6 +653,37 @@ static std::string cache_key(const wt_image *in, int n_in, const wt_image *out, 
   return k;
 }
 
+// Per-launch set-up that every path launching a plan shares: a warp-tile
+// kernel (persistent warps) gets no more blocks than can be resident at
+// once, its tensor maps and its two-level tile split; a block-tile kernel
+// keeps one block per tile.  Then the status word and the launch's queue
+// counters.
+KernelArgs launch_args(Pipeline &p, const RunPlan &plan, Launch &L, Kernel &k, char *ws, int32_t *err, int li,
+                       int dev) {
+  const bool persistent = L.fused && !L.key.otptb;
+  if (L.fused) {
+    const Driver &drv = driver();
+    if (L.smem > 48 * 1024)
+      check_cu(drv.funcSetAttribute((CUfunction)k.function, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                    L.smem),
+               "cuFuncSetAttribute");
+    int per_sm = 0, sms = 0;
+    check_cu(drv.occupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (CUfunction)k.function, L.block,
+                                                           (size_t)L.smem),
+             "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+    check_rt(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    if (per_sm < 1) fail(WT_EUNSUPPORTED, "group kernel cannot be resident (registers/shared memory)");
+    if (persistent) L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
+    L.resident_blocks_per_sm = per_sm;
+  }
+  KernelArgs a;
+  fill_args(p, plan, L, ws, a, persistent);
+  if (persistent) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
+  a.err = err;
+  a.queue = queue_counters(err, li);
+  return a;
+}
+
 void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string *key) {
   Workspace &w = workspace(p, plan.ws_bytes);
   int dev = w.device;
@@ -607,27 +692,7 @@ void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string
   int li = 0;
   for (Launch &L : plan.launches) {
     Kernel &k = get_kernel(p, L, dev);
-    if (L.fused) {
-      // persistent warps: no more blocks than can be resident at once
-      const Driver &drv = driver();
-      if (L.smem > 48 * 1024)
-        check_cu(drv.funcSetAttribute((CUfunction)k.function, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
-                                      L.smem),
-                 "cuFuncSetAttribute");
-      int per_sm = 0, sms = 0;
-      check_cu(drv.occupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (CUfunction)k.function, L.block,
-                                                             (size_t)L.smem),
-               "cuOccupancyMaxActiveBlocksPerMultiprocessor");
-      check_rt(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-      if (per_sm < 1) fail(WT_EUNSUPPORTED, "group kernel cannot be resident (registers/shared memory)");
-      if (!L.key.otptb) L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
-      L.resident_blocks_per_sm = per_sm;
-    }
-    KernelArgs a;
-    fill_args(p, plan, L, w.base, a, L.fused && !L.key.otptb);
-    if (L.fused && !L.key.otptb) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
-    a.err = w.err;
-    a.queue = queue_counters(w.err, li++);
+    KernelArgs a = launch_args(p, plan, L, k, w.base, w.err, li++, dev);
     launch(L, k, a, stream);
     c.functions.push_back(k.function);
     c.args.push_back(a);

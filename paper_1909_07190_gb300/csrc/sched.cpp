@@ -194,19 +194,34 @@ std::vector<StageStats> stage_stats(const Pipeline &p, bool measure) {
     return r;
   }
   const Driver &drv = driver();
-  float *out = nullptr;
-  check_rt(cudaMalloc((void **)&out, 256 * sizeof(float)), "cudaMalloc(preprocessing)");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  // device buffer, events and the current module are released on every
+  // exit, errors included
+  struct Res {
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUmodule mod = nullptr;
+    ~Res() {
+      if (mod) driver().moduleUnload(mod);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      dev_free(out, 256 * sizeof(float));
+    }
+  } res;
+  if (dev_alloc((void **)&res.out, 256 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(WT_ENOMEM, "cannot allocate the preprocessing buffer");
+  }
+  float *out = res.out;
+  check_rt(cudaEventCreate(&res.e0), "cudaEventCreate");
+  check_rt(cudaEventCreate(&res.e1), "cudaEventCreate");
+  cudaEvent_t e0 = res.e0, e1 = res.e1;
   for (size_t s = 0; s < p.stages.size(); s++) {
     char nm[64];
     snprintf(nm, sizeof nm, "wt_micro_%016llx_%zu", (unsigned long long)p.hash, s);
     std::string cubin = compile_cubin(micro_source(p, (int)s, nm), nm, 0);
-    CUmodule mod;
-    check_cu(drv.moduleLoadData(&mod, cubin.data()), "cuModuleLoadData(micro)");
+    check_cu(drv.moduleLoadData(&res.mod, cubin.data()), "cuModuleLoadData(micro)");
     CUfunction f;
-    check_cu(drv.moduleGetFunction(&f, mod, nm), "cuModuleGetFunction(micro)");
+    check_cu(drv.moduleGetFunction(&f, res.mod, nm), "cuModuleGetFunction(micro)");
     int iters = 1 << 16;
     void *args[] = {&out, &iters};
     // one block, one thread (Sec. 6): the time of one stage iteration
@@ -220,12 +235,10 @@ std::vector<StageStats> stage_stats(const Pipeline &p, bool measure) {
     r[s].ns_per_iter = (double)ms * 1e6 / iters;
     int regs = 0;
     if (drv.funcGetAttribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, f) == CUDA_SUCCESS && regs > 0) r[s].regs = regs;
-    drv.moduleUnload(mod);
+    drv.moduleUnload(res.mod);
+    res.mod = nullptr;
     r[s].measured = true;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(out);
   return r;
 }
 

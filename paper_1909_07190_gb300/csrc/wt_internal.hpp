@@ -34,6 +34,23 @@ struct Error {
 };
 [[noreturn]] void fail(wt_status code, const std::string &msg);
 
+// Allocation points (runtime.cpp).  A test can make the n-th allocation of
+// one kind fail (wt_debug_inject_alloc_failure): host points throw
+// std::bad_alloc (WT_ENOMEM at the C boundary), device allocations go
+// through dev_alloc/dev_free, which also count the device bytes the
+// library holds.
+constexpr int kAllocHost = 0, kAllocDevice = 1;
+void host_alloc_point();
+int dev_alloc(void **ptr, size_t bytes);  // cudaError_t
+void dev_free(void *ptr, size_t bytes);
+// Live pipelines (a count kept for leak tests).
+struct LiveCounter {
+  LiveCounter();
+  ~LiveCounter();
+  LiveCounter(const LiveCounter &) = delete;
+  LiveCounter &operator=(const LiveCounter &) = delete;
+};
+
 struct Op {
   int op = 0, slot = 0, dx = 0, dy = 0, chan = -1, mode = 0;
   float value = 0.f;
@@ -76,6 +93,7 @@ struct GroupParams {
                        // tiling the paper compares against)
   int tile_o = 0;      // 3-D groups: planes (rows when streaming planes) per tile
   int zstream = 0;     // 3-D groups: stream along planes instead of rows
+  int test_stall = 0;  // test only: every tile's first staging wait gives up
 };
 
 struct Schedule {
@@ -240,6 +258,10 @@ struct Pipeline {
   // iteration of its body alone and registers; empty until measured
   std::vector<double> pre_ns;
   std::vector<int> pre_regs;
+  // devices (bit d) on which wt_run_static ran this pipeline: wt_check then
+  // also reads the status word of the library's static scratch there
+  uint64_t static_devs = 0;
+  LiveCounter live;
 };
 
 // ir.cpp
@@ -266,6 +288,9 @@ struct CodegenKey {
   bool plain = false;
   bool persistent = false;
   bool pairs = true;  // packed f32x2 arithmetic
+  // test only (WT_FLAG_TEST_STALL): the first chunk of every tile is armed
+  // for bytes no copy delivers, and waits give up after a few polls
+  bool test_stall = false;
   // every tile starts on an even row and the unroll is even: the row parity
   // of each unrolled step is a compile-time constant
   bool even_rows = false;

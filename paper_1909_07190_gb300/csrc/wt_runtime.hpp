@@ -91,7 +91,14 @@ Kernel &get_kernel(const Pipeline &p, const Launch &L, int device);
 Kernel *find_kernel(const Pipeline &p, const Launch &L, int device);
 void set_last_error(const std::string &msg);
 void launch(const Launch &L, Kernel &k, KernelArgs &a, cudaStream_t stream);
+// Per-launch set-up shared by every path that launches a plan (grid of the
+// persistent kernels, tensor maps, tile split, status word, queue counters).
+KernelArgs launch_args(Pipeline &p, const RunPlan &plan, Launch &L, Kernel &k, char *ws, int32_t *err, int li,
+                       int dev);
 Workspace &workspace(Pipeline &p, int64_t bytes);
+// Status word of wt_run_static's scratch on device `dev` (noalloc.cu), or
+// null if no wt_run_static call has set it up there.
+int32_t *static_status_word(int dev);
 void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string *cache_key = nullptr);
 // The cached launches of an earlier run with these images, or null.
 const CachedRun *cached_run(const Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out);

@@ -21,6 +21,7 @@ WT_EXEC_FUSED, WT_EXEC_PLAIN = 0, 1
 WT_MODEL_ANALYTIC, WT_MODEL_LEARNED = 0, 1
 WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT, WT_FLAG_PLAIN, WT_FLAG_OTPTB, WT_FLAG_SMEM16 = 1, 2, 4, 8, 16
 WT_FLAG_ZSTREAM = 32
+WT_FLAG_TEST_STALL = 64
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
            "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14,
            "tapz": 15}
@@ -134,6 +135,8 @@ SIGNATURES = [
     ("wt_debug_compile", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i64)]),
     ("wt_debug_layout", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
+    ("wt_debug_inject_alloc_failure", _i32, [_i32, _i32]),
+    ("wt_debug_live_objects", _i32, [_P(_i64), _P(_i64)]),
 ]
 
 _lock = threading.Lock()
@@ -651,3 +654,18 @@ def costmodel_save(path):
 
 def costmodel_load(path):
     check(load().wt_costmodel_load(str(path).encode()))
+
+
+# ------------------------------------------------------ failure injection
+
+def inject_alloc_failure(kind, after):
+    """Makes the library's allocation of `kind` (0 host, 1 device) after
+    `after` successful ones fail once (after < 0 disarms)."""
+    check(load().wt_debug_inject_alloc_failure(kind, after))
+
+
+def live_objects():
+    """(live pipelines, device bytes held by the library)."""
+    a, b = _i64(), _i64()
+    check(load().wt_debug_live_objects(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

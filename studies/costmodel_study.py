@@ -2,7 +2,7 @@
 train the MLP, and score its schedule picks on held-out schedules against
 exhaustive timing and the analytic model.
 
-  python -m paper_1909_07190_gb300.costmodel_study [--schedules 2000] [--out study.json]
+  python studies/costmodel_study.py [--schedules 2000] [--out study.json]
                                                    [--model model.txt]
 
 Pipelines: the 3-stage sharpen on 2048x2048 and the 11-stage corner response
@@ -28,9 +28,11 @@ import time
 
 import numpy as np
 
-from . import inputs as I
-from . import pipelines as P
-from . import wt
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_1909_07190_gb300 import inputs as I  # noqa: E402
+from paper_1909_07190_gb300 import pipelines as P  # noqa: E402
+from paper_1909_07190_gb300 import wt  # noqa: E402
 
 TILES = (4, 8, 16, 32)
 FRACS = (1.0, 0.5, 0.0)

@@ -3,7 +3,7 @@
 OTPW+RT against OTPTB), with both tilings generated by this library from
 the same group analysis.
 
-  python -m paper_1909_07190_gb300.otptb_study [--pipelines harris,sharpen,blur_rgb] [--reps 20]
+  python studies/otptb_study.py [--pipelines harris,sharpen,blur_rgb] [--reps 20]
 
 Arms, each one fused group over the whole pipeline unless noted:
   plain  per-stage kernels, intermediates in HBM (the unfused baseline)
@@ -25,11 +25,14 @@ from __future__ import annotations
 import argparse
 import itertools
 import json
+import os
 import sys
 
-from . import inputs as I
-from . import pipelines as P
-from . import wt
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_1909_07190_gb300 import inputs as I  # noqa: E402
+from paper_1909_07190_gb300 import pipelines as P  # noqa: E402
+from paper_1909_07190_gb300 import wt  # noqa: E402
 
 SIZES = {"harris": (4096, 4096), "sharpen": (2048, 2048), "blur_rgb": (4096, 4096), "blur": (4096, 4096)}
 OTPTB_GRID = [dict(vec=v, tile_h=t, warps_per_block=w, flags=wt.WT_FLAG_OTPTB)

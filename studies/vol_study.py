@@ -2,7 +2,7 @@
 warp-tile kernel over volumes against the unfused per-stage path, with the
 split (streamed) axis along rows or along planes.
 
-  python -m paper_1909_07190_gb300.vol_study [--pipelines unsharp3d,heat3d] [--reps 20] [--out f.json]
+  python studies/vol_study.py [--pipelines unsharp3d,heat3d] [--reps 20] [--out f.json]
 
 Workloads: 512 x 512 x 256 FP32 volumes (67.1 M voxels, 268 MB), uniform
 [0, 1) from a seed: the 3-D unsharp mask (5-tap binomial blur along x, y
@@ -31,10 +31,12 @@ import json
 import os
 import sys
 
-from . import inputs as I
-from . import pipelines as P
-from . import wt
-from .otptb_study import time_run
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_1909_07190_gb300 import inputs as I  # noqa: E402
+from paper_1909_07190_gb300 import pipelines as P  # noqa: E402
+from paper_1909_07190_gb300 import wt  # noqa: E402
+from otptb_study import time_run  # noqa: E402
 
 W, H, D = 512, 512, 256
 

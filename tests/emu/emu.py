@@ -97,10 +97,11 @@ def _register(lib, images, workspace=None):
         lib.wt_emu_register(workspace.ctypes.data, workspace.nbytes)
 
 
-def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None, workspace=None):
+def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None, workspace=None, allow_err=False):
     """inputs/outputs: HostImage lists.  Runs launch `index` of the plan
     (with at most `max_blocks` blocks: persistent warps then take several
-    tiles each)."""
+    tiles each).  allow_err: a raised error word is returned in d["err"]
+    instead of failing (the tile queue must still be reset)."""
     ii = [x.image() for x in inputs]
     oo = [x.image() for x in outputs]
     ws = None if workspace is None else (workspace.ctypes.data, workspace.nbytes)
@@ -125,10 +126,11 @@ def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None, works
     rc = lib.wt_emu_run(kfn, ctypes.addressof(abuf), gx, gy, gz, d["block"], d["smem"], msg, 512)
     if rc != 0:
         raise RuntimeError("emulated kernel failed: " + msg.value.decode())
-    if err[0] != 0:
+    if err[0] != 0 and not allow_err:
         raise RuntimeError("emulated kernel raised error word %d" % err[0])
     if d["fused"] and (queue[0] != 0 or queue[1] != 0):
         raise RuntimeError("tile queue not reset at kernel exit: %s" % queue)
+    d["err"] = int(err[0])
     return d
 
 

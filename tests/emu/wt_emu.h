@@ -111,7 +111,11 @@ static inline wt_u32 wt_smem_u32(const void *p) {
 static inline unsigned char *wt_emu_sptr(wt_u32 a) { return wt_emu_smem() + a; }
 
 // ------------------------------------------------------ mbarrier / TMA
-// An emulated mbarrier keeps its completed-phase count in the first 4 bytes.
+// An emulated mbarrier keeps its completed-phase count in the first 4 bytes
+// and the transaction bytes still expected in the current phase in the next
+// 4 (arrival count 1: one arrive.expect_tx per phase).  A phase completes
+// when its arrival has happened and every expected byte has been copied, so
+// a phase armed for bytes that no copy delivers never completes.
 static inline void wt_mbar_init(wt_u32 bar, wt_u32) {
   wt_emu_check(wt_emu_sptr(bar), 8, "mbarrier");
   memset(wt_emu_sptr(bar), 0, 8);
@@ -119,12 +123,21 @@ static inline void wt_mbar_init(wt_u32 bar, wt_u32) {
 static inline void wt_fence_mbar_init() {}
 static inline void wt_fence_proxy_async() {}
 static inline void wt_tmap_acquire(const void *) {}
-static inline void wt_mbar_expect_tx(wt_u32 bar, wt_u32) {
-  // the copies that follow complete synchronously: finish the phase now
-  int32_t ph;
+static inline void wt_emu_mbar_tx(wt_u32 bar, int32_t delta) {
+  int32_t ph, tx;
   memcpy(&ph, wt_emu_sptr(bar), 4);
-  ph++;
+  memcpy(&tx, wt_emu_sptr(bar) + 4, 4);
+  tx += delta;
+  if (tx < 0) wt_emu_fail("mbarrier: more bytes copied than expected");
+  if (tx == 0) ph++;
   memcpy(wt_emu_sptr(bar), &ph, 4);
+  memcpy(wt_emu_sptr(bar) + 4, &tx, 4);
+}
+static inline void wt_mbar_expect_tx(wt_u32 bar, wt_u32 bytes) {
+  int32_t tx;
+  memcpy(&tx, wt_emu_sptr(bar) + 4, 4);
+  if (tx != 0) wt_emu_fail("mbarrier armed again before its phase completed");
+  wt_emu_mbar_tx(bar, (int32_t)bytes);
 }
 static inline wt_u32 wt_mbar_try_wait(wt_u32 bar, wt_u32 parity) {
   int32_t ph;
@@ -162,6 +175,8 @@ static inline void wt_tma_load_3d(wt_u32 dst, const WtTmap *map, int x, int y, i
         memcpy(o, s, t.esz);
       }
     }
+  // the whole box counts towards the barrier's transaction bytes
+  wt_emu_mbar_tx(bar, -(int32_t)((long)t.boxw * t.boxh * t.esz));
 }
 
 // ------------------------------------------------------ conversions

@@ -224,3 +224,43 @@ def test_16bit_shared_windows(frac, dtype):
                    params=[dict(tile_h=16, frac_reg=frac, flags=wt.WT_FLAG_SMEM16)])[0][0]
     ref = oracle_out(spec, [img])[0]
     assert np.abs(got - ref).max() <= TOL[dtype] * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name,dtype,W,H", [("harris", "f32", 4096, 4096), ("harris", "f16", 4096, 4096),
+                                            ("sharpen", "f32", 2048, 2048)])
+def test_bench_default_schedule_full_size_sampled(name, dtype, W, H):
+    """The schedule bench.py times (the library's default, installed at
+    pipeline creation) at the benchmark's full size, sampled against the
+    oracle point by point: the four corners, points along all four edges,
+    points on both sides of the warp tiles' seams in x and y, rows of the
+    band of short tiles at the top (the persistent queue's last round), and
+    several hundred random interior points.  The image spans many times the
+    resident warps, so warps take several tiles each."""
+    wt = wtmod()
+    spec = P.by_name(name)
+    img = rnd(I.SEED_BASE + (2 if name == "harris" else 1), W, H, dtype=dtype)
+    p = wt.Pipeline(spec)
+    prm = p.schedule_get()["params"][0]
+    src = wt.DeviceImage(1, H, W, wt.DTYPES[dtype]).upload(img)
+    dst = wt.DeviceImage(1, H, W, wt.DTYPES[dtype])
+    p.run([src.image()], [dst.image()], stream())
+    p.check(stream())
+    got = dst.download()[0]
+    rng = np.random.default_rng(7)
+    T = prm["tile_h"]
+    ow = p.debug_layout(0, [src.image()], [dst.image()])["out_w"]
+    pts = [(0, 0), (W - 1, 0), (0, H - 1), (W - 1, H - 1)]
+    for t in np.linspace(0, 1, 25):
+        pts += [(int(t * (W - 1)), 0), (int(t * (W - 1)), H - 1), (0, int(t * (H - 1))), (W - 1, int(t * (H - 1))),
+                (int(t * (W - 1)), 1), (W - 2, int(t * (H - 1)))]
+    for k in range(1, 12):                       # tile seams in x and y
+        x, y = k * ow, k * T
+        pts += [(x - 1, int(rng.integers(0, H))), (x, int(rng.integers(0, H))),
+                (int(rng.integers(0, W)), y - 1), (int(rng.integers(0, W)), y)]
+    pts += [(int(rng.integers(0, W)), int(rng.integers(0, 600))) for _ in range(150)]   # short-tile band
+    pts += [(int(rng.integers(0, W)), int(rng.integers(0, H))) for _ in range(400)]
+    xs = np.array([q[0] for q in pts])
+    ys = np.array([q[1] for q in pts])
+    ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys)
+    assert np.isfinite(got[ys, xs]).all()
+    assert np.abs(got[ys, xs] - ref).max() <= TOL[dtype]

@@ -161,6 +161,55 @@ def test_sobel_and_box_equal_separable_passes():
     assert np.abs(box - two_pass).max() < 1e-14
 
 
+# ------------------------------------------------- sharpen's output stage
+
+def _sharpen_numpy(img):
+    """The configuration's definition, written with numpy alone: a 5x5
+    binomial blur with numpy's edge padding as clamp-to-edge, then
+    clamp(in + 1.5 (in - blur), 0, 1)."""
+    blur = corr2_edge(img, np.outer(B5, B5))
+    return np.clip(img + 1.5 * (img - blur), 0.0, 1.0)
+
+
+def test_sharpen_step_edge_gain_and_clamp_by_hand():
+    """A vertical step from 0.2 to 0.8: along a row the blur is the 1-D
+    binomial of the step (rows are constant), so every output column has a
+    closed form.  At the two columns beside the edge the unclamped value
+    leaves [0, 1] (the clamp engages at both ends); one column further out
+    it stays inside and shows the 1.5 gain."""
+    img = np.tile(np.where(np.arange(12) < 6, 0.2, 0.8), (9, 1))
+    out = run(P.sharpen(), [img])[0][0]
+    lo, hi = 0.2, 0.8
+    # blur at columns 4, 5 | 6, 7 (edge between 5 and 6), weights /16
+    blur = {4: (15 * lo + 1 * hi) / 16, 5: (11 * lo + 5 * hi) / 16,
+            6: (5 * lo + 11 * hi) / 16, 7: (1 * lo + 15 * hi) / 16}
+    raw = {x: img[0, x] + 1.5 * (img[0, x] - b) for x, b in blur.items()}
+    assert raw[5] < 0.0 and raw[6] > 1.0          # both clamps engage
+    assert 0.0 < raw[4] < 1.0 and 0.0 < raw[7] < 1.0
+    want = {4: lo - 1.5 * (hi - lo) / 16, 5: 0.0, 6: 1.0, 7: hi + 1.5 * (hi - lo) / 16}
+    assert abs(raw[4] - want[4]) < 1e-15 and abs(raw[7] - want[7]) < 1e-15
+    for x, v in want.items():
+        assert np.abs(out[:, x] - v).max() < 1e-15, (x, out[0, x], v)
+    # far from the edge the image is constant: out = in
+    assert np.abs(out[:, :3] - lo).max() < 1e-15 and np.abs(out[:, 9:] - hi).max() < 1e-15
+
+
+@pytest.mark.parametrize("w,h,seed", [(23, 17, 1), (40, 9, 2)])
+def test_sharpen_matches_numpy_definition(w, h, seed):
+    """Random images scaled beyond [0, 1]'s middle so that the clamp engages
+    at both ends, and a 0/1 checkerboard of 3x3 cells (every pixel near a
+    cell edge clamps)."""
+    img = np.clip(rnd(seed, w, h)[0] * 1.4 - 0.2, 0.0, 1.0)
+    want = _sharpen_numpy(img)
+    raw = img + 1.5 * (img - corr2_edge(img, np.outer(B5, B5)))
+    assert (raw < 0).any() and (raw > 1).any()
+    assert np.abs(run(P.sharpen(), [img])[0][0] - want).max() < 1e-14
+    assert np.abs(O.sharpen(img) - want).max() < 1e-14
+    yy, xx = np.mgrid[0:h, 0:w]
+    board = (((yy // 3) + (xx // 3)) % 2).astype(np.float64)
+    assert np.abs(run(P.sharpen(), [board])[0][0] - _sharpen_numpy(board)).max() < 1e-14
+
+
 # ---------------------------------------------------------------- ramps
 
 def ramp(w, h, a, b, c):
