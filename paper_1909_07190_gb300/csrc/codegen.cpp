@@ -142,9 +142,20 @@ struct Ctx {
   // gather-source values loaded for the stage being emitted:
   // (gather node, element, dx, dy) -> variable
   std::map<std::tuple<int, int, int, int>, std::string> gvar;
+  // blocks choose their body by their rows (groups without gather sources):
+  // STEADY or XEDGE where every row the block touches is inside the image
+  bool rowsafe_blocks = false;
   Ctx(const Pipeline &p_, const GroupGeom &g_, const CodegenKey &k_, const FusedLayout &L_)
       : p(p_), g(g_), key(k_), L(L_) {}
 };
+
+// Step bodies of the fused kernel.  STEADY: no guards (every row the block
+// touches is inside the image, the tile inside it along x).  XEDGE: rows
+// inside the image, the tile crossing the left or right image edge: edge
+// columns replicated (clamp-to-edge along x) and stores checked against W.
+// GUARDED: rows may leave the image (top and bottom tiles, steps past the
+// tile): per-node step ranges, row clamps and edge-row replication too.
+enum { STEADY = 0, XEDGE = 1, GUARDED = 2 };
 
 std::string reg(int ni, int slot, int j) {
   return "R" + std::to_string(ni) + "_" + std::to_string(slot) + "_" + std::to_string(j);
@@ -230,36 +241,38 @@ std::string ring_row(int s, const std::string &ri) {
 }
 
 // Row of a register-resident source, loaded from the TMA ring.
-void emit_source_row(Ctx &c, int ni, bool safe, int u) {
+void emit_source_row(Ctx &c, int ni, int mode, int u) {
   const Node &n = c.g.nodes[ni];
   auto &o = c.o;
   const int V = c.V;
   int s = n.src_index;
+  const bool rows = mode == GUARDED;
   emit_shift(c, ni);
   o << "{\n";
-  if (safe) o << "if (k < nsrc) {\n";
-  if (safe) o << "const int ri = wt_clampi(y_top + k, 0, H - 1) - y_top;\n";
+  if (rows) o << "if (k < nsrc) {\n";
+  if (rows) o << "const int ri = wt_clampi(y_top + k, 0, H - 1) - y_top;\n";
   std::vector<std::string> v = names("e", V);
   o << "float";
   for (int e = 0; e < V; e++) o << (e ? ", " : " ") << v[e];
   o << ";\n";
-  // guard-free steps read row kb + u of the chunk that block kb starts
+  // unguarded steps read row kb + u of the chunk that block kb starts
   // (chunks are a multiple of U rows): the block's row pointer plus u rows
   const std::string S = std::to_string(s);
-  emit_load_vec(c, c.key.src_dtypes[s], safe ? ring_row(s, "ri") : "rp" + S + " + " + std::to_string(u) + " * ROWB" + S,
+  emit_load_vec(c, c.key.src_dtypes[s], rows ? ring_row(s, "ri") : "rp" + S + " + " + std::to_string(u) + " * ROWB" + S,
                 v, c.L.esz[s]);
-  if (safe) emit_xfix(c, v);
+  if (mode != STEADY) emit_xfix(c, v);
   int sl = slot_of(n, u, 0);
   emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
-  if (safe) o << "}\n";
+  if (rows) o << "}\n";
   o << "}\n";
 }
 
 // Loads row (age a) of a shared-memory node into temporaries T<ni>_<a>_*.
-void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
+void emit_load_tmp(Ctx &c, int ni, int a, int mode) {
   const Node &n = c.g.nodes[ni];
   auto &o = c.o;
   const int V = c.V;
+  const bool rows = mode == GUARDED;
   o << "{\n";
   std::vector<std::string> v = names("q", V);
   o << "float";
@@ -268,12 +281,12 @@ void emit_load_tmp(Ctx &c, int ni, int a, bool safe) {
   if (n.is_source) {
     int s = n.src_index;
     o << "int ri = k - " << a << ";\n";
-    if (safe) o << "ri = wt_clampi(y_top + ri, 0, H - 1) - y_top;\n";
+    if (rows) o << "ri = wt_clampi(y_top + ri, 0, H - 1) - y_top;\n";
     emit_load_vec(c, c.key.src_dtypes[s], ring_row(s, "ri"), v, c.L.esz[s]);
-    if (safe) emit_xfix(c, v);
+    if (mode != STEADY) emit_xfix(c, v);
   } else {
     o << "int kk = k - " << a << ";\n";
-    if (safe)
+    if (rows)
       o << "{ const int rr = wt_clampi(y_top + kk - (" << n.delay << "), 0, H - 1); kk = rr - y_top + ("
         << n.delay << "); }\n";
     o << "const int sl = ((kk % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
@@ -794,18 +807,45 @@ std::vector<std::pair<int, int>> smem_reads(Ctx &c, int ni_c) {
   return r;
 }
 
-void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
+void emit_store(Ctx &c, int ni, int mode, int u, const std::vector<std::string> &v) {
   const Node &n = c.g.nodes[ni];
   auto &o = c.o;
   const int V = c.V;
   int dt = c.key.dst_dtypes.at(n.dst_index);
   int esz = elem_bytes(dt);
+  const std::string D = std::to_string(n.dst_index);
+  const std::string one_ch = n.channels == 1 && c.g.channels > 1 ? " && ch == 0" : "";
   o << "{\n";
-  if (!safe) {
+  if (c.rowsafe_blocks && mode != GUARDED) {
+    // rows inside the image: the row test is r - y0 = k - halo_t - delay in
+    // [0, T), one unsigned compare; the row address is the block's row
+    // pointer plus u rows
+    o << "if ((unsigned)(kb + (" << u - c.g.halo_t - n.delay << ")) < (unsigned)T" << one_ch << ") {\n";
+    o << "unsigned char *op_ = obk" << D << " + " << u << " * opitch" << D << ";\n";
+    if (mode == STEADY) {
+      o << "if (st_lane) {\n";
+      for (int b = 0; b < V; b += 4)
+        o << "wt_st4_" << dtype_name(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", "
+          << v[b + 2] << ", " << v[b + 3] << ");\n";
+      o << "} } }\n";
+      return;
+    }
+    o << "const int x = xs + lane * " << V << ";\n";
+    o << "if (st_lane) {\n";
+    o << "if (x + " << V << " <= W) {\n";
+    for (int b = 0; b < V; b += 4)
+      o << "wt_st4_" << dtype_name(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", " << v[b + 2]
+        << ", " << v[b + 3] << ");\n";
+    o << "} else {\n";
+    for (int e = 0; e < V; e++)
+      o << "if (x + " << e << " < W) wt_st1_" << dtype_name(dt) << "(op_ + " << e * esz << ", " << v[e] << ");\n";
+    o << "} } } }\n";
+    return;
+  }
+  if (mode != GUARDED) {
     // per-tile row base and lane predicate: the conditional part is the
     // store alone
-    std::string D = std::to_string(n.dst_index);
-    o << "if (r >= y0 && r < y0 + T" << (n.channels == 1 && c.g.channels > 1 ? " && ch == 0" : "") << ") {\n";
+    o << "if (r >= y0 && r < y0 + T" << one_ch << ") {\n";
     o << "unsigned char *op_ = ob" << D << " + (wt_i64)r * ia.dst[" << D << "].pitch;\n";
     o << "if (st_lane) {\n";
     for (int b = 0; b < V; b += 4)
@@ -814,34 +854,28 @@ void emit_store(Ctx &c, int ni, bool safe, const std::vector<std::string> &v) {
     o << "} } }\n";
     return;
   }
-  if (safe) o << "if (r >= y0 && r < y0 + T && r < H)\n";
+  o << "if (r >= y0 && r < y0 + T && r < H)\n";
   if (n.channels == 1 && c.g.channels > 1) o << "if (ch == 0)\n";
   o << "{ const int x = xs + lane * " << V << ";\n";
   o << "if (lane >= " << c.L.lpad / V << " && lane < " << 32 - c.L.rpad / V << ") {\n";
-  std::string d = "ia.dst[" + std::to_string(n.dst_index) + "]";
+  std::string d = "ia.dst[" + D + "]";
   o << "unsigned char *op_ = (unsigned char *)" << d << ".ptr + (wt_i64)"
     << (n.channels > 1 ? "ch" : "0") << " * " << d << ".plane + (wt_i64)r * " << d
     << ".pitch + (wt_i64)x * " << esz << ";\n";
-  auto vec_store = [&]() {
-    for (int b = 0; b < V; b += 4)
-      o << "wt_st4_" << dtype_name(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", "
-        << v[b + 2] << ", " << v[b + 3] << ");\n";
-  };
-  if (!safe) {
-    vec_store();
-  } else {
-    o << "if (x + " << V << " <= W) {\n";
-    vec_store();
-    o << "} else {\n";
-    for (int e = 0; e < V; e++)
-      o << "if (x + " << e << " < W) wt_st1_" << dtype_name(dt) << "(op_ + " << e * esz << ", " << v[e]
-        << ");\n";
-    o << "}\n";
-  }
+  o << "if (x + " << V << " <= W) {\n";
+  for (int b = 0; b < V; b += 4)
+    o << "wt_st4_" << dtype_name(dt) << "(op_ + " << b * esz << ", " << v[b] << ", " << v[b + 1] << ", "
+      << v[b + 2] << ", " << v[b + 3] << ");\n";
+  o << "} else {\n";
+  for (int e = 0; e < V; e++)
+    o << "if (x + " << e << " < W) wt_st1_" << dtype_name(dt) << "(op_ + " << e * esz << ", " << v[e]
+      << ");\n";
+  o << "}\n";
   o << "} } }\n";
 }
 
-void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> &loaded) {
+void emit_stage(Ctx &c, int ni, int mode, int u, std::set<std::pair<int, int>> &loaded) {
+  const bool safe = mode == GUARDED;
   const Node &n = c.g.nodes[ni];
   auto &o = c.o;
   const int V = c.V;
@@ -853,7 +887,7 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
   o << "(void)r;\n";
   for (auto &pr : smem_reads(c, ni)) {
     if (!safe && loaded.count(pr)) continue;
-    emit_load_tmp(c, pr.first, pr.second, safe);
+    emit_load_tmp(c, pr.first, pr.second, mode);
     if (!safe) loaded.insert(pr);
   }
   std::vector<std::string> v = names("v", V);
@@ -874,6 +908,7 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
   }
   if (safe) emit_gather_prologue(c, ni);
   else if (!emit_gwin_step(c, ni, u)) emit_gather_prologue_fast(c, ni);
+  if (mode == XEDGE && !c.gvar.empty()) fail(WT_EINVAL, "internal: x-edge body with gather sources");
   // packed pairs for nodes whose taps all read the producer's own element
   // pairs (dx = 0): a pair shifted by one column would have to be gathered
   // into an aligned register pair first
@@ -888,8 +923,8 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
   } else {
     for (int e = 0; e < V; e++) o << v[e] << " = " << emit_expr(c, ni, e, u) << ";\n";
   }
-  if (safe) {
-    o << "}\n";
+  if (safe) o << "}\n";
+  if (mode != STEADY) {
     // Columns outside the image must hold the edge column's value.  A node
     // computed from edge-replicated producers by taps without an x offset
     // (pointwise or vertical) and without the column parity is replicated
@@ -920,16 +955,17 @@ void emit_stage(Ctx &c, int ni, bool safe, int u, std::set<std::pair<int, int>> 
       o << "}\n";
     }
   }
-  if (n.is_liveout) emit_store(c, ni, safe, v);
+  if (n.is_liveout) emit_store(c, ni, mode, u, v);
   o << "}\n";
   if (safe) o << "}\n";
 }
 
-void emit_step(Ctx &c, bool safe, int u) {
+void emit_step(Ctx &c, int mode, int u) {
   auto &o = c.o;
-  o << "{ // step phase " << u << (safe ? " (guarded)" : " (steady)") << "\n";
+  static const char *names_[3] = {" (steady)", " (x edge)", " (guarded)"};
+  o << "{ // step phase " << u << names_[mode] << "\n";
   o << "const int k = kb + " << u << ";\n";
-  if (safe) o << "if (k >= nsteps) goto wt_tile_end;\n";
+  if (mode == GUARDED) o << "if (k >= nsteps) goto wt_tile_end;\n";
   // temporaries for shared-memory windows used this step
   std::set<std::pair<int, int>> all;
   for (int ni : c.g.order) {
@@ -946,10 +982,10 @@ void emit_step(Ctx &c, bool safe, int u) {
   for (int ni : c.g.order) {
     const Node &n = c.g.nodes[ni];
     if (n.is_source) {
-      if (!n.in_smem) emit_source_row(c, ni, safe, u);
+      if (!n.in_smem) emit_source_row(c, ni, mode, u);
       continue;
     }
-    emit_stage(c, ni, safe, u, loaded);
+    emit_stage(c, ni, mode, u, loaded);
   }
   o << "}\n";
 }
@@ -1003,6 +1039,13 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // -maxrregcount): enough resident blocks that each thread gets <= max_regs
   int min_blocks = 1;
   if (key.max_regs > 0) min_blocks = std::max(1, 65536 / (key.max_regs * 32 * key.nw));
+  if (!key.persistent)
+    o << "static __device__ __forceinline__ void wt_tile_coords(const WtArgs &a, int tile, int &tx, int &ch, int &y0,"
+         " int &T) {\n"
+         "if (tile < a.n_big) { tx = tile % a.tiles_x; const int tr_ = tile / a.tiles_x;"
+         " y0 = a.ty2 * a.tile_h2 + (tr_ % a.ty1) * a.tile_h; ch = tr_ / a.ty1; T = a.tile_h; }\n"
+         "else { const int j_ = tile - a.n_big; tx = j_ % a.tiles_x; const int tr_ = j_ / a.tiles_x;"
+         " y0 = (tr_ % a.ty2) * a.tile_h2; ch = tr_ / a.ty2; T = a.tile_h2; }\n}\n";
   o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", " << min_blocks << ") " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
   o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
@@ -1045,10 +1088,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     // before them, not in the final round
     o << "const WtArgs &ia = a;\n";
     o << "int tx, ch, y0, T;\n";
-    o << "if (tile < a.n_big) { tx = tile % a.tiles_x; const int tr_ = tile / a.tiles_x;"
-         " y0 = a.ty2 * a.tile_h2 + (tr_ % a.ty1) * a.tile_h; ch = tr_ / a.ty1; T = a.tile_h; }\n"
-         "else { const int j_ = tile - a.n_big; tx = j_ % a.tiles_x; const int tr_ = j_ / a.tiles_x;"
-         " y0 = (tr_ % a.ty2) * a.tile_h2; ch = tr_ / a.ty2; T = a.tile_h2; }\n";
+    o << "wt_tile_coords(a, tile, tx, ch, y0, T);\n";
   }
   if (key.persistent) {
     o << "const int T = ia.tile_h, y0 = ty * T;\n";
@@ -1075,6 +1115,33 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
         << ";\n(void)ob" << D << ";\n";
     }
   o << "bool border = xs < 0 || xs + " << 32 * V << " > W || y_top < 0 || y0 + T + " << HB << " > H;\n";
+  c.rowsafe_blocks = g.n_gather == 0;
+  if (c.rowsafe_blocks) {
+    // Unguarded blocks need every row they read inside the image: block kb
+    // reads rows down to y_top + kb - margin (the deepest row a node reads
+    // above its own, delay included) and computes source rows up to
+    // y_top + kb + U - 1 (only rows past the tile's last needed source row,
+    // never stored, may leave the image).
+    int margin = 0;
+    for (size_t i = 0; i < g.nodes.size(); i++) {
+      const Node &n = g.nodes[i];
+      if (n.is_source) continue;
+      int dmin = 0;
+      for (const NodeEdge &e : g.edges)
+        if (e.c == (int)i) dmin = std::min(dmin, e.dymin);
+      margin = std::max(margin, n.delay - dmin);
+    }
+    o << "const int kb_lo_ = " << margin << " - y_top;\n";
+    o << "const int kb_hi_ = y0 + T + " << HB << " <= H ? 0x7fffffff : H - " << c.U << " - y_top;\n";
+    o << "const bool xedge_ = xs < 0 || xs + " << 32 * V << " > W;\n";
+    for (const Node &n : g.nodes)
+      if (n.is_liveout) {
+        const std::string D = std::to_string(n.dst_index);
+        o << "const wt_i64 opitch" << D << " = ia.dst[" << D << "].pitch;\n";
+        o << "unsigned char *obt" << D << " = ob" << D << " + (wt_i64)(y_top - " << n.delay << ") * opitch" << D
+          << ";\n";
+      }
+  }
   // Gather sources: the guard-free body reads them unclamped, in aligned
   // pairs, at every row it computes (garbage rows included: k from 0 to
   // the last unrolled step), so a tile whose footprint reaches past a
@@ -1165,14 +1232,38 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
        " const int gc_ = cbase + kch_; const int ok_ = wt_mbar_wait(bar + 8u * (wt_u32)(gc_ % NB),"
        " (wt_u32)((gc_ / NB) & 1), a.err); if (!__all_sync(WT_FULL, ok_)) { failc = kch_; goto wt_fail; } }\n"
        "if (kc_ == ISSUE) { const int c_ = kch_ + NB - 1; if (c_ * CH < nrows) issue_chunk(c_); }\n";
-  o << "if (!border) {\n";
-  for (int s = 0; s < n_src; s++)
-    o << "const unsigned char *rp" << s << " = lp" << s << " + ((cbase + kch_) % NB) * BUFB" << s << " + kc_ * ROWB"
-      << s << ";\n";
-  for (int u = 0; u < c.U; u++) emit_step(c, false, u);
-  o << "} else {\n";
-  for (int u = 0; u < c.U; u++) emit_step(c, true, u);
-  o << "}\n";
+  auto ring_ptrs = [&]() {
+    for (int s = 0; s < n_src; s++)
+      o << "const unsigned char *rp" << s << " = lp" << s << " + ((cbase + kch_) % NB) * BUFB" << s << " + kc_ * ROWB"
+        << s << ";\n";
+  };
+  if (c.rowsafe_blocks) {
+    // the block's body by its rows: unguarded when every row it touches is
+    // inside the image (x-edge fix-ups in tiles crossing the left or right
+    // edge), guarded otherwise (the first blocks of top tiles, the last
+    // blocks of bottom tiles)
+    o << "if (kb >= kb_lo_ && kb <= kb_hi_) {\n";
+    ring_ptrs();
+    for (const Node &n : g.nodes)
+      if (n.is_liveout) {
+        const std::string D = std::to_string(n.dst_index);
+        o << "unsigned char *obk" << D << " = obt" << D << " + (wt_i64)kb * opitch" << D << ";\n";
+      }
+    o << "if (!xedge_) {\n";
+    for (int u = 0; u < c.U; u++) emit_step(c, STEADY, u);
+    o << "} else {\n";
+    for (int u = 0; u < c.U; u++) emit_step(c, XEDGE, u);
+    o << "}\n} else {\n";
+    for (int u = 0; u < c.U; u++) emit_step(c, GUARDED, u);
+    o << "}\n";
+  } else {
+    o << "if (!border) {\n";
+    ring_ptrs();
+    for (int u = 0; u < c.U; u++) emit_step(c, STEADY, u);
+    o << "} else {\n";
+    for (int u = 0; u < c.U; u++) emit_step(c, GUARDED, u);
+    o << "}\n";
+  }
   o << "kc_ += U;\nif (kc_ == CH) { kc_ = 0; kch_++; }\n";
   o << "}\n";
   o << "wt_tile_end:;\n";

@@ -287,3 +287,20 @@ def test_fused_16bit_shared_windows(name, dtype, tol, frac):
     _, d32 = run_emulated(spec, [img32], params=[prm])
     _, d32b = run_emulated(spec, [img32], params=[dict(tile_h=8, frac_reg=frac)])
     assert d32["name"] == d32b["name"]
+
+
+@pytest.mark.parametrize("name", ["harris", "sharpen"])
+@pytest.mark.parametrize("frac", [1.0, 0.5, 0.0])
+@pytest.mark.parametrize("tile_h", [9, 30])
+def test_block_bodies_by_rows(name, frac, tile_h):
+    """Tall tiles whose blocks change body mid-tile: guarded blocks at the top
+    and bottom of the image, unguarded blocks in between, with x-edge
+    fix-ups in the tiles crossing the left or right edge (including the
+    top-left and bottom-right corners), and register or shared-memory
+    windows carried across the switches."""
+    spec = P.by_name(name)
+    img = rnd(77 + tile_h, 380, 150)
+    got, _ = run_emulated(spec, [img], params=[dict(tile_h=tile_h, frac_reg=frac, warps_per_block=2)],
+                          max_blocks=3)
+    ref = oracle_of(spec, [img])
+    assert np.abs(got[0] - ref[0]).max() <= 1e-5
