@@ -45,7 +45,7 @@ BatchPlan build_batch(Pipeline &p, const wt_image *in, const wt_image *out, int 
   BatchPlan b;
   b.img.reserve(n);
   for (int i = 0; i < n; i++) {
-    b.img.push_back(build_plan(p, in + (size_t)i * n_in, n_in, out + (size_t)i * n_out, n_out));
+    b.img.push_back(build_plan(p, in + (size_t)i * n_in, n_in, out + (size_t)i * n_out, n_out, true));
     const RunPlan &r = b.img.back();
     const RunPlan &r0 = b.img[0];
     if (i == 0) {

@@ -145,6 +145,10 @@ struct Ctx {
   // blocks choose their body by their rows (groups without gather sources):
   // STEADY or XEDGE where every row the block touches is inside the image
   bool rowsafe_blocks = false;
+  // clamp-to-edge along x at the reads (every node's halo at most one
+  // lane wide): edge tiles keep garbage in columns outside the image and
+  // redirect each horizontal read that crosses the edge to the edge column
+  bool edge_reads = false;
   Ctx(const Pipeline &p_, const GroupGeom &g_, const CodegenKey &k_, const FusedLayout &L_)
       : p(p_), g(g_), key(k_), L(L_) {}
 };
@@ -172,37 +176,69 @@ int slot_of(const Node &n, int u, int a) {
 
 int width_of(const Node &n, int V) { return V + n.xl + n.xr; }
 
-// x-fixup of the values `v` (clamp-to-edge along x inside border tiles).
+// x-fixup of the values `v` (clamp-to-edge along x inside border tiles):
+// columns left of 0 take column 0's value, columns right of W - 1 take
+// column W - 1's.  The tile's constants (xl0_: lanes left of column 0;
+// xrl_, xre_: lane and element of column W - 1; fixr_: this lane's
+// elements right of it) are computed once per tile; both branches are
+// uniform across the warp and the replacements are selects.
 void emit_xfix(Ctx &c, const std::vector<std::string> &v) {
   const int V = c.V;
   auto &o = c.o;
-  o << "if (xs < 0) { const int l0_ = (-xs) / " << V << "; const float b0_ = __shfl_sync(WT_FULL, "
-    << v[0] << ", l0_); if (lane < l0_) {";
-  for (int e = 0; e < V; e++) o << " " << v[e] << " = b0_;";
-  o << " } }\n";
-  o << "if (xs + " << 32 * V << " > W) { const int xl_ = W - 1 - xs; const int ll_ = xl_ / " << V
-    << "; const int el_ = xl_ - ll_ * " << V << "; float s_ = " << v[0] << ";";
-  for (int e = 1; e < V; e++) o << " if (el_ == " << e << ") s_ = " << v[e] << ";";
-  o << " const float bl_ = __shfl_sync(WT_FULL, s_, ll_); const int xb_ = xs + lane * " << V << ";";
-  for (int e = 0; e < V; e++) o << " if (xb_ + " << e << " > W - 1) " << v[e] << " = bl_;";
+  o << "if (xl0_ > 0) { const float b0_ = __shfl_sync(WT_FULL, " << v[0] << ", xl0_);";
+  for (int e = 0; e < V; e++) o << " " << v[e] << " = lane < xl0_ ? b0_ : " << v[e] << ";";
+  o << " }\n";
+  o << "if (xrl_ < 32) { float s_ = " << v[0] << ";";
+  for (int e = 1; e < V; e++) o << " s_ = xre_ == " << e << " ? " << v[e] << " : s_;";
+  o << " const float bl_ = __shfl_sync(WT_FULL, s_, xrl_);";
+  for (int e = 0; e < V; e++) o << " " << v[e] << " = (fixr_ >> " << e << ") & 1 ? bl_ : " << v[e] << ";";
   o << " }\n";
 }
 
-// Neighbour columns by warp shuffles: type (3) loads of Sec. 5.
+// Neighbour columns by warp shuffles: type (3) loads of Sec. 5.  In edge
+// tiles with reads redirected at the edge (edge = true): the lane holding
+// column 0 takes its own column 0 for every column left of it, the lane
+// holding column W - 1 its own column W - 1 (edge_v_) for every column
+// right of it; other lanes' out-of-image columns are never read.
 void emit_extend(Ctx &c, const Node &n, const std::vector<std::string> &v,
-                 const std::function<std::string(int)> &tgt) {
+                 const std::function<std::string(int)> &tgt, bool edge = false) {
   const int V = c.V;
   for (int off = -n.xl; off < 0; off++) {
     int q = -((-off + V - 1) / V);
     int el = off - q * V;
-    c.o << tgt(n.xl + off) << " = __shfl_up_sync(WT_FULL, " << v[el] << ", " << -q << ");\n";
+    if (edge)  // every lane takes part in the shuffle, then selects
+      c.o << "{ const float t_ = __shfl_up_sync(WT_FULL, " << v[el] << ", " << -q << "); " << tgt(n.xl + off)
+          << " = fxl_ ? " << v[0] << " : t_; }\n";
+    else
+      c.o << tgt(n.xl + off) << " = __shfl_up_sync(WT_FULL, " << v[el] << ", " << -q << ");\n";
   }
   for (int off = V; off < V + n.xr; off++) {
     int q = off / V;
     int el = off - q * V;
-    c.o << tgt(n.xl + off) << " = __shfl_down_sync(WT_FULL, " << v[el] << ", " << q << ");\n";
+    if (edge)
+      c.o << "{ const float t_ = __shfl_down_sync(WT_FULL, " << v[el] << ", " << q << "); " << tgt(n.xl + off)
+          << " = fxr_ ? edge_v_ : t_; }\n";
+    else
+      c.o << tgt(n.xl + off) << " = __shfl_down_sync(WT_FULL, " << v[el] << ", " << q << ");\n";
   }
   for (int e = 0; e < V; e++) c.o << tgt(n.xl + e) << " = " << v[e] << ";\n";
+}
+
+// Right image edge inside a lane: the elements of the lane holding column
+// W - 1 past that column take its value (edge_v_, also the lane's right
+// halo), so that reads across the edge see the edge column.  Opens a scope
+// that the caller closes after emit_extend.
+void emit_edge_open(Ctx &c, const Node &n, const std::vector<std::string> &v) {
+  const int V = c.V;
+  auto &o = c.o;
+  // column W - 1 at a lane's last element (W a multiple of V): no element
+  // of that lane lies past it, only its right halo does
+  o << "{ float edge_v_ = " << v[V - 1] << ";\n";
+  if (n.xr <= 0) return;
+  o << "if (xrl_ < 32 && xre_ != " << V - 1 << ") {";
+  for (int e = 0; e < V - 1; e++) o << " edge_v_ = xre_ == " << e << " ? " << v[e] << " : edge_v_;";
+  for (int e = 0; e < V; e++) o << " " << v[e] << " = (fixr_ >> " << e << ") & 1 ? edge_v_ : " << v[e] << ";";
+  o << " }\n";
 }
 
 void emit_load_vec(Ctx &c, int dtype, const std::string &addr, const std::vector<std::string> &v,
@@ -260,9 +296,15 @@ void emit_source_row(Ctx &c, int ni, int mode, int u) {
   const std::string S = std::to_string(s);
   emit_load_vec(c, c.key.src_dtypes[s], rows ? ring_row(s, "ri") : "rp" + S + " + " + std::to_string(u) + " * ROWB" + S,
                 v, c.L.esz[s]);
-  if (mode != STEADY) emit_xfix(c, v);
   int sl = slot_of(n, u, 0);
-  emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
+  if (mode != STEADY && c.edge_reads) {
+    emit_edge_open(c, n, v);
+    emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); }, true);
+    o << "}\n";
+  } else {
+    if (mode != STEADY) emit_xfix(c, v);
+    emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
+  }
   if (rows) o << "}\n";
   o << "}\n";
 }
@@ -283,7 +325,7 @@ void emit_load_tmp(Ctx &c, int ni, int a, int mode) {
     o << "int ri = k - " << a << ";\n";
     if (rows) o << "ri = wt_clampi(y_top + ri, 0, H - 1) - y_top;\n";
     emit_load_vec(c, c.key.src_dtypes[s], ring_row(s, "ri"), v, c.L.esz[s]);
-    if (mode != STEADY) emit_xfix(c, v);
+    if (mode != STEADY && !c.edge_reads) emit_xfix(c, v);
   } else {
     o << "int kk = k - " << a << ";\n";
     if (rows)
@@ -293,7 +335,13 @@ void emit_load_tmp(Ctx &c, int ni, int a, int mode) {
     emit_load_vec(c, c.key.win_dtype, "sp" + std::to_string(ni) + " + sl * " +
                       std::to_string(32 * V * elem_bytes(c.key.win_dtype)), v, elem_bytes(c.key.win_dtype));
   }
-  emit_extend(c, n, v, [&](int j) { return tmp(ni, a, j); });
+  if (mode != STEADY && c.edge_reads) {
+    emit_edge_open(c, n, v);
+    emit_extend(c, n, v, [&](int j) { return tmp(ni, a, j); }, true);
+    o << "}\n";
+  } else {
+    emit_extend(c, n, v, [&](int j) { return tmp(ni, a, j); });
+  }
   o << "}\n";
 }
 
@@ -874,6 +922,49 @@ void emit_store(Ctx &c, int ni, int mode, int u, const std::vector<std::string> 
   o << "} } }\n";
 }
 
+// A node that sums n >= 3 horizontally consecutive values of one producer
+// row with unit weights (a box filter's row pass): adjacent outputs share
+// all but one term, so each pair of elements costs n + 1 additions
+// instead of 2 (n - 1).  Returns false for other programs.
+bool emit_box_row(Ctx &c, int ni, int u, const std::vector<std::string> &v) {
+  const Node &n = c.g.nodes[ni];
+  if (c.V % 2) return false;
+  int prod = -1, a = 1 << 20, b = -(1 << 20), taps = 0, adds = 0;
+  for (const KOp &op : n.prog) {
+    if (op.op == WT_OP_TAP) {
+      if (op.dy != 0 || (prod >= 0 && op.node != prod)) return false;
+      prod = op.node;
+      a = std::min(a, op.dx);
+      b = std::max(b, op.dx);
+      taps++;
+    } else if (op.op == WT_OP_ADD) {
+      adds++;
+    } else {
+      return false;
+    }
+  }
+  if (prod < 0 || taps < 3 || adds != taps - 1 || b - a + 1 != taps) return false;
+  const Node &pn = c.g.nodes[prod];
+  if (pn.gather_mode) return false;
+  std::set<int> seen;
+  for (const KOp &op : n.prog)
+    if (op.op == WT_OP_TAP && !seen.insert(op.dx).second) return false;  // repeated tap: weight 2
+  const int age = n.delay - pn.delay;
+  auto val = [&](int j) {
+    if (j < 0 || j >= width_of(pn, c.V)) fail(WT_EINVAL, "internal: tap column out of range");
+    return pn.in_smem ? tmp(prod, age, j) : reg(prod, slot_of(pn, u, age), j);
+  };
+  for (int e = 0; e < c.V; e += 2) {
+    // shared terms of elements e and e + 1: columns e + a + 1 .. e + b
+    std::string sh = val(pn.xl + e + a + 1);
+    for (int d = a + 2; d <= b; d++) sh = "(" + sh + " + " + val(pn.xl + e + d) + ")";
+    c.o << "{ const float sh_ = " << sh << ";\n";
+    c.o << v[e] << " = " << val(pn.xl + e + a) << " + sh_;\n";
+    c.o << v[e + 1] << " = sh_ + " << val(pn.xl + e + 1 + b) << ";\n}\n";
+  }
+  return true;
+}
+
 void emit_stage(Ctx &c, int ni, int mode, int u, std::set<std::pair<int, int>> &loaded) {
   const bool safe = mode == GUARDED;
   const Node &n = c.g.nodes[ni];
@@ -920,7 +1011,7 @@ void emit_stage(Ctx &c, int ni, int mode, int u, std::set<std::pair<int, int>> &
     o << "{\n";
     for (int e = 0; e < V; e += 2) emit_pair(c, ni, e, u, v, tmpid);
     o << "}\n";
-  } else {
+  } else if (!emit_box_row(c, ni, u, v)) {
     for (int e = 0; e < V; e++) o << v[e] << " = " << emit_expr(c, ni, e, u) << ";\n";
   }
   if (safe) o << "}\n";
@@ -933,7 +1024,7 @@ void emit_stage(Ctx &c, int ni, int mode, int u, std::set<std::pair<int, int>> &
     for (const KOp &op : n.prog)
       if ((op.op == WT_OP_TAP && (op.dx != 0 || c.g.nodes[op.node].gather_mode)) || op.op == WT_OP_XPAR)
         xdep = true;
-    if (xdep) emit_xfix(c, v);
+    if (xdep && !c.edge_reads) emit_xfix(c, v);
   }
   if (n.in_smem) {
     o << "{ const int sl = ((k % " << n.window << ") + " << n.window << ") % " << n.window << ";\n";
@@ -944,7 +1035,13 @@ void emit_stage(Ctx &c, int ni, int mode, int u, std::set<std::pair<int, int>> &
     o << "}\n";
   } else {
     int sl = slot_of(n, u, 0);
-    emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
+    if (mode != STEADY && c.edge_reads) {
+      emit_edge_open(c, n, v);
+      emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); }, true);
+      o << "}\n";
+    } else {
+      emit_extend(c, n, v, [&](int j) { return reg(ni, sl, j); });
+    }
     if (safe && n.window > 1) {
       o << "if (r == 0) {\n";
       int wd = width_of(n, V);
@@ -1039,13 +1136,26 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // -maxrregcount): enough resident blocks that each thread gets <= max_regs
   int min_blocks = 1;
   if (key.max_regs > 0) min_blocks = std::max(1, 65536 / (key.max_regs * 32 * key.nw));
-  if (!key.persistent)
+  if (!key.persistent) {
+    // Tile order of the queue: tall tiles, then the band of short ones;
+    // within each, the tiles of the two edge columns first (their x-edge
+    // reads make them the slowest, and a slow tile handed out last would
+    // end the launch alone), then the others row by row, the last row (the
+    // image's bottom, guarded at its end) first.
+    o << "static __device__ __forceinline__ void wt_tile_order(int t, int tiles_x, int nrows, int &tx, int &tr) {\n"
+         "if (tiles_x < 3) { tx = t % tiles_x; tr = t / tiles_x; return; }\n"
+         "const int ne_ = 2 * nrows;\n"
+         "if (t < ne_) { tr = t >> 1; tx = (t & 1) ? tiles_x - 1 : 0; }\n"
+         "else { const int j_ = t - ne_; const int r_ = j_ / (tiles_x - 2); tx = 1 + j_ % (tiles_x - 2);"
+         " tr = r_ == 0 ? nrows - 1 : r_ - 1; }\n}\n";
     o << "static __device__ __forceinline__ void wt_tile_coords(const WtArgs &a, int tile, int &tx, int &ch, int &y0,"
          " int &T) {\n"
-         "if (tile < a.n_big) { tx = tile % a.tiles_x; const int tr_ = tile / a.tiles_x;"
+         "int tr_;\n"
+         "if (tile < a.n_big) { wt_tile_order(tile, a.tiles_x, a.n_big / a.tiles_x, tx, tr_);"
          " y0 = a.ty2 * a.tile_h2 + (tr_ % a.ty1) * a.tile_h; ch = tr_ / a.ty1; T = a.tile_h; }\n"
-         "else { const int j_ = tile - a.n_big; tx = j_ % a.tiles_x; const int tr_ = j_ / a.tiles_x;"
+         "else { wt_tile_order(tile - a.n_big, a.tiles_x, (a.n_tiles - a.n_big) / a.tiles_x, tx, tr_);"
          " y0 = (tr_ % a.ty2) * a.tile_h2; ch = tr_ / a.ty2; T = a.tile_h2; }\n}\n";
+  }
   o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * key.nw << ", " << min_blocks << ") " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
   o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
@@ -1089,9 +1199,11 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     o << "const WtArgs &ia = a;\n";
     o << "int tx, ch, y0, T;\n";
     o << "wt_tile_coords(a, tile, tx, ch, y0, T);\n";
+    // the last tile row is clipped by the image: no steps past its end
+    o << "T = min(T, a.H - y0);\n";
   }
   if (key.persistent) {
-    o << "const int T = ia.tile_h, y0 = ty * T;\n";
+    o << "const int y0 = ty * ia.tile_h;\nconst int T = min(ia.tile_h, ia.H - y0);\n";
     // the image's tensor maps, acquired when the warp moves to a new image
     // (tiles are listed image by image)
     o << "if (img != last_img_) {\nlast_img_ = img;\nif (lane == 0) {";
@@ -1106,6 +1218,18 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   o << "const int nrows = min(nsrc, H - y_top);\n";
   o << "const bool st_lane = lane >= " << L.lpad / V << " && lane < " << 32 - L.rpad / V << ";\n";
   o << "(void)st_lane;\n";
+  // clamp-to-edge along x (emit_xfix): xs is a multiple of V, so the
+  // columns left of 0 are whole lanes; column W - 1 lies in lane xrl_
+  // (32: right of the tile) at element xre_
+  o << "const int xl0_ = xs < 0 ? min(-xs / " << V << ", 31) : 0;\n";
+  o << "const int xr_ = W - 1 - xs;\n";
+  o << "const int xrl_ = xr_ < " << 32 * V - 1 << " ? xr_ / " << V << " : 32;\n";
+  o << "const int xre_ = xr_ - xrl_ * " << V << ";\n";
+  o << "int fixr_ = 0;\n";
+  o << "for (int e_ = 0; e_ < " << V << "; e_++) fixr_ |= (lane * " << V << " + e_ > xr_ ? 1 : 0) << e_;\n";
+  o << "const bool fxl_ = xs < 0 && lane == xl0_;\n";
+  o << "const bool fxr_ = lane == xrl_;\n";
+  o << "(void)xl0_; (void)xrl_; (void)xre_; (void)fixr_; (void)fxl_; (void)fxr_;\n";
   for (const Node &n : g.nodes)
     if (n.is_liveout) {
       std::string D = std::to_string(n.dst_index);
@@ -1116,6 +1240,9 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
     }
   o << "bool border = xs < 0 || xs + " << 32 * V << " > W || y_top < 0 || y0 + T + " << HB << " > H;\n";
   c.rowsafe_blocks = g.n_gather == 0;
+  c.edge_reads = true;
+  for (const Node &n : g.nodes)
+    if (!n.gather_mode && (n.xl > V || n.xr > V)) c.edge_reads = false;
   if (c.rowsafe_blocks) {
     // Unguarded blocks need every row they read inside the image: block kb
     // reads rows down to y_top + kb - margin (the deepest row a node reads

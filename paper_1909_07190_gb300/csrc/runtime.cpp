@@ -57,7 +57,7 @@ static int pick_vec(const GroupParams &gp, const std::vector<int> &src_dtypes) {
 
 // -------------------------------------------------------------- planning
 
-RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out) {
+RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out, bool batched) {
   host_alloc_point();
   if (n_in != (int)p.in_channels.size())
     fail(WT_EINVAL, "expected " + std::to_string(p.in_channels.size()) + " inputs");
@@ -250,6 +250,30 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       level_dims(plan.W, plan.H, L.geom.level, &L.W, &L.H);
       int th = std::max(1, L.params.tile_h);
       int tiles_x = (L.W + L.layout.out_w - 1) / L.layout.out_w;
+      if (!batched) {
+        // Images too small to give each resident warp about two tiles of
+        // this height run shorter tiles (same parity: the kernel's row-
+        // parity folding depends on it), so that every warp has work.
+        static int nsm = 0;
+        if (!nsm) {
+          int dev = 0, v = 0;
+          if (cudaGetDevice(&dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            nsm = v;
+          else
+            nsm = 152;
+          cudaGetLastError();
+        }
+        const int64_t want = 2ll * nsm * 12;  // tiles: about two per resident warp
+        const int64_t cols = (int64_t)tiles_x * L.geom.channels;
+        const int fit = (int)std::max<int64_t>(4, (int64_t)L.H * cols / want);
+        if (fit < th) {
+          int t = fit;
+          if ((t - th) % 2) t--;
+          th = std::max(th % 2 ? 3 : 4, t);
+          L.params.tile_h = th;
+        }
+      }
       int tiles_y = (L.H + th - 1) / th;
       int64_t nt = (int64_t)tiles_x * tiles_y * L.geom.channels;
       if (nt > (1ll << 30)) fail(WT_EUNSUPPORTED, "too many tiles");
@@ -362,9 +386,9 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   char hx[24];
   // the generator's version is part of the name: a kernel whose code
   // changes gets a new name (profiles and caches never mix versions)
-  static const char kCodegenVersion[] = "wt-codegen-16";
+  static const char kCodegenVersion[] = "wt-codegen-20";
   static const char kPlainVersion[] = "wt-plain-2";  // the per-stage kernel's own changes
-  static const char kBatchVersion[] = "wt-batch-13";  // the persistent variant's own changes
+  static const char kBatchVersion[] = "wt-batch-14";  // the persistent variant's own changes
   const std::string ks = key.str();
   uint64_t h = fnv1a(ks.data(), ks.size(), p.hash);
   h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);

@@ -78,7 +78,7 @@ struct Stage {
 };
 
 struct GroupParams {
-  int tile_h = 14;
+  int tile_h = 40;
   int warps_per_block = 2;
   float frac_reg = 1.f;
   int vec = 0;

@@ -79,7 +79,10 @@ struct Workspace {
 
 std::vector<std::vector<int>> schedule_groups(const Pipeline &p);
 GroupParams group_params(const Pipeline &p, int gi);
-RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out);
+// batched: one image of a batch (tile heights are not shortened for small
+// images: the batch's tiles share the resident warps)
+RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out,
+                   bool batched = false);
 std::string launch_source(const Pipeline &p, const Launch &L);
 // Entry-point name of a generated kernel (a hash of the pipeline, the
 // codegen key and the generator version).

@@ -261,7 +261,7 @@ class Pipeline:
         g = (_i32 * n)(*groups)
         prm = (wt_group_params * ng)()
         for i in range(ng):
-            d = dict(tile_h=14, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
+            d = dict(tile_h=40, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
                      n_buffers=0, flags=0)
             if params is not None:
                 d.update(params[i] if isinstance(params, (list, tuple)) else params)
@@ -370,7 +370,7 @@ class Pipeline:
             g = (_i32 * n)(*groups)
             prm = (wt_group_params * ng)()
             for i in range(ng):
-                d = dict(tile_h=14, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
+                d = dict(tile_h=40, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
                          n_buffers=0, flags=0)
                 if params is not None:
                     d.update(params[i] if isinstance(params, (list, tuple)) else params)
