@@ -94,9 +94,6 @@ def peaks():
         return 6800.0, "fallback"
 
 
-FP32_LANE_OPS = 152 * 128 * 2.07e9   # GB300: SMs x FP32 lanes x max SM clock (FMA = 1 op)
-
-
 def ops_per_pixel(spec):
     """FP32 operations of the stage programs per output pixel (level-0
     pixel; channels counted): the algorithmic ALU work of the pipeline."""
@@ -256,8 +253,7 @@ def run_reference(args, rank):
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H,
-                           "channels": 3, "storage": dt},
+                "config": workload_config(args.workload, spec, W, H, W * H),
                 "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                                  "sample": "one 1024x1024x3 blend per step"},
                 "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -265,6 +261,11 @@ def run_reference(args, rank):
         return
     if args.workload == "harris_batch":
         sizes = batch_sizes()
+        ref_config = workload_config(args.workload, spec, W, H, sum(w * h for w, h in sizes), len(sizes))
+    else:
+        ref_config = workload_config(args.workload, spec, W, H,
+                                     W * H * (VOLUME_DEPTH if name in ("unsharp3d", "heat3d") else 1))
+    if args.workload == "harris_batch":
         imgs = [I.round_to(I.uniform_image(seed * 1000 + i, w, h)[0], dt) for i, (w, h) in
                 enumerate(sizes[:max(1, args.steps + args.warmup)])]
         sample = "one image of the 512-image batch per step (its sizes in order)"
@@ -293,8 +294,7 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H,
-                       "channels": VOLUME_DEPTH if name in ("unsharp3d", "heat3d") else 1, "storage": dt},
+            "config": ref_config,
             "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -566,23 +566,44 @@ class Batch:
         return I.round_to(I.uniform_image(self.seed * 1000, w, h)[0], dts)
 
 
-def run_ours(args, rank, world, local):
-    import torch
-    from paper_1909_07190_gb300 import wt
+def workload_config(workload, spec, W, H, px, images=None):
+    """The workload's description, identical in both arms (the repo's kernels
+    and the oracle): what is computed, not how."""
+    name = WORKLOADS[workload][0]
+    cfg = {"workload": workload, "pipeline": name, "width": W, "height": H,
+           "channels": VOLUME_DEPTH if name in ("unsharp3d", "heat3d") else (3 if name == "blend" else 1),
+           "storage": WORKLOADS[workload][3], "stages": len(spec["stages"]), "pixels_per_step": px}
+    if images is not None:
+        cfg["images"] = images
+    return cfg
 
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    name, W, H, dts, seed = WORKLOADS[args.workload]
-    if args.size:
-        # a smaller square case of the same workload (profiling captures)
-        W = H = args.size
+
+def device_fp32_peak(clocks):
+    """FP32 lane operations per second of the device (an FMA counted once):
+    SMs x FP32 lanes per SM (the library's device query) x the maximum SM
+    clock (nvidia-smi's clocks.max.sm during the run, else the driver-written
+    measured peaks file)."""
+    from paper_1909_07190_gb300 import wt
+    cfg = wt.gpu_config(0)
+    mhz = (clocks or {}).get("sm_max_mhz")
+    if not mhz:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = float(json.load(f)["sm_max_mhz"])
+        except Exception:
+            mhz = None
+    if not mhz:
+        return None, cfg.nsms
+    return cfg.nsms * cfg.cores_per_sm * mhz * 1e6, cfg.nsms
+
+
+def make_work(wt, torch, workload, rank, local, size=0):
+    name, W, H, dts, seed = WORKLOADS[workload]
+    if size:
+        W = H = size
     dtype = wt.DTYPES[dts]
     spec = spec_for(name)
-    batched = args.workload == "harris_batch"
-    if batched:
+    if workload == "harris_batch":
         work = Batch(wt, torch, spec, dtype, seed + 7919 * rank)
     elif name == "blend":
         work = Blend(wt, torch, spec, W, H, dtype, seed + 7919 * rank)
@@ -592,30 +613,19 @@ def run_ours(args, rank, world, local):
         work = Volume(wt, torch, spec, W, H, dtype, seed + rank, local, name)
     else:
         work = Single(wt, torch, spec, W, H, dtype, seed + rank, local)
-    stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
+    return name, W, H, dts, spec, work
 
-    fused = wt.Pipeline(spec)
-    if hasattr(work, "schedule"):
-        work.schedule(fused, None)
-    if args.params:
-        prm = json.loads(args.params)
-        if name == "blend":
-            groups, params = P.blend_schedule()
-            fused.schedule(groups=groups, params=[dict(p, **prm) for p in params])
-        else:
-            fused.schedule(params=prm)
-    tune_t0 = time.perf_counter()
-    tune = args.tune == "on" or (args.tune == "auto" and batched)
-    tuning = None
-    if tune:
-        tuned_ms, n_timed = work.tune(fused, sp)
-        tuning = {"schedules_timed": n_timed, "tuned_ms": tuned_ms,
-                  "seconds": round(time.perf_counter() - tune_t0, 1)}
-    plain = wt.Pipeline(spec)
-    plain.schedule(exec_mode=wt.WT_EXEC_PLAIN)
 
-    def capture(step_fn, n):
+def timed_steps(torch, work, step_fn, steps, warmup, per_graph, dist, sampler=None):
+    """Kernel-only time of exactly `steps` steps: CUDA graphs of up to
+    `per_graph` back-to-back steps, replayed, CUDA events around the replays
+    on the capturing stream (no host work inside the region)."""
+    sp = torch.cuda.current_stream().cuda_stream
+    for i in range(max(warmup, getattr(work, "nsets", 1))):  # every buffer set once
+        step_fn(i, sp)
+    torch.cuda.synchronize()
+
+    def capture(n):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             cs = torch.cuda.current_stream().cuda_stream
@@ -623,121 +633,210 @@ def run_ours(args, rank, world, local):
                 step_fn(i, cs)
         return g
 
-    def timed(step_fn, steps, warmup, per_graph, sampler=None):
-        """Kernel-only time of exactly `steps` steps: CUDA graphs of up to
-        `per_graph` back-to-back steps, replayed, CUDA events around the
-        replays (no host work inside the region)."""
-        # every buffer set once (plans and tensor maps are cached per set)
-        for i in range(max(warmup, getattr(work, "nsets", 1))):
-            step_fn(i, sp)
+    n = min(per_graph, steps)
+    full, rem = divmod(steps, n)
+    g = capture(n)
+    gr = capture(rem) if rem else None
+    g.replay()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(full + 2)]
+    ctx = sampler if sampler is not None else _Null()
+    with ctx:
+        ev[0].record(cur)
+        for r in range(full):
+            g.replay()
+            ev[r + 1].record(cur)
+        if gr is not None:
+            gr.replay()
+        ev[full + 1].record(cur)
         torch.cuda.synchronize()
-        n = min(per_graph, steps)
-        full, rem = divmod(steps, n)
-        g = capture(step_fn, n)
-        gr = capture(step_fn, rem) if rem else None
-        g.replay()
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        cur = torch.cuda.current_stream()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(full + 2)]
-        ctx = sampler if sampler is not None else _Null()
-        with ctx:
-            ev[0].record(cur)
-            for r in range(full):
-                g.replay()
-                ev[r + 1].record(cur)
-            if gr is not None:
-                gr.replay()
-            ev[full + 1].record(cur)
-            torch.cuda.synchronize()
-        per = [ev[r].elapsed_time(ev[r + 1]) / n for r in range(full)]
-        total = max_over_ranks(ev[0].elapsed_time(ev[full + 1]), dist, "cuda")
-        if dist is not None:
-            dist.barrier()
-        return total, per
+    per = [ev[r].elapsed_time(ev[r + 1]) / n for r in range(full)]
+    total = max_over_ranks(ev[0].elapsed_time(ev[full + 1]), dist, "cuda")
+    if dist is not None:
+        dist.barrier()
+    return total, per
 
+
+def traffic_record(workload, kname):
+    """ncu figures of the kernel from the committed profile summary (DRAM
+    bytes and executed warp instructions per launch), used only when they
+    were taken on the kernel that ran here (same generated kernel name)."""
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(tpath)).get(workload)
+        if rec and rec.get("kernel") == kname:
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+def measure(wt, torch, workload, args, dist, world, rank, local, steps, warmup, cpu_seconds, size=0):
+    """One workload on this rank: fused rate, unfused rate, roofline of the
+    dominant kernel, end-to-end rate through the host-buffer call and the
+    oracle's CPU rate (rank 0 alone, cpu_seconds > 0)."""
+    name, W, H, dts, spec, work = make_work(wt, torch, workload, rank, local, size)
+    batched = workload == "harris_batch"
+    sp = torch.cuda.current_stream().cuda_stream
+    fused = wt.Pipeline(spec)
+    if hasattr(work, "schedule"):
+        work.schedule(fused, None)
+    if args.params and workload == args.workload:
+        prm = json.loads(args.params)
+        if name == "blend":
+            groups, params = P.blend_schedule()
+            fused.schedule(groups=groups, params=[dict(p, **prm) for p in params])
+        else:
+            fused.schedule(params=prm)
+    tuning = None
+    if args.tune == "on" or (args.tune == "auto" and batched):
+        t0 = time.perf_counter()
+        tuned_ms, n_timed = work.tune(fused, sp)
+        tuning = {"schedules_timed": n_timed, "tuned_ms": tuned_ms, "seconds": round(time.perf_counter() - t0, 1)}
     per_graph = 10 if batched else 100
     sampler = ClockSampler(local)
-    total_f, per_f = timed(lambda i, s: work.run(fused, i, s), args.steps, args.warmup, per_graph, sampler)
+    total_f, per_f = timed_steps(torch, work, lambda i, s: work.run(fused, i, s), steps, warmup, per_graph, dist,
+                                 sampler)
     clocks = sampler.summary()
     fused.check(sp)
     unfused = None
     if not batched:
-        plain_steps = max(3, args.steps // 8)
-        total_p, _ = timed(lambda i, s: work.run(plain, i, s), plain_steps, args.warmup, per_graph)
+        plain = wt.Pipeline(spec)
+        plain.schedule(exec_mode=wt.WT_EXEC_PLAIN)
+        plain_steps = max(3, steps // 8)
+        total_p, _ = timed_steps(torch, work, lambda i, s: work.run(plain, i, s), plain_steps, warmup, per_graph,
+                                 dist)
         plain.check(sp)
         unfused = {"value": job_rate(work.px, world, plain_steps, total_p), "unit": "Mpixels/s",
                    "ms_per_step": total_p / plain_steps, "launches_per_step": plain.launches_per_run()}
-
-    e2e_steps = max(3, min(200, args.steps // 4)) if not batched else 3
-    e2e_value, h2d, d2h = work.e2e(fused, sp, args.warmup if not batched else 1, e2e_steps)
-
-    value = job_rate(work.px, world, args.steps, total_f)
+        plain.close()
+    e2e_steps = max(3, min(200, steps // 4)) if not batched else 3
+    e2e_value, h2d, d2h = work.e2e(fused, sp, warmup if not batched else 1, e2e_steps)
+    value = job_rate(work.px, world, steps, total_f)
     launch_ms = statistics.mean(per_f)
     peak, peak_kind = peaks()
     launches = fused.launches_per_run()
     if hasattr(work, "dominant") and launches > 1:
-        # several launches per run: the roofline is the dominant launch's own
-        # bytes over its own event-timed duration; the whole run beside it
+        # several launches per run: the dominant launch's own bytes over its
+        # own event-timed duration; the whole run beside it
         kname, kbytes, kms, _ = work.dominant(fused, sp, spec)
-        achieved = kbytes / (kms / 1e3) / 1e9
-        run_roof = {"achieved": work.alg_bytes / (launch_ms / 1e3) / 1e9,
-                    "bytes_per_run": work.alg_bytes, "ms_per_run": launch_ms}
+        run_roof = {"achieved": work.alg_bytes / (launch_ms / 1e3) / 1e9, "bytes_per_run": work.alg_bytes,
+                    "ms_per_run": launch_ms, "frac": work.alg_bytes / (launch_ms / 1e3) / 1e9 / peak}
     else:
         kname, kbytes, kms = work.kernel_name(fused), work.alg_bytes // launches, launch_ms
-        achieved = work.alg_bytes / (launch_ms / 1e3) / 1e9
         run_roof = None
-    # DRAM bytes per launch from the committed ncu summary, used only when it
-    # was taken on the kernel that ran here (same generated kernel name)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            rec = json.load(open(tpath)).get(args.workload)
-            if rec and rec.get("kernel") == kname:
-                traffic = rec["dram_bytes_per_launch"]
-        except Exception:
-            traffic = None
-    # stage-program operations per pixel (per voxel: a volume's planes are
-    # its pixels, so the channel count is not a multiplier)
+    achieved = kbytes / (kms / 1e3) / 1e9
+    rec = traffic_record(workload, kname)
+    fp32, nsm = device_fp32_peak(clocks)
     opx = ops_per_pixel(spec) / getattr(work, "planes", 1)
-    line = {
-        "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_f / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": dts, "data": "synthetic",
-        "config": {"workload": args.workload, "pipeline": name, "width": W, "height": H,
-                   "channels": getattr(work, "planes", 1),
-                   "storage": dts, "stages": len(spec["stages"]), "pixels_per_step": work.px,
-                   "l2": work.l2_note, "schedule": fused.schedule_get(),
-                   "tuning": tuning},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kname,
-                     "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms, "whole_run": run_roof,
-                     # the same run against the FP32 ALU: stage-program operations per pixel
-                     # x pixels/s over the derived lane-op peak
-                     "alu": {"ops_per_px": opx,
-                             "achieved_tops": opx * value / 1e6 / world,
-                             "peak_tops": FP32_LANE_OPS / 1e12,
-                             "frac": opx * value * 1e6 / world / FP32_LANE_OPS}},
-        "unfused": unfused,
-        "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * launches,
-        "clocks": clocks,
-    }
-    if batched:
-        line["config"]["images"] = len(work.sizes)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if name == "blend":
-            r, cores, n, dt, sample = cpu_blend_rate(dts, args.cpu_seconds)
-        else:
-            img = work.cpu_sample(dts)
-            cspec = spec if img.ndim == 2 else spec_for_depth(name, img.shape[0])
-            r, cores, n, dt = cpu_oracle_rate(cspec, img, args.cpu_seconds)
-            sample = "%d images of %dx%d%s, %.1f s" % (n, img.shape[-1], img.shape[-2],
-                                                      "" if img.ndim == 2 else "x%d" % img.shape[0], dt)
-        line["cpu_baseline"] = {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle", "sample": sample}
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": rec["dram_bytes_per_launch"] if rec else None, "peak_kind": peak_kind, "kernel": kname,
+            "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms, "whole_run": run_roof}
+    if fp32:
+        # the stage programs' FP32 operations per pixel against the FP32 lanes
+        roof["alu"] = {"ops_per_px": opx, "achieved_tops": opx * value / 1e6 / world, "peak_tops": fp32 / 1e12,
+                       "frac": opx * value * 1e6 / world / fp32}
+    if rec and rec.get("warp_instructions_per_launch") and (clocks or {}).get("sm_mhz"):
+        # issue roof: executed warp instructions over the SMs' issue slots
+        # (4 schedulers, one instruction per cycle each) at the sampled clock
+        slots = nsm * 4 * clocks["sm_mhz"] * 1e6 * kms / 1e3
+        roof["issue"] = {"warp_instructions_per_launch": rec["warp_instructions_per_launch"],
+                         "issue_slots": slots, "frac": rec["warp_instructions_per_launch"] / slots}
+    out = {"value": value, "unit": "Mpixels/s", "ms_per_step": total_f / steps, "steps": steps,
+           "config": workload_config(workload, spec, W, H, work.px, len(work.sizes) if batched else None),
+           "roofline": roof, "unfused": unfused,
+           "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "gpu_launches": steps * launches, "clocks": clocks,
+           "run": {"schedule": fused.schedule_get(), "tuning": tuning, "l2": work.l2_note}}
+    if rank == 0 and world == 1 and cpu_seconds > 0:
+        out["cpu_baseline"] = cpu_baseline(work, name, spec, dts, cpu_seconds)
+    fused.close()
+    return out
+
+
+def cpu_baseline(work, name, spec, dts, seconds):
+    if name == "blend":
+        r, cores, n, dt, sample = cpu_blend_rate(dts, seconds)
+    else:
+        img = work.cpu_sample(dts)
+        cspec = spec if img.ndim == 2 else spec_for_depth(name, img.shape[0])
+        r, cores, n, dt = cpu_oracle_rate(cspec, img, seconds)
+        sample = "%d images of %dx%d%s, %.1f s" % (n, img.shape[-1], img.shape[-2],
+                                                  "" if img.ndim == 2 else "x%d" % img.shape[0], dt)
+    return {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+
+COSTMODEL_FILE = os.path.join(ROOT, "paper_1909_07190_gb300", "costmodel_gb300.txt")
+
+
+def cost_model_entry(wt, torch, workload, rank, local, dist, steps):
+    """The schedules the cost models pick for the workload (DP-Fusion with
+    the analytic model, and with the learned model trained on this GPU kind
+    when its parameters are present), each timed like the headline against
+    the library's default schedule."""
+    name, W, H, dts, spec, work = make_work(wt, torch, workload, rank, local)
+    dtype = wt.DTYPES[dts]
+    out = {"workload": workload, "model_file": None}
+    pipes = {"default": wt.Pipeline(spec)}
+    t0 = time.perf_counter()
+    pipes["analytic"] = wt.Pipeline(spec)
+    pipes["analytic"].schedule_auto(W, H, dtype, wt.WT_MODEL_ANALYTIC)
+    if os.path.exists(COSTMODEL_FILE):
+        wt.costmodel_load(COSTMODEL_FILE)
+        pipes["learned"] = wt.Pipeline(spec)
+        pipes["learned"].schedule_auto(W, H, dtype, wt.WT_MODEL_LEARNED)
+        out["model_file"] = os.path.relpath(COSTMODEL_FILE, ROOT)
+    out["search_seconds"] = round(time.perf_counter() - t0, 2)
+    for k, pipe in pipes.items():
+        total, _ = timed_steps(torch, work, lambda i, s, q=pipe: work.run(q, i, s), steps, 3, 100, dist)
+        out[k] = {"ms": total / steps, "schedule": pipe.schedule_get()}
+    for k in ("analytic", "learned"):
+        if k in out:
+            out[k]["ratio_vs_default"] = out[k]["ms"] / out["default"]["ms"]
+    for pipe in pipes.values():
+        pipe.close()
+    return out
+
+
+# every configuration of the benchmark beside the headline, with its steps
+SECONDARY = (("sharpen", 4000), ("harris_f16", 2000), ("harris_batch", 20), ("blend", 200))
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1909_07190_gb300 import wt
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cpu_s = 0 if args.no_cpu_baseline else args.cpu_seconds
+    head = measure(wt, torch, args.workload, args, dist, world, rank, local, args.steps, args.warmup, cpu_s,
+                   args.size)
+    line = {"metric": METRIC, "value": head["value"], "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": WORKLOADS[args.workload][3], "data": "synthetic",
+            "config": head["config"], "roofline": head["roofline"], "unfused": head["unfused"], "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "run": head["run"]}
+    if "cpu_baseline" in head:
+        line["cpu_baseline"] = head["cpu_baseline"]
+    if world == 1 and args.configs == "all" and not args.size and not args.params:
+        # every other configuration, on the same GPU, after the headline
+        cfgs = {}
+        for wl, steps in SECONDARY:
+            if wl == args.workload:
+                continue
+            m = measure(wt, torch, wl, args, None, 1, rank, local, steps, args.warmup,
+                        min(cpu_s, 4.0) if cpu_s else 0)
+            cfgs[wl] = m
+            torch.cuda.empty_cache()
+        line["configs"] = cfgs
+        line["cost_model"] = cost_model_entry(wt, torch, args.workload, rank, local, None, 500)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -766,6 +865,9 @@ def main():
                          "the default is the workload's own size)")
     ap.add_argument("--params", default="",
                     help="JSON group parameters of a one-group fused schedule (e.g. '{\"tile_h\": 20}')")
+    ap.add_argument("--configs", default="all", choices=["all", "none"],
+                    help="after the headline workload, measure every other configuration (sharpen, FP16 corner "
+                         "response, the 512-image batch, the blend) and the cost models' picks, one GPU only")
     ap.add_argument("--tune", default="auto", choices=["auto", "on", "off"],
                     help="measured schedule search before timing (auto: batches only; single images use the "
                          "library's default schedule)")

@@ -127,9 +127,9 @@ wt_status wt_pipeline_destroy(wt_pipeline *p);
 /* Per-group execution parameters (Sec. 4 OTPW tile, Sec. 5 hybrid tiling). */
 typedef struct {
   int32_t tile_h;          /* T_y: output rows per warp tile (>= 1; default
-                              40).  Single-image runs too small to give every
-                              resident warp about two tiles use a shorter
-                              height of the same parity.                     */
+                              40).  Single-image runs too small to give the
+                              resident warps about 1.5 tiles each use a
+                              shorter height of the same parity.             */
   int32_t warps_per_block; /* 1..16; warps are independent (no block sync)  */
   float frac_reg;          /* fracReg in [0,1]: share of the group's
                               intermediate window bytes kept in registers;

@@ -46,6 +46,14 @@ bool launch_features(const Pipeline &p, const std::vector<int> &seg, const Group
     const int V = prm.vec ? prm.vec : 4;
     GroupGeom g = analyze_group(p, seg, V, prm.frac_reg, 4);
     if (!g.fusable) return false;
+    // the tile height the run will use (shortened for small images)
+    GroupParams prm_in = prm;
+    {
+      const int lp = V * ((g.halo_l + V - 1) / V), rp = V * ((g.halo_r + V - 1) / V);
+      const int ow = std::max(V, 32 * V - lp - rp);
+      prm_in.tile_h = effective_tile_h(prm.tile_h, Hl, (Wl + ow - 1) / ow, g.channels);
+    }
+    const GroupParams &prm = prm_in;
     CostInfo ci = cost_group(p, seg, prm, 128, W0, H0, dtype, cfg, st, current_weights(),
                              pipeline_bytes(p, W0, H0, dtype), &g);
     if (!ci.feasible) return false;
@@ -365,7 +373,7 @@ Schedule learned_schedule(const Pipeline &p, int W, int H, int dtype, const GpuC
           std::vector<char> sig;
           for (const Node &nd : g.nodes) sig.push_back(nd.in_smem);
           if (!seen.insert(sig).second) continue;
-          for (int T : {4, 8, 16, 32})
+          for (int T : {8, 16, 24, 32, 40, 56})
             for (int nw : {2, 4}) {
               GroupParams q;
               q.tile_h = T;

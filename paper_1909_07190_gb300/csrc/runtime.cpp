@@ -57,6 +57,30 @@ static int pick_vec(const GroupParams &gp, const std::vector<int> &src_dtypes) {
 
 // -------------------------------------------------------------- planning
 
+// Images too small to give each resident warp (12 per SM) about 1.5 warp
+// tiles of height T (single-image runs) use shorter tiles of the same parity (the
+// kernel's row-parity folding depends on it), so that every warp has work.
+int effective_tile_h(int T, int H, int tiles_x, int channels) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
+                                                  cudaSuccess && v > 0)
+      nsm = v;
+    else
+      nsm = 152;
+    cudaGetLastError();
+  }
+  T = std::max(1, T);
+  const int64_t want = 3ll * nsm * 12 / 2;  // tiles: about 1.5 per resident warp
+  const int64_t cols = (int64_t)std::max(1, tiles_x) * std::max(1, channels);
+  const int fit = (int)std::max<int64_t>(4, (int64_t)H * cols / want);
+  if (fit >= T) return T;
+  int t = fit;
+  if ((t - T) % 2) t--;
+  return std::max(T % 2 ? 3 : 4, t);
+}
+
 RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out, bool batched) {
   host_alloc_point();
   if (n_in != (int)p.in_channels.size())
@@ -251,28 +275,8 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       int th = std::max(1, L.params.tile_h);
       int tiles_x = (L.W + L.layout.out_w - 1) / L.layout.out_w;
       if (!batched) {
-        // Images too small to give each resident warp about two tiles of
-        // this height run shorter tiles (same parity: the kernel's row-
-        // parity folding depends on it), so that every warp has work.
-        static int nsm = 0;
-        if (!nsm) {
-          int dev = 0, v = 0;
-          if (cudaGetDevice(&dev) == cudaSuccess &&
-              cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            nsm = v;
-          else
-            nsm = 152;
-          cudaGetLastError();
-        }
-        const int64_t want = 2ll * nsm * 12;  // tiles: about two per resident warp
-        const int64_t cols = (int64_t)tiles_x * L.geom.channels;
-        const int fit = (int)std::max<int64_t>(4, (int64_t)L.H * cols / want);
-        if (fit < th) {
-          int t = fit;
-          if ((t - th) % 2) t--;
-          th = std::max(th % 2 ? 3 : 4, t);
-          L.params.tile_h = th;
-        }
+        th = effective_tile_h(th, L.H, tiles_x, L.geom.channels);
+        L.params.tile_h = th;
       }
       int tiles_y = (L.H + th - 1) / th;
       int64_t nt = (int64_t)tiles_x * tiles_y * L.geom.channels;

@@ -34,6 +34,10 @@ struct Error {
 };
 [[noreturn]] void fail(wt_status code, const std::string &msg);
 
+// Tile height single-image runs use for requested height T on a level of
+// height H with tiles_x tile columns (runtime.cpp).
+int effective_tile_h(int T, int H, int tiles_x, int channels);
+
 // Allocation points (runtime.cpp).  A test can make the n-th allocation of
 // one kind fail (wt_debug_inject_alloc_failure): host points throw
 // std::bad_alloc (WT_ENOMEM at the C boundary), device allocations go

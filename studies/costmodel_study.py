@@ -1,21 +1,34 @@
-"""Learned cost model study: collect measured launch times of many schedules,
-train the MLP, and score its schedule picks on held-out schedules against
-exhaustive timing and the analytic model.
+"""Learned cost model study: measure the launch times of many schedules,
+train the MLP on some of them, and score its schedule picks on schedules
+whose launches it has never seen, against exhaustive timing and against the
+analytic model.
 
-  python studies/costmodel_study.py [--schedules 2000] [--out study.json]
-                                                   [--model model.txt]
+  python studies/costmodel_study.py [--out summary.json] [--rows rows.json]
+                                    [--model model.txt]
 
 Pipelines: the 3-stage sharpen on 2048x2048 and the 11-stage corner response
 on 4096x4096, FP32 (synthetic uniform [0,1) images).  Schedules: contiguous
-groupings (all of sharpen's, a seeded sample of the corner response's 1024)
-x warp tile heights {4, 8, 16, 32} x register/shared splits fracReg
-{1, 0.5, 0}.  Each schedule is timed launch by launch
-(wt_schedule_time_launches) and its output is compared with the default
-schedule's (the largest difference is reported).
-Schedules are split 80/20 (seeded); the model trains on the launches of the
-80%, and on the held-out 20% of each pipeline the schedule with the lowest
-predicted time is compared with the fastest measured one
-(t(pick) / t(best)); the analytic model's pick is scored the same way.
+groupings (all 4 of sharpen's, a seeded sample of the corner response's
+1024) x warp tile heights x register/shared splits fracReg {1, 0.5, 0}
+(sharpen also x warps per block {1, 2, 4} x pixels per lane {4, 8}).  Each
+schedule runs once against the default schedule's output (the largest
+difference is reported) and is timed launch by launch
+(wt_schedule_time_launches).
+
+A launch is identified by its feature vector (stage segment, effective tile
+height, pixels per lane, warps, fracReg, ...), so two schedules that share a
+kernel and tile share the launch.  Two held-out splits, in both of which no
+held-out launch appears in training:
+  tile    every schedule of held-out tile heights (corner response 24 and 56
+          rows, sharpen 6 rows) is held out;
+  launch  a seeded 20% of the distinct fused launches is held out, with every
+          schedule that contains one of them.
+The model trains on the launches of the remaining schedules, minus any launch
+that also occurs in a held-out schedule (per-stage kernels), and picks the
+held-out schedule with the lowest predicted time; t(pick) / t(best held-out)
+is reported for it and for the analytic model (Alg. 2 with Table 3's
+weights), with the Spearman rank correlation of predicted and measured
+times.  Finally the model is trained on every launch and saved (--model).
 """
 from __future__ import annotations
 
@@ -34,8 +47,13 @@ from paper_1909_07190_gb300 import inputs as I  # noqa: E402
 from paper_1909_07190_gb300 import pipelines as P  # noqa: E402
 from paper_1909_07190_gb300 import wt  # noqa: E402
 
-TILES = (4, 8, 16, 32)
 FRACS = (1.0, 0.5, 0.0)
+SPACE = {
+    # pipeline: (width, height, tile heights, warps per block, pixels per lane, groupings)
+    "sharpen": (2048, 2048, (4, 6, 8, 10), (1, 2, 4), (4, 8), 4),
+    "harris": (4096, 4096, (8, 16, 24, 32, 40, 56), (2,), (4,), 70),
+}
+HELD_TILES = {"sharpen": {6}, "harris": {24, 56}}
 
 
 def groupings(n, rng, limit):
@@ -60,8 +78,10 @@ def groupings(n, rng, limit):
     return [decode(m) for m in sorted(masks)]
 
 
-def collect(name, W, H, n_sched, rng, stream, log):
+def collect(name, rng, stream, log):
+    """Times every schedule of the pipeline's space, launch by launch."""
     import torch
+    W, H, tiles, warps, vecs, n_group = SPACE[name]
     spec = P.by_name(name)
     n = len(spec["stages"])
     img = I.uniform_image(I.SEED_BASE + (1 if name == "sharpen" else 2), W, H)[0]
@@ -69,23 +89,18 @@ def collect(name, W, H, n_sched, rng, stream, log):
     y = wt.DeviceImage(1, H, W)
     ref = wt.DeviceImage(1, H, W)
     pipe = wt.Pipeline(spec)
-    # reference output: the default schedule (one fused group), whose parity
-    # with the FP64 oracle the GPU test suite establishes
+    # reference output: the default schedule, whose parity with the FP64
+    # oracle the GPU test suite establishes
     pipe.run([x.image()], [ref.image()], stream)
     pipe.check(stream)
-    per = len(TILES) * len(FRACS)
-    gs = groupings(n, rng, max(1, n_sched // per))
-    scheds = [(g, T, fr) for g in gs for T in TILES for fr in FRACS]
-    # compile every kernel first (parallel host threads)
+    scheds = [(g, dict(tile_h=T, frac_reg=fr, warps_per_block=nw, vec=v))
+              for g in groupings(n, rng, n_group) for T in tiles for fr in FRACS for nw in warps for v in vecs]
     t0 = time.time()
-    pipe.prepare([(g, [dict(tile_h=T, frac_reg=fr)] * (max(g) + 1)) for g, T, fr in scheds],
-                 [x.image()], [y.image()])
+    pipe.prepare([(g, [prm] * (max(g) + 1)) for g, prm in scheds], [x.image()], [y.image()])
     log("%s: %d schedules, kernels compiled in %.0f s" % (name, len(scheds), time.time() - t0))
-    rows = []
-    worst = 0.0
-    for k, (g, T, fr) in enumerate(scheds):
+    rows, worst = [], 0.0
+    for k, (g, prm) in enumerate(scheds):
         ng = max(g) + 1
-        prm = dict(tile_h=T, frac_reg=fr)
         pipe.schedule(groups=g, params=[prm] * ng)
         y.t.zero_()
         launches = pipe.time_launches([x.image()], [y.image()], 10, stream)
@@ -99,40 +114,94 @@ def collect(name, W, H, n_sched, rng, stream, log):
         analytic = 0.0
         for gi in range(ng):
             stages = [s for s in range(n) if g[s] == gi]
-            c = pipe.cost_group(stages[0], len(stages), dict(prm, vec=4), 128, W, H)
+            c = pipe.cost_group(stages[0], len(stages), prm, 128, W, H)
             analytic += c["cost"] if c["feasible"] else 1e9
-        rows.append({"pipeline": name, "groups": g, "tile_h": T, "frac_reg": fr, "launch_ms": ms,
-                     "features": feats, "ms": float(sum(ms)), "analytic": analytic, "max_err_vs_ref": err})
-        if (k + 1) % 100 == 0:
+        rows.append({"pipeline": name, "groups": g, "params": prm, "launch_ms": ms, "features": feats,
+                     "ms": float(sum(ms)), "analytic": analytic, "max_err_vs_ref": err})
+        if (k + 1) % 200 == 0:
             log("%s: %d/%d timed" % (name, k + 1, len(scheds)))
     torch.cuda.synchronize()
-    return rows, {"schedules_vs_reference_max_err": worst}
+    return rows, {"schedules": len(rows), "max_err_vs_default": worst}
 
 
-def evaluate(rows, test_idx, predict):
-    """t(pick)/t(best) over the held-out schedules of each pipeline."""
+def launch_key(row, f):
+    return (row["pipeline"],) + tuple(round(v, 5) for v in f)
+
+
+def train(rows, idx, exclude, epochs, seed):
+    """Trains the model on the launches of schedules `idx`, one sample per
+    distinct launch (median of its times), skipping launches in `exclude`."""
+    samples = {}
+    for i in idx:
+        r = rows[i]
+        for f, t in zip(r["features"], r["launch_ms"]):
+            k = launch_key(r, f)
+            if k in exclude:
+                continue
+            samples.setdefault(k, (f, []))[1].append(t)
+    X = np.array([v[0] for v in samples.values()], np.float32)
+    Y = np.array([math.log(float(np.median(v[1]))) for v in samples.values()], np.float32)
+    t0 = time.time()
+    loss = wt.costmodel_train(X, Y, epochs=epochs, batch=64, lr=2e-3, seed=seed)
+    return {"train_launches": int(len(Y)), "final_loss": float(loss), "seconds": time.time() - t0}
+
+
+def predict_ms(row):
+    lp = wt.costmodel_predict(np.array(row["features"], np.float32))
+    return float(np.exp(lp.astype(np.float64)).sum())
+
+
+def spearman(a, b):
+    ra = np.argsort(np.argsort(np.asarray(a)))
+    rb = np.argsort(np.argsort(np.asarray(b)))
+    return float(np.corrcoef(ra, rb)[0, 1]) if len(a) > 2 else float("nan")
+
+
+def evaluate(rows, test_idx):
+    """t(pick) / t(best) over the held-out schedules of each pipeline."""
     out = {}
-    for name in sorted({r["pipeline"] for r in rows}):
+    for name in sorted({rows[i]["pipeline"] for i in test_idx}):
         idx = [i for i in test_idx if rows[i]["pipeline"] == name]
         best = min(rows[i]["ms"] for i in idx)
-        pick_l = min(idx, key=lambda i: predict(rows[i]))
+        pred = [predict_ms(rows[i]) for i in idx]
+        pick_l = idx[int(np.argmin(pred))]
         pick_a = min(idx, key=lambda i: rows[i]["analytic"])
-        true = np.array([rows[i]["ms"] for i in idx])
-        pred = np.array([predict(rows[i]) for i in idx])
-        ra = np.argsort(np.argsort(true))
-        rp = np.argsort(np.argsort(pred))
-        out[name] = {"held_out": len(idx), "best_ms": best,
+        true = [rows[i]["ms"] for i in idx]
+        out[name] = {"held_out_schedules": len(idx), "best_ms": best,
                      "learned_pick_ms": rows[pick_l]["ms"], "learned_ratio": rows[pick_l]["ms"] / best,
+                     "learned_pick": {"groups": rows[pick_l]["groups"], "params": rows[pick_l]["params"]},
                      "analytic_pick_ms": rows[pick_a]["ms"], "analytic_ratio": rows[pick_a]["ms"] / best,
-                     "learned_spearman": float(np.corrcoef(ra, rp)[0, 1])}
+                     "learned_spearman": spearman(pred, true),
+                     "analytic_spearman": spearman([rows[i]["analytic"] for i in idx], true)}
     return out
+
+
+def split_tile(rows):
+    test = [i for i, r in enumerate(rows) if r["params"]["tile_h"] in HELD_TILES[r["pipeline"]]]
+    return test
+
+
+def split_launch(rows, rng):
+    fused = sorted({launch_key(r, f) for r in rows for f in r["features"] if f[17] > 0.5})
+    held = {fused[i] for i in rng.permutation(len(fused))[:max(1, len(fused) // 5)]}
+    return [i for i, r in enumerate(rows) if any(launch_key(r, f) in held for f in r["features"])]
+
+
+def run_split(rows, test, epochs, seed):
+    test_set = set(test)
+    train_idx = [i for i in range(len(rows)) if i not in test_set]
+    exclude = {launch_key(rows[i], f) for i in test for f in rows[i]["features"]}
+    info = train(rows, train_idx, exclude, epochs, seed)
+    info.update({"train_schedules": len(train_idx), "test_schedules": len(test),
+                 "held_out": evaluate(rows, test)})
+    return info
 
 
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("--schedules", type=int, default=2000)
     ap.add_argument("--out", default="")
+    ap.add_argument("--rows", default="")
     ap.add_argument("--model", default="")
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--seed", type=int, default=I.SEED_BASE + 4)
@@ -144,45 +213,25 @@ def main():
         print(m, file=sys.stderr, flush=True)
 
     rows, checks = [], {}
-    n_sharpen = len(TILES) * len(FRACS) * 4
-    for name, W, H, ns in (("sharpen", 2048, 2048, n_sharpen), ("harris", 4096, 4096, args.schedules - n_sharpen)):
-        r, c = collect(name, W, H, ns, rng, stream, log)
+    for name in ("sharpen", "harris"):
+        r, c = collect(name, rng, stream, log)
         rows += r
         checks[name] = c
-    perm = rng.permutation(len(rows))
-    n_train = int(round(0.8 * len(rows)))
-    train_idx, test_idx = sorted(perm[:n_train].tolist()), sorted(perm[n_train:].tolist())
-    # launch-level training samples (a launch seen in several schedules is
-    # averaged)
-    samples = {}
-    for i in train_idx:
-        for f, t in zip(rows[i]["features"], rows[i]["launch_ms"]):
-            key = (rows[i]["pipeline"],) + tuple(round(v, 5) for v in f)
-            samples.setdefault(key, (f, []))[1].append(t)
-    X = np.array([v[0] for v in samples.values()], np.float32)
-    Y = np.array([math.log(float(np.median(v[1]))) for v in samples.values()], np.float32)
-    t0 = time.time()
-    loss = wt.costmodel_train(X, Y, epochs=args.epochs, batch=64, lr=2e-3, seed=args.seed)
-    train_s = time.time() - t0
+    res = {"schedules": len(rows), "parity": checks,
+           "protocol": "launch kernel time: min over 3 samples of the mean of 10 launches",
+           "splits": {"tile": run_split(rows, split_tile(rows), args.epochs, args.seed),
+                      "launch": run_split(rows, split_launch(rows, rng), args.epochs, args.seed)}}
+    # the model kept for scheduling: every launch
+    res["final"] = train(rows, range(len(rows)), set(), args.epochs, args.seed)
     if args.model:
         wt.costmodel_save(args.model)
-    cache = {}
-
-    def predict(r):
-        key = id(r)
-        if key not in cache:
-            lp = wt.costmodel_predict(np.array(r["features"], np.float32))
-            cache[key] = float(np.exp(lp.astype(np.float64)).sum())
-        return cache[key]
-
-    res = {"schedules": len(rows), "train_schedules": len(train_idx), "test_schedules": len(test_idx),
-           "train_launch_samples": int(len(Y)), "final_train_loss": loss, "train_seconds": train_s,
-           "parity": checks, "held_out": evaluate(rows, test_idx, predict),
-           "protocol": "launch kernel time: min over 3 samples of the mean of 10 launches"}
     print(json.dumps(res, indent=1))
     if args.out:
         with open(args.out, "w") as f:
-            json.dump({"result": res, "rows": rows}, f)
+            json.dump(res, f, indent=1)
+    if args.rows:
+        with open(args.rows, "w") as f:
+            json.dump(rows, f)
 
 
 if __name__ == "__main__":
