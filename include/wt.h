@@ -130,7 +130,8 @@ typedef struct {
                               40).  Single-image runs too small to give the
                               resident warps about 1.5 tiles each use a
                               shorter height of the same parity.             */
-  int32_t warps_per_block; /* 1..16; warps are independent (no block sync)  */
+  int32_t warps_per_block; /* 1..16 (default 1); warps are independent (no
+                              block sync)                                   */
   float frac_reg;          /* fracReg in [0,1]: share of the group's
                               intermediate window bytes kept in registers;
                               the rest lives in the warp's shared memory    */
@@ -181,6 +182,12 @@ typedef struct {
  * exits; the run writes no output and wt_check() returns WT_ETIMEOUT.
  * Other kernel kinds ignore the flag.                                      */
 #define WT_FLAG_TEST_STALL 64
+/* Warp-tile kernels of single-image runs launch one warp per tile (blocks
+ * of warps_per_block warps, handed out by the hardware in tile order: the
+ * edge columns' tiles first, tall tiles before a band of short ones).  With
+ * this flag a persistent grid (the resident capacity) pulls tiles from a
+ * device queue instead (the batched kernels always do).                  */
+#define WT_FLAG_TILE_QUEUE 128
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */

@@ -101,7 +101,7 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
         if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB | WT_FLAG_SMEM16 |
-                        WT_FLAG_ZSTREAM | WT_FLAG_TEST_STALL))
+                        WT_FLAG_ZSTREAM | WT_FLAG_TEST_STALL | WT_FLAG_TILE_QUEUE))
           fail(WT_EINVAL, "unknown flags");
         r.tile_o = q.tile_o;
         r.zstream = (q.flags & WT_FLAG_ZSTREAM) ? 1 : 0;
@@ -111,6 +111,7 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.pairs = (q.flags & WT_FLAG_NO_PAIRS) ? 0 : 1;
         r.tile_split = (q.flags & WT_FLAG_NO_TILE_SPLIT) ? 0 : 1;
         r.test_stall = (q.flags & WT_FLAG_TEST_STALL) ? 1 : 0;
+        r.tile_queue = (q.flags & WT_FLAG_TILE_QUEUE) ? 1 : 0;
       }
   } else {
     s.n_groups = n;
@@ -205,7 +206,7 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT) |
                           (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0) |
                           (r.smem16 ? WT_FLAG_SMEM16 : 0) | (r.zstream ? WT_FLAG_ZSTREAM : 0) |
-                          (r.test_stall ? WT_FLAG_TEST_STALL : 0);
+                          (r.test_stall ? WT_FLAG_TEST_STALL : 0) | (r.tile_queue ? WT_FLAG_TILE_QUEUE : 0);
         params[g].tile_o = r.tile_o;
       }
   });
@@ -600,7 +601,10 @@ wt_status wt_debug_kernel_ws(wt_pipeline *p, int32_t launch_index, const wt_imag
       wt::KernelArgs a;
       wt::fill_args(*p, plan, L, (char *)workspace, a, false);
       // as on the GPU with few resident warps: exercises both tile heights
-      if (L.fused && !L.key.otptb) wt::split_tiles(L, a, 4 * L.key.nw);
+      if (L.fused && !L.key.otptb) {
+        wt::split_tiles(L, a, 4 * L.key.nw);
+        a.direct = L.params.tile_queue ? 0 : 1;
+      }
       memcpy(args, &a, sizeof a);
     }
     if (launch) {

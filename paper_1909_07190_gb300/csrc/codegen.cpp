@@ -1184,9 +1184,15 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   // A warp takes its next tile only when it is free (taking it earlier
   // reserves tail tiles for busy warps while others idle).
   if (key.persistent) o << "int last_img_ = -1;\n";
+  // Tiles by block index (a.direct: one tile per warp, the hardware block
+  // scheduler hands out blocks in index order), or pulled by persistent
+  // warps from a device queue (a.queue[0]) until it is empty.
+  o << "int first_ = 1;\n";
   o << "for (;;) {\n";
-  o << "int tile = 0;\nif (lane == 0) tile = atomicAdd(a.queue, 1);\n"
-       "tile = __shfl_sync(WT_FULL, tile, 0);\nif (tile >= a.n_tiles) break;\n";
+  o << "int tile = 0;\n"
+       "if (a.direct) { tile = first_ ? (int)blockIdx.x * " << key.nw << " + warp : a.n_tiles; first_ = 0; }\n"
+       "else { if (lane == 0) tile = atomicAdd(a.queue, 1); tile = __shfl_sync(WT_FULL, tile, 0); }\n"
+       "if (tile >= a.n_tiles) break;\n";
   if (key.persistent) {
     o << "const int *tt_ = a.tile_table + 4 * tile;\nconst int img = tt_[0];\n";
     o << "const WtArgs &ia = ((const WtArgs *)a.img_tab)[img];\n";
@@ -1397,7 +1403,7 @@ std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey 
   o << "cbase += (nrows + CH - 1) / CH;\n";
   o << "}\n";  // tile loop
   o << "wt_exit:\n";
-  o << "if (lane == 0) {\n__threadfence();\nconst int d_ = atomicAdd(a.queue + 1, 1);\n"
+  o << "if (lane == 0 && !a.direct) {\n__threadfence();\nconst int d_ = atomicAdd(a.queue + 1, 1);\n"
        "if (d_ == (int)(gridDim.x * " << key.nw << ") - 1) { atomicExch(a.queue, 0); atomicExch(a.queue + 1, 0); }\n}\n";
   o << "return;\n";
   o << "wt_fail:\n";

@@ -28,7 +28,7 @@ struct __align__(64) WtArgs {
   const int *tile_table;
   int *queue;
   int n_images;
-  int pad0;
+  int direct;      // 1: tile = block index (no queue)
   const void *img_tab;
   int tile_h2, ty1, ty2, n_big;
 };

@@ -390,9 +390,9 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   char hx[24];
   // the generator's version is part of the name: a kernel whose code
   // changes gets a new name (profiles and caches never mix versions)
-  static const char kCodegenVersion[] = "wt-codegen-20";
+  static const char kCodegenVersion[] = "wt-codegen-21";
   static const char kPlainVersion[] = "wt-plain-2";  // the per-stage kernel's own changes
-  static const char kBatchVersion[] = "wt-batch-14";  // the persistent variant's own changes
+  static const char kBatchVersion[] = "wt-batch-15";  // the persistent variant's own changes
   const std::string ks = key.str();
   uint64_t h = fnv1a(ks.data(), ks.size(), p.hash);
   h = fnv1a(kCodegenVersion, sizeof kCodegenVersion, h);
@@ -701,12 +701,18 @@ KernelArgs launch_args(Pipeline &p, const RunPlan &plan, Launch &L, Kernel &k, c
              "cuOccupancyMaxActiveBlocksPerMultiprocessor");
     check_rt(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     if (per_sm < 1) fail(WT_EUNSUPPORTED, "group kernel cannot be resident (registers/shared memory)");
-    if (persistent) L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
+    // one warp per tile in block-index order, or (tile queue) no more
+    // blocks than can be resident at once
+    if (persistent && L.params.tile_queue) L.grid[0] = std::min<unsigned>(L.grid[0], (unsigned)(per_sm * sms));
     L.resident_blocks_per_sm = per_sm;
+    L.resident_warps = per_sm * sms * L.key.nw;
   }
   KernelArgs a;
   fill_args(p, plan, L, ws, a, persistent);
-  if (persistent) split_tiles(L, a, (int)L.grid[0] * L.key.nw);
+  if (persistent) {
+    split_tiles(L, a, L.resident_warps);
+    a.direct = L.params.tile_queue ? 0 : 1;
+  }
   a.err = err;
   a.queue = queue_counters(err, li);
   return a;

@@ -83,7 +83,7 @@ struct Stage {
 
 struct GroupParams {
   int tile_h = 40;
-  int warps_per_block = 2;
+  int warps_per_block = 1;
   float frac_reg = 1.f;
   int vec = 0;
   int max_regs = 0;
@@ -98,6 +98,7 @@ struct GroupParams {
   int tile_o = 0;      // 3-D groups: planes (rows when streaming planes) per tile
   int zstream = 0;     // 3-D groups: stream along planes instead of rows
   int test_stall = 0;  // test only: every tile's first staging wait gives up
+  int tile_queue = 0;  // persistent warps pull tiles from a device queue
 };
 
 struct Schedule {
@@ -220,7 +221,7 @@ struct alignas(64) KernelArgs {
   const int32_t *tile_table;  // 4 ints per tile: image, tx, ty, c
   int32_t *queue;             // atomic tile counter
   int32_t n_images;
-  int32_t pad0;
+  int32_t direct;          // warp-tile kernels: 1 = one tile per warp by block index
   const void *img_tab;        // per-image SrcDesc/DstDesc/tmaps
   // two tile heights: tiles [0, n_big) have tile_h rows and cover tile
   // rows [0, ty1); the rest have tile_h2 rows (short tiles end the run)

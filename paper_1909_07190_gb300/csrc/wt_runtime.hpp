@@ -34,6 +34,7 @@ struct Launch {
   int block = 128;
   int smem = 0;
   int resident_blocks_per_sm = 0;
+  int resident_warps = 0;  // fused launches: resident warps on the device
 };
 
 struct RunPlan {

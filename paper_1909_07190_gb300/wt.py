@@ -22,6 +22,7 @@ WT_MODEL_ANALYTIC, WT_MODEL_LEARNED = 0, 1
 WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT, WT_FLAG_PLAIN, WT_FLAG_OTPTB, WT_FLAG_SMEM16 = 1, 2, 4, 8, 16
 WT_FLAG_ZSTREAM = 32
 WT_FLAG_TEST_STALL = 64
+WT_FLAG_TILE_QUEUE = 128
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
            "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14,
            "tapz": 15}
@@ -261,7 +262,7 @@ class Pipeline:
         g = (_i32 * n)(*groups)
         prm = (wt_group_params * ng)()
         for i in range(ng):
-            d = dict(tile_h=40, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
+            d = dict(tile_h=40, warps_per_block=1, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
                      n_buffers=0, flags=0)
             if params is not None:
                 d.update(params[i] if isinstance(params, (list, tuple)) else params)
@@ -370,7 +371,7 @@ class Pipeline:
             g = (_i32 * n)(*groups)
             prm = (wt_group_params * ng)()
             for i in range(ng):
-                d = dict(tile_h=40, warps_per_block=2, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
+                d = dict(tile_h=40, warps_per_block=1, frac_reg=1.0, vec=0, max_regs=0, chunk_rows=0,
                          n_buffers=0, flags=0)
                 if params is not None:
                     d.update(params[i] if isinstance(params, (list, tuple)) else params)

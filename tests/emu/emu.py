@@ -59,6 +59,7 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
     body = source.split(MARK, 1)[1]
     text = '#include "wt_emu.h"\n' + body + \
         '\nextern "C" long wt_emu_offset_err() { return (long)offsetof(WtArgs, err); }\n' + \
+        'extern "C" long wt_emu_offset_direct() { return (long)offsetof(WtArgs, direct); }\n' + \
         'extern "C" long wt_emu_offset_queue() { return (long)offsetof(WtArgs, queue); }\n' + \
         'extern "C" long wt_emu_offset_tiles() { return (long)offsetof(WtArgs, tile_table); }\n' + \
         'extern "C" long wt_emu_offset_imgtab() { return (long)offsetof(WtArgs, img_tab); }\n'
@@ -120,7 +121,10 @@ def run(pipe: "wt.Pipeline", index: int, inputs, outputs, max_blocks=None, works
                                ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
     msg = ctypes.create_string_buffer(512)
     gx, gy, gz = d["grid"]
-    if max_blocks is not None and d["fused"]:
+    # persistent warps (tile queue): at most max_blocks blocks take several
+    # tiles each; one warp per tile (direct) needs every block
+    direct = int.from_bytes(bytes(args[lib.wt_emu_offset_direct():][:4]), "little")
+    if max_blocks is not None and d["fused"] and not direct:
         gx = min(gx, max_blocks)
     _register(lib, inputs + outputs, workspace)
     rc = lib.wt_emu_run(kfn, ctypes.addressof(abuf), gx, gy, gz, d["block"], d["smem"], msg, 512)

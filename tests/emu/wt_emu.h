@@ -43,7 +43,7 @@ struct alignas(64) WtArgs {
   const int *tile_table;
   int *queue;
   int n_images;
-  int pad0;
+  int direct;
   const void *img_tab;
   int tile_h2, ty1, ty2, n_big;
 };

@@ -304,3 +304,18 @@ def test_block_bodies_by_rows(name, frac, tile_h):
                           max_blocks=3)
     ref = oracle_of(spec, [img])
     assert np.abs(got[0] - ref[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["harris", "sharpen"])
+@pytest.mark.parametrize("warps", [1, 2])
+def test_tile_queue_mode(name, warps):
+    """Persistent warps pulling tiles from the device queue (three blocks
+    take every tile) give the same result as one warp per tile."""
+    spec = P.by_name(name)
+    img = rnd(91 + warps, 300, 170)
+    got, d = run_emulated(spec, [img], params=[dict(tile_h=24, warps_per_block=warps,
+                                                    flags=wt.WT_FLAG_TILE_QUEUE)], max_blocks=3)
+    ref = oracle_of(spec, [img])
+    assert np.abs(got[0] - ref[0]).max() <= 1e-5
+    got1, _ = run_emulated(spec, [img], params=[dict(tile_h=24, warps_per_block=warps)])
+    assert np.abs(got1[0] - ref[0]).max() <= 1e-5
