@@ -596,19 +596,21 @@ wt_status wt_debug_kernel_ws(wt_pipeline *p, int32_t launch_index, const wt_imag
       memcpy(src, s.data(), n);
       src[n] = 0;
     }
+    wt::KernelArgs a;
+    wt::fill_args(*p, plan, L, (char *)workspace, a, false);
+    unsigned gx = L.grid[0];
+    // as on the GPU with few resident warps: exercises both tile heights
+    if (L.fused && !L.key.otptb) {
+      wt::split_tiles(L, a, 4 * L.key.nw);
+      a.direct = L.params.tile_queue ? 0 : 1;
+      if (a.direct) gx = (unsigned)((a.n_tiles + L.key.nw - 1) / L.key.nw);
+    }
     if (args) {
       if (args_cap < (int64_t)sizeof(wt::KernelArgs)) wt::fail(WT_EINVAL, "args buffer too small");
-      wt::KernelArgs a;
-      wt::fill_args(*p, plan, L, (char *)workspace, a, false);
-      // as on the GPU with few resident warps: exercises both tile heights
-      if (L.fused && !L.key.otptb) {
-        wt::split_tiles(L, a, 4 * L.key.nw);
-        a.direct = L.params.tile_queue ? 0 : 1;
-      }
       memcpy(args, &a, sizeof a);
     }
     if (launch) {
-      launch[0] = (int32_t)L.grid[0];
+      launch[0] = (int32_t)gx;
       launch[1] = (int32_t)L.grid[1];
       launch[2] = (int32_t)L.grid[2];
       launch[3] = L.block;

@@ -712,6 +712,8 @@ KernelArgs launch_args(Pipeline &p, const RunPlan &plan, Launch &L, Kernel &k, c
   if (persistent) {
     split_tiles(L, a, L.resident_warps);
     a.direct = L.params.tile_queue ? 0 : 1;
+    // one warp per tile: the grid covers every tile of the split
+    if (a.direct) L.grid[0] = (unsigned)((a.n_tiles + L.key.nw - 1) / L.key.nw);
   }
   a.err = err;
   a.queue = queue_counters(err, li);
