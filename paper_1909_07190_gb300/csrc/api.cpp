@@ -597,7 +597,10 @@ wt_status wt_debug_kernel_ws(wt_pipeline *p, int32_t launch_index, const wt_imag
       src[n] = 0;
     }
     wt::KernelArgs a;
-    wt::fill_args(*p, plan, L, (char *)workspace, a, false);
+    // the argument block (with the caller's workspace when asked for it;
+    // otherwise any base: only the tile counts are used)
+    static char no_ws;
+    wt::fill_args(*p, plan, L, args || workspace ? (char *)workspace : &no_ws, a, false);
     unsigned gx = L.grid[0];
     // as on the GPU with few resident warps: exercises both tile heights
     if (L.fused && !L.key.otptb) {
