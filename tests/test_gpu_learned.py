@@ -160,3 +160,33 @@ def test_learned_schedules_from_measured_launches():
     ref = O.evaluate(spec["stages"], [img[None].astype(np.float64)], spec["outputs"])[0][0]
     assert np.abs(y.download()[0] - ref).max() <= 1e-5
     wt.costmodel_reset()
+
+
+def test_shipped_model_picks_a_fast_corner_response_schedule():
+    """DP-Fusion with the shipped learned model on the 4096x4096 corner
+    response picks a schedule that matches the oracle and runs within 10% of
+    the library's default schedule (the fastest of the measured study)."""
+    import os
+    from paper_1909_07190_gb300 import wt
+    W = H = 4096
+    spec = P.harris()
+    img = I.uniform_image(I.SEED_BASE + 2, W, H)[0]
+    src = wt.DeviceImage(1, H, W).upload(img)
+    dst = wt.DeviceImage(1, H, W)
+    wt.costmodel_load(os.path.join(os.path.dirname(wt.__file__), "costmodel_gb300.txt"))
+    try:
+        p = wt.Pipeline(spec)
+        p.schedule_auto(W, H, wt.WT_F32, wt.WT_MODEL_LEARNED)
+        s = torch.cuda.current_stream().cuda_stream
+        p.run([src.image()], [dst.image()], s)
+        p.check(s)
+        rng = np.random.default_rng(3)
+        xs, ys = rng.integers(0, W, 200), rng.integers(0, H, 200)
+        ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys)
+        assert np.abs(dst.download()[0][ys, xs] - ref).max() <= 1e-5
+        t_learned = p.schedule_time([src.image()], [dst.image()], 0, 20, s)
+        q = wt.Pipeline(spec)
+        t_default = q.schedule_time([src.image()], [dst.image()], 0, 20, s)
+        assert t_learned <= 1.10 * t_default, (t_learned, t_default, p.schedule_get())
+    finally:
+        wt.costmodel_reset()

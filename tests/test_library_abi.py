@@ -195,3 +195,19 @@ def test_preprocess_needs_a_gpu():
     p = wt.Pipeline(P.sharpen())
     with pytest.raises(wt.WtError):
         p.preprocess()
+
+
+def test_shipped_cost_model_loads():
+    """The learned cost model trained on GB300 launch times (by the cost-model
+    study) ships with the package and loads: 18 features, 64 hidden units."""
+    import os
+    from paper_1909_07190_gb300 import wt
+    path = os.path.join(os.path.dirname(wt.__file__), "costmodel_gb300.txt")
+    with open(path) as f:
+        assert f.readline().split() == ["wt-mlp", "1", "18", "64"]
+    wt.costmodel_load(path)
+    try:
+        assert wt.costmodel_ready()
+    finally:
+        wt.costmodel_reset()
+    assert not wt.costmodel_ready()
