@@ -426,11 +426,37 @@ static const int kWarps[] = {2, 4, 8};
 static const int kVec[] = {4, 8};
 static const int kTxn[] = {32, 128};
 
+// HBM bytes of a reduction chain across levels run as one kernel (its
+// producer read once, only its last stage written), FP32 like the per-stage
+// kernels' estimate.
+double chain_bytes(const Pipeline &p, const std::vector<int> &seg, int W0, int H0) {
+  const ChainForm f = chain_form(p, seg);
+  const int pl = f.producer >= 0 ? p.stages[f.producer].level : 0;
+  int pw, ph, lw, lh;
+  level_dims(W0, H0, pl, &pw, &ph);
+  level_dims(W0, H0, p.stages[seg.back()].level, &lw, &lh);
+  return ((double)pw * ph + (double)lw * lh * p.stages[seg.back()].channels) * 4;
+}
+
 SegmentChoice best_for_segment(const Pipeline &p, const std::vector<int> &seg, int W, int H, int dtype,
                                const GpuConfig &cfg, const std::vector<StageStats> &st, const CostWeights &w,
                                double pbytes, const CandidateScorer *scorer) {
   SegmentChoice best;
   best.cost = INFINITY;
+  if (chain_form(p, seg).ok) {
+    // a group spanning levels: the reduction chain kernel (Sec. 5's scaled
+    // groups), costed by its traffic like a per-stage kernel
+    CostInfo ci;
+    ci.t[0] = chain_bytes(p, seg, W, H) / std::max(1.0, pbytes);
+    ci.cost = w.w[0] * ci.t[0];
+    ci.feasible = true;
+    ci.work = work_share(p, seg, W, H);
+    best.cost = ci.cost;
+    best.fused = true;
+    best.prm = GroupParams();
+    best.info = ci;
+    return best;
+  }
   for (int V : kVec) {
     std::set<std::vector<char>> seen;
     for (int fi = 0; fi <= 10; fi++) {

@@ -65,6 +65,8 @@ CostInfo cost_plain(const Pipeline &p, int s, int W0, int H0, int dtype, const C
 // Alternative scorer of a candidate (the learned model); lower is better.
 using CandidateScorer = std::function<double(const std::vector<int> &, const GroupParams &, const CostInfo &)>;
 
+// HBM bytes of a reduction chain across levels run as one kernel.
+double chain_bytes(const Pipeline &p, const std::vector<int> &seg, int W0, int H0);
 struct SegmentChoice {
   double cost = INFINITY;
   bool fused = false;

@@ -90,8 +90,8 @@ def test_scaled_modes_gpu(k, w, h):
 
 
 def test_tune_finds_reduction_chain():
-    """The measured search merges the grid's splat and 2x2 sums into one
-    cross-level group (the DP alone keeps them apart) and keeps parity."""
+    """The measured search keeps the grid's splat and 2x2 sums as one
+    cross-level group and keeps parity."""
     wt = wtmod()
     spec = P.bilateral_filter()
     W, H = 2048, 1024
@@ -107,3 +107,36 @@ def test_tune_finds_reduction_chain():
     p.check(s)
     got = y.download()[0]
     assert close(got, oracle_out(spec, [img])[0])
+
+
+@pytest.mark.parametrize("model", ["analytic", "learned"])
+def test_dp_fusion_proposes_cross_level_group(model):
+    """DP-Fusion with either cost model puts the grid's splat and its 2x2
+    sums (three levels) into one group, run as the reduction-chain kernel,
+    and the 4096x4096 filter it schedules matches the oracle at sampled
+    points."""
+    import os
+    wt = wtmod()
+    spec = P.bilateral_filter()
+    W = H = 4096
+    img = rnd(I.SEED_BASE + 6, W, H)
+    p = wt.Pipeline(spec)
+    if model == "learned":
+        wt.costmodel_load(os.path.join(os.path.dirname(wt.__file__), "costmodel_gb300.txt"))
+    try:
+        p.schedule_auto(W, H, wt.WT_F32, wt.WT_MODEL_LEARNED if model == "learned" else wt.WT_MODEL_ANALYTIC)
+    finally:
+        wt.costmodel_reset()
+    groups = p.schedule_get()["groups"]
+    assert groups[0] == groups[1] == groups[2] and groups[3] != groups[2], groups
+    x = wt.DeviceImage(1, H, W).upload(img)
+    y = wt.DeviceImage(1, H, W)
+    assert p.kernel_name(0, [x.image()], [y.image()]).startswith("wt_chain_")
+    s = torch.cuda.current_stream().cuda_stream
+    p.run([x.image()], [y.image()], s)
+    p.check(s)
+    rng = np.random.default_rng(16)
+    xs = np.concatenate([rng.integers(0, W, 60), [0, W - 1, 0, W - 1]])
+    ys = np.concatenate([rng.integers(0, H, 60), [0, H - 1, H - 1, 0]])
+    ref = O.evaluate_points(spec["stages"], [img.astype(np.float64)], spec["outputs"][0], xs, ys)
+    assert np.abs(y.download()[0][ys, xs] - ref).max() <= 1e-5

@@ -136,3 +136,19 @@ def test_dp_fusion_groups_blend_by_level():
     s = p.schedule_get()
     assert s["groups"] == P.blend_groups()
     assert p.launches_per_run() == 10
+
+
+def test_dp_fusion_proposes_reduction_chain_across_levels():
+    """DP-Fusion (analytic model) groups the bilateral grid's splat and its
+    2x2 sums, three levels, as one group: the reduction-chain kernel reads
+    the image once and writes only the coarsest level, which the traffic
+    term prefers to any split (no GPU needed)."""
+    from paper_1909_07190_gb300 import pipelines as P
+    from paper_1909_07190_gb300 import wt
+    spec = P.bilateral_filter()
+    p = wt.Pipeline(spec)
+    p.schedule_auto(4096, 4096, wt.WT_F32, wt.WT_MODEL_ANALYTIC)
+    g = p.schedule_get()["groups"]
+    assert g[0] == g[1] == g[2] and g[3] != g[2], g
+    img = wt.image(0x10000000, 4096, 4096, 1, wt.WT_F32, 4096 * 4)
+    assert p.kernel_name(0, [img], [img]).startswith("wt_chain_")
