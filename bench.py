@@ -56,10 +56,10 @@ WORKLOADS = {
 }
 VOLUME_DEPTH = 256
 # 3-D group parameters: the fastest of the 3-D study's sweep on one GB300
-VOLUME_PARAMS = {"unsharp3d": dict(tile_h=64, tile_o=4, vec=1, warps_per_block=4, max_regs=128, n_buffers=1,
+VOLUME_PARAMS = {"unsharp3d": dict(tile_h=64, tile_o=4, vec=1, warps_per_block=1, max_regs=128, n_buffers=1,
                                     flags=32),
-                 "heat3d": dict(tile_h=64, tile_o=4, vec=1, warps_per_block=2, max_regs=128, n_buffers=1,
-                                frac_reg=0.0, flags=32)}
+                 "heat3d": dict(tile_h=64, tile_o=4, vec=1, warps_per_block=1, max_regs=128, n_buffers=1,
+                                frac_reg=1.0, flags=32)}
 
 
 def spec_for(name):
@@ -78,6 +78,13 @@ def spec_for_depth(name, depth):
 
 
 BATCH_IMAGES = 512
+
+
+class _Args:
+    batch_images = 0
+
+
+args_global = _Args()  # options the workload classes read (set by main)
 # pyramid levels a tap mode moves (down: the producer is finer)
 LEVEL_DELTA = {"same": 0, "down2": 1, "up2": -1, "down4": 2, "up4": -2, "down8": 3, "up8": -3}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -225,8 +232,8 @@ def cpu_blend_rate(dts, budget_s, w=1024, h=1024):
     return n * w * h / dt / 1e6, O.num_threads(), n, dt, "%d full %dx%dx3 blends, %.1f s" % (n, w, h, dt)
 
 
-def batch_sizes():
-    return I.batch_sizes(I.SEED_BASE + 3, BATCH_IMAGES, 200, 4096)
+def batch_sizes(n=None):
+    return I.batch_sizes(I.SEED_BASE + 3, BATCH_IMAGES, 200, 4096)[:n or BATCH_IMAGES]
 
 
 def run_reference(args, rank):
@@ -513,7 +520,7 @@ class Batch:
         self.wt, self.torch = wt, torch
         self.dtype = dtype
         self.esz = 4 if dtype == wt.WT_F32 else 2
-        self.sizes = batch_sizes()
+        self.sizes = batch_sizes(getattr(args_global, "batch_images", 0))
         self.seed = seed
         self.ins, self.outs = [], []
         for i, (w, h) in enumerate(self.sizes):
@@ -865,6 +872,8 @@ def main():
                          "the default is the workload's own size)")
     ap.add_argument("--params", default="",
                     help="JSON group parameters of a one-group fused schedule (e.g. '{\"tile_h\": 20}')")
+    ap.add_argument("--batch-images", type=int, default=0,
+                    help="the first N images of the 512-image batch (profiling captures of a reduced batch)")
     ap.add_argument("--configs", default="all", choices=["all", "none"],
                     help="after the headline workload, measure every other configuration (sharpen, FP16 corner "
                          "response, the 512-image batch, the blend) and the cost models' picks, one GPU only")
@@ -872,6 +881,7 @@ def main():
                     help="measured schedule search before timing (auto: batches only; single images use the "
                          "library's default schedule)")
     args = ap.parse_args()
+    args_global.batch_images = args.batch_images
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_env()
