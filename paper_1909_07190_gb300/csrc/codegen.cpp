@@ -69,6 +69,16 @@ std::string CodegenKey::str() const {
 
 static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
+// Steps of a warp tile beyond its output rows: the top halo (rows streamed
+// before the first output row) plus the rows after the last output row that
+// a node of the group still computes (its bottom halo and delay).
+int stream_extra_steps(const GroupGeom &g) {
+  int nsx = g.halo_b;
+  for (const Node &n : g.nodes)
+    if (!n.is_source) nsx = std::max(nsx, n.bot + n.delay);
+  return g.halo_t + nsx;
+}
+
 FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key) {
   FusedLayout L;
   L.V = key.vec;
@@ -87,10 +97,7 @@ FusedLayout fused_layout(const GroupGeom &g, const CodegenKey &key) {
   L.chunk = (ch + U - 1) / U * U;
   L.nbuf = std::max(2, key.nbuf);
   L.ring = L.chunk * L.nbuf;
-  int nsx = g.halo_b;
-  for (const Node &n : g.nodes)
-    if (!n.is_source) nsx = std::max(nsx, n.bot + n.delay);
-  L.nsx = nsx;
+  L.nsx = stream_extra_steps(g) - g.halo_t;
   L.src_rows_extra = g.halo_b;
   int off = 0;
   int n_src = 0;

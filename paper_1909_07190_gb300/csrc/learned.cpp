@@ -51,7 +51,7 @@ bool launch_features(const Pipeline &p, const std::vector<int> &seg, const Group
     {
       const int lp = V * ((g.halo_l + V - 1) / V), rp = V * ((g.halo_r + V - 1) / V);
       const int ow = std::max(V, 32 * V - lp - rp);
-      prm_in.tile_h = effective_tile_h(prm.tile_h, Hl, (Wl + ow - 1) / ow, g.channels);
+      prm_in.tile_h = effective_tile_h(prm.tile_h, Hl, (Wl + ow - 1) / ow, g.channels, g);
     }
     const GroupParams &prm = prm_in;
     CostInfo ci = cost_group(p, seg, prm, 128, W0, H0, dtype, cfg, st, current_weights(),

@@ -60,7 +60,7 @@ static int pick_vec(const GroupParams &gp, const std::vector<int> &src_dtypes) {
 // Images too small to give each resident warp (12 per SM) about 1.5 warp
 // tiles of height T (single-image runs) use shorter tiles of the same parity (the
 // kernel's row-parity folding depends on it), so that every warp has work.
-int effective_tile_h(int T, int H, int tiles_x, int channels) {
+int effective_tile_h(int T, int H, int tiles_x, int channels, const GroupGeom &g) {
   static int nsm = 0;
   if (!nsm) {
     int dev = 0, v = 0;
@@ -76,9 +76,19 @@ int effective_tile_h(int T, int H, int tiles_x, int channels) {
   const int64_t cols = (int64_t)std::max(1, tiles_x) * std::max(1, channels);
   const int fit = (int)std::max<int64_t>(4, (int64_t)H * cols / want);
   if (fit >= T) return T;
+  // the tallest height up to `fit` whose steps (the rows plus the group's
+  // streaming halo) fill whole unrolled blocks, so no block computes rows
+  // past the tile's end; the same parity as T when the kernel folds the
+  // row parity
+  const int U = std::max(1, g.unroll), extra = stream_extra_steps(g);
+  const bool parity = g.uses_ypar;
+  for (int t = fit; t >= std::max(3, fit / 2); t--) {
+    if (parity && (t - T) % 2) continue;
+    if ((t + extra) % U == 0) return t;
+  }
   int t = fit;
-  if ((t - T) % 2) t--;
-  return std::max(T % 2 ? 3 : 4, t);
+  if (parity && (t - T) % 2) t--;
+  return std::max(T % 2 && parity ? 3 : 4, t);
 }
 
 RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_out, bool batched) {
@@ -275,7 +285,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       int th = std::max(1, L.params.tile_h);
       int tiles_x = (L.W + L.layout.out_w - 1) / L.layout.out_w;
       if (!batched) {
-        th = effective_tile_h(th, L.H, tiles_x, L.geom.channels);
+        th = effective_tile_h(th, L.H, tiles_x, L.geom.channels, L.geom);
         L.params.tile_h = th;
       }
       int tiles_y = (L.H + th - 1) / th;

@@ -36,7 +36,10 @@ struct Error {
 
 // Tile height single-image runs use for requested height T on a level of
 // height H with tiles_x tile columns (runtime.cpp).
-int effective_tile_h(int T, int H, int tiles_x, int channels);
+struct GroupGeom;
+// Steps of a warp tile beyond its output rows (codegen.cpp).
+int stream_extra_steps(const GroupGeom &g);
+int effective_tile_h(int T, int H, int tiles_x, int channels, const GroupGeom &g);
 
 // Allocation points (runtime.cpp).  A test can make the n-th allocation of
 // one kind fail (wt_debug_inject_alloc_failure): host points throw
