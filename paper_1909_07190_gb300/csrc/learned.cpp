@@ -385,7 +385,7 @@ Schedule learned_schedule(const Pipeline &p, int W, int H, int dtype, const GpuC
           for (const Node &nd : g.nodes) sig.push_back(nd.in_smem);
           if (!seen.insert(sig).second) continue;
           for (int T : {8, 16, 24, 32, 40, 56})
-            for (int nw : {2, 4}) {
+            for (int nw : {1, 2}) {
               GroupParams q;
               q.tile_h = T;
               q.warps_per_block = nw;

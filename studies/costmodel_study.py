@@ -9,8 +9,9 @@ analytic model.
 Pipelines: the 3-stage sharpen on 2048x2048 and the 11-stage corner response
 on 4096x4096, FP32 (synthetic uniform [0,1) images).  Schedules: contiguous
 groupings (all 4 of sharpen's, a seeded sample of the corner response's
-1024) x warp tile heights x register/shared splits fracReg {1, 0.5, 0}
-(sharpen also x warps per block {1, 2, 4} x pixels per lane {4, 8}).  Each
+1024) x warp tile heights x register/shared splits fracReg {1, 0.5, 0} x
+warps per block ({1, 2, 4} for sharpen, {1, 2} for the corner response) x
+pixels per lane {4, 8}: the space DP-Fusion's learned search draws from.  Each
 schedule runs once against the default schedule's output (the largest
 difference is reported) and is timed launch by launch
 (wt_schedule_time_launches).
@@ -51,7 +52,7 @@ FRACS = (1.0, 0.5, 0.0)
 SPACE = {
     # pipeline: (width, height, tile heights, warps per block, pixels per lane, groupings)
     "sharpen": (2048, 2048, (4, 6, 8, 10), (1, 2, 4), (4, 8), 4),
-    "harris": (4096, 4096, (8, 16, 24, 32, 40, 56), (2,), (4,), 70),
+    "harris": (4096, 4096, (8, 16, 24, 32, 40, 56), (1, 2), (4, 8), 40),
 }
 HELD_TILES = {"sharpen": {6}, "harris": {24, 56}}
 
