@@ -562,7 +562,14 @@ int32_t wt_launches_per_run(const wt_pipeline *p) {
                                              gp.n_buffers).ok
                            : ((!gp.otptb && wt::chain_form(*p, groups[gi]).ok) ||
                               wt::analyze_group(*p, groups[gi], 4, 1.f, 4).fusable));
-      if (fused) {
+      const std::vector<wt::CascadeUnit> cu =
+          p->sched.exec == WT_EXEC_FUSED && !gp.plain && !gp.otptb && !zgroup && !wt::chain_form(*p, groups[gi]).ok
+              ? wt::cascade_units(*p, groups[gi])
+              : std::vector<wt::CascadeUnit>();
+      if (!cu.empty()) {
+        for (const wt::CascadeUnit &u : cu)
+          if (u.s2 >= 0 || !p->consumers[u.s1].empty() || p->is_output[u.s1]) n++;
+      } else if (fused) {
         n++;
       } else {
         for (int s : groups[gi])

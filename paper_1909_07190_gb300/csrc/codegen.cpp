@@ -61,6 +61,7 @@ std::string CodegenKey::str() const {
   if (win_dtype != WT_F32) s << "|W" << win_dtype;
   if (down) s << "|D" << tby;
   if (chain) s << "|R";
+  if (cascade) s << "|K" << tby;
   if (vol) s << "|Z" << vol_split << "x" << vol_to << "x" << tby;
   if (test_stall) s << "|STALL";
   return s.str();

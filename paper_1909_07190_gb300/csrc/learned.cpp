@@ -357,9 +357,9 @@ Schedule learned_schedule(const Pipeline &p, int W, int H, int dtype, const GpuC
   std::vector<Cand> cands;
   std::vector<float> feats;
   float fv[kMlpFeatures];
-  // reduction chains across levels (no features: the model was trained on
-  // warp-tile and per-stage launches): their traffic at the device's copy
-  // bandwidth, in ms
+  // reduction chains and down-sampling cascades across levels (no
+  // features: the model was trained on warp-tile and per-stage launches):
+  // their traffic at the device's copy bandwidth, in ms
   std::vector<std::pair<std::pair<int, int>, double>> chains;
   for (int j = 1; j <= n; j++)
     for (int i = std::max(0, j - max_group); i < j; i++) {
@@ -367,6 +367,8 @@ Schedule learned_schedule(const Pipeline &p, int W, int H, int dtype, const GpuC
       for (int s = i; s < j; s++) seg.push_back(s);
       if (chain_form(p, seg).ok)
         chains.push_back({{i, j}, chain_bytes(p, seg, W, H) / cfg.glmem_bw * 1e3});
+      else if (!cascade_units(p, seg).empty())
+        chains.push_back({{i, j}, cascade_bytes(p, seg, W, H) / cfg.glmem_bw * 1e3});
     }
   for (int j = 1; j <= n; j++)
     for (int i = std::max(0, j - max_group); i < j; i++) {
@@ -414,7 +416,7 @@ Schedule learned_schedule(const Pipeline &p, int W, int H, int dtype, const GpuC
     const int i = c.first.first, j = c.first.second;
     if (c.second < seg_cost[i][j]) {
       seg_cost[i][j] = c.second;
-      seg_best[i][j] = (int)cands.size();  // a chain: installed as a fused group
+      seg_best[i][j] = (int)cands.size();  // a chain or cascade: installed as a fused group
       cands.push_back({i, j, true, GroupParams()});
     }
   }

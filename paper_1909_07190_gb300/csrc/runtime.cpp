@@ -183,6 +183,25 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       plan.launches.push_back(L);
       continue;
     }
+    if (fused && !gp.otptb) {
+      const std::vector<CascadeUnit> cu = cascade_units(p, G);
+      if (!cu.empty()) {
+        // down-sampling stages of two levels: each pair one cascade launch
+        // writing both stages, every other stage its streaming kernel
+        for (const CascadeUnit &u : cu) {
+          if (u.s2 < 0 && p.consumers[u.s1].empty() && !p.is_output[u.s1]) continue;  // dead stage
+          materialize(u.s1, true);
+          if (u.s2 >= 0) materialize(u.s2, true);
+          Launch L;
+          L.fused = false;
+          L.stages = u.s2 < 0 ? std::vector<int>{u.s1} : std::vector<int>{u.s1, u.s2};
+          L.params = gp;
+          L.key.cascade = u.s2 >= 0;
+          plan.launches.push_back(L);
+        }
+        continue;
+      }
+    }
     GroupGeom geom;
     if (fused) {
       geom = analyze_group(p, G, 4, gp.frac_reg, 4);
@@ -333,6 +352,34 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "3-D group needs more than 227 KB of shared memory per block");
       L.kname = kernel_name(p, key, false);
       continue;
+    } else if (key.cascade) {
+      const int s1 = L.stages[0], s2 = L.stages[1];
+      const DownForm f1 = down_form(p, s1);
+      const int src = p.stages[s1].inputs[f1.slot];
+      key.plain = true;
+      key.vec = L.params.vec == 8 ? 8 : 4;
+      key.nw = 4;
+      key.tby = std::max(1, L.params.tile_h);
+      L.src.push_back(src);
+      L.src_chan.push_back(0);
+      key.src_dtypes.push_back(loc_of(src).dtype);
+      for (int s : {s1, s2}) {
+        L.dst.push_back(s);
+        key.dst_dtypes.push_back(plan.loc[s].dtype);
+      }
+      int W1, H1;
+      level_dims(plan.W, plan.H, p.stages[s1].level, &W1, &H1);
+      level_dims(plan.W, plan.H, p.stages[s2].level, &L.W, &L.H);
+      L.block = 32 * key.nw;
+      const int64_t wy = (L.H + key.tby - 1) / key.tby;
+      L.grid[0] = (unsigned)((W1 + 30 * key.vec - 1) / (30 * key.vec));
+      L.grid[1] = (unsigned)((wy + key.nw - 1) / key.nw);
+      L.grid[2] = (unsigned)p.stages[s1].channels;
+      if (L.grid[1] > 65535 || L.grid[2] > 65535) fail(WT_EUNSUPPORTED, "image too tall for the cascade kernel");
+      L.smem = cascade_smem(p, s1, key);
+      if (L.smem > 227 * 1024) fail(WT_EUNSUPPORTED, "cascade ring needs more than 227 KB of shared memory");
+      L.kname = kernel_name(p, key, false);
+      continue;
     } else if (key.chain) {
       const ChainForm cf = chain_form(p, L.stages);
       const int last = L.stages.back();
@@ -416,12 +463,15 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   static const char kChainVersion[] = "wt-chain-1";  // the reduction-chain kernel's own changes
   if (key.chain) h = fnv1a(kChainVersion, sizeof kChainVersion, h);
+  static const char kCascadeVersion[] = "wt-cascade-1";  // the two-level down-sampling kernel's own changes
+  if (key.cascade) h = fnv1a(kCascadeVersion, sizeof kCascadeVersion, h);
   static const char kVolVersion[] = "wt-vol-7";  // the 3-D group kernel's own changes
   if (key.vol) h = fnv1a(kVolVersion, sizeof kVolVersion, h);
   snprintf(hx, sizeof hx, "%012llx", (unsigned long long)(h & 0xffffffffffffull));
   if (key.otptb) return std::string("wt_otptb_") + hx;
   if (key.down) return std::string("wt_down_") + hx;
   if (key.chain) return std::string("wt_chain_") + hx;
+  if (key.cascade) return std::string("wt_down2_") + hx;
   if (key.vol) return std::string("wt_vol_") + hx;
   return std::string(fused ? (key.persistent ? "wt_batch_" : "wt_fused_") : "wt_plain_") + hx;
 }
@@ -430,6 +480,7 @@ std::string launch_source(const Pipeline &p, const Launch &L) {
   if (L.key.otptb) return emit_otptb(p, L.geom, L.key, L.kname);
   if (L.key.down) return emit_down(p, L.stages[0], L.key, L.kname);
   if (L.key.chain) return emit_chain(p, L.stages, L.key, L.kname);
+  if (L.key.cascade) return emit_cascade(p, L.stages[0], L.stages[1], L.key, L.kname);
   if (L.key.vol) return emit_vol(p, L.vol, L.key, L.kname);
   if (L.fused) return emit_fused(p, L.geom, L.key, L.kname);
   return emit_plain(p, L.stages[0], L.key, L.kname);

@@ -314,7 +314,11 @@ CostInfo cost_plain(const Pipeline &p, int s, int W0, int H0, int dtype, const C
     int pl = e.producer >= 0 ? p.stages[e.producer].level : 0;
     int pw, ph;
     level_dims(W0, H0, pl, &pw, &ph);
-    bytes += (double)pw * ph * (int)e.chans.size() * 4;
+    // channels read: every producer channel for per-channel taps (-1),
+    // else the distinct fixed ones
+    const int pc = e.producer >= 0 ? p.stages[e.producer].channels : p.in_channels[-e.producer - 1];
+    const bool per_channel = std::find(e.chans.begin(), e.chans.end(), -1) != e.chans.end();
+    bytes += (double)pw * ph * (per_channel ? pc : (int)e.chans.size()) * 4;
   }
   (void)dtype;
   ci.t[0] = bytes / std::max(1.0, pbytes);
@@ -375,6 +379,15 @@ CostInfo cost_group(const Pipeline &p, const std::vector<int> &stages, const Gro
     for (int l = L.lpad / V; l < 32 - L.rpad / V; l++) addr.push_back((int64_t)(L.lpad + (l - L.lpad / V) * V) * esz);
     tx_tile += T * min_gl_txs(addr.data(), (int)addr.size(), V * esz, txn);
   }
+  // gather sources (another level, read by plain loads, not staged): the
+  // source rows and columns under the tile, at the source's scale
+  for (const Node &n : g.nodes) {
+    if (!n.gather_mode) continue;
+    const bool down = n.gather_mode == WT_TAP_DOWN2;
+    const int cols = down ? 2 * 32 * V + 4 : 32 * V / 2 + 2;
+    const int rows = down ? 2 * src_rows + 3 : src_rows / 2 + 2;
+    tx_tile += (int64_t)rows * ((cols * esz + txn - 1) / txn + 1);
+  }
   const double total_tx = (double)tx_tile * tiles;
   int tb_per_sm = 0, warps_sm = 0;
   const double occ = alg2_occupancy(cfg, smem_tb, nw, regs, &tb_per_sm, &warps_sm);
@@ -383,7 +396,7 @@ CostInfo cost_group(const Pipeline &p, const std::vector<int> &stages, const Gro
   double iter_ns = 0;
   int64_t useful = 0, computed = 0;
   for (const Node &n : g.nodes) {
-    if (n.is_source) continue;
+    if (n.is_source || n.gather_mode) continue;  // read, not computed
     double ns = n.synthetic ? 0.5 + 0.5 * (double)n.prog.size() / 3 : st[n.id].ns_per_iter;
     iter_ns += ns;
     computed += (int64_t)32 * V * nsteps;
@@ -438,6 +451,29 @@ double chain_bytes(const Pipeline &p, const std::vector<int> &seg, int W0, int H
   return ((double)pw * ph + (double)lw * lh * p.stages[seg.back()].channels) * 4;
 }
 
+// HBM bytes of a group of down-sampling stages run as cascade launches:
+// each pair reads its first stage's producer once and writes both stages,
+// each other stage reads its producer and writes itself (FP32, like the
+// per-stage kernels' estimate).
+double cascade_bytes(const Pipeline &p, const std::vector<int> &seg, int W0, int H0) {
+  double bytes = 0;
+  for (const CascadeUnit &u : cascade_units(p, seg)) {
+    const DownForm f = down_form(p, u.s1);
+    const int pid = p.stages[u.s1].inputs[f.slot];
+    const int pl = pid >= 0 ? p.stages[pid].level : 0;
+    const int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
+    int w, h;
+    level_dims(W0, H0, pl, &w, &h);
+    bytes += (double)w * h * (f.chan >= 0 ? 1 : pc) * 4;
+    for (int s : {u.s1, u.s2}) {
+      if (s < 0) continue;
+      level_dims(W0, H0, p.stages[s].level, &w, &h);
+      bytes += (double)w * h * p.stages[s].channels * 4;
+    }
+  }
+  return bytes;
+}
+
 SegmentChoice best_for_segment(const Pipeline &p, const std::vector<int> &seg, int W, int H, int dtype,
                                const GpuConfig &cfg, const std::vector<StageStats> &st, const CostWeights &w,
                                double pbytes, const CandidateScorer *scorer) {
@@ -454,6 +490,22 @@ SegmentChoice best_for_segment(const Pipeline &p, const std::vector<int> &seg, i
     best.cost = ci.cost;
     best.fused = true;
     best.prm = GroupParams();
+    best.info = ci;
+    return best;
+  }
+  if (!cascade_units(p, seg).empty()) {
+    // down-sampling stages of two levels: cascade launches (Sec. 5's
+    // scaled groups, each pair's first level kept on chip), costed by
+    // their traffic like a per-stage kernel
+    CostInfo ci;
+    ci.t[0] = cascade_bytes(p, seg, W, H) / std::max(1.0, pbytes);
+    ci.cost = w.w[0] * ci.t[0];
+    ci.feasible = true;
+    ci.work = work_share(p, seg, W, H);
+    best.cost = ci.cost;
+    best.fused = true;
+    best.prm = GroupParams();
+    best.prm.tile_h = 8;  // S2 rows per warp
     best.info = ci;
     return best;
   }

@@ -314,6 +314,9 @@ struct CodegenKey {
   bool down = false;
   // reduction chain across levels (chain.cpp)
   bool chain = false;
+  // two-level down-sampling cascade (cascade.cpp): vec S1 values per lane,
+  // tby S2 rows per warp
+  bool cascade = false;
   // 3-D group (vol.cpp): split (streamed) axis 0 = rows, 1 = planes; vol_to
   // points of the other non-x axis per warp tile; tby streamed points
   bool vol = false;
@@ -371,6 +374,19 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key,
                       const std::string &kname);
 // Dynamic shared memory of the down-sampling kernel (its cp.async ring).
 int down_smem(const Pipeline &p, int sid, const CodegenKey &key);
+// cascade.cpp: S2 reduces S1 one level further (centred form), S1 a
+// streamable down-sampling stage; one kernel streams S1's producer and
+// writes both.
+bool cascade_pair_ok(const Pipeline &p, int s1, int s2);
+struct CascadeUnit {
+  int s1, s2;  // s2 = -1: s1 alone (the single-level streaming kernel)
+};
+// Launch units of a group of down-sampling stages (pairs and singles, in
+// launch order); empty unless every stage is a streamable down-sampling
+// stage and at least one pair forms.
+std::vector<CascadeUnit> cascade_units(const Pipeline &p, const std::vector<int> &seg);
+std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &key, const std::string &kname);
+int cascade_smem(const Pipeline &p, int s1, const CodegenKey &key);
 // chain.cpp: a group S1..Sk, each stage one level coarser: S1 a program of
 // one one-plane producer's DOWN2 taps inside its 2x2 block, every later
 // stage a weighted 2x2 sum of the one before (w[m][i + 2 j] for S(m+2));

@@ -67,6 +67,9 @@ using CandidateScorer = std::function<double(const std::vector<int> &, const Gro
 
 // HBM bytes of a reduction chain across levels run as one kernel.
 double chain_bytes(const Pipeline &p, const std::vector<int> &seg, int W0, int H0);
+// HBM bytes of a group of down-sampling stages run as cascade launches
+// (cascade_units): each pair's first stage is not read back.
+double cascade_bytes(const Pipeline &p, const std::vector<int> &seg, int W0, int H0);
 struct SegmentChoice {
   double cost = INFINITY;
   bool fused = false;

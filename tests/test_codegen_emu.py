@@ -37,7 +37,7 @@ def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mod
         emu.run(p, i, ins, outs, max_blocks, ws)
     per_stage = any((q or {}).get("flags", 0) & wt.WT_FLAG_PLAIN for q in (params or []))
     if exec_mode == wt.WT_EXEC_FUSED and d["n_launches"] == 1 and not per_stage:
-        assert d["fused"] or d["name"].startswith(("wt_chain_", "wt_vol_"))
+        assert d["fused"] or d["name"].startswith(("wt_chain_", "wt_vol_", "wt_down2_"))
     for o in outs:
         assert o.padding_intact(), "kernel wrote outside the image"
     name = {wt.WT_F32: "f32", wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
@@ -319,3 +319,51 @@ def test_tile_queue_mode(name, warps):
     assert np.abs(got[0] - ref[0]).max() <= 1e-5
     got1, _ = run_emulated(spec, [img], params=[dict(tile_h=24, warps_per_block=warps)])
     assert np.abs(got1[0] - ref[0]).max() <= 1e-5
+
+
+def cascade_spec(c=1):
+    """P -> D1 -> D2, two 5x5 binomial reduces; both levels are outputs."""
+    b = P.Builder("cascade", [c])
+    inp = P.input_id(0)
+    d1 = b.stage("d1", P._down(inp), c)
+    d2 = b.stage("d2", P._down(d1), c)
+    b.output(d1)
+    b.output(d2)
+    return b.build()
+
+
+@pytest.mark.parametrize("w,h,tile_h,vec,c,dtype,tol", [
+    (37, 23, 4, 4, 1, wt.WT_F32, 1e-5), (1, 1, 2, 4, 1, wt.WT_F32, 1e-5), (2, 5, 1, 4, 1, wt.WT_F32, 1e-5),
+    (300, 90, 3, 4, 1, wt.WT_F32, 1e-5), (530, 41, 5, 8, 3, wt.WT_F32, 1e-5),
+    (1100, 37, 4, 4, 1, wt.WT_F32, 1e-5), (1203, 29, 3, 8, 1, wt.WT_BF16, 1.6e-2),
+    (2100, 19, 6, 8, 3, wt.WT_F16, 2e-3), (1030, 64, 8, 4, 1, wt.WT_BF16, 1.6e-2)])
+def test_cascade_two_levels(w, h, tile_h, vec, c, dtype, tol):
+    """Two down-sampling levels in one kernel: S1 rows written and fed to
+    S2 on chip.  Small images (every warp at an edge, clamped loads) and
+    wide ones (interior warps stage their producer rows by 16-byte copies);
+    heights with a partial last unrolled round; both levels against the
+    oracle."""
+    spec = cascade_spec(c)
+    dn = {wt.WT_F32: "f32", wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
+    img = rnd(w * 7 + h, w, h, c, dtype=dn)
+    got, d = run_emulated(spec, [img], dtype=dtype, groups=[0, 0], params=[dict(tile_h=tile_h, vec=vec)])
+    assert d["n_launches"] == 1 and d["name"].startswith("wt_down2_")
+    ref = oracle_of(spec, [img])
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() <= tol
+
+
+def test_cascade_blend_groups():
+    """The blend with its Gaussian levels 1-2 and 3-4 as two-level cascade
+    groups (mask pyramid included), the other levels fused per level."""
+    spec = P.blend()
+    w, h = 270, 133
+    A, B = rnd(11, w, h, 3), rnd(12, w, h, 3)
+    M = I.smooth_mask(13, w, h)
+    g = [0] * 6 + [1] * 6 + [2] * 4 + sum([[3 + k] * 4 for k in range(5)], [])
+    params = [dict(tile_h=4), dict(tile_h=2)] + [dict(tile_h=8)] * 6
+    got, d = run_emulated(spec, [A, B, M], groups=g, params=params)
+    p = wt.Pipeline(spec)
+    p.schedule(groups=g, params=params)
+    assert p.launches_per_run() == 3 + 3 + 6
+    assert np.abs(got[0] - oracle_of(spec, [A, B, M])[0]).max() <= 1e-5

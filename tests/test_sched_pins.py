@@ -127,15 +127,26 @@ def test_auto_schedule_blend_groups_by_level():
 
 
 def test_dp_fusion_groups_blend_by_level():
-    """DP-Fusion over the 36-stage blend (stages ordered by level) finds one
-    fused group per pyramid level: taps of the neighbouring level are gather
-    sources, groups never span levels."""
+    """DP-Fusion over the 36-stage blend (stages ordered by level): the
+    Gaussian levels 1-2 and 3-4 as two groups spanning two levels each (a
+    cascade launch per image: each pair's first level is written and
+    reduced again on chip, so its read-back drops out of the traffic term),
+    the coarsest level's stages as per-stage kernels, then one fused group
+    per finer level (taps of the neighbouring level are gather sources)."""
     spec = P.blend()
     p = wt.Pipeline(spec)
     p.schedule_auto(8192, 8192, wt.WT_BF16, wt.WT_MODEL_ANALYTIC)
     s = p.schedule_get()
-    assert s["groups"] == P.blend_groups()
-    assert p.launches_per_run() == 10
+    expect = [0] * 6 + [1] * 6 + [2, 3, 4, 5] + sum([[6 + k] * 4 for k in range(5)], [])
+    assert s["groups"] == expect
+    assert p.launches_per_run() == 3 + 3 + 4 + 5
+    img = wt.image(0x10000000, 8192, 8192, 3, wt.WT_BF16, 8192 * 2)
+    msk = wt.image(0x10000000, 8192, 8192, 1, wt.WT_BF16, 8192 * 2)
+    names = [p.kernel_name(i, [img, img, msk], [img]) for i in range(15)]
+    assert all(n.startswith("wt_down2_") for n in names[:6]), names
+    assert all(n.startswith("wt_down_") for n in names[6:9]), names
+    assert names[9].startswith("wt_plain_"), names
+    assert all(n.startswith("wt_fused_") for n in names[10:]), names
 
 
 def test_dp_fusion_proposes_reduction_chain_across_levels():
