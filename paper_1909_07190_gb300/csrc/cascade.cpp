@@ -156,7 +156,10 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
   std::ostringstream o;
   o << kDeviceSource;
   o << "static_assert(sizeof(WtArgs) == " << sizeof(KernelArgs) << ", \"WtArgs layout\");\n";
-  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * NW << ") " << kname
+  // register cap through the launch bounds: enough resident blocks that
+  // each thread gets at most max_regs
+  const int min_blocks = key.max_regs > 0 ? std::max(1, 65536 / (key.max_regs * 32 * NW)) : 1;
+  o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * NW << ", " << min_blocks << ") " << kname
     << "(const __grid_constant__ WtArgs a) {\n";
   o << "extern __shared__ __align__(128) unsigned char wt_smem[];\n";
   o << "const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;\n";
@@ -191,10 +194,26 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
   o << "float *xb = (float *)(wb + " << (R.ring_bytes + 15) / 16 * 16 << ");\n";
   o << "if (lane < " << 2 * (kLP + kRP) << ") xb[(lane >> 3) * " << R.xr << " + ((lane & 7) < " << kLP
     << " ? (lane & 7) : " << kLP + 32 * VO1 - kLP << " + (lane & 7))] = 0.f;\n";
-  o << "float";
+  // S1 accumulators as packed FP32 pairs, the column weights as pairs
+  o << "wt_u64";
   for (int s = 0; s < NA1; s++)
-    for (int k = 0; k < VO1; k++) o << (s || k ? ", " : " ") << "acc" << s << "_" << k << " = 0.f";
-  o << ";\nfloat";
+    for (int k = 0; k < VO1 / 2; k++) o << (s || k ? ", " : " ") << "acc" << s << "_" << k << " = 0";
+  o << ";\n";
+  for (int dy = DY0; dy <= DY1; dy++)
+    o << "const wt_u64 wy" << dy - DY0 << " = wt_pk(" << float_literal(f1.wy[dy - DY0]) << ", "
+      << float_literal(f1.wy[dy - DY0]) << ");\n";
+  // per-lane copy offsets: the lane's own 2 VO1 values, and the halo
+  // chunks left (lane 0) and right (lane 31) of the warp's columns
+  o << "const wt_u32 mdo = (" << R.ncl * R.che << " + lane * " << 2 * VO1 << ") * " << sesz << ";\n";
+  o << "const wt_i64 mso = (wt_i64)xs * " << sesz << ";\n";
+  o << "const wt_u32 hdo = lane == 0 ? 0u : " << (R.ncl * R.che + 64 * VO1) * sesz << "u;\n";
+  o << "const wt_i64 hso = (wt_i64)(lane == 0 ? 2 * b0 - " << R.ncl * R.che << " : 2 * b0 + " << 64 * VO1 << ") * "
+    << sesz << ";\n";
+  for (int c = 0; c < std::max(R.ncl, R.ncr); c++)
+    o << "const bool hp" << c << " = " << (c < R.ncl ? "lane == 0" : "false") << " || "
+      << (c < R.ncr ? "lane == 31" : "false") << ";\n";
+  o << "(void)mdo; (void)mso; (void)hdo; (void)hso;\n";
+  o << "float";
   for (int s = 0; s < NA2; s++)
     for (int k = 0; k < VO2; k++) o << (s || k ? ", " : " ") << "bcc" << s << "_" << k << " = 0.f";
   o << ";\n";
@@ -207,14 +226,9 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
         << "), 0, Hs - 1) * pitch;\n";
       o << "const wt_u32 sb = wbs + " << (slot * 2 + q) * R.segb << ";\n";
       for (int c = 0; c < 2 * VO1 * sesz / 16; c++)
-        o << "wt_cp_async16(sb + (" << R.ncl * R.che << " + lane * " << 2 * VO1 << ") * " << sesz << " + " << 16 * c
-          << ", gp + (wt_i64)xs * " << sesz << " + " << 16 * c << ");\n";
-      for (int c = 0; c < R.ncl; c++)
-        o << "if (lane == 0) wt_cp_async16(sb + " << 16 * c << ", gp + (wt_i64)(2 * b0 - " << R.ncl * R.che << ") * "
-          << sesz << " + " << 16 * c << ");\n";
-      for (int c = 0; c < R.ncr; c++)
-        o << "if (lane == 31) wt_cp_async16(sb + " << (R.ncl * R.che + 64 * VO1) * sesz + 16 * c
-          << ", gp + (wt_i64)(2 * b0 + " << 64 * VO1 << ") * " << sesz << " + " << 16 * c << ");\n";
+        o << "wt_cp_async16(sb + mdo + " << 16 * c << ", gp + mso + " << 16 * c << ");\n";
+      for (int c = 0; c < std::max(R.ncl, R.ncr); c++)
+        o << "wt_cp_async16_if(hp" << c << ", sb + hdo + " << 16 * c << ", gp + hso + " << 16 * c << ");\n";
       o << "}\n";
     }
   };
@@ -231,11 +245,13 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
   // S1 row j complete in accumulator slot `slot1`; jr = j modulo U
   auto row_done = [&](int slot1, int jr, const std::string &jexpr) {
     o << "{ const int j = " << jexpr << ";\nif (j >= 0) {\nconst int r1 = R1s + j;\n";
-    for (int k = 0; k < VO1; k++) {
-      o << "const float g" << k << " = acc" << slot1 << "_" << k;
-      if (f1.c != 0) o << " + " << float_literal(f1.c);
-      o << ";\n";
-    }
+    o << "float";
+    for (int k = 0; k < VO1; k++) o << (k ? ", " : " ") << "g" << k;
+    o << ";\n";
+    for (int k = 0; k < VO1 / 2; k++)
+      o << "wt_upk(acc" << slot1 << "_" << k << ", g" << 2 * k << ", g" << 2 * k + 1 << ");\n";
+    if (f1.c != 0)
+      for (int k = 0; k < VO1; k++) o << "g" << k << " += " << float_literal(f1.c) << ";\n";
     // S1 to memory: owned lanes and rows inside the image
     o << "if (own && (unsigned)(j - " << R2 << ") < " << 2 * T2 << "u && r1 < H1 && c1 < W1) {\n";
     o << "unsigned char *op_ = dp1 + (wt_i64)r1 * a.dst[0].pitch;\n";
@@ -248,18 +264,26 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
       o << "if (c1 + " << k << " < W1) wt_st1_" << dtype_name(d1) << "(op_ + (wt_i64)(c1 + " << k << ") * " << e1
         << ", g" << k << ");\n";
     o << "}\n}\n";
-    // exchange row (double-buffered by row parity)
+    // S2's taps of S1: the lane's own values and its neighbours' by warp
+    // shuffles; at the image's left and right edges through the exchange
+    // row (double-buffered by row parity), columns clamped to the image
+    o << "float";
+    for (int t = EX0; t <= EX1; t++) o << (t == EX0 ? " " : ", ") << "e" << t - EX0;
+    o << ";\nif (!xedge) {\n";
+    for (int t = EX0; t <= EX1; t++) {
+      if (t < 0)
+        o << "e" << t - EX0 << " = __shfl_up_sync(0xffffffffu, g" << VO1 + t << ", 1);\n";
+      else if (t < VO1)
+        o << "e" << t - EX0 << " = g" << t << ";\n";
+      else
+        o << "e" << t - EX0 << " = __shfl_down_sync(0xffffffffu, g" << t - VO1 << ", 1);\n";
+    }
+    o << "} else {\n";
     o << "float *xr = xb + " << mod(jr, 2) * R.xr << ";\n";
     for (int b = 0; b < VO1; b += 4)
       o << "*(float4 *)(xr + " << kLP + b << " + lane * " << VO1 << ") = make_float4(g" << b << ", g" << b + 1
         << ", g" << b + 2 << ", g" << b + 3 << ");\n";
     o << "__syncwarp();\n";
-    o << "float";
-    for (int t = EX0; t <= EX1; t++) o << (t == EX0 ? " " : ", ") << "e" << t - EX0;
-    o << ";\nif (!xedge) {\n";
-    for (int t = EX0; t <= EX1; t++)
-      o << "e" << t - EX0 << " = xr[" << kLP + t << " + lane * " << VO1 << "];\n";
-    o << "} else {\n";
     for (int t = EX0; t <= EX1; t++)
       o << "e" << t - EX0 << " = xr[" << kLP << " + wt_clampi(c1 + (" << t << "), 0, W1 - 1) - b0];\n";
     o << "}\n";
@@ -324,6 +348,7 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
   // one step: P rows DY0 + 2m and DY0 + 2m + 1 (relative to 2 R1s), ring
   // slot base u (compile time), step index expression mexpr
   auto step = [&](bool fast, int u, const std::string &mexpr) {
+    std::pair<int, int> done{0, 0};  // slot and delta of the S1 row completed by this step
     o << "{\nconst int m = " << mexpr << ";\n";
     if (fast) {
       o << "if (m + " << R.pd << " < " << M << ") {\n";
@@ -356,9 +381,7 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
           o << vn(q, i) << " = wt_ld1_" << dtype_name(sdt) << "(rp" << q << " + (wt_i64)wt_clampi(xs + (" << i - LH
             << "), 0, Ws - 1) * " << sesz << ");\n";
       }
-    }
-    for (int q = 0; q < 2; q++) {
-      // S1 row pass at stride 2
+      // S1 row pass at stride 2 (one P row at a time: fewer live values)
       for (int k = 0; k < VO1; k++) {
         o << "const float h" << q << "_" << k << " = ";
         bool first = true;
@@ -376,13 +399,22 @@ std::string emit_cascade(const Pipeline &p, int s1, int s2, const CodegenKey &ke
         const int delta = (DY0 + q - dy) / 2;  // <= 0
         const int slot = mod(u + delta, NA1);
         if (w == 0 && dy != DY0 && dy != DY1) continue;
-        for (int k = 0; k < VO1; k++)
-          o << "acc" << slot << "_" << k << (dy == DY0 ? " = " : " += ") << float_literal(w) << " * h" << q << "_" << k
-            << ";\n";
-        if (dy == DY1) row_done(slot, mod(u + delta, 2 * NA2), "m + (" + std::to_string(delta) + ")");
+        for (int k = 0; k < VO1 / 2; k++) {
+          const std::string hp = "wt_pk(h" + std::to_string(q) + "_" + std::to_string(2 * k) + ", h" +
+                                 std::to_string(q) + "_" + std::to_string(2 * k + 1) + ")";
+          const std::string acc = "acc" + std::to_string(slot) + "_" + std::to_string(k);
+          if (dy == DY0)
+            o << acc << " = wt_mul2(wy" << dy - DY0 << ", " << hp << ");\n";
+          else
+            o << acc << " = wt_fma2(wy" << dy - DY0 << ", " << hp << ", " << acc << ");\n";
+        }
+        if (dy == DY1) done = {slot, delta};
       }
     }
     if (fast) o << "__syncwarp();\n";  // ring slot read by all lanes before its refill
+    // the completed S1 row (its slot is not touched by the other P row of
+    // the step), after both P rows' values are dead
+    row_done(done.first, mod(u + done.second, 2 * NA2), "m + (" + std::to_string(done.second) + ")");
     o << "}\n";
   };
   for (int fpath = 1; fpath >= 0; fpath--) {

@@ -188,6 +188,12 @@ static __device__ __forceinline__ void wt_cp_async16(wt_u32 dst, const void *src
 static __device__ __forceinline__ void wt_cp_async4(wt_u32 dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
+// the 16-byte copy only where p holds (predicated, no branch)
+static __device__ __forceinline__ void wt_cp_async16_if(bool p, wt_u32 dst, const void *src) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q cp.async.cg.shared.global [%1], [%2], 16;\n}" ::"r"((int)p),
+               "r"(dst), "l"(src)
+               : "memory");
+}
 static __device__ __forceinline__ void wt_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 #define WT_CP_ASYNC_WAIT(n) asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory")
 // ------------------------------- read-only pairs (aligned to their size)

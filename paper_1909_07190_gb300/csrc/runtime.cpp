@@ -360,6 +360,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       key.vec = L.params.vec == 8 ? 8 : 4;
       key.nw = 4;
       key.tby = std::max(1, L.params.tile_h);
+      key.max_regs = L.params.max_regs;
       L.src.push_back(src);
       L.src_chan.push_back(0);
       key.src_dtypes.push_back(loc_of(src).dtype);
@@ -459,11 +460,11 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   if (gather) h = fnv1a(kGatherVersion, sizeof kGatherVersion, h);
   static const char kOtptbVersion[] = "wt-otptb-2";  // the block-tile kernel's own changes
   if (key.otptb) h = fnv1a(kOtptbVersion, sizeof kOtptbVersion, h);
-  static const char kDownVersion[] = "wt-down-4";  // the down-sampling kernel's own changes
+  static const char kDownVersion[] = "wt-down-5";  // the down-sampling kernel's own changes
   if (key.down) h = fnv1a(kDownVersion, sizeof kDownVersion, h);
   static const char kChainVersion[] = "wt-chain-1";  // the reduction-chain kernel's own changes
   if (key.chain) h = fnv1a(kChainVersion, sizeof kChainVersion, h);
-  static const char kCascadeVersion[] = "wt-cascade-1";  // the two-level down-sampling kernel's own changes
+  static const char kCascadeVersion[] = "wt-cascade-3";  // the two-level down-sampling kernel's own changes
   if (key.cascade) h = fnv1a(kCascadeVersion, sizeof kCascadeVersion, h);
   static const char kVolVersion[] = "wt-vol-7";  // the 3-D group kernel's own changes
   if (key.vol) h = fnv1a(kVolVersion, sizeof kVolVersion, h);

@@ -239,10 +239,26 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
     << " <= Ws;\n";
   o << "unsigned char *wb = wt_smem + wid * " << R.warp_bytes << ";\n";
   o << "const wt_u32 wbs = wt_smem_u32(wb);\n(void)wbs;\n";
-  o << "float";
+  // accumulators as packed FP32 pairs (outputs 2k, 2k + 1 of the lane)
+  o << "wt_u64";
   for (int s = 0; s < NA; s++)
-    for (int k = 0; k < VO; k++) o << (s || k ? ", " : " ") << "acc" << s << "_" << k << " = 0.f";
+    for (int k = 0; k < VO / 2; k++) o << (s || k ? ", " : " ") << "acc" << s << "_" << k << " = 0";
   o << ";\n";
+  // the column weights as packed pairs
+  for (int dy = DY0; dy <= DY1; dy++)
+    o << "const wt_u64 wy" << dy - DY0 << " = wt_pk(" << float_literal(f.wy[dy - DY0]) << ", "
+      << float_literal(f.wy[dy - DY0]) << ");\n";
+  // per-lane copy offsets of the fast path: the lane's own 2 VO values, and
+  // the halo chunks left (lane 0) and right (lane 31) of the warp's columns
+  o << "const wt_u32 mdo = (" << R.ncl * R.che << " + lane * " << 2 * VO << ") * " << sesz << ";\n";
+  o << "const wt_i64 mso = (wt_i64)xs * " << sesz << ";\n";
+  o << "const wt_u32 hdo = lane == 0 ? 0u : " << (R.ncl * R.che + 64 * VO) * sesz << "u;\n";
+  o << "const wt_i64 hso = (wt_i64)(lane == 0 ? 2 * xo0 - " << R.ncl * R.che << " : 2 * xo0 + " << 64 * VO << ") * "
+    << sesz << ";\n";
+  for (int c = 0; c < std::max(R.ncl, R.ncr); c++)
+    o << "const bool hp" << c << " = " << (c < R.ncl ? "lane == 0" : "false") << " || "
+      << (c < R.ncr ? "lane == 31" : "false") << ";\n";
+  o << "(void)mdo; (void)mso; (void)hdo; (void)hso;\n";
   auto vn = [](int q, int i) { return "v" + std::to_string(q) + "_" + std::to_string(i); };
   // cp.async of both producer rows of step `mexpr` into ring slot `slot`
   auto issue = [&](int slot, const std::string &mexpr) {
@@ -251,14 +267,9 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         << "), 0, Hs - 1) * pitch;\n";
       o << "const wt_u32 sb = wbs + " << (slot * 2 + q) * R.segb << ";\n";
       for (int c = 0; c < 2 * VO * sesz / 16; c++)
-        o << "wt_cp_async16(sb + (" << R.ncl * R.che << " + lane * " << 2 * VO << ") * " << sesz << " + " << 16 * c
-          << ", gp + (wt_i64)xs * " << sesz << " + " << 16 * c << ");\n";
-      for (int c = 0; c < R.ncl; c++)
-        o << "if (lane == 0) wt_cp_async16(sb + " << 16 * c << ", gp + (wt_i64)(2 * xo0 - " << R.ncl * R.che
-          << ") * " << sesz << " + " << 16 * c << ");\n";
-      for (int c = 0; c < R.ncr; c++)
-        o << "if (lane == 31) wt_cp_async16(sb + " << (R.ncl * R.che + 64 * VO) * sesz + 16 * c
-          << ", gp + (wt_i64)(2 * xo0 + " << 64 * VO << ") * " << sesz << " + " << 16 * c << ");\n";
+        o << "wt_cp_async16(sb + mdo + " << 16 * c << ", gp + mso + " << 16 * c << ");\n";
+      for (int c = 0; c < std::max(R.ncl, R.ncr); c++)
+        o << "wt_cp_async16_if(hp" << c << ", sb + hdo + " << 16 * c << ", gp + hso + " << 16 * c << ");\n";
       o << "}\n";
     }
   };
@@ -320,17 +331,28 @@ std::string emit_down(const Pipeline &p, int sid, const CodegenKey &key, const s
         const int delta = (DY0 + q - dy) / 2;  // <= 0
         const int slot = ((u + delta) % NA + NA) % NA;
         if (w == 0 && dy != DY0) continue;
-        for (int k = 0; k < VO; k++)
-          o << "acc" << slot << "_" << k << (dy == DY0 ? " = " : " += ") << float_literal(w) << " * h" << q << "_" << k
-            << ";\n";
+        for (int k = 0; k < VO / 2; k++) {
+          const std::string hp = "wt_pk(h" + std::to_string(q) + "_" + std::to_string(2 * k) + ", h" +
+                                 std::to_string(q) + "_" + std::to_string(2 * k + 1) + ")";
+          const std::string acc = "acc" + std::to_string(slot) + "_" + std::to_string(k);
+          if (dy == DY0)
+            o << acc << " = wt_mul2(wy" << dy - DY0 << ", " << hp << ");\n";
+          else
+            o << acc << " = wt_fma2(wy" << dy - DY0 << ", " << hp << ", " << acc << ");\n";
+        }
         if (dy != DY1) continue;
         // output row j is complete (rows j < 0 and j >= T are not stored)
         o << "{ const int j = m + (" << delta << "), yo = yo0 + j;\n";
         o << "if (j >= 0 && j < " << T << " && yo < H) {\n";
         o << "unsigned char *op_ = dp + (wt_i64)yo * a.dst[0].pitch;\n";
         std::vector<std::string> outv;
+        o << "float";
+        for (int k = 0; k < VO; k++) o << (k ? ", " : " ") << "o" << k;
+        o << ";\n";
+        for (int k = 0; k < VO / 2; k++)
+          o << "wt_upk(acc" << slot << "_" << k << ", o" << 2 * k << ", o" << 2 * k + 1 << ");\n";
         for (int k = 0; k < VO; k++) {
-          std::string e = "acc" + std::to_string(slot) + "_" + std::to_string(k);
+          std::string e = "o" + std::to_string(k);
           if (f.c != 0) e = "(" + e + " + " + float_literal(f.c) + ")";
           outv.push_back(e);
         }

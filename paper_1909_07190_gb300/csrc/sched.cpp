@@ -505,7 +505,12 @@ SegmentChoice best_for_segment(const Pipeline &p, const std::vector<int> &seg, i
     best.cost = ci.cost;
     best.fused = true;
     best.prm = GroupParams();
-    best.prm.tile_h = 8;  // S2 rows per warp
+    // S2 rows per warp: taller where the coarser level is tall (fewer
+    // re-streamed halo rows), short where it is small (more warps)
+    int lv = 0, w2, h2;
+    for (int s : seg) lv = std::max(lv, p.stages[s].level);
+    level_dims(W, H, lv, &w2, &h2);
+    best.prm.tile_h = std::max(4, std::min(16, h2 / 128));
     best.info = ci;
     return best;
   }

@@ -230,23 +230,45 @@ def blend_groups(levels: int = 6) -> list:
 
 
 def blend_schedule(levels: int = 6) -> tuple:
-    """(groups, params) of the blend's default schedule: blend_groups(), with
-    the pure down-sampling groups of levels 1..levels-2 run as per-stage
-    kernels (each a streaming down-sampling kernel: a fused group of gathers
-    has nothing to keep on chip, and its one-channel mask stage would be
-    computed once per tile channel) and the other groups fused."""
-    groups = blend_groups(levels)
+    """(groups, params) of the blend's default schedule (measured fastest on
+    a GB300 at 8192x8192x3 BF16):
+      - Gaussian levels 1 and 2: per-stage streaming down-sampling kernels
+        (a fused group of gathers has nothing to keep on chip, and its
+        one-channel mask stage would be computed once per tile channel);
+        output rows per warp 14 and 8;
+      - Gaussian levels 3 and 4 (then 5 and 6, ...): one group spanning the
+        two levels, run as two-level cascade launches (each image's level-3
+        reduce written and reduced again on chip), 4 level-4 rows per warp;
+        a level left without a partner runs per stage;
+      - the coarsest level with its blend, then one fused group per finer
+        level: short warp tiles where the level is small; at level 1, 14
+        rows, at level 0, 48 rows, both with 4-row staging chunks and at most
+        112 registers (20 warps per SM: the level-0 group is bound by memory
+        latency; taller level-0 tiles re-read fewer gather rows)."""
     plain = 4  # WT_FLAG_PLAIN
-    # output rows per warp of the streaming down-sampling kernels: shorter
-    # at the small levels, where parallelism, not the row halo, limits them
-    down_rows = [14, 8] + [4] * max(0, levels - 4)
-    params = [dict(flags=plain, tile_h=t) for t in down_rows[:levels - 2]]
-    # fused groups from the coarsest level to level 0: short warp tiles
-    # where the level is small (more tiles in flight); at levels 1 and 0, 14
-    # rows, 4-row staging chunks and at most 112 registers, so that 20 warps
-    # fit on an SM (the level-0 group is bound by memory latency)
-    params += [dict(tile_h=8) if lv >= 2 else dict(tile_h=14, chunk_rows=4, max_regs=112)
-               for lv in range(levels - 1, -1, -1)]
+    groups, params = [], []
+    g = 0
+    k = 1
+    while k <= levels - 2:
+        if k <= 2 or k + 1 > levels - 2:
+            groups += [g] * 3
+            params.append(dict(flags=plain, tile_h=[14, 8][k - 1] if k <= 2 else 4))
+            k += 1
+        else:
+            groups += [g] * 6
+            params.append(dict(tile_h=4))
+            k += 2
+        g += 1
+    groups += [g] * 4  # the coarsest level's reduces and its blend
+    g += 1
+    for _ in range(levels - 1):
+        groups += [g] * 4
+        g += 1
+    for lv in range(levels - 1, -1, -1):
+        if lv >= 2:
+            params.append(dict(tile_h=8))
+        else:
+            params.append(dict(tile_h=14 if lv == 1 else 48, chunk_rows=4, max_regs=112))
     return groups, params
 
 

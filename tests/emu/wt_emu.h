@@ -312,6 +312,9 @@ static inline void wt_cp_async4(wt_u32 dst, const void *src) {
   if (!wt_emu_in_global(src, 4)) { wt_emu_fail("cp.async source outside the registered buffers"); return; }
   memcpy(wt_emu_sptr(dst), src, 4);
 }
+static inline void wt_cp_async16_if(bool p, wt_u32 dst, const void *src) {
+  if (p) wt_cp_async16(dst, src);
+}
 static inline void wt_cp_async_commit() {}
 #define WT_CP_ASYNC_WAIT(n) ((void)(n))
 static inline void wt_ld2_f32(const void *p, float &a, float &b) {

@@ -61,14 +61,15 @@ def test_blend_fused_levels(dtype, w, h, tile_h):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_blend_default_mixed_schedule(dtype):
-    """The default blend schedule: down-sampling groups per stage, the other
-    levels fused (18 launches)."""
+    """The default blend schedule: Gaussian levels 1-2 per stage, levels 3-4
+    as a cascade group (one launch per image), the other levels fused (15
+    launches)."""
     w, h = 555, 301
     A = I.round_to(I.uniform_image(31, w, h, 3), dtype)
     B = I.round_to(I.uniform_image(32, w, h, 3), dtype)
     M = I.round_to(I.smooth_mask(33, w, h), dtype)
     got, p = run_blend(A, B, M, dtype, mixed=True)
-    assert p.launches_per_run() == 18
+    assert p.launches_per_run() == 15
     assert np.abs(got - oracle(A, B, M)).max() <= TOL[dtype]
 
 

@@ -54,8 +54,10 @@ def test_cascade_8192_sampled():
     W = H = 8192
     img = rnd(93, W, H, 3, "bf16")
     got, p = run_pipe(spec, [img], dtype="bf16", groups=[0, 0], params=[dict(tile_h=8)])
-    img_name = wt.image(0x10000000, W, H, 3, wt.WT_BF16, W * 2)
-    assert p.kernel_name(0, [img_name], [img_name, img_name]).startswith("wt_down2_")
+    i0 = wt.image(0x10000000, W, H, 3, wt.WT_BF16, W * 2)
+    i1 = wt.image(0x10000000, W // 2, H // 2, 3, wt.WT_BF16, W)
+    i2 = wt.image(0x10000000, W // 4, H // 4, 3, wt.WT_BF16, W // 2)
+    assert p.kernel_name(0, [i0], [i1, i2]).startswith("wt_down2_")
     rng = np.random.default_rng(11)
     worst = 0.0
     for lvl, size in ((1, 4096), (2, 2048)):

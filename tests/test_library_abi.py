@@ -176,11 +176,12 @@ def test_costmodel_load_rejects_bad_files(tmp_path):
 
 
 def test_launch_count_with_per_stage_groups():
-    """Groups flagged to run per stage count one launch per live stage."""
+    """Groups flagged to run per stage count one launch per live stage, a
+    cascade group one launch per pair of levels of an image."""
     p = wt.Pipeline(P.blend())
     groups, params = P.blend_schedule()
     p.schedule(groups=groups, params=params)
-    assert p.launches_per_run() == 4 * 3 + 6
+    assert p.launches_per_run() == 2 * 3 + 3 + 6
     p.schedule(groups=P.blend_groups())
     assert p.launches_per_run() == 10
 
