@@ -719,8 +719,20 @@ def measure(wt, torch, workload, args, dist, world, rank, local, steps, warmup, 
                                  dist)
         plain.check(sp)
         unfused = {"value": job_rate(work.px, world, plain_steps, total_p), "unit": "Mpixels/s",
-                   "ms_per_step": total_p / plain_steps, "launches_per_step": plain.launches_per_run()}
+                   "ms_per_step": total_p / plain_steps, "launches_per_step": plain.launches_per_run(),
+                   "intermediates": "f32"}
         plain.close()
+        if WORKLOADS[workload][3] != "f32":
+            # the same per-stage kernels with intermediates in the storage type
+            plain16 = wt.Pipeline(spec)
+            plain16.schedule(exec_mode=wt.WT_EXEC_PLAIN, intermediate_dtype=wt.DTYPES[WORKLOADS[workload][3]])
+            total_q, _ = timed_steps(torch, work, lambda i, s: work.run(plain16, i, s), plain_steps, warmup,
+                                     per_graph, dist)
+            plain16.check(sp)
+            unfused["storage_type_intermediates"] = {
+                "value": job_rate(work.px, world, plain_steps, total_q), "unit": "Mpixels/s",
+                "ms_per_step": total_q / plain_steps, "intermediates": WORKLOADS[workload][3]}
+            plain16.close()
     e2e_steps = max(3, min(200, steps // 4)) if not batched else 3
     e2e_value, h2d, d2h = work.e2e(fused, sp, warmup if not batched else 1, e2e_steps)
     value = job_rate(work.px, world, steps, total_f)
@@ -766,15 +778,29 @@ def measure(wt, torch, workload, args, dist, world, rank, local, steps, warmup, 
 
 
 def cpu_baseline(work, name, spec, dts, seconds):
-    if name == "blend":
-        r, cores, n, dt, sample = cpu_blend_rate(dts, seconds)
-    else:
+    """The oracle's rate on all host cores, then on one core (a quarter of
+    the time budget, at least 2 s)."""
+    from oracle import oracle as O
+
+    def rate(budget):
+        if name == "blend":
+            return cpu_blend_rate(dts, budget)
         img = work.cpu_sample(dts)
         cspec = spec if img.ndim == 2 else spec_for_depth(name, img.shape[0])
-        r, cores, n, dt = cpu_oracle_rate(cspec, img, seconds)
-        sample = "%d images of %dx%d%s, %.1f s" % (n, img.shape[-1], img.shape[-2],
-                                                  "" if img.ndim == 2 else "x%d" % img.shape[0], dt)
-    return {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle", "sample": sample}
+        r, cores, n, dt = cpu_oracle_rate(cspec, img, budget)
+        return r, cores, n, dt, "%d images of %dx%d%s, %.1f s" % (n, img.shape[-1], img.shape[-2],
+                                                                "" if img.ndim == 2 else "x%d" % img.shape[0], dt)
+
+    r, cores, _, _, sample = rate(seconds)
+    out = {"value": r, "unit": "Mpixels/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if cores > 1:
+        O.set_num_threads(1)
+        try:
+            r1, _, _, _, sample1 = rate(max(2.0, seconds / 4))
+        finally:
+            O.set_num_threads(cores)
+        out["one_core"] = {"value": r1, "unit": "Mpixels/s", "sample": sample1}
+    return out
 
 
 COSTMODEL_FILE = os.path.join(ROOT, "paper_1909_07190_gb300", "costmodel_gb300.txt")

@@ -27,6 +27,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops from now on (n >= 1; timing only). */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 /* Source coordinate of a tap along one axis (Sec. 2.3; Sec. 5 scaling). */

@@ -115,6 +115,8 @@ void or_blend(const double *A, const double *B, const double *M, int W, int H,
               int C, int levels, double *out);
 
 int or_num_threads(void);
+/* Threads of the parallel loops from now on (n >= 1; timing only). */
+void or_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -96,12 +96,18 @@ def _load():
             lib.or_blend.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, dp]
             lib.or_num_threads.restype = ctypes.c_int
+            lib.or_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
     return _lib
 
 
 def num_threads() -> int:
     return int(_load().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing only)."""
+    _load().or_set_num_threads(int(n))
 
 
 def _f64(a) -> np.ndarray:
