@@ -55,6 +55,23 @@ class HostImage:
         return bool(np.all(np.isnan(pad)))
 
 
+def _runtime_object() -> str:
+    """The emulator runtime, compiled once per content hash (it is the same
+    for every kernel; compiling it with each kernel doubled a cold run)."""
+    rt = os.path.join(HERE, "emu_rt.cpp")
+    h = hashlib.sha1((open(rt).read() + open(os.path.join(HERE, "wt_emu.h")).read()).encode()).hexdigest()[:16]
+    obj = os.path.join(CACHE, "emu_rt_%s.o" % h)
+    if not os.path.exists(obj):
+        os.makedirs(CACHE, exist_ok=True)
+        tmp = obj + ".%d.tmp" % os.getpid()
+        r = subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-c", "-w", "-I", HERE, rt, "-o", tmp],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("emulator runtime compile failed:\n" + r.stderr[-5000:])
+        os.replace(tmp, obj)
+    return obj
+
+
 def _compile(source: str, name: str) -> ctypes.CDLL:
     body = source.split(MARK, 1)[1]
     text = '#include "wt_emu.h"\n' + body + \
@@ -70,14 +87,15 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
     os.makedirs(CACHE, exist_ok=True)
     so = os.path.join(CACHE, "%s_%s.so" % (name, h))
     if not os.path.exists(so):
+        rt = _runtime_object()
         # per-process file names: parallel test workers may build the same
-        # kernel at once
+        # kernel at once.  -O0: the generated kernels are long and run on
+        # small images here, so optimising them costs more than it saves.
         src = os.path.join(CACHE, "%s_%s.%d.cpp" % (name, h, os.getpid()))
         with open(src, "w") as f:
             f.write(text)
         tmp = so + ".%d.tmp" % os.getpid()
-        r = subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-w", "-I", HERE,
-                            src, os.path.join(HERE, "emu_rt.cpp"), "-o", tmp],
+        r = subprocess.run(["g++", "-O0", "-std=c++17", "-fPIC", "-shared", "-w", "-I", HERE, src, rt, "-o", tmp],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("emulator compile failed:\n" + r.stderr[-5000:])
