@@ -188,6 +188,15 @@ typedef struct {
  * this flag a persistent grid (the resident capacity) pulls tiles from a
  * device queue instead (the batched kernels always do).                  */
 #define WT_FLAG_TILE_QUEUE 128
+/* Set on any group of a schedule, a run issues all its launches in plan
+ * order on the caller's stream.  Without it, launches that read nothing an
+ * earlier launch of the run writes (another pyramid's down-sampling, an
+ * independent stage) run concurrently on up to three side streams of the
+ * pipeline, forked from the caller's stream at the run's first launch and
+ * joined back into it after the last, so the run still begins and ends in
+ * the caller's stream order (and a CUDA graph captured from that stream
+ * holds the launches as parallel branches).                               */
+#define WT_FLAG_ONE_STREAM 256
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */

@@ -72,6 +72,14 @@ wt_status wt_debug_layout(wt_pipeline *p, int32_t launch_index, const wt_image *
                           int32_t n_inputs, const wt_image *outputs, int32_t n_outputs,
                           int32_t *out, int32_t cap, int32_t *n_out);
 
+/* Stream lanes of the run plan for these images (the concurrent launches
+ * of WT_FLAG_ONE_STREAM's description): out = [launches, lanes, then per
+ * launch: its lane, the count and indices of the earlier launches on other
+ * lanes it waits for, the count and indices of the stages it computes].
+ * *n_out gets the full length; at most cap values are written.             */
+wt_status wt_debug_lanes(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                         int32_t n_outputs, int32_t *out, int32_t cap, int32_t *n_out);
+
 /* Halo/window analysis of schedule group `group` (Sec. 4 overlap, Sec. 5
  * parallelogram skew): out = [fusable, halo_l, halo_r, halo_t, halo_b,
  * unroll, n_nodes, then per node: id, src_chan, is_source, is_liveout, top,

@@ -101,7 +101,8 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.chunk_rows = q.chunk_rows ? q.chunk_rows : 8;
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
         if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB | WT_FLAG_SMEM16 |
-                        WT_FLAG_ZSTREAM | WT_FLAG_TEST_STALL | WT_FLAG_TILE_QUEUE))
+                        WT_FLAG_ZSTREAM | WT_FLAG_TEST_STALL | WT_FLAG_TILE_QUEUE |
+                        WT_FLAG_ONE_STREAM))
           fail(WT_EINVAL, "unknown flags");
         r.tile_o = q.tile_o;
         r.zstream = (q.flags & WT_FLAG_ZSTREAM) ? 1 : 0;
@@ -112,6 +113,7 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.tile_split = (q.flags & WT_FLAG_NO_TILE_SPLIT) ? 0 : 1;
         r.test_stall = (q.flags & WT_FLAG_TEST_STALL) ? 1 : 0;
         r.tile_queue = (q.flags & WT_FLAG_TILE_QUEUE) ? 1 : 0;
+        r.one_stream = (q.flags & WT_FLAG_ONE_STREAM) ? 1 : 0;
       }
   } else {
     s.n_groups = n;
@@ -206,7 +208,8 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
         params[g].flags = (r.pairs ? 0 : WT_FLAG_NO_PAIRS) | (r.tile_split ? 0 : WT_FLAG_NO_TILE_SPLIT) |
                           (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0) |
                           (r.smem16 ? WT_FLAG_SMEM16 : 0) | (r.zstream ? WT_FLAG_ZSTREAM : 0) |
-                          (r.test_stall ? WT_FLAG_TEST_STALL : 0) | (r.tile_queue ? WT_FLAG_TILE_QUEUE : 0);
+                          (r.test_stall ? WT_FLAG_TEST_STALL : 0) | (r.tile_queue ? WT_FLAG_TILE_QUEUE : 0) |
+                          (r.one_stream ? WT_FLAG_ONE_STREAM : 0);
         params[g].tile_o = r.tile_o;
       }
   });
@@ -732,6 +735,26 @@ wt_status wt_debug_layout(wt_pipeline *p, int32_t launch_index, const wt_image *
       v.push_back(F.bufb[s]);
       v.push_back(F.boxw[s]);
       v.push_back(F.esz[s]);
+    }
+    if (n_out) *n_out = (int32_t)v.size();
+    if (out)
+      for (int i = 0; i < (int)v.size() && i < cap; i++) out[i] = v[i];
+  });
+}
+
+wt_status wt_debug_lanes(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                         int32_t n_outputs, int32_t *out, int32_t cap, int32_t *n_out) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    std::lock_guard<std::mutex> lk(p->mu);
+    wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
+    std::vector<int32_t> v = {(int32_t)plan.launches.size(), plan.n_lanes};
+    for (const wt::Launch &L : plan.launches) {
+      v.push_back(L.lane);
+      v.push_back((int32_t)L.waits.size());
+      v.insert(v.end(), L.waits.begin(), L.waits.end());
+      v.push_back((int32_t)L.stages.size());
+      v.insert(v.end(), L.stages.begin(), L.stages.end());
     }
     if (n_out) *n_out = (int32_t)v.size();
     if (out)

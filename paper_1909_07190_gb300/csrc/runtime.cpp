@@ -441,7 +441,64 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     }
     L.kname = kernel_name(p, key, L.fused, L.fused && L.geom.n_gather > 0);
   }
+  if (!batched) assign_lanes(plan);
   return plan;
+}
+
+void assign_lanes(RunPlan &plan) {
+  const int n = (int)plan.launches.size();
+  bool one = false;
+  for (const Launch &L : plan.launches) one = one || L.params.one_stream != 0;
+  plan.n_lanes = 1;
+  for (Launch &L : plan.launches) {
+    L.lane = 0;
+    L.waits.clear();
+    L.record = false;
+  }
+  if (one || n < 2) return;
+  std::vector<int> tail;  // last launch of each lane
+  std::vector<std::vector<int>> vc(n);
+  for (int j = 0; j < n; j++) {
+    Launch &Lj = plan.launches[j];
+    std::vector<int> deps;  // earlier launches writing a stage this one reads
+    for (int i = 0; i < j; i++) {
+      const std::vector<int> &w = plan.launches[i].dst;
+      for (int s : Lj.src)
+        if (s >= 0 && std::find(w.begin(), w.end(), s) != w.end()) {
+          deps.push_back(i);
+          break;
+        }
+    }
+    int lane = -1;
+    for (int k = (int)deps.size() - 1; k >= 0 && lane < 0; k--)
+      if (tail[plan.launches[deps[k]].lane] == deps[k]) lane = plan.launches[deps[k]].lane;
+    if (lane < 0 && (int)tail.size() < kMaxLanes) {
+      lane = (int)tail.size();
+      tail.push_back(-1);
+    }
+    if (lane < 0) {
+      lane = 0;
+      for (int l = 1; l < (int)tail.size(); l++)
+        if (tail[l] < tail[lane]) lane = l;
+    }
+    Lj.lane = lane;
+    // vector clock: per lane, the latest launch known complete when this
+    // one starts (its lane's previous launch and what that waited for);
+    // a dependency already covered needs no wait
+    vc[j] = tail[lane] >= 0 ? vc[tail[lane]] : std::vector<int>(kMaxLanes, -1);
+    for (int k = (int)deps.size() - 1; k >= 0; k--) {
+      const int d = deps[k], l = plan.launches[d].lane;
+      if (vc[j][l] >= d) continue;
+      Lj.waits.push_back(d);
+      plan.launches[d].record = true;
+      for (int m = 0; m < kMaxLanes; m++) vc[j][m] = std::max(vc[j][m], vc[d][m]);
+    }
+    vc[j][lane] = j;
+    tail[lane] = j;
+  }
+  plan.n_lanes = (int)tail.size();
+  // side lanes end with an event the caller's stream joins
+  for (int l = 1; l < plan.n_lanes; l++) plan.launches[tail[l]].record = true;
 }
 
 std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bool gather) {
@@ -676,6 +733,10 @@ Workspace::~Workspace() {
   for (cudaStream_t s : band_stream)
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : band_events) cudaEventDestroy(e);
+  for (cudaStream_t s : lane_stream)
+    if (s) cudaStreamDestroy(s);
+  if (fork_event) cudaEventDestroy(fork_event);
+  for (cudaEvent_t e : launch_events) cudaEventDestroy(e);
 }
 
 Workspace &workspace(Pipeline &p, int64_t bytes) {
@@ -782,22 +843,86 @@ KernelArgs launch_args(Pipeline &p, const RunPlan &plan, Launch &L, Kernel &k, c
   return a;
 }
 
+// Streams and events of a run on `n_lanes` lanes with `n` launches; false
+// if they cannot be made now (the caller's stream is being captured: the
+// run then goes on one stream).
+static bool lanes_ready(Workspace &w, cudaStream_t user, int n_lanes, int n) {
+  bool have = w.fork_event != nullptr && (int)w.launch_events.size() >= n;
+  for (int l = 1; l < n_lanes; l++) have = have && w.lane_stream[l - 1] != nullptr;
+  if (have) return true;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  check_rt(cudaStreamIsCapturing(user, &cs), "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) return false;
+  for (int l = 1; l < n_lanes; l++)
+    if (!w.lane_stream[l - 1])
+      check_rt(cudaStreamCreateWithFlags(&w.lane_stream[l - 1], cudaStreamNonBlocking), "cudaStreamCreate");
+  if (!w.fork_event) check_rt(cudaEventCreateWithFlags(&w.fork_event, cudaEventDisableTiming), "cudaEventCreate");
+  while ((int)w.launch_events.size() < n) {
+    cudaEvent_t e;
+    check_rt(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    w.launch_events.push_back(e);
+  }
+  return true;
+}
+
+// Issues a run's launches on their lanes: lane 0 is the caller's stream,
+// lanes 1.. the workspace's side streams, which wait for the fork event
+// (everything the caller queued before the run) before their first launch;
+// each launch first waits for the events of its dependencies on other
+// lanes; the caller's stream finally waits for every side lane's last
+// launch.  launch_on(i, stream) issues launch i.
+template <class F>
+static void issue_lanes(Workspace &w, cudaStream_t user, int n_lanes, const std::vector<int> &lane,
+                        const std::vector<std::vector<int>> &waits, const std::vector<char> &record, F &&launch_on) {
+  const int n = (int)lane.size();
+  if (n_lanes <= 1 || !lanes_ready(w, user, n_lanes, n)) {
+    for (int i = 0; i < n; i++) launch_on(i, user);
+    return;
+  }
+  check_rt(cudaEventRecord(w.fork_event, user), "cudaEventRecord");
+  bool forked[kMaxLanes] = {};
+  int last[kMaxLanes];
+  for (int l = 0; l < kMaxLanes; l++) last[l] = -1;
+  for (int i = 0; i < n; i++) {
+    const int l = lane[i];
+    cudaStream_t s = l == 0 ? user : w.lane_stream[l - 1];
+    if (l != 0 && !forked[l]) {
+      check_rt(cudaStreamWaitEvent(s, w.fork_event, 0), "cudaStreamWaitEvent");
+      forked[l] = true;
+    }
+    for (int d : waits[i]) check_rt(cudaStreamWaitEvent(s, w.launch_events[d], 0), "cudaStreamWaitEvent");
+    launch_on(i, s);
+    if (record[i]) check_rt(cudaEventRecord(w.launch_events[i], s), "cudaEventRecord");
+    last[l] = i;
+  }
+  for (int l = 1; l < n_lanes; l++)
+    if (last[l] >= 0) check_rt(cudaStreamWaitEvent(user, w.launch_events[last[l]], 0), "cudaStreamWaitEvent");
+}
+
 void run_plan(Pipeline &p, RunPlan &plan, cudaStream_t stream, const std::string *key) {
   Workspace &w = workspace(p, plan.ws_bytes);
   int dev = w.device;
   CachedRun c;
   if ((int)plan.launches.size() > kMaxLaunches) fail(WT_EUNSUPPORTED, "more than 500 launches per run");
+  // load every kernel and set up every launch before issuing any
+  std::vector<Kernel *> ks;
   int li = 0;
   for (Launch &L : plan.launches) {
     Kernel &k = get_kernel(p, L, dev);
     KernelArgs a = launch_args(p, plan, L, k, w.base, w.err, li++, dev);
-    launch(L, k, a, stream);
+    ks.push_back(&k);
     c.functions.push_back(k.function);
     c.args.push_back(a);
     c.grid.insert(c.grid.end(), {L.grid[0], L.grid[1], L.grid[2]});
     c.block.push_back(L.block);
     c.smem.push_back(L.smem);
+    c.lane.push_back(L.lane);
+    c.waits.push_back(L.waits);
+    c.record.push_back(L.record ? 1 : 0);
   }
+  c.n_lanes = plan.n_lanes;
+  issue_lanes(w, stream, c.n_lanes, c.lane, c.waits, c.record,
+              [&](int i, cudaStream_t s) { launch(plan.launches[i], *ks[i], c.args[i], s); });
   if (!key) return;
   RunCache &rc = p.cache;
   if (rc.device != dev || rc.sched_version != p.sched_version || rc.ws_generation != w.generation) {
@@ -835,13 +960,13 @@ void run(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, int n_o
       if (it != rc.runs.end()) {
         const Driver &drv = driver();
         CachedRun &c = it->second;
-        for (size_t i = 0; i < c.functions.size(); i++) {
+        issue_lanes(*p.ws, stream, c.n_lanes, c.lane, c.waits, c.record, [&](int i, cudaStream_t s) {
           void *params[] = {&c.args[i]};
           check_cu(drv.launchKernel((CUfunction)c.functions[i], c.grid[3 * i], c.grid[3 * i + 1],
                                     c.grid[3 * i + 2], (unsigned)c.block[i], 1, 1, (unsigned)c.smem[i],
-                                    (CUstream)stream, params, nullptr),
+                                    (CUstream)s, params, nullptr),
                    "cuLaunchKernel");
-        }
+        });
         return;
       }
     }

@@ -102,6 +102,7 @@ struct GroupParams {
   int zstream = 0;     // 3-D groups: stream along planes instead of rows
   int test_stall = 0;  // test only: every tile's first staging wait gives up
   int tile_queue = 0;  // persistent warps pull tiles from a device queue
+  int one_stream = 0;  // the run's launches in plan order on the caller's stream
 };
 
 struct Schedule {
@@ -240,6 +241,11 @@ struct CachedRun {
   std::vector<KernelArgs> args;
   std::vector<unsigned> grid;      // 3 per launch
   std::vector<int> block, smem;
+  // stream lanes of the launches (empty: one lane, the caller's stream)
+  std::vector<int> lane;
+  std::vector<std::vector<int>> waits;
+  std::vector<char> record;
+  int n_lanes = 1;
 };
 struct RunCache {
   int device = -1;

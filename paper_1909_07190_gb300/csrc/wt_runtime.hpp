@@ -35,7 +35,16 @@ struct Launch {
   int smem = 0;
   int resident_blocks_per_sm = 0;
   int resident_warps = 0;  // fused launches: resident warps on the device
+  // Stream lane (0: the caller's stream), the earlier launches on other
+  // lanes it waits for, and whether an event is recorded after it (another
+  // lane waits for it, or it ends a side lane).
+  int lane = 0;
+  std::vector<int> waits;
+  bool record = false;
 };
+
+// Most stream lanes a run uses: the caller's stream and three side streams.
+constexpr int kMaxLanes = 4;
 
 struct RunPlan {
   int W = 0, H = 0;
@@ -44,7 +53,16 @@ struct RunPlan {
   std::vector<Loc> in_loc;  // per pipeline input
   std::vector<Launch> launches;
   int64_t ws_bytes = 0;
+  int n_lanes = 1;
 };
+
+// Lanes of a plan's launches: a launch that reads no stage an earlier launch
+// writes may run beside it.  Greedy in plan order: a launch continues the
+// lane whose last launch it depends on, else opens a new lane (at most
+// kMaxLanes), else joins the lane idle longest; it waits by event for its
+// dependencies on other lanes.  Stages never share workspace memory, so
+// reads after writes are the only hazards within a run.
+void assign_lanes(RunPlan &plan);
 
 // Device control block of a workspace: the error word at byte 0 and, from
 // kCtrlQueueOffset, two tile-queue counters per launch (next tile, warps
@@ -71,6 +89,11 @@ struct Workspace {
   // events (created on first use)
   cudaStream_t band_stream[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> band_events;
+  // side streams of concurrent launch lanes (lanes 1..), the fork event and
+  // one event per launch of a run (created by the first run that needs them)
+  cudaStream_t lane_stream[kMaxLanes - 1] = {};
+  cudaEvent_t fork_event = nullptr;
+  std::vector<cudaEvent_t> launch_events;
   // banded host runs captured as CUDA graphs, by image descriptors (null:
   // seen once, captured at the next call)
   std::map<std::string, cudaGraphExec_t> host_graphs;

@@ -23,6 +23,7 @@ WT_FLAG_NO_PAIRS, WT_FLAG_NO_TILE_SPLIT, WT_FLAG_PLAIN, WT_FLAG_OTPTB, WT_FLAG_S
 WT_FLAG_ZSTREAM = 32
 WT_FLAG_TEST_STALL = 64
 WT_FLAG_TILE_QUEUE = 128
+WT_FLAG_ONE_STREAM = 256
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
            "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14,
            "tapz": 15}
@@ -135,6 +136,7 @@ SIGNATURES = [
                                   _i64, _P(_i64), _vp, _i64, _P(_i32), ctypes.c_char_p, _i64, _P(_i64)]),
     ("wt_debug_compile", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i64)]),
     ("wt_debug_layout", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
+    ("wt_debug_lanes", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_inject_alloc_failure", _i32, [_i32, _i32]),
     ("wt_debug_live_objects", _i32, [_P(_i64), _P(_i64)]),
@@ -455,6 +457,26 @@ class Pipeline:
         n = _i64()
         check(load().wt_debug_compile(self.h, index, ia, len(inputs), oa, len(outputs), ctypes.byref(n)))
         return n.value
+
+    def debug_lanes(self, inputs, outputs):
+        """Stream lanes of the run plan: (number of lanes, per launch a dict
+        with its lane, the launches it waits for and its stages)."""
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        n = _i32()
+        check(load().wt_debug_lanes(self.h, ia, len(inputs), oa, len(outputs), None, 0, ctypes.byref(n)))
+        out = (_i32 * n.value)()
+        check(load().wt_debug_lanes(self.h, ia, len(inputs), oa, len(outputs), out, n.value, ctypes.byref(n)))
+        v = list(out)
+        launches, k = [], 2
+        for _ in range(v[0]):
+            lane, nw = v[k], v[k + 1]
+            waits = v[k + 2:k + 2 + nw]
+            k += 2 + nw
+            ns = v[k]
+            launches.append({"lane": lane, "waits": waits, "stages": v[k + 1:k + 1 + ns]})
+            k += 1 + ns
+        return v[1], launches
 
     def debug_layout(self, index, inputs, outputs):
         ia = (wt_image * len(inputs))(*inputs)
