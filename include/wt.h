@@ -197,6 +197,15 @@ typedef struct {
  * the caller's stream order (and a CUDA graph captured from that stream
  * holds the launches as parallel branches).                               */
 #define WT_FLAG_ONE_STREAM 256
+/* Warp-tile group kernels normally defer the constant factors of stage
+ * programs (a filter's normalisation, a weight) to the stages that read
+ * them: a value in registers may hold the stage's value divided by a
+ * compile-time constant, the factor is merged into the next constant or
+ * product and applied once where a value leaves the kernel (HBM stores,
+ * 16-bit shared-memory windows).  Results differ from the undeferred
+ * evaluation by rounding only.  This flag evaluates every stage as
+ * written.                                                                 */
+#define WT_FLAG_NO_FOLD 512
 
 typedef enum {
   WT_EXEC_FUSED = 0, /* warp-tiled group kernels (OTPW + hybrid tiling)     */

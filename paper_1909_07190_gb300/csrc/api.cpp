@@ -102,7 +102,7 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.n_buffers = q.n_buffers ? q.n_buffers : 2;
         if (q.flags & ~(WT_FLAG_NO_PAIRS | WT_FLAG_NO_TILE_SPLIT | WT_FLAG_PLAIN | WT_FLAG_OTPTB | WT_FLAG_SMEM16 |
                         WT_FLAG_ZSTREAM | WT_FLAG_TEST_STALL | WT_FLAG_TILE_QUEUE |
-                        WT_FLAG_ONE_STREAM))
+                        WT_FLAG_ONE_STREAM | WT_FLAG_NO_FOLD))
           fail(WT_EINVAL, "unknown flags");
         r.tile_o = q.tile_o;
         r.zstream = (q.flags & WT_FLAG_ZSTREAM) ? 1 : 0;
@@ -114,6 +114,7 @@ wt::Schedule to_schedule(const wt::Pipeline &p, const wt_schedule_desc *d) {
         r.test_stall = (q.flags & WT_FLAG_TEST_STALL) ? 1 : 0;
         r.tile_queue = (q.flags & WT_FLAG_TILE_QUEUE) ? 1 : 0;
         r.one_stream = (q.flags & WT_FLAG_ONE_STREAM) ? 1 : 0;
+        r.fold = (q.flags & WT_FLAG_NO_FOLD) ? 0 : 1;
       }
   } else {
     s.n_groups = n;
@@ -209,7 +210,7 @@ wt_status wt_schedule_get(const wt_pipeline *p, int32_t *exec, int32_t *n_groups
                           (r.plain ? WT_FLAG_PLAIN : 0) | (r.otptb ? WT_FLAG_OTPTB : 0) |
                           (r.smem16 ? WT_FLAG_SMEM16 : 0) | (r.zstream ? WT_FLAG_ZSTREAM : 0) |
                           (r.test_stall ? WT_FLAG_TEST_STALL : 0) | (r.tile_queue ? WT_FLAG_TILE_QUEUE : 0) |
-                          (r.one_stream ? WT_FLAG_ONE_STREAM : 0);
+                          (r.one_stream ? WT_FLAG_ONE_STREAM : 0) | (r.fold ? 0 : WT_FLAG_NO_FOLD);
         params[g].tile_o = r.tile_o;
       }
   });

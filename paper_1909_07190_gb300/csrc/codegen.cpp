@@ -64,6 +64,7 @@ std::string CodegenKey::str() const {
   if (cascade) s << "|K" << tby;
   if (vol) s << "|Z" << vol_split << "x" << vol_to << "x" << tby;
   if (test_stall) s << "|STALL";
+  if (fold) s << "|S";
   return s.str();
 }
 
@@ -1095,11 +1096,201 @@ void emit_step(Ctx &c, int mode, int u) {
   o << "}\n";
 }
 
+// ------------------------------------------- deferred constant scales
+// A node's registers may hold its value divided by a compile-time constant,
+// the node's scale: a stage that multiplies by constants (a normalised
+// filter, a weight) leaves the factor to its consumers, which merge it into
+// their own constants or products.  A normalised 3-tap column pass then
+// costs two additions instead of a multiply and two fused multiply-adds,
+// and a box mean feeding a product costs no multiply at all.  Every
+// program is rewritten, in evaluation order, into one computing the raw
+// value from its producers' raw values; values leaving the kernel (HBM
+// stores, 16-bit shared-memory windows) are brought back to scale 1.  The
+// results differ from the program as written by rounding only.
+struct SV {
+  std::vector<KOp> ops;  // postfix program of the raw value
+  double s = 1.0;        // value = s * raw
+  bool k = false;        // a constant (one CONST op, s = 1)
+  float v = 0.f;
+};
+
+SV sv_const(float v) {
+  SV x;
+  x.k = true;
+  x.v = v;
+  KOp o;
+  o.op = WT_OP_CONST;
+  o.value = v;
+  x.ops = {o};
+  return x;
+}
+
+SV sv_op(SV a, const SV *b, int op, double s) {
+  if (b) a.ops.insert(a.ops.end(), b->ops.begin(), b->ops.end());
+  KOp o;
+  o.op = op;
+  a.ops.push_back(o);
+  a.s = s;
+  a.k = false;
+  return a;
+}
+
+// raw * m, the scale unchanged (m applied to the raw program)
+SV sv_mul_const(const SV &a, double m) {
+  if (m == 1.0) return a;
+  if (m == -1.0) return sv_op(a, nullptr, WT_OP_NEG, a.s);
+  SV c = sv_const((float)m);
+  return sv_op(a, &c, WT_OP_MUL, a.s);
+}
+
+// the value itself (scale 1)
+SV sv_mat(const SV &a) {
+  if (a.k || a.s == 1.0) return a;
+  SV r = sv_mul_const(a, a.s);
+  r.s = 1.0;
+  return r;
+}
+
+bool sv_scale_ok(double s) {
+  const double m = std::fabs(s);
+  return std::isfinite(s) && m >= std::ldexp(1.0, -40) && m <= std::ldexp(1.0, 40);
+}
+
+float fold_const(int op, float a, float b) {
+  switch (op) {
+    case WT_OP_ADD: return a + b;
+    case WT_OP_SUB: return a - b;
+    case WT_OP_MUL: return a * b;
+    case WT_OP_DIV: return a / b;
+    case WT_OP_MIN: return std::fmin(a, b);
+    case WT_OP_MAX: return std::fmax(a, b);
+  }
+  fail(WT_EINVAL, "internal: opcode");
+}
+
+SV sv_binary(int op, SV a, SV b) {
+  if (a.k && b.k) return sv_const(fold_const(op, a.v, b.v));
+  switch (op) {
+    case WT_OP_MUL:
+      if (a.k && std::isfinite(a.v) && a.v != 0.f) { b.s *= a.v; return b; }
+      if (b.k && std::isfinite(b.v) && b.v != 0.f) { a.s *= b.v; return a; }
+      if (a.k || b.k) break;
+      return sv_op(a, &b, WT_OP_MUL, a.s * b.s);
+    case WT_OP_DIV:
+      if (b.k && std::isfinite(b.v) && b.v != 0.f) { a.s /= b.v; return a; }
+      if (b.k) break;
+      return sv_op(a, &b, WT_OP_DIV, a.s / b.s);
+    case WT_OP_ADD: case WT_OP_SUB: {
+      const int flip = op == WT_OP_ADD ? WT_OP_SUB : WT_OP_ADD;
+      if (a.k) return sv_op(sv_const((float)(a.v / b.s)), &b, op, b.s);
+      if (b.k) {
+        SV c = sv_const((float)(b.v / a.s));
+        return sv_op(a, &c, op, a.s);
+      }
+      if (a.s == b.s) return sv_op(a, &b, op, a.s);
+      // a difference keeps a's scale (a - m b' is one fused multiply-add,
+      // packed too; m a' - b' is not); a sum the smaller one (m >= 1)
+      if (op == WT_OP_SUB || std::fabs(a.s) <= std::fabs(b.s)) {
+        // a's scale: value = s_a (a' +- (s_b / s_a) b')
+        const double m = b.s / a.s;
+        if (m == -1.0) return sv_op(a, &b, flip, a.s);
+        SV mb = sv_mul_const(b, m);
+        return sv_op(a, &mb, op, a.s);
+      }
+      // b's scale: value = s_b ((s_a / s_b) a' +- b')
+      const double m = a.s / b.s;
+      if (m == -1.0) {
+        // -b' +- b'' : b' - a' for ADD, -(a' + b') for SUB
+        if (op == WT_OP_ADD) return sv_op(b, &a, WT_OP_SUB, b.s);
+        return sv_op(a, &b, WT_OP_ADD, -b.s);
+      }
+      SV ma = sv_mul_const(a, m);
+      return sv_op(ma, &b, op, b.s);
+    }
+    case WT_OP_MIN: case WT_OP_MAX: {
+      const int other = op == WT_OP_MIN ? WT_OP_MAX : WT_OP_MIN;
+      if (a.k || b.k) {
+        SV &x = a.k ? b : a;
+        const float kv = a.k ? a.v : b.v;
+        SV c = sv_const((float)(kv / x.s));
+        return sv_op(x, &c, x.s > 0 ? op : other, x.s);
+      }
+      if (a.s == b.s) return sv_op(a, &b, a.s > 0 ? op : other, a.s);
+      break;
+    }
+  }
+  // no scale passes through: both operands at scale 1
+  SV ma = sv_mat(a), mb = sv_mat(b);
+  return sv_op(ma, &mb, op, 1.0);
+}
+
+SV sv_unary(int op, SV a) {
+  if (a.k) {
+    switch (op) {
+      case WT_OP_NEG: return sv_const(-a.v);
+      case WT_OP_ABS: return sv_const(std::fabs(a.v));
+      case WT_OP_SQRT: return sv_const(std::sqrt(a.v));
+    }
+  }
+  switch (op) {
+    case WT_OP_NEG: a.s = -a.s; return a;
+    case WT_OP_ABS: return sv_op(a, nullptr, WT_OP_ABS, std::fabs(a.s));
+    case WT_OP_SQRT:
+      if (a.s > 0) return sv_op(a, nullptr, WT_OP_SQRT, std::sqrt(a.s));
+      return sv_op(sv_mat(a), nullptr, WT_OP_SQRT, 1.0);
+  }
+  fail(WT_EINVAL, "internal: opcode");
+}
+
+// Rewrites the programs of g's computed nodes (evaluation order) so that
+// each computes its raw value; a node whose value is stored keeps scale 1.
+void fold_scales(GroupGeom &g, const CodegenKey &key) {
+  std::vector<double> scale(g.nodes.size(), 1.0);
+  for (int ni : g.order) {
+    Node &n = g.nodes[ni];
+    if (n.is_source || n.gather_mode) continue;
+    std::vector<SV> st;
+    for (const KOp &op : n.prog) {
+      switch (op.op) {
+        case WT_OP_CONST: st.push_back(sv_const(op.value)); break;
+        case WT_OP_TAP: {
+          SV x;
+          x.ops = {op};
+          x.s = scale[op.node];
+          st.push_back(x);
+        } break;
+        case WT_OP_XPAR: case WT_OP_YPAR: case WT_OP_CHAN: {
+          SV x;
+          x.ops = {op};
+          st.push_back(x);
+        } break;
+        case WT_OP_NEG: case WT_OP_ABS: case WT_OP_SQRT:
+          st.back() = sv_unary(op.op, st.back());
+          break;
+        default: {
+          SV b = st.back();
+          st.pop_back();
+          SV a = st.back();
+          st.pop_back();
+          st.push_back(sv_binary(op.op, a, b));
+        }
+      }
+      if (!sv_scale_ok(st.back().s)) st.back() = sv_mat(st.back());
+    }
+    SV r = st.back();
+    const bool keep = n.is_liveout || (n.in_smem && key.win_dtype != WT_F32);
+    if (keep || r.k) r = sv_mat(r);
+    n.prog = r.ops;
+    scale[ni] = r.s;
+  }
+}
+
 }  // namespace
 
 std::string emit_fused(const Pipeline &p, const GroupGeom &g0, const CodegenKey &key,
                        const std::string &kname) {
   GroupGeom g = g0;
+  if (key.fold) fold_scales(g, key);
   FusedLayout L = fused_layout(g, key);
   Ctx c(p, g, key, L);
   c.V = key.vec;

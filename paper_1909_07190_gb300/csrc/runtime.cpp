@@ -246,6 +246,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     key.chunk = L.params.chunk_rows > 0 ? L.params.chunk_rows : 8;
     key.nbuf = L.params.n_buffers > 0 ? L.params.n_buffers : 2;
     key.pairs = L.params.pairs != 0;
+    key.fold = L.fused && !L.params.otptb && L.params.fold != 0;
     key.test_stall = L.params.test_stall != 0;
     key.even_rows = L.fused && L.geom.uses_ypar && L.params.tile_h % 2 == 0;
     L.src.clear();

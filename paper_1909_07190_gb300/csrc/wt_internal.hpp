@@ -102,6 +102,7 @@ struct GroupParams {
   int zstream = 0;     // 3-D groups: stream along planes instead of rows
   int test_stall = 0;  // test only: every tile's first staging wait gives up
   int tile_queue = 0;  // persistent warps pull tiles from a device queue
+  int fold = 1;        // deferred constant scales in warp-tile groups
   int one_stream = 0;  // the run's launches in plan order on the caller's stream
 };
 
@@ -302,6 +303,9 @@ struct CodegenKey {
   bool plain = false;
   bool persistent = false;
   bool pairs = true;  // packed f32x2 arithmetic
+  // warp-tile groups: constant factors of stage programs deferred to the
+  // consumers (register values hold the value over a compile-time scale)
+  bool fold = false;
   // test only (WT_FLAG_TEST_STALL): the first chunk of every tile is armed
   // for bytes no copy delivers, and waits give up after a few polls
   bool test_stall = false;

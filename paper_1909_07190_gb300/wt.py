@@ -24,6 +24,7 @@ WT_FLAG_ZSTREAM = 32
 WT_FLAG_TEST_STALL = 64
 WT_FLAG_TILE_QUEUE = 128
 WT_FLAG_ONE_STREAM = 256
+WT_FLAG_NO_FOLD = 512
 OPCODES = {"const": 1, "tap": 2, "add": 3, "sub": 4, "mul": 5, "div": 6, "min": 7, "max": 8,
            "neg": 9, "abs": 10, "sqrt": 11, "xpar": 12, "ypar": 13, "chan": 14,
            "tapz": 15}

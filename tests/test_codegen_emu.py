@@ -367,3 +367,43 @@ def test_cascade_blend_groups():
     p.schedule(groups=g, params=params)
     assert p.launches_per_run() == 3 + 3 + 6
     assert np.abs(got[0] - oracle_of(spec, [A, B, M])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("name,tol", [("harris", 1e-5), ("sharpen", 1e-5), ("harris_raw", 1e-5)])
+def test_deferred_scales(name, tol):
+    """Constant factors deferred to the consumers (the default) and every
+    stage evaluated as written (WT_FLAG_NO_FOLD) both match the oracle; the
+    deferred kernel's step has fewer packed operations (the normalised
+    column passes and box means keep no multiply)."""
+    spec = P.by_name(name)
+    img = rnd(77, 150, 70)
+    ref = oracle_of(spec, [img])[0]
+    if name == "harris_raw":
+        tol = 1e-5 * float(np.abs(ref).max())
+    srcs = {}
+    for flags in (0, wt.WT_FLAG_NO_FOLD):
+        got, d = run_emulated(spec, [img], params=[dict(tile_h=16, flags=flags)])
+        assert np.abs(got[0] - ref).max() <= tol
+        srcs[flags] = d["source"]
+    # packed arithmetic of the steady-state step
+    ops = {}
+    for f, s in srcs.items():
+        step = s[s.index("step phase 0 (steady)"):s.index("step phase 1 (steady)")]
+        ops[f] = sum(step.count("wt_%s2(" % o) for o in ("add", "sub", "mul", "fma"))
+    if name == "harris_raw":
+        assert ops[0] <= ops[wt.WT_FLAG_NO_FOLD]  # no normalisation to defer
+    else:
+        assert ops[0] < ops[wt.WT_FLAG_NO_FOLD]
+
+
+def test_deferred_scales_blend_level():
+    """A blend level's group (up-sampled gathers, per-level blend,
+    reconstruction) with its stored value brought back to scale 1."""
+    spec = P.blend(levels=2, channels=1)
+    a, b, m = rnd(5, 67, 45), rnd(6, 67, 45), rnd(7, 67, 45)
+    ref = oracle_of(spec, [a, b, m])[0]
+    groups, params = P.blend_schedule(levels=2)
+    for flags in (0, wt.WT_FLAG_NO_FOLD):
+        prm = [dict(q, flags=q.get("flags", 0) | flags) for q in params]
+        got, _ = run_emulated(spec, [a, b, m], groups=groups, params=prm)
+        assert np.abs(got[0] - ref).max() <= 1e-5
