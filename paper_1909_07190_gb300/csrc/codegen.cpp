@@ -65,6 +65,7 @@ std::string CodegenKey::str() const {
   if (vol) s << "|Z" << vol_split << "x" << vol_to << "x" << tby;
   if (test_stall) s << "|STALL";
   if (fold) s << "|S";
+  if (soft_cap) s << "|soft";
   return s.str();
 }
 

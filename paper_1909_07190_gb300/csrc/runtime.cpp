@@ -242,6 +242,10 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
     key.stages = L.stages;
     key.frac_reg = L.params.frac_reg;
     key.max_regs = L.params.max_regs;
+    if (L.fused && !L.params.otptb && key.max_regs == 0) {
+      key.max_regs = kSoftRegCap;
+      key.soft_cap = true;
+    }
     key.nw = std::max(1, std::min(16, L.params.warps_per_block));
     key.chunk = L.params.chunk_rows > 0 ? L.params.chunk_rows : 8;
     key.nbuf = L.params.n_buffers > 0 ? L.params.n_buffers : 2;
@@ -639,6 +643,25 @@ Kernel &get_kernel(const Pipeline &p, const Launch &L, int device) {
   check_cu(drv.moduleLoadData(&mod, cubin.data()), "cuModuleLoadData");
   CUfunction f;
   check_cu(drv.moduleGetFunction(&f, mod, L.kname.c_str()), "cuModuleGetFunction");
+  if (L.key.soft_cap) {
+    int local = 0;
+    drv.funcGetAttribute(&local, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, f);
+    if (local > 0) {
+      // spills under the library's soft register cap: the uncapped kernel
+      // serves this launch (kept under both names)
+      drv.moduleUnload(mod);
+      Launch U = L;
+      U.key.max_regs = 0;
+      U.key.soft_cap = false;
+      U.kname = kernel_name(p, U.key, true, U.geom.n_gather > 0);
+      Kernel k = get_kernel(p, U, device);
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      CacheEntry e;
+      e.k = k;
+      auto ins = g_cache.emplace(key, e);
+      return ins.first->second.k;
+    }
+  }
   CacheEntry e;
   e.k.module = mod;
   e.k.function = f;
