@@ -758,7 +758,9 @@ def measure(wt, torch, workload, args, dist, world, rank, local, steps, warmup, 
     if fp32:
         # the stage programs' FP32 operations per pixel against the FP32 lanes
         roof["alu"] = {"ops_per_px": opx, "achieved_tops": opx * value / 1e6 / world, "peak_tops": fp32 / 1e12,
-                       "frac": opx * value * 1e6 / world / fp32}
+                       "frac": opx * value * 1e6 / world / fp32,
+                       "note": "operations of the stage programs as written; the kernels execute fewer where "
+                               "constants fold (deferred scales, up-sampling phases), so this can exceed 1"}
     if rec and rec.get("warp_instructions_per_launch") and (clocks or {}).get("sm_mhz"):
         # issue roof: executed warp instructions over the SMs' issue slots
         # (4 schedulers, one instruction per cycle each) at the sampled clock

@@ -243,8 +243,8 @@ def blend_schedule(levels: int = 6) -> tuple:
       - the coarsest level with its blend, then one fused group per finer
         level: short warp tiles where the level is small; at level 1, 14
         rows, at level 0, 48 rows, both with 4-row staging chunks and at most
-        112 registers (20 warps per SM: the level-0 group is bound by memory
-        latency; taller level-0 tiles re-read fewer gather rows)."""
+        96 registers (80 used, 25 warps per SM: the level-0 group is bound by
+        memory latency; taller level-0 tiles re-read fewer gather rows)."""
     plain = 4  # WT_FLAG_PLAIN
     groups, params = [], []
     g = 0
@@ -268,7 +268,7 @@ def blend_schedule(levels: int = 6) -> tuple:
         if lv >= 2:
             params.append(dict(tile_h=8))
         else:
-            params.append(dict(tile_h=14 if lv == 1 else 48, chunk_rows=4, max_regs=112))
+            params.append(dict(tile_h=14 if lv == 1 else 48, chunk_rows=4, max_regs=96))
     return groups, params
 
 
