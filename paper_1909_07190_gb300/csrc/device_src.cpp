@@ -213,17 +213,23 @@ static __device__ __forceinline__ void wt_ld2_bf16(const void *p, float &a, floa
 static __device__ __forceinline__ void wt_st4_f32(void *p, float a, float b, float c, float d) {
   *(float4 *)p = make_float4(a, b, c, d);
 }
+// two values rounded (RNE) and packed in one conversion: lo in bits 0-15,
+// hi in bits 16-31 (the instruction puts its first source in the upper half)
+static __device__ __forceinline__ wt_u32 wt_f2h2(float lo, float hi) {
+  wt_u32 r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+static __device__ __forceinline__ wt_u32 wt_f2b2(float lo, float hi) {
+  wt_u32 r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 static __device__ __forceinline__ void wt_st4_f16(void *p, float a, float b, float c, float d) {
-  uint2 v;
-  v.x = (wt_u32)wt_f2h(a) | ((wt_u32)wt_f2h(b) << 16);
-  v.y = (wt_u32)wt_f2h(c) | ((wt_u32)wt_f2h(d) << 16);
-  *(uint2 *)p = v;
+  *(uint2 *)p = make_uint2(wt_f2h2(a, b), wt_f2h2(c, d));
 }
 static __device__ __forceinline__ void wt_st4_bf16(void *p, float a, float b, float c, float d) {
-  uint2 v;
-  v.x = (wt_u32)wt_f2b(a) | ((wt_u32)wt_f2b(b) << 16);
-  v.y = (wt_u32)wt_f2b(c) | ((wt_u32)wt_f2b(d) << 16);
-  *(uint2 *)p = v;
+  *(uint2 *)p = make_uint2(wt_f2b2(a, b), wt_f2b2(c, d));
 }
 // ------------------------------------------------------- scalar accesses
 static __device__ __forceinline__ float wt_ld1_f32(const void *p) { return __ldg((const float *)p); }

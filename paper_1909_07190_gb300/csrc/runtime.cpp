@@ -510,7 +510,7 @@ std::string kernel_name(const Pipeline &p, const CodegenKey &key, bool fused, bo
   char hx[24];
   // the generator's version is part of the name: a kernel whose code
   // changes gets a new name (profiles and caches never mix versions)
-  static const char kCodegenVersion[] = "wt-codegen-21";
+  static const char kCodegenVersion[] = "wt-codegen-22";
   static const char kPlainVersion[] = "wt-plain-2";  // the per-stage kernel's own changes
   static const char kBatchVersion[] = "wt-batch-15";  // the persistent variant's own changes
   const std::string ks = key.str();
