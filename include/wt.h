@@ -430,6 +430,24 @@ wt_status wt_costmodel_features(wt_pipeline *p, int32_t first_stage, int32_t n_s
                                 const wt_group_params *params, int32_t fused, int32_t width,
                                 int32_t height, int32_t dtype, float *features);
 
+/* Training data of the learned model from one run of the installed
+ * schedule on these images (single-image runs, Sec. 6's measured inputs of
+ * the cost function): every launch of the run is timed as by
+ * wt_schedule_time_launches (`reps` repetitions, 3 samples, the minimum of
+ * the means) and described by its features as by wt_costmodel_features
+ * (fused groups with their schedule parameters, per-stage kernels without).
+ * features[i * WT_COSTMODEL_FEATURES ...] and log_ms[i] (natural log of
+ * ms) for row i; stages[2i], stages[2i+1] (may be null) = the launch's
+ * first stage and stage count.  Launches of other kinds (reduction chains,
+ * down-sampling streams and cascades, 3-D groups, block tiles) have no
+ * features and are skipped.  *n_rows gets the row count; arrays of `cap`
+ * rows (null arrays with cap 0 size the call; WT_EINVAL if too small).
+ * Writes the outputs (the run executes).                                   */
+wt_status wt_costmodel_collect(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                               const wt_image *outputs, int32_t n_outputs, int32_t reps, void *stream,
+                               float *features, float *log_ms, int32_t *stages, int32_t cap,
+                               int32_t *n_rows);
+
 /* The MLP training kernel: `steps` Adam steps (beta 0.9/0.999, eps 1e-8,
  * t0 steps taken before) on the mean squared error over mini-batches
  * idx[steps][batch] of rows of x[n][18] with targets y[n], decoupled L2

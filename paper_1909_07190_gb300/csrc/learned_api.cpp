@@ -1,10 +1,13 @@
 // C ABI of the learned cost model and per-launch timing (include/wt.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "wt.h"
+#include "wt_jit.hpp"
 #include "wt_learned.hpp"
 #include "wt_mlp.hpp"
 #include "wt_runtime.hpp"
@@ -88,6 +91,53 @@ wt_status wt_costmodel_features(wt_pipeline *p, int32_t first_stage, int32_t n_s
     auto st = wt::stage_stats(*p, false);
     if (!wt::launch_features(*p, seg, q, fused != 0, width, height, dtype, cfg, st, features))
       wt::fail(WT_EUNSUPPORTED, "launch is infeasible (group does not fuse or does not fit)");
+  });
+}
+
+wt_status wt_costmodel_collect(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
+                               const wt_image *outputs, int32_t n_outputs, int32_t reps, void *stream,
+                               float *features, float *log_ms, int32_t *stages, int32_t cap, int32_t *n_rows) {
+  return guard([&] {
+    if (!p || !inputs || !outputs || reps < 1 || cap < 0) wt::fail(WT_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(p->mu);
+    auto t = wt::time_launches(*p, inputs, n_inputs, outputs, n_outputs, (cudaStream_t)stream, reps);
+    wt::RunPlan plan = wt::build_plan(*p, inputs, n_inputs, outputs, n_outputs);
+    if (plan.launches.size() != t.size()) wt::fail(WT_EUNSUPPORTED, "run plan changed");
+    const auto groups = wt::schedule_groups(*p);
+    int dev = 0;
+    wt::check_rt(cudaGetDevice(&dev), "cudaGetDevice");
+    const wt::GpuConfig cfg = wt::device_config(dev);
+    const auto st = wt::stage_stats(*p, false);
+    const int W = inputs[0].width, H = inputs[0].height, dtype = inputs[0].dtype;
+    int rows = 0;
+    for (size_t i = 0; i < t.size(); i++) {
+      const wt::Launch &L = plan.launches[i];
+      const bool warp_tile = L.fused && !L.key.otptb;
+      const bool per_stage = !L.fused && L.key.plain && !L.key.down && !L.key.cascade && !L.key.chain && !L.key.vol;
+      if (!warp_tile && !per_stage) continue;
+      std::vector<int> seg(L.stages.begin(), L.stages.end());
+      wt::GroupParams q;
+      if (warp_tile) {
+        // the schedule parameters of the group this launch runs
+        for (size_t gi = 0; gi < groups.size(); gi++)
+          if (!groups[gi].empty() && groups[gi][0] == seg[0]) q = wt::group_params(*p, (int)gi);
+        q.vec = L.key.vec;  // the pixels per lane the kernel was generated for
+      }
+      float f[WT_COSTMODEL_FEATURES];
+      if (!wt::launch_features(*p, seg, q, warp_tile, W, H, dtype, cfg, st, f)) continue;
+      if (rows < cap) {
+        if (features) std::memcpy(features + (size_t)rows * WT_COSTMODEL_FEATURES, f, sizeof f);
+        if (log_ms) log_ms[rows] = (float)std::log(std::max(t[i].ms, 1e-9));
+        if (stages) {
+          stages[2 * rows] = seg[0];
+          stages[2 * rows + 1] = (int32_t)seg.size();
+        }
+      } else if (features || log_ms || stages) {
+        wt::fail(WT_EINVAL, "arrays too small for the launches");
+      }
+      rows++;
+    }
+    if (n_rows) *n_rows = rows;
   });
 }
 

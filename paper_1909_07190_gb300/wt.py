@@ -111,6 +111,8 @@ SIGNATURES = [
                                          _P(ctypes.c_double), _P(_i32), _i32, _P(_i32)]),
     ("wt_costmodel_features", _i32, [_vp, _i32, _i32, _P(wt_group_params), _i32, _i32, _i32, _i32,
                                      _P(ctypes.c_float)]),
+    ("wt_costmodel_collect", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _i32, _vp, _P(ctypes.c_float),
+                                    _P(ctypes.c_float), _P(_i32), _i32, _P(_i32)]),
     ("wt_mlp_train_steps", _i32, [_P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float), _i32,
                                   _P(ctypes.c_float), _P(ctypes.c_float), _i32, _P(_i32), _i32, _i32,
                                   ctypes.c_float, ctypes.c_float, _P(ctypes.c_float), _vp]),
@@ -622,6 +624,24 @@ def costmodel_features(pipe, first, n, params=None, fused=True, width=4096, heig
     check(load().wt_costmodel_features(pipe.h, first, n, ctypes.byref(prm) if prm is not None else None,
                                        int(fused), width, height, dtype, _fptr(f)))
     return f
+
+
+def costmodel_collect(pipe, inputs, outputs, reps=10, stream=None):
+    """(features [n, 18], log ms [n], stages [n, 2]) of the timed launches of
+    one run of the installed schedule (see wt_costmodel_collect)."""
+    import numpy as np
+    ia = (wt_image * len(inputs))(*inputs)
+    oa = (wt_image * len(outputs))(*outputs)
+    n = _i32()
+    lib = load()
+    cap = 4 * len(pipe.spec["stages"]) + 4  # at least the launches of any run plan
+    f = np.zeros((cap, COSTMODEL_FEATURES), np.float32)
+    y = np.zeros(cap, np.float32)
+    st = (_i32 * (2 * cap))()
+    check(lib.wt_costmodel_collect(pipe.h, ia, len(inputs), oa, len(outputs), reps, stream, _fptr(f), _fptr(y), st,
+                                   cap, ctypes.byref(n)))
+    k = n.value
+    return f[:k], y[:k], np.array(list(st), np.int32).reshape(-1, 2)[:k]
 
 
 def mlp_train_steps(params, m, v, t0, x, y, idx, lr, weight_decay=0.0):

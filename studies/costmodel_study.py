@@ -13,8 +13,8 @@ groupings (all 4 of sharpen's, a seeded sample of the corner response's
 warps per block ({1, 2, 4} for sharpen, {1, 2} for the corner response) x
 pixels per lane {4, 8}: the space DP-Fusion's learned search draws from.  Each
 schedule runs once against the default schedule's output (the largest
-difference is reported) and is timed launch by launch
-(wt_schedule_time_launches).
+difference is reported) and is timed launch by launch, each launch with its
+features (wt_costmodel_collect).
 
 A launch is identified by its feature vector (stage segment, effective tile
 height, pixels per lane, warps, fracReg, ...), so two schedules that share a
@@ -104,14 +104,13 @@ def collect(name, rng, stream, log):
         ng = max(g) + 1
         pipe.schedule(groups=g, params=[prm] * ng)
         y.t.zero_()
-        launches = pipe.time_launches([x.image()], [y.image()], 10, stream)
+        # every launch timed and described by the library (wt_costmodel_collect)
+        f, log_ms, _ = wt.costmodel_collect(pipe, [x.image()], [y.image()], 10, stream)
         pipe.check(stream)
         err = float((y.view() - ref.view()).abs().max())
         worst = max(worst, err)
-        feats, ms = [], []
-        for first, cnt, fused, t in launches:
-            feats.append(wt.costmodel_features(pipe, first, cnt, prm if fused else None, fused, W, H).tolist())
-            ms.append(t)
+        feats = f.tolist()
+        ms = [float(v) for v in np.exp(log_ms.astype(np.float64))]
         analytic = 0.0
         for gi in range(ng):
             stages = [s for s in range(n) if g[s] == gi]

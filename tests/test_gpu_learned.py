@@ -190,3 +190,50 @@ def test_shipped_model_picks_a_fast_corner_response_schedule():
         assert t_learned <= 1.10 * t_default, (t_learned, t_default, p.schedule_get())
     finally:
         wt.costmodel_reset()
+
+
+def test_costmodel_collect_matches_features_and_launch_times():
+    """wt_costmodel_collect: one row per fused or per-stage launch of the
+    run, its features equal to wt_costmodel_features of that launch, its log
+    time that of wt_schedule_time_launches (re-timed: within a factor of 2);
+    launches without features (the reduction chain) are skipped; the run's
+    output is the schedule's."""
+    from paper_1909_07190_gb300 import wt
+    s = torch.cuda.current_stream().cuda_stream
+    W, H = 1000, 600
+    spec = P.harris()
+    img = I.uniform_image(62, W, H)[0]
+    x = wt.DeviceImage(1, H, W).upload(img)
+    y = wt.DeviceImage(1, H, W)
+    ref = O.evaluate(spec["stages"], [img[None].astype(np.float64)], spec["outputs"])[0][0]
+    groups = [0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3]
+    prm = [dict(tile_h=16, frac_reg=1.0, vec=4, warps_per_block=1)] * 4
+    p = wt.Pipeline(spec)
+    p.schedule(groups=groups, params=prm)
+    f, lm, st = wt.costmodel_collect(p, [x.image()], [y.image()], 5, s)
+    p.check(s)
+    assert np.abs(y.download()[0] - ref).max() <= 1e-5
+    assert f.shape == (4, 18) and lm.shape == (4,)
+    assert [tuple(r) for r in st] == [(0, 2), (2, 3), (5, 3), (8, 3)]
+    t = p.time_launches([x.image()], [y.image()], 5, s)
+    for i, (first, cnt, fused, ms) in enumerate(t):
+        assert fused and (first, cnt) == tuple(st[i])
+        want = wt.costmodel_features(p, first, cnt, prm[i], True, W, H)
+        assert np.allclose(f[i], want, rtol=1e-6, atol=1e-6)
+        assert np.isfinite(lm[i]) and abs(lm[i] - np.log(ms)) < np.log(2.0)
+    # per-stage kernels: every stage a row of its own, fused feature 0
+    q = wt.Pipeline(spec)
+    q.schedule(exec_mode=wt.WT_EXEC_PLAIN)
+    f2, lm2, st2 = wt.costmodel_collect(q, [x.image()], [y.image()], 3, s)
+    assert len(lm2) == len(spec["stages"]) and np.all(f2[:, 17] == 0)
+    assert sorted(r[0] for r in st2) == list(range(len(spec["stages"])))
+    # the bilateral filter's default schedule: the reduction chain has no
+    # features, the blur and the slice (per-stage kernels) do
+    bspec = P.bilateral_filter()
+    b = wt.Pipeline(bspec)
+    bg, bp = P.bilateral_schedule()
+    b.schedule(groups=bg, params=bp)
+    yb = wt.DeviceImage(1, H, W)
+    f3, lm3, st3 = wt.costmodel_collect(b, [x.image()], [yb.image()], 3, s)
+    b.check(s)
+    assert 1 <= len(lm3) < b.launches_per_run() and np.all(np.isfinite(lm3))
