@@ -671,12 +671,15 @@ def timed_steps(torch, work, step_fn, steps, warmup, per_graph, dist, sampler=No
 def traffic_record(workload, kname):
     """ncu figures of the kernel from the committed profile summary (DRAM
     bytes and executed warp instructions per launch), used only when they
-    were taken on the kernel that ran here (same generated kernel name)."""
+    were taken on the kernel that ran here (same generated kernel name).  A
+    workload whose schedule is tuned at run time may list one record per
+    kernel the search picks."""
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(tpath)).get(workload)
-        if rec and rec.get("kernel") == kname:
-            return rec
+        recs = json.load(open(tpath)).get(workload)
+        for rec in (recs if isinstance(recs, list) else [recs]):
+            if rec and rec.get("kernel") == kname:
+                return rec
     except Exception:
         pass
     return None
