@@ -321,7 +321,13 @@ wt_status wt_cost_weights(const double *set7, double *get7);
  * stage outputs[k].  Input and output dtypes may differ.  The first run for
  * a new image size allocates the library's device workspace and compiles
  * the group kernels; later runs allocate nothing and may be captured in a
- * CUDA graph.  Device-side failures are reported by wt_check().           */
+ * CUDA graph.  Launches that read nothing an earlier launch of the run
+ * writes run concurrently on the pipeline's side streams (WT_FLAG_ONE_STREAM
+ * describes the fork and join); the run as a whole stays ordered on
+ * `stream`.  The intermediates, the side streams and their events belong to
+ * the pipeline, so runs of one pipeline must not overlap on the GPU (issue
+ * them on one stream, or order their streams); separate pipelines may run
+ * at the same time.  Device-side failures are reported by wt_check().     */
 wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                  const wt_image *outputs, int32_t n_outputs, void *stream);
 
