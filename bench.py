@@ -391,6 +391,10 @@ class Single:
     def kernel_name(self, pipe):
         return pipe.debug_kernel(0, [self.ins[0].image()], [self.outs[0].image()])["name"]
 
+    def io(self):
+        """Inputs and outputs of one run (the first buffer set)."""
+        return [self.ins[0].image()], [self.outs[0].image()]
+
     def dominant(self, pipe, sp, spec):
         return dominant_launch(pipe, [self.ins[0].image()], [self.outs[0].image()], spec, self.W, self.H, self.esz,
                                sp)
@@ -831,10 +835,15 @@ def cost_model_entry(wt, torch, workload, rank, local, dist, steps):
     out["search_seconds"] = round(time.perf_counter() - t0, 2)
     for k, pipe in pipes.items():
         total, _ = timed_steps(torch, work, lambda i, s, q=pipe: work.run(q, i, s), steps, 3, 100, dist)
-        out[k] = {"ms": total / steps, "schedule": pipe.schedule_get()}
+        out[k] = {"ms": total / steps, "schedule": pipe.schedule_get(),
+                  "kernels": [pipe.kernel_name(j, *work.io()) for j in range(pipe.launches_per_run())]
+                  if hasattr(work, "io") else None}
     for k in ("analytic", "learned"):
         if k in out:
             out[k]["ratio_vs_default"] = out[k]["ms"] / out["default"]["ms"]
+            # the same generated kernels as the default schedule (the headline's)
+            out[k]["same_kernels_as_default"] = (out[k]["kernels"] is not None and
+                                                 out[k]["kernels"] == out["default"]["kernels"])
     for pipe in pipes.values():
         pipe.close()
     return out
