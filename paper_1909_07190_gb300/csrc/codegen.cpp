@@ -66,6 +66,7 @@ std::string CodegenKey::str() const {
   if (test_stall) s << "|STALL";
   if (fold) s << "|S";
   if (soft_cap) s << "|soft";
+  if (shared_planes) s << "|SP";
   return s.str();
 }
 
@@ -1631,6 +1632,20 @@ std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid) {
   return r;
 }
 
+bool plain_shares_planes(const Pipeline &p, int sid) {
+  const Stage &S = p.stages[sid];
+  std::map<int, std::set<int>> planes;  // slot -> fixed planes read by taps up by 4 or 8
+  for (const Op &op : S.ops) {
+    if (op.op != WT_OP_TAP) continue;
+    const int pid = S.inputs[op.slot];
+    const int pc = pid >= 0 ? p.stages[pid].channels : p.in_channels[-pid - 1];
+    if (pc > 1 && op.chan >= 0 && tap_is_up(op.mode) && tap_shift(op.mode) >= 2) planes[op.slot].insert(op.chan);
+  }
+  for (const auto &kv : planes)
+    if (kv.second.size() >= 2) return true;
+  return false;
+}
+
 std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const std::string &kname) {
   const Stage &S = p.stages[sid];
   std::vector<PlainSrc> srcs = plain_sources(p, sid);
@@ -1689,6 +1704,34 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
     int s = r.s;
     int dt = key.src_dtypes.at(s);
     int lo = col_index(r.mode, 0, r.dxmin), hi = col_index(r.mode, PV - 1, r.dxmax);
+    // A fixed plane of a producer whose same row segment an earlier row
+    // already addresses through another fixed plane (a multi-plane grid
+    // read plane by plane): that row's pointer plus the plane offset, and
+    // its descriptor for the clamps, so the column clamps and offsets are
+    // computed once for all the planes.
+    // (Rows of taps up by 4 or 8 only: they load scalars in any case.)
+    const bool scalar_row = tap_is_up(r.mode) && tap_shift(r.mode) >= 2;
+    int same = -1;
+    if (srcs[s].chan >= 0 && scalar_row)
+      for (size_t q = 0; q < ri && same < 0; q++) {
+        const Row &rq = rows[q];
+        if (srcs[rq.s].slot == srcs[s].slot && srcs[rq.s].chan >= 0 && rq.dy == r.dy && rq.dz == r.dz &&
+            rq.mode == r.mode && rq.dxmin == r.dxmin && rq.dxmax == r.dxmax && key.src_dtypes.at(rq.s) == dt)
+          same = (int)q;
+      }
+    if (same >= 0) {
+      const int s0 = rows[same].s;
+      const std::string sd0 = "a.src[" + std::to_string(s0) + "]";
+      o << "const unsigned char *rp" << ri << " = rp" << same << " + (wt_i64)(" << srcs[s].chan - srcs[s0].chan
+        << ") * " << sd0 << ".plane;\n";
+      o << "float";
+      for (int j = lo; j <= hi; j++) o << (j == lo ? " " : ", ") << "L" << ri << "_" << (j - lo);
+      o << ";\n";
+      for (int j = lo; j <= hi; j++)
+        o << "L" << ri << "_" << (j - lo) << " = wt_ld1_" << dtype_name(dt) << "(rp" << ri << " + (rp" << same
+          << "_o" << (j - lo) << "));\n";
+      continue;
+    }
     std::string sd = "a.src[" + std::to_string(s) + "]";
     std::string zc = srcs[s].chan >= 0 ? std::to_string(srcs[s].chan)
                      : r.dz == 0 ? std::string("ch")
@@ -1731,6 +1774,15 @@ std::string emit_plain(const Pipeline &p, int sid, const CodegenKey &key, const 
         << " + (wt_i64)wt_clampi(" << base << " + (" << j << "), 0, " << sd << ".W - 1) * "
         << elem_bytes(dt) << ");\n";
     o << "}\n";
+    // the clamped column offsets of this row, for the planes that share it
+    bool shared = false;
+    for (size_t q = ri + 1; q < rows.size(); q++)
+      if (srcs[rows[q].s].slot == srcs[s].slot && srcs[s].chan >= 0 && tap_is_up(r.mode) && tap_shift(r.mode) >= 2)
+        shared = true;
+    if (shared)
+      for (int j = lo; j <= hi; j++)
+        o << "const wt_i64 rp" << ri << "_o" << (j - lo) << " = (wt_i64)wt_clampi(" << base << " + (" << j
+          << "), 0, " << sd << ".W - 1) * " << elem_bytes(dt) << ";\n";
   }
   for (int e = 0; e < PV; e++) {
     std::vector<std::string> st;

@@ -419,6 +419,7 @@ RunPlan build_plan(Pipeline &p, const wt_image *in, int n_in, const wt_image *ou
       }
       L.dst.push_back(s);
       key.dst_dtypes.push_back(plan.loc[s].dtype);
+      key.shared_planes = plain_shares_planes(p, s);
       level_dims(plan.W, plan.H, p.stages[s].level, &L.W, &L.H);
       const int vo = L.params.vec == 8 ? 8 : 4;  // outputs per lane (default 4)
       if (p.sched.exec == WT_EXEC_FUSED && down_streamable(down_form(p, s), vo)) {

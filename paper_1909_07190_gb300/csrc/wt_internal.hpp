@@ -316,6 +316,9 @@ struct CodegenKey {
   // max_regs is the library's soft cap (the schedule set none): get_kernel
   // rebuilds the kernel uncapped if it spills under it
   bool soft_cap = false;
+  // per-stage kernel reading several fixed planes of one producer through
+  // taps up by 4 or 8: the planes share one row address and column clamps
+  bool shared_planes = false;
   // test only (WT_FLAG_TEST_STALL): the first chunk of every tile is armed
   // for bytes no copy delivers, and waits give up after a few polls
   bool test_stall = false;
@@ -431,6 +434,9 @@ struct PlainSrc {
   int slot, chan;
 };
 std::vector<PlainSrc> plain_sources(const Pipeline &p, int sid);
+// Whether stage sid's per-stage kernel reads two or more fixed planes of
+// one producer through taps up by 4 or 8 (they then share row addressing).
+bool plain_shares_planes(const Pipeline &p, int sid);
 extern const char *kDeviceSource;  // device_src.cpp
 
 // vol.cpp: a fused group over a volume (App. A, generalised hybrid
