@@ -336,10 +336,11 @@ wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
  * host.  Work is ordered after earlier work on `stream`.  Host images use
  * the same layout rules; pinned memory makes the copies asynchronous.
  * Pipelines whose stages are all at level 0, with one-plane inputs of at
- * least 16 MiB, run in 2 to 8 row bands of at least 8 MiB of input (each band's rows plus the pipeline's row
- * halo; results identical to the whole-image run) with the copy-in, the
- * compute and the copy-out of consecutive bands overlapped on the library's
- * own streams.  The second call with the same host image descriptors
+ * least 16 MiB, run in 2 to 8 row bands of at least 8 MiB of input (each
+ * band's rows plus the pipeline's row halo, starting on an even row so
+ * that WT_OP_YPAR reads the whole image's row parity; results identical to
+ * the whole-image run) with the copy-in, the compute and the copy-out of
+ * consecutive bands overlapped on the library's own streams.  The second call with the same host image descriptors
  * captures that work as a CUDA graph; later calls with them replay it (a
  * new schedule or larger staging discards the captured graphs).  Device
  * staging buffers are allocated on first use and kept.                    */

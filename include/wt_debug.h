@@ -80,6 +80,14 @@ wt_status wt_debug_layout(wt_pipeline *p, int32_t launch_index, const wt_image *
 wt_status wt_debug_lanes(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
                          int32_t n_outputs, int32_t *out, int32_t cap, int32_t *n_out);
 
+/* Row bands of wt_run_host for these images (planning only, no device
+ * work): 4 values per band, (y0, y1, ys, ye): the band keeps output rows
+ * [y0, y1) and runs the pipeline on input rows [ys, ye), ys even.
+ * *n_bands = 0 when the call runs the whole image at once.  At most cap
+ * bands are written; *n_bands gets the full count.                         */
+wt_status wt_debug_host_bands(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                              int32_t n_outputs, int32_t *bands, int32_t cap, int32_t *n_bands);
+
 /* Halo/window analysis of schedule group `group` (Sec. 4 overlap, Sec. 5
  * parallelogram skew): out = [fusable, halo_l, halo_r, halo_t, halo_b,
  * unroll, n_nodes, then per node: id, src_chan, is_source, is_liveout, top,

@@ -251,6 +251,49 @@ int pipeline_row_halo(const wt::Pipeline &p) {
   return h;
 }
 
+// Row bands of a banded host run: band b keeps output rows [y0, y1) and
+// runs the pipeline on input rows [ys, ye), its rows and the pipeline's row
+// halo.  ys is even, so a program reading the output row's parity
+// (WT_OP_YPAR) sees the same parity in the band's sub-image as in the
+// whole image.  Empty when the call runs the whole image at once: a stage
+// off level 0, a multi-plane input, inputs and outputs of different
+// heights, or an image too small to split.
+struct HostBand {
+  int y0, y1, ys, ye;
+};
+
+std::vector<HostBand> plan_host_bands(const wt::Pipeline &p, const wt_image *inputs, int n_in,
+                                      const wt_image *outputs, int n_out) {
+  const int h = pipeline_row_halo(p);
+  if (h < 0) return {};
+  const int H = inputs[0].height;
+  for (int j = 0; j < n_in; j++)
+    if (inputs[j].height != H || inputs[j].channels != 1) return {};
+  for (int k = 0; k < n_out; k++)
+    if (outputs[k].height != H) return {};
+  // Up to 8 bands (pipeline fill and drain cost one band's copies), none
+  // shorter than 64 rows or 4 halos, and none copying less than 8 MiB in
+  // (every band adds copies, events and a launch of a short image; on a
+  // GB300 the corner response at 4096^2 ran 6% faster end to end with 8
+  // bands of 8 MiB than with 16 of 4 MiB, and at 2048^2 and 8192^2 no slower).
+  int64_t in_bytes = 0;
+  for (int j = 0; j < n_in; j++) in_bytes += image_bytes(inputs[j]);
+  const int min_rows = std::max(64, 4 * h);
+  const int kBands = (int)std::min<int64_t>({8, H / min_rows, in_bytes / (8 << 20)});
+  if (kBands < 2) return {};
+  const int rows = (H + kBands - 1) / kBands;
+  std::vector<HostBand> bands;
+  for (int y0 = 0; y0 < H; y0 += rows) {
+    HostBand B;
+    B.y0 = y0;
+    B.y1 = std::min(H, y0 + rows);
+    B.ys = std::max(0, y0 - h) & ~1;
+    B.ye = std::min(H, B.y1 + h);
+    bands.push_back(B);
+  }
+  return bands;
+}
+
 // wt_run_host in row bands for single-level pipelines: band b's input rows
 // (with the pipeline's halo) are copied in on one stream while band b-1
 // computes on a second and band b-2's output rows are copied out on a
@@ -261,25 +304,10 @@ int pipeline_row_halo(const wt::Pipeline &p) {
 // qualify (then the caller runs the whole image at once).
 bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt_image *outputs, int n_out,
                      cudaStream_t user, wt::Workspace &w, const std::function<void *(int, const wt_image &)> &stage) {
-  const int h = pipeline_row_halo(p);
-  if (h < 0) return false;
+  const std::vector<HostBand> plan = plan_host_bands(p, inputs, n_in, outputs, n_out);
+  if (plan.empty()) return false;
   const int H = inputs[0].height;
-  for (int j = 0; j < n_in; j++)
-    if (inputs[j].height != H) return false;
-  for (int k = 0; k < n_out; k++)
-    if (outputs[k].height != H) return false;
-  // Up to 8 bands (pipeline fill and drain cost one band's copies), none
-  // shorter than 64 rows or 4 halos, and none copying less than 8 MiB in
-  // (every band adds copies, events and a launch of a short image; on a
-  // GB300 the corner response at 4096^2 ran 6% faster end to end with 8
-  // bands of 8 MiB than with 16 of 4 MiB, and at 2048^2 and 8192^2 no slower).
-  int64_t in_bytes = 0;
-  for (int j = 0; j < n_in; j++) in_bytes += image_bytes(inputs[j]);
-  const int min_rows = std::max(64, 4 * h);
-  const int kBands = (int)std::min<int64_t>({8, H / min_rows, in_bytes / (8 << 20)});
-  if (kBands < 2) return false;
-  const int rows = (H + kBands - 1) / kBands;
-  const int nb = (H + rows - 1) / rows;
+  const int nb = (int)plan.size();
   for (int i = 0; i < 3; i++)
     if (!w.band_stream[i])
       wt::check_rt(cudaStreamCreateWithFlags(&w.band_stream[i], cudaStreamNonBlocking), "cudaStreamCreate");
@@ -294,12 +322,13 @@ bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt
   // (allocated here, never while a graph is being captured)
   std::vector<wt_image> din(inputs, inputs + n_in);
   for (int j = 0; j < n_in; j++) din[j].data = stage(j, inputs[j]);
-  const int brows = rows + 2 * h;
+  int brows = 0;
+  for (const HostBand &B : plan) brows = std::max(brows, B.ye - B.ys);
   std::vector<wt_image> scratch[2];
   for (int q = 0; q < 2; q++)
     for (int k = 0; k < n_out; k++) {
       wt_image sc = outputs[k];
-      sc.height = std::min(H, brows);
+      sc.height = brows;
       sc.data = stage(200 + 16 * q + k, sc);
       scratch[q].push_back(sc);
     }
@@ -310,10 +339,10 @@ bool run_host_banded(wt::Pipeline &p, const wt_image *inputs, int n_in, const wt
   std::vector<Band> bands;
   for (int b = 0; b < nb; b++) {
     Band B;
-    B.y0 = b * rows;
-    B.y1 = std::min(H, B.y0 + rows);
-    B.ys = std::max(0, B.y0 - h);
-    B.ye = std::min(H, B.y1 + h);
+    B.y0 = plan[b].y0;
+    B.y1 = plan[b].y1;
+    B.ys = plan[b].ys;
+    B.ye = plan[b].ye;
     B.in = din;
     B.out = scratch[b % 2];
     for (int j = 0; j < n_in; j++) {
@@ -454,9 +483,7 @@ wt_status wt_run_host(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, 
       if (!inputs[j].data) wt::fail(WT_EINVAL, "null host input");
     for (int k = 0; k < n_outputs; k++)
       if (!outputs[k].data) wt::fail(WT_EINVAL, "null host output");
-    bool single_plane = true;
-    for (int j = 0; j < n_inputs; j++) single_plane = single_plane && inputs[j].channels == 1;
-    if (single_plane && run_host_banded(*p, inputs, n_inputs, outputs, n_outputs, st, w, stage)) return;
+    if (run_host_banded(*p, inputs, n_inputs, outputs, n_outputs, st, w, stage)) return;
     for (int j = 0; j < n_inputs; j++) {
       din[j].data = stage(j, inputs[j]);
       wt::check_rt(cudaMemcpyAsync(din[j].data, inputs[j].data, (size_t)image_bytes(inputs[j]),
@@ -762,6 +789,25 @@ wt_status wt_debug_lanes(wt_pipeline *p, const wt_image *inputs, int32_t n_input
     if (n_out) *n_out = (int32_t)v.size();
     if (out)
       for (int i = 0; i < (int)v.size() && i < cap; i++) out[i] = v[i];
+  });
+}
+
+wt_status wt_debug_host_bands(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
+                              int32_t n_outputs, int32_t *bands, int32_t cap, int32_t *n_bands) {
+  return guard([&] {
+    if (!p) wt::fail(WT_EINVAL, "null pipeline");
+    if (!inputs || !outputs || n_inputs < 1 || n_outputs < 1 || n_inputs > 16 || n_outputs > 16)
+      wt::fail(WT_EINVAL, "bad image arrays");
+    std::lock_guard<std::mutex> lk(p->mu);
+    const std::vector<HostBand> plan = plan_host_bands(*p, inputs, n_inputs, outputs, n_outputs);
+    if (n_bands) *n_bands = (int32_t)plan.size();
+    if (bands)
+      for (int b = 0; b < (int)plan.size() && b < cap; b++) {
+        bands[4 * b] = plan[b].y0;
+        bands[4 * b + 1] = plan[b].y1;
+        bands[4 * b + 2] = plan[b].ys;
+        bands[4 * b + 3] = plan[b].ye;
+      }
   });
 }
 

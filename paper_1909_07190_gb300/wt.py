@@ -140,6 +140,7 @@ SIGNATURES = [
     ("wt_debug_compile", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i64)]),
     ("wt_debug_layout", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_lanes", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
+    ("wt_debug_host_bands", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_inject_alloc_failure", _i32, [_i32, _i32]),
     ("wt_debug_live_objects", _i32, [_P(_i64), _P(_i64)]),
@@ -480,6 +481,18 @@ class Pipeline:
             launches.append({"lane": lane, "waits": waits, "stages": v[k + 1:k + 1 + ns]})
             k += 1 + ns
         return v[1], launches
+
+    def debug_host_bands(self, inputs, outputs):
+        """Row bands of run_host for these images: a list of (y0, y1, ys, ye),
+        kept output rows [y0, y1) computed from input rows [ys, ye); empty
+        when the call runs the whole image at once."""
+        ia = (wt_image * len(inputs))(*inputs)
+        oa = (wt_image * len(outputs))(*outputs)
+        n = _i32()
+        check(load().wt_debug_host_bands(self.h, ia, len(inputs), oa, len(outputs), None, 0, ctypes.byref(n)))
+        out = (_i32 * max(1, 4 * n.value))()
+        check(load().wt_debug_host_bands(self.h, ia, len(inputs), oa, len(outputs), out, n.value, ctypes.byref(n)))
+        return [tuple(out[4 * b:4 * b + 4]) for b in range(n.value)]
 
     def debug_layout(self, index, inputs, outputs):
         ia = (wt_image * len(inputs))(*inputs)

@@ -78,6 +78,22 @@ def test_run_host_bands_multi_output_and_planes():
         assert np.abs(g - r).max() <= 1e-5
 
 
+def test_run_host_bands_row_parity():
+    """A stage reading the output row's parity (a Bayer-like pattern) on an
+    image of two 2049-row bands with a 2-row halo: the second band's
+    sub-image would start on an odd row; bands start on even rows, so the
+    host run equals the device run."""
+    from test_host_bands import parity_pipeline
+    wt = wtmod()
+    spec = parity_pipeline(1)
+    im = [wt.image(1 << 36, 1024, 4097, 1, wt.WT_F32, 4096)]
+    assert [b[2] for b in wt.Pipeline(spec).debug_host_bands(im, im)] == [0, 2046]
+    img = rnd(9, 1024, 4097)
+    got = host_vs_device(spec, img)
+    ref = oracle_out(spec, [img])[0]
+    assert np.abs(got[0][0] - ref).max() <= 1e-5
+
+
 def test_run_host_repeated_calls_replay():
     """Calls with the same host images: the first runs the bands directly,
     the second captures them into a CUDA graph, later ones replay it.  New
