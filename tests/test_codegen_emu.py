@@ -407,3 +407,136 @@ def test_deferred_scales_blend_level():
         prm = [dict(q, flags=q.get("flags", 0) | flags) for q in params]
         got, _ = run_emulated(spec, [a, b, m], groups=groups, params=prm)
         assert np.abs(got[0] - ref).max() <= 1e-5
+
+
+def scaled_dag(seed, n_stages=7):
+    """Seeded random single-level DAG whose stages carry constant factors
+    (normalisations, signs, powers of two and others) under non-linear
+    operations: min and max against constants and against operands of the
+    same factor, abs, sqrt, division by constants and by other values,
+    negation, row and column parity (test input, not a pipeline)."""
+    rng = np.random.default_rng(seed)
+    b = P.Builder("fold%d" % seed, [1, 1])
+    ids = [P.input_id(0), P.input_id(1)]
+    factors = [0.25, 0.125, -0.5, 2.0, 1.0 / 16, 3.0, -1.0, 1.0 / 576]
+    outs = []
+
+    def term():
+        return P.ref(ids[int(rng.integers(0, len(ids)))], int(rng.integers(-2, 3)), int(rng.integers(-2, 3)))
+
+    for s in range(n_stages):
+        c = factors[int(rng.integers(0, len(factors)))]
+        expr = None
+        for w in rng.integers(-2, 3, size=int(rng.integers(1, 4))):
+            w = int(w) or 1
+            t = term() if w == 1 else float(w) * term()
+            expr = t if expr is None else expr + t
+        expr = expr * c if rng.uniform() < 0.5 else c * expr
+        kind = int(rng.integers(0, 12))
+        if kind == 1:
+            expr = P.emin(expr, float(rng.uniform(-0.3, 0.3)))
+        elif kind == 2:
+            expr = P.emax(0.2, expr)
+        elif kind == 3:
+            expr = P.eabs(expr) * 0.5
+        elif kind == 4:
+            expr = P.esqrt(P.eabs(expr) + 0.01)
+        elif kind == 5:
+            expr = expr / 3.0
+        elif kind == 6:
+            expr = expr / (P.eabs(term()) + 1.0)
+        elif kind == 7:
+            expr = 0.75 - expr
+        elif kind == 8:
+            expr = -expr + term() * 0.5
+        elif kind == 9:
+            expr = P.emin(expr, term() * c)
+        elif kind == 10:
+            expr = expr * term() - P.YPAR * 0.25 + P.XPAR * expr
+        elif kind == 11:
+            expr = (expr - term() * (2 * c)) * 4.0
+        sid = b.stage("s%d" % s, expr)
+        ids.append(sid)
+        if rng.uniform() < 0.25:
+            outs.append(sid)
+    if ids[-1] not in outs:
+        outs.append(ids[-1])
+    b.output(*outs)
+    return b.build()
+
+
+@pytest.mark.parametrize("seed", [0, 3, 11, 24, 37])
+def test_deferred_scales_random_programs(seed):
+    """Constant factors carried through min, max, abs, sqrt, division and
+    sums of differently scaled terms: the deferred form and the form as
+    written both match the oracle."""
+    spec = scaled_dag(seed)
+    imgs = [rnd(300 + seed, 61, 29), rnd(400 + seed, 61, 29)]
+    ref = oracle_of(spec, imgs)
+    for flags in (0, wt.WT_FLAG_NO_FOLD):
+        got, _ = run_emulated(spec, imgs, params=[dict(tile_h=8, flags=flags)])
+        for g, r in zip(got, ref):
+            assert np.abs(g - r).max() <= 1e-5 * max(1.0, np.abs(r).max())
+
+
+def multilevel_dag(seed, n_stages=7):
+    """Seeded random DAG over three pyramid levels: each stage sits on a
+    level and reads producers up to two levels finer or coarser (taps
+    scaling by 2 or 4) or on its own level (test input, not a pipeline)."""
+    mode = {0: "same", -1: "down2", 1: "up2", -2: "down4", 2: "up4"}
+    rng = np.random.default_rng(seed)
+    b = P.Builder("ml%d" % seed, [1])
+    nodes = [(P.input_id(0), 0)]
+    outs = []
+    for s in range(n_stages):
+        L = int(rng.integers(0, 3))
+        expr = None
+        for _ in range(int(rng.integers(1, 4))):
+            pid, lp = nodes[int(rng.integers(0, len(nodes)))]
+            t = float(rng.choice([0.25, 0.5, -0.375, 1.0])) * P.ref(pid, int(rng.integers(-2, 3)),
+                                                                    int(rng.integers(-2, 3)), mode=mode[lp - L])
+            expr = t if expr is None else expr + t
+        kind = int(rng.integers(0, 5))
+        if kind == 1:
+            expr = expr + P.YPAR * 0.125 - P.XPAR * 0.25
+        elif kind == 2:
+            expr = P.emin(expr, 0.3)
+        elif kind == 3:
+            expr = P.eabs(expr) * 0.5
+        sid = b.stage("s%d" % s, expr)
+        nodes.append((sid, L))
+        if rng.uniform() < 0.3:
+            outs.append(sid)
+    if nodes[-1][0] not in outs:
+        outs.append(nodes[-1][0])
+    b.output(*outs)
+    return b.build()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 4])
+def test_multilevel_random_groupings(seed):
+    """Random DAGs across pyramid levels under the analytic model's
+    schedule and under random contiguous groupings with random tile
+    parameters, against the oracle."""
+    spec = multilevel_dag(seed)
+    W, H = [(67, 45), (130, 33), (41, 77)][seed % 3]
+    imgs = [rnd(500 + seed, W, H)]
+    ref = oracle_of(spec, imgs)
+    p = wt.Pipeline(spec)
+    p.schedule_auto(W, H)
+    sch = p.schedule_get()
+    schedules = [(sch["groups"], sch["params"])]
+    rng = np.random.default_rng(1000 + seed)
+    for _ in range(2):
+        g, cur = [], 0
+        for i in range(len(spec["stages"])):
+            cur += int(i > 0 and rng.uniform() < 0.35)
+            g.append(cur)
+        prm = [dict(tile_h=int(rng.choice([4, 8, 16])), frac_reg=float(rng.choice([0.0, 0.5, 1.0])),
+                    vec=int(rng.choice([0, 4, 8])), warps_per_block=int(rng.choice([1, 2])))
+               for _ in range(max(g) + 1)]
+        schedules.append((g, prm))
+    for g, prm in schedules:
+        got, _ = run_emulated(spec, imgs, groups=g, params=prm)
+        for a, r in zip(got, ref):
+            assert np.abs(a - r).max() <= 1e-5 * max(1.0, np.abs(r).max())
