@@ -88,6 +88,16 @@ wt_status wt_debug_lanes(wt_pipeline *p, const wt_image *inputs, int32_t n_input
 wt_status wt_debug_host_bands(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs, const wt_image *outputs,
                               int32_t n_outputs, int32_t *bands, int32_t cap, int32_t *n_bands);
 
+/* The analytic model's cost of stages [first, first + n) as one group, as
+ * wt_schedule_auto's DP-Fusion (Alg. 2) weighs it for a width x height
+ * image of `dtype`: the best over the group's tile shapes and fracReg, or
+ * the per-stage kernel for one stage.  *fused = 1 when a group kernel is
+ * the choice.  WT_EINVAL for a range outside the pipeline or longer than
+ * the longest group DP-Fusion forms (16 stages); *cost = +inf when no
+ * kernel can run the range as one group.                                   */
+wt_status wt_debug_segment_cost(wt_pipeline *p, int32_t first, int32_t n, int32_t width, int32_t height,
+                                int32_t dtype, double *cost, int32_t *fused);
+
 /* Halo/window analysis of schedule group `group` (Sec. 4 overlap, Sec. 5
  * parallelogram skew): out = [fusable, halo_l, halo_r, halo_t, halo_b,
  * unroll, n_nodes, then per node: id, src_chan, is_source, is_liveout, top,

@@ -811,6 +811,21 @@ wt_status wt_debug_host_bands(wt_pipeline *p, const wt_image *inputs, int32_t n_
   });
 }
 
+wt_status wt_debug_segment_cost(wt_pipeline *p, int32_t first, int32_t n, int32_t width, int32_t height,
+                                int32_t dtype, double *cost, int32_t *fused) {
+  return guard([&] {
+    if (!p || !cost) wt::fail(WT_EINVAL, "null argument");
+    if (first < 0 || n < 1 || n > wt::kMaxGroupStages || first + n > (int)p->stages.size())
+      wt::fail(WT_EINVAL, "stage range");
+    if (width < 1 || height < 1) wt::fail(WT_EINVAL, "bad size");
+    if (dtype < WT_F32 || dtype > WT_BF16) wt::fail(WT_EINVAL, "bad dtype");
+    std::lock_guard<std::mutex> lk(p->mu);
+    const wt::SegmentChoice c = wt::auto_segment(*p, first, n, width, height, dtype);
+    *cost = c.cost;
+    if (fused) *fused = c.fused ? 1 : 0;
+  });
+}
+
 wt_status wt_debug_group_geometry(wt_pipeline *p, int32_t group, int32_t vec, float frac_reg, int32_t *out,
                                   int32_t cap, int32_t *n_out) {
   return guard([&] {

@@ -598,16 +598,29 @@ Schedule dp_fusion(const Pipeline &p, int W, int H, int dtype, const GpuConfig &
   return s;
 }
 
-Schedule auto_schedule(const Pipeline &p, int W, int H, int dtype, int model) {
+// What the automatic schedule costs groups with: the current device (the
+// GB300 description without one), the stage statistics and the weights.
+static GpuConfig auto_config() {
   int dev = -1;
   bool gpu = cudaGetDevice(&dev) == cudaSuccess;
   cudaGetLastError();
-  GpuConfig cfg = gpu ? device_config(dev) : default_gb300();
+  return gpu ? device_config(dev) : default_gb300();
+}
+
+Schedule auto_schedule(const Pipeline &p, int W, int H, int dtype, int model) {
+  GpuConfig cfg = auto_config();
   std::vector<StageStats> st = stage_stats(p, false);
   CostWeights w = current_weights();
   // the learned model when one is trained or loaded, else the analytic one
-  if (model == WT_MODEL_LEARNED && costmodel_ready()) return learned_schedule(p, W, H, dtype, cfg, st, 16);
-  return dp_fusion(p, W, H, dtype, cfg, st, w, nullptr, 16);
+  if (model == WT_MODEL_LEARNED && costmodel_ready()) return learned_schedule(p, W, H, dtype, cfg, st, kMaxGroupStages);
+  return dp_fusion(p, W, H, dtype, cfg, st, w, nullptr, kMaxGroupStages);
+}
+
+SegmentChoice auto_segment(const Pipeline &p, int first, int n, int W, int H, int dtype) {
+  std::vector<int> seg;
+  for (int s = first; s < first + n; s++) seg.push_back(s);
+  return best_for_segment(p, seg, W, H, dtype, auto_config(), stage_stats(p, false), current_weights(),
+                          pipeline_bytes(p, W, H, dtype), nullptr);
 }
 
 }  // namespace wt

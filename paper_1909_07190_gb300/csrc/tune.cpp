@@ -221,7 +221,7 @@ TuneResult tune(Pipeline &p, const wt_image *in, int n_in, const wt_image *out, 
   // 1. grouping: the cost model's DP-Fusion choice, and all stages in one
   //    group when that group fuses; default tile parameters
   std::vector<Schedule> groupings;
-  Schedule dp = dp_fusion(p, W, H, dtype, cfg, st, w, nullptr, 16);
+  Schedule dp = dp_fusion(p, W, H, dtype, cfg, st, w, nullptr, kMaxGroupStages);
   for (auto &g : dp.params) g = GroupParams();
   groupings.push_back(dp);
   std::vector<int> all((size_t)p.stages.size());

@@ -82,7 +82,12 @@ SegmentChoice best_for_segment(const Pipeline &p, const std::vector<int> &seg, i
 Schedule dp_fusion(const Pipeline &p, int W, int H, int dtype, const GpuConfig &cfg,
                    const std::vector<StageStats> &st, const CostWeights &w, const CandidateScorer *scorer,
                    int max_group);
+// Longest group DP-Fusion forms (stages).
+constexpr int kMaxGroupStages = 16;
 Schedule auto_schedule(const Pipeline &p, int W, int H, int dtype, int model);
+// The analytic model's choice for stages [first, first + n) as
+// wt_schedule_auto's DP-Fusion weighs that group.
+SegmentChoice auto_segment(const Pipeline &p, int first, int n, int W, int H, int dtype);
 
 // learned.cpp (see wt_learned.hpp)
 bool costmodel_ready();

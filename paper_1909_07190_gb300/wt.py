@@ -141,6 +141,7 @@ SIGNATURES = [
     ("wt_debug_layout", _i32, [_vp, _i32, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_lanes", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_host_bands", _i32, [_vp, _P(wt_image), _i32, _P(wt_image), _i32, _P(_i32), _i32, _P(_i32)]),
+    ("wt_debug_segment_cost", _i32, [_vp, _i32, _i32, _i32, _i32, _i32, _P(ctypes.c_double), _P(_i32)]),
     ("wt_debug_group_geometry", _i32, [_vp, _i32, _i32, ctypes.c_float, _P(_i32), _i32, _P(_i32)]),
     ("wt_debug_inject_alloc_failure", _i32, [_i32, _i32]),
     ("wt_debug_live_objects", _i32, [_P(_i64), _P(_i64)]),
@@ -493,6 +494,13 @@ class Pipeline:
         out = (_i32 * max(1, 4 * n.value))()
         check(load().wt_debug_host_bands(self.h, ia, len(inputs), oa, len(outputs), out, n.value, ctypes.byref(n)))
         return [tuple(out[4 * b:4 * b + 4]) for b in range(n.value)]
+
+    def debug_segment_cost(self, first, n, width, height, dtype=WT_F32):
+        """(cost, fused): the analytic model's weight of stages
+        [first, first + n) as one group in wt_schedule_auto's DP-Fusion."""
+        c, f = ctypes.c_double(), _i32()
+        check(load().wt_debug_segment_cost(self.h, first, n, width, height, dtype, ctypes.byref(c), ctypes.byref(f)))
+        return c.value, bool(f.value)
 
     def debug_layout(self, index, inputs, outputs):
         ia = (wt_image * len(inputs))(*inputs)

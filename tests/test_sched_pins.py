@@ -163,3 +163,55 @@ def test_dp_fusion_proposes_reduction_chain_across_levels():
     assert g[0] == g[1] == g[2] and g[3] != g[2], g
     img = wt.image(0x10000000, 4096, 4096, 1, wt.WT_F32, 4096 * 4)
     assert p.kernel_name(0, [img], [img]).startswith("wt_chain_")
+
+
+def _groupings(n, max_group):
+    """Every split of stages 0..n-1 into contiguous groups of at most
+    max_group stages, as lists of (first, end)."""
+    if n == 0:
+        yield []
+        return
+    for k in range(1, min(n, max_group) + 1):
+        for rest in _groupings(n - k, max_group):
+            yield [(0, k)] + [(a + k, b + k) for a, b in rest]
+
+
+@pytest.mark.parametrize("case", ["sharpen_2048", "harris_4096", "harris_600x410_f16", "blur_1024",
+                                  "random6_512", "random9_4096_bf16"])
+def test_dp_fusion_matches_brute_force(case):
+    """Alg. 2's DP over contiguous groupings against enumerating all of
+    them: every grouping's cost is the sum of its groups' costs (the same
+    per-group choice the DP weighs), and the grouping wt_schedule_auto
+    installs reaches the smallest sum."""
+    from test_codegen_emu import random_dag
+    spec, W, H, dt = {
+        "sharpen_2048": (P.sharpen(), 2048, 2048, wt.WT_F32),
+        "harris_4096": (P.harris(), 4096, 4096, wt.WT_F32),
+        "harris_600x410_f16": (P.harris(), 600, 410, wt.WT_F16),
+        "blur_1024": (P.by_name("blur"), 1024, 1024, wt.WT_F32),
+        "random6_512": (random_dag(11, n_stages=6), 512, 512, wt.WT_F32),
+        "random9_4096_bf16": (random_dag(12, n_stages=9), 4096, 4096, wt.WT_BF16),
+    }[case]
+    n = len(spec["stages"])
+    p = wt.Pipeline(spec)
+    cost = {(a, b): p.debug_segment_cost(a, b - a, W, H, dt)[0]
+            for a in range(n) for b in range(a + 1, min(n, a + 16) + 1)}
+    sums = sorted(sum(cost[g] for g in split) for split in _groupings(n, 16))
+    assert len(sums) == 2 ** (n - 1)
+    p.schedule_auto(W, H, dt, wt.WT_MODEL_ANALYTIC)
+    groups = p.schedule_get()["groups"]
+    split = [(groups.index(g), len(groups) - groups[::-1].index(g)) for g in sorted(set(groups))]
+    assert sum(cost[g] for g in split) == pytest.approx(sums[0], rel=1e-12)
+    # the minimum is a real choice, not a tie across every grouping
+    assert sums[-1] > sums[0]
+
+
+def test_segment_cost_ranges():
+    p = wt.Pipeline(P.harris())
+    c, fused = p.debug_segment_cost(0, 11, 4096, 4096)
+    assert fused and c > 0
+    c1, f1 = p.debug_segment_cost(10, 1, 4096, 4096)
+    assert c1 > 0
+    for first, n in [(-1, 2), (0, 0), (5, 7), (0, 17)]:
+        with pytest.raises(wt.WtError):
+            p.debug_segment_cost(first, n, 4096, 4096)
