@@ -116,3 +116,15 @@ def test_batch_rejects_mixed_dtypes():
     i1, o1 = emu.HostImage(1, 20, 30, wt.WT_F16), emu.HostImage(1, 20, 30, wt.WT_F16)
     with pytest.raises(wt.WtError):
         p.debug_batch(0, [i0.image(), i1.image()], [o0.image(), o1.image()], 2)
+
+
+@pytest.mark.parametrize("tile_h", [3, 7])
+def test_batch_row_parity_odd_tiles(tile_h):
+    """A stage reading the output row's parity under odd tile heights:
+    every tile of every image takes the parity of its rows in its own image."""
+    from test_host_bands import parity_pipeline
+    spec = parity_pipeline(1)
+    batch = [[rnd(950 + i, w, h)] for i, (w, h) in enumerate(SIZES)]
+    got, _ = run_batch_emulated(spec, batch, params=[dict(tile_h=tile_h, warps_per_block=2)], max_blocks=3)
+    for imgs, g in zip(batch, got):
+        assert np.abs(g[0] - oracle_of(spec, imgs)[0]).max() <= 1e-5

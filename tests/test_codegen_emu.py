@@ -540,3 +540,18 @@ def test_multilevel_random_groupings(seed):
         got, _ = run_emulated(spec, imgs, groups=g, params=prm)
         for a, r in zip(got, ref):
             assert np.abs(a - r).max() <= 1e-5 * max(1.0, np.abs(r).max())
+
+
+@pytest.mark.parametrize("mode", ["otptb", "queue", "direct"])
+@pytest.mark.parametrize("tile_h", [5, 7])
+def test_row_parity_odd_tiles(mode, tile_h):
+    """Row parity under odd tile heights in the block-tile kernel, the
+    tile-queue kernel and one warp per tile."""
+    from test_host_bands import parity_pipeline
+    spec = parity_pipeline(1)
+    img = rnd(5 + tile_h, 130, 41)
+    prm = {"otptb": dict(tile_h=tile_h, warps_per_block=16, vec=1, flags=wt.WT_FLAG_OTPTB),
+           "queue": dict(tile_h=tile_h, flags=wt.WT_FLAG_TILE_QUEUE),
+           "direct": dict(tile_h=tile_h)}[mode]
+    got, _ = run_emulated(spec, [img], params=[prm], max_blocks=2 if mode == "queue" else None)
+    assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
