@@ -95,7 +95,7 @@ extern "C" wt_status wt_run_static(wt_pipeline *p, const wt_image *inputs, int32
     // intermediates need no clearing
     wt::check_rt(cudaMemsetAsync(base, 0, kStatusBytes, st), "cudaMemsetAsync(status word)");
     wt::run_plan_at(*p, plan, base + kStatusBytes, (int32_t *)base, st, dev);
-    p->static_devs |= uint64_t(1) << dev;
+    if (dev < 64) p->static_devs |= uint64_t(1) << dev;
     wt::set_last_error("");
     return WT_OK;
   } catch (const wt::Error &e) {
