@@ -212,3 +212,62 @@ def test_shipped_cost_model_loads():
     finally:
         wt.costmodel_reset()
     assert not wt.costmodel_ready()
+
+
+def _plan(spec, W, H, dt=wt.WT_F32, groups=None, params=None, exec_mode=None):
+    """Launch shapes of every launch of the run plan (planning only)."""
+    p = wt.Pipeline(spec)
+    if exec_mode is not None:
+        p.schedule(exec_mode=exec_mode)
+    elif params is not None:
+        p.schedule(groups=groups, params=params)
+    es = 4 if dt == wt.WT_F32 else 2
+    pitch = ((W * es + 127) // 128) * 128
+    ins = [wt.image(1 << 40, W, H, c, dt, pitch) for c in spec["inputs"]]
+    outs = [wt.image(1 << 41, W, H, spec["stages"][s]["channels"], dt, pitch) for s in spec["outputs"]]
+    wsb = p.debug_workspace_bytes(ins, outs)
+    return [p.debug_kernel(i, ins, outs, workspace=(1 << 42, max(wsb, 16)))
+            for i in range(p.launches_per_run())]
+
+
+@pytest.mark.parametrize("case", ["fused_64k", "plain_wide", "blend_64k", "otptb_wide", "vol_deep", "vol_wide"])
+def test_large_images_plan_within_launch_limits(case):
+    """Images far larger than the configurations plan into launches whose
+    grids stay inside CUDA's limits (x < 2^31, y and z <= 65535)."""
+    otptb = [dict(tile_h=32, warps_per_block=16, vec=1, flags=wt.WT_FLAG_OTPTB)]
+    g, q = P.blend_schedule()
+    plans = {
+        "fused_64k": lambda: _plan(P.harris(), 65536, 65536),
+        "plain_wide": lambda: _plan(P.harris(), 1 << 24, 64, exec_mode=wt.WT_EXEC_PLAIN),
+        "blend_64k": lambda: _plan(P.blend(), 65536, 65536, wt.WT_BF16, groups=g, params=q),
+        "otptb_wide": lambda: _plan(P.harris(), 1 << 26, 64, params=otptb),
+        "vol_deep": lambda: _plan(P.heat3d(2, depth=70000), 64, 64),
+        "vol_wide": lambda: _plan(P.unsharp3d(depth=8), 65536, 65536),
+    }
+    for d in plans[case]():
+        gx, gy, gz = d["grid"]
+        assert 1 <= gx < 2 ** 31 and 1 <= gy <= 65535 and 1 <= gz <= 65535, d["grid"]
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("fused_max", "too many tiles"),
+    ("queue_1m", "too many tiles"),
+    ("otptb_tall", "too many block tiles"),
+    ("plain_tall", "too tall"),
+    ("down_tall", "too tall"),
+])
+def test_oversized_images_rejected(case, msg):
+    """Beyond the launch limits planning fails with WT_EUNSUPPORTED and a
+    message, rather than launching a truncated grid."""
+    M = 2 ** 31 - 1
+    runs = {
+        "fused_max": lambda: _plan(P.harris(), M, M),
+        "queue_1m": lambda: _plan(P.harris(), 1 << 20, 1 << 20, params=[dict(tile_h=8, flags=wt.WT_FLAG_TILE_QUEUE)]),
+        "otptb_tall": lambda: _plan(P.harris(), 1 << 20, 1 << 22,
+                                    params=[dict(tile_h=32, warps_per_block=16, vec=1, flags=wt.WT_FLAG_OTPTB)]),
+        "plain_tall": lambda: _plan(P.harris(), 2, 1 << 17, exec_mode=wt.WT_EXEC_PLAIN),
+        "down_tall": lambda: _plan(P.blend(), 2, 1 << 30, wt.WT_BF16, *P.blend_schedule()),
+    }
+    with pytest.raises(wt.WtError, match=msg) as e:
+        runs[case]()
+    assert e.value.code == wt.WT_EUNSUPPORTED
