@@ -327,7 +327,13 @@ wt_status wt_cost_weights(const double *set7, double *get7);
  * `stream`.  The intermediates, the side streams and their events belong to
  * the pipeline, so runs of one pipeline must not overlap on the GPU (issue
  * them on one stream, or order their streams); separate pipelines may run
- * at the same time.  Device-side failures are reported by wt_check().     */
+ * at the same time.  Device-side failures are reported by wt_check().
+ * Size limits (WT_EUNSUPPORTED when exceeded, before any launch): a fused
+ * warp-tile group at most 2^30 tiles (a batch: 2^30 over all its images);
+ * a block-tile group at most 65535 rows of tiles; per-stage and
+ * reduction-chain kernels at most 65535 rows of the image they write;
+ * down-sampling and cascade kernels at most 65535 row blocks; every kernel
+ * at most 65535 planes.                                                    */
 wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                  const wt_image *outputs, int32_t n_outputs, void *stream);
 
