@@ -332,8 +332,8 @@ wt_status wt_cost_weights(const double *set7, double *get7);
  * warp-tile group at most 2^30 tiles (a batch: 2^30 over all its images);
  * a block-tile group at most 65535 rows of tiles; per-stage and
  * reduction-chain kernels at most 65535 rows of the image they write;
- * down-sampling and cascade kernels at most 65535 row blocks; every kernel
- * at most 65535 planes.                                                    */
+ * down-sampling and cascade kernels at most 65535 row blocks; block-tile,
+ * per-stage, down-sampling and cascade kernels at most 65535 planes.      */
 wt_status wt_run(wt_pipeline *p, const wt_image *inputs, int32_t n_inputs,
                  const wt_image *outputs, int32_t n_outputs, void *stream);
 
