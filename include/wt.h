@@ -220,7 +220,8 @@ typedef struct {
                                     every group a contiguous run of stages   */
   const wt_group_params *params; /* FUSED: n_groups entries (NULL: defaults) */
   int32_t intermediate_dtype;    /* storage of HBM intermediates (wt_dtype);
-                                    -1 = dtype of the first input           */
+                                    -1: FP32 for WT_EXEC_PLAIN (the unfused
+                                    baseline), else the first input's dtype */
 } wt_schedule_desc;
 
 /* Installs an explicit schedule.  Groups whose taps change level are run

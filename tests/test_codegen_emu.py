@@ -14,12 +14,13 @@ from emu import emu
 
 
 def run_emulated(spec, imgs, dtype=wt.WT_F32, groups=None, params=None, exec_mode=wt.WT_EXEC_FUSED,
-                 launch=0, max_blocks=None):
+                 launch=0, max_blocks=None, mid=-1):
+    """mid: storage type of the intermediates between launches (-1: FP32)."""
     p = wt.Pipeline(spec)
     if exec_mode == wt.WT_EXEC_PLAIN:
-        p.schedule(exec_mode=exec_mode)
+        p.schedule(exec_mode=exec_mode, intermediate_dtype=mid)
     else:
-        p.schedule(groups=groups, params=params)
+        p.schedule(groups=groups, params=params, intermediate_dtype=mid)
     shapes = O.shapes(spec["stages"], [np.zeros((c,) + imgs[0].shape[-2:]) for c in spec["inputs"]])
     ins = [emu.HostImage(c, a.shape[-2], a.shape[-1], dtype) for a, c in zip(imgs, spec["inputs"])]
     for h, a in zip(ins, imgs):
@@ -555,3 +556,22 @@ def test_row_parity_odd_tiles(mode, tile_h):
            "direct": dict(tile_h=tile_h)}[mode]
     got, _ = run_emulated(spec, [img], params=[prm], max_blocks=2 if mode == "queue" else None)
     assert np.abs(got[0] - oracle_of(spec, [img])[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["sharpen", "harris"])
+@pytest.mark.parametrize("dtype,tol", [(wt.WT_F16, 2e-3), (wt.WT_BF16, 1.6e-2)])
+@pytest.mark.parametrize("mode", ["plain", "two_groups"])
+def test_16bit_intermediates(name, dtype, tol, mode):
+    """Intermediates between launches stored in the 16-bit storage type
+    (the unfused path's storage-type variant, and groups linked through
+    the workspace), within the storage type's tolerance of the oracle."""
+    spec = P.by_name(name)
+    dn = {wt.WT_F16: "f16", wt.WT_BF16: "bf16"}[dtype]
+    img = rnd(31, 97, 45, dtype=dn)
+    ref = oracle_of(spec, [img])[0]
+    n = len(spec["stages"])
+    kw = dict(exec_mode=wt.WT_EXEC_PLAIN) if mode == "plain" else \
+        dict(groups=[0] * (n // 2) + [1] * (n - n // 2), params=[dict(tile_h=8)] * 2)
+    got, d = run_emulated(spec, [img], dtype=dtype, mid=dtype, **kw)
+    assert d["n_launches"] >= 2
+    assert np.abs(got[0] - ref).max() <= tol
