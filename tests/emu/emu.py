@@ -7,10 +7,12 @@ against wt_emu.h and executed lane by lane.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import ctypes
 import hashlib
 import os
 import subprocess
+import threading
 
 import numpy as np
 
@@ -72,7 +74,8 @@ def _runtime_object() -> str:
     return obj
 
 
-def _compile(source: str, name: str) -> ctypes.CDLL:
+def _text(source: str):
+    """(translation unit, content hash) of a generated kernel."""
     body = source.split(MARK, 1)[1]
     text = '#include "wt_emu.h"\n' + body + \
         '\nextern "C" long wt_emu_offset_err() { return (long)offsetof(WtArgs, err); }\n' + \
@@ -82,28 +85,61 @@ def _compile(source: str, name: str) -> ctypes.CDLL:
         'extern "C" long wt_emu_offset_imgtab() { return (long)offsetof(WtArgs, img_tab); }\n'
     h = hashlib.sha1((text + open(os.path.join(HERE, "wt_emu.h")).read() +
                       open(os.path.join(HERE, "emu_rt.cpp")).read()).encode()).hexdigest()[:16]
-    if h in _loaded:
-        return _loaded[h]
+    return text, h
+
+
+def _build(text: str, name: str, h: str) -> str:
+    """The shared object of one kernel, compiled unless already cached."""
     os.makedirs(CACHE, exist_ok=True)
     so = os.path.join(CACHE, "%s_%s.so" % (name, h))
     if not os.path.exists(so):
         rt = _runtime_object()
-        # per-process file names: parallel test workers may build the same
-        # kernel at once.  -O0: the generated kernels are long and run on
-        # small images here, so optimising them costs more than it saves.
-        src = os.path.join(CACHE, "%s_%s.%d.cpp" % (name, h, os.getpid()))
+        # per-process and per-thread file names: parallel test workers may
+        # build the same kernel at once.  -O0: the generated kernels are
+        # long and run on small images here, so optimising them costs more
+        # than it saves.
+        tag = "%d.%d" % (os.getpid(), threading.get_ident())
+        src = os.path.join(CACHE, "%s_%s.%s.cpp" % (name, h, tag))
         with open(src, "w") as f:
             f.write(text)
-        tmp = so + ".%d.tmp" % os.getpid()
+        tmp = so + ".%s.tmp" % tag
         r = subprocess.run(["g++", "-O0", "-std=c++17", "-fPIC", "-shared", "-w", "-I", HERE, src, rt, "-o", tmp],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("emulator compile failed:\n" + r.stderr[-5000:])
         os.replace(tmp, so)
         os.remove(src)
-    lib = ctypes.CDLL(so)
+    return so
+
+
+def _compile(source: str, name: str) -> ctypes.CDLL:
+    text, h = _text(source)
+    if h in _loaded:
+        return _loaded[h]
+    lib = ctypes.CDLL(_build(text, name, h))
     _loaded[h] = lib
     return lib
+
+
+def precompile(pipe: "wt.Pipeline", inputs, outputs, workspace=None):
+    """Compiles every launch of the run plan at once (one g++ per kernel,
+    in parallel); run() then finds them built."""
+    ii = [x.image() for x in inputs]
+    oo = [x.image() for x in outputs]
+    ws = None if workspace is None else (workspace.ctypes.data, workspace.nbytes)
+    jobs = {}
+    for i in range(pipe.launches_per_run()):
+        try:
+            d = pipe.debug_kernel(i, ii, oo, ws)
+        except wt.WtError:
+            return  # run() reports it
+        text, h = _text(d["source"])
+        if h not in _loaded:
+            jobs[h] = (text, d["name"], h)
+    if len(jobs) > 1:
+        _runtime_object()
+        with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+            list(ex.map(lambda j: _build(*j), jobs.values()))
 
 
 def _register(lib, images, workspace=None):

@@ -82,7 +82,7 @@ def test_accepted_mutants_are_valid_for_the_oracle():
     assert seen["ok"] > 100 and seen["rejected"] > 100
 
 
-@pytest.mark.parametrize("seed", [2, 3, 14, 19, 24, 27, 38, 41, 45, 47, 68, 95, 101, 111])
+@pytest.mark.parametrize("seed", [2, 3, 14, 19, 24, 38, 45, 47, 68, 111])
 def test_accepted_mutant_kernels_match_the_oracle(seed):
     """Accepted mutants of every kind the library accepts: tap offsets,
     channels and slots, input lists, stage channel counts."""
